@@ -1,0 +1,381 @@
+"""Throughput benchmark of the GB300 LSE library.
+
+One step = one pass of the whole hot path over the benchmark scene: the
+region-based evolution (Eq. 17, prologue + `iters` fused iterations + output)
+and the edge-based one (Eq. 14: edge-indicator precompute + prologue +
+`iters` iterations + output), each through the C ABI.  The scene is the
+8192 x 8192 single-band rectangle scene (about 2000 roofs, 200 road strips,
+noise 0.05), dt = 15, sigma = 1, TS = 9, 300 iterations per term, FP32.
+Every plane is 268 MB, larger than L2, so no flush is needed between steps.
+
+Reported (one JSON line on rank 0):
+  value        Mpixel-iterations/s over all ranks, inputs resident in HBM;
+  e2e          the same with host (pinned) inputs and outputs, copies timed;
+  roofline     the fused region step kernel: algorithmic bytes per launch
+               (12 B/px: read I, read phi, write v) / its mean duration from
+               CUDA events on the library's stream, against measured HBM;
+  cpu_baseline the FP64 oracle on the host cores, on crops of the same scene.
+`--impl reference` times the FP64 oracle alone (the reference arm).
+Under torchrun each rank runs its own replica (no collective on the data
+path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LSE Mpixel-iters/s"
+UNIT = "Mpixel-iters/s"
+BYTES_PER_PX_ITER = 12            # FP32 single band: I 4 + phi 4 + v 4
+WORKLOAD = ("8192x8192 single-band rectangle scene (2000 roofs, 200 road strips, "
+            "noise 0.05); region term (Eq. 17) + edge term (Eq. 14, with g "
+            "precompute) per step; dt=15 sigma=1 TS=9; 300 iterations each; FP32")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--size", type=int, default=8192)
+    ap.add_argument("--iters", type=int, default=300)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """MAX of a scalar over ranks (identity on one rank)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def scene_inputs(size: int):
+    from paper_1409_7474_gb300 import scenes
+    sc = scenes.large_scene(size, size, n_roofs=max(1, 2000 * size * size // 8192 ** 2),
+                            n_roads=max(1, 200 * size // 8192))
+    img = sc["image"]
+    phi_r = scenes.circle_phi(size, size, radius=size / 4)
+    boxes = [(y0 - 6, x0 - 6, y1 + 6, x1 + 6) for (y0, x0, y1, x1) in sc["roof_boxes"][:200]]
+    phi_e = scenes.box_phi(size, size, boxes)
+    return img, phi_r, phi_e
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except ValueError:
+                pass
+        os.remove(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ oracle legs
+def _oracle_crop_job(args):
+    import oracle
+    img, phi_r, phi_e, iters = args
+    oracle.evolve(img, phi_r, "region", iterations=iters)
+    g = oracle.edge_indicator(img, 1.0, 9, 255.0)
+    oracle.evolve(img, phi_e, "edge", g=g, iterations=iters)
+    return img.shape[-1] * img.shape[-2] * iters * 2
+
+
+def oracle_throughput(img, phi_r, phi_e, seconds: float, crop: int = 256):
+    """Runs the FP64 oracle (unchanged) on crops of the scene in one thread per
+    host core (ctypes releases the GIL) for about `seconds`; Mpixel-iters/s."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    H, W = img.shape[-2:]
+    r = np.random.default_rng(0)
+    crops = []
+    for k in range(cores):
+        y = int(r.integers(0, H - crop + 1))
+        x = int(r.integers(0, W - crop + 1))
+        crops.append((np.ascontiguousarray(img[:, y:y + crop, x:x + crop]),
+                      np.ascontiguousarray(phi_r[y:y + crop, x:x + crop]),
+                      np.ascontiguousarray(phi_e[y:y + crop, x:x + crop])))
+    t = time.perf_counter()
+    _oracle_crop_job(crops[0] + (2,))
+    per_iter = (time.perf_counter() - t) / 2
+    iters = max(2, int(seconds / max(per_iter, 1e-6)))
+    t = time.perf_counter()
+    with cf.ThreadPoolExecutor(cores) as ex:
+        work = sum(ex.map(_oracle_crop_job, [c + (iters,) for c in crops]))
+    wall = time.perf_counter() - t
+    return {"value": work / wall / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} crops of {crop}x{crop} px of the benchmark scene, "
+                      f"region + edge term, {iters} iterations each, FP64, one thread "
+                      f"per crop"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    img, phi_r, phi_e = scene_inputs(args.size)
+    cores = os.cpu_count() or 1
+    # the whole run stays near two minutes: each step is a bounded sample
+    per_step_seconds = min(20.0, max(2.0, 120.0 / max(args.steps + args.warmup, 1)))
+    for _ in range(args.warmup):
+        oracle_throughput(img, phi_r, phi_e, seconds=min(per_step_seconds, 3.0))
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_throughput(img, phi_r, phi_e, seconds=per_step_seconds))
+    wall = time.perf_counter() - t0
+    value = statistics.mean(v["value"] for v in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": wall * 1e3 / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "size": args.size},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": vals[0]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def kernel_profile(size: int):
+    """DRAM traffic per launch of the region step kernel from a committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "step_tma_region_traffic.json")
+    src = os.path.join(ROOT, "paper_1409_7474_gb300", "csrc", "lse_step_tma.cu")
+    try:
+        prof = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if prof.get("kernel_sha256_16") != digest:
+        return None
+    per_px = prof["dram_bytes_per_launch"] / prof["pixels"]
+    return per_px * size * size
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    import paper_1409_7474_gb300.lse as lse
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    size, iters = args.size, args.iters
+    img, phi_r, phi_e = scene_inputs(size)
+    npx = size * size
+    px_iters_per_step = npx * iters * 2
+
+    ctx_r = lse.Context(local, max_pixels=npx, max_bands=1)
+    ctx_e = lse.Context(local, max_pixels=npx, max_bands=1)
+    x = torch.from_numpy(img).to(dev)
+    pr = torch.from_numpy(phi_r).to(dev)
+    pe = torch.from_numpy(phi_e).to(dev)
+    out_r = torch.empty((size, size), dtype=torch.float32, device=dev)
+    mask_r = torch.empty((size, size), dtype=torch.uint8, device=dev)
+    out_e = torch.empty_like(out_r)
+    mask_e = torch.empty_like(mask_r)
+    g = torch.empty_like(out_r)
+    stream = torch.cuda.current_stream(dev)
+    common = dict(dt=15.0, sigma=1.0, ts=9, iterations=iters, sync=False)
+
+    def step():
+        ctx_r.evolve(x, pr, "region", phi_out=out_r, mask_out=mask_r, **common)
+        ctx_e.precompute_edge(x, 1.0, 9, 255.0, out=g)
+        ctx_e.evolve(None, pe, "edge", g=g, phi_out=out_e, mask_out=mask_e, **common)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms_r, step_ms_e = [], []
+    with ClockSampler(local) as clocks:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for _ in range(args.steps):
+            step()
+            torch.cuda.synchronize()      # makes the library's loop events readable
+            step_ms_r.append(ctx_r.stats()["elapsed_ms"])
+            step_ms_e.append(ctx_e.stats()["elapsed_ms"])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
+    st_r, st_e = ctx_r.stats(), ctx_e.stats()
+    value = world * px_iters_per_step * args.steps / (ms / 1e3) / 1e6
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    step_kernel_ms = statistics.mean(step_ms_r) / iters
+    alg_bytes = BYTES_PER_PX_ITER * npx
+    achieved = alg_bytes / (step_kernel_ms / 1e3) / 1e9
+    edge_kernel_ms = statistics.mean(step_ms_e) / iters
+    traffic = kernel_profile(size)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "step_tma_kernel<region, r=4>", "peak_source": peak_src,
+                "bytes_per_launch": alg_bytes, "mean_launch_ms": step_kernel_ms,
+                "edge_kernel_frac": alg_bytes / (edge_kernel_ms / 1e3) / 1e9 / peak}
+
+    # e2e: host (pinned) buffers through the same C ABI, copies inside the timing
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.from_numpy(img).pin_memory()
+        hpr = torch.from_numpy(phi_r).pin_memory()
+        hpe = torch.from_numpy(phi_e).pin_memory()
+        ho_r = torch.empty((size, size), dtype=torch.float32).pin_memory()
+        hm_r = torch.empty((size, size), dtype=torch.uint8).pin_memory()
+        ho_e = torch.empty_like(ho_r).pin_memory()
+        hm_e = torch.empty_like(hm_r).pin_memory()
+        hg = torch.empty_like(ho_r).pin_memory()
+
+        def step_host():
+            ctx_r.evolve(hx, hpr, "region", phi_out=ho_r, mask_out=hm_r, **common)
+            ctx_e.precompute_edge(hx, 1.0, 9, 255.0, out=hg)
+            ctx_e.evolve(None, hpe, "edge", g=hg, phi_out=ho_e, mask_out=hm_e, **common)
+
+        step_host()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_host()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        plane = npx * 4
+        e2e = {"value": world * px_iters_per_step * args.steps / (ems / 1e3) / 1e6,
+               "unit": UNIT,
+               # image (region), phi0 (region), image (edge precompute), g, phi0 (edge)
+               "h2d_bytes_per_step": 5 * plane,
+               # v + mask (region), g, v + mask (edge)
+               "d2h_bytes_per_step": 3 * plane + 2 * npx}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_throughput(img, phi_r, phi_e, seconds=args.cpu_seconds)
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        launches = args.steps * (2 * (iters + 2) + 1)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "size": size, "iterations": iters,
+                           "l2": "inputs larger than L2 (268 MB per plane), no flush",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks.summary(), "gpu_launches": launches,
+                "impl": "gb300",
+                "stats": {"region": {k: st_r[k] for k in ("iterations_run", "status",
+                                                          "last_flips", "area_plus")},
+                          "edge": {k: st_e[k] for k in ("iterations_run", "status",
+                                                        "last_flips", "area_plus")}}}
+        print(json.dumps(line))
+    ctx_r.destroy()
+    ctx_e.destroy()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,206 @@
+/*
+ * lse.h -- C ABI of the GB300 library for the fast level set evolutions
+ * (LSE) of Li, Shi, Wang and Miao, "Extracting Man-Made Objects From Remote
+ * Sensing Images via Fast Level Set Evolutions" (arXiv 1409.7474).
+ *
+ * The library evolves a level set function (LSF) phi over an image I with
+ * either data term of the paper:
+ *   region-based (Eq. 17):  R = D / max|D|,
+ *                           D = sum_b (c+_b - c-_b)(2 I_b - c+_b - c-_b),
+ *                           c+ / c- the means of I over phi >= 0 / phi < 0
+ *                           (Eq. 15; per band for vector images);
+ *   edge-based   (Eq. 14):  R = g(I) = 1 / (1 + |grad(G_sigma1 * I)|^2).
+ * Every iteration (Table I steps 2-4, Sec. III-D Steps 2-4) applies the
+ * explicit update of Eq. 18, u = phi + dt * R * |grad phi|, then the Gaussian
+ * regularisation v = G_sigma * u that replaces curvature, then (on
+ * re-initialisation iterations) phi = +1 where v >= 0 and -1 elsewhere.
+ * Discretisation: |grad phi| by unit-spacing central differences with
+ * one-sided differences on the first/last row and column; G_sigma * u is the
+ * same-size convolution with a normalised TS x TS sampled Gaussian and zero
+ * padding outside the image.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Images are band-planar: band b, row y, column x at index (b*H + y)*W + x
+ * (B x H x W, rows contiguous, no padding).  phi, g and the outputs are
+ * H x W, row-major, float32 unless stated.
+ *
+ * Ownership: the caller owns every buffer it passes; the library reads the
+ * inputs and writes the outputs and never frees or keeps them.  A pointer
+ * may name device memory of the context's GPU or host memory (pageable or
+ * pinned); host buffers are staged through device buffers the context owns
+ * (pinned host memory gives asynchronous copies).
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream).  All device work of a call is enqueued on it in order;
+ * device outputs are valid once the stream has reached the end of the call,
+ * host outputs once the caller synchronises the stream.
+ *
+ * Errors: argument errors are returned synchronously, before anything is
+ * enqueued, and lse_last_error() describes them.  Conditions found on the
+ * device (non-finite input, a device wait that ran out, a degenerate region
+ * term) are reported in lse_stats.status after the stream is synchronised.
+ *
+ * A context serves one call at a time: calls that share a context must be
+ * ordered (the same stream, or synchronised), because they share its scratch.
+ */
+#ifndef LSE_H
+#define LSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LSE_OK = 0,
+    LSE_ERR_INVALID_ARG = 1,   /* a bad argument; nothing was enqueued */
+    LSE_ERR_OOM = 2,           /* a device or pinned allocation failed */
+    LSE_ERR_CUDA = 3,          /* a CUDA call failed; see lse_last_error */
+    LSE_ERR_NONFINITE = 4,     /* NaN or Inf in image, phi0 or g (device-side) */
+    LSE_ERR_TIMEOUT = 5,       /* a bounded device wait ran out (device-side) */
+    LSE_WARN_DEGENERATE = 6    /* some iteration ran with R = 0 (see lse_params) */
+} lse_status;
+
+typedef enum {
+    LSE_TERM_REGION = 0,       /* R_Td of Eq. 17 */
+    LSE_TERM_EDGE = 1          /* E_Td = g(I) of Eq. 14 */
+} lse_term;
+
+typedef enum {
+    LSE_F32 = 0,               /* float32 */
+    LSE_F16 = 1,               /* IEEE half */
+    LSE_BF16 = 2,              /* bfloat16 */
+    LSE_U16 = 3                /* uint16, read as float32(value) / 65535.0f */
+} lse_dtype;
+
+/* Parameters of one evolution.
+ *   term            LSE_TERM_REGION or LSE_TERM_EDGE.
+ *   dt              time step of Eq. 18, > 0 (the paper uses 15-18; Sec. IV-D
+ *                   reports instability above 25).
+ *   sigma           standard deviation of G_sigma in Step 4 (sigma of Eq. 17,
+ *                   sigma_2 of the edge term), > 0.
+ *   ts              template size TS of G_sigma: odd, 1 <= ts <= 31 (Table III
+ *                   uses 9 and 15).
+ *   iterations      iterations to run, >= 1.
+ *   reinit_period   1: re-initialise to the binary LSF after every iteration
+ *                   (the listing); 0: never (region term only, Step 3 makes it
+ *                   optional there); k > 1: after iterations k-1, 2k-1, ...
+ *   early_stop_frac 0 disables.  Otherwise the evolution stops after the first
+ *                   iteration in which fewer than early_stop_frac * H * W pixels
+ *                   changed sign (Step 5: stop when phi stops varying).
+ *   storage         LSE_F32 (the only storage type this version accepts).
+ * Region-term degenerate rule (the paper is silent): when phi >= 0 holds
+ * nowhere or everywhere, when max_b |c+_b - c-_b| <= 1e-6 * max_b(|c+_b| +
+ * |c-_b|), or when max|D| = 0, that iteration uses R = 0 and the call ends
+ * with LSE_WARN_DEGENERATE. */
+typedef struct {
+    lse_term term;
+    float dt;
+    float sigma;
+    int ts;
+    int iterations;
+    int reinit_period;
+    float early_stop_frac;
+    lse_dtype storage;
+} lse_params;
+
+/* Result statistics of the last lse_evolve on a context.
+ *   iterations_run  iterations executed (< iterations after an early stop).
+ *   last_flips      pixels whose sign changed in the last executed iteration.
+ *   area_plus       |{v >= 0}| of the returned LSF.
+ *   c_plus/c_minus  region term: Eq. 15 means of each band over v >= 0 and
+ *                   v < 0 of the returned LSF (0 for an empty side); edge
+ *                   term: 0.
+ *   norm            region term: max|D| used by the last executed iteration
+ *                   (0 when R was 0); edge term: 0.
+ *   elapsed_ms      device time of the iteration loop (excludes staging,
+ *                   prologue and output).
+ *   status          LSE_OK, LSE_WARN_DEGENERATE, LSE_ERR_NONFINITE or
+ *                   LSE_ERR_TIMEOUT. */
+typedef struct {
+    int iterations_run;
+    long long last_flips;
+    long long area_plus;
+    double c_plus[8];
+    double c_minus[8];
+    double norm;
+    float elapsed_ms;
+    lse_status status;
+} lse_stats;
+
+typedef struct lse_ctx lse_ctx;
+
+/* Creates a context on CUDA device `device` for images of at most
+ * `max_pixels` = H*W pixels and `max_bands` bands (1..8).  Allocates the
+ * context's device scratch (ping-pong LSF buffers, staging, per-block
+ * partial sums, the device statistics record) and pinned host memory for the
+ * statistics.  Larger row pitches than planned grow the scratch on first
+ * use; that growth is refused while the stream is being captured.
+ * Returns LSE_ERR_INVALID_ARG for a NULL out-pointer, a bad device or sizes,
+ * LSE_ERR_OOM when an allocation fails; *ctx is NULL on failure.
+ * With the environment variable LSE_STEP_KERNEL=generic at creation, the
+ * context runs every iteration on the plain shared-memory step kernel
+ * instead of the TMA-streamed one (a cross-check of the two). */
+lse_status lse_create(lse_ctx **ctx, int device, size_t max_pixels,
+                      int max_bands);
+
+/* Releases everything the context owns.  The caller must have synchronised
+ * the streams of its calls first.  NULL is ignored. */
+void lse_destroy(lse_ctx *ctx);
+
+/* Message for the last error on this context ("" if none).  The string
+ * belongs to the context and lives until its next call or lse_destroy.
+ * A NULL ctx gives the message of the last failed lse_create. */
+const char *lse_last_error(const lse_ctx *ctx);
+
+/* Edge indicator g(I) of Eq. 14, computed once per image (Sec. III-D: the
+ * edge term needs the image convolved with a Gaussian, the region term does
+ * not).
+ *   image       B x H x W in `dtype` (see conventions), host or device.
+ *   sigma1, ts1 the pre-smoothing Gaussian G_sigma1 (sigma1 > 0, odd
+ *               1 <= ts1 <= 31).
+ *   edge_scale  multiplies the band mean before smoothing; 255 reproduces the
+ *               paper's 0..255 intensity scale for images in [0, 1].
+ *   g_out       H x W float32 output, host or device.
+ * Multi-band images use the equal-weight band mean (the paper converts RGB
+ * to one intensity channel and argues for intensity over spectral
+ * information, Sec. V-B).  Gradient and convolution as in the header above. */
+lse_status lse_precompute_edge(lse_ctx *ctx, const void *image,
+                               lse_dtype dtype, int H, int W, int B,
+                               float sigma1, int ts1, float edge_scale,
+                               float *g_out, void *stream);
+
+/* Runs params->iterations iterations of the LSE from phi0.
+ *   image     B x H x W in `dtype`, host or device (region term; for the edge
+ *             term only its finiteness is checked and it may be NULL).
+ *   g         H x W float32 edge indicator from lse_precompute_edge (edge
+ *             term), host or device; must be NULL for the region term.
+ *   phi0      H x W float32 initial LSF (Eq. 13: +1 in the initial region,
+ *             -1 elsewhere; any real values are accepted), host or device.
+ *   phi_out   H x W float32: the smoothed LSF v of the last executed
+ *             iteration, before its re-initialisation.
+ *   mask_out  H x W uint8 (may be NULL): 1 where v >= 0, else 0.
+ *   stats     if non-NULL, the call synchronises `stream` and fills *stats;
+ *             with NULL the call returns without waiting and lse_get_stats
+ *             reads them after the caller synchronises.
+ * B must not exceed the context's max_bands nor H*W its max_pixels. */
+lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype,
+                      int H, int W, int B, const float *g, const float *phi0,
+                      const lse_params *params, float *phi_out,
+                      uint8_t *mask_out, lse_stats *stats, void *stream);
+
+/* Statistics of the last lse_evolve on ctx.  Call after synchronising that
+ * call's stream; returns LSE_ERR_INVALID_ARG if no evolve has run yet. */
+lse_status lse_get_stats(lse_ctx *ctx, lse_stats *stats);
+
+/* Library version string, e.g. "0.1.0". */
+const char *lse_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSE_H */

@@ -1,0 +1,640 @@
+// lse_api.cu -- host side of the C ABI in include/lse.h.
+//
+// Each call validates its arguments before touching the GPU, makes the
+// context's device current (restoring the caller's afterwards), stages host
+// buffers through context-owned device memory, and enqueues everything on
+// the caller's stream:
+//   lse_evolve:  [H2D] -> convert -> prologue -> iterations x ([normaliser]
+//                -> step) -> output -> [D2H] -> D2H of the statistics record
+//   lse_precompute_edge:  [H2D] -> [convert] -> edge -> [D2H]
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "lse_internal.h"
+
+using namespace lse_detail;
+
+struct lse_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t max_pixels = 0;
+    int max_bands = 0;
+    char err[512] = {0};
+    // device scratch
+    float *phi[2] = {nullptr, nullptr};
+    size_t phi_cap = 0;              // elements per buffer
+    float *img = nullptr;
+    size_t img_cap = 0;              // elements
+    float *gbuf = nullptr;
+    size_t g_cap = 0;
+    void *raw_in = nullptr;          // host image staging (caller dtype)
+    size_t raw_cap = 0;              // bytes
+    float *phi0_st = nullptr;
+    size_t phi0_cap = 0;
+    float *g_st = nullptr;
+    size_t g_st_cap = 0;
+    float *out_phi = nullptr;
+    size_t out_cap = 0;
+    uint8_t *out_mask = nullptr;
+    size_t mask_cap = 0;
+    LsePartial *partials = nullptr;
+    int n_partials = 0;
+    LseDevState *st = nullptr;
+    LseDevState *st_host = nullptr;  // pinned mirror
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool have_stats = false;
+    bool force_generic = false;      // LSE_STEP_KERNEL=generic at creation
+};
+
+namespace {
+
+thread_local char g_create_err[512];
+
+void set_err(lse_ctx *ctx, const char *fmt, ...)
+{
+    char *buf = ctx ? ctx->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+enum PtrKind { PTR_NULL = 0, PTR_HOST = 1, PTR_DEVICE = 2, PTR_BAD = 3 };
+
+PtrKind classify(const void *p, int device)
+{
+    if (!p) return PTR_NULL;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PTR_HOST;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
+        return at.device == device ? PTR_DEVICE : PTR_BAD;
+    return PTR_HOST;
+}
+
+size_t dtype_size(int dt)
+{
+    return dt == LSE_F32 ? 4 : 2;
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+lse_status cuda_fail(lse_ctx *ctx, cudaError_t e, const char *what)
+{
+    set_err(ctx, "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LSE_ERR_OOM : LSE_ERR_CUDA;
+}
+
+// Grows a device buffer to at least `bytes`; refuses while capturing.
+lse_status ensure(lse_ctx *ctx, void **p, size_t *cap, size_t bytes,
+                  cudaStream_t s, const char *name)
+{
+    if (*cap >= bytes && *p) return LSE_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+        cs != cudaStreamCaptureStatusNone) {
+        set_err(ctx, "buffer '%s' must grow to %zu bytes while the stream is "
+                     "being captured; run one call of this shape uncaptured first",
+                name, bytes);
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (*p) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise before growing scratch");
+        cudaFree(*p);
+        *p = nullptr;
+        *cap = 0;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        set_err(ctx, "cudaMalloc of %zu bytes for '%s' failed", bytes, name);
+        return LSE_ERR_OOM;
+    }
+    *cap = bytes;
+    return LSE_OK;
+}
+
+template <typename T>
+lse_status ensure_t(lse_ctx *ctx, T **p, size_t *cap_elems, size_t elems,
+                    cudaStream_t s, const char *name)
+{
+    size_t cap_bytes = *cap_elems * sizeof(T);
+    void *vp = *p;
+    lse_status r = ensure(ctx, &vp, &cap_bytes, elems * sizeof(T), s, name);
+    *p = static_cast<T *>(vp);
+    *cap_elems = cap_bytes / sizeof(T);
+    return r;
+}
+
+void gauss_taps(double sigma, int rad, double *out)
+{
+    double total = 0.0;
+    for (int k = 0; k <= rad; ++k) {
+        out[k] = exp(-(double)(k * k) / (2.0 * sigma * sigma));
+        total += k == 0 ? out[k] : 2.0 * out[k];
+    }
+    for (int k = 0; k <= rad; ++k) out[k] /= total;
+}
+
+bool reinit_after(int n, int period)
+{
+    if (period == 1) return true;
+    if (period <= 0) return false;
+    return ((n + 1) % period) == 0;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
+                                  void *, const cuuint64_t *, const cuuint64_t *,
+                                  const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// Row tensor map over a pitched float32 array of `bands` planes.
+bool encode_rows(CUtensorMap *m, const float *base, int W, int H, int pitch,
+                 size_t band_stride, int bands, int box_w)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)bands};
+    cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)band_stride * 4};
+    cuuint32_t box[3] = {(cuuint32_t)box_w, 1, (cuuint32_t)bands};
+    cuuint32_t es[3] = {1, 1, 1};
+    const cuuint32_t rank = bands > 1 ? 3 : 2;
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, (void *)base, dims,
+                    strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+lse_status check_image_args(lse_ctx *ctx, lse_dtype dtype, int H, int W, int B)
+{
+    if (H < 1 || W < 1) {
+        set_err(ctx, "H and W must be >= 1 (got %d x %d)", H, W);
+        return LSE_ERR_INVALID_ARG;
+    }
+    if ((size_t)H * (size_t)W > ctx->max_pixels) {
+        set_err(ctx, "H*W = %zu exceeds the context's max_pixels %zu",
+                (size_t)H * W, ctx->max_pixels);
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (B < 1 || B > ctx->max_bands) {
+        set_err(ctx, "B = %d outside 1..%d (context max_bands)", B, ctx->max_bands);
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (dtype < LSE_F32 || dtype > LSE_U16) {
+        set_err(ctx, "unknown image dtype %d", (int)dtype);
+        return LSE_ERR_INVALID_ARG;
+    }
+    return LSE_OK;
+}
+
+// Grows both LSF buffers to `elems` elements each.
+lse_status ensure_phi(lse_ctx *ctx, size_t elems, cudaStream_t s)
+{
+    if (ctx->phi_cap >= elems && ctx->phi[0] && ctx->phi[1]) return LSE_OK;
+    size_t c0 = ctx->phi_cap * 4, c1 = ctx->phi_cap * 4;
+    void *p0 = ctx->phi[0], *p1 = ctx->phi[1];
+    lse_status r = ensure(ctx, &p0, &c0, elems * 4, s, "lsf");
+    ctx->phi[0] = static_cast<float *>(p0);
+    if (r == LSE_OK) r = ensure(ctx, &p1, &c1, elems * 4, s, "lsf");
+    ctx->phi[1] = static_cast<float *>(p1);
+    ctx->phi_cap = (r == LSE_OK) ? elems : 0;
+    return r;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// Makes `image` available as pitched float32 on the device.
+lse_status stage_image(lse_ctx *ctx, const void *image, PtrKind kind,
+                       lse_dtype dtype, int H, int W, int B, cudaStream_t s,
+                       const float **img_out, int *pitch_out, size_t *band_stride)
+{
+    if (kind == PTR_DEVICE && dtype == LSE_F32 && (W % 4) == 0 && aligned16(image)) {
+        *img_out = static_cast<const float *>(image);
+        *pitch_out = W;
+        *band_stride = (size_t)H * W;
+        return LSE_OK;
+    }
+    const void *src = image;
+    lse_status r;
+    if (kind == PTR_HOST) {
+        size_t bytes = (size_t)B * H * W * dtype_size(dtype);
+        if ((r = ensure(ctx, &ctx->raw_in, &ctx->raw_cap, bytes, s, "image staging")) != LSE_OK)
+            return r;
+        cudaError_t e = cudaMemcpyAsync(ctx->raw_in, image, bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy image to device");
+        src = ctx->raw_in;
+    }
+    const int pitch = round_up(W, 32);
+    if ((r = ensure_t(ctx, &ctx->img, &ctx->img_cap, (size_t)B * H * pitch, s, "image")) != LSE_OK)
+        return r;
+    cudaError_t e = launch_convert(src, dtype, H, W, B, ctx->img, pitch, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "convert image");
+    *img_out = ctx->img;
+    *pitch_out = pitch;
+    *band_stride = (size_t)H * pitch;
+    return LSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lse_version(void) { return "0.1.0"; }
+
+const char *lse_last_error(const lse_ctx *ctx)
+{
+    return ctx ? ctx->err : g_create_err;
+}
+
+void lse_destroy(lse_ctx *ctx)
+{
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    void *bufs[] = {ctx->phi[0], ctx->phi[1], ctx->img, ctx->gbuf, ctx->raw_in,
+                    ctx->phi0_st, ctx->g_st, ctx->out_phi, ctx->out_mask,
+                    ctx->partials, ctx->st};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (ctx->st_host) cudaFreeHost(ctx->st_host);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+}
+
+lse_status lse_create(lse_ctx **out, int device, size_t max_pixels, int max_bands)
+{
+    if (!out) {
+        set_err(nullptr, "lse_create: ctx out-pointer is NULL");
+        return LSE_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (max_pixels < 1 || max_bands < 1 || max_bands > LSE_MAXB) {
+        set_err(nullptr, "lse_create: need max_pixels >= 1 and 1 <= max_bands <= %d",
+                LSE_MAXB);
+        return LSE_ERR_INVALID_ARG;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        set_err(nullptr, "lse_create: device %d not available (%d devices)", device, ndev);
+        return LSE_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(device);
+    if (!g.ok) {
+        set_err(nullptr, "lse_create: cannot make device %d current", device);
+        return LSE_ERR_CUDA;
+    }
+    lse_ctx *ctx = new lse_ctx();
+    ctx->device = device;
+    ctx->max_pixels = max_pixels;
+    ctx->max_bands = max_bands;
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    ctx->n_partials = partials_needed(ctx->sm_count);
+    const char *kern = getenv("LSE_STEP_KERNEL");
+    ctx->force_generic = kern && strcmp(kern, "generic") == 0;
+    cudaError_t e = cudaMalloc(&ctx->partials, sizeof(LsePartial) * ctx->n_partials);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->st, sizeof(LseDevState));
+    if (e == cudaSuccess) e = cudaMemset(ctx->st, 0, sizeof(LseDevState));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->st_host, sizeof(LseDevState));
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+    if (e == cudaSuccess) {
+        // plan for a square image of max_pixels; other shapes grow on demand
+        size_t side = (size_t)ceil(sqrt((double)max_pixels));
+        size_t pitch = (side + 31) / 32 * 32;
+        size_t elems = side * pitch;
+        if (elems < max_pixels) elems = max_pixels;
+        e = cudaMalloc(&ctx->phi[0], elems * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->phi[1], elems * 4);
+        if (e == cudaSuccess) ctx->phi_cap = elems;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_err(nullptr, "lse_create: allocation failed: %s", cudaGetErrorString(e));
+        lse_destroy(ctx);
+        return LSE_ERR_OOM;
+    }
+    *out = ctx;
+    return LSE_OK;
+}
+
+lse_status lse_get_stats(lse_ctx *ctx, lse_stats *stats)
+{
+    if (!ctx || !stats) return LSE_ERR_INVALID_ARG;
+    if (!ctx->have_stats) {
+        set_err(ctx, "no lse_evolve has run on this context");
+        return LSE_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    const LseDevState &h = *ctx->st_host;
+    memset(stats, 0, sizeof(*stats));
+    stats->iterations_run = h.iterations_run;
+    stats->last_flips = h.last_flips;
+    stats->area_plus = h.area_plus;
+    for (int b = 0; b < 8; ++b) {
+        stats->c_plus[b] = h.c_plus[b];
+        stats->c_minus[b] = h.c_minus[b];
+    }
+    stats->norm = h.norm_used;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        ms = -1.0f;
+    }
+    stats->elapsed_ms = ms;
+    if (h.status_bits & LSE_SBIT_NONFINITE) stats->status = LSE_ERR_NONFINITE;
+    else if (h.status_bits & LSE_SBIT_TIMEOUT) stats->status = LSE_ERR_TIMEOUT;
+    else if (h.status_bits & LSE_SBIT_DEGENERATE) stats->status = LSE_WARN_DEGENERATE;
+    else stats->status = LSE_OK;
+    return LSE_OK;
+}
+
+lse_status lse_precompute_edge(lse_ctx *ctx, const void *image, lse_dtype dtype,
+                               int H, int W, int B, float sigma1, int ts1,
+                               float edge_scale, float *g_out, void *stream)
+{
+    if (!ctx) return LSE_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
+    lse_status r = check_image_args(ctx, dtype, H, W, B);
+    if (r != LSE_OK) return r;
+    if (!image || !g_out) {
+        set_err(ctx, "image and g_out must not be NULL");
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (!(sigma1 > 0.0f) || !isfinite(sigma1) || ts1 < 1 || ts1 > 31 || (ts1 % 2) == 0) {
+        set_err(ctx, "need sigma1 > 0 and odd 1 <= ts1 <= 31 (got %g, %d)", sigma1, ts1);
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (!isfinite(edge_scale)) {
+        set_err(ctx, "edge_scale must be finite");
+        return LSE_ERR_INVALID_ARG;
+    }
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return cuda_fail(ctx, cudaErrorInvalidDevice, "set device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PtrKind ki = classify(image, ctx->device), ko = classify(g_out, ctx->device);
+    if (ki == PTR_BAD || ko == PTR_BAD) {
+        set_err(ctx, "a device pointer belongs to another GPU than the context's");
+        return LSE_ERR_INVALID_ARG;
+    }
+    const float *img;
+    int pitch;
+    size_t band_stride;
+    if ((r = stage_image(ctx, image, ki, dtype, H, W, B, s, &img, &pitch, &band_stride)) != LSE_OK)
+        return r;
+    float *dst = g_out;
+    if (ko == PTR_HOST) {
+        if ((r = ensure_t(ctx, &ctx->out_phi, &ctx->out_cap, (size_t)H * W, s, "output staging")) != LSE_OK)
+            return r;
+        dst = ctx->out_phi;
+    }
+    const int rad1 = (ts1 - 1) / 2;
+    double taps[16];
+    gauss_taps(sigma1, rad1, taps);
+    cudaError_t e = launch_edge(img, pitch, band_stride, H, W, B, taps, rad1,
+                                (double)edge_scale, dst, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "edge kernel");
+    if (ko == PTR_HOST) {
+        e = cudaMemcpyAsync(g_out, dst, (size_t)H * W * 4, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy g to host");
+    }
+    return LSE_OK;
+}
+
+lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
+                      int W, int B, const float *g, const float *phi0,
+                      const lse_params *params, float *phi_out, uint8_t *mask_out,
+                      lse_stats *stats, void *stream)
+{
+    if (!ctx) return LSE_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (!params) {
+        set_err(ctx, "params must not be NULL");
+        return LSE_ERR_INVALID_ARG;
+    }
+    const lse_params p = *params;
+    lse_status r = check_image_args(ctx, dtype, H, W, B);
+    if (r != LSE_OK) return r;
+    if (p.term != LSE_TERM_REGION && p.term != LSE_TERM_EDGE) {
+        set_err(ctx, "unknown term %d", (int)p.term);
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (!(p.dt > 0.0f) || !isfinite(p.dt) || !(p.sigma > 0.0f) || !isfinite(p.sigma)) {
+        set_err(ctx, "need finite dt > 0 and sigma > 0 (got %g, %g)", p.dt, p.sigma);
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (p.ts < 1 || p.ts > 31 || (p.ts % 2) == 0) {
+        set_err(ctx, "ts must be odd and in 1..31 (got %d)", p.ts);
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (p.iterations < 1 || p.reinit_period < 0) {
+        set_err(ctx, "need iterations >= 1 and reinit_period >= 0");
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (!(p.early_stop_frac >= 0.0f) || !(p.early_stop_frac < 1.0f)) {
+        set_err(ctx, "early_stop_frac must be in [0, 1)");
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (p.storage != LSE_F32) {
+        set_err(ctx, "storage %d is not supported by this version (use LSE_F32)",
+                (int)p.storage);
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (p.term == LSE_TERM_EDGE && p.reinit_period != 1) {
+        set_err(ctx, "the edge term needs reinit_period = 1 (Step 3: without "
+                     "re-initialisation its LSF only grows)");
+        return LSE_ERR_INVALID_ARG;
+    }
+    const bool region = p.term == LSE_TERM_REGION;
+    if (!phi0 || !phi_out || (region && !image) || (!region && !g) || (region && g)) {
+        set_err(ctx, "need phi0, phi_out, image (region) or g (edge); g must be "
+                     "NULL for the region term");
+        return LSE_ERR_INVALID_ARG;
+    }
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return cuda_fail(ctx, cudaErrorInvalidDevice, "set device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const PtrKind ki = classify(image, ctx->device), kg = classify(g, ctx->device),
+                  kp = classify(phi0, ctx->device), ko = classify(phi_out, ctx->device),
+                  km = classify(mask_out, ctx->device);
+    if (ki == PTR_BAD || kg == PTR_BAD || kp == PTR_BAD || ko == PTR_BAD || km == PTR_BAD) {
+        set_err(ctx, "a device pointer belongs to another GPU than the context's");
+        return LSE_ERR_INVALID_ARG;
+    }
+    cudaError_t e;
+
+    // data term on the device: image bands (region) or g (edge)
+    const float *data = nullptr;
+    int pitch = 0;
+    size_t band_stride = 0;
+    const float *g_src = nullptr;
+    int g_src_pitch = W;
+    float *g_dst = nullptr;
+    if (region) {
+        if ((r = stage_image(ctx, image, ki, dtype, H, W, B, s, &data, &pitch, &band_stride)) != LSE_OK)
+            return r;
+    } else {
+        g_src = g;
+        if (kg == PTR_HOST) {
+            if ((r = ensure_t(ctx, &ctx->g_st, &ctx->g_st_cap, (size_t)H * W, s, "g staging")) != LSE_OK)
+                return r;
+            e = cudaMemcpyAsync(ctx->g_st, g, (size_t)H * W * 4, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "copy g to device");
+            g_src = ctx->g_st;
+        }
+        if (kg == PTR_DEVICE && (W % 4) == 0 && aligned16(g)) {
+            data = g;
+            pitch = W;
+        } else {
+            pitch = round_up(W, 32);
+            if ((r = ensure_t(ctx, &ctx->gbuf, &ctx->g_cap, (size_t)H * pitch, s, "g")) != LSE_OK)
+                return r;
+            g_dst = ctx->gbuf;
+            data = ctx->gbuf;
+        }
+        band_stride = (size_t)H * pitch;
+    }
+    // LSF ping-pong buffers share the data term's pitch
+    if ((r = ensure_phi(ctx, (size_t)H * pitch, s)) != LSE_OK) return r;
+    const float *phi0_src = phi0;
+    if (kp == PTR_HOST) {
+        if ((r = ensure_t(ctx, &ctx->phi0_st, &ctx->phi0_cap, (size_t)H * W, s, "phi0 staging")) != LSE_OK)
+            return r;
+        e = cudaMemcpyAsync(ctx->phi0_st, phi0, (size_t)H * W * 4, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy phi0 to device");
+        phi0_src = ctx->phi0_st;
+    }
+    float *out_phi = phi_out;
+    uint8_t *out_mask = mask_out;
+    if (ko == PTR_HOST) {
+        if ((r = ensure_t(ctx, &ctx->out_phi, &ctx->out_cap, (size_t)H * W, s, "output staging")) != LSE_OK)
+            return r;
+        out_phi = ctx->out_phi;
+    }
+    if (km == PTR_HOST) {
+        if ((r = ensure_t(ctx, &ctx->out_mask, &ctx->mask_cap, (size_t)H * W, s, "mask staging")) != LSE_OK)
+            return r;
+        out_mask = ctx->out_mask;
+    }
+
+    const int nred = ctx->sm_count * 4;
+    e = launch_prologue(region ? data : nullptr, pitch, band_stride, phi0_src, g_src,
+                        g_src_pitch, ctx->phi[0], g_dst, pitch, H, W, B, p.term,
+                        p.dt, ctx->st, ctx->partials, nred, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "prologue");
+
+    // the step's work decomposition and tensor maps
+    StepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.H = H;
+    a.W = W;
+    a.B = region ? B : 1;
+    a.term = p.term;
+    a.rad = (p.ts - 1) / 2;
+    double taps[16];
+    gauss_taps(p.sigma, a.rad, taps);
+    for (int k = 0; k < 16; ++k) a.taps[k] = k <= a.rad ? (float)taps[k] : 0.0f;
+    a.dt = p.dt;
+    a.half_dt = 0.5f * p.dt;
+    a.early_thresh = p.early_stop_frac > 0.0f ? (double)p.early_stop_frac * H * W : 0.0;
+    a.npix = (long long)H * W;
+    a.pitch = pitch;
+    a.band_stride = band_stride;
+    a.data = data;
+    a.st = ctx->st;
+    a.partials = ctx->partials;
+    int nblocks = 0, wpc = 0;
+    bool use_tma = !ctx->force_generic &&
+                   plan_step_tma(H, W, a.B, p.term, a.rad, ctx->sm_count, &a, &nblocks, &wpc);
+    CUtensorMap phi_maps[2], data_map;
+    if (use_tma) {
+        use_tma = encode_rows(&phi_maps[0], ctx->phi[0], W, H, pitch, 0, 1, 136) &&
+                  encode_rows(&phi_maps[1], ctx->phi[1], W, H, pitch, 0, 1, 136) &&
+                  encode_rows(&data_map, data, W, H, pitch, band_stride, a.B, 128);
+    }
+    if (!use_tma) nblocks = ctx->sm_count * 4;
+
+    e = cudaEventRecord(ctx->ev0, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
+    for (int n = 0; n < p.iterations; ++n) {
+        if (region && B > 1) {
+            e = launch_normaliser(data, pitch, band_stride, H, W, B, p.dt, ctx->st,
+                                  ctx->partials, nred, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "normaliser");
+        }
+        a.iter = n;
+        a.phi_in = ctx->phi[n & 1];
+        a.phi_out = ctx->phi[(n + 1) & 1];
+        a.out_buf = (n + 1) & 1;
+        a.binarise_in = (n > 0 && reinit_after(n - 1, p.reinit_period)) ? 1 : 0;
+        if (use_tma)
+            e = launch_step_tma(a, phi_maps[n & 1], data_map, nblocks, wpc, s);
+        else
+            e = launch_step_generic(a, nblocks, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "step");
+    }
+    e = cudaEventRecord(ctx->ev1, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
+    e = launch_output(ctx->phi, pitch, H, W, ctx->st, out_phi, out_mask, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "output");
+    if (ko == PTR_HOST) {
+        e = cudaMemcpyAsync(phi_out, out_phi, (size_t)H * W * 4, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy phi to host");
+    }
+    if (km == PTR_HOST) {
+        e = cudaMemcpyAsync(mask_out, out_mask, (size_t)H * W, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy mask to host");
+    }
+    e = cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(LseDevState), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy statistics");
+    ctx->have_stats = true;
+    if (stats) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
+        return lse_get_stats(ctx, stats);
+    }
+    return LSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// lse_edge.cu -- edge indicator g(I) = 1 / (1 + |grad(G_sigma1 * J)|^2) of
+// Eq. 14, computed once per image, J = edge_scale * (band mean of I).
+//
+// One CTA per 32 x 32 output tile.  J is staged with a (r1 + 1) halo (zero
+// outside the image: the 'same' convolution's padding), smoothed separably
+// (rows, then columns) on the tile plus a one-pixel ring, and differentiated
+// with central differences, one-sided on the first/last row and column.
+//
+// The arithmetic is FP64.  g enters every iteration as dt * g * |grad phi|,
+// so an error of e in g moves the LSF by up to ~20 e; keeping the LSF within
+// 1e-5 of the FP64 reference needs g to ~5e-7, which FP32 cannot deliver for
+// differences of smoothed intensities near 100.  The kernel runs once per
+// image, so FP64 costs little; g is rounded to FP32 on store.
+#include "lse_internal.h"
+
+namespace {
+
+constexpr int kTile = 32;
+constexpr int kThreads = 256;
+
+struct Taps64 {
+    double t[16];
+};
+
+__global__ void __launch_bounds__(kThreads)
+edge_kernel(const float *__restrict__ img, int pitch, size_t band_stride,
+            int H, int W, int B, Taps64 taps, int r1, double edge_scale,
+            float *__restrict__ g_out)
+{
+    extern __shared__ double smem[];
+    const int JN = kTile + 2 * r1 + 2;     // staged J rows / cols
+    const int SN = kTile + 2;              // S rows / cols (tile + 1 ring)
+    double *J = smem;                      // JN x JN
+    double *Hh = J + JN * JN;              // JN x SN
+    double *S = Hh + JN * SN;              // SN x SN
+    const int x0 = blockIdx.x * kTile;
+    const int y0 = blockIdx.y * kTile;
+    const double inv_b = 1.0 / (double)B;
+
+    for (int i = threadIdx.x; i < JN * JN; i += blockDim.x) {
+        int jy = i / JN, jx = i - jy * JN;
+        int gy = y0 - 1 - r1 + jy, gx = x0 - 1 - r1 + jx;
+        double v = 0.0;
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+            const float *p = img + (size_t)gy * pitch + gx;
+            double acc = 0.0;
+            for (int b = 0; b < B; ++b) acc += (double)p[b * band_stride];
+            v = edge_scale * (acc * inv_b);
+        }
+        J[i] = v;
+    }
+    __syncthreads();
+    // rows: Hh[jy][c] = sum_k G(k) J[jy][c + r1 + k], c <-> column x0 - 1 + c
+    for (int i = threadIdx.x; i < JN * SN; i += blockDim.x) {
+        int jy = i / SN, c = i - jy * SN;
+        const double *row = J + jy * JN + c + r1;
+        double acc = taps.t[0] * row[0];
+        for (int k = 1; k <= r1; ++k) acc += taps.t[k] * (row[-k] + row[k]);
+        Hh[i] = acc;
+    }
+    __syncthreads();
+    // columns: S[r][c] = sum_k G(k) Hh[r + r1 + k][c], r <-> row y0 - 1 + r
+    for (int i = threadIdx.x; i < SN * SN; i += blockDim.x) {
+        int r = i / SN, c = i - r * SN;
+        const double *col = Hh + (r + r1) * SN + c;
+        double acc = taps.t[0] * col[0];
+        for (int k = 1; k <= r1; ++k) acc += taps.t[k] * (col[-k * SN] + col[k * SN]);
+        S[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTile * kTile; i += blockDim.x) {
+        int ty = i / kTile, tx = i - ty * kTile;
+        int y = y0 + ty, x = x0 + tx;
+        if (y >= H || x >= W) continue;
+        const double *s = S + (ty + 1) * SN + (tx + 1);
+        double sx, sy;
+        if (W == 1) sx = 0.0;
+        else if (x == 0) sx = s[1] - s[0];
+        else if (x == W - 1) sx = s[0] - s[-1];
+        else sx = 0.5 * (s[1] - s[-1]);
+        if (H == 1) sy = 0.0;
+        else if (y == 0) sy = s[SN] - s[0];
+        else if (y == H - 1) sy = s[0] - s[-SN];
+        else sy = 0.5 * (s[SN] - s[-SN]);
+        g_out[(size_t)y * W + x] = (float)(1.0 / (1.0 + sx * sx + sy * sy));
+    }
+}
+
+}  // namespace
+
+namespace lse_detail {
+
+cudaError_t launch_edge(const float *img, int pitch, size_t band_stride,
+                          int H, int W, int B, const double *taps1, int rad1,
+                          double edge_scale, float *g_out, cudaStream_t s)
+{
+    Taps64 t;
+    for (int k = 0; k < 16; ++k) t.t[k] = k <= rad1 ? taps1[k] : 0.0;
+    const int JN = kTile + 2 * rad1 + 2, SN = kTile + 2;
+    size_t smem = sizeof(double) * ((size_t)JN * JN + (size_t)JN * SN + (size_t)SN * SN);
+    cudaError_t e = cudaFuncSetAttribute(
+        edge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    if (e != cudaSuccess) return e;
+    dim3 grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile);
+    edge_kernel<<<grid, kThreads, smem, s>>>(img, pitch, band_stride, H, W, B,
+                                             t, rad1, edge_scale, g_out);
+    return cudaGetLastError();
+}
+
+}  // namespace lse_detail

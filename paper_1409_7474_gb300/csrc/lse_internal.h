@@ -1,0 +1,145 @@
+// lse_internal.h -- shared declarations of the GB300 LSE library (internal).
+//
+// Device-side state lives in one LseDevState record per context.  Every
+// kernel that reduces over the image writes one LsePartial per CTA; the last
+// CTA to finish (ticket counter) sums them in CTA order, so every reduction
+// is deterministic for a fixed launch configuration.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lse.h"
+
+#define LSE_MAXB 8
+// Relative contrast below which c+ and c- count as equal (degenerate rule).
+#define LSE_CONTRAST_TOL 1e-6
+
+// status_bits of LseDevState
+#define LSE_SBIT_NONFINITE 1u
+#define LSE_SBIT_TIMEOUT 2u
+#define LSE_SBIT_DEGENERATE 4u
+#define LSE_SBIT_ABORT (LSE_SBIT_NONFINITE | LSE_SBIT_TIMEOUT)
+
+// Bounded spin: try_wait polls on an mbarrier before a wait is declared lost.
+#define LSE_WAIT_LIMIT (1u << 24)
+
+struct alignas(16) LseDevState {
+    // constants of the call (prologue)
+    double imin, imax;          // range of band 0 (single-band normaliser)
+    long long npix;
+    // coefficients of the next step: u = phi + s' * sum_b a[b] (I_b - m[b]),
+    // with s' = 2 |grad phi| and a[b] = dt * alpha[b] / (2 M)
+    float a[LSE_MAXB];
+    float m[LSE_MAXB];
+    float af[LSE_MAXB];         // alpha[b] as float (normaliser pass)
+    double alpha[LSE_MAXB];     // 2 (c+ - c-)
+    double mid[LSE_MAXB];       // (c+ + c-) / 2
+    double c_plus[LSE_MAXB], c_minus[LSE_MAXB];
+    double norm;                // M = max|D| for the next step
+    double norm_used;           // M of the last executed step
+    long long area_plus;        // |{phi >= 0}| of the current LSF
+    long long last_flips;
+    int iterations_run;
+    int done;                   // early stop reached: later steps do nothing
+    int last_buf;               // ping-pong buffer holding the latest v
+    int zero_force;             // next step's force is zero (degenerate rule)
+    unsigned int status_bits;
+    unsigned int ticket;        // last-CTA-done counter, reset by the last CTA
+};
+
+struct alignas(16) LsePartial {
+    double sp[LSE_MAXB];        // sum of I_b over phi >= 0
+    double sm[LSE_MAXB];        // sum of I_b over phi < 0
+    long long n_plus;
+    long long flips;
+    float fmax, fmin;           // normaliser / prologue range
+    unsigned int bits;          // status bits seen by the CTA
+    int pad;
+};
+
+// Arguments common to the step kernels.
+struct StepArgs {
+    int H, W, B;
+    int term;                   // LSE_TERM_*
+    int binarise_in;            // phi_in holds v of a re-initialised step
+    int iter;                   // 0-based iteration index
+    int rad;                    // (ts - 1) / 2
+    float taps[16];             // 1-D taps G[0..rad] (symmetric)
+    float dt;                   // time step of Eq. 18
+    float half_dt;              // 0.5 * dt (edge term)
+    double early_thresh;        // stop when flips < early_thresh (<= 0: off)
+    long long npix;
+    int pitch;                  // row pitch (elements) of phi and data
+    size_t band_stride;         // elements between bands of data
+    const float *phi_in;
+    float *phi_out;
+    int out_buf;                // index of phi_out in the ping-pong pair
+    const float *data;          // image bands (region) or g (edge)
+    LseDevState *st;
+    LsePartial *partials;
+    // work decomposition of the TMA kernel
+    int useful;                 // output columns per warp strip
+    int n_strips;
+    int n_rowblocks;
+    int th;                     // output rows per item
+    int n_items;
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ float lse_sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------- host side
+namespace lse_detail {
+
+// Kernel launchers, one per translation unit.  Each returns the
+// cudaGetLastError() of its launch.
+cudaError_t launch_convert(const void *src, int dtype, int H, int W, int B,
+                           float *dst, int pitch, cudaStream_t s);
+cudaError_t launch_prologue(const float *img, int img_pitch, size_t band_stride,
+                            const float *phi0, const float *g, int g_pitch,
+                            float *phi_dst, float *g_dst, int pitch, int H,
+                            int W, int B, int term, float dt,
+                            LseDevState *st, LsePartial *partials, int nblocks,
+                            cudaStream_t s);
+cudaError_t launch_normaliser(const float *img, int pitch, size_t band_stride,
+                              int H, int W, int B, float dt, LseDevState *st,
+                              LsePartial *partials, int nblocks, cudaStream_t s);
+cudaError_t launch_output(float *const *bufs, int pitch, int H, int W,
+                          const LseDevState *st, float *phi_out,
+                          uint8_t *mask_out, cudaStream_t s);
+cudaError_t launch_edge(const float *img, int pitch, size_t band_stride, int H,
+                        int W, int B, const double *taps1, int rad1,
+                        double edge_scale, float *g_out, cudaStream_t s);
+cudaError_t launch_step_generic(const StepArgs &a, int nblocks, cudaStream_t s);
+// TMA step: returns cudaErrorNotSupported when no instantiation fits
+// (radius or band count), so the caller can take the generic kernel.
+cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap &phi_map,
+                            const CUtensorMap &data_map, int nblocks,
+                            int warps_per_block, cudaStream_t s);
+// Work decomposition of the TMA step for a shape on `sm_count` SMs.
+bool plan_step_tma(int H, int W, int B, int term, int rad, int sm_count,
+                   StepArgs *a, int *nblocks, int *warps_per_block);
+int partials_needed(int sm_count);
+
+}  // namespace lse_detail

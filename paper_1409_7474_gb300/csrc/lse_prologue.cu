@@ -1,0 +1,247 @@
+// lse_prologue.cu -- once-per-call and per-iteration helper kernels:
+//   convert     caller image (f32/f16/bf16/u16, B x H x W) -> pitched f32
+//   prologue    copies phi0 (and g) into the pitched work buffers, checks
+//               finiteness, reduces the statistics of phi0 (Eq. 15 sums,
+//               |{phi0 >= 0}|, the range of band 0) and finalises the
+//               coefficients of the first step
+//   normaliser  M = max_x |D(x)| for vector images (Eq. 17), one pass over I
+//   output      v of the last executed step -> caller's phi_out and mask
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lse_reduce.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads)
+convert_kernel(const void *__restrict__ src, int dtype, int H, int W, int B,
+               float *__restrict__ dst, int pitch)
+{
+    const long long n = (long long)B * H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long row = i / W;          // b * H + y
+        int x = (int)(i - row * W);
+        float v;
+        switch (dtype) {
+        case LSE_F16:
+            v = __half2float(static_cast<const __half *>(src)[i]);
+            break;
+        case LSE_BF16:
+            v = __bfloat162float(static_cast<const __nv_bfloat16 *>(src)[i]);
+            break;
+        case LSE_U16:
+            v = (float)static_cast<const uint16_t *>(src)[i] / 65535.0f;  // IEEE division
+            break;
+        default:
+            v = static_cast<const float *>(src)[i];
+        }
+        dst[row * pitch + x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+prologue_kernel(const float *__restrict__ img, int img_pitch, size_t band_stride,
+                const float *__restrict__ phi0, const float *__restrict__ g,
+                int g_pitch, float *__restrict__ phi_dst,
+                float *__restrict__ g_dst, int pitch, int H, int W, int B,
+                int term, float dt, LseDevState *st, LsePartial *partials)
+{
+    LseAcc acc;
+    acc.clear();
+    const long long n = (long long)H * W;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        int y = (int)(p / W);
+        int x = (int)(p - (long long)y * W);
+        float v = phi0[p];
+        if (!isfinite(v)) acc.bits |= LSE_SBIT_NONFINITE;
+        phi_dst[(size_t)y * pitch + x] = v;
+        const bool pos = v >= 0.0f;
+        acc.n_plus += pos;
+        if (term == LSE_TERM_EDGE) {
+            float gv = g[(size_t)y * g_pitch + x];
+            if (!isfinite(gv)) acc.bits |= LSE_SBIT_NONFINITE;
+            if (g_dst) g_dst[(size_t)y * pitch + x] = gv;
+        } else {
+            for (int b = 0; b < B; ++b) {
+                float iv = img[b * band_stride + (size_t)y * img_pitch + x];
+                if (!isfinite(iv)) acc.bits |= LSE_SBIT_NONFINITE;
+                if (pos) acc.sp[b] += iv;
+                else acc.sm[b] += iv;
+                if (b == 0) {
+                    acc.fmax = fmaxf(acc.fmax, iv);
+                    acc.fmin = fminf(acc.fmin, iv);
+                }
+            }
+        }
+    }
+    const int nb = term == LSE_TERM_EDGE ? 0 : B;
+    LseAcc r;
+    lse_cta_reduce(acc, nb, &r);
+    if (!lse_publish_and_ticket(r, nb, partials, st)) return;
+    LseAcc t;
+    lse_sum_partials(partials, gridDim.x, nb, &t);
+    if (threadIdx.x == 0) {
+        st->npix = n;
+        st->status_bits = t.bits;
+        st->imin = t.fmin;
+        st->imax = t.fmax;
+        st->last_flips = 0;
+        st->iterations_run = 0;
+        st->done = 0;
+        st->last_buf = 0;
+        st->norm_used = 0.0;
+        if (term == LSE_TERM_REGION) {
+            lse_region_coeffs(st, t, B, dt);
+        } else {
+            st->area_plus = t.n_plus;
+            st->zero_force = 0;
+            st->norm = 0.0;
+            for (int b = 0; b < LSE_MAXB; ++b) {
+                st->c_plus[b] = 0.0;
+                st->c_minus[b] = 0.0;
+            }
+        }
+        __threadfence();
+        st->ticket = 0;
+    }
+}
+
+// M = max_x |sum_b alpha_b (I_b(x) - mid_b)| for B > 1, then the step
+// coefficients a_b = dt alpha_b / (2 M).  Skipped when the statistics already
+// made the force zero or the evolution has stopped.
+__global__ void __launch_bounds__(kThreads)
+normaliser_kernel(const float *__restrict__ img, int pitch, size_t band_stride,
+                  int H, int W, int B, float dt, LseDevState *st,
+                  LsePartial *partials)
+{
+    if (st->done || st->zero_force || (st->status_bits & LSE_SBIT_ABORT)) return;
+    float af[LSE_MAXB], m[LSE_MAXB];
+#pragma unroll
+    for (int b = 0; b < LSE_MAXB; ++b) {
+        af[b] = st->af[b];
+        m[b] = st->m[b];
+    }
+    LseAcc acc;
+    acc.clear();
+    const long long n = (long long)H * W;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        int y = (int)(p / W);
+        int x = (int)(p - (long long)y * W);
+        const float *src = img + (size_t)y * pitch + x;
+        float d = 0.0f;
+#pragma unroll
+        for (int b = 0; b < LSE_MAXB; ++b)
+            if (b < B) d = fmaf(af[b], __ldg(src + b * band_stride) - m[b], d);
+        acc.fmax = fmaxf(acc.fmax, d);
+        acc.fmin = fminf(acc.fmin, d);
+    }
+    LseAcc r;
+    lse_cta_reduce(acc, 0, &r);
+    if (!lse_publish_and_ticket(r, 0, partials, st)) return;
+    LseAcc t;
+    lse_sum_partials(partials, gridDim.x, 0, &t);
+    if (threadIdx.x == 0) {
+        double M = fmax(fabs((double)t.fmax), fabs((double)t.fmin));
+        st->norm = M;
+        if (M > 0.0) {
+            for (int b = 0; b < LSE_MAXB; ++b)
+                st->a[b] = b < B ? (float)((double)dt * st->alpha[b] / (2.0 * M)) : 0.0f;
+        } else {
+            st->zero_force = 1;
+            for (int b = 0; b < LSE_MAXB; ++b) st->a[b] = 0.0f;
+        }
+        __threadfence();
+        st->ticket = 0;
+    }
+}
+
+struct BufPair {
+    float *b[2];
+};
+
+__global__ void __launch_bounds__(kThreads)
+output_kernel(BufPair bufs, int pitch, int H, int W, const LseDevState *st,
+              float *__restrict__ phi_out, uint8_t *__restrict__ mask_out)
+{
+    if (st->status_bits & LSE_SBIT_ABORT) return;
+    const float *src = bufs.b[st->last_buf];
+    const long long n = (long long)H * W;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        int y = (int)(p / W);
+        int x = (int)(p - (long long)y * W);
+        float v = src[(size_t)y * pitch + x];
+        phi_out[p] = v;
+        if (mask_out) mask_out[p] = v >= 0.0f ? 1 : 0;
+    }
+}
+
+int grid_for(long long n, int cap)
+{
+    long long blocks = (n + kThreads - 1) / kThreads;
+    if (blocks < 1) blocks = 1;
+    return (int)(blocks < cap ? blocks : cap);
+}
+
+}  // namespace
+
+namespace lse_detail {
+
+cudaError_t launch_convert(const void *src, int dtype, int H, int W, int B,
+                           float *dst, int pitch, cudaStream_t s)
+{
+    int grid = grid_for((long long)B * H * W, 4096);
+    convert_kernel<<<grid, kThreads, 0, s>>>(src, dtype, H, W, B, dst, pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prologue(const float *img, int img_pitch, size_t band_stride,
+                            const float *phi0, const float *g, int g_pitch,
+                            float *phi_dst, float *g_dst, int pitch, int H,
+                            int W, int B, int term, float dt,
+                            LseDevState *st, LsePartial *partials, int nblocks,
+                            cudaStream_t s)
+{
+    int grid = grid_for((long long)H * W, nblocks);
+    prologue_kernel<<<grid, kThreads, 0, s>>>(img, img_pitch, band_stride, phi0,
+                                              g, g_pitch, phi_dst, g_dst, pitch,
+                                              H, W, B, term, dt, st, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normaliser(const float *img, int pitch, size_t band_stride,
+                              int H, int W, int B, float dt, LseDevState *st,
+                              LsePartial *partials, int nblocks, cudaStream_t s)
+{
+    int grid = grid_for((long long)H * W, nblocks);
+    normaliser_kernel<<<grid, kThreads, 0, s>>>(img, pitch, band_stride, H, W,
+                                                B, dt, st, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_output(float *const *bufs, int pitch, int H, int W,
+                          const LseDevState *st, float *phi_out,
+                          uint8_t *mask_out, cudaStream_t s)
+{
+    BufPair bp;
+    bp.b[0] = bufs[0];
+    bp.b[1] = bufs[1];
+    int grid = grid_for((long long)H * W, 4096);
+    output_kernel<<<grid, kThreads, 0, s>>>(bp, pitch, H, W, st, phi_out,
+                                            mask_out);
+    return cudaGetLastError();
+}
+
+int partials_needed(int sm_count)
+{
+    // the widest reducing launch: 2 CTAs of 8 warps per SM (TMA step) or
+    // 8 CTAs of 256 threads per SM (grid-stride kernels)
+    return sm_count * 8;
+}
+
+}  // namespace lse_detail

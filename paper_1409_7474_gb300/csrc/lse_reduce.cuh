@@ -1,0 +1,213 @@
+// lse_reduce.cuh -- deterministic CTA/grid reductions and the per-iteration
+// finalisation of the region statistics (internal).
+//
+// Every reducing kernel accumulates per thread, reduces its CTA in a fixed
+// order (warp shuffles, then warps in index order), writes one LsePartial per
+// CTA, and the last CTA to take a ticket sums the partials in CTA order and
+// finalises.  The last CTA resets the ticket for the next launch.
+#pragma once
+
+#include "lse_internal.h"
+
+struct LseAcc {
+    double sp[LSE_MAXB];
+    double sm[LSE_MAXB];
+    long long n_plus;
+    long long flips;
+    float fmax, fmin;
+    unsigned int bits;
+
+    __device__ __forceinline__ void clear()
+    {
+#pragma unroll
+        for (int b = 0; b < LSE_MAXB; ++b) {
+            sp[b] = 0.0;
+            sm[b] = 0.0;
+        }
+        n_plus = 0;
+        flips = 0;
+        fmax = -INFINITY;
+        fmin = INFINITY;
+        bits = 0;
+    }
+};
+
+// Reduces `acc` over the CTA (blockDim.x a multiple of 32, <= 1024) into
+// `out` (visible to thread 0 after return).  `nb` bands are summed.
+__device__ __forceinline__ void lse_cta_reduce(const LseAcc &acc, int nb,
+                                               LseAcc *out)
+{
+    __shared__ double s_d[32][2 * LSE_MAXB];
+    __shared__ long long s_l[32][2];
+    __shared__ float s_f[32][2];
+    __shared__ unsigned int s_u[32];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+#pragma unroll
+    for (int b = 0; b < LSE_MAXB; ++b) {
+        if (b < nb) {
+            double p = warp_sum_d(acc.sp[b]);
+            double m = warp_sum_d(acc.sm[b]);
+            if (lane == 0) {
+                s_d[warp][b] = p;
+                s_d[warp][LSE_MAXB + b] = m;
+            }
+        }
+    }
+    long long np = warp_sum_ll(acc.n_plus);
+    long long fl = warp_sum_ll(acc.flips);
+    float fx = acc.fmax, fn = acc.fmin;
+    unsigned int bits = acc.bits;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fx = fmaxf(fx, __shfl_xor_sync(0xffffffffu, fx, o));
+        fn = fminf(fn, __shfl_xor_sync(0xffffffffu, fn, o));
+        bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+    }
+    if (lane == 0) {
+        s_l[warp][0] = np;
+        s_l[warp][1] = fl;
+        s_f[warp][0] = fx;
+        s_f[warp][1] = fn;
+        s_u[warp] = bits;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out->clear();
+        for (int w = 0; w < nwarps; ++w) {
+            for (int b = 0; b < nb; ++b) {
+                out->sp[b] += s_d[w][b];
+                out->sm[b] += s_d[w][LSE_MAXB + b];
+            }
+            out->n_plus += s_l[w][0];
+            out->flips += s_l[w][1];
+            out->fmax = fmaxf(out->fmax, s_f[w][0]);
+            out->fmin = fminf(out->fmin, s_f[w][1]);
+            out->bits |= s_u[w];
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void lse_store_partial(const LseAcc &r, int nb,
+                                                  LsePartial *p)
+{
+    for (int b = 0; b < LSE_MAXB; ++b) {
+        p->sp[b] = b < nb ? r.sp[b] : 0.0;
+        p->sm[b] = b < nb ? r.sm[b] : 0.0;
+    }
+    p->n_plus = r.n_plus;
+    p->flips = r.flips;
+    p->fmax = r.fmax;
+    p->fmin = r.fmin;
+    p->bits = r.bits;
+}
+
+// Writes this CTA's partial and returns true in the CTA that finished last.
+// The CTA-wide result `r` is only meaningful in thread 0.
+__device__ __forceinline__ bool lse_publish_and_ticket(const LseAcc &r, int nb,
+                                                       LsePartial *partials,
+                                                       LseDevState *st)
+{
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        lse_store_partial(r, nb, partials + blockIdx.x);
+        __threadfence();
+        unsigned int t = atomicAdd(&st->ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    bool last = s_last != 0;
+    if (last) __threadfence();
+    return last;
+}
+
+// In the last CTA: sums all partials in CTA order into `total` (thread 0).
+__device__ __forceinline__ void lse_sum_partials(const LsePartial *partials,
+                                                 int nparts, int nb,
+                                                 LseAcc *total)
+{
+    LseAcc a;
+    a.clear();
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        const LsePartial *p = partials + i;
+        for (int b = 0; b < nb; ++b) {
+            a.sp[b] += __ldcg(&p->sp[b]);
+            a.sm[b] += __ldcg(&p->sm[b]);
+        }
+        a.n_plus += __ldcg(&p->n_plus);
+        a.flips += __ldcg(&p->flips);
+        a.fmax = fmaxf(a.fmax, __ldcg(&p->fmax));
+        a.fmin = fminf(a.fmin, __ldcg(&p->fmin));
+        a.bits |= __ldcg(&p->bits);
+    }
+    lse_cta_reduce(a, nb, total);
+}
+
+// Region statistics of the current LSF -> c+/c- and the coefficients of the
+// next step (Eqs. 15 and 17).  For one band the normaliser has the closed
+// form M = |c+ - c-| max(|2 Imax - c+ - c-|, |2 Imin - c+ - c-|) (|2I - s|
+// is convex in I, so its maximum over the image sits at Imin or Imax); for
+// several bands M comes from the normaliser pass.  Thread 0 only.
+__device__ __forceinline__ void lse_region_coeffs(LseDevState *st,
+                                                  const LseAcc &t, int B,
+                                                  float dt)
+{
+    const long long N = st->npix;
+    const long long np = t.n_plus;
+    const long long nm = N - np;
+    double contrast = 0.0, scale = 0.0;
+    for (int b = 0; b < B; ++b) {
+        double cp = np > 0 ? t.sp[b] / (double)np : 0.0;
+        double cm = nm > 0 ? t.sm[b] / (double)nm : 0.0;
+        st->c_plus[b] = cp;
+        st->c_minus[b] = cm;
+        st->alpha[b] = 2.0 * (cp - cm);
+        st->mid[b] = 0.5 * (cp + cm);
+        st->af[b] = (float)st->alpha[b];
+        st->m[b] = (float)st->mid[b];
+        contrast = fmax(contrast, fabs(cp - cm));
+        scale = fmax(scale, fabs(cp) + fabs(cm));
+    }
+    st->area_plus = np;
+    int zero = (np == 0 || nm == 0 || contrast <= LSE_CONTRAST_TOL * scale);
+    st->norm = 0.0;
+    if (!zero && B == 1) {
+        double s = st->c_plus[0] + st->c_minus[0];
+        double M = fabs(st->c_plus[0] - st->c_minus[0]) *
+                   fmax(fabs(2.0 * st->imax - s), fabs(2.0 * st->imin - s));
+        if (!(M > 0.0)) {
+            zero = 1;
+        } else {
+            st->norm = M;
+            st->a[0] = (float)((double)dt * st->alpha[0] / (2.0 * M));
+        }
+    }
+    if (zero)
+        for (int b = 0; b < LSE_MAXB; ++b) st->a[b] = 0.0f;
+    st->zero_force = zero;
+}
+
+// End of one executed step (thread 0 of the last CTA): record the step,
+// then compute the statistics of the new LSF and the next step's
+// coefficients.  `t` holds the grid-wide sums over the new LSF.
+__device__ __forceinline__ void lse_step_finalize(const StepArgs &a,
+                                                  const LseAcc &t)
+{
+    LseDevState *st = a.st;
+    st->status_bits |= t.bits;
+    st->last_flips = t.flips;
+    st->iterations_run = a.iter + 1;
+    st->last_buf = a.out_buf;
+    if (a.term == LSE_TERM_REGION) {
+        if (st->zero_force) st->status_bits |= LSE_SBIT_DEGENERATE;
+        st->norm_used = st->zero_force ? 0.0 : st->norm;
+        lse_region_coeffs(st, t, a.B, a.dt);
+    } else {
+        st->area_plus = t.n_plus;
+    }
+    if (a.early_thresh > 0.0 && (double)t.flips < a.early_thresh) st->done = 1;
+    __threadfence();
+    st->ticket = 0;
+}

@@ -1,0 +1,265 @@
+"""Thin ctypes binding of the C ABI in ``include/lse.h``.
+
+Argument marshalling only: every step of the evolution runs in the CUDA
+library ``liblse.so`` built in-tree by ``paper_1409_7474_gb300._build``.  The
+binding accepts torch tensors (CUDA or CPU) and numpy arrays; CPU buffers are
+passed to the library as host pointers and staged by it.  There is no CPU
+fallback: if the library is missing this module raises on import.
+
+Names follow the C ABI: ``create``/``Context``, ``precompute_edge``,
+``evolve``, ``destroy``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+try:
+    import torch
+except ImportError:  # the binding itself only needs ctypes and numpy
+    torch = None
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblse.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with "
+        "`python -c 'import __graft_entry__ as g; g.build()'` "
+        "(the library has no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ------------------------------------------------------------------ C types
+LSE_OK = 0
+LSE_ERR_INVALID_ARG = 1
+LSE_ERR_OOM = 2
+LSE_ERR_CUDA = 3
+LSE_ERR_NONFINITE = 4
+LSE_ERR_TIMEOUT = 5
+LSE_WARN_DEGENERATE = 6
+STATUS_NAMES = {0: "LSE_OK", 1: "LSE_ERR_INVALID_ARG", 2: "LSE_ERR_OOM",
+                3: "LSE_ERR_CUDA", 4: "LSE_ERR_NONFINITE", 5: "LSE_ERR_TIMEOUT",
+                6: "LSE_WARN_DEGENERATE"}
+
+TERM_REGION = 0
+TERM_EDGE = 1
+F32, F16, BF16, U16 = 0, 1, 2, 3
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("term", ctypes.c_int), ("dt", ctypes.c_float),
+                ("sigma", ctypes.c_float), ("ts", ctypes.c_int),
+                ("iterations", ctypes.c_int), ("reinit_period", ctypes.c_int),
+                ("early_stop_frac", ctypes.c_float), ("storage", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations_run", ctypes.c_int), ("last_flips", ctypes.c_longlong),
+                ("area_plus", ctypes.c_longlong), ("c_plus", ctypes.c_double * 8),
+                ("c_minus", ctypes.c_double * 8), ("norm", ctypes.c_double),
+                ("elapsed_ms", ctypes.c_float), ("status", ctypes.c_int)]
+
+    def to_dict(self, bands: int = 8) -> dict:
+        return {"iterations_run": self.iterations_run,
+                "last_flips": self.last_flips, "area_plus": self.area_plus,
+                "c_plus": list(self.c_plus[:bands]),
+                "c_minus": list(self.c_minus[:bands]), "norm": self.norm,
+                "elapsed_ms": self.elapsed_ms,
+                "status": STATUS_NAMES.get(self.status, str(self.status))}
+
+
+_vp = ctypes.c_void_p
+_lib.lse_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int]
+_lib.lse_create.restype = ctypes.c_int
+_lib.lse_destroy.argtypes = [_vp]
+_lib.lse_destroy.restype = None
+_lib.lse_last_error.argtypes = [_vp]
+_lib.lse_last_error.restype = ctypes.c_char_p
+_lib.lse_precompute_edge.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_float, ctypes.c_int,
+                                     ctypes.c_float, _vp, _vp]
+_lib.lse_precompute_edge.restype = ctypes.c_int
+_lib.lse_evolve.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                            ctypes.c_int, _vp, _vp, ctypes.POINTER(Params), _vp, _vp,
+                            ctypes.POINTER(Stats), _vp]
+_lib.lse_evolve.restype = ctypes.c_int
+_lib.lse_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
+_lib.lse_get_stats.restype = ctypes.c_int
+_lib.lse_version.argtypes = []
+_lib.lse_version.restype = ctypes.c_char_p
+
+SYMBOLS = ("lse_create", "lse_destroy", "lse_last_error", "lse_precompute_edge",
+           "lse_evolve", "lse_get_stats", "lse_version")
+
+
+class LseError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def version() -> str:
+    return _lib.lse_version().decode()
+
+
+# ------------------------------------------------------------------ marshalling
+def _is_torch(x) -> bool:
+    return torch is not None and isinstance(x, torch.Tensor)
+
+
+def _dtype_code(x) -> int:
+    if _is_torch(x):
+        m = {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}
+        if hasattr(torch, "uint16"):
+            m[torch.uint16] = U16
+        if x.dtype not in m:
+            raise TypeError(f"unsupported image dtype {x.dtype}")
+        return m[x.dtype]
+    m = {np.dtype(np.float32): F32, np.dtype(np.float16): F16, np.dtype(np.uint16): U16}
+    if x.dtype not in m:
+        raise TypeError(f"unsupported image dtype {x.dtype}")
+    return m[x.dtype]
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("arrays must be C-contiguous")
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _shape3(image):
+    shp = tuple(image.shape)
+    if len(shp) == 2:
+        return 1, shp[0], shp[1]
+    if len(shp) == 3:
+        return shp
+    raise ValueError("image must be H x W or B x H x W")
+
+
+def _stream_ptr(stream, device: int):
+    if stream is not None:
+        return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    if torch is not None and torch.cuda.is_available():
+        return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _empty_like_place(ref, shape, np_dtype, torch_dtype):
+    if _is_torch(ref):
+        return torch.empty(shape, dtype=torch_dtype, device=ref.device,
+                           pin_memory=False)
+    return np.empty(shape, dtype=np_dtype)
+
+
+class Context:
+    """An ``lse_ctx``: device scratch for images up to ``max_pixels`` pixels
+    and ``max_bands`` bands on CUDA device ``device``."""
+
+    def __init__(self, device: int = 0, max_pixels: int = 1 << 20,
+                 max_bands: int = 4):
+        h = ctypes.c_void_p()
+        rc = _lib.lse_create(ctypes.byref(h), int(device), int(max_pixels), int(max_bands))
+        if rc != LSE_OK:
+            raise LseError(rc, _lib.lse_last_error(None).decode())
+        self._h = h
+        self.device = int(device)
+        self.max_pixels = int(max_pixels)
+        self.max_bands = int(max_bands)
+
+    # -- lifetime
+    def destroy(self):
+        if getattr(self, "_h", None):
+            _lib.lse_destroy(self._h)
+            self._h = None
+
+    close = destroy
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def _check(self, rc: int):
+        if rc != LSE_OK:
+            raise LseError(rc, _lib.lse_last_error(self._h).decode())
+
+    # -- calls
+    def precompute_edge(self, image, sigma1: float = 1.0, ts1: int = 9,
+                        edge_scale: float = 255.0, out=None, stream=None):
+        """g(I) of Eq. 14 (H x W float32), on the image's device or host."""
+        B, H, W = _shape3(image)
+        if out is None:
+            out = _empty_like_place(image, (H, W), np.float32,
+                                    torch.float32 if torch is not None else None)
+        self._check(_lib.lse_precompute_edge(
+            self._h, _ptr(image), _dtype_code(image), H, W, B, float(sigma1),
+            int(ts1), float(edge_scale), _ptr(out), _stream_ptr(stream, self.device)))
+        return out
+
+    def evolve(self, image, phi0, term: str = "region", g=None, dt: float = 15.0,
+               sigma: float = 1.0, ts: int = 9, iterations: int = 200,
+               reinit_period: int = 1, early_stop_frac: float = 0.0,
+               phi_out=None, mask_out=None, stream=None, sync: bool = True):
+        """Runs the evolution.  Returns (phi_out, mask_out, stats or None).
+
+        With ``sync`` the call waits for the stream and returns the statistics
+        dict; otherwise it returns at once and ``stats()`` reads them after the
+        caller synchronises."""
+        term_code = TERM_REGION if term in ("region", TERM_REGION) else TERM_EDGE
+        ref = image if image is not None else phi0
+        if image is not None:
+            B, H, W = _shape3(image)
+            dcode = _dtype_code(image)
+        else:
+            B, (H, W), dcode = 1, tuple(phi0.shape), F32
+        if phi_out is None:
+            phi_out = _empty_like_place(ref, (H, W), np.float32,
+                                        torch.float32 if torch is not None else None)
+        if mask_out is None:
+            mask_out = _empty_like_place(ref, (H, W), np.uint8,
+                                         torch.uint8 if torch is not None else None)
+        p = Params(term_code, float(dt), float(sigma), int(ts), int(iterations),
+                   int(reinit_period), float(early_stop_frac), F32)
+        st = Stats()
+        rc = _lib.lse_evolve(self._h, _ptr(image) if term_code == TERM_REGION else None,
+                             dcode, H, W, B,
+                             _ptr(g) if term_code == TERM_EDGE else None, _ptr(phi0),
+                             ctypes.byref(p), _ptr(phi_out), _ptr(mask_out),
+                             ctypes.byref(st) if sync else None,
+                             _stream_ptr(stream, self.device))
+        self._check(rc)
+        return phi_out, mask_out, (st.to_dict(B) if sync else None)
+
+    def stats(self, bands: int = 8) -> dict:
+        st = Stats()
+        self._check(_lib.lse_get_stats(self._h, ctypes.byref(st)))
+        return st.to_dict(bands)
+
+
+def create(device: int = 0, max_pixels: int = 1 << 20, max_bands: int = 4) -> Context:
+    return Context(device, max_pixels, max_bands)
+
+
+def destroy(ctx: Context) -> None:
+    ctx.destroy()
+
+
+def raw_library():
+    """The loaded ctypes CDLL (for tests that call the C ABI directly)."""
+    return _lib

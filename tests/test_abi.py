@@ -1,0 +1,78 @@
+"""The C-ABI library loads without a GPU, exports what include/lse.h
+declares, lays its structs out as the header does, and rejects bad
+arguments before touching a device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lse.h")
+
+
+@pytest.fixture(scope="module")
+def lse():
+    from paper_1409_7474_gb300 import _build
+    if not os.path.exists(_build.LIB):
+        _build.build()
+    import paper_1409_7474_gb300.lse as lse
+    return lse
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lse_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lse):
+    names = declared_functions()
+    assert names == sorted(lse.SYMBOLS)
+    lib = lse.raw_library()
+    for n in names:
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", lse.LIB_PATH],
+                         capture_output=True, text=True, check=True).stdout
+    for n in names:
+        assert re.search(rf"\bT {n}\b", out), n
+
+
+def test_struct_layout_matches_header(lse, tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "lse.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(lse_params),"
+        " sizeof(lse_stats), offsetof(lse_stats, c_plus), offsetof(lse_stats, norm),"
+        " offsetof(lse_stats, status));return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert vals == [ctypes.sizeof(lse.Params), ctypes.sizeof(lse.Stats),
+                    lse.Stats.c_plus.offset, lse.Stats.norm.offset,
+                    lse.Stats.status.offset]
+
+
+def test_version_and_errors_without_gpu(lse):
+    lib = lse.raw_library()
+    assert lse.version() == "0.1.0"
+    h = ctypes.c_void_p()
+    assert lib.lse_create(None, 0, 16, 1) == lse.LSE_ERR_INVALID_ARG
+    assert lib.lse_create(ctypes.byref(h), 0, 0, 1) == lse.LSE_ERR_INVALID_ARG
+    assert lib.lse_create(ctypes.byref(h), 0, 16, 9) == lse.LSE_ERR_INVALID_ARG
+    assert b"max_bands" in lib.lse_last_error(None)
+    p = lse.Params(0, 15.0, 1.0, 9, 10, 1, 0.0, 0)
+    assert lib.lse_evolve(None, None, 0, 8, 8, 1, None, None, ctypes.byref(p),
+                          None, None, None, None) == lse.LSE_ERR_INVALID_ARG
+    assert lib.lse_precompute_edge(None, None, 0, 8, 8, 1, 1.0, 9, 255.0,
+                                   None, None) == lse.LSE_ERR_INVALID_ARG
+    st = lse.Stats()
+    assert lib.lse_get_stats(None, ctypes.byref(st)) == lse.LSE_ERR_INVALID_ARG
+    lib.lse_destroy(None)
+
+
+def test_no_cpu_fallback_in_binding(lse):
+    # the binding refuses to import without the library
+    src = open(os.path.join(ROOT, "paper_1409_7474_gb300", "lse.py")).read()
+    assert "raise ImportError" in src and "oracle" not in src
