@@ -608,6 +608,8 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
         a.phi_out = ctx->phi[(n + 1) & 1];
         a.out_buf = (n + 1) & 1;
         a.binarise_in = (n > 0 && reinit_after(n - 1, p.reinit_period)) ? 1 : 0;
+        // sign changes matter for the early stop and the last step's statistics
+        a.count_flips = (p.early_stop_frac > 0.0f || n == p.iterations - 1) ? 1 : 0;
         if (use_tma)
             e = launch_step_tma(a, phi_maps[n & 1], data_map, nblocks, wpc, s);
         else

@@ -65,6 +65,7 @@ struct StepArgs {
     int term;                   // LSE_TERM_*
     int binarise_in;            // phi_in holds v of a re-initialised step
     int iter;                   // 0-based iteration index
+    int count_flips;            // count sign changes (early stop, last step)
     int rad;                    // (ts - 1) / 2
     float taps[16];             // 1-D taps G[0..rad] (symmetric)
     float dt;                   // time step of Eq. 18

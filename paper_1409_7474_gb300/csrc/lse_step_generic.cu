@@ -19,7 +19,7 @@ constexpr int kTile = 32;
 constexpr int kThreads = 256;
 
 __global__ void __launch_bounds__(kThreads)
-step_generic_kernel(const StepArgs a)
+step_generic_kernel(const __grid_constant__ StepArgs a)
 {
     LseDevState *st = a.st;
     if (st->done || (st->status_bits & LSE_SBIT_ABORT)) return;

@@ -1,0 +1,19 @@
+// lse_step_tma_edge.cu -- instantiations of the fused step for one data term
+// (one translation unit per term so the build compiles them in parallel).
+#include "lse_step_tma.cuh"
+
+namespace lse_detail {
+
+cudaError_t launch_step_tma_edge(const StepArgs &a, const CUtensorMap &pm,
+                                   const CUtensorMap &dm, int nblocks, int wpc,
+                                   cudaStream_t s)
+{
+    return lse_tma::launch_kind<lse_tma::K_EDGE>(a, pm, dm, nblocks, wpc, s);
+}
+
+int step_tma_warp_bytes_edge(int rad)
+{
+    return lse_tma::warp_bytes_for<lse_tma::K_EDGE>(rad);
+}
+
+}  // namespace lse_detail

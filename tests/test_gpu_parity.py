@@ -279,6 +279,8 @@ def test_bad_arguments_are_rejected(torch, ctx):
 # ---------------------------------------------------------------- edge indicator
 @pytest.mark.parametrize("B,sigma1,ts1", [(1, 1.0, 9), (1, 3.0, 15), (4, 1.0, 9), (3, 1.7, 31)])
 def test_edge_indicator(torch, ctx, B, sigma1, ts1):
+    # the C ABI takes sigma1 as float32: give the oracle the same value
+    sigma1 = float(np.float32(sigma1))
     img = rng_scene(B, 140, 210, B + ts1)
     g = ctx.precompute_edge(dev(torch, img), sigma1, ts1, 255.0)
     torch.cuda.synchronize()
