@@ -33,6 +33,8 @@
 // status bit, drains the loads still in flight (again bounded) and skips the
 // rest of the warp's work; the CTA still reaches its reduction.
 #pragma once
+#include <type_traits>
+
 #include "lse_reduce.cuh"
 
 namespace lse_tma {
@@ -271,23 +273,24 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
     }
     const bool lane_out = lane >= HL && lane < 32 - HL;
 
-    for (int k = 0; k < my_items && !failed; ++k) {
-        const int base = k * NR;
-        int xs, ys;
-        item_origin(k, xs, ys);
+    // One item: stream its NR rows.  FAST is the hot specialisation: the
+    // item and its halo lie inside the image, phi is binary (the previous
+    // step re-initialised) and sign changes are not counted.  Everything
+    // else (image borders, a real-valued phi, flip counting) takes the
+    // general instantiation, so the hot loop stays small.
+    auto run_item = [&](int base, int xs, int ys, auto fast_tag) {
+        constexpr bool FAST = decltype(fast_tag)::value;
         const int x0 = xs + 4 * lane;
-        const bool interior = xs >= 1 && xs + 128 < W && ys >= 0 && ys + NR - 1 < H;
-
-        __syncwarp();   // all lanes are done with the previous item's stages
-        issue_upto(base + S - 1);
-        if (!wait_upto(base + 1)) break;
-        int s1 = w_stage - 1;      // stage of the newest waited row
+        const bool interior = FAST || (xs >= 1 && xs + 128 < W && ys >= 0 && ys + NR - 1 < H);
+        const bool bin_in = FAST || binarise;
+        const bool flips = !FAST && count_flips;
+        int s1 = w_stage - 1;      // stage of the newest waited row (row 1)
         if (s1 < 0) s1 += S;
         int s0 = s1 - 1;
         if (s0 < 0) s0 += S;
         float4 p0 = ld4(phi_at(s0) + 4 + 4 * lane);
         float4 pp = ld4(phi_at(s1) + 4 + 4 * lane);
-        if (binarise) {
+        if (bin_in) {
             p0 = make_float4(bin(p0.x), bin(p0.y), bin(p0.z), bin(p0.w));
             pp = make_float4(bin(pp.x), bin(pp.y), bin(pp.z), bin(pp.w));
         }
@@ -302,169 +305,163 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
 #pragma unroll
             for (int kk = 0; kk < P; ++kk) {
                 const int r = r0 + kk;
-                if (r <= NR - 2 && !failed) {
-                    __syncwarp();
-                    issue_upto(base + (r > RAD ? r - RAD : 0) + S - 1);
-                    if (wait_upto(base + r + 1)) {
-                        // stages of rows r + 1, r and r - RAD
-                        int sn = w_stage - 1;
-                        if (sn < 0) sn += S;
-                        int sr = sn - 1;
-                        if (sr < 0) sr += S;
-                        int so = sn - 1 - RAD;
-                        if (so < 0) so += S;
-                        pm = p0;
-                        p0 = pp;
-                        pp = ld4(phi_at(sn) + 4 + 4 * lane);
-                        if (binarise)
-                            pp = make_float4(bin(pp.x), bin(pp.y), bin(pp.z), bin(pp.w));
-                        // x-neighbours of this lane's four columns in row r
-                        float lft = __shfl_up_sync(0xffffffffu, p0.w, 1);
-                        float rgt = __shfl_down_sync(0xffffffffu, p0.x, 1);
-                        if (lane == 0) {
-                            lft = phi_at(sr)[3];
-                            if (binarise) lft = bin(lft);
-                        }
-                        if (lane == 31) {
-                            rgt = phi_at(sr)[132];
-                            if (binarise) rgt = bin(rgt);
-                        }
-                        // data term factor t = 0.5 dt R
-                        float t[4];
-                        if (KIND == K_EDGE) {
-                            const float4 g4 = ld4(data_at(sr, 0) + 4 * lane);
+                if (r > NR - 2 || failed) continue;
+                __syncwarp();
+                issue_upto(base + (r > RAD ? r - RAD : 0) + S - 1);
+                if (!wait_upto(base + r + 1)) continue;
+                // stages of rows r + 1, r and r - RAD
+                int sn = w_stage - 1;
+                if (sn < 0) sn += S;
+                int sr = sn - 1;
+                if (sr < 0) sr += S;
+                int so = sn - 1 - RAD;
+                if (so < 0) so += S;
+                pm = p0;
+                p0 = pp;
+                pp = ld4(phi_at(sn) + 4 + 4 * lane);
+                if (bin_in) pp = make_float4(bin(pp.x), bin(pp.y), bin(pp.z), bin(pp.w));
+                // x-neighbours of this lane's four columns in row r
+                float lft = __shfl_up_sync(0xffffffffu, p0.w, 1);
+                float rgt = __shfl_down_sync(0xffffffffu, p0.x, 1);
+                if (lane == 0) {
+                    lft = phi_at(sr)[3];
+                    if (bin_in) lft = bin(lft);
+                }
+                if (lane == 31) {
+                    rgt = phi_at(sr)[132];
+                    if (bin_in) rgt = bin(rgt);
+                }
+                // data term factor t = 0.5 dt R
+                float t[4];
+                if (KIND == K_EDGE) {
+                    const float4 g4 = ld4(data_at(sr, 0) + 4 * lane);
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) t[j] = half_dt * comp(g4, j);
-                        } else {
-                            const float4 d4 = ld4(data_at(sr, 0) + 4 * lane);
+                    for (int j = 0; j < 4; ++j) t[j] = half_dt * comp(g4, j);
+                } else {
+                    const float4 d4 = ld4(data_at(sr, 0) + 4 * lane);
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) t[j] = coef[0] * (comp(d4, j) - mid[0]);
-                            if (KIND == K_REGION_MB) {
+                    for (int j = 0; j < 4; ++j) t[j] = coef[0] * (comp(d4, j) - mid[0]);
+                    if (KIND == K_REGION_MB) {
 #pragma unroll
-                                for (int b = 1; b < NB; ++b) {
-                                    if (b < B) {
-                                        const float4 e4 = ld4(data_at(sr, b) + 4 * lane);
+                        for (int b = 1; b < NB; ++b) {
+                            if (b < B) {
+                                const float4 e4 = ld4(data_at(sr, b) + 4 * lane);
 #pragma unroll
-                                        for (int j = 0; j < 4; ++j)
-                                            t[j] = fmaf(coef[b], comp(e4, j) - mid[b], t[j]);
-                                    }
-                                }
+                                for (int j = 0; j < 4; ++j)
+                                    t[j] = fmaf(coef[b], comp(e4, j) - mid[b], t[j]);
                             }
                         }
-                        // u = phi + t * 2|grad phi|
-                        const float c[6] = {lft, p0.x, p0.y, p0.z, p0.w, rgt};
-                        float u[4];
-                        if (interior) {
+                    }
+                }
+                // u = phi + t * 2|grad phi|
+                const float c[6] = {lft, p0.x, p0.y, p0.z, p0.w, rgt};
+                float u[4];
+                if (interior) {
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                const float dx = c[j + 2] - c[j];
-                                const float dy = comp(pp, j) - comp(pm, j);
-                                const float q = fmaf(dx, dx, dy * dy);
-                                // a binary LSF gives q in {0, 4, 8}: sqrt exactly
-                                const float s2 = binarise ? (q > 6.0f ? kTwoRootTwo : 0.5f * q)
-                                                          : sqrtf(q);
-                                u[j] = fmaf(t[j], s2, c[j + 1]);
-                            }
-                        } else {
-                            const int y = ys + r;
-                            const bool yin = y >= 0 && y < H;
+                    for (int j = 0; j < 4; ++j) {
+                        const float dx = c[j + 2] - c[j];
+                        const float dy = comp(pp, j) - comp(pm, j);
+                        const float q = fmaf(dx, dx, dy * dy);
+                        float s2;
+                        if (FAST)      // binary phi: q in {0, 4, 8}, sqrt exactly
+                            s2 = q > 6.0f ? kTwoRootTwo : 0.5f * q;
+                        else
+                            s2 = sqrtf(q);
+                        u[j] = fmaf(t[j], s2, c[j + 1]);
+                    }
+                } else {
+                    const int y = ys + r;
+                    const bool yin = y >= 0 && y < H;
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                const int x = x0 + j;
-                                float dx, dy;
-                                if (W == 1) dx = 0.0f;
-                                else if (x == 0) dx = 2.0f * (c[j + 2] - c[j + 1]);
-                                else if (x == W - 1) dx = 2.0f * (c[j + 1] - c[j]);
-                                else dx = c[j + 2] - c[j];
-                                if (H == 1) dy = 0.0f;
-                                else if (y == 0) dy = 2.0f * (comp(pp, j) - c[j + 1]);
-                                else if (y == H - 1) dy = 2.0f * (c[j + 1] - comp(pm, j));
-                                else dy = comp(pp, j) - comp(pm, j);
-                                const bool in = yin && x >= 0 && x < W;
-                                u[j] = in ? fmaf(t[j], sqrtf(fmaf(dx, dx, dy * dy)), c[j + 1])
-                                          : 0.0f;
-                            }
+                    for (int j = 0; j < 4; ++j) {
+                        const int x = x0 + j;
+                        float dx, dy;
+                        if (W == 1) dx = 0.0f;
+                        else if (x == 0) dx = 2.0f * (c[j + 2] - c[j + 1]);
+                        else if (x == W - 1) dx = 2.0f * (c[j + 1] - c[j]);
+                        else dx = c[j + 2] - c[j];
+                        if (H == 1) dy = 0.0f;
+                        else if (y == 0) dy = 2.0f * (comp(pp, j) - c[j + 1]);
+                        else if (y == H - 1) dy = 2.0f * (c[j + 1] - comp(pm, j));
+                        else dy = comp(pp, j) - comp(pm, j);
+                        const bool in = yin && x >= 0 && x < W;
+                        u[j] = in ? fmaf(t[j], sqrtf(fmaf(dx, dx, dy * dy)), c[j + 1]) : 0.0f;
+                    }
+                }
+                // horizontal pass: U[c + 4 HL] = u at relative column c
+                float U[4 + 8 * HL];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) U[4 * HL + j] = u[j];
+#pragma unroll
+                for (int o = 1; o <= HL; ++o) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (j - 4 * o >= -RAD)
+                            U[4 * HL + j - 4 * o] = __shfl_up_sync(0xffffffffu, u[j], o);
+                        if (j + 4 * o <= 3 + RAD)
+                            U[4 * HL + j + 4 * o] = __shfl_down_sync(0xffffffffu, u[j], o);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float h = tp[0] * U[4 * HL + j];
+#pragma unroll
+                    for (int q = 1; q <= RAD; ++q)
+                        h = fmaf(tp[q], U[4 * HL + j - q] + U[4 * HL + j + q], h);
+                    ring_h[kk][j] = h;
+                }
+                if (r < 2 * RAD + 1) continue;
+                // vertical pass and output of row r - RAD
+                float v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float acc = tp[0] * ring_h[(kk - RAD + P) % P][j];
+#pragma unroll
+                    for (int q = 1; q <= RAD; ++q)
+                        acc = fmaf(tp[q],
+                                   ring_h[(kk - RAD - q + 2 * P) % P][j] +
+                                       ring_h[(kk - RAD + q + P) % P][j],
+                                   acc);
+                    v[j] = acc;
+                }
+                const int yo = ys + r - RAD;
+                if (!lane_out || (!FAST && yo >= H)) continue;
+                float *dst = a.phi_out + (size_t)yo * a.pitch + x0;
+                const bool full = FAST || x0 + 3 < W;
+                if (full) {
+                    *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (x0 + j < W) dst[j] = v[j];
+                }
+                float4 old4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (flips) old4 = ld4(phi_at(so) + 4 + 4 * lane);
+                float dsel[NB][4];
+                if (T::REGION) {
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        if (b < B) {
+                            const float4 e4 = ld4(data_at(so, b) + 4 * lane);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) dsel[b][j] = comp(e4, j);
                         }
-                        // horizontal pass: U[c + 4 HL] = u at relative column c
-                        float U[4 + 8 * HL];
+                    }
+                }
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) U[4 * HL + j] = u[j];
+                for (int j = 0; j < 4; ++j) {
+                    const bool ok = full || x0 + j < W;
+                    const bool pos = ok && v[j] >= 0.0f;
+                    cnt += pos;
+                    if (flips) nflip += ok && (v[j] >= 0.0f) != (comp(old4, j) >= 0.0f);
+                    if (T::REGION) {
 #pragma unroll
-                        for (int o = 1; o <= HL; ++o) {
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                if (j - 4 * o >= -RAD)
-                                    U[4 * HL + j - 4 * o] = __shfl_up_sync(0xffffffffu, u[j], o);
-                                if (j + 4 * o <= 3 + RAD)
-                                    U[4 * HL + j + 4 * o] = __shfl_down_sync(0xffffffffu, u[j], o);
-                            }
-                        }
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            float h = tp[0] * U[4 * HL + j];
-#pragma unroll
-                            for (int q = 1; q <= RAD; ++q)
-                                h = fmaf(tp[q], U[4 * HL + j - q] + U[4 * HL + j + q], h);
-                            ring_h[kk][j] = h;
-                        }
-                        // vertical pass and output of row r - RAD
-                        if (r >= 2 * RAD + 1) {
-                            float v[4];
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                float acc = tp[0] * ring_h[(kk - RAD + P) % P][j];
-#pragma unroll
-                                for (int q = 1; q <= RAD; ++q)
-                                    acc = fmaf(tp[q],
-                                               ring_h[(kk - RAD - q + 2 * P) % P][j] +
-                                                   ring_h[(kk - RAD + q + P) % P][j],
-                                               acc);
-                                v[j] = acc;
-                            }
-                            const int yo = ys + r - RAD;
-                            if (lane_out && yo < H) {
-                                float *dst = a.phi_out + (size_t)yo * a.pitch + x0;
-                                const bool full = x0 + 3 < W;
-                                if (full) {
-                                    *reinterpret_cast<float4 *>(dst) =
-                                        make_float4(v[0], v[1], v[2], v[3]);
-                                } else {
-#pragma unroll
-                                    for (int j = 0; j < 4; ++j)
-                                        if (x0 + j < W) dst[j] = v[j];
-                                }
-                                float4 old4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                                if (count_flips) old4 = ld4(phi_at(so) + 4 + 4 * lane);
-                                float dsel[NB][4];
-                                if (T::REGION) {
-#pragma unroll
-                                    for (int b = 0; b < NB; ++b) {
-                                        if (b < B) {
-                                            const float4 e4 = ld4(data_at(so, b) + 4 * lane);
-#pragma unroll
-                                            for (int j = 0; j < 4; ++j) dsel[b][j] = comp(e4, j);
-                                        }
-                                    }
-                                }
-#pragma unroll
-                                for (int j = 0; j < 4; ++j) {
-                                    const bool ok = full || x0 + j < W;
-                                    const bool pos = ok && v[j] >= 0.0f;
-                                    cnt += pos;
-                                    if (count_flips)
-                                        nflip += ok && (v[j] >= 0.0f) != (comp(old4, j) >= 0.0f);
-                                    if (T::REGION) {
-#pragma unroll
-                                        for (int b = 0; b < NB; ++b) {
-                                            if (b < B) {
-                                                const float d = ok ? dsel[b][j] : 0.0f;
-                                                const float sel = pos ? d : 0.0f;
-                                                fsp[b] += sel;
-                                                fsm[b] += d - sel;
-                                            }
-                                        }
-                                    }
-                                }
+                        for (int b = 0; b < NB; ++b) {
+                            if (b < B) {
+                                const float d = ok ? dsel[b][j] : 0.0f;
+                                const float sel = pos ? d : 0.0f;
+                                fsp[b] += sel;
+                                fsm[b] += d - sel;
                             }
                         }
                     }
@@ -478,6 +475,21 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
                 fsp[b] = fsm[b] = 0.0f;
             }
         }
+    };
+
+    for (int k = 0; k < my_items && !failed; ++k) {
+        const int base = k * NR;
+        int xs, ys;
+        item_origin(k, xs, ys);
+        __syncwarp();   // all lanes are done with the previous item's stages
+        issue_upto(base + S - 1);
+        if (!wait_upto(base + 1)) break;
+        const bool fast = binarise && !count_flips && xs >= 1 && xs + 128 < W &&
+                          ys >= 0 && ys + NR - 1 < H;
+        if (fast)
+            run_item(base, xs, ys, std::true_type{});
+        else
+            run_item(base, xs, ys, std::false_type{});
     }
     if (failed) {
         if (lane == 0) atomicOr(&st->status_bits, LSE_SBIT_TIMEOUT);
