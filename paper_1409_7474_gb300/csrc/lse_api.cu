@@ -607,7 +607,16 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
         a.phi_in = ctx->phi[n & 1];
         a.phi_out = ctx->phi[(n + 1) & 1];
         a.out_buf = (n + 1) & 1;
-        a.binarise_in = (n > 0 && reinit_after(n - 1, p.reinit_period)) ? 1 : 0;
+        // A re-initialising step other than the last stores sign(v) directly
+        // (the TMA kernel), unless an early stop may make it the last one;
+        // then it stores v and the next step binarises on load.
+        auto stores_bin = [&](int k) {
+            return use_tma && reinit_after(k, p.reinit_period) && k < p.iterations - 1 &&
+                   p.early_stop_frac == 0.0f;
+        };
+        a.store_bin = stores_bin(n) ? 1 : 0;
+        a.binary_in = (n > 0 && stores_bin(n - 1)) ? 1 : 0;
+        a.binarise_in = (n > 0 && reinit_after(n - 1, p.reinit_period) && !stores_bin(n - 1)) ? 1 : 0;
         // sign changes matter for the early stop and the last step's statistics
         a.count_flips = (p.early_stop_frac > 0.0f || n == p.iterations - 1) ? 1 : 0;
         if (use_tma)

@@ -66,6 +66,8 @@ struct StepArgs {
     int binarise_in;            // phi_in holds v of a re-initialised step
     int iter;                   // 0-based iteration index
     int count_flips;            // count sign changes (early stop, last step)
+    int store_bin;              // store sign(v) as +-1 (this step re-initialises)
+    int binary_in;              // phi_in holds +-1 only (previous step stored sign(v))
     int rad;                    // (ts - 1) / 2
     float taps[16];             // 1-D taps G[0..rad] (symmetric)
     float dt;                   // time step of Eq. 18

@@ -52,6 +52,10 @@ bool plan_step_tma(int H, int W, int B, int term, int rad, int sm_count,
     if (per_strip < 1) per_strip = 1;
     int th = (H + per_strip - 1) / per_strip;
     if (th < 16) th = 16;
+    // the kernel streams th + 2 rad u-rows per item in whole ring periods of
+    // 2 rad + 1 rows: round th up so that th + 2 rad is a multiple of it
+    const int period = 2 * rad + 1;
+    th = ((th + 2 * rad + period - 1) / period) * period - 2 * rad;
     const int n_rowblocks = (H + th - 1) / th;
     const int n_items = n_strips * n_rowblocks;
     a->useful = useful;

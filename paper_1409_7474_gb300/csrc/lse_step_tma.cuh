@@ -29,6 +29,22 @@
 // Nothing but the inputs' halo is recomputed, and HBM sees each input byte
 // about once (halo rows/columns of neighbouring strips hit L2).
 //
+// Image borders cost no per-pixel logic: at x = 0 the listing's one-sided
+// difference phi(1) - phi(0) equals the central difference against a ghost
+// value phi(-1) = 2 phi(0) - phi(1) (and likewise at the last column and
+// the first/last row; a dimension of size 1 gets ghosts equal to phi(0), so
+// its difference is 0).  Ghost columns are written into the staged row in
+// shared memory, ghost rows into the register window; u is zeroed outside
+// the image by per-column masks and per-row flags.  Every item then runs
+// the same code, so the work is balanced across warps.
+//
+// BIN instantiations read a binary LSF stored by the previous step (which
+// wrote sign(v) because it re-initialised): |grad phi|^2 then takes only the
+// values 0, 4, 8 (16, 20, 32 at borders) and its square root comes from a
+// 17-entry table filled with sqrtf, exactly.  The other instantiation reads
+// a real LSF (the first step, or a caller-chosen reinit period) and uses
+// sqrtf.
+//
 // The mbarrier waits are bounded: a wait that runs out sets the TIMEOUT
 // status bit, drains the loads still in flight (again bounded) and skips the
 // rest of the warp's work; the CTA still reaches its reduction.
@@ -145,13 +161,18 @@ __device__ __forceinline__ float4 ld4(const float *p)
     return *reinterpret_cast<const float4 *>(p);
 }
 
+__device__ __forceinline__ float4 bin4(float4 v)
+{
+    return make_float4(bin(v.x), bin(v.y), bin(v.z), bin(v.w));
+}
+
 __device__ __forceinline__ float comp(const float4 &v, int j)
 {
     return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
 }
 
 // ---------------------------------------------------------------- kernel
-template <int KIND, int RAD>
+template <int KIND, int RAD, bool BIN>
 __global__ void __launch_bounds__(256, 2)
 step_tma_kernel(const __grid_constant__ StepArgs a,
                 const __grid_constant__ CUtensorMap phi_map,
@@ -161,24 +182,37 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
     using T = KindTraits<KIND>;
     constexpr int HL = G::HL, P = G::P, S = G::S;
     constexpr int NB = T::NB;
-    constexpr float kTwoRootTwo = 2.8284271247461903f;   // sqrt(8), exactly rounded
+    constexpr int SF = G::STAGE / 4;         // floats per stage
+    constexpr int PHI = NB * kDataBox;       // float offset of phi in a stage
 
     LseDevState *st = a.st;
     if (st->done || (st->status_bits & LSE_SBIT_ABORT)) return;
 
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    extern __shared__ float smem_f[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpc = blockDim.x >> 5;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem) + warp * S;
-    const unsigned char *ring = smem + ((wpc * S * 8 + 127) & ~127) + warp * G::WARP_BYTES;
-    const uint32_t bar0 = smem_u32(bars);
-    const uint32_t ring0 = smem_u32(ring);
+    const uint32_t sm0 = smem_u32(smem_f);
+    const int sbase = (int)(((128u - (sm0 & 127u)) & 127u) >> 2);
+    const int lut = sbase;                                   // 32 floats
+    const int ring = sbase + 32 + ((2 * wpc * S + 31) & ~31) + warp * S * SF;
+    const uint32_t bar0 = sm0 + 4u * (uint32_t)(sbase + 32 + 2 * warp * S);
+    const uint32_t ring0 = sm0 + 4u * (uint32_t)ring;
+
+    if (BIN) {
+        // sqrt table indexed by bits(q) >> 21 & 31 for q in {0,4,8,16,20,32}
+        if (threadIdx.x < 32) {
+            const int t = threadIdx.x;
+            const float q = t == 4 ? 4.f : t == 8 ? 8.f : t == 12 ? 16.f
+                          : t == 13 ? 20.f : t == 16 ? 32.f : 0.f;
+            smem_f[lut + t] = sqrtf(q);
+        }
+        __syncthreads();
+    }
 
     const int H = a.H, W = a.W, B = (KIND == K_REGION_MB) ? a.B : 1;
     const int th = a.th, NR = th + 2 * RAD + 2;
+    const int n_per = (th + 2 * RAD) / P;    // u-rows per item = n_per * P
     const int gw = blockIdx.x * wpc + warp;
     const int NW = gridDim.x * wpc;
     const int my_items = a.n_items > gw ? (a.n_items - gw + NW - 1) / NW : 0;
@@ -195,8 +229,9 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
         mid[b] = T::REGION ? st->m[b] : 0.0f;
     }
     const float half_dt = a.half_dt;
-    const bool binarise = a.binarise_in != 0;
+    const bool binarise_in = !BIN && a.binarise_in != 0;
     const bool count_flips = a.count_flips != 0;
+    const bool store_bin = a.store_bin != 0;
 
     if (lane == 0) {
         for (int s = 0; s < S; ++s) mbar_init(bar0 + 8 * s, 1);
@@ -204,292 +239,301 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
     }
     __syncwarp();
 
-    auto item_origin = [&](int k, int &xs, int &ys) {
+    // ---- producer: identical bookkeeping in every lane, lane 0 issues
+    int p_seq = 0, p_stage = 0, p_rr = 0, p_k = 0, p_xs = 0, p_y = 0;
+    auto origin = [&](int k, int &xs, int &ys) {
         const int item = gw + k * NW;
         const int rb = item / a.n_strips;
         xs = (item - rb * a.n_strips) * G::USEFUL - 4 * HL;
         ys = rb * th - (RAD + 1);
     };
-
-    // producer: the same bookkeeping in every lane, lane 0 issues the copies
-    int p_seq = 0, p_stage = 0, p_rr = 0, p_k = 0, p_xs = 0, p_y = 0;
-    if (my_items > 0) item_origin(0, p_xs, p_y);
-    auto issue_upto = [&](int limit) {
-        if (limit > total_seq - 1) limit = total_seq - 1;
-        if (p_seq > limit) return;
-        if (lane == 0) fence_proxy_async();
-        while (p_seq <= limit) {
-            if (lane == 0) {
-                const uint32_t bar = bar0 + 8 * p_stage;
-                const uint32_t dst = ring0 + p_stage * G::STAGE;
-                mbar_expect_tx(bar, tx_bytes);
-                tma_load_2d(dst + NB * kDataSlot, &phi_map, p_xs - 4, p_y, bar);
-                if (KIND == K_REGION_MB)
-                    tma_load_3d(dst, &data_map, p_xs, p_y, 0, bar);
-                else
-                    tma_load_2d(dst, &data_map, p_xs, p_y, bar);
-            }
-            ++p_seq;
-            ++p_y;
-            p_stage = (p_stage + 1 == S) ? 0 : p_stage + 1;
-            if (++p_rr == NR) {
-                p_rr = 0;
-                if (++p_k < my_items) item_origin(p_k, p_xs, p_y);
-            }
+    if (my_items > 0) origin(0, p_xs, p_y);
+    auto issue_one = [&]() {
+        if (lane == 0) {
+            const uint32_t bar = bar0 + 8 * p_stage;
+            const uint32_t dst = ring0 + (uint32_t)(p_stage * G::STAGE);
+            fence_proxy_async();
+            mbar_expect_tx(bar, tx_bytes);
+            tma_load_2d(dst + PHI * 4, &phi_map, p_xs - 4, p_y, bar);
+            if (KIND == K_REGION_MB)
+                tma_load_3d(dst, &data_map, p_xs, p_y, 0, bar);
+            else
+                tma_load_2d(dst, &data_map, p_xs, p_y, bar);
+        }
+        ++p_seq;
+        ++p_y;
+        p_stage = (p_stage + 1 == S) ? 0 : p_stage + 1;
+        if (++p_rr == NR) {
+            p_rr = 0;
+            if (++p_k < my_items) origin(p_k, p_xs, p_y);
         }
     };
-    // consumer: waits in sequence order
+    // ---- consumer: waits strictly in order; returns the waited stage
     int w_seq = 0, w_stage = 0;
     uint32_t w_par = 0;
     bool failed = false;
-    auto wait_upto = [&](int q) {
-        while (!failed && w_seq <= q) {
-            if (!wait_stage(bar0 + 8 * w_stage, w_par)) {
+    auto wait_one = [&]() -> int {
+        const int sw = w_stage;
+        if (!failed) {
+            if (wait_stage(bar0 + 8 * sw, w_par)) {
+                ++w_seq;
+                if (++w_stage == S) {
+                    w_stage = 0;
+                    w_par ^= 1u;
+                }
+            } else {
                 failed = true;     // the drain below waits for this row again
-                break;
-            }
-            ++w_seq;
-            if (++w_stage == S) {
-                w_stage = 0;
-                w_par ^= 1u;
             }
         }
-        return !failed;
-    };
-    auto phi_at = [&](int stage) -> const float * {
-        return reinterpret_cast<const float *>(ring + stage * G::STAGE + NB * kDataSlot);
-    };
-    auto data_at = [&](int stage, int b) -> const float * {
-        return reinterpret_cast<const float *>(ring + stage * G::STAGE + b * kDataSlot);
+        return sw;
     };
 
     int cnt = 0, nflip = 0;
-    float fsp[NB], fsm[NB];
-    double dsp[NB], dsm[NB];
+    float fsp[NB], fsa[NB];
+    double dsp[NB], dsa[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        fsp[b] = fsm[b] = 0.0f;
-        dsp[b] = dsm[b] = 0.0;
+        fsp[b] = fsa[b] = 0.0f;
+        dsp[b] = dsa[b] = 0.0;
     }
     const bool lane_out = lane >= HL && lane < 32 - HL;
-
-    // One item: stream its NR rows.  FAST is the hot specialisation: the
-    // item and its halo lie inside the image, phi is binary (the previous
-    // step re-initialised) and sign changes are not counted.  Everything
-    // else (image borders, a real-valued phi, flip counting) takes the
-    // general instantiation, so the hot loop stays small.
-    auto run_item = [&](int base, int xs, int ys, auto fast_tag) {
-        constexpr bool FAST = decltype(fast_tag)::value;
-        const int x0 = xs + 4 * lane;
-        const bool interior = FAST || (xs >= 1 && xs + 128 < W && ys >= 0 && ys + NR - 1 < H);
-        const bool bin_in = FAST || binarise;
-        const bool flips = !FAST && count_flips;
-        int s1 = w_stage - 1;      // stage of the newest waited row (row 1)
-        if (s1 < 0) s1 += S;
-        int s0 = s1 - 1;
-        if (s0 < 0) s0 += S;
-        float4 p0 = ld4(phi_at(s0) + 4 + 4 * lane);
-        float4 pp = ld4(phi_at(s1) + 4 + 4 * lane);
-        if (bin_in) {
-            p0 = make_float4(bin(p0.x), bin(p0.y), bin(p0.z), bin(p0.w));
-            pp = make_float4(bin(pp.x), bin(pp.y), bin(pp.z), bin(pp.w));
-        }
-        float4 pm = p0;
-        float ring_h[P][4];
-#pragma unroll
-        for (int i = 0; i < P; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) ring_h[i][j] = 0.0f;
-
-        for (int r0 = 1; r0 <= NR - 2 && !failed; r0 += P) {
-#pragma unroll
-            for (int kk = 0; kk < P; ++kk) {
-                const int r = r0 + kk;
-                if (r > NR - 2 || failed) continue;
-                __syncwarp();
-                issue_upto(base + (r > RAD ? r - RAD : 0) + S - 1);
-                if (!wait_upto(base + r + 1)) continue;
-                // stages of rows r + 1, r and r - RAD
-                int sn = w_stage - 1;
-                if (sn < 0) sn += S;
-                int sr = sn - 1;
-                if (sr < 0) sr += S;
-                int so = sn - 1 - RAD;
-                if (so < 0) so += S;
-                pm = p0;
-                p0 = pp;
-                pp = ld4(phi_at(sn) + 4 + 4 * lane);
-                if (bin_in) pp = make_float4(bin(pp.x), bin(pp.y), bin(pp.z), bin(pp.w));
-                // x-neighbours of this lane's four columns in row r
-                float lft = __shfl_up_sync(0xffffffffu, p0.w, 1);
-                float rgt = __shfl_down_sync(0xffffffffu, p0.x, 1);
-                if (lane == 0) {
-                    lft = phi_at(sr)[3];
-                    if (bin_in) lft = bin(lft);
-                }
-                if (lane == 31) {
-                    rgt = phi_at(sr)[132];
-                    if (bin_in) rgt = bin(rgt);
-                }
-                // data term factor t = 0.5 dt R
-                float t[4];
-                if (KIND == K_EDGE) {
-                    const float4 g4 = ld4(data_at(sr, 0) + 4 * lane);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) t[j] = half_dt * comp(g4, j);
-                } else {
-                    const float4 d4 = ld4(data_at(sr, 0) + 4 * lane);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) t[j] = coef[0] * (comp(d4, j) - mid[0]);
-                    if (KIND == K_REGION_MB) {
-#pragma unroll
-                        for (int b = 1; b < NB; ++b) {
-                            if (b < B) {
-                                const float4 e4 = ld4(data_at(sr, b) + 4 * lane);
-#pragma unroll
-                                for (int j = 0; j < 4; ++j)
-                                    t[j] = fmaf(coef[b], comp(e4, j) - mid[b], t[j]);
-                            }
-                        }
-                    }
-                }
-                // u = phi + t * 2|grad phi|
-                const float c[6] = {lft, p0.x, p0.y, p0.z, p0.w, rgt};
-                float u[4];
-                if (interior) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float dx = c[j + 2] - c[j];
-                        const float dy = comp(pp, j) - comp(pm, j);
-                        const float q = fmaf(dx, dx, dy * dy);
-                        float s2;
-                        if (FAST)      // binary phi: q in {0, 4, 8}, sqrt exactly
-                            s2 = q > 6.0f ? kTwoRootTwo : 0.5f * q;
-                        else
-                            s2 = sqrtf(q);
-                        u[j] = fmaf(t[j], s2, c[j + 1]);
-                    }
-                } else {
-                    const int y = ys + r;
-                    const bool yin = y >= 0 && y < H;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int x = x0 + j;
-                        float dx, dy;
-                        if (W == 1) dx = 0.0f;
-                        else if (x == 0) dx = 2.0f * (c[j + 2] - c[j + 1]);
-                        else if (x == W - 1) dx = 2.0f * (c[j + 1] - c[j]);
-                        else dx = c[j + 2] - c[j];
-                        if (H == 1) dy = 0.0f;
-                        else if (y == 0) dy = 2.0f * (comp(pp, j) - c[j + 1]);
-                        else if (y == H - 1) dy = 2.0f * (c[j + 1] - comp(pm, j));
-                        else dy = comp(pp, j) - comp(pm, j);
-                        const bool in = yin && x >= 0 && x < W;
-                        u[j] = in ? fmaf(t[j], sqrtf(fmaf(dx, dx, dy * dy)), c[j + 1]) : 0.0f;
-                    }
-                }
-                // horizontal pass: U[c + 4 HL] = u at relative column c
-                float U[4 + 8 * HL];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) U[4 * HL + j] = u[j];
-#pragma unroll
-                for (int o = 1; o <= HL; ++o) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        if (j - 4 * o >= -RAD)
-                            U[4 * HL + j - 4 * o] = __shfl_up_sync(0xffffffffu, u[j], o);
-                        if (j + 4 * o <= 3 + RAD)
-                            U[4 * HL + j + 4 * o] = __shfl_down_sync(0xffffffffu, u[j], o);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float h = tp[0] * U[4 * HL + j];
-#pragma unroll
-                    for (int q = 1; q <= RAD; ++q)
-                        h = fmaf(tp[q], U[4 * HL + j - q] + U[4 * HL + j + q], h);
-                    ring_h[kk][j] = h;
-                }
-                if (r < 2 * RAD + 1) continue;
-                // vertical pass and output of row r - RAD
-                float v[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float acc = tp[0] * ring_h[(kk - RAD + P) % P][j];
-#pragma unroll
-                    for (int q = 1; q <= RAD; ++q)
-                        acc = fmaf(tp[q],
-                                   ring_h[(kk - RAD - q + 2 * P) % P][j] +
-                                       ring_h[(kk - RAD + q + P) % P][j],
-                                   acc);
-                    v[j] = acc;
-                }
-                const int yo = ys + r - RAD;
-                if (!lane_out || (!FAST && yo >= H)) continue;
-                float *dst = a.phi_out + (size_t)yo * a.pitch + x0;
-                const bool full = FAST || x0 + 3 < W;
-                if (full) {
-                    *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (x0 + j < W) dst[j] = v[j];
-                }
-                float4 old4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (flips) old4 = ld4(phi_at(so) + 4 + 4 * lane);
-                float dsel[NB][4];
-                if (T::REGION) {
-#pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        if (b < B) {
-                            const float4 e4 = ld4(data_at(so, b) + 4 * lane);
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) dsel[b][j] = comp(e4, j);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const bool ok = full || x0 + j < W;
-                    const bool pos = ok && v[j] >= 0.0f;
-                    cnt += pos;
-                    if (flips) nflip += ok && (v[j] >= 0.0f) != (comp(old4, j) >= 0.0f);
-                    if (T::REGION) {
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) {
-                            if (b < B) {
-                                const float d = ok ? dsel[b][j] : 0.0f;
-                                const float sel = pos ? d : 0.0f;
-                                fsp[b] += sel;
-                                fsm[b] += d - sel;
-                            }
-                        }
-                    }
-                }
-            }
-            // fold this period's FP32 sums into FP64
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                dsp[b] += (double)fsp[b];
-                dsm[b] += (double)fsm[b];
-                fsp[b] = fsm[b] = 0.0f;
-            }
-        }
-    };
 
     for (int k = 0; k < my_items && !failed; ++k) {
         const int base = k * NR;
         int xs, ys;
-        item_origin(k, xs, ys);
-        __syncwarp();   // all lanes are done with the previous item's stages
-        issue_upto(base + S - 1);
-        if (!wait_upto(base + 1)) break;
-        const bool fast = binarise && !count_flips && xs >= 1 && xs + 128 < W &&
-                          ys >= 0 && ys + NR - 1 < H;
-        if (fast)
-            run_item(base, xs, ys, std::true_type{});
-        else
-            run_item(base, xs, ys, std::false_type{});
+        origin(k, xs, ys);
+        const int x0 = xs + 4 * lane;
+        // per-column masks: u inside the image, output/statistics columns
+        bool inx[4], okx[4], oneL[4], oneR[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int x = x0 + j;
+            inx[j] = x >= 0 && x < W;
+            okx[j] = lane_out && x < W;
+            oneL[j] = x == 0;
+            oneR[j] = x == W - 1;
+        }
+        const bool full = lane_out && x0 + 3 < W;
+        const bool ghost_l = xs <= 0;                    // x = -1 in this strip
+        const bool ghost_r = xs <= W - 1 && W - 1 < xs + 128;
+
+        // ghost columns of a staged binary row (lane 0; BIN only)
+        auto patch = [&](int stage) {
+            if (BIN && (ghost_l || ghost_r)) {
+                if (lane == 0) {
+                    const int row = ring + stage * SF + PHI;
+                    if (ghost_l) {
+                        const float f0 = smem_f[row + 4 - xs];
+                        const float f1 = W > 1 ? smem_f[row + 5 - xs] : f0;
+                        smem_f[row + 3 - xs] = 2.0f * f0 - f1;
+                    }
+                    if (ghost_r) {
+                        const float fe = smem_f[row + W + 3 - xs];
+                        const float fd = W > 1 ? smem_f[row + W + 2 - xs] : fe;
+                        smem_f[row + W + 4 - xs] = 2.0f * fe - fd;
+                    }
+                }
+                __syncwarp();
+            }
+        };
+
+        __syncwarp();   // every lane is done with the previous item's stages
+        {
+            int lim = base + S - 1;
+            if (lim > total_seq - 1) lim = total_seq - 1;
+            while (p_seq <= lim) issue_one();
+        }
+        const int s_a = wait_one();
+        const int s_b = wait_one();
+        patch(s_a);
+        patch(s_b);
+        float4 p0 = ld4(&smem_f[ring + s_a * SF + PHI + 4 + 4 * lane]);
+        float4 pp = ld4(&smem_f[ring + s_b * SF + PHI + 4 + 4 * lane]);
+        if (binarise_in) {
+            p0 = bin4(p0);
+            pp = bin4(pp);
+        }
+        float4 pm = p0;
+        float ring_h[P][4];
+
+        // one u-row: u of row r, its horizontal pass into ring slot kk, and
+        // (OUT) the vertical pass, store and statistics of row r - RAD
+        auto row = [&](const int r, const int kk, const bool OUT) {
+            __syncwarp();
+            if (r > RAD && p_seq < total_seq && p_seq <= base + r - RAD + S - 1) issue_one();
+            const int sn = wait_one();          // stage of row r + 1
+            patch(sn);
+            int sr = sn - 1;
+            if (sr < 0) sr += S;
+            int so = sn - 1 - RAD;
+            if (so < 0) so += S;
+            const int rowN = ring + sn * SF, rowR = ring + sr * SF, rowO = ring + so * SF;
+            pm = p0;
+            p0 = pp;
+            pp = ld4(&smem_f[rowN + PHI + 4 + 4 * lane]);
+            if (binarise_in) pp = bin4(pp);
+            // x-neighbours of this lane's columns in row r
+            float lft = __shfl_up_sync(0xffffffffu, p0.w, 1);
+            float rgt = __shfl_down_sync(0xffffffffu, p0.x, 1);
+            {
+                float e = smem_f[rowR + PHI + (lane == 0 ? 3 : 132)];
+                if (binarise_in) e = bin(e);
+                if (lane == 0) lft = e;
+                if (lane == 31) rgt = e;
+            }
+            // ghost rows (uniform per row)
+            const int y = ys + r;
+            float4 pmx = pm, ppx = pp;
+            if (y <= 0 || y >= H - 1) {
+                if (H == 1) {
+                    pmx = p0;
+                    ppx = p0;
+                } else if (y == 0) {
+                    pmx = make_float4(2.f * p0.x - pp.x, 2.f * p0.y - pp.y,
+                                      2.f * p0.z - pp.z, 2.f * p0.w - pp.w);
+                } else if (y == H - 1) {
+                    ppx = make_float4(2.f * p0.x - pm.x, 2.f * p0.y - pm.y,
+                                      2.f * p0.z - pm.z, 2.f * p0.w - pm.w);
+                }
+            }
+            const bool yin = y >= 0 && y < H;
+            // data term factor t = 0.5 dt R
+            float t[4];
+            if (KIND == K_EDGE) {
+                const float4 g4 = ld4(&smem_f[rowR + 4 * lane]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) t[j] = half_dt * comp(g4, j);
+            } else {
+                const float4 d4 = ld4(&smem_f[rowR + 4 * lane]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) t[j] = coef[0] * (comp(d4, j) - mid[0]);
+                if (KIND == K_REGION_MB) {
+#pragma unroll
+                    for (int b = 1; b < NB; ++b) {
+                        if (b < B) {
+                            const float4 e4 = ld4(&smem_f[rowR + b * kDataBox + 4 * lane]);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                t[j] = fmaf(coef[b], comp(e4, j) - mid[b], t[j]);
+                        }
+                    }
+                }
+            }
+            // u = phi + t * 2|grad phi| (zero outside the image)
+            const float c[6] = {lft, p0.x, p0.y, p0.z, p0.w, rgt};
+            float u[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float dx = c[j + 2] - c[j];
+                if (!BIN) {    // real LSF: one-sided differences by flags
+                    if (W == 1) dx = 0.0f;
+                    else if (oneL[j]) dx = 2.0f * (c[j + 2] - c[j + 1]);
+                    else if (oneR[j]) dx = 2.0f * (c[j + 1] - c[j]);
+                }
+                const float dy = comp(ppx, j) - comp(pmx, j);
+                const float q = fmaf(dx, dx, dy * dy);
+                float s2;
+                if (BIN)
+                    s2 = smem_f[lut + ((__float_as_uint(q) >> 21) & 31u)];
+                else
+                    s2 = sqrtf(q);
+                const float uu = fmaf(t[j], s2, c[j + 1]);
+                u[j] = (inx[j] && yin) ? uu : 0.0f;
+            }
+            // horizontal pass: U[c + 4 HL] = u at relative column c
+            float U[4 + 8 * HL];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) U[4 * HL + j] = u[j];
+#pragma unroll
+            for (int o = 1; o <= HL; ++o) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (j - 4 * o >= -RAD)
+                        U[4 * HL + j - 4 * o] = __shfl_up_sync(0xffffffffu, u[j], o);
+                    if (j + 4 * o <= 3 + RAD)
+                        U[4 * HL + j + 4 * o] = __shfl_down_sync(0xffffffffu, u[j], o);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float h = tp[0] * U[4 * HL + j];
+#pragma unroll
+                for (int q = 1; q <= RAD; ++q)
+                    h = fmaf(tp[q], U[4 * HL + j - q] + U[4 * HL + j + q], h);
+                ring_h[kk][j] = h;
+            }
+            if (!OUT) return;
+            // vertical pass of row r - RAD
+            float v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float acc = tp[0] * ring_h[(kk - RAD + P) % P][j];
+#pragma unroll
+                for (int q = 1; q <= RAD; ++q)
+                    acc = fmaf(tp[q],
+                               ring_h[(kk - RAD - q + 2 * P) % P][j] +
+                                   ring_h[(kk - RAD + q + P) % P][j],
+                               acc);
+                v[j] = acc;
+            }
+            const int yo = ys + r - RAD;
+            if (yo >= H) return;
+            bool pos[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) pos[j] = v[j] >= 0.0f;
+            float w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) w[j] = store_bin ? (pos[j] ? 1.0f : -1.0f) : v[j];
+            float *dst = a.phi_out + (size_t)yo * a.pitch + x0;
+            if (full) {
+                *reinterpret_cast<float4 *>(dst) = make_float4(w[0], w[1], w[2], w[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (okx[j]) dst[j] = w[j];
+            }
+            if (count_flips) {
+                const float4 o4 = ld4(&smem_f[rowO + PHI + 4 + 4 * lane]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    nflip += okx[j] && pos[j] != (comp(o4, j) >= 0.0f);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cnt += okx[j] && pos[j];
+            if (T::REGION) {
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    if (b < B) {
+                        const float4 e4 = ld4(&smem_f[rowO + b * kDataBox + 4 * lane]);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float d = okx[j] ? comp(e4, j) : 0.0f;
+                            fsp[b] += pos[j] ? d : 0.0f;
+                            fsa[b] += d;
+                        }
+                    }
+                }
+            }
+        };
+        auto fold = [&]() {
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                dsp[b] += (double)fsp[b];
+                dsa[b] += (double)fsa[b];
+                fsp[b] = fsa[b] = 0.0f;
+            }
+        };
+
+        // warm-up period: rows 1 .. P, the first output at row P = 2 RAD + 1
+#pragma unroll
+        for (int kk = 0; kk < P; ++kk) row(1 + kk, kk, kk == P - 1);
+        fold();
+        for (int per = 1; per < n_per && !failed; ++per) {
+            const int r0 = 1 + per * P;
+#pragma unroll
+            for (int kk = 0; kk < P; ++kk) row(r0 + kk, kk, true);
+            fold();
+        }
     }
     if (failed) {
         if (lane == 0) atomicOr(&st->status_bits, LSE_SBIT_TIMEOUT);
@@ -509,7 +553,7 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         acc.sp[b] = dsp[b];
-        acc.sm[b] = dsm[b];
+        acc.sm[b] = dsa[b] - dsp[b];
     }
     acc.n_plus = cnt;
     acc.flips = nflip;
@@ -527,7 +571,8 @@ template <int KIND, int RAD>
 int smem_bytes(int wpc)
 {
     using G = Geo<KIND, RAD>;
-    return 128 + ((wpc * G::S * 8 + 127) & ~127) + wpc * G::WARP_BYTES;
+    // alignment slack + sqrt table + mbarriers + per-warp rings
+    return 128 + 128 + ((wpc * G::S * 8 + 127) & ~127) + wpc * G::WARP_BYTES;
 }
 
 template <int KIND, int RAD>
@@ -536,11 +581,12 @@ cudaError_t launch_one(const StepArgs &a, const CUtensorMap &pm,
                        cudaStream_t s)
 {
     const int smem = smem_bytes<KIND, RAD>(wpc);
-    cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<KIND, RAD>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+    auto kern = a.binary_in ? step_tma_kernel<KIND, RAD, true>
+                            : step_tma_kernel<KIND, RAD, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem);
     if (e != cudaSuccess) return e;
-    step_tma_kernel<KIND, RAD><<<nblocks, 32 * wpc, smem, s>>>(a, pm, dm);
+    kern<<<nblocks, 32 * wpc, smem, s>>>(a, pm, dm);
     return cudaGetLastError();
 }
 
