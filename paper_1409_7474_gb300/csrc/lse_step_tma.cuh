@@ -288,13 +288,17 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
         return sw;
     };
 
-    int cnt = 0, nflip = 0;
-    float fsp[NB], fsa[NB];
-    double dsp[NB], dsa[NB];
+    // per-lane sums: sum of w = sign(v) over output pixels (fsw_cnt), and per
+    // band sum d and sum d w; FP32 within a ring period, FP64 across periods
+    long long cnt2 = 0;      // sum over items of (sum w + valid pixels)
+    int nflip = 0;
+    float fsw_cnt = 0.0f;
+    float fsw[NB], fsa[NB];
+    double dsw[NB], dsa[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        fsp[b] = fsa[b] = 0.0f;
-        dsp[b] = dsa[b] = 0.0;
+        fsw[b] = fsa[b] = 0.0f;
+        dsw[b] = dsa[b] = 0.0;
     }
     const bool lane_out = lane >= HL && lane < 32 - HL;
 
@@ -303,16 +307,23 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
         int xs, ys;
         origin(k, xs, ys);
         const int x0 = xs + 4 * lane;
-        // per-column masks: u inside the image, output/statistics columns
-        bool inx[4], okx[4], oneL[4], oneR[4];
+        // per-column masks (1 or 0): u inside the image, output columns
+        float inf[4], okf[4];
+        bool oneL[4], oneR[4];
+        int nvalid = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int x = x0 + j;
-            inx[j] = x >= 0 && x < W;
-            okx[j] = lane_out && x < W;
+            inf[j] = (x >= 0 && x < W) ? 1.0f : 0.0f;
+            okf[j] = (lane_out && x < W) ? 1.0f : 0.0f;
+            nvalid += (lane_out && x < W) ? 1 : 0;
             oneL[j] = x == 0;
             oneR[j] = x == W - 1;
         }
+        // uniform per item: does the strip touch the image's left/right edge,
+        // and is every output lane's float4 inside the image?
+        const bool xborder = xs < 0 || xs + 128 > W;
+        const bool ragged = xs + 4 * (32 - HL) > W;
         const bool full = lane_out && x0 + 3 < W;
         const bool ghost_l = xs <= 0;                    // x = -1 in this strip
         const bool ghost_r = xs <= W - 1 && W - 1 < xs + 128;
@@ -437,8 +448,15 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
                     s2 = smem_f[lut + ((__float_as_uint(q) >> 21) & 31u)];
                 else
                     s2 = sqrtf(q);
-                const float uu = fmaf(t[j], s2, c[j + 1]);
-                u[j] = (inx[j] && yin) ? uu : 0.0f;
+                u[j] = fmaf(t[j], s2, c[j + 1]);
+            }
+            if (xborder) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) u[j] *= inf[j];
+            }
+            if (!yin) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) u[j] = 0.0f;
             }
             // horizontal pass: U[c + 4 HL] = u at relative column c
             float U[4 + 8 * HL];
@@ -478,38 +496,64 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
             }
             const int yo = ys + r - RAD;
             if (yo >= H) return;
-            bool pos[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) pos[j] = v[j] >= 0.0f;
-            float w[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) w[j] = store_bin ? (pos[j] ? 1.0f : -1.0f) : v[j];
             float *dst = a.phi_out + (size_t)yo * a.pitch + x0;
-            if (full) {
-                *reinterpret_cast<float4 *>(dst) = make_float4(w[0], w[1], w[2], w[3]);
+            if (store_bin) {
+                // w = sign(v): the count is (sum w + valid) / 2 and the band sums
+                // over v >= 0 are (sum d + sum d w) / 2 (d zero off the image)
+                float w[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) w[j] = v[j] >= 0.0f ? 1.0f : -1.0f;
+                if (full) *reinterpret_cast<float4 *>(dst) = make_float4(w[0], w[1], w[2], w[3]);
+                if (ragged && !full) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (okf[j] != 0.0f) dst[j] = w[j];
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) fsw_cnt = fmaf(w[j], okf[j], fsw_cnt);
+                if (T::REGION) {
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        if (b < B) {
+                            const float4 e4 = ld4(&smem_f[rowO + b * kDataBox + 4 * lane]);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const float d = comp(e4, j) * okf[j];
+                                fsw[b] = fmaf(d, w[j], fsw[b]);
+                                fsa[b] += d;
+                            }
+                        }
+                    }
+                }
             } else {
+                if (full) *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+                if (ragged && !full) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (okx[j]) dst[j] = w[j];
-            }
-            if (count_flips) {
-                const float4 o4 = ld4(&smem_f[rowO + PHI + 4 + 4 * lane]);
+                    for (int j = 0; j < 4; ++j)
+                        if (okf[j] != 0.0f) dst[j] = v[j];
+                }
+                float w[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    nflip += okx[j] && pos[j] != (comp(o4, j) >= 0.0f);
-            }
+                for (int j = 0; j < 4; ++j) w[j] = v[j] >= 0.0f ? 1.0f : -1.0f;
+                if (count_flips) {
+                    const float4 o4 = ld4(&smem_f[rowO + PHI + 4 + 4 * lane]);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) cnt += okx[j] && pos[j];
-            if (T::REGION) {
+                    for (int j = 0; j < 4; ++j)
+                        nflip += (okf[j] != 0.0f) && ((w[j] > 0.0f) != (comp(o4, j) >= 0.0f));
+                }
 #pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    if (b < B) {
-                        const float4 e4 = ld4(&smem_f[rowO + b * kDataBox + 4 * lane]);
+                for (int j = 0; j < 4; ++j) fsw_cnt = fmaf(w[j], okf[j], fsw_cnt);
+                if (T::REGION) {
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const float d = okx[j] ? comp(e4, j) : 0.0f;
-                            fsp[b] += pos[j] ? d : 0.0f;
-                            fsa[b] += d;
+                    for (int b = 0; b < NB; ++b) {
+                        if (b < B) {
+                            const float4 e4 = ld4(&smem_f[rowO + b * kDataBox + 4 * lane]);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const float d = comp(e4, j) * okf[j];
+                                fsw[b] = fmaf(d, w[j], fsw[b]);
+                                fsa[b] += d;
+                            }
                         }
                     }
                 }
@@ -518,22 +562,27 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
         auto fold = [&]() {
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                dsp[b] += (double)fsp[b];
+                dsw[b] += (double)fsw[b];
                 dsa[b] += (double)fsa[b];
-                fsp[b] = fsa[b] = 0.0f;
+                fsw[b] = fsa[b] = 0.0f;
             }
         };
 
-        // warm-up period: rows 1 .. P, the first output at row P = 2 RAD + 1
-#pragma unroll
-        for (int kk = 0; kk < P; ++kk) row(1 + kk, kk, kk == P - 1);
-        fold();
-        for (int per = 1; per < n_per && !failed; ++per) {
+        // rows 1 .. NR - 2 in whole ring periods; outputs start at 2 RAD + 1
+        for (int per = 0; per < n_per && !failed; ++per) {
             const int r0 = 1 + per * P;
 #pragma unroll
-            for (int kk = 0; kk < P; ++kk) row(r0 + kk, kk, true);
+            for (int kk = 0; kk < P; ++kk) row(r0 + kk, kk, r0 + kk >= 2 * RAD + 1);
             fold();
         }
+        // exact integer count: fsw_cnt holds sum w (|sum| <= 4 th) exactly;
+        // rows at or beyond H produced no output
+        {
+            const int y0 = ys + RAD + 1;
+            const int rows = H - y0 < th ? H - y0 : th;
+            cnt2 += (long long)fsw_cnt + (long long)nvalid * (rows > 0 ? rows : 0);
+        }
+        fsw_cnt = 0.0f;
     }
     if (failed) {
         if (lane == 0) atomicOr(&st->status_bits, LSE_SBIT_TIMEOUT);
@@ -552,10 +601,10 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
     acc.clear();
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        acc.sp[b] = dsp[b];
-        acc.sm[b] = dsa[b] - dsp[b];
+        acc.sp[b] = 0.5 * (dsa[b] + dsw[b]);
+        acc.sm[b] = 0.5 * (dsa[b] - dsw[b]);
     }
-    acc.n_plus = cnt;
+    acc.n_plus = cnt2 / 2;
     acc.flips = nflip;
     const int nb = T::REGION ? B : 0;
     LseAcc r;
