@@ -3,47 +3,48 @@
 // One pass over the image per iteration computes, for every pixel,
 //   u = phi + dt R |grad phi|                        (Eq. 18)
 //   v = G_sigma * u                                  (Table I step 4)
-// with R = D / max|D| (Eq. 17) or R = g (Eq. 14), stores v, and accumulates
-// the sums that the next iteration's region statistics need (Eq. 15): count
-// and intensity sums over v >= 0 and v < 0, plus the number of sign changes.
-// The last CTA finalises c+/c- and the next step's coefficients.
+// with R = D / max|D| (Eq. 17) or R = g (Eq. 14), stores v (or sign(v) when
+// the step re-initialises, Table I step 3), and accumulates the sums that
+// the next iteration's region statistics need (Eq. 15): the count and the
+// band sums over v >= 0, plus the number of sign changes when asked.  The
+// last CTA finalises c+/c- and the next step's coefficients.
 //
-// Work decomposition.  Each warp owns a vertical strip of 128 columns and a
-// block of `th` output rows ("item").  Lane l holds columns xs + 4l .. +3.
-// The outer `HL` lanes on each side only supply the horizontal halo of the
-// Gaussian, so a strip yields 4 (32 - 2 HL) output columns.  The warp streams
-// down the strip one row at a time:
-//   * TMA (cp.async.bulk.tensor, zero fill outside the image) loads each
-//     row of phi (136 floats: the strip plus 4 columns each side) and of the
-//     data term (128 floats per band) into a per-warp ring of shared-memory
-//     stages, each with its own mbarrier; lane 0 issues loads up to
-//     `S - RAD - 2` rows ahead of use;
+// Work decomposition.  Each warp owns a vertical strip of 256 columns and a
+// block of `th` output rows ("item").  Lane l holds eight columns: half A at
+// xs + 4l .. +3 and half B at xs + 128 + 4l .. +3.  The outermost HL lanes
+// (A's first, B's last) only supply the Gaussian's horizontal halo, so a
+// strip yields 256 - 8 HL output columns.  The warp streams down its strip
+// one row at a time:
+//   * TMA (cp.async.bulk.tensor, zero fill outside the image) loads each row
+//     of phi (264 floats: the strip and 4 columns each side, in two boxes)
+//     and of the data term (256 floats per band) into a per-warp ring of
+//     shared-memory stages with one mbarrier each; the warp issues its own
+//     loads (one predicated lane) up to PF rows ahead of use;
 //   * phi rows y-1, y, y+1 sit in registers; u of row y is computed in
-//     registers, its horizontal Gaussian pass takes the neighbouring lanes'
-//     u by warp shuffles;
+//     registers; the horizontal Gaussian pass takes neighbouring lanes' u by
+//     warp shuffles (A's last lane and B's first lane exchange across the
+//     halves);
 //   * the vertical pass keeps the last 2 RAD + 1 horizontally smoothed rows
-//     in a register ring (the row loop is unrolled by the ring period so
-//     every ring index is a compile-time constant);
-//   * the output row (RAD rows behind) is written with 16-byte stores and
-//     its statistics read phi and the data term from the ring.
-// Nothing but the inputs' halo is recomputed, and HBM sees each input byte
-// about once (halo rows/columns of neighbouring strips hit L2).
+//     in a register ring; the row loop is unrolled by the ring period, so
+//     ring indices are compile-time constants;
+//   * the output row (RAD rows behind) is written with 16-byte stores; its
+//     statistics read the data term still held in the ring.
+// Inputs are read from HBM about once (the halo of neighbouring strips and
+// row blocks hits L2); nothing but the halo is recomputed.
 //
 // Image borders cost no per-pixel logic: at x = 0 the listing's one-sided
 // difference phi(1) - phi(0) equals the central difference against a ghost
-// value phi(-1) = 2 phi(0) - phi(1) (and likewise at the last column and
-// the first/last row; a dimension of size 1 gets ghosts equal to phi(0), so
-// its difference is 0).  Ghost columns are written into the staged row in
-// shared memory, ghost rows into the register window; u is zeroed outside
-// the image by per-column masks and per-row flags.  Every item then runs
-// the same code, so the work is balanced across warps.
+// value phi(-1) = 2 phi(0) - phi(1) (likewise at the last column and the
+// first/last row; a dimension of size 1 gets ghosts equal to phi(0), whose
+// difference is 0).  Ghost columns are written into the staged row, ghost
+// rows into the register window; u is zeroed outside the image.  Every item
+// runs the same code, so the work is balanced across warps.
 //
-// BIN instantiations read a binary LSF stored by the previous step (which
-// wrote sign(v) because it re-initialised): |grad phi|^2 then takes only the
-// values 0, 4, 8 (16, 20, 32 at borders) and its square root comes from a
-// 17-entry table filled with sqrtf, exactly.  The other instantiation reads
-// a real LSF (the first step, or a caller-chosen reinit period) and uses
-// sqrtf.
+// BIN instantiations read a binary LSF stored by the previous step: then
+// |grad phi|^2 (in units of 4) takes only the values 0, 4, 8, 16, 20, 32 and
+// its square root comes from a table filled with sqrtf, exactly.  The other
+// instantiation reads a real LSF (the first step, or a caller-chosen reinit
+// period) and uses sqrtf with explicit one-sided differences.
 //
 // The mbarrier waits are bounded: a wait that runs out sets the TIMEOUT
 // status bit, drains the loads still in flight (again bounded) and skips the
@@ -55,25 +56,25 @@
 
 namespace lse_tma {
 
-constexpr int kPhiBox = 136;       // phi floats per staged row
-constexpr int kDataBox = 128;      // data floats per staged row and band
+constexpr int kCols = 256;          // strip width (columns held by a warp)
+constexpr int kPhiBox = kCols + 8;  // phi floats per staged row
 constexpr int kPhiBytes = kPhiBox * 4;
-constexpr int kPhiSlot = 640;      // phi bytes per stage, 128-byte aligned
-constexpr int kDataSlot = kDataBox * 4;
+constexpr int kPhiSlot = 1152;      // phi bytes per stage, 128-byte aligned
+constexpr int kDataSlot = kCols * 4;
 
 enum Kind { K_REGION1 = 0, K_REGION_MB = 1, K_EDGE = 2 };
 
 template <int KIND>
 struct KindTraits {
     static constexpr int NB = KIND == K_REGION_MB ? 4 : 1;   // bands staged
-    static constexpr int PF = KIND == K_REGION_MB ? 4 : 5;   // rows of prefetch
+    static constexpr int PF = KIND == K_REGION_MB ? 3 : 5;   // rows of prefetch
     static constexpr bool REGION = KIND != K_EDGE;
 };
 
 template <int KIND, int RAD>
 struct Geo {
     static constexpr int HL = (RAD + 3) / 4;
-    static constexpr int USEFUL = 4 * (32 - 2 * HL);
+    static constexpr int USEFUL = kCols - 8 * HL;
     static constexpr int P = 2 * RAD + 1;
     static constexpr int S = RAD + 2 + KindTraits<KIND>::PF;
     static constexpr int STAGE = KindTraits<KIND>::NB * kDataSlot + kPhiSlot;
@@ -97,17 +98,6 @@ __device__ __forceinline__ void fence_mbar_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-__device__ __forceinline__ void fence_proxy_async()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 ::"r"(bar), "r"(bytes) : "memory");
-}
-
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
@@ -121,25 +111,52 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map,
-                                            int x, int y, uint32_t bar)
+// Issues one staged row from the lane with `on` set: the proxy fence orders
+// the warp's earlier reads of the stage before the asynchronous copies
+// overwrite it.  phi arrives in two boxes (256 + 8 columns).
+__device__ __forceinline__ void issue_row(bool on, uint32_t bar, uint32_t tx,
+                                          uint32_t dst_data, uint32_t dst_phi,
+                                          const CUtensorMap *dmap,
+                                          const CUtensorMap *pmap,
+                                          const CUtensorMap *tmap, int xs, int y,
+                                          bool three_d)
 {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map,
-                                            int x, int y, int z, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z),
-          "r"(bar)
-        : "memory");
+    const uint64_t dm = reinterpret_cast<uint64_t>(dmap);
+    const uint64_t pm = reinterpret_cast<uint64_t>(pmap);
+    const uint64_t tm = reinterpret_cast<uint64_t>(tmap);
+    if (three_d) {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\t"
+            "setp.ne.b32 q, %0, 0;\n\t"
+            "@q fence.proxy.async.shared::cta;\n\t"
+            "@q mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n\t"
+            "@q cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%3], [%5, {%7, %8}], [%1];\n\t"
+            "@q cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%4], [%13, {%9, %8}], [%1];\n\t"
+            "@q cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%10], [%6, {%11, %8, %12}], [%1];\n\t}"
+            ::"r"((int)on), "r"(bar), "r"(tx), "r"(dst_phi), "r"(dst_phi + 1024u), "l"(pm),
+              "l"(dm), "r"(xs - 4), "r"(y), "r"(xs + kCols - 4), "r"(dst_data), "r"(xs),
+              "r"(0), "l"(tm)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\t"
+            "setp.ne.b32 q, %0, 0;\n\t"
+            "@q fence.proxy.async.shared::cta;\n\t"
+            "@q mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n\t"
+            "@q cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%3], [%5, {%7, %8}], [%1];\n\t"
+            "@q cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%4], [%12, {%9, %8}], [%1];\n\t"
+            "@q cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%10], [%6, {%11, %8}], [%1];\n\t}"
+            ::"r"((int)on), "r"(bar), "r"(tx), "r"(dst_phi), "r"(dst_phi + 1024u), "l"(pm),
+              "l"(dm), "r"(xs - 4), "r"(y), "r"(xs + kCols - 4), "r"(dst_data), "r"(xs),
+              "l"(tm)
+            : "memory");
+    }
 }
 
 // Bounded wait on one stage; warp-uniform result.
@@ -161,11 +178,6 @@ __device__ __forceinline__ float4 ld4(const float *p)
     return *reinterpret_cast<const float4 *>(p);
 }
 
-__device__ __forceinline__ float4 bin4(float4 v)
-{
-    return make_float4(bin(v.x), bin(v.y), bin(v.z), bin(v.w));
-}
-
 __device__ __forceinline__ float comp(const float4 &v, int j)
 {
     return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
@@ -173,9 +185,10 @@ __device__ __forceinline__ float comp(const float4 &v, int j)
 
 // ---------------------------------------------------------------- kernel
 template <int KIND, int RAD, bool BIN>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(128, 2)
 step_tma_kernel(const __grid_constant__ StepArgs a,
                 const __grid_constant__ CUtensorMap phi_map,
+                const __grid_constant__ CUtensorMap phi_tail_map,
                 const __grid_constant__ CUtensorMap data_map)
 {
     using G = Geo<KIND, RAD>;
@@ -183,7 +196,8 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
     constexpr int HL = G::HL, P = G::P, S = G::S;
     constexpr int NB = T::NB;
     constexpr int SF = G::STAGE / 4;         // floats per stage
-    constexpr int PHI = NB * kDataBox;       // float offset of phi in a stage
+    constexpr int PHI = NB * kCols;          // float offset of phi in a stage
+    constexpr int C = 8;                     // columns per lane (A: 0..3, B: 4..7)
 
     LseDevState *st = a.st;
     if (st->done || (st->status_bits & LSE_SBIT_ABORT)) return;
@@ -249,17 +263,9 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
     };
     if (my_items > 0) origin(0, p_xs, p_y);
     auto issue_one = [&]() {
-        if (lane == 0) {
-            const uint32_t bar = bar0 + 8 * p_stage;
-            const uint32_t dst = ring0 + (uint32_t)(p_stage * G::STAGE);
-            fence_proxy_async();
-            mbar_expect_tx(bar, tx_bytes);
-            tma_load_2d(dst + PHI * 4, &phi_map, p_xs - 4, p_y, bar);
-            if (KIND == K_REGION_MB)
-                tma_load_3d(dst, &data_map, p_xs, p_y, 0, bar);
-            else
-                tma_load_2d(dst, &data_map, p_xs, p_y, bar);
-        }
+        const uint32_t dst = ring0 + (uint32_t)(p_stage * G::STAGE);
+        issue_row(lane == 0, bar0 + 8 * p_stage, tx_bytes, dst, dst + PHI * 4,
+                  &data_map, &phi_map, &phi_tail_map, p_xs, p_y, KIND == K_REGION_MB);
         ++p_seq;
         ++p_y;
         p_stage = (p_stage + 1 == S) ? 0 : p_stage + 1;
@@ -300,33 +306,38 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
         fsw[b] = fsa[b] = 0.0f;
         dsw[b] = dsa[b] = 0.0;
     }
-    const bool lane_out = lane >= HL && lane < 32 - HL;
+    // output lanes: A's lanes from HL on, B's lanes below 32 - HL
+    const bool outA = lane >= HL, outB = lane < 32 - HL;
+    const int offA = 4 * lane, offB = 128 + 4 * lane;   // data offsets
 
     for (int k = 0; k < my_items && !failed; ++k) {
         const int base = k * NR;
         int xs, ys;
         origin(k, xs, ys);
-        const int x0 = xs + 4 * lane;
+        const int xA = xs + offA, xB = xs + offB;
         // per-column masks (1 or 0): u inside the image, output columns
-        float inf[4], okf[4];
-        bool oneL[4], oneR[4];
+        float inf[C], okf[C];
+        bool oneL[C], oneR[C];
         int nvalid = 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int x = x0 + j;
+        for (int j = 0; j < C; ++j) {
+            const int x = (j < 4 ? xA : xB) + (j & 3);
+            const bool out = j < 4 ? outA : outB;
             inf[j] = (x >= 0 && x < W) ? 1.0f : 0.0f;
-            okf[j] = (lane_out && x < W) ? 1.0f : 0.0f;
-            nvalid += (lane_out && x < W) ? 1 : 0;
+            okf[j] = (out && x < W) ? 1.0f : 0.0f;
+            nvalid += (out && x < W) ? 1 : 0;
             oneL[j] = x == 0;
             oneR[j] = x == W - 1;
         }
         // uniform per item: does the strip touch the image's left/right edge,
-        // and is every output lane's float4 inside the image?
-        const bool xborder = xs < 0 || xs + 128 > W;
-        const bool ragged = xs + 4 * (32 - HL) > W;
-        const bool full = lane_out && x0 + 3 < W;
+        // and does an output float4 cross the right edge?
+        const bool xborder = xs < 0 || xs + kCols > W;
+        const bool ragged = xs + kCols - 4 * HL > W;
+        const bool fullA = outA && xA + 3 < W, fullB = outB && xB + 3 < W;
         const bool ghost_l = xs <= 0;                    // x = -1 in this strip
-        const bool ghost_r = xs <= W - 1 && W - 1 < xs + 128;
+        const bool ghost_r = xs <= W - 1 && W - 1 < xs + kCols;
+        // last u-row whose output row lies inside the image
+        const int r_out_max = H - 1 - ys + RAD;
 
         // ghost columns of a staged binary row (lane 0; BIN only)
         auto patch = [&](int stage) {
@@ -358,20 +369,36 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
         const int s_b = wait_one();
         patch(s_a);
         patch(s_b);
-        float4 p0 = ld4(&smem_f[ring + s_a * SF + PHI + 4 + 4 * lane]);
-        float4 pp = ld4(&smem_f[ring + s_b * SF + PHI + 4 + 4 * lane]);
-        if (binarise_in) {
-            p0 = bin4(p0);
-            pp = bin4(pp);
+        float p0[C], pp[C], pm[C];
+        {
+            const int ra = ring + s_a * SF + PHI, rb = ring + s_b * SF + PHI;
+            const float4 a0 = ld4(&smem_f[ra + 4 + offA]), b0 = ld4(&smem_f[ra + 4 + offB]);
+            const float4 a1 = ld4(&smem_f[rb + 4 + offA]), b1 = ld4(&smem_f[rb + 4 + offB]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                p0[j] = comp(a0, j);
+                p0[4 + j] = comp(b0, j);
+                pp[j] = comp(a1, j);
+                pp[4 + j] = comp(b1, j);
+            }
+            if (binarise_in) {
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    p0[j] = bin(p0[j]);
+                    pp[j] = bin(pp[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < C; ++j) pm[j] = p0[j];
         }
-        float4 pm = p0;
-        float ring_h[P][4];
+        float ring_h[P][C];
 
         // one u-row: u of row r, its horizontal pass into ring slot kk, and
-        // (OUT) the vertical pass, store and statistics of row r - RAD
-        auto row = [&](const int r, const int kk, const bool OUT) {
+        // (when r >= 2 RAD + 1) the vertical pass, store and statistics of
+        // row r - RAD
+        auto row = [&](const int r, const int kk) {
             __syncwarp();
-            if (r > RAD && p_seq < total_seq && p_seq <= base + r - RAD + S - 1) issue_one();
+            if (r > RAD && p_seq < total_seq) issue_one();
             const int sn = wait_one();          // stage of row r + 1
             patch(sn);
             int sr = sn - 1;
@@ -379,112 +406,162 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
             int so = sn - 1 - RAD;
             if (so < 0) so += S;
             const int rowN = ring + sn * SF, rowR = ring + sr * SF, rowO = ring + so * SF;
-            pm = p0;
-            p0 = pp;
-            pp = ld4(&smem_f[rowN + PHI + 4 + 4 * lane]);
-            if (binarise_in) pp = bin4(pp);
-            // x-neighbours of this lane's columns in row r
-            float lft = __shfl_up_sync(0xffffffffu, p0.w, 1);
-            float rgt = __shfl_down_sync(0xffffffffu, p0.x, 1);
-            {
-                float e = smem_f[rowR + PHI + (lane == 0 ? 3 : 132)];
-                if (binarise_in) e = bin(e);
-                if (lane == 0) lft = e;
-                if (lane == 31) rgt = e;
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                pm[j] = p0[j];
+                p0[j] = pp[j];
             }
-            // ghost rows (uniform per row)
-            const int y = ys + r;
-            float4 pmx = pm, ppx = pp;
-            if (y <= 0 || y >= H - 1) {
-                if (H == 1) {
-                    pmx = p0;
-                    ppx = p0;
-                } else if (y == 0) {
-                    pmx = make_float4(2.f * p0.x - pp.x, 2.f * p0.y - pp.y,
-                                      2.f * p0.z - pp.z, 2.f * p0.w - pp.w);
-                } else if (y == H - 1) {
-                    ppx = make_float4(2.f * p0.x - pm.x, 2.f * p0.y - pm.y,
-                                      2.f * p0.z - pm.z, 2.f * p0.w - pm.w);
+            {
+                const float4 na = ld4(&smem_f[rowN + PHI + 4 + offA]);
+                const float4 nb = ld4(&smem_f[rowN + PHI + 4 + offB]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    pp[j] = comp(na, j);
+                    pp[4 + j] = comp(nb, j);
+                }
+                if (binarise_in) {
+#pragma unroll
+                    for (int j = 0; j < C; ++j) pp[j] = bin(pp[j]);
                 }
             }
-            const bool yin = y >= 0 && y < H;
+            // x-neighbours of the lane's columns in row r
+            float lA = __shfl_up_sync(0xffffffffu, p0[3], 1);           // A lane-1
+            float rB = __shfl_down_sync(0xffffffffu, p0[4], 1);         // B lane+1
+            const float rA = __shfl_sync(0xffffffffu, lane == 0 ? p0[4] : p0[0], (lane + 1) & 31);
+            const float lB = __shfl_sync(0xffffffffu, lane == 31 ? p0[3] : p0[7], (lane + 31) & 31);
+            {
+                float e = smem_f[rowR + PHI + (lane == 0 ? 3 : 4 + kCols)];
+                if (binarise_in) e = bin(e);
+                if (lane == 0) lA = e;
+                if (lane == 31) rB = e;
+            }
+            // ghost rows and rows outside the image (uniform per row)
+            const int y = ys + r;
+            float pmx[C], ppx[C];
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                pmx[j] = pm[j];
+                ppx[j] = pp[j];
+            }
+            bool yin = true;
+            if ((unsigned)(y - 1) >= (unsigned)(H - 2)) {   // y <= 0 or y >= H - 1
+                yin = y >= 0 && y < H;
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    if (H == 1) {
+                        pmx[j] = p0[j];
+                        ppx[j] = p0[j];
+                    } else if (y == 0) {
+                        pmx[j] = 2.f * p0[j] - pp[j];
+                    } else if (y == H - 1) {
+                        ppx[j] = 2.f * p0[j] - pm[j];
+                    }
+                }
+            }
             // data term factor t = 0.5 dt R
-            float t[4];
-            if (KIND == K_EDGE) {
-                const float4 g4 = ld4(&smem_f[rowR + 4 * lane]);
+            float t[C];
+            {
+                const float4 da = ld4(&smem_f[rowR + offA]), db = ld4(&smem_f[rowR + offB]);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) t[j] = half_dt * comp(g4, j);
-            } else {
-                const float4 d4 = ld4(&smem_f[rowR + 4 * lane]);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) t[j] = coef[0] * (comp(d4, j) - mid[0]);
+                for (int j = 0; j < 4; ++j) {
+                    if (KIND == K_EDGE) {
+                        t[j] = half_dt * comp(da, j);
+                        t[4 + j] = half_dt * comp(db, j);
+                    } else {
+                        t[j] = coef[0] * (comp(da, j) - mid[0]);
+                        t[4 + j] = coef[0] * (comp(db, j) - mid[0]);
+                    }
+                }
                 if (KIND == K_REGION_MB) {
 #pragma unroll
                     for (int b = 1; b < NB; ++b) {
                         if (b < B) {
-                            const float4 e4 = ld4(&smem_f[rowR + b * kDataBox + 4 * lane]);
+                            const float4 ea = ld4(&smem_f[rowR + b * kCols + offA]);
+                            const float4 eb = ld4(&smem_f[rowR + b * kCols + offB]);
 #pragma unroll
-                            for (int j = 0; j < 4; ++j)
-                                t[j] = fmaf(coef[b], comp(e4, j) - mid[b], t[j]);
+                            for (int j = 0; j < 4; ++j) {
+                                t[j] = fmaf(coef[b], comp(ea, j) - mid[b], t[j]);
+                                t[4 + j] = fmaf(coef[b], comp(eb, j) - mid[b], t[4 + j]);
+                            }
                         }
                     }
                 }
             }
             // u = phi + t * 2|grad phi| (zero outside the image)
-            const float c[6] = {lft, p0.x, p0.y, p0.z, p0.w, rgt};
-            float u[4];
+            const float cA[6] = {lA, p0[0], p0[1], p0[2], p0[3], rA};
+            const float cB[6] = {lB, p0[4], p0[5], p0[6], p0[7], rB};
+            float u[C];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float dx = c[j + 2] - c[j];
+            for (int j = 0; j < C; ++j) {
+                const float *cc = j < 4 ? cA : cB;
+                const int jj = j & 3;
+                float dx = cc[jj + 2] - cc[jj];
                 if (!BIN) {    // real LSF: one-sided differences by flags
                     if (W == 1) dx = 0.0f;
-                    else if (oneL[j]) dx = 2.0f * (c[j + 2] - c[j + 1]);
-                    else if (oneR[j]) dx = 2.0f * (c[j + 1] - c[j]);
+                    else if (oneL[j]) dx = 2.0f * (cc[jj + 2] - cc[jj + 1]);
+                    else if (oneR[j]) dx = 2.0f * (cc[jj + 1] - cc[jj]);
                 }
-                const float dy = comp(ppx, j) - comp(pmx, j);
+                const float dy = ppx[j] - pmx[j];
                 const float q = fmaf(dx, dx, dy * dy);
                 float s2;
                 if (BIN)
                     s2 = smem_f[lut + ((__float_as_uint(q) >> 21) & 31u)];
                 else
                     s2 = sqrtf(q);
-                u[j] = fmaf(t[j], s2, c[j + 1]);
+                u[j] = fmaf(t[j], s2, cc[jj + 1]);
             }
             if (xborder) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) u[j] *= inf[j];
+                for (int j = 0; j < C; ++j) u[j] *= inf[j];
             }
             if (!yin) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) u[j] = 0.0f;
+                for (int j = 0; j < C; ++j) u[j] = 0.0f;
             }
-            // horizontal pass: U[c + 4 HL] = u at relative column c
-            float U[4 + 8 * HL];
+            // horizontal pass.  UA[c + 4 HL], UB[c + 4 HL] = u at column c
+            // relative to the lane's first A / B column.
+            float UA[4 + 8 * HL], UB[4 + 8 * HL];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) U[4 * HL + j] = u[j];
+            for (int j = 0; j < 4; ++j) {
+                UA[4 * HL + j] = u[j];
+                UB[4 * HL + j] = u[4 + j];
+            }
 #pragma unroll
             for (int o = 1; o <= HL; ++o) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    if (j - 4 * o >= -RAD)
-                        U[4 * HL + j - 4 * o] = __shfl_up_sync(0xffffffffu, u[j], o);
-                    if (j + 4 * o <= 3 + RAD)
-                        U[4 * HL + j + 4 * o] = __shfl_down_sync(0xffffffffu, u[j], o);
+                    if (j - 4 * o >= -RAD) {
+                        // A: lane - o (A's first lanes are halo: no wrap)
+                        UA[4 * HL + j - 4 * o] = __shfl_up_sync(0xffffffffu, u[j], o);
+                        // B: lane - o, wrapping to A's last lanes
+                        UB[4 * HL + j - 4 * o] = __shfl_sync(
+                            0xffffffffu, lane >= 32 - o ? u[j] : u[4 + j], (lane + 32 - o) & 31);
+                    }
+                    if (j + 4 * o <= 3 + RAD) {
+                        // A: lane + o, wrapping to B's first lanes
+                        UA[4 * HL + j + 4 * o] = __shfl_sync(
+                            0xffffffffu, lane < o ? u[4 + j] : u[j], (lane + o) & 31);
+                        // B: lane + o (B's last lanes are halo: no wrap)
+                        UB[4 * HL + j + 4 * o] = __shfl_down_sync(0xffffffffu, u[4 + j], o);
+                    }
                 }
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float h = tp[0] * U[4 * HL + j];
+                float ha = tp[0] * UA[4 * HL + j], hb = tp[0] * UB[4 * HL + j];
 #pragma unroll
-                for (int q = 1; q <= RAD; ++q)
-                    h = fmaf(tp[q], U[4 * HL + j - q] + U[4 * HL + j + q], h);
-                ring_h[kk][j] = h;
+                for (int q = 1; q <= RAD; ++q) {
+                    ha = fmaf(tp[q], UA[4 * HL + j - q] + UA[4 * HL + j + q], ha);
+                    hb = fmaf(tp[q], UB[4 * HL + j - q] + UB[4 * HL + j + q], hb);
+                }
+                ring_h[kk][j] = ha;
+                ring_h[kk][4 + j] = hb;
             }
-            if (!OUT) return;
+            if (r < 2 * RAD + 1 || r > r_out_max) return;
             // vertical pass of row r - RAD
-            float v[4];
+            float v[C];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < C; ++j) {
                 float acc = tp[0] * ring_h[(kk - RAD + P) % P][j];
 #pragma unroll
                 for (int q = 1; q <= RAD; ++q)
@@ -495,65 +572,46 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
                 v[j] = acc;
             }
             const int yo = ys + r - RAD;
-            if (yo >= H) return;
-            float *dst = a.phi_out + (size_t)yo * a.pitch + x0;
-            if (store_bin) {
-                // w = sign(v): the count is (sum w + valid) / 2 and the band sums
-                // over v >= 0 are (sum d + sum d w) / 2 (d zero off the image)
-                float w[4];
+            float *dst = a.phi_out + (size_t)yo * a.pitch + xs;
+            // w = sign(v): the count is (sum w + valid) / 2 and the band sums
+            // over v >= 0 are (sum d + sum d w) / 2 (d zero off the image)
+            float w[C];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) w[j] = v[j] >= 0.0f ? 1.0f : -1.0f;
-                if (full) *reinterpret_cast<float4 *>(dst) = make_float4(w[0], w[1], w[2], w[3]);
-                if (ragged && !full) {
+            for (int j = 0; j < C; ++j) w[j] = v[j] >= 0.0f ? 1.0f : -1.0f;
+            float sv[C];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (okf[j] != 0.0f) dst[j] = w[j];
+            for (int j = 0; j < C; ++j) sv[j] = store_bin ? w[j] : v[j];
+            if (fullA) *reinterpret_cast<float4 *>(dst + offA) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+            if (fullB) *reinterpret_cast<float4 *>(dst + offB) = make_float4(sv[4], sv[5], sv[6], sv[7]);
+            if (ragged) {
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    const bool full = j < 4 ? fullA : fullB;
+                    if (!full && okf[j] != 0.0f) dst[(j < 4 ? offA : offB) + (j & 3)] = sv[j];
                 }
+            }
+            if (count_flips) {
+                const float4 oa = ld4(&smem_f[rowO + PHI + 4 + offA]);
+                const float4 ob = ld4(&smem_f[rowO + PHI + 4 + offB]);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) fsw_cnt = fmaf(w[j], okf[j], fsw_cnt);
-                if (T::REGION) {
-#pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        if (b < B) {
-                            const float4 e4 = ld4(&smem_f[rowO + b * kDataBox + 4 * lane]);
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                const float d = comp(e4, j) * okf[j];
-                                fsw[b] = fmaf(d, w[j], fsw[b]);
-                                fsa[b] += d;
-                            }
-                        }
-                    }
+                for (int j = 0; j < 4; ++j) {
+                    nflip += (okf[j] != 0.0f) && ((w[j] > 0.0f) != (comp(oa, j) >= 0.0f));
+                    nflip += (okf[4 + j] != 0.0f) && ((w[4 + j] > 0.0f) != (comp(ob, j) >= 0.0f));
                 }
-            } else {
-                if (full) *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
-                if (ragged && !full) {
+            }
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (okf[j] != 0.0f) dst[j] = v[j];
-                }
-                float w[4];
+            for (int j = 0; j < C; ++j) fsw_cnt = fmaf(w[j], okf[j], fsw_cnt);
+            if (T::REGION) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) w[j] = v[j] >= 0.0f ? 1.0f : -1.0f;
-                if (count_flips) {
-                    const float4 o4 = ld4(&smem_f[rowO + PHI + 4 + 4 * lane]);
+                for (int b = 0; b < NB; ++b) {
+                    if (b < B) {
+                        const float4 ea = ld4(&smem_f[rowO + b * kCols + offA]);
+                        const float4 eb = ld4(&smem_f[rowO + b * kCols + offB]);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        nflip += (okf[j] != 0.0f) && ((w[j] > 0.0f) != (comp(o4, j) >= 0.0f));
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) fsw_cnt = fmaf(w[j], okf[j], fsw_cnt);
-                if (T::REGION) {
-#pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        if (b < B) {
-                            const float4 e4 = ld4(&smem_f[rowO + b * kDataBox + 4 * lane]);
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                const float d = comp(e4, j) * okf[j];
-                                fsw[b] = fmaf(d, w[j], fsw[b]);
-                                fsa[b] += d;
-                            }
+                        for (int j = 0; j < C; ++j) {
+                            const float d = (j < 4 ? comp(ea, j) : comp(eb, j - 4)) * okf[j];
+                            fsw[b] = fmaf(d, w[j], fsw[b]);
+                            fsa[b] += d;
                         }
                     }
                 }
@@ -572,10 +630,10 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
         for (int per = 0; per < n_per && !failed; ++per) {
             const int r0 = 1 + per * P;
 #pragma unroll
-            for (int kk = 0; kk < P; ++kk) row(r0 + kk, kk, r0 + kk >= 2 * RAD + 1);
+            for (int kk = 0; kk < P; ++kk) row(r0 + kk, kk);
             fold();
         }
-        // exact integer count: fsw_cnt holds sum w (|sum| <= 4 th) exactly;
+        // exact integer count: fsw_cnt holds sum w (|sum| <= 8 th) exactly;
         // rows at or beyond H produced no output
         {
             const int y0 = ys + RAD + 1;
@@ -626,8 +684,8 @@ int smem_bytes(int wpc)
 
 template <int KIND, int RAD>
 cudaError_t launch_one(const StepArgs &a, const CUtensorMap &pm,
-                       const CUtensorMap &dm, int nblocks, int wpc,
-                       cudaStream_t s)
+                       const CUtensorMap &tm, const CUtensorMap &dm, int nblocks,
+                       int wpc, cudaStream_t s)
 {
     const int smem = smem_bytes<KIND, RAD>(wpc);
     auto kern = a.binary_in ? step_tma_kernel<KIND, RAD, true>
@@ -635,23 +693,23 @@ cudaError_t launch_one(const StepArgs &a, const CUtensorMap &pm,
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem);
     if (e != cudaSuccess) return e;
-    kern<<<nblocks, 32 * wpc, smem, s>>>(a, pm, dm);
+    kern<<<nblocks, 32 * wpc, smem, s>>>(a, pm, tm, dm);
     return cudaGetLastError();
 }
 
 template <int KIND>
 cudaError_t launch_kind(const StepArgs &a, const CUtensorMap &pm,
-                        const CUtensorMap &dm, int nblocks, int wpc,
-                        cudaStream_t s)
+                        const CUtensorMap &tm, const CUtensorMap &dm, int nblocks,
+                        int wpc, cudaStream_t s)
 {
     switch (a.rad) {
-    case 1: return launch_one<KIND, 1>(a, pm, dm, nblocks, wpc, s);
-    case 2: return launch_one<KIND, 2>(a, pm, dm, nblocks, wpc, s);
-    case 3: return launch_one<KIND, 3>(a, pm, dm, nblocks, wpc, s);
-    case 4: return launch_one<KIND, 4>(a, pm, dm, nblocks, wpc, s);
-    case 5: return launch_one<KIND, 5>(a, pm, dm, nblocks, wpc, s);
-    case 6: return launch_one<KIND, 6>(a, pm, dm, nblocks, wpc, s);
-    case 7: return launch_one<KIND, 7>(a, pm, dm, nblocks, wpc, s);
+    case 1: return launch_one<KIND, 1>(a, pm, tm, dm, nblocks, wpc, s);
+    case 2: return launch_one<KIND, 2>(a, pm, tm, dm, nblocks, wpc, s);
+    case 3: return launch_one<KIND, 3>(a, pm, tm, dm, nblocks, wpc, s);
+    case 4: return launch_one<KIND, 4>(a, pm, tm, dm, nblocks, wpc, s);
+    case 5: return launch_one<KIND, 5>(a, pm, tm, dm, nblocks, wpc, s);
+    case 6: return launch_one<KIND, 6>(a, pm, tm, dm, nblocks, wpc, s);
+    case 7: return launch_one<KIND, 7>(a, pm, tm, dm, nblocks, wpc, s);
     default: return cudaErrorNotSupported;
     }
 }
