@@ -587,15 +587,12 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
     int nblocks = 0, wpc = 0;
     bool use_tma = !ctx->force_generic &&
                    plan_step_tma(H, W, a.B, p.term, a.rad, ctx->sm_count, &a, &nblocks, &wpc);
-    // the fused step stages 264 phi columns per row (boxes of 256 and 8)
-    // and 256 data columns per band
-    CUtensorMap phi_maps[2], phi_tail_maps[2], data_map;
+    // the fused step stages 136 phi columns and 128 data columns per band
+    CUtensorMap phi_maps[2], data_map;
     if (use_tma) {
-        use_tma = encode_rows(&phi_maps[0], ctx->phi[0], W, H, pitch, 0, 1, 256) &&
-                  encode_rows(&phi_maps[1], ctx->phi[1], W, H, pitch, 0, 1, 256) &&
-                  encode_rows(&phi_tail_maps[0], ctx->phi[0], W, H, pitch, 0, 1, 8) &&
-                  encode_rows(&phi_tail_maps[1], ctx->phi[1], W, H, pitch, 0, 1, 8) &&
-                  encode_rows(&data_map, data, W, H, pitch, band_stride, a.B, 256);
+        use_tma = encode_rows(&phi_maps[0], ctx->phi[0], W, H, pitch, 0, 1, 136) &&
+                  encode_rows(&phi_maps[1], ctx->phi[1], W, H, pitch, 0, 1, 136) &&
+                  encode_rows(&data_map, data, W, H, pitch, band_stride, a.B, 128);
     }
     if (!use_tma) nblocks = ctx->sm_count * 4;
 
@@ -624,8 +621,7 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
         // sign changes matter for the early stop and the last step's statistics
         a.count_flips = (p.early_stop_frac > 0.0f || n == p.iterations - 1) ? 1 : 0;
         if (use_tma)
-            e = launch_step_tma(a, phi_maps[n & 1], phi_tail_maps[n & 1], data_map, nblocks,
-                                wpc, s);
+            e = launch_step_tma(a, phi_maps[n & 1], data_map, nblocks, wpc, s);
         else
             e = launch_step_generic(a, nblocks, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step");

@@ -138,7 +138,6 @@ cudaError_t launch_step_generic(const StepArgs &a, int nblocks, cudaStream_t s);
 // TMA step: returns cudaErrorNotSupported when no instantiation fits
 // (radius or band count), so the caller can take the generic kernel.
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap &phi_map,
-                            const CUtensorMap &phi_tail_map,
                             const CUtensorMap &data_map, int nblocks,
                             int warps_per_block, cudaStream_t s);
 // Work decomposition of the TMA step for a shape on `sm_count` SMs.

@@ -5,11 +5,11 @@
 
 namespace lse_detail {
 
-cudaError_t launch_step_tma_region1(const StepArgs &, const CUtensorMap &, const CUtensorMap &,
+cudaError_t launch_step_tma_region1(const StepArgs &, const CUtensorMap &,
                                    const CUtensorMap &, int, int, cudaStream_t);
-cudaError_t launch_step_tma_edge(const StepArgs &, const CUtensorMap &, const CUtensorMap &,
+cudaError_t launch_step_tma_edge(const StepArgs &, const CUtensorMap &,
                                    const CUtensorMap &, int, int, cudaStream_t);
-cudaError_t launch_step_tma_multiband(const StepArgs &, const CUtensorMap &, const CUtensorMap &,
+cudaError_t launch_step_tma_multiband(const StepArgs &, const CUtensorMap &,
                                    const CUtensorMap &, int, int, cudaStream_t);
 int step_tma_warp_bytes_region1(int rad);
 int step_tma_warp_bytes_edge(int rad);
@@ -38,15 +38,15 @@ bool plan_step_tma(int H, int W, int B, int term, int rad, int sm_count,
     int per_warp = kind == lse_tma::K_EDGE ? step_tma_warp_bytes_edge(rad)
                  : kind == lse_tma::K_REGION1 ? step_tma_warp_bytes_region1(rad)
                                               : step_tma_warp_bytes_multiband(rad);
-    // 2 CTAs of up to 4 warps per SM (8 warps of up to 255 registers): each
+    // 2 CTAs of up to 8 warps per SM (16 warps of up to 128 registers): each
     // CTA gets 113 KB of the SM's 228 KB less 1 KB reserved; 6 KB of that is
     // the reduction's static shared memory
     const int budget = (113 - 6) * 1024 - 256;
     int wpc = budget / per_warp;
-    if (wpc > 4) wpc = 4;
+    if (wpc > 8) wpc = 8;
     if (wpc < 1) return false;
     const int hl = (rad + 3) / 4;
-    const int useful = 256 - 8 * hl;
+    const int useful = 128 - 8 * hl;
     const int n_strips = (W + useful - 1) / useful;
     const int max_warps = sm_count * 2 * wpc;
     int per_strip = max_warps / n_strips;
@@ -72,17 +72,16 @@ bool plan_step_tma(int H, int W, int B, int term, int rad, int sm_count,
 }
 
 cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap &phi_map,
-                            const CUtensorMap &phi_tail_map,
                             const CUtensorMap &data_map, int nblocks,
                             int warps_per_block, cudaStream_t s)
 {
     switch (kind_of(a.term, a.B)) {
     case lse_tma::K_EDGE:
-        return launch_step_tma_edge(a, phi_map, phi_tail_map, data_map, nblocks, warps_per_block, s);
+        return launch_step_tma_edge(a, phi_map, data_map, nblocks, warps_per_block, s);
     case lse_tma::K_REGION1:
-        return launch_step_tma_region1(a, phi_map, phi_tail_map, data_map, nblocks, warps_per_block, s);
+        return launch_step_tma_region1(a, phi_map, data_map, nblocks, warps_per_block, s);
     default:
-        return launch_step_tma_multiband(a, phi_map, phi_tail_map, data_map, nblocks, warps_per_block, s);
+        return launch_step_tma_multiband(a, phi_map, data_map, nblocks, warps_per_block, s);
     }
 }
 

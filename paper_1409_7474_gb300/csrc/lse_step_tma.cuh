@@ -9,21 +9,21 @@
 // band sums over v >= 0, plus the number of sign changes when asked.  The
 // last CTA finalises c+/c- and the next step's coefficients.
 //
-// Work decomposition.  Each warp owns a vertical strip of 256 columns and a
-// block of `th` output rows ("item").  Lane l holds eight columns: half A at
-// xs + 4l .. +3 and half B at xs + 128 + 4l .. +3.  The outermost HL lanes
-// (A's first, B's last) only supply the Gaussian's horizontal halo, so a
-// strip yields 256 - 8 HL output columns.  The warp streams down its strip
-// one row at a time:
+// Work decomposition.  Each warp owns a vertical strip of 128 columns and a
+// block of `th` output rows ("item").  Lane l holds columns xs + 4l .. +3.
+// The outermost HL lanes on each side only supply the Gaussian's horizontal
+// halo, so a strip yields 4 (32 - 2 HL) output columns.  (Eight columns per
+// lane halves the per-row bookkeeping but needs twice the registers, and
+// the lost occupancy costs more than it saves.)  The warp streams down its
+// strip one row at a time:
 //   * TMA (cp.async.bulk.tensor, zero fill outside the image) loads each row
-//     of phi (264 floats: the strip and 4 columns each side, in two boxes)
-//     and of the data term (256 floats per band) into a per-warp ring of
-//     shared-memory stages with one mbarrier each; the warp issues its own
-//     loads (one predicated lane) up to PF rows ahead of use;
+//     of phi (136 floats: the strip and 4 columns each side) and of the data
+//     term (128 floats per band) into a per-warp ring of shared-memory
+//     stages with one mbarrier each; the warp issues its own loads (one
+//     predicated lane) up to PF rows ahead of use;
 //   * phi rows y-1, y, y+1 sit in registers; u of row y is computed in
 //     registers; the horizontal Gaussian pass takes neighbouring lanes' u by
-//     warp shuffles (A's last lane and B's first lane exchange across the
-//     halves);
+//     warp shuffles;
 //   * the vertical pass keeps the last 2 RAD + 1 horizontally smoothed rows
 //     in a register ring; the row loop is unrolled by the ring period, so
 //     ring indices are compile-time constants;
@@ -56,10 +56,10 @@
 
 namespace lse_tma {
 
-constexpr int kCols = 256;          // strip width (columns held by a warp)
+constexpr int kCols = 128;          // strip width (columns held by a warp)
 constexpr int kPhiBox = kCols + 8;  // phi floats per staged row
 constexpr int kPhiBytes = kPhiBox * 4;
-constexpr int kPhiSlot = 1152;      // phi bytes per stage, 128-byte aligned
+constexpr int kPhiSlot = 640;       // phi bytes per stage, 128-byte aligned
 constexpr int kDataSlot = kCols * 4;
 
 enum Kind { K_REGION1 = 0, K_REGION_MB = 1, K_EDGE = 2 };
@@ -74,7 +74,7 @@ struct KindTraits {
 template <int KIND, int RAD>
 struct Geo {
     static constexpr int HL = (RAD + 3) / 4;
-    static constexpr int USEFUL = kCols - 8 * HL;
+    static constexpr int USEFUL = kCols - 8 * HL;   // 4 (32 - 2 HL)
     static constexpr int P = 2 * RAD + 1;
     static constexpr int S = RAD + 2 + KindTraits<KIND>::PF;
     static constexpr int STAGE = KindTraits<KIND>::NB * kDataSlot + kPhiSlot;
@@ -113,17 +113,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 
 // Issues one staged row from the lane with `on` set: the proxy fence orders
 // the warp's earlier reads of the stage before the asynchronous copies
-// overwrite it.  phi arrives in two boxes (256 + 8 columns).
+// overwrite it.
 __device__ __forceinline__ void issue_row(bool on, uint32_t bar, uint32_t tx,
                                           uint32_t dst_data, uint32_t dst_phi,
                                           const CUtensorMap *dmap,
-                                          const CUtensorMap *pmap,
-                                          const CUtensorMap *tmap, int xs, int y,
+                                          const CUtensorMap *pmap, int xs, int y,
                                           bool three_d)
 {
     const uint64_t dm = reinterpret_cast<uint64_t>(dmap);
     const uint64_t pm = reinterpret_cast<uint64_t>(pmap);
-    const uint64_t tm = reinterpret_cast<uint64_t>(tmap);
     if (three_d) {
         asm volatile(
             "{\n\t.reg .pred q;\n\t"
@@ -131,14 +129,11 @@ __device__ __forceinline__ void issue_row(bool on, uint32_t bar, uint32_t tx,
             "@q fence.proxy.async.shared::cta;\n\t"
             "@q mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n\t"
             "@q cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%3], [%5, {%7, %8}], [%1];\n\t"
-            "@q cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%4], [%13, {%9, %8}], [%1];\n\t"
+            " [%3], [%4, {%6, %7}], [%1];\n\t"
             "@q cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%10], [%6, {%11, %8, %12}], [%1];\n\t}"
-            ::"r"((int)on), "r"(bar), "r"(tx), "r"(dst_phi), "r"(dst_phi + 1024u), "l"(pm),
-              "l"(dm), "r"(xs - 4), "r"(y), "r"(xs + kCols - 4), "r"(dst_data), "r"(xs),
-              "r"(0), "l"(tm)
+            " [%8], [%5, {%9, %7, %10}], [%1];\n\t}"
+            ::"r"((int)on), "r"(bar), "r"(tx), "r"(dst_phi), "l"(pm), "l"(dm), "r"(xs - 4),
+              "r"(y), "r"(dst_data), "r"(xs), "r"(0)
             : "memory");
     } else {
         asm volatile(
@@ -147,14 +142,11 @@ __device__ __forceinline__ void issue_row(bool on, uint32_t bar, uint32_t tx,
             "@q fence.proxy.async.shared::cta;\n\t"
             "@q mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n\t"
             "@q cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%3], [%5, {%7, %8}], [%1];\n\t"
+            " [%3], [%4, {%6, %7}], [%1];\n\t"
             "@q cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%4], [%12, {%9, %8}], [%1];\n\t"
-            "@q cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%10], [%6, {%11, %8}], [%1];\n\t}"
-            ::"r"((int)on), "r"(bar), "r"(tx), "r"(dst_phi), "r"(dst_phi + 1024u), "l"(pm),
-              "l"(dm), "r"(xs - 4), "r"(y), "r"(xs + kCols - 4), "r"(dst_data), "r"(xs),
-              "l"(tm)
+            " [%8], [%5, {%9, %7}], [%1];\n\t}"
+            ::"r"((int)on), "r"(bar), "r"(tx), "r"(dst_phi), "l"(pm), "l"(dm), "r"(xs - 4),
+              "r"(y), "r"(dst_data), "r"(xs)
             : "memory");
     }
 }
@@ -185,10 +177,9 @@ __device__ __forceinline__ float comp(const float4 &v, int j)
 
 // ---------------------------------------------------------------- kernel
 template <int KIND, int RAD, bool BIN>
-__global__ void __launch_bounds__(128, 2)
+__global__ void __launch_bounds__(256, 2)
 step_tma_kernel(const __grid_constant__ StepArgs a,
                 const __grid_constant__ CUtensorMap phi_map,
-                const __grid_constant__ CUtensorMap phi_tail_map,
                 const __grid_constant__ CUtensorMap data_map)
 {
     using G = Geo<KIND, RAD>;
@@ -197,7 +188,7 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
     constexpr int NB = T::NB;
     constexpr int SF = G::STAGE / 4;         // floats per stage
     constexpr int PHI = NB * kCols;          // float offset of phi in a stage
-    constexpr int C = 8;                     // columns per lane (A: 0..3, B: 4..7)
+    constexpr int C = 4;                     // columns per lane
 
     LseDevState *st = a.st;
     if (st->done || (st->status_bits & LSE_SBIT_ABORT)) return;
@@ -265,7 +256,7 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
     auto issue_one = [&]() {
         const uint32_t dst = ring0 + (uint32_t)(p_stage * G::STAGE);
         issue_row(lane == 0, bar0 + 8 * p_stage, tx_bytes, dst, dst + PHI * 4,
-                  &data_map, &phi_map, &phi_tail_map, p_xs, p_y, KIND == K_REGION_MB);
+                  &data_map, &phi_map, p_xs, p_y, KIND == K_REGION_MB);
         ++p_seq;
         ++p_y;
         p_stage = (p_stage + 1 == S) ? 0 : p_stage + 1;
@@ -306,26 +297,25 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
         fsw[b] = fsa[b] = 0.0f;
         dsw[b] = dsa[b] = 0.0;
     }
-    // output lanes: A's lanes from HL on, B's lanes below 32 - HL
-    const bool outA = lane >= HL, outB = lane < 32 - HL;
-    const int offA = 4 * lane, offB = 128 + 4 * lane;   // data offsets
+    // output lanes: all but the HL halo lanes at each side
+    const bool lane_out = lane >= HL && lane < 32 - HL;
+    const int off = 4 * lane;                            // data offset
 
     for (int k = 0; k < my_items && !failed; ++k) {
         const int base = k * NR;
         int xs, ys;
         origin(k, xs, ys);
-        const int xA = xs + offA, xB = xs + offB;
+        const int x0 = xs + off;
         // per-column masks (1 or 0): u inside the image, output columns
         float inf[C], okf[C];
         bool oneL[C], oneR[C];
         int nvalid = 0;
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-            const int x = (j < 4 ? xA : xB) + (j & 3);
-            const bool out = j < 4 ? outA : outB;
+            const int x = x0 + j;
             inf[j] = (x >= 0 && x < W) ? 1.0f : 0.0f;
-            okf[j] = (out && x < W) ? 1.0f : 0.0f;
-            nvalid += (out && x < W) ? 1 : 0;
+            okf[j] = (lane_out && x < W) ? 1.0f : 0.0f;
+            nvalid += (lane_out && x < W) ? 1 : 0;
             oneL[j] = x == 0;
             oneR[j] = x == W - 1;
         }
@@ -333,11 +323,14 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
         // and does an output float4 cross the right edge?
         const bool xborder = xs < 0 || xs + kCols > W;
         const bool ragged = xs + kCols - 4 * HL > W;
-        const bool fullA = outA && xA + 3 < W, fullB = outB && xB + 3 < W;
+        const bool full = lane_out && x0 + 3 < W;
         const bool ghost_l = xs <= 0;                    // x = -1 in this strip
         const bool ghost_r = xs <= W - 1 && W - 1 < xs + kCols;
         // last u-row whose output row lies inside the image
         const int r_out_max = H - 1 - ys + RAD;
+        // u-rows r with y = ys + r <= 0 or >= H - 1 need ghost rows or zeros:
+        // (unsigned)(y - 1) >= hm2 catches them (every row when H <= 2)
+        const unsigned hm2 = H >= 2 ? (unsigned)(H - 2) : 0u;
 
         // ghost columns of a staged binary row (lane 0; BIN only)
         auto patch = [&](int stage) {
@@ -372,14 +365,12 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
         float p0[C], pp[C], pm[C];
         {
             const int ra = ring + s_a * SF + PHI, rb = ring + s_b * SF + PHI;
-            const float4 a0 = ld4(&smem_f[ra + 4 + offA]), b0 = ld4(&smem_f[ra + 4 + offB]);
-            const float4 a1 = ld4(&smem_f[rb + 4 + offA]), b1 = ld4(&smem_f[rb + 4 + offB]);
+            const float4 a0 = ld4(&smem_f[ra + 4 + off]);
+            const float4 a1 = ld4(&smem_f[rb + 4 + off]);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 p0[j] = comp(a0, j);
-                p0[4 + j] = comp(b0, j);
                 pp[j] = comp(a1, j);
-                pp[4 + j] = comp(b1, j);
             }
             if (binarise_in) {
 #pragma unroll
@@ -412,28 +403,22 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
                 p0[j] = pp[j];
             }
             {
-                const float4 na = ld4(&smem_f[rowN + PHI + 4 + offA]);
-                const float4 nb = ld4(&smem_f[rowN + PHI + 4 + offB]);
+                const float4 na = ld4(&smem_f[rowN + PHI + 4 + off]);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    pp[j] = comp(na, j);
-                    pp[4 + j] = comp(nb, j);
-                }
+                for (int j = 0; j < 4; ++j) pp[j] = comp(na, j);
                 if (binarise_in) {
 #pragma unroll
                     for (int j = 0; j < C; ++j) pp[j] = bin(pp[j]);
                 }
             }
             // x-neighbours of the lane's columns in row r
-            float lA = __shfl_up_sync(0xffffffffu, p0[3], 1);           // A lane-1
-            float rB = __shfl_down_sync(0xffffffffu, p0[4], 1);         // B lane+1
-            const float rA = __shfl_sync(0xffffffffu, lane == 0 ? p0[4] : p0[0], (lane + 1) & 31);
-            const float lB = __shfl_sync(0xffffffffu, lane == 31 ? p0[3] : p0[7], (lane + 31) & 31);
+            float lft = __shfl_up_sync(0xffffffffu, p0[3], 1);
+            float rgt = __shfl_down_sync(0xffffffffu, p0[0], 1);
             {
                 float e = smem_f[rowR + PHI + (lane == 0 ? 3 : 4 + kCols)];
                 if (binarise_in) e = bin(e);
-                if (lane == 0) lA = e;
-                if (lane == 31) rB = e;
+                if (lane == 0) lft = e;
+                if (lane == 31) rgt = e;
             }
             // ghost rows and rows outside the image (uniform per row)
             const int y = ys + r;
@@ -444,7 +429,7 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
                 ppx[j] = pp[j];
             }
             bool yin = true;
-            if ((unsigned)(y - 1) >= (unsigned)(H - 2)) {   // y <= 0 or y >= H - 1
+            if ((unsigned)(y - 1) >= hm2) {                 // y <= 0 or y >= H - 1
                 yin = y >= 0 && y < H;
 #pragma unroll
                 for (int j = 0; j < C; ++j) {
@@ -461,40 +446,32 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
             // data term factor t = 0.5 dt R
             float t[C];
             {
-                const float4 da = ld4(&smem_f[rowR + offA]), db = ld4(&smem_f[rowR + offB]);
+                const float4 da = ld4(&smem_f[rowR + off]);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    if (KIND == K_EDGE) {
+                    if (KIND == K_EDGE)
                         t[j] = half_dt * comp(da, j);
-                        t[4 + j] = half_dt * comp(db, j);
-                    } else {
+                    else
                         t[j] = coef[0] * (comp(da, j) - mid[0]);
-                        t[4 + j] = coef[0] * (comp(db, j) - mid[0]);
-                    }
                 }
                 if (KIND == K_REGION_MB) {
 #pragma unroll
                     for (int b = 1; b < NB; ++b) {
                         if (b < B) {
-                            const float4 ea = ld4(&smem_f[rowR + b * kCols + offA]);
-                            const float4 eb = ld4(&smem_f[rowR + b * kCols + offB]);
+                            const float4 ea = ld4(&smem_f[rowR + b * kCols + off]);
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
+                            for (int j = 0; j < 4; ++j)
                                 t[j] = fmaf(coef[b], comp(ea, j) - mid[b], t[j]);
-                                t[4 + j] = fmaf(coef[b], comp(eb, j) - mid[b], t[4 + j]);
-                            }
                         }
                     }
                 }
             }
             // u = phi + t * 2|grad phi| (zero outside the image)
-            const float cA[6] = {lA, p0[0], p0[1], p0[2], p0[3], rA};
-            const float cB[6] = {lB, p0[4], p0[5], p0[6], p0[7], rB};
+            const float cc[6] = {lft, p0[0], p0[1], p0[2], p0[3], rgt};
             float u[C];
 #pragma unroll
             for (int j = 0; j < C; ++j) {
-                const float *cc = j < 4 ? cA : cB;
-                const int jj = j & 3;
+                const int jj = j;
                 float dx = cc[jj + 2] - cc[jj];
                 if (!BIN) {    // real LSF: one-sided differences by flags
                     if (W == 1) dx = 0.0f;
@@ -518,44 +495,27 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
 #pragma unroll
                 for (int j = 0; j < C; ++j) u[j] = 0.0f;
             }
-            // horizontal pass.  UA[c + 4 HL], UB[c + 4 HL] = u at column c
-            // relative to the lane's first A / B column.
-            float UA[4 + 8 * HL], UB[4 + 8 * HL];
+            // horizontal pass: U[c + 4 HL] = u at relative column c
+            float U[4 + 8 * HL];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                UA[4 * HL + j] = u[j];
-                UB[4 * HL + j] = u[4 + j];
-            }
+            for (int j = 0; j < 4; ++j) U[4 * HL + j] = u[j];
 #pragma unroll
             for (int o = 1; o <= HL; ++o) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    if (j - 4 * o >= -RAD) {
-                        // A: lane - o (A's first lanes are halo: no wrap)
-                        UA[4 * HL + j - 4 * o] = __shfl_up_sync(0xffffffffu, u[j], o);
-                        // B: lane - o, wrapping to A's last lanes
-                        UB[4 * HL + j - 4 * o] = __shfl_sync(
-                            0xffffffffu, lane >= 32 - o ? u[j] : u[4 + j], (lane + 32 - o) & 31);
-                    }
-                    if (j + 4 * o <= 3 + RAD) {
-                        // A: lane + o, wrapping to B's first lanes
-                        UA[4 * HL + j + 4 * o] = __shfl_sync(
-                            0xffffffffu, lane < o ? u[4 + j] : u[j], (lane + o) & 31);
-                        // B: lane + o (B's last lanes are halo: no wrap)
-                        UB[4 * HL + j + 4 * o] = __shfl_down_sync(0xffffffffu, u[4 + j], o);
-                    }
+                    if (j - 4 * o >= -RAD)
+                        U[4 * HL + j - 4 * o] = __shfl_up_sync(0xffffffffu, u[j], o);
+                    if (j + 4 * o <= 3 + RAD)
+                        U[4 * HL + j + 4 * o] = __shfl_down_sync(0xffffffffu, u[j], o);
                 }
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float ha = tp[0] * UA[4 * HL + j], hb = tp[0] * UB[4 * HL + j];
+                float h = tp[0] * U[4 * HL + j];
 #pragma unroll
-                for (int q = 1; q <= RAD; ++q) {
-                    ha = fmaf(tp[q], UA[4 * HL + j - q] + UA[4 * HL + j + q], ha);
-                    hb = fmaf(tp[q], UB[4 * HL + j - q] + UB[4 * HL + j + q], hb);
-                }
-                ring_h[kk][j] = ha;
-                ring_h[kk][4 + j] = hb;
+                for (int q = 1; q <= RAD; ++q)
+                    h = fmaf(tp[q], U[4 * HL + j - q] + U[4 * HL + j + q], h);
+                ring_h[kk][j] = h;
             }
             if (r < 2 * RAD + 1 || r > r_out_max) return;
             // vertical pass of row r - RAD
@@ -581,23 +541,17 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
             float sv[C];
 #pragma unroll
             for (int j = 0; j < C; ++j) sv[j] = store_bin ? w[j] : v[j];
-            if (fullA) *reinterpret_cast<float4 *>(dst + offA) = make_float4(sv[0], sv[1], sv[2], sv[3]);
-            if (fullB) *reinterpret_cast<float4 *>(dst + offB) = make_float4(sv[4], sv[5], sv[6], sv[7]);
+            if (full) *reinterpret_cast<float4 *>(dst + off) = make_float4(sv[0], sv[1], sv[2], sv[3]);
             if (ragged) {
 #pragma unroll
-                for (int j = 0; j < C; ++j) {
-                    const bool full = j < 4 ? fullA : fullB;
-                    if (!full && okf[j] != 0.0f) dst[(j < 4 ? offA : offB) + (j & 3)] = sv[j];
-                }
+                for (int j = 0; j < C; ++j)
+                    if (!full && okf[j] != 0.0f) dst[off + j] = sv[j];
             }
             if (count_flips) {
-                const float4 oa = ld4(&smem_f[rowO + PHI + 4 + offA]);
-                const float4 ob = ld4(&smem_f[rowO + PHI + 4 + offB]);
+                const float4 oa = ld4(&smem_f[rowO + PHI + 4 + off]);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < 4; ++j)
                     nflip += (okf[j] != 0.0f) && ((w[j] > 0.0f) != (comp(oa, j) >= 0.0f));
-                    nflip += (okf[4 + j] != 0.0f) && ((w[4 + j] > 0.0f) != (comp(ob, j) >= 0.0f));
-                }
             }
 #pragma unroll
             for (int j = 0; j < C; ++j) fsw_cnt = fmaf(w[j], okf[j], fsw_cnt);
@@ -605,11 +559,10 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
                     if (b < B) {
-                        const float4 ea = ld4(&smem_f[rowO + b * kCols + offA]);
-                        const float4 eb = ld4(&smem_f[rowO + b * kCols + offB]);
+                        const float4 ea = ld4(&smem_f[rowO + b * kCols + off]);
 #pragma unroll
                         for (int j = 0; j < C; ++j) {
-                            const float d = (j < 4 ? comp(ea, j) : comp(eb, j - 4)) * okf[j];
+                            const float d = comp(ea, j) * okf[j];
                             fsw[b] = fmaf(d, w[j], fsw[b]);
                             fsa[b] += d;
                         }
@@ -633,7 +586,7 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
             for (int kk = 0; kk < P; ++kk) row(r0 + kk, kk);
             fold();
         }
-        // exact integer count: fsw_cnt holds sum w (|sum| <= 8 th) exactly;
+        // exact integer count: fsw_cnt holds sum w (|sum| <= 4 th) exactly;
         // rows at or beyond H produced no output
         {
             const int y0 = ys + RAD + 1;
@@ -684,8 +637,7 @@ int smem_bytes(int wpc)
 
 template <int KIND, int RAD>
 cudaError_t launch_one(const StepArgs &a, const CUtensorMap &pm,
-                       const CUtensorMap &tm, const CUtensorMap &dm, int nblocks,
-                       int wpc, cudaStream_t s)
+                       const CUtensorMap &dm, int nblocks, int wpc, cudaStream_t s)
 {
     const int smem = smem_bytes<KIND, RAD>(wpc);
     auto kern = a.binary_in ? step_tma_kernel<KIND, RAD, true>
@@ -693,23 +645,22 @@ cudaError_t launch_one(const StepArgs &a, const CUtensorMap &pm,
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem);
     if (e != cudaSuccess) return e;
-    kern<<<nblocks, 32 * wpc, smem, s>>>(a, pm, tm, dm);
+    kern<<<nblocks, 32 * wpc, smem, s>>>(a, pm, dm);
     return cudaGetLastError();
 }
 
 template <int KIND>
 cudaError_t launch_kind(const StepArgs &a, const CUtensorMap &pm,
-                        const CUtensorMap &tm, const CUtensorMap &dm, int nblocks,
-                        int wpc, cudaStream_t s)
+                        const CUtensorMap &dm, int nblocks, int wpc, cudaStream_t s)
 {
     switch (a.rad) {
-    case 1: return launch_one<KIND, 1>(a, pm, tm, dm, nblocks, wpc, s);
-    case 2: return launch_one<KIND, 2>(a, pm, tm, dm, nblocks, wpc, s);
-    case 3: return launch_one<KIND, 3>(a, pm, tm, dm, nblocks, wpc, s);
-    case 4: return launch_one<KIND, 4>(a, pm, tm, dm, nblocks, wpc, s);
-    case 5: return launch_one<KIND, 5>(a, pm, tm, dm, nblocks, wpc, s);
-    case 6: return launch_one<KIND, 6>(a, pm, tm, dm, nblocks, wpc, s);
-    case 7: return launch_one<KIND, 7>(a, pm, tm, dm, nblocks, wpc, s);
+    case 1: return launch_one<KIND, 1>(a, pm, dm, nblocks, wpc, s);
+    case 2: return launch_one<KIND, 2>(a, pm, dm, nblocks, wpc, s);
+    case 3: return launch_one<KIND, 3>(a, pm, dm, nblocks, wpc, s);
+    case 4: return launch_one<KIND, 4>(a, pm, dm, nblocks, wpc, s);
+    case 5: return launch_one<KIND, 5>(a, pm, dm, nblocks, wpc, s);
+    case 6: return launch_one<KIND, 6>(a, pm, dm, nblocks, wpc, s);
+    case 7: return launch_one<KIND, 7>(a, pm, dm, nblocks, wpc, s);
     default: return cudaErrorNotSupported;
     }
 }

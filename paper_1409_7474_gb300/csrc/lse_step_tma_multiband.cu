@@ -5,10 +5,10 @@
 namespace lse_detail {
 
 cudaError_t launch_step_tma_multiband(const StepArgs &a, const CUtensorMap &pm,
-                                   const CUtensorMap &tm, const CUtensorMap &dm,
-                                   int nblocks, int wpc, cudaStream_t s)
+                                   const CUtensorMap &dm, int nblocks, int wpc,
+                                   cudaStream_t s)
 {
-    return lse_tma::launch_kind<lse_tma::K_REGION_MB>(a, pm, tm, dm, nblocks, wpc, s);
+    return lse_tma::launch_kind<lse_tma::K_REGION_MB>(a, pm, dm, nblocks, wpc, s);
 }
 
 int step_tma_warp_bytes_multiband(int rad)
