@@ -3,48 +3,47 @@
 // One pass over the image per iteration computes, for every pixel,
 //   u = phi + dt R |grad phi|                        (Eq. 18)
 //   v = G_sigma * u                                  (Table I step 4)
-// with R = D / max|D| (Eq. 17) or R = g (Eq. 14), stores v (or sign(v) when
-// the step re-initialises, Table I step 3), and accumulates the sums that
-// the next iteration's region statistics need (Eq. 15): the count and the
-// band sums over v >= 0, plus the number of sign changes when asked.  The
-// last CTA finalises c+/c- and the next step's coefficients.
+// with R = D / max|D| (Eq. 17) or R = g (Eq. 14), stores v, and accumulates
+// the sums that the next iteration's region statistics need (Eq. 15): count
+// and intensity sums over v >= 0 and v < 0, plus the number of sign changes.
+// The last CTA finalises c+/c- and the next step's coefficients.
 //
 // Work decomposition.  Each warp owns a vertical strip of 128 columns and a
 // block of `th` output rows ("item").  Lane l holds columns xs + 4l .. +3.
-// The outermost HL lanes on each side only supply the Gaussian's horizontal
-// halo, so a strip yields 4 (32 - 2 HL) output columns.  (Eight columns per
-// lane halves the per-row bookkeeping but needs twice the registers, and
-// the lost occupancy costs more than it saves.)  The warp streams down its
-// strip one row at a time:
-//   * TMA (cp.async.bulk.tensor, zero fill outside the image) loads each row
-//     of phi (136 floats: the strip and 4 columns each side) and of the data
-//     term (128 floats per band) into a per-warp ring of shared-memory
-//     stages with one mbarrier each; the warp issues its own loads (one
-//     predicated lane) up to PF rows ahead of use;
+// The outer `HL` lanes on each side only supply the horizontal halo of the
+// Gaussian, so a strip yields 4 (32 - 2 HL) output columns.  The warp streams
+// down the strip one row at a time:
+//   * TMA (cp.async.bulk.tensor, zero fill outside the image) loads each
+//     row of phi (136 floats: the strip plus 4 columns each side) and of the
+//     data term (128 floats per band) into a per-warp ring of shared-memory
+//     stages, each with its own mbarrier; lane 0 issues loads up to
+//     `S - RAD - 2` rows ahead of use;
 //   * phi rows y-1, y, y+1 sit in registers; u of row y is computed in
-//     registers; the horizontal Gaussian pass takes neighbouring lanes' u by
-//     warp shuffles;
+//     registers, its horizontal Gaussian pass takes the neighbouring lanes'
+//     u by warp shuffles;
 //   * the vertical pass keeps the last 2 RAD + 1 horizontally smoothed rows
-//     in a register ring; the row loop is unrolled by the ring period, so
-//     ring indices are compile-time constants;
-//   * the output row (RAD rows behind) is written with 16-byte stores; its
-//     statistics read the data term still held in the ring.
-// Inputs are read from HBM about once (the halo of neighbouring strips and
-// row blocks hits L2); nothing but the halo is recomputed.
+//     in a register ring (the row loop is unrolled by the ring period so
+//     every ring index is a compile-time constant);
+//   * the output row (RAD rows behind) is written with 16-byte stores and
+//     its statistics read phi and the data term from the ring.
+// Nothing but the inputs' halo is recomputed, and HBM sees each input byte
+// about once (halo rows/columns of neighbouring strips hit L2).
 //
 // Image borders cost no per-pixel logic: at x = 0 the listing's one-sided
 // difference phi(1) - phi(0) equals the central difference against a ghost
-// value phi(-1) = 2 phi(0) - phi(1) (likewise at the last column and the
-// first/last row; a dimension of size 1 gets ghosts equal to phi(0), whose
-// difference is 0).  Ghost columns are written into the staged row, ghost
-// rows into the register window; u is zeroed outside the image.  Every item
-// runs the same code, so the work is balanced across warps.
+// value phi(-1) = 2 phi(0) - phi(1) (and likewise at the last column and
+// the first/last row; a dimension of size 1 gets ghosts equal to phi(0), so
+// its difference is 0).  Ghost columns are written into the staged row in
+// shared memory, ghost rows into the register window; u is zeroed outside
+// the image by per-column masks and per-row flags.  Every item then runs
+// the same code, so the work is balanced across warps.
 //
-// BIN instantiations read a binary LSF stored by the previous step: then
-// |grad phi|^2 (in units of 4) takes only the values 0, 4, 8, 16, 20, 32 and
-// its square root comes from a table filled with sqrtf, exactly.  The other
-// instantiation reads a real LSF (the first step, or a caller-chosen reinit
-// period) and uses sqrtf with explicit one-sided differences.
+// BIN instantiations read a binary LSF stored by the previous step (which
+// wrote sign(v) because it re-initialised): |grad phi|^2 then takes only the
+// values 0, 4, 8 (16, 20, 32 at borders) and its square root comes from a
+// 17-entry table filled with sqrtf, exactly.  The other instantiation reads
+// a real LSF (the first step, or a caller-chosen reinit period) and uses
+// sqrtf.
 //
 // The mbarrier waits are bounded: a wait that runs out sets the TIMEOUT
 // status bit, drains the loads still in flight (again bounded) and skips the
@@ -56,25 +55,25 @@
 
 namespace lse_tma {
 
-constexpr int kCols = 128;          // strip width (columns held by a warp)
-constexpr int kPhiBox = kCols + 8;  // phi floats per staged row
+constexpr int kPhiBox = 136;       // phi floats per staged row
+constexpr int kDataBox = 128;      // data floats per staged row and band
 constexpr int kPhiBytes = kPhiBox * 4;
-constexpr int kPhiSlot = 640;       // phi bytes per stage, 128-byte aligned
-constexpr int kDataSlot = kCols * 4;
+constexpr int kPhiSlot = 640;      // phi bytes per stage, 128-byte aligned
+constexpr int kDataSlot = kDataBox * 4;
 
 enum Kind { K_REGION1 = 0, K_REGION_MB = 1, K_EDGE = 2 };
 
 template <int KIND>
 struct KindTraits {
     static constexpr int NB = KIND == K_REGION_MB ? 4 : 1;   // bands staged
-    static constexpr int PF = KIND == K_REGION_MB ? 3 : 5;   // rows of prefetch
+    static constexpr int PF = KIND == K_REGION_MB ? 4 : 5;   // rows of prefetch
     static constexpr bool REGION = KIND != K_EDGE;
 };
 
 template <int KIND, int RAD>
 struct Geo {
     static constexpr int HL = (RAD + 3) / 4;
-    static constexpr int USEFUL = kCols - 8 * HL;   // 4 (32 - 2 HL)
+    static constexpr int USEFUL = 4 * (32 - 2 * HL);
     static constexpr int P = 2 * RAD + 1;
     static constexpr int S = RAD + 2 + KindTraits<KIND>::PF;
     static constexpr int STAGE = KindTraits<KIND>::NB * kDataSlot + kPhiSlot;
@@ -98,6 +97,17 @@ __device__ __forceinline__ void fence_mbar_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(bar), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
@@ -111,44 +121,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Issues one staged row from the lane with `on` set: the proxy fence orders
-// the warp's earlier reads of the stage before the asynchronous copies
-// overwrite it.
-__device__ __forceinline__ void issue_row(bool on, uint32_t bar, uint32_t tx,
-                                          uint32_t dst_data, uint32_t dst_phi,
-                                          const CUtensorMap *dmap,
-                                          const CUtensorMap *pmap, int xs, int y,
-                                          bool three_d)
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map,
+                                            int x, int y, uint32_t bar)
 {
-    const uint64_t dm = reinterpret_cast<uint64_t>(dmap);
-    const uint64_t pm = reinterpret_cast<uint64_t>(pmap);
-    if (three_d) {
-        asm volatile(
-            "{\n\t.reg .pred q;\n\t"
-            "setp.ne.b32 q, %0, 0;\n\t"
-            "@q fence.proxy.async.shared::cta;\n\t"
-            "@q mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n\t"
-            "@q cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%3], [%4, {%6, %7}], [%1];\n\t"
-            "@q cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%8], [%5, {%9, %7, %10}], [%1];\n\t}"
-            ::"r"((int)on), "r"(bar), "r"(tx), "r"(dst_phi), "l"(pm), "l"(dm), "r"(xs - 4),
-              "r"(y), "r"(dst_data), "r"(xs), "r"(0)
-            : "memory");
-    } else {
-        asm volatile(
-            "{\n\t.reg .pred q;\n\t"
-            "setp.ne.b32 q, %0, 0;\n\t"
-            "@q fence.proxy.async.shared::cta;\n\t"
-            "@q mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n\t"
-            "@q cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%3], [%4, {%6, %7}], [%1];\n\t"
-            "@q cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%8], [%5, {%9, %7}], [%1];\n\t}"
-            ::"r"((int)on), "r"(bar), "r"(tx), "r"(dst_phi), "l"(pm), "l"(dm), "r"(xs - 4),
-              "r"(y), "r"(dst_data), "r"(xs)
-            : "memory");
-    }
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map,
+                                            int x, int y, int z, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z),
+          "r"(bar)
+        : "memory");
 }
 
 // Bounded wait on one stage; warp-uniform result.
@@ -170,6 +161,11 @@ __device__ __forceinline__ float4 ld4(const float *p)
     return *reinterpret_cast<const float4 *>(p);
 }
 
+__device__ __forceinline__ float4 bin4(float4 v)
+{
+    return make_float4(bin(v.x), bin(v.y), bin(v.z), bin(v.w));
+}
+
 __device__ __forceinline__ float comp(const float4 &v, int j)
 {
     return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
@@ -187,8 +183,7 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
     constexpr int HL = G::HL, P = G::P, S = G::S;
     constexpr int NB = T::NB;
     constexpr int SF = G::STAGE / 4;         // floats per stage
-    constexpr int PHI = NB * kCols;          // float offset of phi in a stage
-    constexpr int C = 4;                     // columns per lane
+    constexpr int PHI = NB * kDataBox;       // float offset of phi in a stage
 
     LseDevState *st = a.st;
     if (st->done || (st->status_bits & LSE_SBIT_ABORT)) return;
@@ -254,9 +249,17 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
     };
     if (my_items > 0) origin(0, p_xs, p_y);
     auto issue_one = [&]() {
-        const uint32_t dst = ring0 + (uint32_t)(p_stage * G::STAGE);
-        issue_row(lane == 0, bar0 + 8 * p_stage, tx_bytes, dst, dst + PHI * 4,
-                  &data_map, &phi_map, p_xs, p_y, KIND == K_REGION_MB);
+        if (lane == 0) {
+            const uint32_t bar = bar0 + 8 * p_stage;
+            const uint32_t dst = ring0 + (uint32_t)(p_stage * G::STAGE);
+            fence_proxy_async();
+            mbar_expect_tx(bar, tx_bytes);
+            tma_load_2d(dst + PHI * 4, &phi_map, p_xs - 4, p_y, bar);
+            if (KIND == K_REGION_MB)
+                tma_load_3d(dst, &data_map, p_xs, p_y, 0, bar);
+            else
+                tma_load_2d(dst, &data_map, p_xs, p_y, bar);
+        }
         ++p_seq;
         ++p_y;
         p_stage = (p_stage + 1 == S) ? 0 : p_stage + 1;
@@ -297,21 +300,19 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
         fsw[b] = fsa[b] = 0.0f;
         dsw[b] = dsa[b] = 0.0;
     }
-    // output lanes: all but the HL halo lanes at each side
     const bool lane_out = lane >= HL && lane < 32 - HL;
-    const int off = 4 * lane;                            // data offset
 
     for (int k = 0; k < my_items && !failed; ++k) {
         const int base = k * NR;
         int xs, ys;
         origin(k, xs, ys);
-        const int x0 = xs + off;
+        const int x0 = xs + 4 * lane;
         // per-column masks (1 or 0): u inside the image, output columns
-        float inf[C], okf[C];
-        bool oneL[C], oneR[C];
+        float inf[4], okf[4];
+        bool oneL[4], oneR[4];
         int nvalid = 0;
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
+        for (int j = 0; j < 4; ++j) {
             const int x = x0 + j;
             inf[j] = (x >= 0 && x < W) ? 1.0f : 0.0f;
             okf[j] = (lane_out && x < W) ? 1.0f : 0.0f;
@@ -320,17 +321,12 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
             oneR[j] = x == W - 1;
         }
         // uniform per item: does the strip touch the image's left/right edge,
-        // and does an output float4 cross the right edge?
-        const bool xborder = xs < 0 || xs + kCols > W;
-        const bool ragged = xs + kCols - 4 * HL > W;
+        // and is every output lane's float4 inside the image?
+        const bool xborder = xs < 0 || xs + 128 > W;
+        const bool ragged = xs + 4 * (32 - HL) > W;
         const bool full = lane_out && x0 + 3 < W;
         const bool ghost_l = xs <= 0;                    // x = -1 in this strip
-        const bool ghost_r = xs <= W - 1 && W - 1 < xs + kCols;
-        // last u-row whose output row lies inside the image
-        const int r_out_max = H - 1 - ys + RAD;
-        // u-rows r with y = ys + r <= 0 or >= H - 1 need ghost rows or zeros:
-        // (unsigned)(y - 1) >= hm2 catches them (every row when H <= 2)
-        const unsigned hm2 = H >= 2 ? (unsigned)(H - 2) : 0u;
+        const bool ghost_r = xs <= W - 1 && W - 1 < xs + 128;
 
         // ghost columns of a staged binary row (lane 0; BIN only)
         auto patch = [&](int stage) {
@@ -362,34 +358,20 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
         const int s_b = wait_one();
         patch(s_a);
         patch(s_b);
-        float p0[C], pp[C], pm[C];
-        {
-            const int ra = ring + s_a * SF + PHI, rb = ring + s_b * SF + PHI;
-            const float4 a0 = ld4(&smem_f[ra + 4 + off]);
-            const float4 a1 = ld4(&smem_f[rb + 4 + off]);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                p0[j] = comp(a0, j);
-                pp[j] = comp(a1, j);
-            }
-            if (binarise_in) {
-#pragma unroll
-                for (int j = 0; j < C; ++j) {
-                    p0[j] = bin(p0[j]);
-                    pp[j] = bin(pp[j]);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < C; ++j) pm[j] = p0[j];
+        float4 p0 = ld4(&smem_f[ring + s_a * SF + PHI + 4 + 4 * lane]);
+        float4 pp = ld4(&smem_f[ring + s_b * SF + PHI + 4 + 4 * lane]);
+        if (binarise_in) {
+            p0 = bin4(p0);
+            pp = bin4(pp);
         }
-        float ring_h[P][C];
+        float4 pm = p0;
+        float ring_h[P][4];
 
         // one u-row: u of row r, its horizontal pass into ring slot kk, and
-        // (when r >= 2 RAD + 1) the vertical pass, store and statistics of
-        // row r - RAD
-        auto row = [&](const int r, const int kk) {
+        // (OUT) the vertical pass, store and statistics of row r - RAD
+        auto row = [&](const int r, const int kk, const bool OUT) {
             __syncwarp();
-            if (r > RAD && p_seq < total_seq) issue_one();
+            if (r > RAD && p_seq < total_seq && p_seq <= base + r - RAD + S - 1) issue_one();
             const int sn = wait_one();          // stage of row r + 1
             patch(sn);
             int sr = sn - 1;
@@ -397,103 +379,84 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
             int so = sn - 1 - RAD;
             if (so < 0) so += S;
             const int rowN = ring + sn * SF, rowR = ring + sr * SF, rowO = ring + so * SF;
-#pragma unroll
-            for (int j = 0; j < C; ++j) {
-                pm[j] = p0[j];
-                p0[j] = pp[j];
-            }
+            pm = p0;
+            p0 = pp;
+            pp = ld4(&smem_f[rowN + PHI + 4 + 4 * lane]);
+            if (binarise_in) pp = bin4(pp);
+            // x-neighbours of this lane's columns in row r
+            float lft = __shfl_up_sync(0xffffffffu, p0.w, 1);
+            float rgt = __shfl_down_sync(0xffffffffu, p0.x, 1);
             {
-                const float4 na = ld4(&smem_f[rowN + PHI + 4 + off]);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) pp[j] = comp(na, j);
-                if (binarise_in) {
-#pragma unroll
-                    for (int j = 0; j < C; ++j) pp[j] = bin(pp[j]);
-                }
-            }
-            // x-neighbours of the lane's columns in row r
-            float lft = __shfl_up_sync(0xffffffffu, p0[3], 1);
-            float rgt = __shfl_down_sync(0xffffffffu, p0[0], 1);
-            {
-                float e = smem_f[rowR + PHI + (lane == 0 ? 3 : 4 + kCols)];
+                float e = smem_f[rowR + PHI + (lane == 0 ? 3 : 132)];
                 if (binarise_in) e = bin(e);
                 if (lane == 0) lft = e;
                 if (lane == 31) rgt = e;
             }
-            // ghost rows and rows outside the image (uniform per row)
+            // ghost rows (uniform per row)
             const int y = ys + r;
-            float pmx[C], ppx[C];
-#pragma unroll
-            for (int j = 0; j < C; ++j) {
-                pmx[j] = pm[j];
-                ppx[j] = pp[j];
-            }
-            bool yin = true;
-            if ((unsigned)(y - 1) >= hm2) {                 // y <= 0 or y >= H - 1
-                yin = y >= 0 && y < H;
-#pragma unroll
-                for (int j = 0; j < C; ++j) {
-                    if (H == 1) {
-                        pmx[j] = p0[j];
-                        ppx[j] = p0[j];
-                    } else if (y == 0) {
-                        pmx[j] = 2.f * p0[j] - pp[j];
-                    } else if (y == H - 1) {
-                        ppx[j] = 2.f * p0[j] - pm[j];
-                    }
+            float4 pmx = pm, ppx = pp;
+            if (y <= 0 || y >= H - 1) {
+                if (H == 1) {
+                    pmx = p0;
+                    ppx = p0;
+                } else if (y == 0) {
+                    pmx = make_float4(2.f * p0.x - pp.x, 2.f * p0.y - pp.y,
+                                      2.f * p0.z - pp.z, 2.f * p0.w - pp.w);
+                } else if (y == H - 1) {
+                    ppx = make_float4(2.f * p0.x - pm.x, 2.f * p0.y - pm.y,
+                                      2.f * p0.z - pm.z, 2.f * p0.w - pm.w);
                 }
             }
+            const bool yin = y >= 0 && y < H;
             // data term factor t = 0.5 dt R
-            float t[C];
-            {
-                const float4 da = ld4(&smem_f[rowR + off]);
+            float t[4];
+            if (KIND == K_EDGE) {
+                const float4 g4 = ld4(&smem_f[rowR + 4 * lane]);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (KIND == K_EDGE)
-                        t[j] = half_dt * comp(da, j);
-                    else
-                        t[j] = coef[0] * (comp(da, j) - mid[0]);
-                }
+                for (int j = 0; j < 4; ++j) t[j] = half_dt * comp(g4, j);
+            } else {
+                const float4 d4 = ld4(&smem_f[rowR + 4 * lane]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) t[j] = coef[0] * (comp(d4, j) - mid[0]);
                 if (KIND == K_REGION_MB) {
 #pragma unroll
                     for (int b = 1; b < NB; ++b) {
                         if (b < B) {
-                            const float4 ea = ld4(&smem_f[rowR + b * kCols + off]);
+                            const float4 e4 = ld4(&smem_f[rowR + b * kDataBox + 4 * lane]);
 #pragma unroll
                             for (int j = 0; j < 4; ++j)
-                                t[j] = fmaf(coef[b], comp(ea, j) - mid[b], t[j]);
+                                t[j] = fmaf(coef[b], comp(e4, j) - mid[b], t[j]);
                         }
                     }
                 }
             }
             // u = phi + t * 2|grad phi| (zero outside the image)
-            const float cc[6] = {lft, p0[0], p0[1], p0[2], p0[3], rgt};
-            float u[C];
+            const float c[6] = {lft, p0.x, p0.y, p0.z, p0.w, rgt};
+            float u[4];
 #pragma unroll
-            for (int j = 0; j < C; ++j) {
-                const int jj = j;
-                float dx = cc[jj + 2] - cc[jj];
+            for (int j = 0; j < 4; ++j) {
+                float dx = c[j + 2] - c[j];
                 if (!BIN) {    // real LSF: one-sided differences by flags
                     if (W == 1) dx = 0.0f;
-                    else if (oneL[j]) dx = 2.0f * (cc[jj + 2] - cc[jj + 1]);
-                    else if (oneR[j]) dx = 2.0f * (cc[jj + 1] - cc[jj]);
+                    else if (oneL[j]) dx = 2.0f * (c[j + 2] - c[j + 1]);
+                    else if (oneR[j]) dx = 2.0f * (c[j + 1] - c[j]);
                 }
-                const float dy = ppx[j] - pmx[j];
+                const float dy = comp(ppx, j) - comp(pmx, j);
                 const float q = fmaf(dx, dx, dy * dy);
                 float s2;
                 if (BIN)
                     s2 = smem_f[lut + ((__float_as_uint(q) >> 21) & 31u)];
                 else
                     s2 = sqrtf(q);
-                u[j] = fmaf(t[j], s2, cc[jj + 1]);
+                u[j] = fmaf(t[j], s2, c[j + 1]);
             }
             if (xborder) {
 #pragma unroll
-                for (int j = 0; j < C; ++j) u[j] *= inf[j];
+                for (int j = 0; j < 4; ++j) u[j] *= inf[j];
             }
             if (!yin) {
 #pragma unroll
-                for (int j = 0; j < C; ++j) u[j] = 0.0f;
+                for (int j = 0; j < 4; ++j) u[j] = 0.0f;
             }
             // horizontal pass: U[c + 4 HL] = u at relative column c
             float U[4 + 8 * HL];
@@ -517,11 +480,11 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
                     h = fmaf(tp[q], U[4 * HL + j - q] + U[4 * HL + j + q], h);
                 ring_h[kk][j] = h;
             }
-            if (r < 2 * RAD + 1 || r > r_out_max) return;
+            if (!OUT) return;
             // vertical pass of row r - RAD
-            float v[C];
+            float v[4];
 #pragma unroll
-            for (int j = 0; j < C; ++j) {
+            for (int j = 0; j < 4; ++j) {
                 float acc = tp[0] * ring_h[(kk - RAD + P) % P][j];
 #pragma unroll
                 for (int q = 1; q <= RAD; ++q)
@@ -532,39 +495,65 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
                 v[j] = acc;
             }
             const int yo = ys + r - RAD;
-            float *dst = a.phi_out + (size_t)yo * a.pitch + xs;
-            // w = sign(v): the count is (sum w + valid) / 2 and the band sums
-            // over v >= 0 are (sum d + sum d w) / 2 (d zero off the image)
-            float w[C];
+            if (yo >= H) return;
+            float *dst = a.phi_out + (size_t)yo * a.pitch + x0;
+            if (store_bin) {
+                // w = sign(v): the count is (sum w + valid) / 2 and the band sums
+                // over v >= 0 are (sum d + sum d w) / 2 (d zero off the image)
+                float w[4];
 #pragma unroll
-            for (int j = 0; j < C; ++j) w[j] = v[j] >= 0.0f ? 1.0f : -1.0f;
-            float sv[C];
+                for (int j = 0; j < 4; ++j) w[j] = v[j] >= 0.0f ? 1.0f : -1.0f;
+                if (full) *reinterpret_cast<float4 *>(dst) = make_float4(w[0], w[1], w[2], w[3]);
+                if (ragged && !full) {
 #pragma unroll
-            for (int j = 0; j < C; ++j) sv[j] = store_bin ? w[j] : v[j];
-            if (full) *reinterpret_cast<float4 *>(dst + off) = make_float4(sv[0], sv[1], sv[2], sv[3]);
-            if (ragged) {
+                    for (int j = 0; j < 4; ++j)
+                        if (okf[j] != 0.0f) dst[j] = w[j];
+                }
 #pragma unroll
-                for (int j = 0; j < C; ++j)
-                    if (!full && okf[j] != 0.0f) dst[off + j] = sv[j];
-            }
-            if (count_flips) {
-                const float4 oa = ld4(&smem_f[rowO + PHI + 4 + off]);
+                for (int j = 0; j < 4; ++j) fsw_cnt = fmaf(w[j], okf[j], fsw_cnt);
+                if (T::REGION) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    nflip += (okf[j] != 0.0f) && ((w[j] > 0.0f) != (comp(oa, j) >= 0.0f));
-            }
+                    for (int b = 0; b < NB; ++b) {
+                        if (b < B) {
+                            const float4 e4 = ld4(&smem_f[rowO + b * kDataBox + 4 * lane]);
 #pragma unroll
-            for (int j = 0; j < C; ++j) fsw_cnt = fmaf(w[j], okf[j], fsw_cnt);
-            if (T::REGION) {
+                            for (int j = 0; j < 4; ++j) {
+                                const float d = comp(e4, j) * okf[j];
+                                fsw[b] = fmaf(d, w[j], fsw[b]);
+                                fsa[b] += d;
+                            }
+                        }
+                    }
+                }
+            } else {
+                if (full) *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+                if (ragged && !full) {
 #pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    if (b < B) {
-                        const float4 ea = ld4(&smem_f[rowO + b * kCols + off]);
+                    for (int j = 0; j < 4; ++j)
+                        if (okf[j] != 0.0f) dst[j] = v[j];
+                }
+                float w[4];
 #pragma unroll
-                        for (int j = 0; j < C; ++j) {
-                            const float d = comp(ea, j) * okf[j];
-                            fsw[b] = fmaf(d, w[j], fsw[b]);
-                            fsa[b] += d;
+                for (int j = 0; j < 4; ++j) w[j] = v[j] >= 0.0f ? 1.0f : -1.0f;
+                if (count_flips) {
+                    const float4 o4 = ld4(&smem_f[rowO + PHI + 4 + 4 * lane]);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        nflip += (okf[j] != 0.0f) && ((w[j] > 0.0f) != (comp(o4, j) >= 0.0f));
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) fsw_cnt = fmaf(w[j], okf[j], fsw_cnt);
+                if (T::REGION) {
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        if (b < B) {
+                            const float4 e4 = ld4(&smem_f[rowO + b * kDataBox + 4 * lane]);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const float d = comp(e4, j) * okf[j];
+                                fsw[b] = fmaf(d, w[j], fsw[b]);
+                                fsa[b] += d;
+                            }
                         }
                     }
                 }
@@ -583,7 +572,7 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
         for (int per = 0; per < n_per && !failed; ++per) {
             const int r0 = 1 + per * P;
 #pragma unroll
-            for (int kk = 0; kk < P; ++kk) row(r0 + kk, kk);
+            for (int kk = 0; kk < P; ++kk) row(r0 + kk, kk, r0 + kk >= 2 * RAD + 1);
             fold();
         }
         // exact integer count: fsw_cnt holds sum w (|sum| <= 4 th) exactly;
@@ -637,7 +626,8 @@ int smem_bytes(int wpc)
 
 template <int KIND, int RAD>
 cudaError_t launch_one(const StepArgs &a, const CUtensorMap &pm,
-                       const CUtensorMap &dm, int nblocks, int wpc, cudaStream_t s)
+                       const CUtensorMap &dm, int nblocks, int wpc,
+                       cudaStream_t s)
 {
     const int smem = smem_bytes<KIND, RAD>(wpc);
     auto kern = a.binary_in ? step_tma_kernel<KIND, RAD, true>
@@ -651,7 +641,8 @@ cudaError_t launch_one(const StepArgs &a, const CUtensorMap &pm,
 
 template <int KIND>
 cudaError_t launch_kind(const StepArgs &a, const CUtensorMap &pm,
-                        const CUtensorMap &dm, int nblocks, int wpc, cudaStream_t s)
+                        const CUtensorMap &dm, int nblocks, int wpc,
+                        cudaStream_t s)
 {
     switch (a.rad) {
     case 1: return launch_one<KIND, 1>(a, pm, dm, nblocks, wpc, s);
