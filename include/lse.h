@@ -199,6 +199,36 @@ lse_status lse_get_stats(lse_ctx *ctx, lse_stats *stats);
 /* Library version string, e.g. "0.1.0". */
 const char *lse_version(void);
 
+/* lse_evolve without any allocation, for callers that cannot allocate GPU
+ * memory: code that runs inside a host framework or memory pool that owns
+ * all device memory, or a serving loop that must not allocate (cudaMalloc
+ * can synchronise the device and its latency is unbounded).  The paper has
+ * no counterpart; this is an interface of this library.
+ *
+ * Same computation and results as lse_evolve with the same arguments, with
+ * these limits:
+ *   - image (region term) or g (edge term), phi0, phi_out and mask_out (may
+ *     be NULL) are device memory of the current device; image and g are
+ *     float32 (dtype LSE_F32 is implied) and 16-byte aligned;
+ *   - W is a multiple of 4 and H * W <= LSE_STATIC_MAX_PIXELS (262144,
+ *     e.g. 512 x 512); 1 <= B <= 4;
+ *   - stats->elapsed_ms is -1 (timing would need CUDA events).
+ * Anything else returns LSE_ERR_INVALID_ARG without touching the GPU, and
+ * lse_last_error(NULL) says why.  The call allocates nothing: its scratch
+ * (two LSF planes, per-block partial sums, the device statistics record,
+ * about 2.7 MB) is a fixed array in the library's device memory that every
+ * GPU which loads the library holds until the process exits.  The first
+ * call on each device looks up that array's device address; make that
+ * first call before capturing a stream.  All calls on a device share the
+ * array: calls whose work overlaps on the GPU race and must be ordered by
+ * the caller (one stream, or synchronisation).  Each call clears the parts
+ * of the array that must start at zero. */
+#define LSE_STATIC_MAX_PIXELS 262144
+lse_status lse_evolve_static(const float *image, int H, int W, int B,
+                             const float *g, const float *phi0,
+                             const lse_params *params, float *phi_out,
+                             uint8_t *mask_out, lse_stats *stats, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -278,6 +278,16 @@ lse_status stage_image(lse_ctx *ctx, const void *image, PtrKind kind,
 
 }  // namespace
 
+namespace lse_detail {
+
+// Message for lse_last_error(NULL) from calls that have no context.
+void set_contextless_error(const char *msg)
+{
+    snprintf(g_create_err, sizeof(g_create_err), "%s", msg);
+}
+
+}  // namespace lse_detail
+
 extern "C" {
 
 const char *lse_version(void) { return "0.1.0"; }

@@ -144,5 +144,7 @@ cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap &phi_map,
 bool plan_step_tma(int H, int W, int B, int term, int rad, int sm_count,
                    StepArgs *a, int *nblocks, int *warps_per_block);
 int partials_needed(int sm_count);
+// Sets the message lse_last_error(NULL) returns (calls without a context).
+void set_contextless_error(const char *msg);
 
 }  // namespace lse_detail

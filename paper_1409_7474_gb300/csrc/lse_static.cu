@@ -1,0 +1,289 @@
+// lse_static.cu -- lse_evolve_static: the evolution without allocation.
+//
+// Some callers cannot allocate device memory: code running inside a host
+// framework or memory pool that owns all of the GPU's memory, or a serving
+// loop that must not call cudaMalloc (it may synchronise the device and its
+// latency is unbounded).  This entry point runs the same kernels as
+// lse_evolve, but every piece of scratch they need lives in one fixed array
+// of this file, `g_static_scratch`, which each GPU that loads the library
+// holds until the process exits:
+//   two LSF planes of LSE_STATIC_MAX_PIXELS floats (the ping-pong buffers),
+//   4096 per-block partial sums, and the device statistics record
+//   (about 2.7 MB in all).
+// Host code cannot use the array's name as a device address, so the first
+// call on each device looks the address up with cudaGetSymbolAddress (with
+// that device current) and caches it.  Calls share the array: the caller
+// orders calls whose work would overlap.  Each call clears the statistics
+// record (its last-block ticket must start at zero); everything else is
+// written before it is read.
+#include <math.h>
+#include <mutex>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "lse_internal.h"
+
+using namespace lse_detail;
+
+namespace {
+
+constexpr size_t kPlane = LSE_STATIC_MAX_PIXELS;          // floats per LSF plane
+constexpr int kMaxPartials = 4096;
+constexpr size_t kPhiBytes = 2 * kPlane * sizeof(float);
+constexpr size_t kPartialOff = kPhiBytes;
+constexpr size_t kStateOff = (kPartialOff + kMaxPartials * sizeof(LsePartial) + 255) & ~size_t(255);
+constexpr size_t kScratchBytes = kStateOff + ((sizeof(LseDevState) + 255) & ~size_t(255));
+
+static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+unsigned char *g_scratch_ptr[kMaxDevices];   // device address, per device
+
+lse_status fail(const char *fmt, ...)
+{
+    char msg[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof(msg), fmt, ap);
+    va_end(ap);
+    set_contextless_error(msg);
+    return LSE_ERR_INVALID_ARG;
+}
+
+lse_status cuda_fail(cudaError_t e, const char *what)
+{
+    char msg[512];
+    snprintf(msg, sizeof(msg), "%s: %s", what, cudaGetErrorString(e));
+    set_contextless_error(msg);
+    return LSE_ERR_CUDA;
+}
+
+bool on_device(const void *p, int dev)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) &&
+           at.device == dev;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+bool reinit_after(int n, int period)
+{
+    if (period == 1) return true;
+    if (period <= 0) return false;
+    return ((n + 1) % period) == 0;
+}
+
+void gauss_taps(double sigma, int rad, double *out)
+{
+    double total = 0.0;
+    for (int k = 0; k <= rad; ++k) {
+        out[k] = exp(-(double)(k * k) / (2.0 * sigma * sigma));
+        total += k == 0 ? out[k] : 2.0 * out[k];
+    }
+    for (int k = 0; k <= rad; ++k) out[k] /= total;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
+                                  void *, const cuuint64_t *, const cuuint64_t *,
+                                  const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool encode_rows(CUtensorMap *m, const float *base, int W, int H, int pitch,
+                 size_t band_stride, int bands, int box_w)
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)bands};
+    cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)band_stride * 4};
+    cuuint32_t box[3] = {(cuuint32_t)box_w, 1, (cuuint32_t)bands};
+    cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, bands > 1 ? 3 : 2, (void *)base, dims,
+              strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The array's device address on `dev` (current), looked up on first use.
+unsigned char *scratch_on(int dev, cudaError_t *err)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        *err = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (*err != cudaSuccess) return nullptr;
+        g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *err = cudaSuccess;
+    return g_scratch_ptr[dev];
+}
+
+}  // namespace
+
+extern "C" lse_status lse_evolve_static(const float *image, int H, int W, int B,
+                                        const float *g, const float *phi0,
+                                        const lse_params *params, float *phi_out,
+                                        uint8_t *mask_out, lse_stats *stats,
+                                        void *stream)
+{
+    set_contextless_error("");
+    if (!params) return fail("lse_evolve_static: params must not be NULL");
+    const lse_params p = *params;
+    if (H < 1 || W < 1 || (W % 4) != 0)
+        return fail("lse_evolve_static: need H >= 1 and W a positive multiple of 4 "
+                    "(got %d x %d)", H, W);
+    if ((size_t)H * (size_t)W > kPlane)
+        return fail("lse_evolve_static: H*W = %zu exceeds LSE_STATIC_MAX_PIXELS = %zu; "
+                    "use lse_evolve", (size_t)H * W, kPlane);
+    if (B < 1 || B > 4) return fail("lse_evolve_static: B = %d outside 1..4", B);
+    if (p.term != LSE_TERM_REGION && p.term != LSE_TERM_EDGE)
+        return fail("lse_evolve_static: unknown term %d", (int)p.term);
+    if (!(p.dt > 0.0f) || !isfinite(p.dt) || !(p.sigma > 0.0f) || !isfinite(p.sigma))
+        return fail("lse_evolve_static: need finite dt > 0 and sigma > 0");
+    if (p.ts < 1 || p.ts > 31 || (p.ts % 2) == 0)
+        return fail("lse_evolve_static: ts must be odd and in 1..31 (got %d)", p.ts);
+    if (p.iterations < 1 || p.reinit_period < 0)
+        return fail("lse_evolve_static: need iterations >= 1 and reinit_period >= 0");
+    if (!(p.early_stop_frac >= 0.0f) || !(p.early_stop_frac < 1.0f))
+        return fail("lse_evolve_static: early_stop_frac must be in [0, 1)");
+    if (p.storage != LSE_F32) return fail("lse_evolve_static: storage must be LSE_F32");
+    const bool region = p.term == LSE_TERM_REGION;
+    if (!region && p.reinit_period != 1)
+        return fail("lse_evolve_static: the edge term needs reinit_period = 1");
+    const float *data = region ? image : g;
+    if (!data || !phi0 || !phi_out || (region && g) || (!region && image))
+        return fail("lse_evolve_static: need phi0, phi_out and exactly one of image "
+                    "(region term) or g (edge term)");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: no current device");
+    if (dev < 0 || dev >= kMaxDevices) return fail("lse_evolve_static: device %d", dev);
+    if (!on_device(data, dev) || !on_device(phi0, dev) || !on_device(phi_out, dev) ||
+        (mask_out && !on_device(mask_out, dev)))
+        return fail("lse_evolve_static: buffers must be device memory of the current "
+                    "device (no host staging without allocation)");
+    if (!aligned16(data))
+        return fail("lse_evolve_static: image / g must be 16-byte aligned");
+    int sm_count = 0;
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (partials_needed(sm_count) > kMaxPartials)
+        return fail("lse_evolve_static: %d SMs need more partial sums than the fixed %d",
+                    sm_count, kMaxPartials);
+
+    unsigned char *scratch = scratch_on(dev, &e);
+    if (!scratch) return cuda_fail(e, "lse_evolve_static: cudaGetSymbolAddress");
+    float *phi[2] = {reinterpret_cast<float *>(scratch),
+                     reinterpret_cast<float *>(scratch) + kPlane};
+    LsePartial *partials = reinterpret_cast<LsePartial *>(scratch + kPartialOff);
+    LseDevState *st = reinterpret_cast<LseDevState *>(scratch + kStateOff);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    // the ticket and the counters of the statistics record start at zero
+    e = cudaMemsetAsync(st, 0, sizeof(LseDevState), s);
+    if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: clear state");
+    const int pitch = W;
+    const size_t band_stride = (size_t)H * W;
+    const int nred = sm_count * 4;
+    e = launch_prologue(region ? data : nullptr, pitch, band_stride, phi0,
+                        region ? nullptr : g, W, phi[0], nullptr, pitch, H, W, B,
+                        p.term, p.dt, st, partials, nred, s);
+    if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: prologue");
+
+    StepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.H = H;
+    a.W = W;
+    a.B = region ? B : 1;
+    a.term = p.term;
+    a.rad = (p.ts - 1) / 2;
+    double taps[16];
+    gauss_taps(p.sigma, a.rad, taps);
+    for (int k = 0; k < 16; ++k) a.taps[k] = k <= a.rad ? (float)taps[k] : 0.0f;
+    a.dt = p.dt;
+    a.half_dt = 0.5f * p.dt;
+    a.early_thresh = p.early_stop_frac > 0.0f ? (double)p.early_stop_frac * H * W : 0.0;
+    a.npix = (long long)H * W;
+    a.pitch = pitch;
+    a.band_stride = band_stride;
+    a.data = data;
+    a.st = st;
+    a.partials = partials;
+    int nblocks = 0, wpc = 0;
+    const char *kern = getenv("LSE_STEP_KERNEL");
+    bool use_tma = !(kern && strcmp(kern, "generic") == 0) &&
+                   plan_step_tma(H, W, a.B, p.term, a.rad, sm_count, &a, &nblocks, &wpc);
+    CUtensorMap phi_maps[2], data_map;
+    if (use_tma)
+        use_tma = encode_rows(&phi_maps[0], phi[0], W, H, pitch, 0, 1, 136) &&
+                  encode_rows(&phi_maps[1], phi[1], W, H, pitch, 0, 1, 136) &&
+                  encode_rows(&data_map, data, W, H, pitch, band_stride, a.B, 128);
+    if (!use_tma) nblocks = sm_count * 4;
+
+    auto stores_bin = [&](int k) {
+        return use_tma && reinit_after(k, p.reinit_period) && k < p.iterations - 1 &&
+               p.early_stop_frac == 0.0f;
+    };
+    for (int n = 0; n < p.iterations; ++n) {
+        if (region && B > 1) {
+            e = launch_normaliser(data, pitch, band_stride, H, W, B, p.dt, st, partials,
+                                  nred, s);
+            if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: normaliser");
+        }
+        a.iter = n;
+        a.phi_in = phi[n & 1];
+        a.phi_out = phi[(n + 1) & 1];
+        a.out_buf = (n + 1) & 1;
+        a.store_bin = stores_bin(n) ? 1 : 0;
+        a.binary_in = (n > 0 && stores_bin(n - 1)) ? 1 : 0;
+        a.binarise_in =
+            (n > 0 && reinit_after(n - 1, p.reinit_period) && !stores_bin(n - 1)) ? 1 : 0;
+        a.count_flips = (p.early_stop_frac > 0.0f || n == p.iterations - 1) ? 1 : 0;
+        if (use_tma)
+            e = launch_step_tma(a, phi_maps[n & 1], data_map, nblocks, wpc, s);
+        else
+            e = launch_step_generic(a, nblocks, s);
+        if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: step");
+    }
+    e = launch_output(phi, pitch, H, W, st, phi_out, mask_out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: output");
+    if (stats) {
+        LseDevState h;
+        e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: read statistics");
+        memset(stats, 0, sizeof(*stats));
+        stats->iterations_run = h.iterations_run;
+        stats->last_flips = h.last_flips;
+        stats->area_plus = h.area_plus;
+        for (int b = 0; b < 8; ++b) {
+            stats->c_plus[b] = h.c_plus[b];
+            stats->c_minus[b] = h.c_minus[b];
+        }
+        stats->norm = h.norm_used;
+        stats->elapsed_ms = -1.0f;
+        if (h.status_bits & LSE_SBIT_NONFINITE) stats->status = LSE_ERR_NONFINITE;
+        else if (h.status_bits & LSE_SBIT_TIMEOUT) stats->status = LSE_ERR_TIMEOUT;
+        else if (h.status_bits & LSE_SBIT_DEGENERATE) stats->status = LSE_WARN_DEGENERATE;
+        else stats->status = LSE_OK;
+    }
+    return LSE_OK;
+}

@@ -90,9 +90,14 @@ _lib.lse_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
 _lib.lse_get_stats.restype = ctypes.c_int
 _lib.lse_version.argtypes = []
 _lib.lse_version.restype = ctypes.c_char_p
+_lib.lse_evolve_static.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                   ctypes.POINTER(Params), _vp, _vp, ctypes.POINTER(Stats),
+                                   _vp]
+_lib.lse_evolve_static.restype = ctypes.c_int
 
 SYMBOLS = ("lse_create", "lse_destroy", "lse_last_error", "lse_precompute_edge",
-           "lse_evolve", "lse_get_stats", "lse_version")
+           "lse_evolve", "lse_get_stats", "lse_version", "lse_evolve_static")
+STATIC_MAX_PIXELS = 262144
 
 
 class LseError(RuntimeError):
