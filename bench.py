@@ -216,12 +216,14 @@ def kernel_profile(size: int):
     """DRAM traffic per launch of the region step kernel from a committed ncu
     summary, if it was taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "step_tma_region_traffic.json")
-    src = os.path.join(ROOT, "paper_1409_7474_gb300", "csrc", "lse_step_tma.cu")
     try:
         prof = json.load(open(path))
     except (OSError, ValueError):
         return None
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for rel in prof.get("hashed_sources", []):
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    digest = h.hexdigest()[:16]
     if prof.get("kernel_sha256_16") != digest:
         return None
     per_px = prof["dram_bytes_per_launch"] / prof["pixels"]
