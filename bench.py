@@ -212,10 +212,17 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
-def kernel_profile(size: int):
+def step_form() -> str:
+    """The region step kernel that runs: the tile form unless LSE_STEP_KERNEL
+    narrows the library's choice."""
+    return {"stream": "tma", "generic": "generic"}.get(os.environ.get("LSE_STEP_KERNEL", ""),
+                                                        "tile")
+
+
+def kernel_profile(size: int, form: str):
     """DRAM traffic per launch of the region step kernel from a committed ncu
     summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "step_tma_region_traffic.json")
+    path = os.path.join(ROOT, "profiles", f"step_{form}_region_traffic.json")
     try:
         prof = json.load(open(path))
     except (OSError, ValueError):
@@ -304,10 +311,11 @@ def main():
     alg_bytes = BYTES_PER_PX_ITER * npx
     achieved = alg_bytes / (step_kernel_ms / 1e3) / 1e9
     edge_kernel_ms = statistics.mean(step_ms_e) / iters
-    traffic = kernel_profile(size)
+    form = step_form()
+    traffic = kernel_profile(size, form)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "step_tma_kernel<region, r=4>", "peak_source": peak_src,
+                "kernel": f"step_{form}_kernel<region, r=4>", "peak_source": peak_src,
                 "bytes_per_launch": alg_bytes, "mean_launch_ms": step_kernel_ms,
                 "edge_kernel_frac": alg_bytes / (edge_kernel_ms / 1e3) / 1e9 / peak}
 

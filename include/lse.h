@@ -141,9 +141,11 @@ typedef struct lse_ctx lse_ctx;
  * use; that growth is refused while the stream is being captured.
  * Returns LSE_ERR_INVALID_ARG for a NULL out-pointer, a bad device or sizes,
  * LSE_ERR_OOM when an allocation fails; *ctx is NULL on failure.
- * With the environment variable LSE_STEP_KERNEL=generic at creation, the
- * context runs every iteration on the plain shared-memory step kernel
- * instead of the TMA-streamed one (a cross-check of the two). */
+ * The step kernel is chosen per call: the TMA tile form for one band or the
+ * edge term, the TMA streaming form for 2-4 bands, the plain shared-memory
+ * kernel for what neither covers.  The environment variable LSE_STEP_KERNEL
+ * at creation narrows the choice, for cross-checks: "stream" skips the tile
+ * form, "generic" runs every iteration on the plain kernel. */
 lse_status lse_create(lse_ctx **ctx, int device, size_t max_pixels,
                       int max_bands);
 

@@ -46,7 +46,7 @@ struct lse_ctx {
     LseDevState *st_host = nullptr;  // pinned mirror
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool have_stats = false;
-    bool force_generic = false;      // LSE_STEP_KERNEL=generic at creation
+    int step_form = 0;               // LSE_STEP_KERNEL at creation (LSE_FORM_*)
 };
 
 namespace {
@@ -146,64 +146,6 @@ lse_status ensure_t(lse_ctx *ctx, T **p, size_t *cap_elems, size_t elems,
     *p = static_cast<T *>(vp);
     *cap_elems = cap_bytes / sizeof(T);
     return r;
-}
-
-void gauss_taps(double sigma, int rad, double *out)
-{
-    double total = 0.0;
-    for (int k = 0; k <= rad; ++k) {
-        out[k] = exp(-(double)(k * k) / (2.0 * sigma * sigma));
-        total += k == 0 ? out[k] : 2.0 * out[k];
-    }
-    for (int k = 0; k <= rad; ++k) out[k] /= total;
-}
-
-bool reinit_after(int n, int period)
-{
-    if (period == 1) return true;
-    if (period <= 0) return false;
-    return ((n + 1) % period) == 0;
-}
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
-                                  void *, const cuuint64_t *, const cuuint64_t *,
-                                  const cuuint32_t *, const cuuint32_t *,
-                                  CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn()
-{
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-        cudaGetLastError();
-    }
-    return fn;
-}
-
-// Row tensor map over a pitched float32 array of `bands` planes.
-bool encode_rows(CUtensorMap *m, const float *base, int W, int H, int pitch,
-                 size_t band_stride, int bands, int box_w)
-{
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
-    cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)bands};
-    cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)band_stride * 4};
-    cuuint32_t box[3] = {(cuuint32_t)box_w, 1, (cuuint32_t)bands};
-    cuuint32_t es[3] = {1, 1, 1};
-    const cuuint32_t rank = bands > 1 ? 3 : 2;
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, (void *)base, dims,
-                    strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
 }
 
 lse_status check_image_args(lse_ctx *ctx, lse_dtype dtype, int H, int W, int B)
@@ -341,8 +283,7 @@ lse_status lse_create(lse_ctx **out, int device, size_t max_pixels, int max_band
     ctx->max_bands = max_bands;
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     ctx->n_partials = partials_needed(ctx->sm_count);
-    const char *kern = getenv("LSE_STEP_KERNEL");
-    ctx->force_generic = kern && strcmp(kern, "generic") == 0;
+    ctx->step_form = step_form_from_env();
     cudaError_t e = cudaMalloc(&ctx->partials, sizeof(LsePartial) * ctx->n_partials);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->st, sizeof(LseDevState));
     if (e == cudaSuccess) e = cudaMemset(ctx->st, 0, sizeof(LseDevState));
@@ -574,37 +515,10 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
                         p.dt, ctx->st, ctx->partials, nred, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "prologue");
 
-    // the step's work decomposition and tensor maps
-    StepArgs a;
-    memset(&a, 0, sizeof(a));
-    a.H = H;
-    a.W = W;
-    a.B = region ? B : 1;
-    a.term = p.term;
-    a.rad = (p.ts - 1) / 2;
-    double taps[16];
-    gauss_taps(p.sigma, a.rad, taps);
-    for (int k = 0; k < 16; ++k) a.taps[k] = k <= a.rad ? (float)taps[k] : 0.0f;
-    a.dt = p.dt;
-    a.half_dt = 0.5f * p.dt;
-    a.early_thresh = p.early_stop_frac > 0.0f ? (double)p.early_stop_frac * H * W : 0.0;
-    a.npix = (long long)H * W;
-    a.pitch = pitch;
-    a.band_stride = band_stride;
-    a.data = data;
-    a.st = ctx->st;
-    a.partials = ctx->partials;
-    int nblocks = 0, wpc = 0;
-    bool use_tma = !ctx->force_generic &&
-                   plan_step_tma(H, W, a.B, p.term, a.rad, ctx->sm_count, &a, &nblocks, &wpc);
-    // the fused step stages 136 phi columns and 128 data columns per band
-    CUtensorMap phi_maps[2], data_map;
-    if (use_tma) {
-        use_tma = encode_rows(&phi_maps[0], ctx->phi[0], W, H, pitch, 0, 1, 136) &&
-                  encode_rows(&phi_maps[1], ctx->phi[1], W, H, pitch, 0, 1, 136) &&
-                  encode_rows(&data_map, data, W, H, pitch, band_stride, a.B, 128);
-    }
-    if (!use_tma) nblocks = ctx->sm_count * 4;
+    // the step's kernel, work decomposition and tensor maps
+    StepPlan plan;
+    plan_step(H, W, B, p, pitch, band_stride, data, ctx->phi, ctx->st, ctx->partials,
+              ctx->sm_count, ctx->step_form, &plan);
 
     e = cudaEventRecord(ctx->ev0, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
@@ -614,26 +528,7 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
                                   ctx->partials, nred, s);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "normaliser");
         }
-        a.iter = n;
-        a.phi_in = ctx->phi[n & 1];
-        a.phi_out = ctx->phi[(n + 1) & 1];
-        a.out_buf = (n + 1) & 1;
-        // A re-initialising step other than the last stores sign(v) directly
-        // (the TMA kernel), unless an early stop may make it the last one;
-        // then it stores v and the next step binarises on load.
-        auto stores_bin = [&](int k) {
-            return use_tma && reinit_after(k, p.reinit_period) && k < p.iterations - 1 &&
-                   p.early_stop_frac == 0.0f;
-        };
-        a.store_bin = stores_bin(n) ? 1 : 0;
-        a.binary_in = (n > 0 && stores_bin(n - 1)) ? 1 : 0;
-        a.binarise_in = (n > 0 && reinit_after(n - 1, p.reinit_period) && !stores_bin(n - 1)) ? 1 : 0;
-        // sign changes matter for the early stop and the last step's statistics
-        a.count_flips = (p.early_stop_frac > 0.0f || n == p.iterations - 1) ? 1 : 0;
-        if (use_tma)
-            e = launch_step_tma(a, phi_maps[n & 1], data_map, nblocks, wpc, s);
-        else
-            e = launch_step_generic(a, nblocks, s);
+        e = launch_step(plan, n, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step");
     }
     e = cudaEventRecord(ctx->ev1, s);

@@ -143,7 +143,37 @@ cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap &phi_map,
 // Work decomposition of the TMA step for a shape on `sm_count` SMs.
 bool plan_step_tma(int H, int W, int B, int term, int rad, int sm_count,
                    StepArgs *a, int *nblocks, int *warps_per_block);
+// Tile-form step (one band or the edge term): work decomposition and launch.
+// Its tensor maps have boxes of 136 x (66) phi and 128 x 64 data elements.
+bool plan_step_tile(int H, int W, int B, int term, int rad, int sm_count,
+                    StepArgs *a, int *nblocks);
+cudaError_t launch_step_tile(const StepArgs &a, const CUtensorMap &phi_map,
+                             const CUtensorMap &data_map, int nblocks, cudaStream_t s);
 int partials_needed(int sm_count);
+
+// Which step kernel a call runs.  LSE_STEP_KERNEL=generic or =stream at
+// context creation (at each call for lse_evolve_static) narrows the choice.
+enum { LSE_FORM_AUTO = 0, LSE_FORM_TILE = 1, LSE_FORM_STREAM = 2, LSE_FORM_GENERIC = 3 };
+
+struct StepPlan {
+    StepArgs args;
+    int form;                   // LSE_FORM_TILE / _STREAM / _GENERIC
+    int nblocks, wpc;
+    CUtensorMap phi_maps[2], data_map;
+    float *phi[2];              // the ping-pong pair (phi_maps[i] maps phi[i])
+    int iterations, reinit_period;
+    bool early_stop;
+};
+
+void gauss_taps(double sigma, int rad, double *out);
+int step_form_from_env();
+// Fills the step arguments for a call and picks its kernel (`requested` is
+// LSE_FORM_AUTO, _STREAM or _GENERIC).
+void plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_stride,
+               const float *data, float *const phi[2], LseDevState *st,
+               LsePartial *partials, int sm_count, int requested, StepPlan *plan);
+// Launches iteration n (0-based) of the plan.
+cudaError_t launch_step(StepPlan &plan, int n, cudaStream_t s);
 // Sets the message lse_last_error(NULL) returns (calls without a context).
 void set_contextless_error(const char *msg);
 

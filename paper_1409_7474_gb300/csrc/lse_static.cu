@@ -75,54 +75,6 @@ bool on_device(const void *p, int dev)
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-bool reinit_after(int n, int period)
-{
-    if (period == 1) return true;
-    if (period <= 0) return false;
-    return ((n + 1) % period) == 0;
-}
-
-void gauss_taps(double sigma, int rad, double *out)
-{
-    double total = 0.0;
-    for (int k = 0; k <= rad; ++k) {
-        out[k] = exp(-(double)(k * k) / (2.0 * sigma * sigma));
-        total += k == 0 ? out[k] : 2.0 * out[k];
-    }
-    for (int k = 0; k <= rad; ++k) out[k] /= total;
-}
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
-                                  void *, const cuuint64_t *, const cuuint64_t *,
-                                  const cuuint32_t *, const cuuint32_t *,
-                                  CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-bool encode_rows(CUtensorMap *m, const float *base, int W, int H, int pitch,
-                 size_t band_stride, int bands, int box_w)
-{
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
-    cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)bands};
-    cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)band_stride * 4};
-    cuuint32_t box[3] = {(cuuint32_t)box_w, 1, (cuuint32_t)bands};
-    cuuint32_t es[3] = {1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, bands > 1 ? 3 : 2, (void *)base, dims,
-              strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 // The array's device address on `dev` (current), looked up on first use.
 unsigned char *scratch_on(int dev, cudaError_t *err)
 {
@@ -208,59 +160,16 @@ extern "C" lse_status lse_evolve_static(const float *image, int H, int W, int B,
                         p.term, p.dt, st, partials, nred, s);
     if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: prologue");
 
-    StepArgs a;
-    memset(&a, 0, sizeof(a));
-    a.H = H;
-    a.W = W;
-    a.B = region ? B : 1;
-    a.term = p.term;
-    a.rad = (p.ts - 1) / 2;
-    double taps[16];
-    gauss_taps(p.sigma, a.rad, taps);
-    for (int k = 0; k < 16; ++k) a.taps[k] = k <= a.rad ? (float)taps[k] : 0.0f;
-    a.dt = p.dt;
-    a.half_dt = 0.5f * p.dt;
-    a.early_thresh = p.early_stop_frac > 0.0f ? (double)p.early_stop_frac * H * W : 0.0;
-    a.npix = (long long)H * W;
-    a.pitch = pitch;
-    a.band_stride = band_stride;
-    a.data = data;
-    a.st = st;
-    a.partials = partials;
-    int nblocks = 0, wpc = 0;
-    const char *kern = getenv("LSE_STEP_KERNEL");
-    bool use_tma = !(kern && strcmp(kern, "generic") == 0) &&
-                   plan_step_tma(H, W, a.B, p.term, a.rad, sm_count, &a, &nblocks, &wpc);
-    CUtensorMap phi_maps[2], data_map;
-    if (use_tma)
-        use_tma = encode_rows(&phi_maps[0], phi[0], W, H, pitch, 0, 1, 136) &&
-                  encode_rows(&phi_maps[1], phi[1], W, H, pitch, 0, 1, 136) &&
-                  encode_rows(&data_map, data, W, H, pitch, band_stride, a.B, 128);
-    if (!use_tma) nblocks = sm_count * 4;
-
-    auto stores_bin = [&](int k) {
-        return use_tma && reinit_after(k, p.reinit_period) && k < p.iterations - 1 &&
-               p.early_stop_frac == 0.0f;
-    };
+    StepPlan plan;
+    plan_step(H, W, B, p, pitch, band_stride, data, phi, st, partials, sm_count,
+              step_form_from_env(), &plan);
     for (int n = 0; n < p.iterations; ++n) {
         if (region && B > 1) {
             e = launch_normaliser(data, pitch, band_stride, H, W, B, p.dt, st, partials,
                                   nred, s);
             if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: normaliser");
         }
-        a.iter = n;
-        a.phi_in = phi[n & 1];
-        a.phi_out = phi[(n + 1) & 1];
-        a.out_buf = (n + 1) & 1;
-        a.store_bin = stores_bin(n) ? 1 : 0;
-        a.binary_in = (n > 0 && stores_bin(n - 1)) ? 1 : 0;
-        a.binarise_in =
-            (n > 0 && reinit_after(n - 1, p.reinit_period) && !stores_bin(n - 1)) ? 1 : 0;
-        a.count_flips = (p.early_stop_frac > 0.0f || n == p.iterations - 1) ? 1 : 0;
-        if (use_tma)
-            e = launch_step_tma(a, phi_maps[n & 1], data_map, nblocks, wpc, s);
-        else
-            e = launch_step_generic(a, nblocks, s);
+        e = launch_step(plan, n, s);
         if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: step");
     }
     e = launch_output(phi, pitch, H, W, st, phi_out, mask_out, s);

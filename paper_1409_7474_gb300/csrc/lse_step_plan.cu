@@ -1,0 +1,168 @@
+// lse_step_plan.cu -- the per-call set-up of the step: its arguments, which
+// step kernel runs (tile form, streaming form or the generic kernel), the
+// tensor maps of the TMA forms, and the per-iteration flags.  Shared by
+// lse_evolve and lse_evolve_static.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "lse_internal.h"
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
+                                  void *, const cuuint64_t *, const cuuint64_t *,
+                                  const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor map over a pitched float32 array of `bands` planes; boxes of
+// box_w x box_h elements (x all bands).
+bool encode_box(CUtensorMap *m, const float *base, int W, int H, int pitch,
+                size_t band_stride, int bands, int box_w, int box_h)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)bands};
+    cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)band_stride * 4};
+    cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, (cuuint32_t)bands};
+    cuuint32_t es[3] = {1, 1, 1};
+    const cuuint32_t rank = bands > 1 ? 3 : 2;
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, (void *)base, dims,
+                    strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool reinit_after(int n, int period)
+{
+    if (period == 1) return true;
+    if (period <= 0) return false;
+    return ((n + 1) % period) == 0;
+}
+
+}  // namespace
+
+namespace lse_detail {
+
+void gauss_taps(double sigma, int rad, double *out)
+{
+    double total = 0.0;
+    for (int k = 0; k <= rad; ++k) {
+        out[k] = exp(-(double)(k * k) / (2.0 * sigma * sigma));
+        total += k == 0 ? out[k] : 2.0 * out[k];
+    }
+    for (int k = 0; k <= rad; ++k) out[k] /= total;
+}
+
+int step_form_from_env()
+{
+    const char *k = getenv("LSE_STEP_KERNEL");
+    if (!k) return LSE_FORM_AUTO;
+    if (strcmp(k, "generic") == 0) return LSE_FORM_GENERIC;
+    if (strcmp(k, "stream") == 0) return LSE_FORM_STREAM;
+    return LSE_FORM_AUTO;
+}
+
+void plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_stride,
+               const float *data, float *const phi[2], LseDevState *st,
+               LsePartial *partials, int sm_count, int requested, StepPlan *plan)
+{
+    StepArgs &a = plan->args;
+    memset(&a, 0, sizeof(a));
+    const bool region = p.term == LSE_TERM_REGION;
+    a.H = H;
+    a.W = W;
+    a.B = region ? B : 1;
+    a.term = p.term;
+    a.rad = (p.ts - 1) / 2;
+    double taps[16];
+    gauss_taps(p.sigma, a.rad, taps);
+    for (int k = 0; k < 16; ++k) a.taps[k] = k <= a.rad ? (float)taps[k] : 0.0f;
+    a.dt = p.dt;
+    a.half_dt = 0.5f * p.dt;
+    a.early_thresh = p.early_stop_frac > 0.0f ? (double)p.early_stop_frac * H * W : 0.0;
+    a.npix = (long long)H * W;
+    a.pitch = pitch;
+    a.band_stride = band_stride;
+    a.data = data;
+    a.st = st;
+    a.partials = partials;
+    plan->phi[0] = phi[0];
+    plan->phi[1] = phi[1];
+    plan->iterations = p.iterations;
+    plan->reinit_period = p.reinit_period;
+    plan->early_stop = p.early_stop_frac > 0.0f;
+    plan->wpc = 0;
+
+    plan->form = LSE_FORM_GENERIC;
+    if (requested == LSE_FORM_AUTO &&
+        plan_step_tile(H, W, a.B, p.term, a.rad, sm_count, &a, &plan->nblocks) &&
+        encode_box(&plan->phi_maps[0], phi[0], W, H, pitch, 0, 1, 136, 66) &&
+        encode_box(&plan->phi_maps[1], phi[1], W, H, pitch, 0, 1, 136, 66) &&
+        encode_box(&plan->data_map, data, W, H, pitch, band_stride, 1, 128, 64)) {
+        plan->form = LSE_FORM_TILE;
+    } else if (requested != LSE_FORM_GENERIC &&
+               plan_step_tma(H, W, a.B, p.term, a.rad, sm_count, &a, &plan->nblocks,
+                             &plan->wpc) &&
+               encode_box(&plan->phi_maps[0], phi[0], W, H, pitch, 0, 1, 136, 1) &&
+               encode_box(&plan->phi_maps[1], phi[1], W, H, pitch, 0, 1, 136, 1) &&
+               encode_box(&plan->data_map, data, W, H, pitch, band_stride, a.B, 128, 1)) {
+        plan->form = LSE_FORM_STREAM;
+    } else {
+        plan->nblocks = sm_count * 4;
+    }
+}
+
+// A re-initialising step other than the last stores sign(v) directly (the
+// TMA forms), unless an early stop may make it the last one; then it stores
+// v and the next step binarises on load.
+static bool stores_bin(const StepPlan &plan, int k)
+{
+    return plan.form != LSE_FORM_GENERIC && reinit_after(k, plan.reinit_period) &&
+           k < plan.iterations - 1 && !plan.early_stop;
+}
+
+cudaError_t launch_step(StepPlan &plan, int n, cudaStream_t s)
+{
+    StepArgs &a = plan.args;
+    a.iter = n;
+    a.phi_in = plan.phi[n & 1];
+    a.phi_out = plan.phi[(n + 1) & 1];
+    a.out_buf = (n + 1) & 1;
+    a.store_bin = stores_bin(plan, n) ? 1 : 0;
+    a.binary_in = (n > 0 && stores_bin(plan, n - 1)) ? 1 : 0;
+    a.binarise_in =
+        (n > 0 && reinit_after(n - 1, plan.reinit_period) && !stores_bin(plan, n - 1)) ? 1 : 0;
+    // sign changes matter for the early stop and the last step's statistics
+    a.count_flips = (plan.early_stop || n == plan.iterations - 1) ? 1 : 0;
+    switch (plan.form) {
+    case LSE_FORM_TILE:
+        return launch_step_tile(a, plan.phi_maps[n & 1], plan.data_map, plan.nblocks, s);
+    case LSE_FORM_STREAM:
+        return launch_step_tma(a, plan.phi_maps[n & 1], plan.data_map, plan.nblocks,
+                               plan.wpc, s);
+    default:
+        return launch_step_generic(a, plan.nblocks, s);
+    }
+}
+
+}  // namespace lse_detail

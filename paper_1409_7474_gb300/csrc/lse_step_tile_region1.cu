@@ -1,0 +1,13 @@
+// lse_step_tile_region1.cu -- instantiations of the tile-form step for the
+// single-band region term (Eq. 17).
+#include "lse_step_tile.cuh"
+
+namespace lse_detail {
+
+cudaError_t launch_step_tile_region1(const StepArgs &a, const CUtensorMap &pm,
+                                     const CUtensorMap &dm, int nblocks, cudaStream_t s)
+{
+    return lse_tile::launch_tile_kind<0>(a, pm, dm, nblocks, s);
+}
+
+}  // namespace lse_detail

@@ -1,6 +1,7 @@
 // lse_step_tma.cu -- work decomposition and dispatch of the fused step
-// kernel (the kernel itself is in lse_step_tma.cuh; one instantiation file per
-// data term).
+// kernels: the streaming form (lse_step_tma.cuh, any band count) and the tile
+// form (lse_step_tile.cuh, one band or the edge term); one instantiation file
+// per form and data term.
 #include "lse_step_tma.cuh"
 
 namespace lse_detail {
@@ -14,6 +15,10 @@ cudaError_t launch_step_tma_multiband(const StepArgs &, const CUtensorMap &,
 int step_tma_warp_bytes_region1(int rad);
 int step_tma_warp_bytes_edge(int rad);
 int step_tma_warp_bytes_multiband(int rad);
+cudaError_t launch_step_tile_region1(const StepArgs &, const CUtensorMap &,
+                                     const CUtensorMap &, int, cudaStream_t);
+cudaError_t launch_step_tile_edge(const StepArgs &, const CUtensorMap &,
+                                  const CUtensorMap &, int, cudaStream_t);
 
 }  // namespace lse_detail
 
@@ -83,6 +88,36 @@ cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap &phi_map,
     default:
         return launch_step_tma_multiband(a, phi_map, data_map, nblocks, warps_per_block, s);
     }
+}
+
+// Tile form: tiles of (64 - 2 rad) output rows x (128 - 8 ceil(rad / 4))
+// output columns, walked by up to 2 CTAs per SM.
+bool plan_step_tile(int H, int W, int B, int term, int rad, int sm_count,
+                    StepArgs *a, int *nblocks)
+{
+    if (rad < 1 || rad > 7) return false;
+    if (term == LSE_TERM_REGION && B != 1) return false;
+    const int hl = (rad + 3) / 4;
+    const int useful = 128 - 8 * hl;
+    const int th = 64 - 2 * rad;
+    const int tiles_x = (W + useful - 1) / useful;
+    const int tiles_y = (H + th - 1) / th;
+    a->useful = useful;
+    a->n_strips = tiles_x;
+    a->n_rowblocks = tiles_y;
+    a->th = th;
+    a->n_items = tiles_x * tiles_y;
+    int blocks = a->n_items;
+    if (blocks > sm_count * 2) blocks = sm_count * 2;
+    *nblocks = blocks;
+    return true;
+}
+
+cudaError_t launch_step_tile(const StepArgs &a, const CUtensorMap &phi_map,
+                             const CUtensorMap &data_map, int nblocks, cudaStream_t s)
+{
+    if (a.term == LSE_TERM_EDGE) return launch_step_tile_edge(a, phi_map, data_map, nblocks, s);
+    return launch_step_tile_region1(a, phi_map, data_map, nblocks, s);
 }
 
 }  // namespace lse_detail

@@ -197,26 +197,45 @@ def test_runs_are_bitwise_deterministic(torch, ctx):
     assert a[2]["c_plus"] == b[2]["c_plus"] and a[2]["last_flips"] == b[2]["last_flips"]
 
 
-def test_tma_kernel_agrees_with_plain_kernel(torch):
+@pytest.mark.parametrize("term", ["region", "edge"])
+def test_step_forms_agree(torch, term):
+    """The tile form, the streaming form and the plain shared-memory kernel
+    (LSE_STEP_KERNEL selects them) compute the same step: the two TMA forms
+    sum in the same order, so one iteration agrees bit for bit; the plain
+    kernel agrees to rounding.  Four iterations with re-initialisation run
+    the +-1 input and output variants."""
     code = r"""
 import numpy as np, torch, sys
 sys.path.insert(0, %r)
 import paper_1409_7474_gb300.lse as lse
 from paper_1409_7474_gb300 import scenes
-img, _, _ = scenes.rect_scene(300, 410, 120, 70)
-phi0 = scenes.circle_phi(300, 410, radius=90)
-with lse.Context(0, 300 * 410, 1) as c:
-    v, m, st = c.evolve(torch.from_numpy(img).cuda(), torch.from_numpy(phi0).cuda(), iterations=1)
-    np.save(sys.argv[1], v.cpu().numpy())
+img, _, _ = scenes.rect_scene(300, 412, 120, 70)
+phi0 = scenes.circle_phi(300, 412, radius=90)
+x = torch.from_numpy(img).cuda()
+p = torch.from_numpy(phi0).cuda()
+out = {}
+with lse.Context(0, 300 * 412, 1) as c:
+    g = c.precompute_edge(x) if sys.argv[2] == "edge" else None
+    for it in (1, 4):
+        v, m, st = c.evolve(x, p, sys.argv[2], g=g, iterations=it)
+        out["v%%d" %% it] = v.cpu().numpy()
+        out["m%%d" %% it] = m.cpu().numpy()
+np.savez(sys.argv[1], **out)
 """ % os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    outs = []
-    for kern in ("tma", "generic"):
-        path = f"/tmp/lse_kernel_{kern}_{os.getpid()}.npy"
+    outs = {}
+    for kern in ("tile", "stream", "generic"):
+        path = f"/tmp/lse_kernel_{kern}_{os.getpid()}.npz"
         env = dict(os.environ, LSE_STEP_KERNEL=kern)
-        subprocess.run([sys.executable, "-c", code, path], env=env, check=True, timeout=300)
-        outs.append(np.load(path))
+        subprocess.run([sys.executable, "-c", code, path, term], env=env, check=True,
+                       timeout=300)
+        with np.load(path) as z:
+            outs[kern] = {k: z[k] for k in z.files}
         os.remove(path)
-    assert np.abs(outs[0] - outs[1]).max() <= 4e-6
+    t, s_, g = outs["tile"], outs["stream"], outs["generic"]
+    assert np.array_equal(t["v1"].view(np.uint32), s_["v1"].view(np.uint32))
+    assert np.abs(t["v1"] - g["v1"]).max() <= 4e-6
+    for other in (s_, g):
+        assert (t["m4"] != other["m4"]).mean() <= 1e-4
 
 
 # ---------------------------------------------------------------- options
