@@ -239,7 +239,7 @@ cudaError_t launch_output(float *const *bufs, int pitch, int H, int W,
 
 int partials_needed(int sm_count)
 {
-    // the widest reducing launch: 2 CTAs of 8 warps per SM (TMA step) or
+    // the widest reducing launch: 3 CTAs of 8 warps per SM (TMA step) or
     // 8 CTAs of 256 threads per SM (grid-stride kernels)
     return sm_count * 8;
 }

@@ -1,32 +1,40 @@
-// lse_step_tile.cuh -- the fused LSE iteration, tile form (single-band
-// region term and edge term, TS = 3..15).
+// lse_step_tile.cuh -- the fused LSE iteration, tile form (one band of the
+// region term, or the edge term; TS = 3..15).
 //
 // Same arithmetic as the streaming kernel (lse_step_tma.cuh): per pixel
 //   u = phi + dt R |grad phi|                        (Eq. 18)
 //   v = G_sigma * u                                  (Table I step 4)
 // then v (or sign(v) on re-initialising steps, Table I step 3) is stored and
-// the next iteration's region sums are accumulated (Eq. 15).
+// the next iteration's region sums are accumulated (Eq. 15).  Both forms sum
+// in the same order, so their v agree bit for bit.
 //
 // Work decomposition.  A persistent CTA of 8 warps walks a static list of
-// tiles of TH output rows x (128 - 8 HL) output columns.  Per tile:
-//   1. TMA stages phi on the tile + (RAD + 1) halo rows and 4 halo columns
-//      (136 x (TH + 2 RAD + 2) floats) and the data term on the tile + RAD
-//      halo rows (128 x (TH + 2 RAD)); ghost columns are patched in for
-//      tiles on the image's left/right edge;
-//   2. each warp takes every 8th u-row: lane l computes u for 4 columns in
-//      registers, the horizontal Gaussian pass takes neighbouring lanes' u
-//      by shuffles, and the result h goes to shared memory;
-//   3. each warp takes TH / 8 consecutive output rows: lane l slides a
-//      2 RAD + 1 row register window of h down its 4 columns, stores v and
+// tiles of TH = 64 - 2 RAD output rows x (128 - 8 HL) output columns.  Per
+// tile:
+//   1. TMA stages phi on the tile plus RAD + 1 halo rows and 4 halo columns
+//      per side (136 x 66 floats) and the data term on the tile plus RAD halo
+//      rows (128 x 64); ghost columns are patched in on the image's edges;
+//   2. u pass: warp w takes the 8 consecutive u rows 8w .. 8w + 7, rolling
+//      the three phi rows of the gradient through registers; lane l holds 4
+//      columns, the horizontal Gaussian pass takes neighbouring lanes' u by
+//      shuffles, and h overwrites the phi row the warp has just consumed
+//      (phi rows shared with the next warp are read before a barrier);
+//   3. vertical pass: warp w takes RPW consecutive output rows, sliding a
+//      2 RAD + 1 row register ring down its 4 columns of h; it stores v and
 //      accumulates the statistics.
-// The next tile's phi is loaded while step 3 runs (its buffer is free after
-// step 2) and its data term right after; a second CTA on the SM overlaps
-// the rest.  Per-row bookkeeping is per tile, not per row.
+// With h in the phi buffer a CTA needs 70 KB of shared memory, so three CTAs
+// share an SM (radius <= 4) and cover each other's TMA waits; the next tile
+// is loaded as soon as the vertical pass is done.
 //
-// Waits on the TMA mbarriers are bounded (LSE_WAIT_LIMIT polls): a wait
-// that runs out sets the TIMEOUT status bit, drains the copies in flight
-// (bounded) and stops the CTA's tile loop; the CTA still reaches its
-// reduction.
+// FAST instantiations serve the steady state of a re-initialising evolution
+// (phi = +-1 in, sign(v) out, no sign-change count): ghost columns make the
+// image border a plain central difference and |grad phi| takes one of six
+// values, read from a table of correctly rounded square roots.  The general
+// instantiations take any input and every per-step option.
+//
+// Waits on the TMA mbarriers are bounded (LSE_WAIT_LIMIT polls): a wait that
+// runs out sets the TIMEOUT status bit, drains the copies in flight (bounded)
+// and ends the CTA's tile loop; the CTA still takes part in the reduction.
 #pragma once
 
 #include "lse_reduce.cuh"
@@ -36,25 +44,25 @@ namespace lse_tile {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kURows = 64;            // u / h rows per tile (TH + 2 RAD)
+constexpr int kURowsPerWarp = kURows / kWarps;
+constexpr int kPhiRows = kURows + 2;  // staged phi rows
 constexpr int kPhiW = 136;            // staged phi columns
 constexpr int kDataW = 128;           // staged data columns
 
 template <int RAD>
 struct TileGeo {
-    static constexpr int HL = (RAD + 3) / 4;
+    static constexpr int HL = (RAD + 3) / 4;                    // halo lanes per side
     static constexpr int USEFUL = 128 - 8 * HL;                 // output columns
     static constexpr int TH = kURows - 2 * RAD;                 // output rows
-    static constexpr int PHI_ROWS = kURows + 2;
-    static constexpr int ROWS_PER_WARP = (TH + kWarps - 1) / kWarps;
-    static constexpr int PHI_FLOATS = PHI_ROWS * kPhiW;
-    static constexpr int DATA_FLOATS = kURows * kDataW;
-    static constexpr int H_FLOATS = kURows * kDataW;
-    // shared memory: [lut 32][2 mbarriers (4 floats), pad to 32][phi][data][h]
-    static constexpr int PHI_OFF = 64;
-    static constexpr int DATA_OFF = PHI_OFF + ((PHI_FLOATS + 31) & ~31);
-    static constexpr int H_OFF = DATA_OFF + DATA_FLOATS;
-    static constexpr int FLOATS = H_OFF + H_FLOATS;
+    static constexpr int RPW = (TH + kWarps - 1) / kWarps;      // output rows per warp
+    // shared memory (floats): [sqrt table 32][2 mbarriers][old-sign words
+    // 64 x 4][phi, then h: 66 x 136][data 64 x 128]
+    static constexpr int SIGN_OFF = 64;
+    static constexpr int PHI_OFF = SIGN_OFF + kURows * 4;
+    static constexpr int DATA_OFF = PHI_OFF + ((kPhiRows * kPhiW + 31) & ~31);
+    static constexpr int FLOATS = DATA_OFF + kURows * kDataW;
     static constexpr int BYTES = FLOATS * 4 + 128;              // + alignment slack
+    static constexpr int MIN_BLOCKS = RAD <= 4 ? 3 : 2;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -103,19 +111,29 @@ __device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap *map, in
 
 __device__ __forceinline__ float bin(float v) { return v >= 0.0f ? 1.0f : -1.0f; }
 
+__device__ __forceinline__ float4 bin4(float4 v)
+{
+    return make_float4(bin(v.x), bin(v.y), bin(v.z), bin(v.w));
+}
+
 __device__ __forceinline__ float comp(const float4 &v, int j)
 {
     return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
 }
 
-template <int KIND_EDGE, int RAD, bool BIN>
-__global__ void __launch_bounds__(kThreads, 2)
+__device__ __forceinline__ float4 lds4(const float *p)
+{
+    return *reinterpret_cast<const float4 *>(p);
+}
+
+template <int KIND_EDGE, int RAD, bool FAST>
+__global__ void __launch_bounds__(kThreads, TileGeo<RAD>::MIN_BLOCKS)
 step_tile_kernel(const __grid_constant__ StepArgs a,
                  const __grid_constant__ CUtensorMap phi_map,
                  const __grid_constant__ CUtensorMap data_map)
 {
     using G = TileGeo<RAD>;
-    constexpr int HL = G::HL, TH = G::TH, P = 2 * RAD + 1;
+    constexpr int HL = G::HL, TH = G::TH, P = 2 * RAD + 1, RPW = G::RPW;
     constexpr bool EDGE = KIND_EDGE != 0;
 
     LseDevState *st = a.st;
@@ -123,17 +141,17 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
 
     extern __shared__ float smem_f[];
     const uint32_t sm0 = smem_u32(smem_f);
-    const int sb = (int)(((128u - (sm0 & 127u)) & 127u) >> 2);   // aligned base
+    const int sb = (int)(((128u - (sm0 & 127u)) & 127u) >> 2);   // 128-byte aligned base
     float *lut = smem_f + sb;
-    float *phi_s = smem_f + sb + G::PHI_OFF;
-    float *dat_s = smem_f + sb + G::DATA_OFF;
-    float *h_s = smem_f + sb + G::H_OFF;
+    uint32_t *sign_w = reinterpret_cast<uint32_t *>(smem_f + sb + G::SIGN_OFF);
+    float *buf = smem_f + sb + G::PHI_OFF;
+    const float *dat = smem_f + sb + G::DATA_OFF;
     const uint32_t bar_phi = sm0 + 4u * (uint32_t)(sb + 32);
     const uint32_t bar_dat = bar_phi + 8;
     const uint32_t phi_dst = sm0 + 4u * (uint32_t)(sb + G::PHI_OFF);
     const uint32_t dat_dst = sm0 + 4u * (uint32_t)(sb + G::DATA_OFF);
-    constexpr uint32_t kPhiBytes = G::PHI_FLOATS * 4;
-    constexpr uint32_t kDatBytes = G::DATA_FLOATS * 4;
+    constexpr uint32_t kPhiBytes = kPhiRows * kPhiW * 4;
+    constexpr uint32_t kDatBytes = kURows * kDataW * 4;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -141,7 +159,7 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
     const int H = a.H, W = a.W;
     const int tiles_x = a.n_strips, n_tiles = a.n_items;
 
-    if (tid < 32) {
+    if (FAST && tid < 32) {
         // sqrt table indexed by bits(q) >> 21 & 31 for q in {0,4,8,16,20,32}
         const float q = tid == 4 ? 4.f : tid == 8 ? 8.f : tid == 12 ? 16.f
                       : tid == 13 ? 20.f : tid == 16 ? 32.f : 0.f;
@@ -159,31 +177,24 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
     for (int k = 0; k <= RAD; ++k) tp[k] = a.taps[k];
     const float coef = EDGE ? a.half_dt : st->a[0];
     const float mid = EDGE ? 0.0f : st->m[0];
-    const bool binarise_in = !BIN && a.binarise_in != 0;
-    const bool count_flips = a.count_flips != 0;
-    const bool store_bin = a.store_bin != 0;
+    const bool binarise_in = !FAST && a.binarise_in != 0;
+    const bool count_flips = !FAST && a.count_flips != 0;
+    const bool store_bin = FAST || a.store_bin != 0;
 
     auto origin = [&](int t, int &xs, int &ys) {
         const int ty = t / tiles_x;
         xs = (t - ty * tiles_x) * G::USEFUL - 4 * HL;   // first staged data column
         ys = ty * TH - (RAD + 1);                        // first staged phi row
     };
-    auto load_phi = [&](int t) {
+    auto load_tile = [&](int t) {
         int xs, ys;
         origin(t, xs, ys);
         tma_box(phi_dst, &phi_map, xs - 4, ys, bar_phi, kPhiBytes);
-    };
-    auto load_dat = [&](int t) {
-        int xs, ys;
-        origin(t, xs, ys);
         tma_box(dat_dst, &data_map, xs, ys + 1, bar_dat, kDatBytes);
     };
 
     int t = blockIdx.x;
-    if (tid == 0 && t < n_tiles) {
-        load_phi(t);
-        load_dat(t);
-    }
+    if (tid == 0 && t < n_tiles) load_tile(t);
     uint32_t par = 0;
     bool failed = false;
 
@@ -191,6 +202,7 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
     int nflip = 0;
     double dsw = 0.0, dsa = 0.0;
     const bool lane_out = lane >= HL && lane < 32 - HL;
+    const int eidx = lane == 0 ? 3 : 132;        // phi column beyond the warp's edge
 
     for (; t < n_tiles; t += gridDim.x) {
         int xs, ys;
@@ -200,95 +212,108 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
             failed = true;
             break;
         }
-        // ghost columns for a binary phi on the image's left/right edge
-        const bool ghost_l = xs <= 0;
-        const bool ghost_r = xs <= W - 1 && W - 1 < xs + 128;
-        if (BIN && (ghost_l || ghost_r)) {
-            for (int rr = tid; rr < G::PHI_ROWS; rr += kThreads) {
-                float *row = phi_s + rr * kPhiW;
-                if (ghost_l) {
+        if (FAST && (xs <= 0 || xs + 128 > W - 1)) {
+            // ghost columns 2 phi(0) - phi(1) and 2 phi(W-1) - phi(W-2)
+            const bool gl = xs <= 0, gr = xs <= W - 1 && W - 1 < xs + 128;
+            for (int rr = tid; rr < kPhiRows; rr += kThreads) {
+                float *row = buf + rr * kPhiW;
+                if (gl) {
                     const float f0 = row[4 - xs];
                     const float f1 = W > 1 ? row[5 - xs] : f0;
                     row[3 - xs] = 2.0f * f0 - f1;
                 }
-                if (ghost_r) {
+                if (gr) {
                     const float fe = row[W + 3 - xs];
                     const float fd = W > 1 ? row[W + 2 - xs] : fe;
                     row[W + 4 - xs] = 2.0f * fe - fd;
                 }
             }
-            // the buffer is refilled by TMA later: order these writes first
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
         }
-        // per-column masks of this lane
-        float inf[4];
+        const bool xborder = xs < 0 || xs + 128 > W;
+        float inb[4], okf[4];
         bool oneL[4], oneR[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int x = x0 + j;
-            inf[j] = (x >= 0 && x < W) ? 1.0f : 0.0f;
+            inb[j] = (x >= 0 && x < W) ? 1.0f : 0.0f;
+            okf[j] = (lane_out && x < W) ? 1.0f : 0.0f;
             oneL[j] = x == 0;
             oneR[j] = x == W - 1;
         }
-        const bool xborder = xs < 0 || xs + 128 > W;
 
-        // ---- u and horizontal pass: warp w takes u-rows w, w + 8, ...
+        // ---- u pass: u rows ur0 .. ur0 + 7 (centre phi row = slot ur + 1)
+        const int ur0 = warp * kURowsPerWarp;
+        const float *bl = buf + 4 + 4 * lane;
+        float4 pm = lds4(bl + ur0 * kPhiW);
+        float4 pc = lds4(bl + (ur0 + 1) * kPhiW);
+        float ec = buf[(ur0 + 1) * kPhiW + eidx];
+        if (binarise_in) {
+            pm = bin4(pm);
+            pc = bin4(pc);
+            ec = bin(ec);
+        }
+        __syncthreads();   // rows 8w and 8w + 1 are in registers before warp w - 1 overwrites them
 #pragma unroll 2
-        for (int ur = warp; ur < kURows; ur += kWarps) {
+        for (int i = 0; i < kURowsPerWarp; ++i) {
+            const int ur = ur0 + i;
             const int y = ys + 1 + ur;
-            const float *pr = phi_s + ur * kPhiW;      // rows y-1, y, y+1
-            float4 m4 = *reinterpret_cast<const float4 *>(pr + 4 + 4 * lane);
-            float4 c4 = *reinterpret_cast<const float4 *>(pr + kPhiW + 4 + 4 * lane);
-            float4 p4 = *reinterpret_cast<const float4 *>(pr + 2 * kPhiW + 4 + 4 * lane);
-            float e = pr[kPhiW + (lane == 0 ? 3 : 132)];
+            float4 pp = lds4(bl + (ur + 2) * kPhiW);
+            float ep = buf[(ur + 2) * kPhiW + eidx];
+            const float4 d4 = lds4(dat + ur * kDataW + 4 * lane);
             if (binarise_in) {
-                m4 = make_float4(bin(m4.x), bin(m4.y), bin(m4.z), bin(m4.w));
-                c4 = make_float4(bin(c4.x), bin(c4.y), bin(c4.z), bin(c4.w));
-                p4 = make_float4(bin(p4.x), bin(p4.y), bin(p4.z), bin(p4.w));
-                e = bin(e);
+                pp = bin4(pp);
+                ep = bin(ep);
             }
-            float lft = __shfl_up_sync(0xffffffffu, c4.w, 1);
-            float rgt = __shfl_down_sync(0xffffffffu, c4.x, 1);
-            if (lane == 0) lft = e;
-            if (lane == 31) rgt = e;
-            float pm[4] = {m4.x, m4.y, m4.z, m4.w};
-            float pp[4] = {p4.x, p4.y, p4.z, p4.w};
-            const float c[6] = {lft, c4.x, c4.y, c4.z, c4.w, rgt};
+            if (count_flips) {
+                // old signs of this row for the sign-change count
+                const uint32_t s0 = __ballot_sync(0xffffffffu, pc.x >= 0.0f);
+                const uint32_t s1 = __ballot_sync(0xffffffffu, pc.y >= 0.0f);
+                const uint32_t s2 = __ballot_sync(0xffffffffu, pc.z >= 0.0f);
+                const uint32_t s3 = __ballot_sync(0xffffffffu, pc.w >= 0.0f);
+                if (lane == 0)
+                    *reinterpret_cast<uint4 *>(sign_w + 4 * ur) = make_uint4(s0, s1, s2, s3);
+            }
+            float lft = __shfl_up_sync(0xffffffffu, pc.w, 1);
+            float rgt = __shfl_down_sync(0xffffffffu, pc.x, 1);
+            if (lane == 0) lft = ec;
+            if (lane == 31) rgt = ec;
+            const float c[6] = {lft, pc.x, pc.y, pc.z, pc.w, rgt};
+            float up[4] = {pm.x, pm.y, pm.z, pm.w};
+            float dn[4] = {pp.x, pp.y, pp.z, pp.w};
             bool yin = true;
-            if (y <= 0 || y >= H - 1) {                 // ghost rows, rows outside
+            if (y <= 0 || y >= H - 1) {                 // ghost rows; rows outside
                 yin = y >= 0 && y < H;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (H == 1) {
-                        pm[j] = c[j + 1];
-                        pp[j] = c[j + 1];
+                        up[j] = c[j + 1];
+                        dn[j] = c[j + 1];
                     } else if (y == 0) {
-                        pm[j] = 2.f * c[j + 1] - pp[j];
+                        up[j] = 2.f * c[j + 1] - dn[j];
                     } else if (y == H - 1) {
-                        pp[j] = 2.f * c[j + 1] - pm[j];
+                        dn[j] = 2.f * c[j + 1] - up[j];
                     }
                 }
             }
-            const float4 d4 = *reinterpret_cast<const float4 *>(dat_s + ur * kDataW + 4 * lane);
             float u[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float dx = c[j + 2] - c[j];
-                if (!BIN) {
+                if (!FAST) {
                     if (W == 1) dx = 0.0f;
                     else if (oneL[j]) dx = 2.0f * (c[j + 2] - c[j + 1]);
                     else if (oneR[j]) dx = 2.0f * (c[j + 1] - c[j]);
                 }
-                const float dy = pp[j] - pm[j];
+                const float dy = dn[j] - up[j];
                 const float q = fmaf(dx, dx, dy * dy);
-                const float s2 = BIN ? lut[(__float_as_uint(q) >> 21) & 31u] : sqrtf(q);
+                const float s2 = FAST ? lut[(__float_as_uint(q) >> 21) & 31u] : sqrtf(q);
                 const float tj = EDGE ? coef * comp(d4, j) : coef * (comp(d4, j) - mid);
                 u[j] = fmaf(tj, s2, c[j + 1]);
             }
             if (xborder) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) u[j] *= inf[j];
+                for (int j = 0; j < 4; ++j) u[j] *= inb[j];
             }
             if (!yin) {
 #pragma unroll
@@ -316,88 +341,89 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
                     h = fmaf(tp[q], U[4 * HL + j - q] + U[4 * HL + j + q], h);
                 hv[j] = h;
             }
-            *reinterpret_cast<float4 *>(h_s + ur * kDataW + 4 * lane) =
+            // h of u row ur replaces phi slot ur + 2, read above by this warp
+            *reinterpret_cast<float4 *>(buf + (ur + 2) * kPhiW + 4 + 4 * lane) =
                 make_float4(hv[0], hv[1], hv[2], hv[3]);
+            pm = pc;
+            pc = pp;
+            ec = ep;
         }
+        // the buffer is refilled by TMA after the vertical pass
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        // the phi buffer is free (unless flips read it below): fetch the next tile's
-        const int tn = t + gridDim.x;
-        if (!count_flips && tid == 0 && tn < n_tiles) load_phi(tn);
 
-        // ---- vertical pass: warp w takes output rows w*RPW .. +RPW-1
+        // ---- vertical pass: output rows r_first .. r_first + RPW - 1
         {
-            constexpr int RPW = G::ROWS_PER_WARP;
-            const int r_first = warp * RPW;              // output row within the tile
-            float win[P + RPW - 1][4];
-#pragma unroll
-            for (int i = 0; i < P + RPW - 1; ++i) {
-                const int hr = r_first + i;               // h row (u-row index)
+            const int r_first = warp * RPW;
+            float rg[P][4];
+            auto ldh = [&](int hr, float *dst) {
                 if (hr < kURows) {
-                    const float4 h4 = *reinterpret_cast<const float4 *>(h_s + hr * kDataW + 4 * lane);
-                    win[i][0] = h4.x;
-                    win[i][1] = h4.y;
-                    win[i][2] = h4.z;
-                    win[i][3] = h4.w;
+                    const float4 h4 = lds4(bl + (hr + 2) * kPhiW);
+                    dst[0] = h4.x;
+                    dst[1] = h4.y;
+                    dst[2] = h4.z;
+                    dst[3] = h4.w;
                 } else {
-                    win[i][0] = win[i][1] = win[i][2] = win[i][3] = 0.0f;
+                    dst[0] = dst[1] = dst[2] = dst[3] = 0.0f;
                 }
-            }
+            };
+#pragma unroll
+            for (int i = 0; i < P - 1; ++i) ldh(r_first + i, rg[i]);
             float fsw = 0.0f, fsa = 0.0f, fcnt = 0.0f;
 #pragma unroll
             for (int k = 0; k < RPW; ++k) {
+                ldh(r_first + k + P - 1, rg[(k + P - 1) % P]);
                 const int ro = r_first + k;
                 const int yo = ys + RAD + 1 + ro;
-                if (ro >= TH || yo >= H) continue;
-                float v[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float acc = tp[0] * win[k + RAD][j];
-#pragma unroll
-                    for (int q = 1; q <= RAD; ++q)
-                        acc = fmaf(tp[q], win[k + RAD - q][j] + win[k + RAD + q][j], acc);
-                    v[j] = acc;
-                }
-                float w[4], okf[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    w[j] = v[j] >= 0.0f ? 1.0f : -1.0f;
-                    okf[j] = (lane_out && x0 + j < W) ? 1.0f : 0.0f;
-                }
-                float *dst = a.phi_out + (size_t)yo * a.pitch + x0;
-                const float s0 = store_bin ? w[0] : v[0], s1 = store_bin ? w[1] : v[1];
-                const float s2 = store_bin ? w[2] : v[2], s3 = store_bin ? w[3] : v[3];
-                if (lane_out) {
-                    if (x0 + 3 < W) {
-                        *reinterpret_cast<float4 *>(dst) = make_float4(s0, s1, s2, s3);
-                    } else {
-                        const float sv[4] = {s0, s1, s2, s3};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (x0 + j < W) dst[j] = sv[j];
-                    }
-                }
-                if (count_flips) {
-                    const float4 o4 = *reinterpret_cast<const float4 *>(
-                        phi_s + (ro + RAD + 1) * kPhiW + 4 + 4 * lane);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        nflip += (okf[j] != 0.0f) && ((w[j] > 0.0f) != (comp(o4, j) >= 0.0f));
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) fcnt = fmaf(w[j], okf[j], fcnt);
-                if (!EDGE) {
-                    const float4 d4 = *reinterpret_cast<const float4 *>(
-                        dat_s + (ro + RAD) * kDataW + 4 * lane);
+                if (ro < TH && yo < H) {
+                    float v[4], w[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const float d = comp(d4, j) * okf[j];
-                        fsw = fmaf(d, w[j], fsw);
-                        fsa += d;
+                        float acc = tp[0] * rg[(k + RAD) % P][j];
+#pragma unroll
+                        for (int q = 1; q <= RAD; ++q)
+                            acc = fmaf(tp[q], rg[(k + RAD - q) % P][j] + rg[(k + RAD + q) % P][j],
+                                       acc);
+                        v[j] = acc;
+                        w[j] = acc >= 0.0f ? 1.0f : -1.0f;
+                    }
+                    float *dst = a.phi_out + (size_t)yo * a.pitch + x0;
+                    float sv[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) sv[j] = store_bin ? w[j] : v[j];
+                    if (lane_out) {
+                        if (x0 + 3 < W) {
+                            *reinterpret_cast<float4 *>(dst) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                if (x0 + j < W) dst[j] = sv[j];
+                        }
+                    }
+                    if (count_flips) {
+                        const uint4 sw = *reinterpret_cast<const uint4 *>(sign_w + 4 * (ro + RAD));
+                        const uint32_t wd[4] = {sw.x, sw.y, sw.z, sw.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            nflip += (okf[j] != 0.0f) && ((w[j] > 0.0f) != (((wd[j] >> lane) & 1u) != 0));
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) fcnt = fmaf(w[j], okf[j], fcnt);
+                    if (!EDGE) {
+                        // outside the image the staged data is zero; halo lanes drop their sums below
+                        const float4 d4 = lds4(dat + (ro + RAD) * kDataW + 4 * lane);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            fsw = fmaf(comp(d4, j), w[j], fsw);
+                            fsa += comp(d4, j);
+                        }
                     }
                 }
             }
-            dsw += (double)fsw;
-            dsa += (double)fsa;
+            if (!EDGE && lane_out) {
+                dsw += (double)fsw;
+                dsa += (double)fsa;
+            }
             // valid output pixels of this lane in this tile
             int rows = TH;
             if (ys + RAD + 1 + TH > H) rows = H - (ys + RAD + 1);
@@ -405,14 +431,12 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
             rv = rv < 0 ? 0 : (rv > RPW ? RPW : rv);
             int cv = 0;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) cv += (lane_out && x0 + j < W) ? 1 : 0;
+            for (int j = 0; j < 4; ++j) cv += okf[j] != 0.0f ? 1 : 0;
             cnt2 += (long long)fcnt + (long long)cv * rv;
         }
         __syncthreads();
-        if (tid == 0 && tn < n_tiles) {
-            if (count_flips) load_phi(tn);
-            load_dat(tn);
-        }
+        const int tn = t + gridDim.x;
+        if (tid == 0 && tn < n_tiles) load_tile(tn);
         par ^= 1u;
     }
     if (failed) {
@@ -437,13 +461,19 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
     if (threadIdx.x == 0) lse_step_finalize(a, tot);
 }
 
+// FAST: the steady state of a re-initialising evolution.
+__host__ __device__ inline bool is_fast(const StepArgs &a)
+{
+    return a.binary_in && a.store_bin && !a.count_flips && !a.binarise_in;
+}
+
 template <int KIND_EDGE, int RAD>
 cudaError_t launch_tile_one(const StepArgs &a, const CUtensorMap &pm, const CUtensorMap &dm,
                             int nblocks, cudaStream_t s)
 {
     using G = TileGeo<RAD>;
-    auto kern = a.binary_in ? step_tile_kernel<KIND_EDGE, RAD, true>
-                            : step_tile_kernel<KIND_EDGE, RAD, false>;
+    auto kern = is_fast(a) ? step_tile_kernel<KIND_EDGE, RAD, true>
+                           : step_tile_kernel<KIND_EDGE, RAD, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          G::BYTES);
     if (e != cudaSuccess) return e;
@@ -466,5 +496,8 @@ cudaError_t launch_tile_kind(const StepArgs &a, const CUtensorMap &pm, const CUt
     default: return cudaErrorNotSupported;
     }
 }
+
+// CTAs per SM the tile form runs at for a radius (its launch bounds).
+inline int tile_blocks_per_sm(int rad) { return rad <= 4 ? 3 : 2; }
 
 }  // namespace lse_tile

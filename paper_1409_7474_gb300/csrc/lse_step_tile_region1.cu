@@ -10,4 +10,6 @@ cudaError_t launch_step_tile_region1(const StepArgs &a, const CUtensorMap &pm,
     return lse_tile::launch_tile_kind<0>(a, pm, dm, nblocks, s);
 }
 
+int step_tile_blocks_per_sm(int rad) { return lse_tile::tile_blocks_per_sm(rad); }
+
 }  // namespace lse_detail

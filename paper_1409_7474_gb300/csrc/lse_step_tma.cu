@@ -19,6 +19,7 @@ cudaError_t launch_step_tile_region1(const StepArgs &, const CUtensorMap &,
                                      const CUtensorMap &, int, cudaStream_t);
 cudaError_t launch_step_tile_edge(const StepArgs &, const CUtensorMap &,
                                   const CUtensorMap &, int, cudaStream_t);
+int step_tile_blocks_per_sm(int rad);
 
 }  // namespace lse_detail
 
@@ -91,7 +92,7 @@ cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap &phi_map,
 }
 
 // Tile form: tiles of (64 - 2 rad) output rows x (128 - 8 ceil(rad / 4))
-// output columns, walked by up to 2 CTAs per SM.
+// output columns, walked by as many CTAs as fit on the SMs at once.
 bool plan_step_tile(int H, int W, int B, int term, int rad, int sm_count,
                     StepArgs *a, int *nblocks)
 {
@@ -108,7 +109,8 @@ bool plan_step_tile(int H, int W, int B, int term, int rad, int sm_count,
     a->th = th;
     a->n_items = tiles_x * tiles_y;
     int blocks = a->n_items;
-    if (blocks > sm_count * 2) blocks = sm_count * 2;
+    const int resident = sm_count * step_tile_blocks_per_sm(rad);
+    if (blocks > resident) blocks = resident;
     *nblocks = blocks;
     return true;
 }
