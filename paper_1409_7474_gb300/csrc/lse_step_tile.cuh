@@ -37,6 +37,8 @@
 // and ends the CTA's tile loop; the CTA still takes part in the reduction.
 #pragma once
 
+#include <type_traits>
+
 #include "lse_reduce.cuh"
 
 namespace lse_tile {
@@ -177,6 +179,7 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
     for (int k = 0; k <= RAD; ++k) tp[k] = a.taps[k];
     const float coef = EDGE ? a.half_dt : st->a[0];
     const float mid = EDGE ? 0.0f : st->m[0];
+    const float sqrt8 = sqrtf(8.0f);
     const bool binarise_in = !FAST && a.binarise_in != 0;
     const bool count_flips = !FAST && a.count_flips != 0;
     const bool store_bin = FAST || a.store_bin != 0;
@@ -203,6 +206,8 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
     double dsw = 0.0, dsa = 0.0;
     const bool lane_out = lane >= HL && lane < 32 - HL;
     const int eidx = lane == 0 ? 3 : 132;        // phi column beyond the warp's edge
+    const float *bl = buf + 4 + 4 * lane;        // this lane's 4 columns of a phi / h slot
+    const float *dl = dat + 4 * lane;
 
     for (; t < n_tiles; t += gridDim.x) {
         int xs, ys;
@@ -212,7 +217,11 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
             failed = true;
             break;
         }
-        if (FAST && (xs <= 0 || xs + 128 > W - 1)) {
+        // tiles that touch column 0 or W - 1 (or lie partly outside) take the
+        // border code; so do tiles whose u rows reach row 0 or H - 1
+        const bool xborder = xs < 0 || xs + 128 >= W;
+        const bool interior = !xborder && ys >= 0 && ys + kPhiRows <= H;
+        if (FAST && xborder) {
             // ghost columns 2 phi(0) - phi(1) and 2 phi(W-1) - phi(W-2)
             const bool gl = xs <= 0, gr = xs <= W - 1 && W - 1 < xs + 128;
             for (int rr = tid; rr < kPhiRows; rr += kThreads) {
@@ -230,7 +239,6 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
             }
             __syncthreads();
         }
-        const bool xborder = xs < 0 || xs + 128 > W;
         float inb[4], okf[4];
         bool oneL[4], oneR[4];
 #pragma unroll
@@ -244,7 +252,6 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
 
         // ---- u pass: u rows ur0 .. ur0 + 7 (centre phi row = slot ur + 1)
         const int ur0 = warp * kURowsPerWarp;
-        const float *bl = buf + 4 + 4 * lane;
         float4 pm = lds4(bl + ur0 * kPhiW);
         float4 pc = lds4(bl + (ur0 + 1) * kPhiW);
         float ec = buf[(ur0 + 1) * kPhiW + eidx];
@@ -254,13 +261,15 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
             ec = bin(ec);
         }
         __syncthreads();   // rows 8w and 8w + 1 are in registers before warp w - 1 overwrites them
-#pragma unroll 2
-        for (int i = 0; i < kURowsPerWarp; ++i) {
-            const int ur = ur0 + i;
-            const int y = ys + 1 + ur;
+
+        // One u row: u (Eq. 18) on the lane's 4 columns, the horizontal
+        // Gaussian pass, h stored over the phi slot just read.  IN: interior
+        // tile (no ghost rows, no columns outside the image or on its edge).
+        auto urow = [&](auto in_tag, int ur) {
+            constexpr bool IN = decltype(in_tag)::value;
             float4 pp = lds4(bl + (ur + 2) * kPhiW);
             float ep = buf[(ur + 2) * kPhiW + eidx];
-            const float4 d4 = lds4(dat + ur * kDataW + 4 * lane);
+            const float4 d4 = lds4(dl + ur * kDataW);
             if (binarise_in) {
                 pp = bin4(pp);
                 ep = bin(ep);
@@ -282,17 +291,20 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
             float up[4] = {pm.x, pm.y, pm.z, pm.w};
             float dn[4] = {pp.x, pp.y, pp.z, pp.w};
             bool yin = true;
-            if (y <= 0 || y >= H - 1) {                 // ghost rows; rows outside
-                yin = y >= 0 && y < H;
+            if (!IN) {
+                const int y = ys + 1 + ur;
+                if (y <= 0 || y >= H - 1) {             // ghost rows; rows outside
+                    yin = y >= 0 && y < H;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (H == 1) {
-                        up[j] = c[j + 1];
-                        dn[j] = c[j + 1];
-                    } else if (y == 0) {
-                        up[j] = 2.f * c[j + 1] - dn[j];
-                    } else if (y == H - 1) {
-                        dn[j] = 2.f * c[j + 1] - up[j];
+                    for (int j = 0; j < 4; ++j) {
+                        if (H == 1) {
+                            up[j] = c[j + 1];
+                            dn[j] = c[j + 1];
+                        } else if (y == 0) {
+                            up[j] = 2.f * c[j + 1] - dn[j];
+                        } else if (y == H - 1) {
+                            dn[j] = 2.f * c[j + 1] - up[j];
+                        }
                     }
                 }
             }
@@ -300,24 +312,30 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float dx = c[j + 2] - c[j];
-                if (!FAST) {
+                if (!FAST && !IN) {
                     if (W == 1) dx = 0.0f;
                     else if (oneL[j]) dx = 2.0f * (c[j + 2] - c[j + 1]);
                     else if (oneR[j]) dx = 2.0f * (c[j + 1] - c[j]);
                 }
                 const float dy = dn[j] - up[j];
                 const float q = fmaf(dx, dx, dy * dy);
-                const float s2 = FAST ? lut[(__float_as_uint(q) >> 21) & 31u] : sqrtf(q);
+                // +-1 phi off the image border: q is 0, 4 or 8, and sqrt(q) is
+                // q / 2 (exact) or sqrt(8)
+                const float s2 = !FAST ? sqrtf(q)
+                               : IN ? (q == 8.0f ? sqrt8 : 0.5f * q)
+                                    : lut[(__float_as_uint(q) >> 21) & 31u];
                 const float tj = EDGE ? coef * comp(d4, j) : coef * (comp(d4, j) - mid);
                 u[j] = fmaf(tj, s2, c[j + 1]);
             }
-            if (xborder) {
+            if (!IN) {
+                if (xborder) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) u[j] *= inb[j];
-            }
-            if (!yin) {
+                    for (int j = 0; j < 4; ++j) u[j] *= inb[j];
+                }
+                if (!yin) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) u[j] = 0.0f;
+                    for (int j = 0; j < 4; ++j) u[j] = 0.0f;
+                }
             }
             float U[4 + 8 * HL];
 #pragma unroll
@@ -342,11 +360,18 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
                 hv[j] = h;
             }
             // h of u row ur replaces phi slot ur + 2, read above by this warp
-            *reinterpret_cast<float4 *>(buf + (ur + 2) * kPhiW + 4 + 4 * lane) =
+            *reinterpret_cast<float4 *>(const_cast<float *>(bl) + (ur + 2) * kPhiW) =
                 make_float4(hv[0], hv[1], hv[2], hv[3]);
             pm = pc;
             pc = pp;
             ec = ep;
+        };
+        if (interior) {
+#pragma unroll
+            for (int i = 0; i < kURowsPerWarp; ++i) urow(std::true_type{}, ur0 + i);
+        } else {
+#pragma unroll 2
+            for (int i = 0; i < kURowsPerWarp; ++i) urow(std::false_type{}, ur0 + i);
         }
         // the buffer is refilled by TMA after the vertical pass
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -355,80 +380,84 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
         // ---- vertical pass: output rows r_first .. r_first + RPW - 1
         {
             const int r_first = warp * RPW;
+            int rows = H - (ys + RAD + 1);               // valid output rows of the tile
+            rows = rows < TH ? rows : TH;
+            int rv = rows - r_first;
+            rv = rv < 0 ? 0 : (rv > RPW ? RPW : rv);
+            // x0 + 4 <= pitch whenever x0 < W (x0 and the pitch are multiples
+            // of 4): the lane stores all 4 columns, the padding is scratch
+            const bool st_ok = lane_out && x0 < W;
+            float *dst = a.phi_out + (size_t)(ys + RAD + 1 + r_first) * a.pitch + x0;
+            const size_t pitch = (size_t)a.pitch;
             float rg[P][4];
-            auto ldh = [&](int hr, float *dst) {
-                if (hr < kURows) {
-                    const float4 h4 = lds4(bl + (hr + 2) * kPhiW);
-                    dst[0] = h4.x;
-                    dst[1] = h4.y;
-                    dst[2] = h4.z;
-                    dst[3] = h4.w;
-                } else {
-                    dst[0] = dst[1] = dst[2] = dst[3] = 0.0f;
-                }
+            // h rows past the tile read other shared memory (finite values);
+            // their outputs are never used
+            auto ldh = [&](int hr, float *d) {
+                const float4 h4 = lds4(bl + (hr + 2) * kPhiW);
+                d[0] = h4.x;
+                d[1] = h4.y;
+                d[2] = h4.z;
+                d[3] = h4.w;
             };
-#pragma unroll
-            for (int i = 0; i < P - 1; ++i) ldh(r_first + i, rg[i]);
             float fsw = 0.0f, fsa = 0.0f, fcnt = 0.0f;
+            auto vrows = [&](auto full_tag) {
+                constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
-            for (int k = 0; k < RPW; ++k) {
-                ldh(r_first + k + P - 1, rg[(k + P - 1) % P]);
-                const int ro = r_first + k;
-                const int yo = ys + RAD + 1 + ro;
-                if (ro < TH && yo < H) {
-                    float v[4], w[4];
+                for (int i = 0; i < P - 1; ++i) ldh(r_first + i, rg[i]);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        float acc = tp[0] * rg[(k + RAD) % P][j];
-#pragma unroll
-                        for (int q = 1; q <= RAD; ++q)
-                            acc = fmaf(tp[q], rg[(k + RAD - q) % P][j] + rg[(k + RAD + q) % P][j],
-                                       acc);
-                        v[j] = acc;
-                        w[j] = acc >= 0.0f ? 1.0f : -1.0f;
-                    }
-                    float *dst = a.phi_out + (size_t)yo * a.pitch + x0;
-                    float sv[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) sv[j] = store_bin ? w[j] : v[j];
-                    if (lane_out) {
-                        if (x0 + 3 < W) {
-                            *reinterpret_cast<float4 *>(dst) = make_float4(sv[0], sv[1], sv[2], sv[3]);
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 4; ++j)
-                                if (x0 + j < W) dst[j] = sv[j];
-                        }
-                    }
-                    if (count_flips) {
-                        const uint4 sw = *reinterpret_cast<const uint4 *>(sign_w + 4 * (ro + RAD));
-                        const uint32_t wd[4] = {sw.x, sw.y, sw.z, sw.w};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            nflip += (okf[j] != 0.0f) && ((w[j] > 0.0f) != (((wd[j] >> lane) & 1u) != 0));
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) fcnt = fmaf(w[j], okf[j], fcnt);
-                    if (!EDGE) {
-                        // outside the image the staged data is zero; halo lanes drop their sums below
-                        const float4 d4 = lds4(dat + (ro + RAD) * kDataW + 4 * lane);
+                for (int k = 0; k < RPW; ++k) {
+                    ldh(r_first + k + P - 1, rg[(k + P - 1) % P]);
+                    const int ro = r_first + k;
+                    if (FULL || k < rv) {
+                        float v[4], w[4];
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            fsw = fmaf(comp(d4, j), w[j], fsw);
-                            fsa += comp(d4, j);
+                            float acc = tp[0] * rg[(k + RAD) % P][j];
+#pragma unroll
+                            for (int q = 1; q <= RAD; ++q)
+                                acc = fmaf(tp[q],
+                                           rg[(k + RAD - q) % P][j] + rg[(k + RAD + q) % P][j],
+                                           acc);
+                            v[j] = acc;
+                            w[j] = acc >= 0.0f ? 1.0f : -1.0f;
+                        }
+                        if (st_ok) {
+                            float4 sv = store_bin ? make_float4(w[0], w[1], w[2], w[3])
+                                                  : make_float4(v[0], v[1], v[2], v[3]);
+                            *reinterpret_cast<float4 *>(dst + k * pitch) = sv;
+                        }
+                        if (count_flips) {
+                            const uint4 sw =
+                                *reinterpret_cast<const uint4 *>(sign_w + 4 * (ro + RAD));
+                            const uint32_t wd[4] = {sw.x, sw.y, sw.z, sw.w};
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                nflip += (okf[j] != 0.0f) &&
+                                         ((w[j] > 0.0f) != (((wd[j] >> lane) & 1u) != 0));
+                        }
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) fcnt = fmaf(w[j], okf[j], fcnt);
+                        if (!EDGE) {
+                            // outside the image the staged data is zero; halo
+                            // lanes drop their sums below
+                            const float4 d4 = lds4(dl + (ro + RAD) * kDataW);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                fsw = fmaf(comp(d4, j), w[j], fsw);
+                                fsa += comp(d4, j);
+                            }
                         }
                     }
                 }
-            }
+            };
+            if (rv == RPW)
+                vrows(std::true_type{});
+            else
+                vrows(std::false_type{});
             if (!EDGE && lane_out) {
                 dsw += (double)fsw;
                 dsa += (double)fsa;
             }
-            // valid output pixels of this lane in this tile
-            int rows = TH;
-            if (ys + RAD + 1 + TH > H) rows = H - (ys + RAD + 1);
-            int rv = rows - r_first;
-            rv = rv < 0 ? 0 : (rv > RPW ? RPW : rv);
             int cv = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) cv += okf[j] != 0.0f ? 1 : 0;
