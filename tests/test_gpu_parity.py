@@ -66,9 +66,9 @@ def rng_scene(B, H, W, seed):
     return img.astype(np.float32)
 
 
-# ---------------------------------------------------------------- config 1
+# ------------------------------------------------ 256 x 256 rectangle scene
 @pytest.mark.parametrize("sigma", [1.0, 3.0])
-def test_config1_one_step(torch, ctx, sigma):
+def test_rectangle_256_one_step(torch, ctx, sigma):
     img, truth, _ = scenes.rect_scene()
     phi0 = scenes.circle_phi(256, 256)
     v, m, st = gpu_evolve(torch, ctx, img, phi0, dt=15.0, sigma=sigma, ts=9, iterations=1)
@@ -83,7 +83,7 @@ def test_config1_one_step(torch, ctx, sigma):
 
 
 @pytest.mark.parametrize("sigma", [1.0, 3.0])
-def test_config1_200_iterations(torch, ctx, sigma):
+def test_rectangle_256_200_iterations(torch, ctx, sigma):
     img, truth, _ = scenes.rect_scene()
     phi0 = scenes.circle_phi(256, 256)
     v, m, st = gpu_evolve(torch, ctx, img, phi0, dt=15.0, sigma=sigma, ts=9, iterations=200)
@@ -315,7 +315,7 @@ def scene2048():
     return scenes.multiband_scene(2048, 2048, 4, seed=7)
 
 
-def test_config2_region_vector_term(torch, ctx, scene2048):
+def test_multiband_2048_region_vector_term(torch, ctx, scene2048):
     u16 = scene2048["image"]
     img = u16.astype(np.float32) / np.float32(65535.0)
     phi0 = scenes.circle_phi(2048, 2048, radius=512)
@@ -330,7 +330,7 @@ def test_config2_region_vector_term(torch, ctx, scene2048):
     assert_mask_parity(m.cpu().numpy(), m_ref)
 
 
-def test_config2_edge_term(torch, ctx, scene2048):
+def test_multiband_2048_edge_term(torch, ctx, scene2048):
     u16 = scene2048["image"]
     img = u16.astype(np.float32) / np.float32(65535.0)
     y0, x0, y1, x1 = scene2048["runway_box"]
