@@ -14,7 +14,9 @@ Reported (one JSON line on rank 0):
   roofline     the fused region step kernel: algorithmic bytes per launch
                (12 B/px: read I, read phi, write v) / its mean duration from
                CUDA events on the library's stream, against measured HBM;
-  cpu_baseline the FP64 oracle on the host cores, on crops of the same scene.
+  cpu_baseline the FP64 oracle on the host cores, on crops of the same scene;
+  storage_variants  the same workload with BF16 and F16 storage of the data
+               term and the LSF (FP32 arithmetic, 6 B/px per region step).
 `--impl reference` times the FP64 oracle alone (the reference arm).
 Under torchrun each rank runs its own replica (no collective on the data
 path): weak scaling.
@@ -56,6 +58,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the 16-bit storage variants")
     return ap.parse_args()
 
 
@@ -356,6 +360,46 @@ def main():
                # v + mask (region), g, v + mask (edge)
                "d2h_bytes_per_step": 3 * plane + 2 * npx}
 
+    # the same workload with 16-bit storage of the data term and the LSF
+    # (FP32 arithmetic): 6 bytes per pixel-iteration of the region step
+    variants = None
+    if not args.no_variants:
+        variants = {}
+        for sto in ("bf16", "f16"):
+            vcommon = dict(common, storage=sto)
+
+            def vstep():
+                ctx_r.evolve(x, pr, "region", phi_out=out_r, mask_out=mask_r, **vcommon)
+                ctx_e.precompute_edge(x, 1.0, 9, 255.0, out=g)
+                ctx_e.evolve(None, pe, "edge", g=g, phi_out=out_e, mask_out=mask_e, **vcommon)
+
+            vstep()
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            v_ms_r, v_ms_e = [], []
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            for _ in range(args.steps):
+                vstep()
+                torch.cuda.synchronize()
+                v_ms_r.append(ctx_r.stats()["elapsed_ms"])
+                v_ms_e.append(ctx_e.stats()["elapsed_ms"])
+            q1.record(stream)
+            torch.cuda.synchronize()
+            vms = max_over_ranks(q0.elapsed_time(q1), world, dev)
+            kms = statistics.mean(v_ms_r) / iters
+            vbytes = 6 * npx
+            variants[sto] = {
+                "value": world * px_iters_per_step * args.steps / (vms / 1e3) / 1e6,
+                "ms_per_step": vms / args.steps,
+                "region_step_ms": kms,
+                "bytes_per_launch": vbytes,
+                "frac": vbytes / (kms / 1e3) / 1e9 / peak,
+                "edge_step_frac": vbytes / (statistics.mean(v_ms_e) / iters / 1e3) / 1e9 / peak,
+                "status": [ctx_r.stats()["status"], ctx_e.stats()["status"]]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_throughput(img, phi_r, phi_e, seconds=args.cpu_seconds)
@@ -374,6 +418,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks.summary(), "gpu_launches": launches,
+                "storage_variants": variants,
                 "impl": "gb300",
                 "stats": {"region": {k: st_r[k] for k in ("iterations_run", "status",
                                                           "last_flips", "area_plus")},

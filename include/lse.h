@@ -91,7 +91,18 @@ typedef enum {
  *   early_stop_frac 0 disables.  Otherwise the evolution stops after the first
  *                   iteration in which fewer than early_stop_frac * H * W pixels
  *                   changed sign (Step 5: stop when phi stops varying).
- *   storage         LSE_F32 (the only storage type this version accepts).
+ *   storage         type of the work planes in HBM: LSE_F32, or LSE_F16 /
+ *                   LSE_BF16 for one band (or the edge term) with ts <= 15.
+ *                   16-bit storage rounds the data term (I or g) to the type
+ *                   once (round to nearest even) and keeps the LSF between
+ *                   iterations in it; arithmetic stays FP32 and the region
+ *                   sums FP64.  A re-initialised LSF is +-1, which the 16-bit
+ *                   types hold exactly, so with reinit_period = 1 the only
+ *                   rounding is the data term's and that of the final v
+ *                   (returned as FP32 after rounding to the type).  Other
+ *                   storage values, or 16-bit storage outside those cases,
+ *                   give LSE_ERR_INVALID_ARG.  Not an equation of the paper,
+ *                   whose own runs are FP64 (Sec. IV-A).
  * Region-term degenerate rule (the paper is silent): when phi >= 0 holds
  * nowhere or everywhere, when max_b |c+_b - c-_b| <= 1e-6 * max_b(|c+_b| +
  * |c-_b|), or when max|D| = 0, that iteration uses R = 0 and the call ends

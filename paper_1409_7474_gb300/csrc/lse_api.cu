@@ -36,6 +36,8 @@ struct lse_ctx {
     size_t phi0_cap = 0;
     float *g_st = nullptr;
     size_t g_st_cap = 0;
+    uint16_t *q16 = nullptr;         // data term as F16 / BF16 (16-bit storage)
+    size_t q16_cap = 0;
     float *out_phi = nullptr;
     size_t out_cap = 0;
     uint8_t *out_mask = nullptr;
@@ -244,7 +246,7 @@ void lse_destroy(lse_ctx *ctx)
     if (!ctx) return;
     DeviceGuard g(ctx->device);
     void *bufs[] = {ctx->phi[0], ctx->phi[1], ctx->img, ctx->gbuf, ctx->raw_in,
-                    ctx->phi0_st, ctx->g_st, ctx->out_phi, ctx->out_mask,
+                    ctx->phi0_st, ctx->g_st, ctx->out_phi, ctx->out_mask, ctx->q16,
                     ctx->partials, ctx->st};
     for (void *p : bufs)
         if (p) cudaFree(p);
@@ -427,9 +429,12 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
         set_err(ctx, "early_stop_frac must be in [0, 1)");
         return LSE_ERR_INVALID_ARG;
     }
-    if (p.storage != LSE_F32) {
-        set_err(ctx, "storage %d is not supported by this version (use LSE_F32)",
-                (int)p.storage);
+    if (p.storage != LSE_F32 && p.storage != LSE_F16 && p.storage != LSE_BF16) {
+        set_err(ctx, "storage must be LSE_F32, LSE_F16 or LSE_BF16 (got %d)", (int)p.storage);
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (p.storage != LSE_F32 && ((p.term == LSE_TERM_REGION && B != 1) || p.ts > 15)) {
+        set_err(ctx, "16-bit storage needs one band (or the edge term) and ts <= 15");
         return LSE_ERR_INVALID_ARG;
     }
     if (p.term == LSE_TERM_EDGE && p.reinit_period != 1) {
@@ -486,6 +491,24 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
         }
         band_stride = (size_t)H * pitch;
     }
+    // 16-bit storage: the data term becomes an F16 / BF16 plane, and the LSF
+    // planes hold the same type
+    const int sto = p.storage;
+    const void *data_s = data;
+    if (sto != LSE_F32) {
+        const int pitch16 = round_up(W, 32);
+        if ((r = ensure_t(ctx, &ctx->q16, &ctx->q16_cap, (size_t)H * pitch16, s, "16-bit data")) != LSE_OK)
+            return r;
+        const float *src = region ? data : g_src;
+        const int src_pitch = region ? pitch : g_src_pitch;
+        e = launch_quantise(src, src_pitch, H, W, ctx->q16, pitch16, sto, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "quantise");
+        data_s = ctx->q16;
+        pitch = pitch16;
+        band_stride = (size_t)H * pitch16;
+        g_src = nullptr;
+        g_dst = nullptr;
+    }
     // LSF ping-pong buffers share the data term's pitch
     if ((r = ensure_phi(ctx, (size_t)H * pitch, s)) != LSE_OK) return r;
     const float *phi0_src = phi0;
@@ -510,15 +533,20 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
     }
 
     const int nred = ctx->sm_count * 4;
-    e = launch_prologue(region ? data : nullptr, pitch, band_stride, phi0_src, g_src,
-                        g_src_pitch, ctx->phi[0], g_dst, pitch, H, W, B, p.term,
-                        p.dt, ctx->st, ctx->partials, nred, s);
+    e = launch_prologue(region ? data_s : nullptr, pitch, band_stride, phi0_src,
+                        region ? nullptr : (sto == LSE_F32 ? (const void *)g_src : data_s),
+                        sto == LSE_F32 ? g_src_pitch : pitch, ctx->phi[0], g_dst, pitch, H,
+                        W, B, p.term, p.dt, sto, ctx->st, ctx->partials, nred, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "prologue");
 
     // the step's kernel, work decomposition and tensor maps
     StepPlan plan;
-    plan_step(H, W, B, p, pitch, band_stride, data, ctx->phi, ctx->st, ctx->partials,
-              ctx->sm_count, ctx->step_form, &plan);
+    if (!plan_step(H, W, B, p, pitch, band_stride, data_s, ctx->phi, ctx->st, ctx->partials,
+                   ctx->sm_count, ctx->step_form, &plan)) {
+        set_err(ctx, "16-bit storage runs on the tile-form step only (LSE_STEP_KERNEL "
+                     "narrowed the choice, or its tensor maps could not be encoded)");
+        return LSE_ERR_INVALID_ARG;
+    }
 
     e = cudaEventRecord(ctx->ev0, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
@@ -533,7 +561,7 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
     }
     e = cudaEventRecord(ctx->ev1, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
-    e = launch_output(ctx->phi, pitch, H, W, ctx->st, out_phi, out_mask, s);
+    e = launch_output(ctx->phi, pitch, H, W, sto, ctx->st, out_phi, out_mask, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "output");
     if (ko == PTR_HOST) {
         e = cudaMemcpyAsync(phi_out, out_phi, (size_t)H * W * 4, cudaMemcpyDeviceToHost, s);

@@ -69,6 +69,7 @@ struct StepArgs {
     int store_bin;              // store sign(v) as +-1 (this step re-initialises)
     int binary_in;              // phi_in holds +-1 only (previous step stored sign(v))
     int rad;                    // (ts - 1) / 2
+    int storage;                // LSE_F32 / LSE_F16 / LSE_BF16: phi and data planes
     float taps[16];             // 1-D taps G[0..rad] (symmetric)
     float dt;                   // time step of Eq. 18
     float half_dt;              // 0.5 * dt (edge term)
@@ -119,16 +120,21 @@ namespace lse_detail {
 // cudaGetLastError() of its launch.
 cudaError_t launch_convert(const void *src, int dtype, int H, int W, int B,
                            float *dst, int pitch, cudaStream_t s);
-cudaError_t launch_prologue(const float *img, int img_pitch, size_t band_stride,
-                            const float *phi0, const float *g, int g_pitch,
-                            float *phi_dst, float *g_dst, int pitch, int H,
-                            int W, int B, int term, float dt,
+// Pitched FP32 plane -> pitched F16 / BF16 plane (16-bit storage).
+cudaError_t launch_quantise(const float *src, int src_pitch, int H, int W, void *dst,
+                            int pitch, int storage, cudaStream_t s);
+// img, g and phi_dst are planes of the storage type (LSE_F32 / LSE_F16 /
+// LSE_BF16); g_dst (FP32 storage only) receives a pitched copy of g.
+cudaError_t launch_prologue(const void *img, int img_pitch, size_t band_stride,
+                            const float *phi0, const void *g, int g_pitch,
+                            void *phi_dst, float *g_dst, int pitch, int H,
+                            int W, int B, int term, float dt, int storage,
                             LseDevState *st, LsePartial *partials, int nblocks,
                             cudaStream_t s);
 cudaError_t launch_normaliser(const float *img, int pitch, size_t band_stride,
                               int H, int W, int B, float dt, LseDevState *st,
                               LsePartial *partials, int nblocks, cudaStream_t s);
-cudaError_t launch_output(float *const *bufs, int pitch, int H, int W,
+cudaError_t launch_output(float *const *bufs, int pitch, int H, int W, int storage,
                           const LseDevState *st, float *phi_out,
                           uint8_t *mask_out, cudaStream_t s);
 cudaError_t launch_edge(const float *img, int pitch, size_t band_stride, int H,
@@ -169,8 +175,10 @@ void gauss_taps(double sigma, int rad, double *out);
 int step_form_from_env();
 // Fills the step arguments for a call and picks its kernel (`requested` is
 // LSE_FORM_AUTO, _STREAM or _GENERIC).
-void plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_stride,
-               const float *data, float *const phi[2], LseDevState *st,
+// Returns false when no step kernel serves the call (16-bit storage outside
+// the tile form).
+bool plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_stride,
+               const void *data, float *const phi[2], LseDevState *st,
                LsePartial *partials, int sm_count, int requested, StepPlan *plan);
 // Launches iteration n (0-based) of the plan.
 cudaError_t launch_step(StepPlan &plan, int n, cudaStream_t s);

@@ -1,5 +1,6 @@
 // lse_prologue.cu -- once-per-call and per-iteration helper kernels:
 //   convert     caller image (f32/f16/bf16/u16, B x H x W) -> pitched f32
+//   quantise    pitched f32 plane -> pitched f16 / bf16 plane (16-bit storage)
 //   prologue    copies phi0 (and g) into the pitched work buffers, checks
 //               finiteness, reduces the statistics of phi0 (Eq. 15 sums,
 //               |{phi0 >= 0}|, the range of band 0) and finalises the
@@ -14,6 +15,34 @@
 namespace {
 
 constexpr int kThreads = 256;
+
+// A value of a work plane stored as `storage` (LSE_F32 / LSE_F16 / LSE_BF16).
+__device__ __forceinline__ float load_as(const void *p, size_t i, int storage)
+{
+    if (storage == LSE_F16) return __half2float(static_cast<const __half *>(p)[i]);
+    if (storage == LSE_BF16) return __bfloat162float(static_cast<const __nv_bfloat16 *>(p)[i]);
+    return static_cast<const float *>(p)[i];
+}
+
+__device__ __forceinline__ void store_as(void *p, size_t i, float v, int storage)
+{
+    if (storage == LSE_F16) static_cast<__half *>(p)[i] = __float2half_rn(v);
+    else if (storage == LSE_BF16) static_cast<__nv_bfloat16 *>(p)[i] = __float2bfloat16_rn(v);
+    else static_cast<float *>(p)[i] = v;
+}
+
+__global__ void __launch_bounds__(kThreads)
+quantise_kernel(const float *__restrict__ src, int src_pitch, int H, int W,
+                void *__restrict__ dst, int pitch, int storage)
+{
+    const long long n = (long long)H * W;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(p / W);
+        const int x = (int)(p - (long long)y * W);
+        store_as(dst, (size_t)y * pitch + x, src[(size_t)y * src_pitch + x], storage);
+    }
+}
 
 __global__ void __launch_bounds__(kThreads)
 convert_kernel(const void *__restrict__ src, int dtype, int H, int W, int B,
@@ -43,11 +72,11 @@ convert_kernel(const void *__restrict__ src, int dtype, int H, int W, int B,
 }
 
 __global__ void __launch_bounds__(kThreads)
-prologue_kernel(const float *__restrict__ img, int img_pitch, size_t band_stride,
-                const float *__restrict__ phi0, const float *__restrict__ g,
-                int g_pitch, float *__restrict__ phi_dst,
+prologue_kernel(const void *__restrict__ img, int img_pitch, size_t band_stride,
+                const float *__restrict__ phi0, const void *__restrict__ g,
+                int g_pitch, void *__restrict__ phi_dst,
                 float *__restrict__ g_dst, int pitch, int H, int W, int B,
-                int term, float dt, LseDevState *st, LsePartial *partials)
+                int term, float dt, int storage, LseDevState *st, LsePartial *partials)
 {
     LseAcc acc;
     acc.clear();
@@ -58,16 +87,16 @@ prologue_kernel(const float *__restrict__ img, int img_pitch, size_t band_stride
         int x = (int)(p - (long long)y * W);
         float v = phi0[p];
         if (!isfinite(v)) acc.bits |= LSE_SBIT_NONFINITE;
-        phi_dst[(size_t)y * pitch + x] = v;
+        store_as(phi_dst, (size_t)y * pitch + x, v, storage);
         const bool pos = v >= 0.0f;
         acc.n_plus += pos;
         if (term == LSE_TERM_EDGE) {
-            float gv = g[(size_t)y * g_pitch + x];
+            float gv = load_as(g, (size_t)y * g_pitch + x, storage);
             if (!isfinite(gv)) acc.bits |= LSE_SBIT_NONFINITE;
             if (g_dst) g_dst[(size_t)y * pitch + x] = gv;
         } else {
             for (int b = 0; b < B; ++b) {
-                float iv = img[b * band_stride + (size_t)y * img_pitch + x];
+                float iv = load_as(img, b * band_stride + (size_t)y * img_pitch + x, storage);
                 if (!isfinite(iv)) acc.bits |= LSE_SBIT_NONFINITE;
                 if (pos) acc.sp[b] += iv;
                 else acc.sm[b] += iv;
@@ -161,21 +190,21 @@ normaliser_kernel(const float *__restrict__ img, int pitch, size_t band_stride,
 }
 
 struct BufPair {
-    float *b[2];
+    const void *b[2];
 };
 
 __global__ void __launch_bounds__(kThreads)
-output_kernel(BufPair bufs, int pitch, int H, int W, const LseDevState *st,
+output_kernel(BufPair bufs, int pitch, int H, int W, int storage, const LseDevState *st,
               float *__restrict__ phi_out, uint8_t *__restrict__ mask_out)
 {
     if (st->status_bits & LSE_SBIT_ABORT) return;
-    const float *src = bufs.b[st->last_buf];
+    const void *src = bufs.b[st->last_buf];
     const long long n = (long long)H * W;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
         int y = (int)(p / W);
         int x = (int)(p - (long long)y * W);
-        float v = src[(size_t)y * pitch + x];
+        float v = load_as(src, (size_t)y * pitch + x, storage);
         phi_out[p] = v;
         if (mask_out) mask_out[p] = v >= 0.0f ? 1 : 0;
     }
@@ -200,17 +229,25 @@ cudaError_t launch_convert(const void *src, int dtype, int H, int W, int B,
     return cudaGetLastError();
 }
 
-cudaError_t launch_prologue(const float *img, int img_pitch, size_t band_stride,
-                            const float *phi0, const float *g, int g_pitch,
-                            float *phi_dst, float *g_dst, int pitch, int H,
-                            int W, int B, int term, float dt,
+cudaError_t launch_quantise(const float *src, int src_pitch, int H, int W, void *dst,
+                            int pitch, int storage, cudaStream_t s)
+{
+    int grid = grid_for((long long)H * W, 4096);
+    quantise_kernel<<<grid, kThreads, 0, s>>>(src, src_pitch, H, W, dst, pitch, storage);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prologue(const void *img, int img_pitch, size_t band_stride,
+                            const float *phi0, const void *g, int g_pitch,
+                            void *phi_dst, float *g_dst, int pitch, int H,
+                            int W, int B, int term, float dt, int storage,
                             LseDevState *st, LsePartial *partials, int nblocks,
                             cudaStream_t s)
 {
     int grid = grid_for((long long)H * W, nblocks);
     prologue_kernel<<<grid, kThreads, 0, s>>>(img, img_pitch, band_stride, phi0,
                                               g, g_pitch, phi_dst, g_dst, pitch,
-                                              H, W, B, term, dt, st, partials);
+                                              H, W, B, term, dt, storage, st, partials);
     return cudaGetLastError();
 }
 
@@ -224,7 +261,7 @@ cudaError_t launch_normaliser(const float *img, int pitch, size_t band_stride,
     return cudaGetLastError();
 }
 
-cudaError_t launch_output(float *const *bufs, int pitch, int H, int W,
+cudaError_t launch_output(float *const *bufs, int pitch, int H, int W, int storage,
                           const LseDevState *st, float *phi_out,
                           uint8_t *mask_out, cudaStream_t s)
 {
@@ -232,7 +269,7 @@ cudaError_t launch_output(float *const *bufs, int pitch, int H, int W,
     bp.b[0] = bufs[0];
     bp.b[1] = bufs[1];
     int grid = grid_for((long long)H * W, 4096);
-    output_kernel<<<grid, kThreads, 0, s>>>(bp, pitch, H, W, st, phi_out,
+    output_kernel<<<grid, kThreads, 0, s>>>(bp, pitch, H, W, storage, st, phi_out,
                                             mask_out);
     return cudaGetLastError();
 }

@@ -157,11 +157,11 @@ extern "C" lse_status lse_evolve_static(const float *image, int H, int W, int B,
     const int nred = sm_count * 4;
     e = launch_prologue(region ? data : nullptr, pitch, band_stride, phi0,
                         region ? nullptr : g, W, phi[0], nullptr, pitch, H, W, B,
-                        p.term, p.dt, st, partials, nred, s);
+                        p.term, p.dt, LSE_F32, st, partials, nred, s);
     if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: prologue");
 
     StepPlan plan;
-    plan_step(H, W, B, p, pitch, band_stride, data, phi, st, partials, sm_count,
+    (void)plan_step(H, W, B, p, pitch, band_stride, data, phi, st, partials, sm_count,
               step_form_from_env(), &plan);
     for (int n = 0; n < p.iterations; ++n) {
         if (region && B > 1) {
@@ -172,7 +172,7 @@ extern "C" lse_status lse_evolve_static(const float *image, int H, int W, int B,
         e = launch_step(plan, n, s);
         if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: step");
     }
-    e = launch_output(phi, pitch, H, W, st, phi_out, mask_out, s);
+    e = launch_output(phi, pitch, H, W, LSE_F32, st, phi_out, mask_out, s);
     if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: output");
     if (stats) {
         LseDevState h;

@@ -33,19 +33,24 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-// Tensor map over a pitched float32 array of `bands` planes; boxes of
-// box_w x box_h elements (x all bands).
-bool encode_box(CUtensorMap *m, const float *base, int W, int H, int pitch,
+// Tensor map over a pitched array of `bands` planes of the storage type
+// (LSE_F32 / LSE_F16 / LSE_BF16); boxes of box_w x box_h elements (x all
+// bands).  pitch and band_stride count elements.
+bool encode_box(CUtensorMap *m, const void *base, int storage, int W, int H, int pitch,
                 size_t band_stride, int bands, int box_w, int box_h)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
+    const int es_bytes = storage == LSE_F32 ? 4 : 2;
+    const CUtensorMapDataType ty = storage == LSE_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : storage == LSE_BF16   ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)bands};
-    cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)band_stride * 4};
+    cuuint64_t strides[2] = {(cuuint64_t)pitch * es_bytes, (cuuint64_t)band_stride * es_bytes};
     cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, (cuuint32_t)bands};
     cuuint32_t es[3] = {1, 1, 1};
     const cuuint32_t rank = bands > 1 ? 3 : 2;
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, (void *)base, dims,
+    CUresult r = fn(m, ty, rank, const_cast<void *>(base), dims,
                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -82,8 +87,8 @@ int step_form_from_env()
     return LSE_FORM_AUTO;
 }
 
-void plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_stride,
-               const float *data, float *const phi[2], LseDevState *st,
+bool plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_stride,
+               const void *data, float *const phi[2], LseDevState *st,
                LsePartial *partials, int sm_count, int requested, StepPlan *plan)
 {
     StepArgs &a = plan->args;
@@ -103,7 +108,8 @@ void plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_
     a.npix = (long long)H * W;
     a.pitch = pitch;
     a.band_stride = band_stride;
-    a.data = data;
+    a.data = static_cast<const float *>(data);
+    a.storage = p.storage;
     a.st = st;
     a.partials = partials;
     plan->phi[0] = phi[0];
@@ -114,22 +120,28 @@ void plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_
     plan->wpc = 0;
 
     plan->form = LSE_FORM_GENERIC;
+    const int sto = p.storage;
+    // 16-bit storage: the data box starts with phi's, 4 columns left of the tile
+    const int data_box_w = sto == LSE_F32 ? 128 : 136;
     if (requested == LSE_FORM_AUTO &&
         plan_step_tile(H, W, a.B, p.term, a.rad, sm_count, &a, &plan->nblocks) &&
-        encode_box(&plan->phi_maps[0], phi[0], W, H, pitch, 0, 1, 136, 66) &&
-        encode_box(&plan->phi_maps[1], phi[1], W, H, pitch, 0, 1, 136, 66) &&
-        encode_box(&plan->data_map, data, W, H, pitch, band_stride, 1, 128, 64)) {
+        encode_box(&plan->phi_maps[0], phi[0], sto, W, H, pitch, 0, 1, 136, 66) &&
+        encode_box(&plan->phi_maps[1], phi[1], sto, W, H, pitch, 0, 1, 136, 66) &&
+        encode_box(&plan->data_map, data, sto, W, H, pitch, band_stride, 1, data_box_w, 64)) {
         plan->form = LSE_FORM_TILE;
+    } else if (sto != LSE_F32) {
+        return false;
     } else if (requested != LSE_FORM_GENERIC &&
                plan_step_tma(H, W, a.B, p.term, a.rad, sm_count, &a, &plan->nblocks,
                              &plan->wpc) &&
-               encode_box(&plan->phi_maps[0], phi[0], W, H, pitch, 0, 1, 136, 1) &&
-               encode_box(&plan->phi_maps[1], phi[1], W, H, pitch, 0, 1, 136, 1) &&
-               encode_box(&plan->data_map, data, W, H, pitch, band_stride, a.B, 128, 1)) {
+               encode_box(&plan->phi_maps[0], phi[0], sto, W, H, pitch, 0, 1, 136, 1) &&
+               encode_box(&plan->phi_maps[1], phi[1], sto, W, H, pitch, 0, 1, 136, 1) &&
+               encode_box(&plan->data_map, data, sto, W, H, pitch, band_stride, a.B, 128, 1)) {
         plan->form = LSE_FORM_STREAM;
     } else {
         plan->nblocks = sm_count * 4;
     }
+    return true;
 }
 
 // A re-initialising step other than the last stores sign(v) directly (the

@@ -37,6 +37,9 @@
 // and ends the CTA's tile loop; the CTA still takes part in the reduction.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <type_traits>
 
 #include "lse_reduce.cuh"
@@ -49,21 +52,104 @@ constexpr int kURows = 64;            // u / h rows per tile (TH + 2 RAD)
 constexpr int kURowsPerWarp = kURows / kWarps;
 constexpr int kPhiRows = kURows + 2;  // staged phi rows
 constexpr int kPhiW = 136;            // staged phi columns
-constexpr int kDataW = 128;           // staged data columns
 
-template <int RAD>
+// Storage of phi and of the data term in HBM: float, or half / bfloat16
+// (FP32 arithmetic either way).  A lane moves its 4 columns as one 16- or
+// 8-byte access.
+template <class T>
+struct Stor;
+
+template <>
+struct Stor<float> {
+    __device__ static float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+    __device__ static float ld1(const float *p) { return *p; }
+    __device__ static float from(float v) { return v; }
+    __device__ static float to(float v) { return v; }
+    __device__ static void st4(float *p, float a, float b, float c, float d)
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+    }
+};
+
+template <>
+struct Stor<__nv_bfloat16> {
+    using T = __nv_bfloat16;
+    __device__ static float4 ld4(const T *p)
+    {
+        const uint2 r = *reinterpret_cast<const uint2 *>(p);
+        const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.x));
+        const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.y));
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
+    __device__ static float ld1(const T *p) { return __bfloat162float(*p); }
+    __device__ static float from(T v) { return __bfloat162float(v); }
+    __device__ static T to(float v) { return __float2bfloat16_rn(v); }
+    __device__ static void st4(T *p, float a, float b, float c, float d)
+    {
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b);
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(c, d);
+        uint2 r;
+        r.x = *reinterpret_cast<const uint32_t *>(&lo);
+        r.y = *reinterpret_cast<const uint32_t *>(&hi);
+        *reinterpret_cast<uint2 *>(p) = r;
+    }
+};
+
+template <>
+struct Stor<__half> {
+    using T = __half;
+    __device__ static float4 ld4(const T *p)
+    {
+        const uint2 r = *reinterpret_cast<const uint2 *>(p);
+        const float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&r.x));
+        const float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&r.y));
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
+    __device__ static float ld1(const T *p) { return __half2float(*p); }
+    __device__ static float from(T v) { return __half2float(v); }
+    __device__ static T to(float v) { return __float2half_rn(v); }
+    __device__ static void st4(T *p, float a, float b, float c, float d)
+    {
+        const __half2 lo = __floats2half2_rn(a, b);
+        const __half2 hi = __floats2half2_rn(c, d);
+        uint2 r;
+        r.x = *reinterpret_cast<const uint32_t *>(&lo);
+        r.y = *reinterpret_cast<const uint32_t *>(&hi);
+        *reinterpret_cast<uint2 *>(p) = r;
+    }
+};
+
+// Shared-memory layout.  FP32 storage: h overwrites the phi rows (70 KB per
+// CTA); the data box is the 128 tile columns.  16-bit storage: a TMA box must
+// start on 16 bytes, so the data box starts with phi's, 4 columns left of the
+// tile (136 wide), and h has its own FP32 buffer (69 KB per CTA).
+template <int RAD, class T>
 struct TileGeo {
+    static constexpr bool WIDE = sizeof(T) == 4;
     static constexpr int HL = (RAD + 3) / 4;                    // halo lanes per side
     static constexpr int USEFUL = 128 - 8 * HL;                 // output columns
     static constexpr int TH = kURows - 2 * RAD;                 // output rows
     static constexpr int RPW = (TH + kWarps - 1) / kWarps;      // output rows per warp
-    // shared memory (floats): [sqrt table 32][2 mbarriers][old-sign words
-    // 64 x 4][phi, then h: 66 x 136][data 64 x 128]
+    static constexpr int DATA_W = WIDE ? 128 : kPhiW;           // staged data columns
+    static constexpr int DATA_X0 = WIDE ? 0 : 4;                // tile column 0 within it
+    static constexpr int PHI_BYTES = kPhiRows * kPhiW * (int)sizeof(T);
+    static constexpr int DATA_BYTES = kURows * DATA_W * (int)sizeof(T);
+    // offsets in floats: [sqrt table 32][2 mbarriers][old-sign words 64 x 4]
+    // [phi][data][h (16-bit storage only)]
     static constexpr int SIGN_OFF = 64;
     static constexpr int PHI_OFF = SIGN_OFF + kURows * 4;
-    static constexpr int DATA_OFF = PHI_OFF + ((kPhiRows * kPhiW + 31) & ~31);
-    static constexpr int FLOATS = DATA_OFF + kURows * kDataW;
+    static constexpr int DATA_OFF = PHI_OFF + ((PHI_BYTES / 4 + 31) & ~31);
+    static constexpr int HBUF_OFF = DATA_OFF + ((DATA_BYTES / 4 + 31) & ~31);
+    static constexpr int FLOATS = WIDE ? DATA_OFF + DATA_BYTES / 4 : HBUF_OFF + kURows * 128;
     static constexpr int BYTES = FLOATS * 4 + 128;              // + alignment slack
+    // h of u row ur: float index (ur + H_ROW0) * H_STRIDE + H_COL0 + 4 lane
+    // from the phi buffer (FP32) or from the h buffer (16-bit)
+    static constexpr int H_STRIDE = WIDE ? kPhiW : 128;
+    static constexpr int H_ROW0 = WIDE ? 2 : 0;
+    static constexpr int H_COL0 = WIDE ? 4 : 0;
+    // the vertical pass reads h rows up to 8 RPW - 1 + 2 RAD; past row 63
+    // they lie in other shared memory (FP32) or are clamped (16-bit)
+    static constexpr bool CLAMP_H = !WIDE && 8 * RPW - 1 + 2 * RAD > kURows - 1;
     static constexpr int MIN_BLOCKS = RAD <= 4 ? 3 : 2;
 };
 
@@ -128,13 +214,14 @@ __device__ __forceinline__ float4 lds4(const float *p)
     return *reinterpret_cast<const float4 *>(p);
 }
 
-template <int KIND_EDGE, int RAD, bool FAST>
-__global__ void __launch_bounds__(kThreads, TileGeo<RAD>::MIN_BLOCKS)
+template <int KIND_EDGE, int RAD, bool FAST, class T>
+__global__ void __launch_bounds__(kThreads, TileGeo<RAD, T>::MIN_BLOCKS)
 step_tile_kernel(const __grid_constant__ StepArgs a,
                  const __grid_constant__ CUtensorMap phi_map,
                  const __grid_constant__ CUtensorMap data_map)
 {
-    using G = TileGeo<RAD>;
+    using G = TileGeo<RAD, T>;
+    using S = Stor<T>;
     constexpr int HL = G::HL, TH = G::TH, P = 2 * RAD + 1, RPW = G::RPW;
     constexpr bool EDGE = KIND_EDGE != 0;
 
@@ -146,14 +233,15 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
     const int sb = (int)(((128u - (sm0 & 127u)) & 127u) >> 2);   // 128-byte aligned base
     float *lut = smem_f + sb;
     uint32_t *sign_w = reinterpret_cast<uint32_t *>(smem_f + sb + G::SIGN_OFF);
-    float *buf = smem_f + sb + G::PHI_OFF;
-    const float *dat = smem_f + sb + G::DATA_OFF;
+    T *buf = reinterpret_cast<T *>(smem_f + sb + G::PHI_OFF);
+    const T *dat = reinterpret_cast<const T *>(smem_f + sb + G::DATA_OFF);
+    float *hbase = G::WIDE ? smem_f + sb + G::PHI_OFF : smem_f + sb + G::HBUF_OFF;
     const uint32_t bar_phi = sm0 + 4u * (uint32_t)(sb + 32);
     const uint32_t bar_dat = bar_phi + 8;
     const uint32_t phi_dst = sm0 + 4u * (uint32_t)(sb + G::PHI_OFF);
     const uint32_t dat_dst = sm0 + 4u * (uint32_t)(sb + G::DATA_OFF);
-    constexpr uint32_t kPhiBytes = kPhiRows * kPhiW * 4;
-    constexpr uint32_t kDatBytes = kURows * kDataW * 4;
+    constexpr uint32_t kPhiBytes = G::PHI_BYTES;
+    constexpr uint32_t kDatBytes = G::DATA_BYTES;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -193,7 +281,7 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
         int xs, ys;
         origin(t, xs, ys);
         tma_box(phi_dst, &phi_map, xs - 4, ys, bar_phi, kPhiBytes);
-        tma_box(dat_dst, &data_map, xs, ys + 1, bar_dat, kDatBytes);
+        tma_box(dat_dst, &data_map, xs - G::DATA_X0, ys + 1, bar_dat, kDatBytes);
     };
 
     int t = blockIdx.x;
@@ -206,8 +294,9 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
     double dsw = 0.0, dsa = 0.0;
     const bool lane_out = lane >= HL && lane < 32 - HL;
     const int eidx = lane == 0 ? 3 : 132;        // phi column beyond the warp's edge
-    const float *bl = buf + 4 + 4 * lane;        // this lane's 4 columns of a phi / h slot
-    const float *dl = dat + 4 * lane;
+    const T *bl = buf + 4 + 4 * lane;            // this lane's 4 columns of a phi row
+    const T *dl = dat + G::DATA_X0 + 4 * lane;   // ... of a data row
+    float *hl = hbase + G::H_COL0 + 4 * lane;    // ... of an h row
 
     for (; t < n_tiles; t += gridDim.x) {
         int xs, ys;
@@ -225,16 +314,16 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
             // ghost columns 2 phi(0) - phi(1) and 2 phi(W-1) - phi(W-2)
             const bool gl = xs <= 0, gr = xs <= W - 1 && W - 1 < xs + 128;
             for (int rr = tid; rr < kPhiRows; rr += kThreads) {
-                float *row = buf + rr * kPhiW;
+                T *row = buf + rr * kPhiW;
                 if (gl) {
-                    const float f0 = row[4 - xs];
-                    const float f1 = W > 1 ? row[5 - xs] : f0;
-                    row[3 - xs] = 2.0f * f0 - f1;
+                    const float f0 = S::from(row[4 - xs]);
+                    const float f1 = W > 1 ? S::from(row[5 - xs]) : f0;
+                    row[3 - xs] = S::to(2.0f * f0 - f1);
                 }
                 if (gr) {
-                    const float fe = row[W + 3 - xs];
-                    const float fd = W > 1 ? row[W + 2 - xs] : fe;
-                    row[W + 4 - xs] = 2.0f * fe - fd;
+                    const float fe = S::from(row[W + 3 - xs]);
+                    const float fd = W > 1 ? S::from(row[W + 2 - xs]) : fe;
+                    row[W + 4 - xs] = S::to(2.0f * fe - fd);
                 }
             }
             __syncthreads();
@@ -252,9 +341,9 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
 
         // ---- u pass: u rows ur0 .. ur0 + 7 (centre phi row = slot ur + 1)
         const int ur0 = warp * kURowsPerWarp;
-        float4 pm = lds4(bl + ur0 * kPhiW);
-        float4 pc = lds4(bl + (ur0 + 1) * kPhiW);
-        float ec = buf[(ur0 + 1) * kPhiW + eidx];
+        float4 pm = S::ld4(bl + ur0 * kPhiW);
+        float4 pc = S::ld4(bl + (ur0 + 1) * kPhiW);
+        float ec = S::ld1(buf + (ur0 + 1) * kPhiW + eidx);
         if (binarise_in) {
             pm = bin4(pm);
             pc = bin4(pc);
@@ -267,9 +356,9 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
         // tile (no ghost rows, no columns outside the image or on its edge).
         auto urow = [&](auto in_tag, int ur) {
             constexpr bool IN = decltype(in_tag)::value;
-            float4 pp = lds4(bl + (ur + 2) * kPhiW);
-            float ep = buf[(ur + 2) * kPhiW + eidx];
-            const float4 d4 = lds4(dl + ur * kDataW);
+            float4 pp = S::ld4(bl + (ur + 2) * kPhiW);
+            float ep = S::ld1(buf + (ur + 2) * kPhiW + eidx);
+            const float4 d4 = S::ld4(dl + ur * G::DATA_W);
             if (binarise_in) {
                 pp = bin4(pp);
                 ep = bin(ep);
@@ -359,8 +448,9 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
                     h = fmaf(tp[q], U[4 * HL + j - q] + U[4 * HL + j + q], h);
                 hv[j] = h;
             }
-            // h of u row ur replaces phi slot ur + 2, read above by this warp
-            *reinterpret_cast<float4 *>(const_cast<float *>(bl) + (ur + 2) * kPhiW) =
+            // FP32 storage: h of u row ur replaces phi slot ur + 2, read above
+            // by this warp
+            *reinterpret_cast<float4 *>(hl + (ur + G::H_ROW0) * G::H_STRIDE) =
                 make_float4(hv[0], hv[1], hv[2], hv[3]);
             pm = pc;
             pc = pp;
@@ -387,13 +477,14 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
             // x0 + 4 <= pitch whenever x0 < W (x0 and the pitch are multiples
             // of 4): the lane stores all 4 columns, the padding is scratch
             const bool st_ok = lane_out && x0 < W;
-            float *dst = a.phi_out + (size_t)(ys + RAD + 1 + r_first) * a.pitch + x0;
+            T *dst = reinterpret_cast<T *>(a.phi_out) + (size_t)(ys + RAD + 1 + r_first) * a.pitch + x0;
             const size_t pitch = (size_t)a.pitch;
             float rg[P][4];
             // h rows past the tile read other shared memory (finite values);
             // their outputs are never used
             auto ldh = [&](int hr, float *d) {
-                const float4 h4 = lds4(bl + (hr + 2) * kPhiW);
+                if (G::CLAMP_H) hr = hr < kURows - 1 ? hr : kURows - 1;
+                const float4 h4 = lds4(hl + (hr + G::H_ROW0) * G::H_STRIDE);
                 d[0] = h4.x;
                 d[1] = h4.y;
                 d[2] = h4.z;
@@ -422,9 +513,10 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
                             w[j] = acc >= 0.0f ? 1.0f : -1.0f;
                         }
                         if (st_ok) {
-                            float4 sv = store_bin ? make_float4(w[0], w[1], w[2], w[3])
-                                                  : make_float4(v[0], v[1], v[2], v[3]);
-                            *reinterpret_cast<float4 *>(dst + k * pitch) = sv;
+                            if (store_bin)
+                                S::st4(dst + k * pitch, w[0], w[1], w[2], w[3]);
+                            else
+                                S::st4(dst + k * pitch, v[0], v[1], v[2], v[3]);
                         }
                         if (count_flips) {
                             const uint4 sw =
@@ -440,7 +532,7 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
                         if (!EDGE) {
                             // outside the image the staged data is zero; halo
                             // lanes drop their sums below
-                            const float4 d4 = lds4(dl + (ro + RAD) * kDataW);
+                            const float4 d4 = S::ld4(dl + (ro + RAD) * G::DATA_W);
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
                                 fsw = fmaf(comp(d4, j), w[j], fsw);
@@ -496,13 +588,13 @@ __host__ __device__ inline bool is_fast(const StepArgs &a)
     return a.binary_in && a.store_bin && !a.count_flips && !a.binarise_in;
 }
 
-template <int KIND_EDGE, int RAD>
+template <int KIND_EDGE, int RAD, class T>
 cudaError_t launch_tile_one(const StepArgs &a, const CUtensorMap &pm, const CUtensorMap &dm,
                             int nblocks, cudaStream_t s)
 {
-    using G = TileGeo<RAD>;
-    auto kern = is_fast(a) ? step_tile_kernel<KIND_EDGE, RAD, true>
-                           : step_tile_kernel<KIND_EDGE, RAD, false>;
+    using G = TileGeo<RAD, T>;
+    auto kern = is_fast(a) ? step_tile_kernel<KIND_EDGE, RAD, true, T>
+                           : step_tile_kernel<KIND_EDGE, RAD, false, T>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          G::BYTES);
     if (e != cudaSuccess) return e;
@@ -510,18 +602,18 @@ cudaError_t launch_tile_one(const StepArgs &a, const CUtensorMap &pm, const CUte
     return cudaGetLastError();
 }
 
-template <int KIND_EDGE>
+template <int KIND_EDGE, class T>
 cudaError_t launch_tile_kind(const StepArgs &a, const CUtensorMap &pm, const CUtensorMap &dm,
                              int nblocks, cudaStream_t s)
 {
     switch (a.rad) {
-    case 1: return launch_tile_one<KIND_EDGE, 1>(a, pm, dm, nblocks, s);
-    case 2: return launch_tile_one<KIND_EDGE, 2>(a, pm, dm, nblocks, s);
-    case 3: return launch_tile_one<KIND_EDGE, 3>(a, pm, dm, nblocks, s);
-    case 4: return launch_tile_one<KIND_EDGE, 4>(a, pm, dm, nblocks, s);
-    case 5: return launch_tile_one<KIND_EDGE, 5>(a, pm, dm, nblocks, s);
-    case 6: return launch_tile_one<KIND_EDGE, 6>(a, pm, dm, nblocks, s);
-    case 7: return launch_tile_one<KIND_EDGE, 7>(a, pm, dm, nblocks, s);
+    case 1: return launch_tile_one<KIND_EDGE, 1, T>(a, pm, dm, nblocks, s);
+    case 2: return launch_tile_one<KIND_EDGE, 2, T>(a, pm, dm, nblocks, s);
+    case 3: return launch_tile_one<KIND_EDGE, 3, T>(a, pm, dm, nblocks, s);
+    case 4: return launch_tile_one<KIND_EDGE, 4, T>(a, pm, dm, nblocks, s);
+    case 5: return launch_tile_one<KIND_EDGE, 5, T>(a, pm, dm, nblocks, s);
+    case 6: return launch_tile_one<KIND_EDGE, 6, T>(a, pm, dm, nblocks, s);
+    case 7: return launch_tile_one<KIND_EDGE, 7, T>(a, pm, dm, nblocks, s);
     default: return cudaErrorNotSupported;
     }
 }

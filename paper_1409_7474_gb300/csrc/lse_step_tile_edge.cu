@@ -1,5 +1,5 @@
 // lse_step_tile_edge.cu -- instantiations of the tile-form step for the edge
-// term E = g (Eq. 14).
+// term E = g (Eq. 14), FP32 storage.
 #include "lse_step_tile.cuh"
 
 namespace lse_detail {
@@ -7,7 +7,7 @@ namespace lse_detail {
 cudaError_t launch_step_tile_edge(const StepArgs &a, const CUtensorMap &pm,
                                   const CUtensorMap &dm, int nblocks, cudaStream_t s)
 {
-    return lse_tile::launch_tile_kind<1>(a, pm, dm, nblocks, s);
+    return lse_tile::launch_tile_kind<1, float>(a, pm, dm, nblocks, s);
 }
 
 }  // namespace lse_detail

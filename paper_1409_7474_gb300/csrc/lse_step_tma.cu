@@ -20,6 +20,10 @@ cudaError_t launch_step_tile_region1(const StepArgs &, const CUtensorMap &,
 cudaError_t launch_step_tile_edge(const StepArgs &, const CUtensorMap &,
                                   const CUtensorMap &, int, cudaStream_t);
 int step_tile_blocks_per_sm(int rad);
+cudaError_t launch_step_tile_bf16(const StepArgs &, const CUtensorMap &,
+                                  const CUtensorMap &, int, cudaStream_t);
+cudaError_t launch_step_tile_f16(const StepArgs &, const CUtensorMap &,
+                                 const CUtensorMap &, int, cudaStream_t);
 
 }  // namespace lse_detail
 
@@ -118,6 +122,8 @@ bool plan_step_tile(int H, int W, int B, int term, int rad, int sm_count,
 cudaError_t launch_step_tile(const StepArgs &a, const CUtensorMap &phi_map,
                              const CUtensorMap &data_map, int nblocks, cudaStream_t s)
 {
+    if (a.storage == LSE_BF16) return launch_step_tile_bf16(a, phi_map, data_map, nblocks, s);
+    if (a.storage == LSE_F16) return launch_step_tile_f16(a, phi_map, data_map, nblocks, s);
     if (a.term == LSE_TERM_EDGE) return launch_step_tile_edge(a, phi_map, data_map, nblocks, s);
     return launch_step_tile_region1(a, phi_map, data_map, nblocks, s);
 }

@@ -47,6 +47,7 @@ STATUS_NAMES = {0: "LSE_OK", 1: "LSE_ERR_INVALID_ARG", 2: "LSE_ERR_OOM",
 TERM_REGION = 0
 TERM_EDGE = 1
 F32, F16, BF16, U16 = 0, 1, 2, 3
+STORAGE = {"f32": F32, "f16": F16, "bf16": BF16}
 
 
 class Params(ctypes.Structure):
@@ -220,12 +221,14 @@ class Context:
     def evolve(self, image, phi0, term: str = "region", g=None, dt: float = 15.0,
                sigma: float = 1.0, ts: int = 9, iterations: int = 200,
                reinit_period: int = 1, early_stop_frac: float = 0.0,
-               phi_out=None, mask_out=None, stream=None, sync: bool = True):
+               phi_out=None, mask_out=None, stream=None, sync: bool = True,
+               storage: str = "f32"):
         """Runs the evolution.  Returns (phi_out, mask_out, stats or None).
 
         With ``sync`` the call waits for the stream and returns the statistics
         dict; otherwise it returns at once and ``stats()`` reads them after the
-        caller synchronises."""
+        caller synchronises.  ``storage`` ("f32", "f16" or "bf16") is the type
+        of the work planes in HBM (``lse_params.storage``)."""
         term_code = TERM_REGION if term in ("region", TERM_REGION) else TERM_EDGE
         ref = image if image is not None else phi0
         if image is not None:
@@ -240,7 +243,7 @@ class Context:
             mask_out = _empty_like_place(ref, (H, W), np.uint8,
                                          torch.uint8 if torch is not None else None)
         p = Params(term_code, float(dt), float(sigma), int(ts), int(iterations),
-                   int(reinit_period), float(early_stop_frac), F32)
+                   int(reinit_period), float(early_stop_frac), STORAGE[storage])
         st = Stats()
         rc = _lib.lse_evolve(self._h, _ptr(image) if term_code == TERM_REGION else None,
                              dcode, H, W, B,
