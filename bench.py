@@ -16,7 +16,10 @@ Reported (one JSON line on rank 0):
                CUDA events on the library's stream, against measured HBM;
   cpu_baseline the FP64 oracle on the host cores, on crops of the same scene;
   storage_variants  the same workload with BF16 and F16 storage of the data
-               term and the LSF (FP32 arithmetic, 6 B/px per region step).
+               term and the LSF (FP32 arithmetic, 6 B/px per region step);
+  batch        256 uneven images (sides 128-1024, caps 100-600, early stop)
+               through lse_evolve_batch with and without a CUDA graph, and
+               one lse_evolve call per image in sequence.
 `--impl reference` times the FP64 oracle alone (the reference arm).
 Under torchrun each rank runs its own replica (no collective on the data
 path): weak scaling.
@@ -60,6 +63,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the 16-bit storage variants")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched uneven-image measurement")
+    ap.add_argument("--batch-images", type=int, default=256)
     return ap.parse_args()
 
 
@@ -216,6 +222,68 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def batch_measurement(torch, lse, dev, n_images: int, seed: int = 3):
+    """The uneven-image work list (sides 128-1024, 1 or 4 bands, region or
+    edge term, caps 100-600, early stop at 1e-4 of the pixels) run three
+    ways on one context: one lse_evolve call per image in sequence, and
+    lse_evolve_batch with and without CUDA-graph capture.  Each is timed with
+    CUDA events around the whole call (staging, prologues, iterations,
+    outputs); g of the edge images is computed beforehand for all three."""
+    from paper_1409_7474_gb300 import scenes
+    probs = scenes.batch_problems(n_images, seed=seed)
+    ctx = lse.Context(dev.index, max_pixels=1024 * 1024, max_bands=4)
+    items = []
+    for q in probs:
+        img = torch.from_numpy(q["image"]).to(dev)
+        it = {"phi0": torch.from_numpy(q["phi0"]).to(dev), "term": q["term"],
+              "iterations": q["iterations"], "early_stop_frac": q["early_stop_frac"]}
+        H, W = q["phi0"].shape
+        it["phi_out"] = torch.empty((H, W), dtype=torch.float32, device=dev)
+        it["mask_out"] = torch.empty((H, W), dtype=torch.uint8, device=dev)
+        if q["term"] == "region":
+            it["image"] = img
+        else:
+            it["g"] = ctx.precompute_edge(img, 1.0, 9, 255.0)
+        items.append(it)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        out = fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1), out
+
+    def sequential():
+        runs = []
+        for it in items:
+            ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
+                       iterations=it["iterations"], early_stop_frac=it["early_stop_frac"],
+                       phi_out=it["phi_out"], mask_out=it["mask_out"], sync=False)
+            runs.append(None)
+        return runs
+
+    ctx.evolve_batch(items, use_graph=False)      # warm-up: scratch, modules
+    ms_graph, res = timed(lambda: ctx.evolve_batch(items, use_graph=True))
+    ms_direct, _ = timed(lambda: ctx.evolve_batch(items, use_graph=False))
+    sequential()
+    ms_seq, _ = timed(sequential)
+    px_it = sum(int(it["phi0"].numel()) * r[2]["iterations_run"] for it, r in zip(items, res))
+    ctx.destroy()
+    out = {"workload": f"{n_images} uneven images: sides log-uniform 128-1024, 1 or 4 bands, "
+                       "region or edge term, caps U{100..600}, early stop 1e-4",
+           "pixel_iterations": px_it, "unit": "Mpixel-iters/s"}
+    for name, ms in (("batch_graph", ms_graph), ("batch_direct", ms_direct),
+                     ("sequential", ms_seq)):
+        out[name] = {"ms": ms, "value": px_it / (ms / 1e3) / 1e6,
+                     "images_per_s": n_images / (ms / 1e3)}
+    return out
+
+
 def step_form() -> str:
     """The region step kernel that runs: the tile form unless LSE_STEP_KERNEL
     narrows the library's choice."""
@@ -400,6 +468,10 @@ def main():
                 "edge_step_frac": vbytes / (statistics.mean(v_ms_e) / iters / 1e3) / 1e9 / peak,
                 "status": [ctx_r.stats()["status"], ctx_e.stats()["status"]]}
 
+    batch = None
+    if not args.no_batch:
+        batch = batch_measurement(torch, lse, dev, args.batch_images)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_throughput(img, phi_r, phi_e, seconds=args.cpu_seconds)
@@ -418,7 +490,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks.summary(), "gpu_launches": launches,
-                "storage_variants": variants,
+                "storage_variants": variants, "batch": batch,
                 "impl": "gb300",
                 "stats": {"region": {k: st_r[k] for k in ("iterations_run", "status",
                                                           "last_flips", "area_plus")},

@@ -242,6 +242,48 @@ lse_status lse_evolve_static(const float *image, int H, int W, int B,
                              const lse_params *params, float *phi_out,
                              uint8_t *mask_out, lse_stats *stats, void *stream);
 
+/* One image of a batched evolution (lse_evolve_batch).  Every pointer is
+ * device memory of the context's GPU.
+ *   image     region term: B x H x W planar of `dtype` (f32/f16/bf16/u16,
+ *             u16 read as value/65535); NULL for the edge term.
+ *   g         edge term: H x W FP32 g(I) (lse_precompute_edge); NULL for the
+ *             region term.
+ *   phi0      H x W FP32 initial LSF.
+ *   params    this image's parameters (term, dt, sigma, ts, iteration cap,
+ *             reinit_period, early_stop_frac); storage must be LSE_F32.
+ *   phi_out   H x W FP32: v of the image's last executed iteration.
+ *   mask_out  H x W uint8 mask v >= 0, or NULL. */
+typedef struct {
+    const void *image;
+    lse_dtype dtype;
+    int H, W, B;
+    const float *g;
+    const float *phi0;
+    lse_params params;
+    float *phi_out;
+    uint8_t *mask_out;
+} lse_problem;
+
+#define LSE_BATCH_MAX 65536
+
+/* Runs the n independent evolutions of `problems` together (the paper has
+ * no counterpart: it extracts one object per run).  Each image keeps its own
+ * statistics (Eq. 15 and 17 per image), iteration cap and early stop, and
+ * its results are bit for bit those of lse_evolve on that image alone.
+ * Images that need the same step kernel (term, band count, template size)
+ * share one launch per iteration, so small images fill the GPU together;
+ * use_graph != 0 captures the whole iteration loop in a CUDA graph and
+ * launches it once.  stats (host, n entries, may be NULL) receives each
+ * image's statistics; elapsed_ms is the time of the whole iteration loop.
+ * The call synchronises `stream` before it returns.  Context scratch grows
+ * to hold every image's planes (about (B + 2) * 4 * H * round_up(W, 32)
+ * bytes per image).  Returns LSE_ERR_INVALID_ARG (nothing enqueued) when an
+ * image fails lse_evolve's checks, uses host memory, 16-bit storage, or
+ * needs the plain step kernel (ts > 15, more than 4 bands); LSE_ERR_OOM
+ * when scratch cannot grow; LSE_ERR_CUDA on a launch failure. */
+lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems,
+                            int use_graph, lse_stats *stats, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,47 +13,17 @@
 #include <stdlib.h>
 #include <string.h>
 
-#include "lse_internal.h"
+#include "lse_ctx.h"
 
 using namespace lse_detail;
-
-struct lse_ctx {
-    int device = 0;
-    int sm_count = 0;
-    size_t max_pixels = 0;
-    int max_bands = 0;
-    char err[512] = {0};
-    // device scratch
-    float *phi[2] = {nullptr, nullptr};
-    size_t phi_cap = 0;              // elements per buffer
-    float *img = nullptr;
-    size_t img_cap = 0;              // elements
-    float *gbuf = nullptr;
-    size_t g_cap = 0;
-    void *raw_in = nullptr;          // host image staging (caller dtype)
-    size_t raw_cap = 0;              // bytes
-    float *phi0_st = nullptr;
-    size_t phi0_cap = 0;
-    float *g_st = nullptr;
-    size_t g_st_cap = 0;
-    uint16_t *q16 = nullptr;         // data term as F16 / BF16 (16-bit storage)
-    size_t q16_cap = 0;
-    float *out_phi = nullptr;
-    size_t out_cap = 0;
-    uint8_t *out_mask = nullptr;
-    size_t mask_cap = 0;
-    LsePartial *partials = nullptr;
-    int n_partials = 0;
-    LseDevState *st = nullptr;
-    LseDevState *st_host = nullptr;  // pinned mirror
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    bool have_stats = false;
-    int step_form = 0;               // LSE_STEP_KERNEL at creation (LSE_FORM_*)
-};
 
 namespace {
 
 thread_local char g_create_err[512];
+
+}  // namespace
+
+namespace lse_detail {
 
 void set_err(lse_ctx *ctx, const char *fmt, ...)
 {
@@ -64,21 +34,7 @@ void set_err(lse_ctx *ctx, const char *fmt, ...)
     va_end(ap);
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard()
-    {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
-enum PtrKind { PTR_NULL = 0, PTR_HOST = 1, PTR_DEVICE = 2, PTR_BAD = 3 };
 
 PtrKind classify(const void *p, int device)
 {
@@ -138,17 +94,6 @@ lse_status ensure(lse_ctx *ctx, void **p, size_t *cap, size_t bytes,
     return LSE_OK;
 }
 
-template <typename T>
-lse_status ensure_t(lse_ctx *ctx, T **p, size_t *cap_elems, size_t elems,
-                    cudaStream_t s, const char *name)
-{
-    size_t cap_bytes = *cap_elems * sizeof(T);
-    void *vp = *p;
-    lse_status r = ensure(ctx, &vp, &cap_bytes, elems * sizeof(T), s, name);
-    *p = static_cast<T *>(vp);
-    *cap_elems = cap_bytes / sizeof(T);
-    return r;
-}
 
 lse_status check_image_args(lse_ctx *ctx, lse_dtype dtype, int H, int W, int B)
 {
@@ -220,9 +165,61 @@ lse_status stage_image(lse_ctx *ctx, const void *image, PtrKind kind,
     return LSE_OK;
 }
 
-}  // namespace
+lse_status check_params(lse_ctx *ctx, const lse_params &p, int B)
+{
+    if (p.term != LSE_TERM_REGION && p.term != LSE_TERM_EDGE) {
+        set_err(ctx, "unknown term %d", (int)p.term);
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (!(p.dt > 0.0f) || !isfinite(p.dt) || !(p.sigma > 0.0f) || !isfinite(p.sigma)) {
+        set_err(ctx, "need finite dt > 0 and sigma > 0 (got %g, %g)", p.dt, p.sigma);
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (p.ts < 1 || p.ts > 31 || (p.ts % 2) == 0) {
+        set_err(ctx, "ts must be odd and in 1..31 (got %d)", p.ts);
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (p.iterations < 1 || p.reinit_period < 0) {
+        set_err(ctx, "need iterations >= 1 and reinit_period >= 0");
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (!(p.early_stop_frac >= 0.0f) || !(p.early_stop_frac < 1.0f)) {
+        set_err(ctx, "early_stop_frac must be in [0, 1)");
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (p.storage != LSE_F32 && p.storage != LSE_F16 && p.storage != LSE_BF16) {
+        set_err(ctx, "storage must be LSE_F32, LSE_F16 or LSE_BF16 (got %d)", (int)p.storage);
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (p.storage != LSE_F32 && ((p.term == LSE_TERM_REGION && B != 1) || p.ts > 15)) {
+        set_err(ctx, "16-bit storage needs one band (or the edge term) and ts <= 15");
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (p.term == LSE_TERM_EDGE && p.reinit_period != 1) {
+        set_err(ctx, "the edge term needs reinit_period = 1 (Step 3: without "
+                     "re-initialisation its LSF only grows)");
+        return LSE_ERR_INVALID_ARG;
+    }
+    return LSE_OK;
+}
 
-namespace lse_detail {
+void fill_stats(const LseDevState &h, float elapsed_ms, lse_stats *stats)
+{
+    memset(stats, 0, sizeof(*stats));
+    stats->iterations_run = h.iterations_run;
+    stats->last_flips = h.last_flips;
+    stats->area_plus = h.area_plus;
+    for (int b = 0; b < 8; ++b) {
+        stats->c_plus[b] = h.c_plus[b];
+        stats->c_minus[b] = h.c_minus[b];
+    }
+    stats->norm = h.norm_used;
+    stats->elapsed_ms = elapsed_ms;
+    if (h.status_bits & LSE_SBIT_NONFINITE) stats->status = LSE_ERR_NONFINITE;
+    else if (h.status_bits & LSE_SBIT_TIMEOUT) stats->status = LSE_ERR_TIMEOUT;
+    else if (h.status_bits & LSE_SBIT_DEGENERATE) stats->status = LSE_WARN_DEGENERATE;
+    else stats->status = LSE_OK;
+}
 
 // Message for lse_last_error(NULL) from calls that have no context.
 void set_contextless_error(const char *msg)
@@ -247,10 +244,12 @@ void lse_destroy(lse_ctx *ctx)
     DeviceGuard g(ctx->device);
     void *bufs[] = {ctx->phi[0], ctx->phi[1], ctx->img, ctx->gbuf, ctx->raw_in,
                     ctx->phi0_st, ctx->g_st, ctx->out_phi, ctx->out_mask, ctx->q16,
-                    ctx->partials, ctx->st};
+                    ctx->partials, ctx->st, ctx->arena, ctx->tables};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (ctx->st_host) cudaFreeHost(ctx->st_host);
+    if (ctx->bhost) cudaFreeHost(ctx->bhost);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     delete ctx;
@@ -320,26 +319,12 @@ lse_status lse_get_stats(lse_ctx *ctx, lse_stats *stats)
         return LSE_ERR_INVALID_ARG;
     }
     DeviceGuard g(ctx->device);
-    const LseDevState &h = *ctx->st_host;
-    memset(stats, 0, sizeof(*stats));
-    stats->iterations_run = h.iterations_run;
-    stats->last_flips = h.last_flips;
-    stats->area_plus = h.area_plus;
-    for (int b = 0; b < 8; ++b) {
-        stats->c_plus[b] = h.c_plus[b];
-        stats->c_minus[b] = h.c_minus[b];
-    }
-    stats->norm = h.norm_used;
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) != cudaSuccess) {
         cudaGetLastError();
         ms = -1.0f;
     }
-    stats->elapsed_ms = ms;
-    if (h.status_bits & LSE_SBIT_NONFINITE) stats->status = LSE_ERR_NONFINITE;
-    else if (h.status_bits & LSE_SBIT_TIMEOUT) stats->status = LSE_ERR_TIMEOUT;
-    else if (h.status_bits & LSE_SBIT_DEGENERATE) stats->status = LSE_WARN_DEGENERATE;
-    else stats->status = LSE_OK;
+    fill_stats(*ctx->st_host, ms, stats);
     return LSE_OK;
 }
 
@@ -409,39 +394,7 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
     const lse_params p = *params;
     lse_status r = check_image_args(ctx, dtype, H, W, B);
     if (r != LSE_OK) return r;
-    if (p.term != LSE_TERM_REGION && p.term != LSE_TERM_EDGE) {
-        set_err(ctx, "unknown term %d", (int)p.term);
-        return LSE_ERR_INVALID_ARG;
-    }
-    if (!(p.dt > 0.0f) || !isfinite(p.dt) || !(p.sigma > 0.0f) || !isfinite(p.sigma)) {
-        set_err(ctx, "need finite dt > 0 and sigma > 0 (got %g, %g)", p.dt, p.sigma);
-        return LSE_ERR_INVALID_ARG;
-    }
-    if (p.ts < 1 || p.ts > 31 || (p.ts % 2) == 0) {
-        set_err(ctx, "ts must be odd and in 1..31 (got %d)", p.ts);
-        return LSE_ERR_INVALID_ARG;
-    }
-    if (p.iterations < 1 || p.reinit_period < 0) {
-        set_err(ctx, "need iterations >= 1 and reinit_period >= 0");
-        return LSE_ERR_INVALID_ARG;
-    }
-    if (!(p.early_stop_frac >= 0.0f) || !(p.early_stop_frac < 1.0f)) {
-        set_err(ctx, "early_stop_frac must be in [0, 1)");
-        return LSE_ERR_INVALID_ARG;
-    }
-    if (p.storage != LSE_F32 && p.storage != LSE_F16 && p.storage != LSE_BF16) {
-        set_err(ctx, "storage must be LSE_F32, LSE_F16 or LSE_BF16 (got %d)", (int)p.storage);
-        return LSE_ERR_INVALID_ARG;
-    }
-    if (p.storage != LSE_F32 && ((p.term == LSE_TERM_REGION && B != 1) || p.ts > 15)) {
-        set_err(ctx, "16-bit storage needs one band (or the edge term) and ts <= 15");
-        return LSE_ERR_INVALID_ARG;
-    }
-    if (p.term == LSE_TERM_EDGE && p.reinit_period != 1) {
-        set_err(ctx, "the edge term needs reinit_period = 1 (Step 3: without "
-                     "re-initialisation its LSF only grows)");
-        return LSE_ERR_INVALID_ARG;
-    }
+    if ((r = check_params(ctx, p, B)) != LSE_OK) return r;
     const bool region = p.term == LSE_TERM_REGION;
     if (!phi0 || !phi_out || (region && !image) || (!region && !g) || (region && g)) {
         set_err(ctx, "need phi0, phi_out, image (region) or g (edge); g must be "

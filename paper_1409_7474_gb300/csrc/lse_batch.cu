@@ -1,0 +1,346 @@
+// lse_batch.cu -- lse_evolve_batch: many independent evolutions (images of
+// any size, term, band count and iteration cap) advanced together.
+//
+// Every image keeps what lse_evolve would give it alone: its own planes,
+// statistics record, partials, tensor maps and CTA count, so its results are
+// bit for bit those of lse_evolve.  What changes is the launch structure:
+// images are grouped into classes by step kernel (form, term, bands, radius),
+// and iteration n of every image of a class is one launch whose CTAs find
+// their image in a CTA table.  An image past its cap or stopped early leaves
+// its CTAs idle.  The whole loop (max cap x classes launches) can be
+// captured in a CUDA graph and replayed as one submission.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "lse_ctx.h"
+
+using namespace lse_detail;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Grows the context's pinned host mirror to at least `bytes`.
+lse_status ensure_host(lse_ctx *ctx, size_t bytes, cudaStream_t s)
+{
+    if (ctx->bhost_cap >= bytes && ctx->bhost) return LSE_OK;
+    if (ctx->bhost) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise before growing host mirror");
+        cudaFreeHost(ctx->bhost);
+        ctx->bhost = nullptr;
+        ctx->bhost_cap = 0;
+    }
+    cudaError_t e = cudaMallocHost(&ctx->bhost, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->bhost = nullptr;
+        set_err(ctx, "cudaMallocHost of %zu bytes failed", bytes);
+        return LSE_ERR_OOM;
+    }
+    ctx->bhost_cap = bytes;
+    return LSE_OK;
+}
+
+struct Layout {
+    int pitch;
+    size_t data, phi0, phi1;    // byte offsets in the arena
+};
+
+// A class of images served by one step kernel instantiation.
+struct ClassKey {
+    int form, term, bands, rad, wpc;
+    bool operator<(const ClassKey &o) const
+    {
+        return std::tie(form, term, bands, rad, wpc) <
+               std::tie(o.form, o.term, o.bands, o.rad, o.wpc);
+    }
+};
+
+struct Class {
+    std::vector<int> items;
+    int nblocks = 0;            // step CTAs
+    int nnblocks = 0;           // normaliser CTAs (vector region images)
+    size_t blk_off = 0, nblk_off = 0;   // byte offsets of the CTA tables
+};
+
+int grid_for(long long n, int cap)
+{
+    long long blocks = (n + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    return (int)(blocks < cap ? blocks : cap);
+}
+
+cudaError_t launch_class(const ClassKey &k, const Class &c, const BatchItem *items,
+                         const unsigned char *tables, int n, cudaStream_t s)
+{
+    const int *blk = reinterpret_cast<const int *>(tables + c.blk_off);
+    if (k.form == LSE_FORM_TILE) {
+        return k.term == LSE_TERM_EDGE
+                   ? launch_step_tile_batch_edge(k.rad, items, blk, n, c.nblocks, s)
+                   : launch_step_tile_batch_region1(k.rad, items, blk, n, c.nblocks, s);
+    }
+    if (k.term == LSE_TERM_EDGE)
+        return launch_step_tma_batch_edge(k.rad, items, blk, n, c.nblocks, k.wpc, s);
+    if (k.bands == 1)
+        return launch_step_tma_batch_region1(k.rad, items, blk, n, c.nblocks, k.wpc, s);
+    const int *nblk = reinterpret_cast<const int *>(tables + c.nblk_off);
+    cudaError_t e = launch_normaliser_batch(items, nblk, n, c.nnblocks, s);
+    if (e != cudaSuccess) return e;
+    return launch_step_tma_batch_multiband(k.rad, items, blk, n, c.nblocks, k.wpc, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, int use_graph,
+                            lse_stats *stats, void *stream)
+{
+    if (!ctx) return LSE_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (n < 1 || n > LSE_BATCH_MAX || !problems) {
+        set_err(ctx, "lse_evolve_batch: need 1 <= n <= %d images and a problem array",
+                LSE_BATCH_MAX);
+        return LSE_ERR_INVALID_ARG;
+    }
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return cuda_fail(ctx, cudaErrorInvalidDevice, "set device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    lse_status r;
+
+    // ---- validation (nothing is enqueued before every image passes)
+    for (int i = 0; i < n; ++i) {
+        const lse_problem &q = problems[i];
+        const bool region = q.params.term == LSE_TERM_REGION;
+        if (q.H < 1 || q.W < 1 || q.B < 1 || q.B > LSE_MAXB) {
+            set_err(ctx, "lse_evolve_batch: image %d: need H, W >= 1 and 1 <= B <= %d", i,
+                    LSE_MAXB);
+            return LSE_ERR_INVALID_ARG;
+        }
+        if (region && q.dtype != LSE_F32 && q.dtype != LSE_F16 && q.dtype != LSE_BF16 &&
+            q.dtype != LSE_U16) {
+            set_err(ctx, "lse_evolve_batch: image %d: unknown dtype %d", i, (int)q.dtype);
+            return LSE_ERR_INVALID_ARG;
+        }
+        if ((r = check_params(ctx, q.params, q.B)) != LSE_OK) return r;
+        if (q.params.storage != LSE_F32) {
+            set_err(ctx, "lse_evolve_batch: image %d: batches use LSE_F32 storage", i);
+            return LSE_ERR_INVALID_ARG;
+        }
+        const bool ok = classify(q.phi0, ctx->device) == PTR_DEVICE &&
+                        classify(q.phi_out, ctx->device) == PTR_DEVICE &&
+                        (!q.mask_out || classify(q.mask_out, ctx->device) == PTR_DEVICE) &&
+                        (region ? (classify(q.image, ctx->device) == PTR_DEVICE && !q.g)
+                                : classify(q.g, ctx->device) == PTR_DEVICE);
+        if (!ok) {
+            set_err(ctx, "lse_evolve_batch: image %d: image (region) or g (edge), phi0, "
+                         "phi_out and mask_out must be device memory of the context's GPU",
+                    i);
+            return LSE_ERR_INVALID_ARG;
+        }
+    }
+
+    // ---- arena: per image [data][phi0][phi1]; then states, partials, items
+    std::vector<Layout> lay(n);
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        const lse_problem &q = problems[i];
+        const int pitch = round_up(q.W, 32);
+        const int bands = q.params.term == LSE_TERM_REGION ? q.B : 1;
+        const size_t plane = (size_t)q.H * pitch * 4;
+        lay[i].pitch = pitch;
+        lay[i].data = off;
+        off = align_up(off + plane * bands);
+        lay[i].phi0 = off;
+        off = align_up(off + plane);
+        lay[i].phi1 = off;
+        off = align_up(off + plane);
+    }
+    const int nparts = partials_needed(ctx->sm_count);
+    const size_t st_off = off;
+    off = align_up(off + sizeof(LseDevState) * n);
+    const size_t part_off = off;
+    off = align_up(off + sizeof(LsePartial) * (size_t)nparts * n);
+    const size_t item_off = off;
+    off = align_up(off + sizeof(BatchItem) * n);
+    if ((r = ensure(ctx, &ctx->arena, &ctx->arena_cap, off, s, "batch arena")) != LSE_OK) return r;
+    unsigned char *A = static_cast<unsigned char *>(ctx->arena);
+    LseDevState *states = reinterpret_cast<LseDevState *>(A + st_off);
+    LsePartial *partials = reinterpret_cast<LsePartial *>(A + part_off);
+    BatchItem *d_items = reinterpret_cast<BatchItem *>(A + item_off);
+    cudaError_t e = cudaMemsetAsync(states, 0, sizeof(LseDevState) * n, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_evolve_batch: clear states");
+
+    // ---- staging and prologue of every image; the plan of its step
+    std::vector<BatchItem> items(n);
+    std::map<ClassKey, Class> classes;
+    std::vector<ClassKey> key_of(n);
+    const int nred = ctx->sm_count * 4;
+    for (int i = 0; i < n; ++i) {
+        const lse_problem &q = problems[i];
+        const lse_params &p = q.params;
+        const bool region = p.term == LSE_TERM_REGION;
+        const int pitch = lay[i].pitch;
+        const size_t bstride = (size_t)q.H * pitch;
+        float *data = reinterpret_cast<float *>(A + lay[i].data);
+        float *phi[2] = {reinterpret_cast<float *>(A + lay[i].phi0),
+                         reinterpret_cast<float *>(A + lay[i].phi1)};
+        if (region) {
+            e = launch_convert(q.image, q.dtype, q.H, q.W, q.B, data, pitch, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_evolve_batch: convert");
+        }
+        LsePartial *parts = partials + (size_t)nparts * i;
+        e = launch_prologue(region ? data : nullptr, pitch, bstride, q.phi0,
+                            region ? nullptr : q.g, q.W, phi[0], region ? nullptr : data, pitch,
+                            q.H, q.W, q.B, p.term, p.dt, LSE_F32, states + i, parts, nred, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_evolve_batch: prologue");
+        StepPlan plan;
+        plan_step(q.H, q.W, q.B, p, pitch, bstride, data, phi, states + i, parts, ctx->sm_count,
+                  ctx->step_form, &plan);
+        if (plan.form == LSE_FORM_GENERIC) {
+            set_err(ctx, "lse_evolve_batch: image %d needs the plain step kernel (ts > 15, "
+                         "more than 4 bands, or LSE_STEP_KERNEL=generic); run it with "
+                         "lse_evolve",
+                    i);
+            return LSE_ERR_INVALID_ARG;
+        }
+        BatchItem &it = items[i];
+        memset(&it, 0, sizeof(it));
+        it.phi_maps[0] = plan.phi_maps[0];
+        it.phi_maps[1] = plan.phi_maps[1];
+        it.data_map = plan.data_map;
+        it.args = plan.args;
+        it.phi[0] = phi[0];
+        it.phi[1] = phi[1];
+        it.nblocks = plan.nblocks;
+        it.cap = p.iterations;
+        it.reinit_period = p.reinit_period;
+        it.early_stop = p.early_stop_frac > 0.0f;
+        const int bands = region ? q.B : 1;
+        ClassKey k{plan.form, p.term, bands, plan.args.rad, plan.wpc};
+        key_of[i] = k;
+        Class &c = classes[k];
+        it.start = c.nblocks;
+        c.nblocks += it.nblocks;
+        if (region && q.B > 1) {
+            it.nnblocks = grid_for((long long)q.H * q.W, nred);
+            it.nstart = c.nnblocks;
+            c.nnblocks += it.nnblocks;
+        }
+        c.items.push_back(i);
+    }
+
+    // ---- CTA tables and the work list, uploaded once
+    size_t toff = 0;
+    for (auto &kc : classes) {
+        kc.second.blk_off = toff;
+        toff = align_up(toff + sizeof(int) * kc.second.nblocks);
+        kc.second.nblk_off = toff;
+        toff = align_up(toff + sizeof(int) * kc.second.nnblocks);
+    }
+    if ((r = ensure(ctx, &ctx->tables, &ctx->tables_cap, toff, s, "batch tables")) != LSE_OK)
+        return r;
+    const size_t hbytes = align_up(sizeof(BatchItem) * n) + toff + sizeof(LseDevState) * n;
+    if ((r = ensure_host(ctx, hbytes, s)) != LSE_OK) return r;
+    unsigned char *Hh = static_cast<unsigned char *>(ctx->bhost);
+    memcpy(Hh, items.data(), sizeof(BatchItem) * n);
+    unsigned char *ht = Hh + align_up(sizeof(BatchItem) * n);
+    for (auto &kc : classes) {
+        int *blk = reinterpret_cast<int *>(ht + kc.second.blk_off);
+        int *nblk = reinterpret_cast<int *>(ht + kc.second.nblk_off);
+        for (int i : kc.second.items) {
+            for (int b = 0; b < items[i].nblocks; ++b) blk[items[i].start + b] = i;
+            for (int b = 0; b < items[i].nnblocks; ++b) nblk[items[i].nstart + b] = i;
+        }
+    }
+    e = cudaMemcpyAsync(d_items, Hh, sizeof(BatchItem) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && toff)
+        e = cudaMemcpyAsync(ctx->tables, ht, toff, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_evolve_batch: upload work list");
+    const unsigned char *tables = static_cast<const unsigned char *>(ctx->tables);
+
+    // ---- the iteration loop: one launch per class and iteration
+    int maxcap = 0;
+    for (int i = 0; i < n; ++i) maxcap = std::max(maxcap, problems[i].params.iterations);
+    auto enqueue_loop = [&]() -> cudaError_t {
+        for (int it = 0; it < maxcap; ++it)
+            for (auto &kc : classes) {
+                cudaError_t le = launch_class(kc.first, kc.second, d_items, tables, it, s);
+                if (le != cudaSuccess) return le;
+            }
+        return cudaSuccess;
+    };
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (use_graph) {
+        // kernel attributes are set by one launch per class in which every
+        // image is past its cap (its CTAs return at once), outside the capture
+        for (auto &kc : classes) {
+            e = launch_class(kc.first, kc.second, d_items, tables, maxcap, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_evolve_batch: prepare");
+        }
+        // capture on the context's own stream (the caller's may be the legacy
+        // default stream, which cannot be captured); the graph runs on `s`
+        if (!ctx->cap_stream) {
+            e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_evolve_batch: capture stream");
+        }
+        cudaStream_t cs = ctx->cap_stream;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t le = cudaSuccess;
+            for (int it = 0; it < maxcap && le == cudaSuccess; ++it)
+                for (auto &kc : classes) {
+                    le = launch_class(kc.first, kc.second, d_items, tables, it, cs);
+                    if (le != cudaSuccess) break;
+                }
+            e = cudaStreamEndCapture(cs, &graph);
+            if (le != cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(ctx, e, "lse_evolve_batch: capture");
+        }
+    }
+    e = cudaEventRecord(ctx->ev0, s);
+    if (e == cudaSuccess) e = use_graph ? cudaGraphLaunch(exec, s) : enqueue_loop();
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev1, s);
+    if (e != cudaSuccess) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(ctx, e, "lse_evolve_batch: iterations");
+    }
+
+    // ---- outputs and statistics
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const lse_problem &q = problems[i];
+        e = launch_output(items[i].phi, lay[i].pitch, q.H, q.W, LSE_F32, states + i,
+                          q.phi_out, q.mask_out, s);
+    }
+    LseDevState *hs = reinterpret_cast<LseDevState *>(ht + toff);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hs, states, sizeof(LseDevState) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_evolve_batch: outputs");
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        ms = -1.0f;
+    }
+    if (stats)
+        for (int i = 0; i < n; ++i) fill_stats(hs[i], ms, stats + i);
+    return LSE_OK;
+}
+
+}  // extern "C"

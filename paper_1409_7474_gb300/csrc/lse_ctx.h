@@ -1,0 +1,97 @@
+// lse_ctx.h -- the context record behind lse_ctx and the host helpers the
+// C-ABI entry points share (internal).
+#pragma once
+
+#include "lse_internal.h"
+
+struct lse_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t max_pixels = 0;
+    int max_bands = 0;
+    char err[512] = {0};
+    // device scratch
+    float *phi[2] = {nullptr, nullptr};
+    size_t phi_cap = 0;              // elements per buffer
+    float *img = nullptr;
+    size_t img_cap = 0;              // elements
+    float *gbuf = nullptr;
+    size_t g_cap = 0;
+    void *raw_in = nullptr;          // host image staging (caller dtype)
+    size_t raw_cap = 0;              // bytes
+    float *phi0_st = nullptr;
+    size_t phi0_cap = 0;
+    float *g_st = nullptr;
+    size_t g_st_cap = 0;
+    uint16_t *q16 = nullptr;         // data term as F16 / BF16 (16-bit storage)
+    size_t q16_cap = 0;
+    float *out_phi = nullptr;
+    size_t out_cap = 0;
+    uint8_t *out_mask = nullptr;
+    size_t mask_cap = 0;
+    LsePartial *partials = nullptr;
+    int n_partials = 0;
+    LseDevState *st = nullptr;
+    LseDevState *st_host = nullptr;  // pinned mirror
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool have_stats = false;
+    int step_form = 0;               // LSE_STEP_KERNEL at creation (LSE_FORM_*)
+    // lse_evolve_batch: per-image planes, states and partials; the work list
+    // and CTA tables; a pinned mirror for uploads and the states
+    void *arena = nullptr;
+    size_t arena_cap = 0;            // bytes
+    void *tables = nullptr;
+    size_t tables_cap = 0;           // bytes
+    void *bhost = nullptr;
+    size_t bhost_cap = 0;            // bytes (pinned)
+    cudaStream_t cap_stream = nullptr;  // stream on which batches are captured
+};
+
+namespace lse_detail {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+enum PtrKind { PTR_NULL = 0, PTR_HOST = 1, PTR_DEVICE = 2, PTR_BAD = 3 };
+
+// Formats the message lse_last_error returns (ctx NULL: the thread's
+// context-free message).
+void set_err(lse_ctx *ctx, const char *fmt, ...);
+// Host, device (of `device`), or device memory of another GPU.
+PtrKind classify(const void *p, int device);
+size_t dtype_size(int dt);
+int round_up(int v, int m);
+lse_status cuda_fail(lse_ctx *ctx, cudaError_t e, const char *what);
+// Grows a device buffer to at least `bytes`; refuses while capturing.
+lse_status ensure(lse_ctx *ctx, void **p, size_t *cap, size_t bytes, cudaStream_t s,
+                  const char *name);
+bool aligned16(const void *p);
+// Validates lse_params for an image of B bands (messages via set_err).
+lse_status check_params(lse_ctx *ctx, const lse_params &p, int B);
+// Converts a device state record into the caller's statistics.
+void fill_stats(const LseDevState &h, float elapsed_ms, lse_stats *stats);
+
+template <typename T>
+lse_status ensure_t(lse_ctx *ctx, T **p, size_t *cap_elems, size_t elems,
+                    cudaStream_t s, const char *name)
+{
+    size_t cap_bytes = *cap_elems * sizeof(T);
+    void *vp = *p;
+    lse_status r = ensure(ctx, &vp, &cap_bytes, elems * sizeof(T), s, name);
+    *p = static_cast<T *>(vp);
+    *cap_elems = cap_bytes / sizeof(T);
+    return r;
+}
+
+}  // namespace lse_detail

@@ -91,6 +91,54 @@ struct StepArgs {
     int n_items;
 };
 
+// One image of a batched evolution (lse_evolve_batch), in device memory.
+// The CTAs [start, start + nblocks) of its class's step launch work on it;
+// vector images also own the normaliser CTAs [nstart, nstart + nnblocks).
+struct alignas(64) BatchItem {
+    CUtensorMap phi_maps[2];    // tensor maps of phi[0], phi[1]
+    CUtensorMap data_map;
+    StepArgs args;              // iteration-independent step arguments
+    float *phi[2];              // the ping-pong pair
+    int start, nblocks;
+    int cap;                    // iterations to run
+    int reinit_period;
+    int early_stop;
+    int nstart, nnblocks;
+};
+
+// Re-initialisation after iteration n (0-based) with period `period`
+// (1: every iteration, 0: never, k: after iterations k-1, 2k-1, ...).
+__host__ __device__ inline bool lse_reinit_after(int n, int period)
+{
+    if (period == 1) return true;
+    if (period <= 0) return false;
+    return ((n + 1) % period) == 0;
+}
+
+// The per-iteration fields of the step arguments for iteration n of an
+// evolution of `cap` iterations on the ping-pong pair phi[2].  A
+// re-initialising step other than the last stores sign(v) directly when the
+// kernel can (`bin_out`), unless an early stop may make it the last one;
+// then it stores v and the next step binarises on load.  Sign changes are
+// counted for the early stop and on the last step.
+__host__ __device__ inline void lse_iteration_flags(StepArgs &a, int n, int cap,
+                                                    int reinit_period, bool early_stop,
+                                                    bool bin_out, float *const phi[2])
+{
+    auto stores_bin = [&](int k) {
+        return bin_out && lse_reinit_after(k, reinit_period) && k < cap - 1 && !early_stop;
+    };
+    a.iter = n;
+    a.phi_in = phi[n & 1];
+    a.phi_out = phi[(n + 1) & 1];
+    a.out_buf = (n + 1) & 1;
+    a.store_bin = stores_bin(n) ? 1 : 0;
+    a.binary_in = (n > 0 && stores_bin(n - 1)) ? 1 : 0;
+    a.binarise_in =
+        (n > 0 && lse_reinit_after(n - 1, reinit_period) && !stores_bin(n - 1)) ? 1 : 0;
+    a.count_flips = (early_stop || n == cap - 1) ? 1 : 0;
+}
+
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ float lse_sqrt_approx(float x)
 {
@@ -156,6 +204,23 @@ bool plan_step_tile(int H, int W, int B, int term, int rad, int sm_count,
 cudaError_t launch_step_tile(const StepArgs &a, const CUtensorMap &phi_map,
                              const CUtensorMap &data_map, int nblocks, cudaStream_t s);
 int partials_needed(int sm_count);
+
+// Batched launches (lse_evolve_batch): iteration n over every image of one
+// class; CTA blockIdx.x works on image blk_item[blockIdx.x].  Step kernels
+// of the tile form (one band, edge term) and of the streaming form.
+cudaError_t launch_step_tile_batch_region1(int rad, const BatchItem *items, const int *blk_item,
+                                           int n, int nblocks, cudaStream_t s);
+cudaError_t launch_step_tile_batch_edge(int rad, const BatchItem *items, const int *blk_item,
+                                        int n, int nblocks, cudaStream_t s);
+cudaError_t launch_step_tma_batch_region1(int rad, const BatchItem *items, const int *blk_item,
+                                          int n, int nblocks, int wpc, cudaStream_t s);
+cudaError_t launch_step_tma_batch_edge(int rad, const BatchItem *items, const int *blk_item,
+                                       int n, int nblocks, int wpc, cudaStream_t s);
+cudaError_t launch_step_tma_batch_multiband(int rad, const BatchItem *items,
+                                            const int *blk_item, int n, int nblocks, int wpc,
+                                            cudaStream_t s);
+cudaError_t launch_normaliser_batch(const BatchItem *items, const int *blk_item, int n,
+                                    int nblocks, cudaStream_t s);
 
 // Which step kernel a call runs.  LSE_STEP_KERNEL=generic or =stream at
 // context creation (at each call for lse_evolve_static) narrows the choice.

@@ -142,10 +142,10 @@ prologue_kernel(const void *__restrict__ img, int img_pitch, size_t band_stride,
 // M = max_x |sum_b alpha_b (I_b(x) - mid_b)| for B > 1, then the step
 // coefficients a_b = dt alpha_b / (2 M).  Skipped when the statistics already
 // made the force zero or the evolution has stopped.
-__global__ void __launch_bounds__(kThreads)
-normaliser_kernel(const float *__restrict__ img, int pitch, size_t band_stride,
-                  int H, int W, int B, float dt, LseDevState *st,
-                  LsePartial *partials)
+__device__ __forceinline__ void normaliser(const float *__restrict__ img, int pitch,
+                                           size_t band_stride, int H, int W, int B, float dt,
+                                           LseDevState *st, LsePartial *partials, int cta,
+                                           int ncta)
 {
     if (st->done || st->zero_force || (st->status_bits & LSE_SBIT_ABORT)) return;
     float af[LSE_MAXB], m[LSE_MAXB];
@@ -157,8 +157,8 @@ normaliser_kernel(const float *__restrict__ img, int pitch, size_t band_stride,
     LseAcc acc;
     acc.clear();
     const long long n = (long long)H * W;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-         p += (long long)gridDim.x * blockDim.x) {
+    for (long long p = cta * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)ncta * blockDim.x) {
         int y = (int)(p / W);
         int x = (int)(p - (long long)y * W);
         const float *src = img + (size_t)y * pitch + x;
@@ -171,9 +171,9 @@ normaliser_kernel(const float *__restrict__ img, int pitch, size_t band_stride,
     }
     LseAcc r;
     lse_cta_reduce(acc, 0, &r);
-    if (!lse_publish_and_ticket(r, 0, partials, st)) return;
+    if (!lse_publish_and_ticket_at(r, 0, partials, st, cta, ncta)) return;
     LseAcc t;
-    lse_sum_partials(partials, gridDim.x, 0, &t);
+    lse_sum_partials(partials, ncta, 0, &t);
     if (threadIdx.x == 0) {
         double M = fmax(fabs((double)t.fmax), fabs((double)t.fmin));
         st->norm = M;
@@ -187,6 +187,26 @@ normaliser_kernel(const float *__restrict__ img, int pitch, size_t band_stride,
         __threadfence();
         st->ticket = 0;
     }
+}
+
+__global__ void __launch_bounds__(kThreads)
+normaliser_kernel(const float *__restrict__ img, int pitch, size_t band_stride,
+                  int H, int W, int B, float dt, LseDevState *st,
+                  LsePartial *partials)
+{
+    normaliser(img, pitch, band_stride, H, W, B, dt, st, partials, blockIdx.x, gridDim.x);
+}
+
+// The normaliser of iteration n for a batch of vector images.
+__global__ void __launch_bounds__(kThreads)
+normaliser_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ blk_item,
+                        int n)
+{
+    const BatchItem &it = items[blk_item[blockIdx.x]];
+    if (n >= it.cap) return;
+    const StepArgs &a = it.args;
+    normaliser(a.data, a.pitch, a.band_stride, a.H, a.W, a.B, a.dt, a.st, a.partials,
+               blockIdx.x - it.nstart, it.nnblocks);
 }
 
 struct BufPair {
@@ -258,6 +278,13 @@ cudaError_t launch_normaliser(const float *img, int pitch, size_t band_stride,
     int grid = grid_for((long long)H * W, nblocks);
     normaliser_kernel<<<grid, kThreads, 0, s>>>(img, pitch, band_stride, H, W,
                                                 B, dt, st, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normaliser_batch(const BatchItem *items, const int *blk_item, int n,
+                                    int nblocks, cudaStream_t s)
+{
+    normaliser_batch_kernel<<<nblocks, kThreads, 0, s>>>(items, blk_item, n);
     return cudaGetLastError();
 }
 

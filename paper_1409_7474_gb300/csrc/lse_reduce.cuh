@@ -104,23 +104,32 @@ __device__ __forceinline__ void lse_store_partial(const LseAcc &r, int nb,
     p->bits = r.bits;
 }
 
-// Writes this CTA's partial and returns true in the CTA that finished last.
-// The CTA-wide result `r` is only meaningful in thread 0.
-__device__ __forceinline__ bool lse_publish_and_ticket(const LseAcc &r, int nb,
-                                                       LsePartial *partials,
-                                                       LseDevState *st)
+// Writes the partial of CTA `cta` of the `ncta` CTAs reducing into `st` and
+// returns true in the one that finished last.  The CTA-wide result `r` is
+// only meaningful in thread 0.
+__device__ __forceinline__ bool lse_publish_and_ticket_at(const LseAcc &r, int nb,
+                                                          LsePartial *partials,
+                                                          LseDevState *st, int cta, int ncta)
 {
     __shared__ int s_last;
     if (threadIdx.x == 0) {
-        lse_store_partial(r, nb, partials + blockIdx.x);
+        lse_store_partial(r, nb, partials + cta);
         __threadfence();
         unsigned int t = atomicAdd(&st->ticket, 1u);
-        s_last = (t == gridDim.x - 1);
+        s_last = (t == (unsigned int)ncta - 1);
     }
     __syncthreads();
     bool last = s_last != 0;
     if (last) __threadfence();
     return last;
+}
+
+// The same for a grid that reduces into one state record.
+__device__ __forceinline__ bool lse_publish_and_ticket(const LseAcc &r, int nb,
+                                                       LsePartial *partials,
+                                                       LseDevState *st)
+{
+    return lse_publish_and_ticket_at(r, nb, partials, st, blockIdx.x, gridDim.x);
 }
 
 // In the last CTA: sums all partials in CTA order into `total` (thread 0).

@@ -57,13 +57,6 @@ bool encode_box(CUtensorMap *m, const void *base, int storage, int W, int H, int
     return r == CUDA_SUCCESS;
 }
 
-bool reinit_after(int n, int period)
-{
-    if (period == 1) return true;
-    if (period <= 0) return false;
-    return ((n + 1) % period) == 0;
-}
-
 }  // namespace
 
 namespace lse_detail {
@@ -144,28 +137,11 @@ bool plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_
     return true;
 }
 
-// A re-initialising step other than the last stores sign(v) directly (the
-// TMA forms), unless an early stop may make it the last one; then it stores
-// v and the next step binarises on load.
-static bool stores_bin(const StepPlan &plan, int k)
-{
-    return plan.form != LSE_FORM_GENERIC && reinit_after(k, plan.reinit_period) &&
-           k < plan.iterations - 1 && !plan.early_stop;
-}
-
 cudaError_t launch_step(StepPlan &plan, int n, cudaStream_t s)
 {
     StepArgs &a = plan.args;
-    a.iter = n;
-    a.phi_in = plan.phi[n & 1];
-    a.phi_out = plan.phi[(n + 1) & 1];
-    a.out_buf = (n + 1) & 1;
-    a.store_bin = stores_bin(plan, n) ? 1 : 0;
-    a.binary_in = (n > 0 && stores_bin(plan, n - 1)) ? 1 : 0;
-    a.binarise_in =
-        (n > 0 && reinit_after(n - 1, plan.reinit_period) && !stores_bin(plan, n - 1)) ? 1 : 0;
-    // sign changes matter for the early stop and the last step's statistics
-    a.count_flips = (plan.early_stop || n == plan.iterations - 1) ? 1 : 0;
+    lse_iteration_flags(a, n, plan.iterations, plan.reinit_period, plan.early_stop,
+                        plan.form != LSE_FORM_GENERIC, plan.phi);
     switch (plan.form) {
     case LSE_FORM_TILE:
         return launch_step_tile(a, plan.phi_maps[n & 1], plan.data_map, plan.nblocks, s);

@@ -214,11 +214,11 @@ __device__ __forceinline__ float4 lds4(const float *p)
     return *reinterpret_cast<const float4 *>(p);
 }
 
+// One step over the tiles of one image, run by CTA `cta` of the `ncta` CTAs
+// given to it.
 template <int KIND_EDGE, int RAD, bool FAST, class T>
-__global__ void __launch_bounds__(kThreads, TileGeo<RAD, T>::MIN_BLOCKS)
-step_tile_kernel(const __grid_constant__ StepArgs a,
-                 const __grid_constant__ CUtensorMap phi_map,
-                 const __grid_constant__ CUtensorMap data_map)
+__device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *phi_map,
+                                          const CUtensorMap *data_map, int cta, int ncta)
 {
     using G = TileGeo<RAD, T>;
     using S = Stor<T>;
@@ -280,11 +280,11 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
     auto load_tile = [&](int t) {
         int xs, ys;
         origin(t, xs, ys);
-        tma_box(phi_dst, &phi_map, xs - 4, ys, bar_phi, kPhiBytes);
-        tma_box(dat_dst, &data_map, xs - G::DATA_X0, ys + 1, bar_dat, kDatBytes);
+        tma_box(phi_dst, phi_map, xs - 4, ys, bar_phi, kPhiBytes);
+        tma_box(dat_dst, data_map, xs - G::DATA_X0, ys + 1, bar_dat, kDatBytes);
     };
 
-    int t = blockIdx.x;
+    int t = cta;
     if (tid == 0 && t < n_tiles) load_tile(t);
     uint32_t par = 0;
     bool failed = false;
@@ -298,7 +298,7 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
     const T *dl = dat + G::DATA_X0 + 4 * lane;   // ... of a data row
     float *hl = hbase + G::H_COL0 + 4 * lane;    // ... of an h row
 
-    for (; t < n_tiles; t += gridDim.x) {
+    for (; t < n_tiles; t += ncta) {
         int xs, ys;
         origin(t, xs, ys);
         const int x0 = xs + 4 * lane;
@@ -556,7 +556,7 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
             cnt2 += (long long)fcnt + (long long)cv * rv;
         }
         __syncthreads();
-        const int tn = t + gridDim.x;
+        const int tn = t + ncta;
         if (tid == 0 && tn < n_tiles) load_tile(tn);
         par ^= 1u;
     }
@@ -576,10 +576,36 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
     const int nb = EDGE ? 0 : 1;
     LseAcc r;
     lse_cta_reduce(acc, nb, &r);
-    if (!lse_publish_and_ticket(r, nb, a.partials, st)) return;
+    if (!lse_publish_and_ticket_at(r, nb, a.partials, st, cta, ncta)) return;
     LseAcc tot;
-    lse_sum_partials(a.partials, gridDim.x, nb, &tot);
+    lse_sum_partials(a.partials, ncta, nb, &tot);
     if (threadIdx.x == 0) lse_step_finalize(a, tot);
+}
+
+template <int KIND_EDGE, int RAD, bool FAST, class T>
+__global__ void __launch_bounds__(kThreads, TileGeo<RAD, T>::MIN_BLOCKS)
+step_tile_kernel(const __grid_constant__ StepArgs a,
+                 const __grid_constant__ CUtensorMap phi_map,
+                 const __grid_constant__ CUtensorMap data_map)
+{
+    tile_step<KIND_EDGE, RAD, FAST, T>(a, &phi_map, &data_map, blockIdx.x, gridDim.x);
+}
+
+// Iteration n of a batch of images of one class (term, radius): CTA
+// blockIdx.x works on image blk_item[blockIdx.x] with that image's CTA
+// count, statistics and iteration cap; its per-iteration flags are derived
+// here, so the launches of a whole evolution can be captured in a graph.
+template <int KIND_EDGE, int RAD>
+__global__ void __launch_bounds__(kThreads, TileGeo<RAD, float>::MIN_BLOCKS)
+step_tile_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ blk_item,
+                       int n)
+{
+    const BatchItem &it = items[blk_item[blockIdx.x]];
+    if (n >= it.cap) return;
+    StepArgs a = it.args;
+    lse_iteration_flags(a, n, it.cap, it.reinit_period, it.early_stop != 0, true, it.phi);
+    tile_step<KIND_EDGE, RAD, false, float>(a, &it.phi_maps[n & 1], &it.data_map,
+                                            blockIdx.x - it.start, it.nblocks);
 }
 
 // FAST: the steady state of a re-initialising evolution.
@@ -620,5 +646,34 @@ cudaError_t launch_tile_kind(const StepArgs &a, const CUtensorMap &pm, const CUt
 
 // CTAs per SM the tile form runs at for a radius (its launch bounds).
 inline int tile_blocks_per_sm(int rad) { return rad <= 4 ? 3 : 2; }
+
+template <int KIND_EDGE, int RAD>
+cudaError_t launch_tile_batch_one(const BatchItem *items, const int *blk_item, int n,
+                                  int nblocks, cudaStream_t s)
+{
+    using G = TileGeo<RAD, float>;
+    auto kern = step_tile_batch_kernel<KIND_EDGE, RAD>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         G::BYTES);
+    if (e != cudaSuccess) return e;
+    kern<<<nblocks, kThreads, G::BYTES, s>>>(items, blk_item, n);
+    return cudaGetLastError();
+}
+
+template <int KIND_EDGE>
+cudaError_t launch_tile_batch(int rad, const BatchItem *items, const int *blk_item, int n,
+                              int nblocks, cudaStream_t s)
+{
+    switch (rad) {
+    case 1: return launch_tile_batch_one<KIND_EDGE, 1>(items, blk_item, n, nblocks, s);
+    case 2: return launch_tile_batch_one<KIND_EDGE, 2>(items, blk_item, n, nblocks, s);
+    case 3: return launch_tile_batch_one<KIND_EDGE, 3>(items, blk_item, n, nblocks, s);
+    case 4: return launch_tile_batch_one<KIND_EDGE, 4>(items, blk_item, n, nblocks, s);
+    case 5: return launch_tile_batch_one<KIND_EDGE, 5>(items, blk_item, n, nblocks, s);
+    case 6: return launch_tile_batch_one<KIND_EDGE, 6>(items, blk_item, n, nblocks, s);
+    case 7: return launch_tile_batch_one<KIND_EDGE, 7>(items, blk_item, n, nblocks, s);
+    default: return cudaErrorNotSupported;
+    }
+}
 
 }  // namespace lse_tile

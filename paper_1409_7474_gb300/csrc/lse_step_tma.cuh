@@ -172,11 +172,11 @@ __device__ __forceinline__ float comp(const float4 &v, int j)
 }
 
 // ---------------------------------------------------------------- kernel
+// One step over the strips of one image, run by CTA `cta` of the `ncta`
+// CTAs given to it.
 template <int KIND, int RAD, bool BIN>
-__global__ void __launch_bounds__(256, 2)
-step_tma_kernel(const __grid_constant__ StepArgs a,
-                const __grid_constant__ CUtensorMap phi_map,
-                const __grid_constant__ CUtensorMap data_map)
+__device__ __forceinline__ void tma_step(const StepArgs &a, const CUtensorMap *phi_map,
+                                         const CUtensorMap *data_map, int cta, int ncta)
 {
     using G = Geo<KIND, RAD>;
     using T = KindTraits<KIND>;
@@ -213,8 +213,8 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
     const int H = a.H, W = a.W, B = (KIND == K_REGION_MB) ? a.B : 1;
     const int th = a.th, NR = th + 2 * RAD + 2;
     const int n_per = (th + 2 * RAD) / P;    // u-rows per item = n_per * P
-    const int gw = blockIdx.x * wpc + warp;
-    const int NW = gridDim.x * wpc;
+    const int gw = cta * wpc + warp;
+    const int NW = ncta * wpc;
     const int my_items = a.n_items > gw ? (a.n_items - gw + NW - 1) / NW : 0;
     const int total_seq = my_items * NR;
     const uint32_t tx_bytes = kPhiBytes + kDataSlot * B;
@@ -254,11 +254,11 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
             const uint32_t dst = ring0 + (uint32_t)(p_stage * G::STAGE);
             fence_proxy_async();
             mbar_expect_tx(bar, tx_bytes);
-            tma_load_2d(dst + PHI * 4, &phi_map, p_xs - 4, p_y, bar);
+            tma_load_2d(dst + PHI * 4, phi_map, p_xs - 4, p_y, bar);
             if (KIND == K_REGION_MB)
-                tma_load_3d(dst, &data_map, p_xs, p_y, 0, bar);
+                tma_load_3d(dst, data_map, p_xs, p_y, 0, bar);
             else
-                tma_load_2d(dst, &data_map, p_xs, p_y, bar);
+                tma_load_2d(dst, data_map, p_xs, p_y, bar);
         }
         ++p_seq;
         ++p_y;
@@ -609,10 +609,34 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
     const int nb = T::REGION ? B : 0;
     LseAcc r;
     lse_cta_reduce(acc, nb, &r);
-    if (!lse_publish_and_ticket(r, nb, a.partials, st)) return;
+    if (!lse_publish_and_ticket_at(r, nb, a.partials, st, cta, ncta)) return;
     LseAcc tot;
-    lse_sum_partials(a.partials, gridDim.x, nb, &tot);
+    lse_sum_partials(a.partials, ncta, nb, &tot);
     if (threadIdx.x == 0) lse_step_finalize(a, tot);
+}
+
+template <int KIND, int RAD, bool BIN>
+__global__ void __launch_bounds__(256, 2)
+step_tma_kernel(const __grid_constant__ StepArgs a,
+                const __grid_constant__ CUtensorMap phi_map,
+                const __grid_constant__ CUtensorMap data_map)
+{
+    tma_step<KIND, RAD, BIN>(a, &phi_map, &data_map, blockIdx.x, gridDim.x);
+}
+
+// Iteration n of a batch of images of one class (term, bands, radius); see
+// step_tile_batch_kernel.
+template <int KIND, int RAD>
+__global__ void __launch_bounds__(256, 2)
+step_tma_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ blk_item,
+                      int n)
+{
+    const BatchItem &it = items[blk_item[blockIdx.x]];
+    if (n >= it.cap) return;
+    StepArgs a = it.args;
+    lse_iteration_flags(a, n, it.cap, it.reinit_period, it.early_stop != 0, true, it.phi);
+    tma_step<KIND, RAD, false>(a, &it.phi_maps[n & 1], &it.data_map, blockIdx.x - it.start,
+                               it.nblocks);
 }
 
 // ------------------------------------------------------------ launch
@@ -652,6 +676,35 @@ cudaError_t launch_kind(const StepArgs &a, const CUtensorMap &pm,
     case 5: return launch_one<KIND, 5>(a, pm, dm, nblocks, wpc, s);
     case 6: return launch_one<KIND, 6>(a, pm, dm, nblocks, wpc, s);
     case 7: return launch_one<KIND, 7>(a, pm, dm, nblocks, wpc, s);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+template <int KIND, int RAD>
+cudaError_t launch_batch_one(const BatchItem *items, const int *blk_item, int n, int nblocks,
+                             int wpc, cudaStream_t s)
+{
+    const int smem = smem_bytes<KIND, RAD>(wpc);
+    auto kern = step_tma_batch_kernel<KIND, RAD>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem);
+    if (e != cudaSuccess) return e;
+    kern<<<nblocks, 32 * wpc, smem, s>>>(items, blk_item, n);
+    return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t launch_batch_kind(int rad, const BatchItem *items, const int *blk_item, int n,
+                              int nblocks, int wpc, cudaStream_t s)
+{
+    switch (rad) {
+    case 1: return launch_batch_one<KIND, 1>(items, blk_item, n, nblocks, wpc, s);
+    case 2: return launch_batch_one<KIND, 2>(items, blk_item, n, nblocks, wpc, s);
+    case 3: return launch_batch_one<KIND, 3>(items, blk_item, n, nblocks, wpc, s);
+    case 4: return launch_batch_one<KIND, 4>(items, blk_item, n, nblocks, wpc, s);
+    case 5: return launch_batch_one<KIND, 5>(items, blk_item, n, nblocks, wpc, s);
+    case 6: return launch_batch_one<KIND, 6>(items, blk_item, n, nblocks, wpc, s);
+    case 7: return launch_batch_one<KIND, 7>(items, blk_item, n, nblocks, wpc, s);
     default: return cudaErrorNotSupported;
     }
 }

@@ -16,4 +16,11 @@ int step_tma_warp_bytes_edge(int rad)
     return lse_tma::warp_bytes_for<lse_tma::K_EDGE>(rad);
 }
 
+cudaError_t launch_step_tma_batch_edge(int rad, const BatchItem *items, const int *blk_item,
+                                       int n, int nblocks, int wpc, cudaStream_t s)
+{
+    return lse_tma::launch_batch_kind<lse_tma::K_EDGE>(rad, items, blk_item, n, nblocks, wpc,
+                                                      s);
+}
+
 }  // namespace lse_detail

@@ -72,6 +72,14 @@ class Stats(ctypes.Structure):
                 "status": STATUS_NAMES.get(self.status, str(self.status))}
 
 
+class Problem(ctypes.Structure):
+    """lse_problem: one image of lse_evolve_batch (device pointers)."""
+    _fields_ = [("image", ctypes.c_void_p), ("dtype", ctypes.c_int),
+                ("H", ctypes.c_int), ("W", ctypes.c_int), ("B", ctypes.c_int),
+                ("g", ctypes.c_void_p), ("phi0", ctypes.c_void_p), ("params", Params),
+                ("phi_out", ctypes.c_void_p), ("mask_out", ctypes.c_void_p)]
+
+
 _vp = ctypes.c_void_p
 _lib.lse_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int]
 _lib.lse_create.restype = ctypes.c_int
@@ -95,9 +103,13 @@ _lib.lse_evolve_static.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int
                                    ctypes.POINTER(Params), _vp, _vp, ctypes.POINTER(Stats),
                                    _vp]
 _lib.lse_evolve_static.restype = ctypes.c_int
+_lib.lse_evolve_batch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
+                                  ctypes.POINTER(Stats), _vp]
+_lib.lse_evolve_batch.restype = ctypes.c_int
 
 SYMBOLS = ("lse_create", "lse_destroy", "lse_last_error", "lse_precompute_edge",
-           "lse_evolve", "lse_get_stats", "lse_version", "lse_evolve_static")
+           "lse_evolve", "lse_get_stats", "lse_version", "lse_evolve_static",
+           "lse_evolve_batch")
 STATIC_MAX_PIXELS = 262144
 
 
@@ -253,6 +265,44 @@ class Context:
                              _stream_ptr(stream, self.device))
         self._check(rc)
         return phi_out, mask_out, (st.to_dict(B) if sync else None)
+
+    def evolve_batch(self, items, use_graph: bool = True, stream=None):
+        """lse_evolve_batch over `items`, a list of dicts with the keys of
+        ``evolve`` (image or g, phi0, term, dt, sigma, ts, iterations,
+        reinit_period, early_stop_frac, and optionally phi_out / mask_out),
+        all CUDA tensors.  Returns a list of (phi_out, mask_out, stats)."""
+        n = len(items)
+        probs = (Problem * n)()
+        outs = []
+        for i, it in enumerate(items):
+            term = it.get("term", "region")
+            term_code = TERM_REGION if term in ("region", TERM_REGION) else TERM_EDGE
+            phi0 = it["phi0"]
+            H, W = (int(d) for d in phi0.shape)
+            image = it.get("image") if term_code == TERM_REGION else None
+            if image is not None:
+                B, _, _ = _shape3(image)
+                dcode = _dtype_code(image)
+            else:
+                B, dcode = 1, F32
+            phi_out = it.get("phi_out")
+            if phi_out is None:
+                phi_out = torch.empty((H, W), dtype=torch.float32, device=phi0.device)
+            mask_out = it.get("mask_out")
+            if mask_out is None:
+                mask_out = torch.empty((H, W), dtype=torch.uint8, device=phi0.device)
+            p = Params(term_code, float(it.get("dt", 15.0)), float(it.get("sigma", 1.0)),
+                       int(it.get("ts", 9)), int(it.get("iterations", 200)),
+                       int(it.get("reinit_period", 1)), float(it.get("early_stop_frac", 0.0)),
+                       F32)
+            probs[i] = Problem(_ptr(image), dcode, H, W, B,
+                               _ptr(it.get("g")) if term_code == TERM_EDGE else None,
+                               _ptr(phi0), p, _ptr(phi_out), _ptr(mask_out))
+            outs.append((phi_out, mask_out, B))
+        st = (Stats * n)()
+        self._check(_lib.lse_evolve_batch(self._h, n, probs, 1 if use_graph else 0, st,
+                                          _stream_ptr(stream, self.device)))
+        return [(o[0], o[1], st[i].to_dict(o[2])) for i, o in enumerate(outs)]
 
     def stats(self, bands: int = 8) -> dict:
         st = Stats()

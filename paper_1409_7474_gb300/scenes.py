@@ -233,3 +233,37 @@ def tile_scene(side_h: int, side_w: int, bands: int, seed: int,
     img = levels[truth.astype(np.int64)].transpose(2, 0, 1)
     img = img + rng.normal(0.0, noise, size=img.shape)
     return img.astype(np.float32), (y0, x0, y0 + rh, x0 + rw)
+
+
+def batch_problems(n: int, seed: int, min_side: int = 128, max_side: int = 1024,
+                   cap_range=(100, 600), early_stop_frac: float = 1e-4):
+    """A work list of n independent images of uneven size (tile_scene).
+
+    Sides are log-uniform in [min_side, max_side] (height and width drawn
+    separately); half the images have one band and half four; half use the
+    region term and half the edge term; each has an iteration cap drawn
+    uniformly from cap_range (inclusive) and an early stop when fewer than
+    early_stop_frac * H * W pixels change sign.  phi0 is +1 inside a centred
+    circle of radius min(H, W) / 3 (region) or -1 inside a box 10 % of the
+    tile outside the object (edge).  Returns a list of dicts with the keys
+    image, phi0, term, iterations, early_stop_frac.
+    """
+    rng = np.random.default_rng(seed)
+    lo, hi = np.log(min_side), np.log(max_side)
+    out = []
+    for i in range(n):
+        H = int(round(np.exp(rng.uniform(lo, hi))))
+        W = int(round(np.exp(rng.uniform(lo, hi))))
+        bands = 1 if rng.random() < 0.5 else 4
+        term = "region" if rng.random() < 0.5 else "edge"
+        cap = int(rng.integers(cap_range[0], cap_range[1] + 1))
+        img, (y0, x0, y1, x1) = tile_scene(H, W, bands, seed=int(rng.integers(1 << 31)))
+        if term == "region":
+            phi0 = circle_phi(H, W, radius=min(H, W) / 3.0)
+        else:
+            my, mx = max(int(0.1 * H), 2), max(int(0.1 * W), 2)
+            phi0 = box_phi(H, W, [(max(y0 - my, 0), max(x0 - mx, 0),
+                                   min(y1 + my, H), min(x1 + mx, W))])
+        out.append({"image": img, "phi0": phi0, "term": term, "iterations": cap,
+                    "early_stop_frac": early_stop_frac})
+    return out

@@ -54,6 +54,20 @@ def test_struct_layout_matches_header(lse, tmp_path):
                     lse.Stats.status.offset]
 
 
+def test_problem_layout_matches_header(lse, tmp_path):
+    src = tmp_path / "problem.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "lse.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(lse_problem),"
+        " offsetof(lse_problem, g), offsetof(lse_problem, params),"
+        " offsetof(lse_problem, phi_out), offsetof(lse_problem, mask_out));return 0;}\n")
+    exe = tmp_path / "problem"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert vals == [ctypes.sizeof(lse.Problem), lse.Problem.g.offset, lse.Problem.params.offset,
+                    lse.Problem.phi_out.offset, lse.Problem.mask_out.offset]
+
+
 def test_version_and_errors_without_gpu(lse):
     lib = lse.raw_library()
     assert lse.version() == "0.1.0"
@@ -69,6 +83,7 @@ def test_version_and_errors_without_gpu(lse):
                                    None, None) == lse.LSE_ERR_INVALID_ARG
     st = lse.Stats()
     assert lib.lse_get_stats(None, ctypes.byref(st)) == lse.LSE_ERR_INVALID_ARG
+    assert lib.lse_evolve_batch(None, 1, None, 1, None, None) == lse.LSE_ERR_INVALID_ARG
     lib.lse_destroy(None)
 
 

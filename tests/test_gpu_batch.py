@@ -1,0 +1,152 @@
+"""lse_evolve_batch: uneven images advanced together, vs lse_evolve alone and
+vs the FP64 oracle.
+
+Every image of a batch keeps its own planes, statistics, CTA count,
+iteration cap and early stop, so its results must equal lse_evolve's on the
+same image bit for bit, with and without CUDA-graph capture.  lse_evolve is
+itself held to the oracle by the parity tests; a few small batch images are
+also compared with the oracle directly (mask parity, the early stop's
+iteration count).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from _parity import assert_mask_parity
+from paper_1409_7474_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need CUDA"
+    return t
+
+
+@pytest.fixture(scope="module")
+def lse():
+    import paper_1409_7474_gb300.lse as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(lse, torch):
+    c = lse.Context(0, max_pixels=1024 * 1024, max_bands=4)
+    yield c
+    c.destroy()
+
+
+def device_items(torch, ctx, probs):
+    """The work list on the device; the edge images get g from the library."""
+    items = []
+    for q in probs:
+        img = torch.from_numpy(q["image"]).cuda()
+        it = {"phi0": torch.from_numpy(q["phi0"]).cuda(), "term": q["term"],
+              "iterations": q["iterations"], "early_stop_frac": q["early_stop_frac"]}
+        if q["term"] == "region":
+            it["image"] = img
+        else:
+            it["g"] = ctx.precompute_edge(img, 1.0, 9, 255.0)
+        items.append(it)
+    torch.cuda.synchronize()
+    return items
+
+
+def single(torch, ctx, it):
+    v, m, st = ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
+                          iterations=it["iterations"],
+                          early_stop_frac=it["early_stop_frac"])
+    torch.cuda.synchronize()
+    return v.cpu().numpy(), m.cpu().numpy(), st
+
+
+def same_bits(a, b):
+    return np.array_equal(np.asarray(a).view(np.uint32), np.asarray(b).view(np.uint32))
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_equals_single_calls(torch, ctx, use_graph):
+    probs = scenes.batch_problems(24, seed=11, min_side=40, max_side=400, cap_range=(3, 40))
+    for k, q in enumerate(probs):        # half with the early stop, half without
+        if k % 2:
+            q["early_stop_frac"] = 0.0
+    items = device_items(torch, ctx, probs)
+    res = ctx.evolve_batch(items, use_graph=use_graph)
+    torch.cuda.synchronize()
+    for it, (v, m, st) in zip(items, res):
+        v1, m1, st1 = single(torch, ctx, it)
+        assert same_bits(v.cpu().numpy(), v1)
+        assert np.array_equal(m.cpu().numpy(), m1)
+        for key in ("iterations_run", "last_flips", "area_plus", "status"):
+            assert st[key] == st1[key], key
+        assert st["c_plus"] == st1["c_plus"] and st["c_minus"] == st1["c_minus"]
+
+
+def test_batch_against_oracle(torch, ctx):
+    probs = scenes.batch_problems(6, seed=5, min_side=48, max_side=160, cap_range=(10, 30))
+    items = device_items(torch, ctx, probs)
+    res = ctx.evolve_batch(items, use_graph=True)
+    torch.cuda.synchronize()
+    for q, (v, m, st) in zip(probs, res):
+        if q["term"] == "region":
+            _, m_ref, st_ref = oracle.evolve(q["image"], q["phi0"], iterations=q["iterations"],
+                                             early_stop_frac=q["early_stop_frac"])
+        else:
+            g = oracle.edge_indicator(q["image"], 1.0, 9, 255.0)
+            _, m_ref, st_ref = oracle.evolve(q["image"], q["phi0"], term="edge", g=g,
+                                             iterations=q["iterations"],
+                                             early_stop_frac=q["early_stop_frac"])
+        assert st["iterations_run"] == st_ref["iterations_run"]
+        assert_mask_parity(m.cpu().numpy(), m_ref)
+
+
+def test_uneven_caps_and_early_stop(torch, ctx):
+    """Images stop at their own caps; a converged image stops early while the
+    others go on."""
+    img, truth, _ = scenes.rect_scene(noise=0.0)
+    phi_t = np.where(truth, 1.0, -1.0).astype(np.float32)
+    img2, _, _ = scenes.rect_scene(96, 128, 40, 30)
+    x, x2 = torch.from_numpy(img).cuda(), torch.from_numpy(img2).cuda()
+    items = [
+        {"image": x, "phi0": torch.from_numpy(phi_t).cuda(), "iterations": 50,
+         "early_stop_frac": 1e-4},
+        {"image": x2, "phi0": torch.from_numpy(scenes.circle_phi(96, 128, radius=30)).cuda(),
+         "iterations": 7},
+        {"image": x2, "phi0": torch.from_numpy(scenes.circle_phi(96, 128, radius=30)).cuda(),
+         "iterations": 13},
+    ]
+    res = ctx.evolve_batch(items)
+    torch.cuda.synchronize()
+    assert [r[2]["iterations_run"] for r in res] == [1, 7, 13]
+    assert np.array_equal(res[0][1].cpu().numpy().astype(bool), truth)
+    _, m7, _ = oracle.evolve(img2, scenes.circle_phi(96, 128, radius=30), iterations=7)
+    assert_mask_parity(res[1][1].cpu().numpy(), m7)
+
+
+def test_batch_rejections(torch, lse, ctx):
+    lib = lse.raw_library()
+    x = torch.rand((1, 64, 64), device="cuda")
+    phi = torch.ones((64, 64), device="cuda")
+    out = torch.empty_like(phi)
+
+    def run(image, params, phi0=phi):
+        probs = (lse.Problem * 1)()
+        probs[0] = lse.Problem(ctypes.c_void_p(image.data_ptr()), lse.F32, 64, 64, 1, None,
+                               ctypes.c_void_p(phi0.data_ptr()), params,
+                               ctypes.c_void_p(out.data_ptr()), None)
+        return lib.lse_evolve_batch(ctx._h, 1, probs, 1, None, None)
+
+    ok = lse.Params(lse.TERM_REGION, 15.0, 1.0, 9, 3, 1, 0.0, lse.F32)
+    assert run(x, ok) == lse.LSE_OK
+    big_ts = lse.Params(lse.TERM_REGION, 15.0, 1.0, 17, 3, 1, 0.0, lse.F32)
+    assert run(x, big_ts) == lse.LSE_ERR_INVALID_ARG
+    assert b"plain step kernel" in lib.lse_last_error(ctx._h)
+    half = lse.Params(lse.TERM_REGION, 15.0, 1.0, 9, 3, 1, 0.0, lse.BF16)
+    assert run(x, half) == lse.LSE_ERR_INVALID_ARG
+    host_phi = torch.ones((64, 64))
+    assert run(x, ok, phi0=host_phi) == lse.LSE_ERR_INVALID_ARG
+    assert b"device memory" in lib.lse_last_error(ctx._h)
