@@ -19,7 +19,10 @@ Reported (one JSON line on rank 0):
                term and the LSF (FP32 arithmetic, 6 B/px per region step);
   batch        256 uneven images (sides 128-1024, caps 100-600, early stop)
                through lse_evolve_batch with and without a CUDA graph, and
-               one lse_evolve call per image in sequence.
+               one lse_evolve call per image in sequence;
+  serve        Poisson-arriving requests through lse_server (continuous
+               batching in a 40 GiB budget) against one lse_evolve call per
+               request: p50 / p99 latency and requests/s.
 `--impl reference` times the FP64 oracle alone (the reference arm).
 Under torchrun each rank runs its own replica (no collective on the data
 path): weak scaling.
@@ -66,6 +69,10 @@ def parse():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched uneven-image measurement")
     ap.add_argument("--batch-images", type=int, default=256)
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the continuous-batching serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=96)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     return ap.parse_args()
 
 
@@ -222,6 +229,101 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def serve_measurement(torch, lse, dev, n_req: int, rate: float, seed: int = 9,
+                      ticks: int = 16, budget: int = 40 << 30):
+    """Requests arriving as a Poisson process (rate per second) of uneven
+    images (sides 256-2048, 1 or 4 bands, region or edge term, caps
+    100-600, early stop at 1e-4 of the pixels), replayed in real time:
+    through lse_server (continuous batching, `ticks` iterations per advance,
+    a `budget`-byte memory budget), and one lse_evolve call per request in
+    arrival order.  Latency = completion - arrival; throughput = requests
+    over the makespan."""
+    import time
+    from paper_1409_7474_gb300 import scenes
+    distinct = max(n_req // 2, 1)
+    probs = scenes.batch_problems(distinct, seed=seed, min_side=256, max_side=2048)
+    ctx = lse.Context(dev.index, max_pixels=2048 * 2048, max_bands=4)
+    base = []
+    for q in probs:
+        img = torch.from_numpy(q["image"]).to(dev)
+        it = {"phi0": torch.from_numpy(q["phi0"]).to(dev), "term": q["term"],
+              "iterations": q["iterations"], "early_stop_frac": q["early_stop_frac"]}
+        if q["term"] == "region":
+            it["image"] = img
+        else:
+            it["g"] = ctx.precompute_edge(img, 1.0, 9, 255.0)
+        base.append(it)
+    items = []
+    for k in range(n_req):
+        it = dict(base[k % distinct])
+        H, W = it["phi0"].shape
+        it["phi_out"] = torch.empty((H, W), dtype=torch.float32, device=dev)
+        it["mask_out"] = torch.empty((H, W), dtype=torch.uint8, device=dev)
+        items.append(it)
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    px_it_cap = sum(int(it["phi0"].numel()) * it["iterations"] for it in items)
+    torch.cuda.synchronize()
+
+    def wait_until(t0, t):
+        while time.perf_counter() - t0 < t:
+            pass
+
+    # warm-up of both paths (modules, scratch)
+    sv = lse.Server(ctx, budget)
+    sv.submit(dict(items[0], iterations=2))
+    while sv.advance(2):
+        pass
+    ctx.evolve(items[0].get("image"), items[0]["phi0"], items[0]["term"], g=items[0].get("g"),
+               iterations=2)
+    torch.cuda.synchronize()
+
+    # continuous batching
+    done = np.zeros(n_req)
+    t0 = time.perf_counter()
+    k, live = 0, {}
+    while len(live) or k < n_req:
+        now = time.perf_counter() - t0
+        while k < n_req and arrivals[k] <= now:
+            live[sv.submit(items[k])] = k
+            k += 1
+        if not live:
+            wait_until(t0, arrivals[k])
+            continue
+        sv.advance(ticks)
+        for rid in list(live):
+            if sv.poll(rid) is not None:
+                done[live.pop(rid)] = time.perf_counter() - t0
+    lat_s = done - arrivals
+    span_s = done.max() - arrivals[0]
+    sv.destroy()
+
+    # one request at a time
+    done_q = np.zeros(n_req)
+    t0 = time.perf_counter()
+    for k, it in enumerate(items):
+        wait_until(t0, arrivals[k])
+        ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
+                   iterations=it["iterations"], early_stop_frac=it["early_stop_frac"],
+                   phi_out=it["phi_out"], mask_out=it["mask_out"])
+        done_q[k] = time.perf_counter() - t0
+    lat_q = done_q - arrivals
+    span_q = done_q.max() - arrivals[0]
+    ctx.destroy()
+
+    def summary(lat, span):
+        return {"p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "requests_per_s": n_req / span, "makespan_s": float(span)}
+
+    return {"workload": f"{n_req} requests, Poisson arrivals at {rate:g}/s; sides "
+                        "log-uniform 256-2048, 1 or 4 bands, region or edge term, caps "
+                        "U{100..600}, early stop 1e-4; FP32 storage; "
+                        f"budget {budget >> 30} GiB; {ticks} iterations per advance",
+            "pixel_iterations_at_caps": px_it_cap,
+            "server": summary(lat_s, span_s), "sequential": summary(lat_q, span_q)}
+
+
 def batch_measurement(torch, lse, dev, n_images: int, seed: int = 3):
     """The uneven-image work list (sides 128-1024, 1 or 4 bands, region or
     edge term, caps 100-600, early stop at 1e-4 of the pixels) run three
@@ -471,6 +573,9 @@ def main():
     batch = None
     if not args.no_batch:
         batch = batch_measurement(torch, lse, dev, args.batch_images)
+    serve = None
+    if not args.no_serve and world == 1:
+        serve = serve_measurement(torch, lse, dev, args.serve_requests, args.serve_rate)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -490,7 +595,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks.summary(), "gpu_launches": launches,
-                "storage_variants": variants, "batch": batch,
+                "storage_variants": variants, "batch": batch, "serve": serve,
                 "impl": "gb300",
                 "stats": {"region": {k: st_r[k] for k in ("iterations_run", "status",
                                                           "last_flips", "area_plus")},

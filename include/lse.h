@@ -284,6 +284,44 @@ typedef struct {
 lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems,
                             int use_graph, lse_stats *stats, void *stream);
 
+/* ------------------------------------------------------------ serving
+ * A server runs evolution requests with continuous batching (the paper has
+ * no counterpart).  Requests are queued on submission and admitted, first
+ * come first served, while their planes fit the server's device-memory
+ * budget; every lse_server_advance call then runs the next iterations of all
+ * admitted requests together (in the launches lse_evolve_batch uses) and
+ * retires those that reached their cap or stopped early, writing their
+ * phi_out / mask_out.  A request's result is bit for bit that of lse_evolve
+ * on the same image, whatever else runs beside it.  One server belongs to
+ * one context; its calls are not thread-safe. */
+typedef struct lse_server lse_server;
+
+/* Creates a server on ctx's GPU whose requests share budget_bytes (>= 1 MiB)
+ * of device memory, allocated here.  Returns LSE_ERR_OOM when that fails. */
+lse_status lse_server_create(lse_ctx *ctx, size_t budget_bytes, lse_server **out);
+
+/* Waits for the device, then frees the server (NULL is ignored).  Requests
+ * still queued or running are dropped. */
+void lse_server_destroy(lse_server *sv);
+
+/* Queues one request and returns its id (> 0).  The request's buffers (as
+ * lse_problem: device memory of the context's GPU) must stay valid until
+ * lse_server_poll reports it done.  Returns LSE_ERR_INVALID_ARG for
+ * lse_evolve's argument errors, host memory, storage other than LSE_F32,
+ * ts > 15, more than 4 bands, or a request larger than the budget. */
+lse_status lse_server_submit(lse_server *sv, const lse_problem *problem, long long *id);
+
+/* Admits queued requests that fit, runs `ticks` iterations of every running
+ * request on `stream`, retires the finished ones, and synchronises the
+ * stream.  *running (may be NULL) receives the number of requests still
+ * running. */
+lse_status lse_server_advance(lse_server *sv, int ticks, int *running, void *stream);
+
+/* *state = 0 queued, 1 running, 2 done.  When done, *stats (may be NULL)
+ * receives the request's statistics (elapsed_ms = -1) and the server forgets
+ * the request: a later poll of the id returns LSE_ERR_INVALID_ARG. */
+lse_status lse_server_poll(lse_server *sv, long long id, int *state, lse_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

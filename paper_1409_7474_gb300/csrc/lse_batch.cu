@@ -17,6 +17,7 @@
 #include <tuple>
 #include <vector>
 
+#include "lse_classes.h"
 #include "lse_ctx.h"
 
 using namespace lse_detail;
@@ -54,50 +55,88 @@ struct Layout {
     size_t data, phi0, phi1;    // byte offsets in the arena
 };
 
-// A class of images served by one step kernel instantiation.
-struct ClassKey {
-    int form, term, bands, rad, wpc;
-    bool operator<(const ClassKey &o) const
-    {
-        return std::tie(form, term, bands, rad, wpc) <
-               std::tie(o.form, o.term, o.bands, o.rad, o.wpc);
-    }
-};
+}  // namespace
 
-struct Class {
-    std::vector<int> items;
-    int nblocks = 0;            // step CTAs
-    int nnblocks = 0;           // normaliser CTAs (vector region images)
-    size_t blk_off = 0, nblk_off = 0;   // byte offsets of the CTA tables
-};
+namespace lse_detail {
 
-int grid_for(long long n, int cap)
+ClassKey class_of(const StepPlan &plan, int term, int bands)
 {
-    long long blocks = (n + 255) / 256;
-    if (blocks < 1) blocks = 1;
-    return (int)(blocks < cap ? blocks : cap);
+    return ClassKey{plan.form, term, bands, plan.args.rad, plan.wpc};
+}
+
+size_t layout_classes(ClassMap &classes, BatchItem *items)
+{
+    size_t toff = 0;
+    for (auto &kc : classes) {
+        Class &c = kc.second;
+        std::stable_sort(c.items.begin(), c.items.end(), [&](int a, int b) {
+            return items[a].iter0 + items[a].cap > items[b].iter0 + items[b].cap;
+        });
+        c.ends.clear();
+        c.pre.assign(1, 0);
+        c.npre.assign(1, 0);
+        c.nblocks = c.nnblocks = 0;
+        for (int i : c.items) {
+            BatchItem &it = items[i];
+            it.start = c.nblocks;
+            c.nblocks += it.nblocks;
+            it.nstart = c.nnblocks;
+            c.nnblocks += it.nnblocks;
+            c.ends.push_back(it.iter0 + it.cap);
+            c.pre.push_back(c.nblocks);
+            c.npre.push_back(c.nnblocks);
+        }
+        c.blk_off = toff;
+        toff = align_up(toff + sizeof(int) * c.nblocks);
+        c.nblk_off = toff;
+        toff = align_up(toff + sizeof(int) * c.nnblocks);
+    }
+    return toff;
+}
+
+void fill_tables(const ClassMap &classes, const BatchItem *items, unsigned char *host_tables)
+{
+    for (auto &kc : classes) {
+        int *blk = reinterpret_cast<int *>(host_tables + kc.second.blk_off);
+        int *nblk = reinterpret_cast<int *>(host_tables + kc.second.nblk_off);
+        for (int i : kc.second.items) {
+            for (int b = 0; b < items[i].nblocks; ++b) blk[items[i].start + b] = i;
+            for (int b = 0; b < items[i].nnblocks; ++b) nblk[items[i].nstart + b] = i;
+        }
+    }
 }
 
 cudaError_t launch_class(const ClassKey &k, const Class &c, const BatchItem *items,
-                         const unsigned char *tables, int n, cudaStream_t s)
+                         const unsigned char *tables, long long n, cudaStream_t s, int k_act)
 {
+    if (k_act < 0) k_act = (int)c.items.size();
+    const int nb = c.pre[k_act], nnb = c.npre[k_act];
+    if (nb == 0) return cudaSuccess;
     const int *blk = reinterpret_cast<const int *>(tables + c.blk_off);
     if (k.form == LSE_FORM_TILE) {
         return k.term == LSE_TERM_EDGE
-                   ? launch_step_tile_batch_edge(k.rad, items, blk, n, c.nblocks, s)
-                   : launch_step_tile_batch_region1(k.rad, items, blk, n, c.nblocks, s);
+                   ? launch_step_tile_batch_edge(k.rad, items, blk, n, nb, s)
+                   : launch_step_tile_batch_region1(k.rad, items, blk, n, nb, s);
     }
     if (k.term == LSE_TERM_EDGE)
-        return launch_step_tma_batch_edge(k.rad, items, blk, n, c.nblocks, k.wpc, s);
+        return launch_step_tma_batch_edge(k.rad, items, blk, n, nb, k.wpc, s);
     if (k.bands == 1)
-        return launch_step_tma_batch_region1(k.rad, items, blk, n, c.nblocks, k.wpc, s);
+        return launch_step_tma_batch_region1(k.rad, items, blk, n, nb, k.wpc, s);
     const int *nblk = reinterpret_cast<const int *>(tables + c.nblk_off);
-    cudaError_t e = launch_normaliser_batch(items, nblk, n, c.nnblocks, s);
+    cudaError_t e = launch_normaliser_batch(items, nblk, n, nnb, s);
     if (e != cudaSuccess) return e;
-    return launch_step_tma_batch_multiband(k.rad, items, blk, n, c.nblocks, k.wpc, s);
+    return launch_step_tma_batch_multiband(k.rad, items, blk, n, nb, k.wpc, s);
 }
 
-}  // namespace
+int normaliser_blocks(long long npix, int sm_count)
+{
+    long long blocks = (npix + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    const int cap = sm_count * 4;
+    return (int)(blocks < cap ? blocks : cap);
+}
+
+}  // namespace lse_detail
 
 extern "C" {
 
@@ -181,8 +220,7 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
 
     // ---- staging and prologue of every image; the plan of its step
     std::vector<BatchItem> items(n);
-    std::map<ClassKey, Class> classes;
-    std::vector<ClassKey> key_of(n);
+    ClassMap classes;
     const int nred = ctx->sm_count * 4;
     for (int i = 0; i < n; ++i) {
         const lse_problem &q = problems[i];
@@ -224,43 +262,21 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
         it.cap = p.iterations;
         it.reinit_period = p.reinit_period;
         it.early_stop = p.early_stop_frac > 0.0f;
-        const int bands = region ? q.B : 1;
-        ClassKey k{plan.form, p.term, bands, plan.args.rad, plan.wpc};
-        key_of[i] = k;
-        Class &c = classes[k];
-        it.start = c.nblocks;
-        c.nblocks += it.nblocks;
-        if (region && q.B > 1) {
-            it.nnblocks = grid_for((long long)q.H * q.W, nred);
-            it.nstart = c.nnblocks;
-            c.nnblocks += it.nnblocks;
-        }
-        c.items.push_back(i);
+        it.iter0 = 0;
+        if (region && q.B > 1) it.nnblocks = normaliser_blocks((long long)q.H * q.W, ctx->sm_count);
+        classes[class_of(plan, p.term, region ? q.B : 1)].items.push_back(i);
     }
 
     // ---- CTA tables and the work list, uploaded once
-    size_t toff = 0;
-    for (auto &kc : classes) {
-        kc.second.blk_off = toff;
-        toff = align_up(toff + sizeof(int) * kc.second.nblocks);
-        kc.second.nblk_off = toff;
-        toff = align_up(toff + sizeof(int) * kc.second.nnblocks);
-    }
+    const size_t toff = layout_classes(classes, items.data());
     if ((r = ensure(ctx, &ctx->tables, &ctx->tables_cap, toff, s, "batch tables")) != LSE_OK)
         return r;
     const size_t hbytes = align_up(sizeof(BatchItem) * n) + toff + sizeof(LseDevState) * n;
     if ((r = ensure_host(ctx, hbytes, s)) != LSE_OK) return r;
     unsigned char *Hh = static_cast<unsigned char *>(ctx->bhost);
-    memcpy(Hh, items.data(), sizeof(BatchItem) * n);
     unsigned char *ht = Hh + align_up(sizeof(BatchItem) * n);
-    for (auto &kc : classes) {
-        int *blk = reinterpret_cast<int *>(ht + kc.second.blk_off);
-        int *nblk = reinterpret_cast<int *>(ht + kc.second.nblk_off);
-        for (int i : kc.second.items) {
-            for (int b = 0; b < items[i].nblocks; ++b) blk[items[i].start + b] = i;
-            for (int b = 0; b < items[i].nnblocks; ++b) nblk[items[i].nstart + b] = i;
-        }
-    }
+    fill_tables(classes, items.data(), ht);
+    memcpy(Hh, items.data(), sizeof(BatchItem) * n);
     e = cudaMemcpyAsync(d_items, Hh, sizeof(BatchItem) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && toff)
         e = cudaMemcpyAsync(ctx->tables, ht, toff, cudaMemcpyHostToDevice, s);
@@ -270,10 +286,11 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
     // ---- the iteration loop: one launch per class and iteration
     int maxcap = 0;
     for (int i = 0; i < n; ++i) maxcap = std::max(maxcap, problems[i].params.iterations);
-    auto enqueue_loop = [&]() -> cudaError_t {
+    auto enqueue_loop = [&](cudaStream_t q) -> cudaError_t {
         for (int it = 0; it < maxcap; ++it)
             for (auto &kc : classes) {
-                cudaError_t le = launch_class(kc.first, kc.second, d_items, tables, it, s);
+                cudaError_t le = launch_class(kc.first, kc.second, d_items, tables, it, q,
+                                              kc.second.active(it));
                 if (le != cudaSuccess) return le;
             }
         return cudaSuccess;
@@ -296,12 +313,7 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
         cudaStream_t cs = ctx->cap_stream;
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t le = cudaSuccess;
-            for (int it = 0; it < maxcap && le == cudaSuccess; ++it)
-                for (auto &kc : classes) {
-                    le = launch_class(kc.first, kc.second, d_items, tables, it, cs);
-                    if (le != cudaSuccess) break;
-                }
+            cudaError_t le = enqueue_loop(cs);
             e = cudaStreamEndCapture(cs, &graph);
             if (le != cudaSuccess) e = le;
         }
@@ -312,7 +324,7 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
         }
     }
     e = cudaEventRecord(ctx->ev0, s);
-    if (e == cudaSuccess) e = use_graph ? cudaGraphLaunch(exec, s) : enqueue_loop();
+    if (e == cudaSuccess) e = use_graph ? cudaGraphLaunch(exec, s) : enqueue_loop(s);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev1, s);
     if (e != cudaSuccess) {
         if (exec) cudaGraphExecDestroy(exec);

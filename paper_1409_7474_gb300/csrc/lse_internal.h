@@ -91,9 +91,10 @@ struct StepArgs {
     int n_items;
 };
 
-// One image of a batched evolution (lse_evolve_batch), in device memory.
-// The CTAs [start, start + nblocks) of its class's step launch work on it;
-// vector images also own the normaliser CTAs [nstart, nstart + nnblocks).
+// One image of a batched evolution (lse_evolve_batch, lse_server), in device
+// memory.  The CTAs [start, start + nblocks) of its class's step launch work
+// on it; vector images also own the normaliser CTAs [nstart, nstart +
+// nnblocks).  Launch index t runs the image's iteration t - iter0.
 struct alignas(64) BatchItem {
     CUtensorMap phi_maps[2];    // tensor maps of phi[0], phi[1]
     CUtensorMap data_map;
@@ -104,6 +105,7 @@ struct alignas(64) BatchItem {
     int reinit_period;
     int early_stop;
     int nstart, nnblocks;
+    long long iter0;            // launch index of the image's iteration 0
 };
 
 // Re-initialisation after iteration n (0-based) with period `period`
@@ -209,17 +211,17 @@ int partials_needed(int sm_count);
 // class; CTA blockIdx.x works on image blk_item[blockIdx.x].  Step kernels
 // of the tile form (one band, edge term) and of the streaming form.
 cudaError_t launch_step_tile_batch_region1(int rad, const BatchItem *items, const int *blk_item,
-                                           int n, int nblocks, cudaStream_t s);
+                                           long long n, int nblocks, cudaStream_t s);
 cudaError_t launch_step_tile_batch_edge(int rad, const BatchItem *items, const int *blk_item,
-                                        int n, int nblocks, cudaStream_t s);
+                                        long long n, int nblocks, cudaStream_t s);
 cudaError_t launch_step_tma_batch_region1(int rad, const BatchItem *items, const int *blk_item,
-                                          int n, int nblocks, int wpc, cudaStream_t s);
+                                          long long n, int nblocks, int wpc, cudaStream_t s);
 cudaError_t launch_step_tma_batch_edge(int rad, const BatchItem *items, const int *blk_item,
-                                       int n, int nblocks, int wpc, cudaStream_t s);
+                                       long long n, int nblocks, int wpc, cudaStream_t s);
 cudaError_t launch_step_tma_batch_multiband(int rad, const BatchItem *items,
-                                            const int *blk_item, int n, int nblocks, int wpc,
+                                            const int *blk_item, long long n, int nblocks, int wpc,
                                             cudaStream_t s);
-cudaError_t launch_normaliser_batch(const BatchItem *items, const int *blk_item, int n,
+cudaError_t launch_normaliser_batch(const BatchItem *items, const int *blk_item, long long n,
                                     int nblocks, cudaStream_t s);
 
 // Which step kernel a call runs.  LSE_STEP_KERNEL=generic or =stream at

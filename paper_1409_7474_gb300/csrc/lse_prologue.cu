@@ -200,10 +200,11 @@ normaliser_kernel(const float *__restrict__ img, int pitch, size_t band_stride,
 // The normaliser of iteration n for a batch of vector images.
 __global__ void __launch_bounds__(kThreads)
 normaliser_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ blk_item,
-                        int n)
+                        long long launch)
 {
     const BatchItem &it = items[blk_item[blockIdx.x]];
-    if (n >= it.cap) return;
+    const long long nl = launch - it.iter0;
+    if (nl < 0 || nl >= it.cap) return;
     const StepArgs &a = it.args;
     normaliser(a.data, a.pitch, a.band_stride, a.H, a.W, a.B, a.dt, a.st, a.partials,
                blockIdx.x - it.nstart, it.nnblocks);
@@ -281,7 +282,7 @@ cudaError_t launch_normaliser(const float *img, int pitch, size_t band_stride,
     return cudaGetLastError();
 }
 
-cudaError_t launch_normaliser_batch(const BatchItem *items, const int *blk_item, int n,
+cudaError_t launch_normaliser_batch(const BatchItem *items, const int *blk_item, long long n,
                                     int nblocks, cudaStream_t s)
 {
     normaliser_batch_kernel<<<nblocks, kThreads, 0, s>>>(items, blk_item, n);

@@ -598,10 +598,12 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
 template <int KIND_EDGE, int RAD>
 __global__ void __launch_bounds__(kThreads, TileGeo<RAD, float>::MIN_BLOCKS)
 step_tile_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ blk_item,
-                       int n)
+                       long long launch)
 {
     const BatchItem &it = items[blk_item[blockIdx.x]];
-    if (n >= it.cap) return;
+    const long long nl = launch - it.iter0;
+    if (nl < 0 || nl >= it.cap) return;
+    const int n = (int)nl;
     StepArgs a = it.args;
     lse_iteration_flags(a, n, it.cap, it.reinit_period, it.early_stop != 0, true, it.phi);
     tile_step<KIND_EDGE, RAD, false, float>(a, &it.phi_maps[n & 1], &it.data_map,
@@ -648,7 +650,7 @@ cudaError_t launch_tile_kind(const StepArgs &a, const CUtensorMap &pm, const CUt
 inline int tile_blocks_per_sm(int rad) { return rad <= 4 ? 3 : 2; }
 
 template <int KIND_EDGE, int RAD>
-cudaError_t launch_tile_batch_one(const BatchItem *items, const int *blk_item, int n,
+cudaError_t launch_tile_batch_one(const BatchItem *items, const int *blk_item, long long n,
                                   int nblocks, cudaStream_t s)
 {
     using G = TileGeo<RAD, float>;
@@ -661,7 +663,7 @@ cudaError_t launch_tile_batch_one(const BatchItem *items, const int *blk_item, i
 }
 
 template <int KIND_EDGE>
-cudaError_t launch_tile_batch(int rad, const BatchItem *items, const int *blk_item, int n,
+cudaError_t launch_tile_batch(int rad, const BatchItem *items, const int *blk_item, long long n,
                               int nblocks, cudaStream_t s)
 {
     switch (rad) {

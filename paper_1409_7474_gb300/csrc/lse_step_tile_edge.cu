@@ -10,7 +10,7 @@ cudaError_t launch_step_tile_edge(const StepArgs &a, const CUtensorMap &pm,
     return lse_tile::launch_tile_kind<1, float>(a, pm, dm, nblocks, s);
 }
 
-cudaError_t launch_step_tile_batch_edge(int rad, const BatchItem *items, const int *blk_item, int n,
+cudaError_t launch_step_tile_batch_edge(int rad, const BatchItem *items, const int *blk_item, long long n,
                      int nblocks, cudaStream_t s)
 {
     return lse_tile::launch_tile_batch<1>(rad, items, blk_item, n, nblocks, s);

@@ -12,7 +12,7 @@ cudaError_t launch_step_tile_region1(const StepArgs &a, const CUtensorMap &pm,
 
 int step_tile_blocks_per_sm(int rad) { return lse_tile::tile_blocks_per_sm(rad); }
 
-cudaError_t launch_step_tile_batch_region1(int rad, const BatchItem *items, const int *blk_item, int n,
+cudaError_t launch_step_tile_batch_region1(int rad, const BatchItem *items, const int *blk_item, long long n,
                      int nblocks, cudaStream_t s)
 {
     return lse_tile::launch_tile_batch<0>(rad, items, blk_item, n, nblocks, s);

@@ -629,10 +629,12 @@ step_tma_kernel(const __grid_constant__ StepArgs a,
 template <int KIND, int RAD>
 __global__ void __launch_bounds__(256, 2)
 step_tma_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ blk_item,
-                      int n)
+                      long long launch)
 {
     const BatchItem &it = items[blk_item[blockIdx.x]];
-    if (n >= it.cap) return;
+    const long long nl = launch - it.iter0;
+    if (nl < 0 || nl >= it.cap) return;
+    const int n = (int)nl;
     StepArgs a = it.args;
     lse_iteration_flags(a, n, it.cap, it.reinit_period, it.early_stop != 0, true, it.phi);
     tma_step<KIND, RAD, false>(a, &it.phi_maps[n & 1], &it.data_map, blockIdx.x - it.start,
@@ -681,7 +683,7 @@ cudaError_t launch_kind(const StepArgs &a, const CUtensorMap &pm,
 }
 
 template <int KIND, int RAD>
-cudaError_t launch_batch_one(const BatchItem *items, const int *blk_item, int n, int nblocks,
+cudaError_t launch_batch_one(const BatchItem *items, const int *blk_item, long long n, int nblocks,
                              int wpc, cudaStream_t s)
 {
     const int smem = smem_bytes<KIND, RAD>(wpc);
@@ -694,7 +696,7 @@ cudaError_t launch_batch_one(const BatchItem *items, const int *blk_item, int n,
 }
 
 template <int KIND>
-cudaError_t launch_batch_kind(int rad, const BatchItem *items, const int *blk_item, int n,
+cudaError_t launch_batch_kind(int rad, const BatchItem *items, const int *blk_item, long long n,
                               int nblocks, int wpc, cudaStream_t s)
 {
     switch (rad) {

@@ -17,7 +17,7 @@ int step_tma_warp_bytes_region1(int rad)
 }
 
 cudaError_t launch_step_tma_batch_region1(int rad, const BatchItem *items, const int *blk_item,
-                                          int n, int nblocks, int wpc, cudaStream_t s)
+                                          long long n, int nblocks, int wpc, cudaStream_t s)
 {
     return lse_tma::launch_batch_kind<lse_tma::K_REGION1>(rad, items, blk_item, n, nblocks,
                                                          wpc, s);

@@ -106,10 +106,22 @@ _lib.lse_evolve_static.restype = ctypes.c_int
 _lib.lse_evolve_batch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
                                   ctypes.POINTER(Stats), _vp]
 _lib.lse_evolve_batch.restype = ctypes.c_int
+_lib.lse_server_create.argtypes = [_vp, ctypes.c_size_t, ctypes.POINTER(_vp)]
+_lib.lse_server_create.restype = ctypes.c_int
+_lib.lse_server_destroy.argtypes = [_vp]
+_lib.lse_server_destroy.restype = None
+_lib.lse_server_submit.argtypes = [_vp, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_longlong)]
+_lib.lse_server_submit.restype = ctypes.c_int
+_lib.lse_server_advance.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp]
+_lib.lse_server_advance.restype = ctypes.c_int
+_lib.lse_server_poll.argtypes = [_vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(Stats)]
+_lib.lse_server_poll.restype = ctypes.c_int
 
 SYMBOLS = ("lse_create", "lse_destroy", "lse_last_error", "lse_precompute_edge",
            "lse_evolve", "lse_get_stats", "lse_version", "lse_evolve_static",
-           "lse_evolve_batch")
+           "lse_evolve_batch", "lse_server_create", "lse_server_destroy",
+           "lse_server_submit", "lse_server_advance", "lse_server_poll")
 STATIC_MAX_PIXELS = 262144
 
 
@@ -275,29 +287,7 @@ class Context:
         probs = (Problem * n)()
         outs = []
         for i, it in enumerate(items):
-            term = it.get("term", "region")
-            term_code = TERM_REGION if term in ("region", TERM_REGION) else TERM_EDGE
-            phi0 = it["phi0"]
-            H, W = (int(d) for d in phi0.shape)
-            image = it.get("image") if term_code == TERM_REGION else None
-            if image is not None:
-                B, _, _ = _shape3(image)
-                dcode = _dtype_code(image)
-            else:
-                B, dcode = 1, F32
-            phi_out = it.get("phi_out")
-            if phi_out is None:
-                phi_out = torch.empty((H, W), dtype=torch.float32, device=phi0.device)
-            mask_out = it.get("mask_out")
-            if mask_out is None:
-                mask_out = torch.empty((H, W), dtype=torch.uint8, device=phi0.device)
-            p = Params(term_code, float(it.get("dt", 15.0)), float(it.get("sigma", 1.0)),
-                       int(it.get("ts", 9)), int(it.get("iterations", 200)),
-                       int(it.get("reinit_period", 1)), float(it.get("early_stop_frac", 0.0)),
-                       F32)
-            probs[i] = Problem(_ptr(image), dcode, H, W, B,
-                               _ptr(it.get("g")) if term_code == TERM_EDGE else None,
-                               _ptr(phi0), p, _ptr(phi_out), _ptr(mask_out))
+            probs[i], phi_out, mask_out, B = _problem(it)
             outs.append((phi_out, mask_out, B))
         st = (Stats * n)()
         self._check(_lib.lse_evolve_batch(self._h, n, probs, 1 if use_graph else 0, st,
@@ -308,6 +298,86 @@ class Context:
         st = Stats()
         self._check(_lib.lse_get_stats(self._h, ctypes.byref(st)))
         return st.to_dict(bands)
+
+
+def _problem(it: dict):
+    """An lse_problem from a dict of CUDA tensors (see Context.evolve_batch);
+    returns (problem, phi_out, mask_out, bands)."""
+    term = it.get("term", "region")
+    term_code = TERM_REGION if term in ("region", TERM_REGION) else TERM_EDGE
+    phi0 = it["phi0"]
+    H, W = (int(d) for d in phi0.shape)
+    image = it.get("image") if term_code == TERM_REGION else None
+    if image is not None:
+        B, _, _ = _shape3(image)
+        dcode = _dtype_code(image)
+    else:
+        B, dcode = 1, F32
+    phi_out = it.get("phi_out")
+    if phi_out is None:
+        phi_out = torch.empty((H, W), dtype=torch.float32, device=phi0.device)
+    mask_out = it.get("mask_out")
+    if mask_out is None:
+        mask_out = torch.empty((H, W), dtype=torch.uint8, device=phi0.device)
+    p = Params(term_code, float(it.get("dt", 15.0)), float(it.get("sigma", 1.0)),
+               int(it.get("ts", 9)), int(it.get("iterations", 200)),
+               int(it.get("reinit_period", 1)), float(it.get("early_stop_frac", 0.0)), F32)
+    prob = Problem(_ptr(image), dcode, H, W, B,
+                   _ptr(it.get("g")) if term_code == TERM_EDGE else None,
+                   _ptr(phi0), p, _ptr(phi_out), _ptr(mask_out))
+    return prob, phi_out, mask_out, B
+
+
+class Server:
+    """An lse_server on a Context: continuous batching of requests within a
+    device-memory budget (bytes)."""
+
+    QUEUED, RUNNING, DONE = 0, 1, 2
+
+    def __init__(self, ctx: Context, budget_bytes: int):
+        h = ctypes.c_void_p()
+        ctx._check(_lib.lse_server_create(ctx._h, int(budget_bytes), ctypes.byref(h)))
+        self._h = h
+        self.ctx = ctx
+        self._keep = {}      # the tensors of each request until it is done
+
+    def submit(self, item: dict) -> int:
+        """Queues a request (a dict as in Context.evolve_batch); returns its id."""
+        prob, phi_out, mask_out, B = _problem(item)
+        rid = ctypes.c_longlong()
+        self.ctx._check(_lib.lse_server_submit(self._h, ctypes.byref(prob), ctypes.byref(rid)))
+        self._keep[rid.value] = (item, phi_out, mask_out, B)
+        return rid.value
+
+    def advance(self, ticks: int, stream=None) -> int:
+        """Admits, runs `ticks` iterations of every running request, retires
+        the finished ones; returns the number still running."""
+        running = ctypes.c_int()
+        self.ctx._check(_lib.lse_server_advance(self._h, int(ticks), ctypes.byref(running),
+                                                _stream_ptr(stream, self.ctx.device)))
+        return running.value
+
+    def poll(self, rid: int):
+        """None while queued or running; (phi_out, mask_out, stats) once done."""
+        state = ctypes.c_int()
+        st = Stats()
+        self.ctx._check(_lib.lse_server_poll(self._h, int(rid), ctypes.byref(state),
+                                             ctypes.byref(st)))
+        if state.value != self.DONE:
+            return None
+        item, phi_out, mask_out, B = self._keep.pop(rid)
+        return phi_out, mask_out, st.to_dict(B)
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            _lib.lse_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def create(device: int = 0, max_pixels: int = 1 << 20, max_bands: int = 4) -> Context:
