@@ -81,6 +81,15 @@ def _load():
             lib.oracle_gradient.restype = None
             lib.oracle_conv_same.argtypes = [dp, i, i, dp, i, dp]
             lib.oracle_conv_same.restype = None
+            lib.oracle_conv_same_padded.argtypes = [dp, i, i, dp, i, i, dp]
+            lib.oracle_conv_same_padded.restype = None
+            lib.oracle_step_variant.argtypes = [dp, i, i, i, i, dp, dp, d, d, i, i, i, i,
+                                                dp, dp, dp, dp]
+            lib.oracle_step_variant.restype = i
+            lib.oracle_evolve_variant.argtypes = [dp, i, i, i, i, dp, dp, d, d, i, i, i, d,
+                                                  i, i, dp, ctypes.POINTER(ctypes.c_ubyte),
+                                                  ctypes.POINTER(OracleStats)]
+            lib.oracle_evolve_variant.restype = i
             lib.oracle_edge_indicator.argtypes = [dp, i, i, i, d, i, d, dp]
             lib.oracle_edge_indicator.restype = None
             lib.oracle_region_stats.argtypes = [dp, i, i, i, dp, dp, dp]
@@ -140,13 +149,22 @@ def gradient(f):
     return fx, fy
 
 
-def conv_same(f, G):
-    """'same'-size zero-padded 2-D convolution (Table I step 4)."""
+ORDERS = {"listing": 0, "table1": 1}
+PADDINGS = {"zero": 0, "replicate": 1}
+
+
+def conv_same(f, G, padding: str = "zero"):
+    """'same'-size 2-D convolution (Table I step 4), zero padding (the
+    listing's) or replicate padding (the nearest image value)."""
     f = _f64(f)
     G = _f64(G)
     H, W = f.shape
     out = np.empty_like(f)
-    _load().oracle_conv_same(_ptr(f), H, W, _ptr(G), G.shape[0], _ptr(out))
+    if padding == "zero":
+        _load().oracle_conv_same(_ptr(f), H, W, _ptr(G), G.shape[0], _ptr(out))
+    else:
+        _load().oracle_conv_same_padded(_ptr(f), H, W, _ptr(G), G.shape[0],
+                                        PADDINGS[padding], _ptr(out))
     return out
 
 
@@ -208,10 +226,11 @@ def update(image, phi, term="region", g=None, dt: float = 15.0):
 
 
 def step(image, phi, term="region", g=None, dt: float = 15.0,
-         sigma: float = 1.0, ts: int = 9):
+         sigma: float = 1.0, ts: int = 9, order: str = "listing",
+         reinit: bool = True, padding: str = "zero"):
     """One iteration v = G_sigma * (phi + dt R |grad phi|), not binarised.
-
-    Returns (v, norm, c_plus, c_minus, zero_force).
+    In the Table I order with ``reinit`` the update is binarised before the
+    smoothing.  Returns (v, norm, c_plus, c_minus, zero_force).
     """
     img = _image3(image)
     B, H, W = img.shape
@@ -221,9 +240,15 @@ def step(image, phi, term="region", g=None, dt: float = 15.0,
     norm = np.zeros(1)
     cp = np.zeros(B)
     cm = np.zeros(B)
-    z = _load().oracle_step(_ptr(img), H, W, B, _term(term), _ptr(gg),
-                            _ptr(phi), float(dt), float(sigma), int(ts),
-                            _ptr(v), _ptr(norm), _ptr(cp), _ptr(cm))
+    if order == "listing" and padding == "zero":
+        z = _load().oracle_step(_ptr(img), H, W, B, _term(term), _ptr(gg),
+                                _ptr(phi), float(dt), float(sigma), int(ts),
+                                _ptr(v), _ptr(norm), _ptr(cp), _ptr(cm))
+    else:
+        z = _load().oracle_step_variant(_ptr(img), H, W, B, _term(term), _ptr(gg),
+                                        _ptr(phi), float(dt), float(sigma), int(ts),
+                                        ORDERS[order], int(bool(reinit)), PADDINGS[padding],
+                                        _ptr(v), _ptr(norm), _ptr(cp), _ptr(cm))
     return v, float(norm[0]), cp, cm, bool(z)
 
 
@@ -254,8 +279,10 @@ def step_sampled(image, phi, ys, xs, term="region", g=None, dt: float = 15.0,
 
 def evolve(image, phi0, term="region", g=None, dt: float = 15.0,
            sigma: float = 1.0, ts: int = 9, iterations: int = 200,
-           reinit_period: int = 1, early_stop_frac: float = 0.0):
-    """The whole evolution of Table I.  Returns (v, mask, stats_dict)."""
+           reinit_period: int = 1, early_stop_frac: float = 0.0,
+           order: str = "listing", padding: str = "zero"):
+    """The whole evolution of Table I (in the listing's step order unless
+    ``order`` = "table1").  Returns (v, mask, stats_dict)."""
     img = _image3(image)
     B, H, W = img.shape
     phi0 = _f64(phi0)
@@ -263,11 +290,18 @@ def evolve(image, phi0, term="region", g=None, dt: float = 15.0,
     v = np.empty((H, W))
     mask = np.empty((H, W), np.uint8)
     st = OracleStats()
-    rc = _load().oracle_evolve(
-        _ptr(img), H, W, B, _term(term), _ptr(gg), _ptr(phi0), float(dt),
-        float(sigma), int(ts), int(iterations), int(reinit_period),
-        float(early_stop_frac), _ptr(v),
-        mask.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), ctypes.byref(st))
+    if order == "listing" and padding == "zero":
+        rc = _load().oracle_evolve(
+            _ptr(img), H, W, B, _term(term), _ptr(gg), _ptr(phi0), float(dt),
+            float(sigma), int(ts), int(iterations), int(reinit_period),
+            float(early_stop_frac), _ptr(v),
+            mask.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), ctypes.byref(st))
+    else:
+        rc = _load().oracle_evolve_variant(
+            _ptr(img), H, W, B, _term(term), _ptr(gg), _ptr(phi0), float(dt),
+            float(sigma), int(ts), int(iterations), int(reinit_period),
+            float(early_stop_frac), ORDERS[order], PADDINGS[padding], _ptr(v),
+            mask.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), ctypes.byref(st))
     if rc != 0:
         raise ValueError("oracle_evolve rejected its arguments")
     stats = {

@@ -47,6 +47,16 @@
  *                          early stop once fewer than early_stop_frac * H * W
  *                          pixels change sign in one iteration.
  *
+ * Two variants, reached through the *_variant / *_padded entry points (the
+ * plain entry points are the method as read above):
+ *   Table I order ........ Table I lists update (step 2), re-initialisation
+ *                          (step 3), then regularisation (step 4): on a
+ *                          re-initialising iteration u is binarised first
+ *                          (u >= 0 -> +1, the same tie rule) and v = G * that;
+ *                          the next iteration starts from v itself.
+ *   replicate padding .... the convolution takes the nearest image value
+ *                          outside the image instead of 0.
+ *
  * Degenerate cases the paper leaves open: when phi >= 0 holds nowhere or
  * everywhere, when the two sides' means agree to within rounding, or when
  * max|D| = 0, the region force is taken as R = 0 (the iteration only smooths)
@@ -62,6 +72,10 @@
 
 #define ORACLE_TERM_REGION 0
 #define ORACLE_TERM_EDGE 1
+#define ORACLE_ORDER_LISTING 0  /* update, smooth, re-initialise */
+#define ORACLE_ORDER_TABLE1 1   /* update, re-initialise, smooth */
+#define ORACLE_PAD_ZERO 0
+#define ORACLE_PAD_REPLICATE 1
 #define ORACLE_MAX_BANDS 8
 /* Relative contrast below which c+ and c- count as equal (see above). */
 #define ORACLE_CONTRAST_TOL 1e-6
@@ -124,32 +138,46 @@ void oracle_gradient(const double *f, int H, int W, double *fx, double *fy)
 }
 
 /* ------------------------------------------------------------------ */
-/* 'same'-size 2-D convolution, zero outside the image.              */
-/* out(y,x) = sum_{i,j} G(i,j) f(y - i, x - j), i,j in [-r, r].       */
+/* 'same'-size 2-D convolution.                                       */
+/* out(y,x) = sum_{i,j} G(i,j) f(y - i, x - j), i,j in [-r, r], with  */
+/* f = 0 outside the image (pad = ORACLE_PAD_ZERO) or f = its nearest */
+/* image value there (ORACLE_PAD_REPLICATE).                          */
 /* ------------------------------------------------------------------ */
 static double conv_at(const double *f, int H, int W, const double *G, int ts,
-                      int y, int x)
+                      int y, int x, int pad)
 {
     int r = (ts - 1) / 2;
     double acc = 0.0;
     for (int i = -r; i <= r; ++i) {
         int yy = y - i;
-        if (yy < 0 || yy >= H) continue;
+        if (yy < 0 || yy >= H) {
+            if (pad == ORACLE_PAD_ZERO) continue;
+            yy = yy < 0 ? 0 : H - 1;
+        }
         for (int j = -r; j <= r; ++j) {
             int xx = x - j;
-            if (xx < 0 || xx >= W) continue;
+            if (xx < 0 || xx >= W) {
+                if (pad == ORACLE_PAD_ZERO) continue;
+                xx = xx < 0 ? 0 : W - 1;
+            }
             acc += G[(i + r) * ts + (j + r)] * f[(size_t)yy * W + xx];
         }
     }
     return acc;
 }
 
-void oracle_conv_same(const double *f, int H, int W, const double *G, int ts,
-                      double *out)
+void oracle_conv_same_padded(const double *f, int H, int W, const double *G, int ts,
+                             int pad, double *out)
 {
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x)
-            out[(size_t)y * W + x] = conv_at(f, H, W, G, ts, y, x);
+            out[(size_t)y * W + x] = conv_at(f, H, W, G, ts, y, x, pad);
+}
+
+void oracle_conv_same(const double *f, int H, int W, const double *G, int ts,
+                      double *out)
+{
+    oracle_conv_same_padded(f, H, W, G, ts, ORACLE_PAD_ZERO, out);
 }
 
 /* ------------------------------------------------------------------ */
@@ -328,12 +356,15 @@ int oracle_region_force(const double *I, int H, int W, int B,
     return c.zero_force;
 }
 
-/* One iteration without re-initialisation: v = G_sigma * (phi + dt R |grad phi|).
- * Returns 1 when the region force was zero by the degenerate rule. */
-int oracle_step(const double *I, int H, int W, int B, int term,
-                const double *g, const double *phi, double dt, double sigma,
-                int ts, double *v, double *norm_out, double *c_plus,
-                double *c_minus)
+/* One iteration: u = phi + dt R |grad phi| (Eq. 18); in the Table I order
+ * on a re-initialising iteration u -> (u >= 0 ? 1 : -1) (Table I step 3);
+ * v = G_sigma * u with the given padding (Table I step 4).  The listing's
+ * re-initialisation of v is the caller's.  Returns 1 when the region force
+ * was zero by the degenerate rule. */
+int oracle_step_variant(const double *I, int H, int W, int B, int term,
+                        const double *g, const double *phi, double dt, double sigma,
+                        int ts, int order, int reinit, int pad, double *v,
+                        double *norm_out, double *c_plus, double *c_minus)
 {
     size_t N = (size_t)H * W;
     double *u = (double *)malloc(N * sizeof(double));
@@ -343,8 +374,10 @@ int oracle_step(const double *I, int H, int W, int B, int term,
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x)
             u[(size_t)y * W + x] = update_at(&c, y, x);
+    if (order == ORACLE_ORDER_TABLE1 && reinit)
+        for (size_t p = 0; p < N; ++p) u[p] = u[p] >= 0.0 ? 1.0 : -1.0;
     oracle_gaussian_taps(sigma, ts, G);
-    oracle_conv_same(u, H, W, G, ts, v);
+    oracle_conv_same_padded(u, H, W, G, ts, pad, v);
     if (norm_out) *norm_out = c.norm;
     if (c_plus && c_minus)
         for (int b = 0; b < B; ++b) {
@@ -354,6 +387,18 @@ int oracle_step(const double *I, int H, int W, int B, int term,
     free(u);
     free(G);
     return c.zero_force;
+}
+
+/* One iteration without re-initialisation: v = G_sigma * (phi + dt R |grad phi|),
+ * zero padding. */
+int oracle_step(const double *I, int H, int W, int B, int term,
+                const double *g, const double *phi, double dt, double sigma,
+                int ts, double *v, double *norm_out, double *c_plus,
+                double *c_minus)
+{
+    return oracle_step_variant(I, H, W, B, term, g, phi, dt, sigma, ts,
+                               ORACLE_ORDER_LISTING, 0, ORACLE_PAD_ZERO, v, norm_out,
+                               c_plus, c_minus);
 }
 
 /* The same iteration evaluated only at n sample pixels (ys[k], xs[k]).
@@ -404,14 +449,15 @@ static int reinit_after(int n, int period)
     return ((n + 1) % period) == 0;
 }
 
-/* The whole evolution (Table I steps 2-6).  Returns 0, or -1 on bad input.
- * v_out receives the last smoothed LSF v (before its re-initialisation);
+/* The whole evolution (Table I steps 2-6) in the given step order and
+ * padding.  Returns 0, or -1 on bad input.  v_out receives the last smoothed
+ * LSF v (in the listing's order: before its re-initialisation);
  * mask_out[p] = (v_out[p] >= 0). */
-int oracle_evolve(const double *I, int H, int W, int B, int term,
-                  const double *g, const double *phi0, double dt,
-                  double sigma, int ts, int iterations, int reinit_period,
-                  double early_stop_frac, double *v_out,
-                  unsigned char *mask_out, oracle_stats *st)
+int oracle_evolve_variant(const double *I, int H, int W, int B, int term,
+                          const double *g, const double *phi0, double dt,
+                          double sigma, int ts, int iterations, int reinit_period,
+                          double early_stop_frac, int order, int pad, double *v_out,
+                          unsigned char *mask_out, oracle_stats *st)
 {
     if (H < 1 || W < 1 || B < 1 || B > ORACLE_MAX_BANDS || ts < 1 ||
         (ts % 2) == 0 || iterations < 1)
@@ -423,8 +469,10 @@ int oracle_evolve(const double *I, int H, int W, int B, int term,
     memset(st, 0, sizeof(*st));
     for (int n = 0; n < iterations; ++n) {
         double norm = 0.0;
-        st->degenerate |= oracle_step(I, H, W, B, term, g, phi, dt, sigma, ts,
-                                      v_out, &norm, NULL, NULL) &&
+        const int reinit_n = reinit_after(n, reinit_period);
+        st->degenerate |= oracle_step_variant(I, H, W, B, term, g, phi, dt, sigma, ts,
+                                              order, reinit_n, pad, v_out, &norm, NULL,
+                                              NULL) &&
                           term == ORACLE_TERM_REGION;
         st->norm = norm;
         long long flips = 0;
@@ -432,7 +480,8 @@ int oracle_evolve(const double *I, int H, int W, int B, int term,
             if ((v_out[p] >= 0.0) != (phi[p] >= 0.0)) ++flips;
         st->last_flips = flips;
         st->iterations_run = n + 1;
-        int reinit = reinit_after(n, reinit_period);
+        /* in the Table I order the re-initialisation came before smoothing */
+        int reinit = reinit_n && order == ORACLE_ORDER_LISTING;
         for (size_t p = 0; p < N; ++p)
             phi[p] = reinit ? (v_out[p] >= 0.0 ? 1.0 : -1.0) : v_out[p];
         if (early_stop_frac > 0.0 && (double)flips < early_stop_frac * (double)N)
@@ -450,4 +499,16 @@ int oracle_evolve(const double *I, int H, int W, int B, int term,
     }
     free(phi);
     return 0;
+}
+
+/* The evolution in the listing's order with zero padding. */
+int oracle_evolve(const double *I, int H, int W, int B, int term,
+                  const double *g, const double *phi0, double dt,
+                  double sigma, int ts, int iterations, int reinit_period,
+                  double early_stop_frac, double *v_out,
+                  unsigned char *mask_out, oracle_stats *st)
+{
+    return oracle_evolve_variant(I, H, W, B, term, g, phi0, dt, sigma, ts, iterations,
+                                 reinit_period, early_stop_frac, ORACLE_ORDER_LISTING,
+                                 ORACLE_PAD_ZERO, v_out, mask_out, st);
 }

@@ -49,6 +49,13 @@ MUTATIONS = {
                     "double a = region_numerator_at(c, p);"),
     # update without the LSF itself
     "no_phi_term": ("return c->phi[p] + c->dt", "return 0.0 + c->dt"),
+    # replicate padding clamping to the far border
+    "replicate_far_side": ("yy = yy < 0 ? 0 : H - 1;", "yy = yy < 0 ? H - 1 : 0;"),
+    # Table I re-initialisation with the tie u = 0 sent to -1
+    "table1_tie": ("u[p] = u[p] >= 0.0 ? 1.0 : -1.0;", "u[p] = u[p] > 0.0 ? 1.0 : -1.0;"),
+    # Table I order without its re-initialisation before smoothing
+    "table1_no_binarise": ("if (order == ORACLE_ORDER_TABLE1 && reinit)",
+                           "if (order == ORACLE_ORDER_TABLE1 && 0)"),
 }
 
 

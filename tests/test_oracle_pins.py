@@ -420,3 +420,105 @@ def test_reinit_period_zero_keeps_real_lsf():
     v2, _, _ = oracle.evolve(img, phi0, iterations=2, reinit_period=0)
     ref, *_ = oracle.step(img, v1)
     np.testing.assert_allclose(v2, ref, rtol=1e-14, atol=1e-14)
+
+
+# ---------------------------------------------------------------- variants: Table I order, replicate padding
+def replicate_conv(f, G):
+    """'same' convolution with the nearest image value outside (scipy)."""
+    return ndimage.convolve(f, G, mode="nearest")
+
+
+def independent_variant_step(I, phi, term, g=None, dt=15.0, sigma=1.0, ts=9,
+                             order="listing", reinit=True, padding="zero"):
+    """independent_step's update, then Table I's re-initialisation of u when
+    asked, then the smoothing with zero (scipy impulse matrix) or replicate
+    (scipy 'nearest') padding."""
+    B, H, W = I.shape
+    fx, fy = np_gradient(phi)
+    s = np.hypot(fx, fy)
+    if term == "region":
+        P = phi >= 0
+        D = np.zeros_like(phi)
+        for b in range(B):
+            cp = I[b][P].mean()
+            cm = I[b][~P].mean()
+            D += -(I[b] - cp) ** 2 + (I[b] - cm) ** 2
+        R = D / np.abs(D).max()
+    else:
+        R = g
+    u = phi + dt * R * s
+    if order == "table1" and reinit:
+        u = np.where(u >= 0, 1.0, -1.0)
+    g1 = gauss_1d(sigma, ts)
+    G = np.outer(g1, g1)
+    if padding == "zero":
+        return (conv_matrix(H, W, G) @ u.ravel()).reshape(H, W)
+    return replicate_conv(u, G)
+
+
+def test_replicate_convolution_matches_scipy_nearest():
+    f = rng_image((13, 17), 70)
+    G = np.random.default_rng(71).uniform(0.0, 1.0, (5, 5))   # asymmetric
+    np.testing.assert_allclose(oracle.conv_same(f, G, "replicate"), replicate_conv(f, G),
+                               rtol=1e-12, atol=1e-14)
+    # a 1-pixel-wide image: every outside value is that column's
+    f1 = rng_image((9, 1), 72)
+    np.testing.assert_allclose(oracle.conv_same(f1, G, "replicate"), replicate_conv(f1, G),
+                               rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("term,B,H,W,order,reinit,padding", [
+    ("region", 1, 9, 11, "table1", True, "zero"),
+    ("region", 3, 8, 10, "table1", True, "replicate"),
+    ("region", 1, 10, 9, "listing", True, "replicate"),
+    ("edge", 1, 9, 9, "table1", True, "zero"),
+    ("edge", 4, 8, 12, "listing", True, "replicate"),
+    ("region", 2, 9, 9, "table1", False, "zero"),
+])
+def test_variant_step_against_independent_formulation(term, B, H, W, order, reinit, padding):
+    I = rng_image((B, H, W), 80 + B)
+    phi = rng_phi(H, W, 81 + H)
+    g = oracle.edge_indicator(I) if term == "edge" else None
+    v, *_ = oracle.step(I, phi, term=term, g=g, order=order, reinit=reinit, padding=padding)
+    ref = independent_variant_step(I, phi, term, g=g, order=order, reinit=reinit,
+                                   padding=padding)
+    np.testing.assert_allclose(v, ref, rtol=1e-11, atol=1e-12)
+
+
+@pytest.mark.parametrize("padding", ["zero", "replicate"])
+def test_table1_evolution_against_independent_formulation(padding):
+    I = rng_image((1, 9, 10), 90)
+    phi0 = rng_phi(9, 10, 91)
+    phi = phi0.copy()
+    for _ in range(5):
+        v_ref = independent_variant_step(I, phi, "region", order="table1", padding=padding)
+        phi = v_ref                   # Table I: the next iteration starts from v
+    v, mask, st = oracle.evolve(I, phi0, iterations=5, order="table1", padding=padding)
+    np.testing.assert_allclose(v, v_ref, rtol=1e-11, atol=1e-12)
+    assert np.array_equal(mask.astype(bool), v_ref >= 0)
+
+
+def test_table1_order_keeps_v_within_one_and_replicate_keeps_constants():
+    I = rng_image((1, 20, 24), 92)
+    phi0 = rng_phi(20, 24, 93)
+    for padding in ("zero", "replicate"):
+        v, _, _ = oracle.evolve(I, phi0, iterations=4, order="table1", padding=padding)
+        assert np.abs(v).max() <= 1.0 + 1e-12
+    # a constant LSF has no gradient, so u = phi: replicate padding keeps it,
+    # zero padding pulls the border toward 0
+    g = np.full((12, 14), 0.5)
+    ones = np.ones((12, 14))
+    v_rep, *_ = oracle.step(I[:, :12, :14], ones, term="edge", g=g, padding="replicate")
+    v_zero, *_ = oracle.step(I[:, :12, :14], ones, term="edge", g=g)
+    np.testing.assert_allclose(v_rep, 1.0, rtol=0, atol=1e-14)
+    assert v_zero[0, 0] < 0.75 and abs(v_zero[6, 7] - 1.0) < 1e-14
+
+
+def test_table1_tie_goes_to_plus():
+    # constant image: R = 0 (degenerate), so u = phi; where phi = 0 the
+    # re-initialisation before smoothing must give +1
+    I = np.full((1, 7, 7), 0.4)
+    phi = np.full((7, 7), -1.0)
+    phi[2:5, 2:5] = 0.0
+    v, *_ = oracle.step(I, phi, ts=1, order="table1")
+    assert (v[2:5, 2:5] == 1.0).all() and (v[0] == -1.0).all()
