@@ -76,6 +76,16 @@ typedef enum {
     LSE_U16 = 3                /* uint16, read as float32(value) / 65535.0f */
 } lse_dtype;
 
+typedef enum {
+    LSE_ORDER_LISTING = 0,     /* update, smooth, re-initialise (the listing) */
+    LSE_ORDER_TABLE1 = 1       /* update, re-initialise, smooth (Table I) */
+} lse_order;
+
+typedef enum {
+    LSE_PAD_ZERO = 0,          /* G_sigma * u with u = 0 outside the image */
+    LSE_PAD_REPLICATE = 1      /* G_sigma * u with u = its nearest image value */
+} lse_padding;
+
 /* Parameters of one evolution.
  *   term            LSE_TERM_REGION or LSE_TERM_EDGE.
  *   dt              time step of Eq. 18, > 0 (the paper uses 15-18; Sec. IV-D
@@ -103,6 +113,19 @@ typedef enum {
  *                   storage values, or 16-bit storage outside those cases,
  *                   give LSE_ERR_INVALID_ARG.  Not an equation of the paper,
  *                   whose own runs are FP64 (Sec. IV-A).
+ *   order           LSE_ORDER_LISTING (default): each iteration updates,
+ *                   smooths, then re-initialises v, as the paper's MATLAB
+ *                   listing of the edge-based LSE does.  LSE_ORDER_TABLE1:
+ *                   the order of Table I (steps 2, 3, 4): on a
+ *                   re-initialising iteration u is binarised (u >= 0 -> +1,
+ *                   else -1) before it is smoothed, and the next iteration
+ *                   starts from the real-valued v.
+ *   padding         LSE_PAD_ZERO (default): the listing's conv2 'same', u = 0
+ *                   outside the image.  LSE_PAD_REPLICATE: u outside the image
+ *                   takes the value of the nearest image pixel.
+ *                   A non-default order or padding runs on the plain
+ *                   shared-memory step kernel, FP32 storage only; batches,
+ *                   the server and lse_evolve_static reject it.
  * Region-term degenerate rule (the paper is silent): when phi >= 0 holds
  * nowhere or everywhere, when max_b |c+_b - c-_b| <= 1e-6 * max_b(|c+_b| +
  * |c-_b|), or when max|D| = 0, that iteration uses R = 0 and the call ends
@@ -116,6 +139,8 @@ typedef struct {
     int reinit_period;
     float early_stop_frac;
     lse_dtype storage;
+    lse_order order;
+    lse_padding padding;
 } lse_params;
 
 /* Result statistics of the last lse_evolve on a context.

@@ -195,6 +195,15 @@ lse_status check_params(lse_ctx *ctx, const lse_params &p, int B)
         set_err(ctx, "16-bit storage needs one band (or the edge term) and ts <= 15");
         return LSE_ERR_INVALID_ARG;
     }
+    if ((p.order != LSE_ORDER_LISTING && p.order != LSE_ORDER_TABLE1) ||
+        (p.padding != LSE_PAD_ZERO && p.padding != LSE_PAD_REPLICATE)) {
+        set_err(ctx, "unknown order %d or padding %d", (int)p.order, (int)p.padding);
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (p.storage != LSE_F32 && (p.order != LSE_ORDER_LISTING || p.padding != LSE_PAD_ZERO)) {
+        set_err(ctx, "the Table I order and replicate padding need LSE_F32 storage");
+        return LSE_ERR_INVALID_ARG;
+    }
     if (p.term == LSE_TERM_EDGE && p.reinit_period != 1) {
         set_err(ctx, "the edge term needs reinit_period = 1 (Step 3: without "
                      "re-initialisation its LSF only grows)");

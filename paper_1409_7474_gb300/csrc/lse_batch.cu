@@ -170,8 +170,10 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
             return LSE_ERR_INVALID_ARG;
         }
         if ((r = check_params(ctx, q.params, q.B)) != LSE_OK) return r;
-        if (q.params.storage != LSE_F32) {
-            set_err(ctx, "lse_evolve_batch: image %d: batches use LSE_F32 storage", i);
+        if (q.params.storage != LSE_F32 || q.params.order != LSE_ORDER_LISTING ||
+            q.params.padding != LSE_PAD_ZERO) {
+            set_err(ctx, "lse_evolve_batch: image %d: batches use LSE_F32 storage, the "
+                         "listing's order and zero padding", i);
             return LSE_ERR_INVALID_ARG;
         }
         const bool ok = classify(q.phi0, ctx->device) == PTR_DEVICE &&

@@ -70,6 +70,9 @@ struct StepArgs {
     int binary_in;              // phi_in holds +-1 only (previous step stored sign(v))
     int rad;                    // (ts - 1) / 2
     int storage;                // LSE_F32 / LSE_F16 / LSE_BF16: phi and data planes
+    int order;                  // LSE_ORDER_*: LISTING, or TABLE1 (generic kernel)
+    int pad;                    // LSE_PAD_*: ZERO, or REPLICATE (generic kernel)
+    int reinit_u;               // Table I order: binarise u before smoothing
     float taps[16];             // 1-D taps G[0..rad] (symmetric)
     float dt;                   // time step of Eq. 18
     float half_dt;              // 0.5 * dt (edge term)
@@ -139,6 +142,15 @@ __host__ __device__ inline void lse_iteration_flags(StepArgs &a, int n, int cap,
     a.binarise_in =
         (n > 0 && lse_reinit_after(n - 1, reinit_period) && !stores_bin(n - 1)) ? 1 : 0;
     a.count_flips = (early_stop || n == cap - 1) ? 1 : 0;
+    a.reinit_u = 0;
+    if (a.order == LSE_ORDER_TABLE1) {
+        // Table I: the re-initialisation (step 3) acts on u, before the
+        // smoothing (step 4); the next iteration reads v as it is
+        a.store_bin = 0;
+        a.binary_in = 0;
+        a.binarise_in = 0;
+        a.reinit_u = lse_reinit_after(n, reinit_period) ? 1 : 0;
+    }
 }
 
 // ---------------------------------------------------------------- helpers

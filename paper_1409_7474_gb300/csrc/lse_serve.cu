@@ -252,9 +252,10 @@ lse_status lse_server_submit(lse_server *sv, const lse_problem *problem, long lo
         return LSE_ERR_INVALID_ARG;
     }
     if ((r = check_params(ctx, q.params, q.B)) != LSE_OK) return r;
-    if (q.params.storage != LSE_F32 || q.params.ts > 15 || (region && q.B > 4)) {
-        set_err(ctx, "lse_server_submit: the server runs LSE_F32 storage, ts <= 15 and at "
-                     "most 4 bands");
+    if (q.params.storage != LSE_F32 || q.params.ts > 15 || (region && q.B > 4) ||
+        q.params.order != LSE_ORDER_LISTING || q.params.padding != LSE_PAD_ZERO) {
+        set_err(ctx, "lse_server_submit: the server runs LSE_F32 storage, ts <= 15, at "
+                     "most 4 bands, the listing's order and zero padding");
         return LSE_ERR_INVALID_ARG;
     }
     {

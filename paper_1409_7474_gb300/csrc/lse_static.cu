@@ -118,6 +118,8 @@ extern "C" lse_status lse_evolve_static(const float *image, int H, int W, int B,
     if (!(p.early_stop_frac >= 0.0f) || !(p.early_stop_frac < 1.0f))
         return fail("lse_evolve_static: early_stop_frac must be in [0, 1)");
     if (p.storage != LSE_F32) return fail("lse_evolve_static: storage must be LSE_F32");
+    if (p.order != LSE_ORDER_LISTING || p.padding != LSE_PAD_ZERO)
+        return fail("lse_evolve_static: only the listing's order and zero padding");
     const bool region = p.term == LSE_TERM_REGION;
     if (!region && p.reinit_period != 1)
         return fail("lse_evolve_static: the edge term needs reinit_period = 1");

@@ -6,11 +6,16 @@
 //      previous iteration re-initialised; Table I step 3);
 //   2. u = phi + dt R |grad phi| (Eq. 18) on the tile + r halo, with R the
 //      region term of Eq. 17 or the edge term of Eq. 14, and u = 0 outside the
-//      image (the zero padding of the 'same' convolution);
-//   3. separable Gaussian G_sigma * u (Table I step 4): rows, then columns;
+//      image (the zero padding of the 'same' convolution), or, with replicate
+//      padding, u of the nearest image pixel; in the Table I order a
+//      re-initialising iteration binarises u here (Table I step 3);
+//   3. separable Gaussian G_sigma * u (Table I step 4): rows, then columns
+//      (replicate padding is separable too: clamping rows and columns one
+//      after the other reaches the same nearest pixel);
 //   4. v -> phi_out, and the sums of the next iteration's statistics.
-// It serves radii the TMA kernel does not instantiate and is the plain
-// restatement the faster kernel is checked against.
+// It serves radii the TMA kernel does not instantiate, the Table I step
+// order and replicate padding, and is the plain restatement the faster
+// kernels are checked against.
 #include "lse_reduce.cuh"
 
 namespace {
@@ -61,8 +66,13 @@ step_generic_kernel(const __grid_constant__ StepArgs a)
             int uy = i / UN, ux = i - uy * UN;
             int gy = y0 - R + uy, gx = x0 - R + ux;
             float u = 0.0f;
-            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-                const float *c = P + (uy + 1) * PN + (ux + 1);
+            const bool inside = gy >= 0 && gy < H && gx >= 0 && gx < W;
+            if (inside || a.pad == LSE_PAD_REPLICATE) {
+                // replicate padding: u outside the image is u at the nearest
+                // image pixel, which lies in this tile's window of P
+                gy = min(max(gy, 0), H - 1);
+                gx = min(max(gx, 0), W - 1);
+                const float *c = P + (gy - (y0 - R - 1)) * PN + (gx - (x0 - R - 1));
                 // twice the listing's gradient: central R - L, one-sided 2 (b - a)
                 float dx, dy;
                 if (W == 1) dx = 0.0f;
@@ -84,6 +94,8 @@ step_generic_kernel(const __grid_constant__ StepArgs a)
                     t = a.half_dt * d[0];
                 }
                 u = fmaf(t, s2, c[0]);
+                // Table I order: re-initialise u itself, before the smoothing
+                if (a.reinit_u) u = u >= 0.0f ? 1.0f : -1.0f;
             }
             U[i] = u;
         }

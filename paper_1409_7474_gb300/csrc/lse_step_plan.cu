@@ -103,6 +103,8 @@ bool plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_
     a.band_stride = band_stride;
     a.data = static_cast<const float *>(data);
     a.storage = p.storage;
+    a.order = p.order;
+    a.pad = p.padding;
     a.st = st;
     a.partials = partials;
     plan->phi[0] = phi[0];
@@ -116,6 +118,11 @@ bool plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_
     const int sto = p.storage;
     // 16-bit storage: the data box starts with phi's, 4 columns left of the tile
     const int data_box_w = sto == LSE_F32 ? 128 : 136;
+    // the Table I order and replicate padding run on the plain kernel only
+    if (p.order != LSE_ORDER_LISTING || p.padding != LSE_PAD_ZERO) {
+        if (sto != LSE_F32) return false;
+        requested = LSE_FORM_GENERIC;
+    }
     if (requested == LSE_FORM_AUTO &&
         plan_step_tile(H, W, a.B, p.term, a.rad, sm_count, &a, &plan->nblocks) &&
         encode_box(&plan->phi_maps[0], phi[0], sto, W, H, pitch, 0, 1, 136, 66) &&

@@ -48,13 +48,16 @@ TERM_REGION = 0
 TERM_EDGE = 1
 F32, F16, BF16, U16 = 0, 1, 2, 3
 STORAGE = {"f32": F32, "f16": F16, "bf16": BF16}
+ORDERS = {"listing": 0, "table1": 1}        # lse_order
+PADDINGS = {"zero": 0, "replicate": 1}      # lse_padding
 
 
 class Params(ctypes.Structure):
     _fields_ = [("term", ctypes.c_int), ("dt", ctypes.c_float),
                 ("sigma", ctypes.c_float), ("ts", ctypes.c_int),
                 ("iterations", ctypes.c_int), ("reinit_period", ctypes.c_int),
-                ("early_stop_frac", ctypes.c_float), ("storage", ctypes.c_int)]
+                ("early_stop_frac", ctypes.c_float), ("storage", ctypes.c_int),
+                ("order", ctypes.c_int), ("padding", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -246,13 +249,15 @@ class Context:
                sigma: float = 1.0, ts: int = 9, iterations: int = 200,
                reinit_period: int = 1, early_stop_frac: float = 0.0,
                phi_out=None, mask_out=None, stream=None, sync: bool = True,
-               storage: str = "f32"):
+               storage: str = "f32", order: str = "listing", padding: str = "zero"):
         """Runs the evolution.  Returns (phi_out, mask_out, stats or None).
 
         With ``sync`` the call waits for the stream and returns the statistics
         dict; otherwise it returns at once and ``stats()`` reads them after the
         caller synchronises.  ``storage`` ("f32", "f16" or "bf16") is the type
-        of the work planes in HBM (``lse_params.storage``)."""
+        of the work planes in HBM (``lse_params.storage``); ``order``
+        ("listing" or "table1") and ``padding`` ("zero" or "replicate") are
+        ``lse_params.order`` and ``lse_params.padding``."""
         term_code = TERM_REGION if term in ("region", TERM_REGION) else TERM_EDGE
         ref = image if image is not None else phi0
         if image is not None:
@@ -267,7 +272,8 @@ class Context:
             mask_out = _empty_like_place(ref, (H, W), np.uint8,
                                          torch.uint8 if torch is not None else None)
         p = Params(term_code, float(dt), float(sigma), int(ts), int(iterations),
-                   int(reinit_period), float(early_stop_frac), STORAGE[storage])
+                   int(reinit_period), float(early_stop_frac), STORAGE[storage],
+                   ORDERS[order], PADDINGS[padding])
         st = Stats()
         rc = _lib.lse_evolve(self._h, _ptr(image) if term_code == TERM_REGION else None,
                              dcode, H, W, B,

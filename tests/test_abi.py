@@ -43,15 +43,17 @@ def test_struct_layout_matches_header(lse, tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "lse.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(lse_params),"
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(lse_params),"
         " sizeof(lse_stats), offsetof(lse_stats, c_plus), offsetof(lse_stats, norm),"
-        " offsetof(lse_stats, status));return 0;}\n")
+        " offsetof(lse_stats, status), offsetof(lse_params, order),"
+        " offsetof(lse_params, padding));return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert vals == [ctypes.sizeof(lse.Params), ctypes.sizeof(lse.Stats),
                     lse.Stats.c_plus.offset, lse.Stats.norm.offset,
-                    lse.Stats.status.offset]
+                    lse.Stats.status.offset, lse.Params.order.offset,
+                    lse.Params.padding.offset]
 
 
 def test_problem_layout_matches_header(lse, tmp_path):
