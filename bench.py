@@ -175,6 +175,7 @@ def oracle_throughput(img, phi_r, phi_e, seconds: float, crop: int = 256):
     host core (ctypes releases the GIL) for about `seconds`; Mpixel-iters/s."""
     import oracle
     oracle.build()
+    oracle.set_threads(1)     # one thread per crop: the crops run side by side
     cores = os.cpu_count() or 1
     H, W = img.shape[-2:]
     r = np.random.default_rng(0)

@@ -4,8 +4,11 @@ TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
 package.  The GPU library never calls it and shares no code with it.
 
-The arithmetic lives in ``lse_oracle.c`` (plain C, double precision, no
-OpenMP); this module only builds it with gcc and marshals numpy arrays.
+The arithmetic lives in ``lse_oracle.c`` (plain C, double precision); this
+module only builds it with gcc and marshals numpy arrays.  The build enables
+OpenMP when gcc has it: the per-pixel maps then run their rows on several
+threads (``OMP_NUM_THREADS`` caps them), with results independent of the
+thread count.
 Each wrapper names the part of the paper it follows; the C file's header has
 the full list and the readings taken where the paper is silent.
 """
@@ -48,16 +51,18 @@ def build(force: bool = False) -> str:
     """Compile lse_oracle.c into a shared library next to it.
 
     ``-ffp-contract=off`` keeps gcc from fusing multiply-adds, so the x86 and
-    Arm builds round identically.
+    Arm builds round identically.  ``-fopenmp`` is dropped when gcc cannot
+    build with it.
     """
     if force or not os.path.exists(_LIB_PATH) or (
         os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
     ):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(
-            ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared",
-             "-fPIC", "-o", tmp, _SRC, "-lm"]
-        )
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared",
+                "-fPIC", "-o", tmp, _SRC, "-lm"]
+        r = subprocess.run(base + ["-fopenmp"], capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -75,6 +80,8 @@ def _load():
             ip = ctypes.POINTER(ctypes.c_int)
             i = ctypes.c_int
             d = ctypes.c_double
+            lib.oracle_set_threads.argtypes = [i]
+            lib.oracle_set_threads.restype = None
             lib.oracle_gaussian_taps.argtypes = [d, i, dp]
             lib.oracle_gaussian_taps.restype = None
             lib.oracle_gradient.argtypes = [dp, i, i, dp, dp]
@@ -116,6 +123,13 @@ def _load():
 def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
 
+
+
+def set_threads(n: int) -> None:
+    """Threads the per-pixel maps may use (0: the OpenMP default).  Results do
+    not depend on it; a caller that runs several oracle calls side by side
+    sets 1."""
+    _load().oracle_set_threads(int(n))
 
 def _ptr(a: np.ndarray | None):
     if a is None:

@@ -11,6 +11,12 @@
  *
  * Everything is double precision, row-major, pixel (y, x) at y*W + x; a
  * multi-band image is band-planar: band b, pixel (y, x) at (b*H + y)*W + x.
+ * Where the build enables OpenMP, the two per-pixel maps (the update and the
+ * convolution) and the maximum max|D| spread their pixels over threads; every
+ * pixel is still computed by one thread in the order written here, and a
+ * maximum does not depend on the order it is taken in, so results do not
+ * depend on the thread count.  Every sum over pixels (region statistics,
+ * counts) stays one sequential loop.
  *
  * What each piece follows in the paper:
  *   gaussian taps ........ G_sigma of Table I step 4 / Sec. III-D Step 4: the
@@ -69,6 +75,23 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the per-pixel maps (OpenMP builds): 0 = the OpenMP default. */
+static int g_threads = 0;
+
+void oracle_set_threads(int n) { g_threads = n > 0 ? n : 0; }
+
+static int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return g_threads > 0 ? g_threads : omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 #define ORACLE_TERM_REGION 0
 #define ORACLE_TERM_EDGE 1
@@ -169,6 +192,9 @@ static double conv_at(const double *f, int H, int W, const double *G, int ts,
 void oracle_conv_same_padded(const double *f, int H, int W, const double *G, int ts,
                              int pad, double *out)
 {
+    /* each output pixel is one thread's own sum, taken in the order above */
+#pragma omp parallel for schedule(static) num_threads(oracle_threads()) \
+    if ((size_t)H * W >= 65536)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x)
             out[(size_t)y * W + x] = conv_at(f, H, W, G, ts, y, x, pad);
@@ -286,6 +312,9 @@ static void prepare_ctx(step_ctx *c)
         return;
     }
     double m = 0.0;
+    /* a maximum does not depend on the order it is taken in */
+#pragma omp parallel for reduction(max : m) schedule(static) \
+    num_threads(oracle_threads()) if (N >= 65536)
     for (size_t p = 0; p < N; ++p) {
         double a = fabs(region_numerator_at(c, p));
         if (a > m) m = a;
@@ -371,6 +400,8 @@ int oracle_step_variant(const double *I, int H, int W, int B, int term,
     double *G = (double *)malloc((size_t)ts * ts * sizeof(double));
     step_ctx c;
     fill_ctx(&c, I, H, W, B, term, g, phi, dt);
+#pragma omp parallel for schedule(static) num_threads(oracle_threads()) \
+    if (N >= 65536)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x)
             u[(size_t)y * W + x] = update_at(&c, y, x);

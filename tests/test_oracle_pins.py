@@ -522,3 +522,27 @@ def test_table1_tie_goes_to_plus():
     phi[2:5, 2:5] = 0.0
     v, *_ = oracle.step(I, phi, ts=1, order="table1")
     assert (v[2:5, 2:5] == 1.0).all() and (v[0] == -1.0).all()
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    # the per-pixel maps and max|D| may run on several threads; every value,
+    # sum and count must come out the same as on one thread (sizes above the
+    # threshold at which the maps go parallel)
+    I = rng_image((3, 260, 270), 94)
+    phi0 = rng_phi(260, 270, 95)
+    g = oracle.edge_indicator(I, 1.0, 9, 255.0)
+    runs = []
+    try:
+        for n in (1, 4, 0):
+            oracle.set_threads(n)
+            v, mask, st = oracle.evolve(I, phi0, iterations=3)
+            ve, _, ste = oracle.evolve(I, phi0, "edge", g=g, iterations=3,
+                                       padding="replicate")
+            runs.append((v, mask, st, ve, ste, oracle.edge_indicator(I, 1.0, 9, 255.0)))
+    finally:
+        oracle.set_threads(0)
+    for other in runs[1:]:
+        assert np.array_equal(runs[0][0], other[0]) and np.array_equal(runs[0][1], other[1])
+        assert runs[0][2]["norm"] == other[2]["norm"]
+        assert np.array_equal(runs[0][2]["c_plus"], other[2]["c_plus"])
+        assert np.array_equal(runs[0][3], other[3]) and np.array_equal(runs[0][5], other[5])
