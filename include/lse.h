@@ -309,6 +309,29 @@ typedef struct {
 lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems,
                             int use_graph, lse_stats *stats, void *stream);
 
+/* Tile-height autotuner (the paper has no counterpart; its runs are
+ * single-threaded MATLAB).  The fused step for one band or the edge term
+ * works on tiles of 64 rows (8 warps per CTA, 3 CTAs per SM) or 32 rows
+ * (4 warps, 6 CTAs per SM): tall tiles recompute fewer halo rows, short
+ * tiles give small images enough CTAs to fill the GPU.  lse_autotune runs
+ * `iterations` iterations (1..1000, no early stop) of the given problems
+ * with each tile height, through lse_evolve_batch on scratch outputs (the
+ * problems' phi_out and mask_out are not written), and keeps the faster
+ * height per shape class in the context: term, storage type, template size
+ * and the power of two of the image's tile count.  Problems in one class are
+ * timed together, as a batch.  Later lse_evolve, lse_evolve_batch and
+ * lse_server_* calls on ctx use the table, so an image still gets the same
+ * bits from each of them; untuned classes use 64-row tiles (32 when the
+ * environment variable LSE_TILE_ROWS=32 was set at lse_create).  Changing an
+ * image's tile height regroups the partial sums of its region statistics,
+ * so its results may change in the last bits (within the parity tolerances).
+ * tile_rows (host, n entries, may be NULL) receives each problem's chosen
+ * height in rows, 0 where the tile form does not apply (more than one band
+ * of the region term, ts > 15, ts = 1).  Problems must pass lse_evolve_batch's
+ * checks; its errors are returned.  Synchronises `stream`. */
+lse_status lse_autotune(lse_ctx *ctx, int n, const lse_problem *problems, int iterations,
+                        int *tile_rows, void *stream);
+
 /* ------------------------------------------------------------ serving
  * A server runs evolution requests with continuous batching (the paper has
  * no counterpart).  Requests are queued on submission and admitted, first

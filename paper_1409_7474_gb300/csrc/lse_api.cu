@@ -253,7 +253,7 @@ void lse_destroy(lse_ctx *ctx)
     DeviceGuard g(ctx->device);
     void *bufs[] = {ctx->phi[0], ctx->phi[1], ctx->img, ctx->gbuf, ctx->raw_in,
                     ctx->phi0_st, ctx->g_st, ctx->out_phi, ctx->out_mask, ctx->q16,
-                    ctx->partials, ctx->st, ctx->arena, ctx->tables};
+                    ctx->partials, ctx->st, ctx->arena, ctx->tables, ctx->tune_out};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (ctx->st_host) cudaFreeHost(ctx->st_host);
@@ -294,6 +294,7 @@ lse_status lse_create(lse_ctx **out, int device, size_t max_pixels, int max_band
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     ctx->n_partials = partials_needed(ctx->sm_count);
     ctx->step_form = step_form_from_env();
+    ctx->tile_nw_default = tile_nw_from_env();
     cudaError_t e = cudaMalloc(&ctx->partials, sizeof(LsePartial) * ctx->n_partials);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->st, sizeof(LseDevState));
     if (e == cudaSuccess) e = cudaMemset(ctx->st, 0, sizeof(LseDevState));
@@ -504,7 +505,8 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
     // the step's kernel, work decomposition and tensor maps
     StepPlan plan;
     if (!plan_step(H, W, B, p, pitch, band_stride, data_s, ctx->phi, ctx->st, ctx->partials,
-                   ctx->sm_count, ctx->step_form, &plan)) {
+                   ctx->sm_count, ctx->step_form, tile_nw_for(ctx, H, W, p.term, sto, p.ts),
+                   &plan)) {
         set_err(ctx, "16-bit storage runs on the tile-form step only (LSE_STEP_KERNEL "
                      "narrowed the choice, or its tensor maps could not be encoded)");
         return LSE_ERR_INVALID_ARG;

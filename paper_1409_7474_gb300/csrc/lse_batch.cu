@@ -50,18 +50,73 @@ lse_status ensure_host(lse_ctx *ctx, size_t bytes, cudaStream_t s)
     return LSE_OK;
 }
 
-struct Layout {
-    int pitch;
-    size_t data, phi0, phi1;    // byte offsets in the arena
-};
-
 }  // namespace
 
 namespace lse_detail {
 
 ClassKey class_of(const StepPlan &plan, int term, int bands)
 {
-    return ClassKey{plan.form, term, bands, plan.args.rad, plan.wpc};
+    return ClassKey{plan.form, term, bands, plan.args.rad, plan.wpc, plan.args.storage,
+                    plan.form == LSE_FORM_TILE ? plan.args.nw : 0};
+}
+
+ImagePlanes image_planes(const lse_problem &q)
+{
+    ImagePlanes L;
+    L.pitch = round_up(q.W, 32);
+    L.es = q.params.storage == LSE_F32 ? 4 : 2;
+    const int bands = q.params.term == LSE_TERM_REGION ? q.B : 1;
+    const size_t plane = (size_t)q.H * L.pitch * L.es;
+    L.data = 0;
+    L.phi0 = align_up(plane * bands);
+    L.phi1 = L.phi0 + align_up(plane);
+    L.end = L.phi1 + align_up(plane);
+    return L;
+}
+
+cudaError_t stage_problem(const lse_problem &q, unsigned char *base, const ImagePlanes &L,
+                          LseDevState *st, LsePartial *parts, int nred, int sm_count,
+                          int form, int tile_nw, StepPlan *plan, bool *planned,
+                          cudaStream_t s)
+{
+    const lse_params &p = q.params;
+    const bool region = p.term == LSE_TERM_REGION;
+    const int sto = p.storage;
+    const int pitch = L.pitch;
+    const size_t bstride = (size_t)q.H * pitch;
+    void *data = base + L.data;
+    float *phi[2] = {reinterpret_cast<float *>(base + L.phi0),
+                     reinterpret_cast<float *>(base + L.phi1)};
+    cudaError_t e = cudaSuccess;
+    *planned = false;
+    if (sto == LSE_F32) {
+        if (region) e = launch_convert(q.image, q.dtype, q.H, q.W, q.B, static_cast<float *>(data),
+                                       pitch, s);
+        if (e == cudaSuccess)
+            e = launch_prologue(region ? data : nullptr, pitch, bstride, q.phi0,
+                                region ? nullptr : q.g, q.W, phi[0],
+                                region ? nullptr : static_cast<float *>(data), pitch, q.H, q.W,
+                                q.B, p.term, p.dt, LSE_F32, st, parts, nred, s);
+    } else {
+        // one band or g: FP32 first (into the two LSF planes, which together
+        // hold at least H x pitch floats), then rounded to the storage type
+        if (region) {
+            float *tmp = phi[0];
+            e = launch_convert(q.image, q.dtype, q.H, q.W, 1, tmp, pitch, s);
+            if (e == cudaSuccess) e = launch_quantise(tmp, pitch, q.H, q.W, data, pitch, sto, s);
+        } else {
+            e = launch_quantise(q.g, q.W, q.H, q.W, data, pitch, sto, s);
+        }
+        if (e == cudaSuccess)
+            e = launch_prologue(region ? data : nullptr, pitch, bstride, q.phi0,
+                                region ? nullptr : data, pitch, phi[0], nullptr, pitch, q.H,
+                                q.W, q.B, p.term, p.dt, sto, st, parts, nred, s);
+    }
+    if (e != cudaSuccess) return e;
+    *planned = plan_step(q.H, q.W, q.B, p, pitch, bstride, data, phi, st, parts, sm_count, form,
+                         tile_nw, plan) &&
+               plan->form != LSE_FORM_GENERIC;
+    return cudaSuccess;
 }
 
 size_t layout_classes(ClassMap &classes, BatchItem *items)
@@ -113,11 +168,8 @@ cudaError_t launch_class(const ClassKey &k, const Class &c, const BatchItem *ite
     const int nb = c.pre[k_act], nnb = c.npre[k_act];
     if (nb == 0) return cudaSuccess;
     const int *blk = reinterpret_cast<const int *>(tables + c.blk_off);
-    if (k.form == LSE_FORM_TILE) {
-        return k.term == LSE_TERM_EDGE
-                   ? launch_step_tile_batch_edge(k.rad, items, blk, n, nb, s)
-                   : launch_step_tile_batch_region1(k.rad, items, blk, n, nb, s);
-    }
+    if (k.form == LSE_FORM_TILE)
+        return launch_step_tile_batch(k.storage, k.term, k.nw, k.rad, items, blk, n, nb, s);
     if (k.term == LSE_TERM_EDGE)
         return launch_step_tma_batch_edge(k.rad, items, blk, n, nb, k.wpc, s);
     if (k.bands == 1)
@@ -170,10 +222,9 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
             return LSE_ERR_INVALID_ARG;
         }
         if ((r = check_params(ctx, q.params, q.B)) != LSE_OK) return r;
-        if (q.params.storage != LSE_F32 || q.params.order != LSE_ORDER_LISTING ||
-            q.params.padding != LSE_PAD_ZERO) {
-            set_err(ctx, "lse_evolve_batch: image %d: batches use LSE_F32 storage, the "
-                         "listing's order and zero padding", i);
+        if (q.params.order != LSE_ORDER_LISTING || q.params.padding != LSE_PAD_ZERO) {
+            set_err(ctx, "lse_evolve_batch: image %d: batches use the listing's order and "
+                         "zero padding", i);
             return LSE_ERR_INVALID_ARG;
         }
         const bool ok = classify(q.phi0, ctx->device) == PTR_DEVICE &&
@@ -190,20 +241,13 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
     }
 
     // ---- arena: per image [data][phi0][phi1]; then states, partials, items
-    std::vector<Layout> lay(n);
+    std::vector<ImagePlanes> lay(n);
+    std::vector<size_t> base(n);
     size_t off = 0;
     for (int i = 0; i < n; ++i) {
-        const lse_problem &q = problems[i];
-        const int pitch = round_up(q.W, 32);
-        const int bands = q.params.term == LSE_TERM_REGION ? q.B : 1;
-        const size_t plane = (size_t)q.H * pitch * 4;
-        lay[i].pitch = pitch;
-        lay[i].data = off;
-        off = align_up(off + plane * bands);
-        lay[i].phi0 = off;
-        off = align_up(off + plane);
-        lay[i].phi1 = off;
-        off = align_up(off + plane);
+        lay[i] = image_planes(problems[i]);
+        base[i] = off;
+        off += lay[i].end;
     }
     const int nparts = partials_needed(ctx->sm_count);
     const size_t st_off = off;
@@ -228,24 +272,14 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
         const lse_problem &q = problems[i];
         const lse_params &p = q.params;
         const bool region = p.term == LSE_TERM_REGION;
-        const int pitch = lay[i].pitch;
-        const size_t bstride = (size_t)q.H * pitch;
-        float *data = reinterpret_cast<float *>(A + lay[i].data);
-        float *phi[2] = {reinterpret_cast<float *>(A + lay[i].phi0),
-                         reinterpret_cast<float *>(A + lay[i].phi1)};
-        if (region) {
-            e = launch_convert(q.image, q.dtype, q.H, q.W, q.B, data, pitch, s);
-            if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_evolve_batch: convert");
-        }
         LsePartial *parts = partials + (size_t)nparts * i;
-        e = launch_prologue(region ? data : nullptr, pitch, bstride, q.phi0,
-                            region ? nullptr : q.g, q.W, phi[0], region ? nullptr : data, pitch,
-                            q.H, q.W, q.B, p.term, p.dt, LSE_F32, states + i, parts, nred, s);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_evolve_batch: prologue");
         StepPlan plan;
-        plan_step(q.H, q.W, q.B, p, pitch, bstride, data, phi, states + i, parts, ctx->sm_count,
-                  ctx->step_form, &plan);
-        if (plan.form == LSE_FORM_GENERIC) {
+        bool planned = false;
+        e = stage_problem(q, A + base[i], lay[i], states + i, parts, nred, ctx->sm_count,
+                          ctx->step_form, tile_nw_for(ctx, q.H, q.W, p.term, p.storage, p.ts),
+                          &plan, &planned, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_evolve_batch: staging and prologue");
+        if (!planned) {
             set_err(ctx, "lse_evolve_batch: image %d needs the plain step kernel (ts > 15, "
                          "more than 4 bands, or LSE_STEP_KERNEL=generic); run it with "
                          "lse_evolve",
@@ -258,8 +292,8 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
         it.phi_maps[1] = plan.phi_maps[1];
         it.data_map = plan.data_map;
         it.args = plan.args;
-        it.phi[0] = phi[0];
-        it.phi[1] = phi[1];
+        it.phi[0] = plan.phi[0];
+        it.phi[1] = plan.phi[1];
         it.nblocks = plan.nblocks;
         it.cap = p.iterations;
         it.reinit_period = p.reinit_period;
@@ -337,7 +371,7 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
     // ---- outputs and statistics
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         const lse_problem &q = problems[i];
-        e = launch_output(items[i].phi, lay[i].pitch, q.H, q.W, LSE_F32, states + i,
+        e = launch_output(items[i].phi, lay[i].pitch, q.H, q.W, q.params.storage, states + i,
                           q.phi_out, q.mask_out, s);
     }
     LseDevState *hs = reinterpret_cast<LseDevState *>(ht + toff);

@@ -2,7 +2,7 @@
 // internal; shared by lse_evolve_batch and lse_server).
 //
 // A class is the set of images served by one step kernel instantiation
-// (form, term, bands, radius, warps per CTA).  Its images are laid out
+// (form, term, bands, radius, warps per CTA, storage type, tile height).  Its images are laid out
 // longest-running first, so launch t needs only the CTAs of the images that
 // are still running: a prefix of the class's CTA table.
 #pragma once
@@ -16,13 +16,34 @@
 namespace lse_detail {
 
 struct ClassKey {
-    int form, term, bands, rad, wpc;
+    int form, term, bands, rad, wpc, storage, nw;
     bool operator<(const ClassKey &o) const
     {
-        return std::tie(form, term, bands, rad, wpc) <
-               std::tie(o.form, o.term, o.bands, o.rad, o.wpc);
+        return std::tie(form, term, bands, rad, wpc, storage, nw) <
+               std::tie(o.form, o.term, o.bands, o.rad, o.wpc, o.storage, o.nw);
     }
 };
+
+// Planes of one image in a batch arena or a server slot, as byte offsets
+// from the image's base: the data term (`bands` planes: the image bands, or
+// g), then the two LSF planes; each plane is H x pitch elements of the
+// storage type (4 or 2 bytes) and starts on 256 bytes.
+struct ImagePlanes {
+    int pitch;
+    int es;                        // bytes per element
+    size_t data, phi0, phi1, end;
+};
+ImagePlanes image_planes(const lse_problem &q);
+
+// Stages image q at `base` as lse_evolve would (the data term converted to
+// FP32, or rounded to the 16-bit storage type through an FP32 copy held in
+// the LSF planes), runs its prologue into st / parts with `nred` CTAs, and
+// plans its step.  Returns the first CUDA error; *planned is false when no
+// batched step kernel serves the image.
+cudaError_t stage_problem(const lse_problem &q, unsigned char *base, const ImagePlanes &L,
+                          LseDevState *st, LsePartial *parts, int nred, int sm_count,
+                          int form, int tile_nw, StepPlan *plan, bool *planned,
+                          cudaStream_t s);
 
 struct Class {
     std::vector<int> items;        // indices into the item array

@@ -2,7 +2,14 @@
 // C-ABI entry points share (internal).
 #pragma once
 
+#include <map>
+#include <tuple>
+
 #include "lse_internal.h"
+
+// Key of the tile-height table: term, storage type, radius, and the bucket
+// floor(log2(tiles)) of the image's tile count at 64-row tiles.
+using TuneKey = std::tuple<int, int, int, int>;
 
 struct lse_ctx {
     int device = 0;
@@ -36,6 +43,13 @@ struct lse_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool have_stats = false;
     int step_form = 0;               // LSE_STEP_KERNEL at creation (LSE_FORM_*)
+    // tile form: warps per CTA (8: 64-row tiles, 4: 32-row) per shape class,
+    // chosen by lse_autotune; tile_nw_default (LSE_TILE_ROWS at creation)
+    // for shapes it has not tuned
+    std::map<TuneKey, int> tile_tune;
+    int tile_nw_default = 8;
+    float *tune_out = nullptr;       // lse_autotune: outputs of its trial runs
+    size_t tune_out_cap = 0;         // bytes
     // lse_evolve_batch: per-image planes, states and partials; the work list
     // and CTA tables; a pinned mirror for uploads and the states
     void *arena = nullptr;
@@ -81,6 +95,9 @@ bool aligned16(const void *p);
 lse_status check_params(lse_ctx *ctx, const lse_params &p, int B);
 // Converts a device state record into the caller's statistics.
 void fill_stats(const LseDevState &h, float elapsed_ms, lse_stats *stats);
+// Warps per CTA of the tile-form step for an image on this context: the
+// lse_autotune choice for its shape class, else the context's default.
+int tile_nw_for(const lse_ctx *ctx, int H, int W, int term, int storage, int ts);
 
 template <typename T>
 lse_status ensure_t(lse_ctx *ctx, T **p, size_t *cap_elems, size_t elems,

@@ -92,13 +92,14 @@ struct StepArgs {
     int n_rowblocks;
     int th;                     // output rows per item
     int n_items;
+    int nw;                     // tile form: warps per CTA (8: 64-row tiles, 4: 32-row)
 };
 
 // One image of a batched evolution (lse_evolve_batch, lse_server), in device
 // memory.  The CTAs [start, start + nblocks) of its class's step launch work
 // on it; vector images also own the normaliser CTAs [nstart, nstart +
 // nnblocks).  Launch index t runs the image's iteration t - iter0.
-struct alignas(64) BatchItem {
+struct alignas(128) BatchItem {   // CUtensorMap needs 128-byte alignment
     CUtensorMap phi_maps[2];    // tensor maps of phi[0], phi[1]
     CUtensorMap data_map;
     StepArgs args;              // iteration-independent step arguments
@@ -212,8 +213,10 @@ cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap &phi_map,
 bool plan_step_tma(int H, int W, int B, int term, int rad, int sm_count,
                    StepArgs *a, int *nblocks, int *warps_per_block);
 // Tile-form step (one band or the edge term): work decomposition and launch.
-// Its tensor maps have boxes of 136 x (66) phi and 128 x 64 data elements.
-bool plan_step_tile(int H, int W, int B, int term, int rad, int sm_count,
+// nw = warps per CTA (8 or 4): tiles of 8 nw u rows; its tensor maps have
+// boxes of 136 x (8 nw + 2) phi and 128 (136 for 16-bit) x 8 nw data
+// elements.
+bool plan_step_tile(int H, int W, int B, int term, int rad, int nw, int sm_count,
                     StepArgs *a, int *nblocks);
 cudaError_t launch_step_tile(const StepArgs &a, const CUtensorMap &phi_map,
                              const CUtensorMap &data_map, int nblocks, cudaStream_t s);
@@ -222,10 +225,9 @@ int partials_needed(int sm_count);
 // Batched launches (lse_evolve_batch): iteration n over every image of one
 // class; CTA blockIdx.x works on image blk_item[blockIdx.x].  Step kernels
 // of the tile form (one band, edge term) and of the streaming form.
-cudaError_t launch_step_tile_batch_region1(int rad, const BatchItem *items, const int *blk_item,
-                                           long long n, int nblocks, cudaStream_t s);
-cudaError_t launch_step_tile_batch_edge(int rad, const BatchItem *items, const int *blk_item,
-                                        long long n, int nblocks, cudaStream_t s);
+cudaError_t launch_step_tile_batch(int storage, int term, int nw, int rad,
+                                   const BatchItem *items, const int *blk_item, long long n,
+                                   int nblocks, cudaStream_t s);
 cudaError_t launch_step_tma_batch_region1(int rad, const BatchItem *items, const int *blk_item,
                                           long long n, int nblocks, int wpc, cudaStream_t s);
 cudaError_t launch_step_tma_batch_edge(int rad, const BatchItem *items, const int *blk_item,
@@ -252,13 +254,17 @@ struct StepPlan {
 
 void gauss_taps(double sigma, int rad, double *out);
 int step_form_from_env();
+// Warps per CTA of the tile form unless tuned: 4 when LSE_TILE_ROWS=32,
+// else 8 (64-row tiles).
+int tile_nw_from_env();
 // Fills the step arguments for a call and picks its kernel (`requested` is
-// LSE_FORM_AUTO, _STREAM or _GENERIC).
-// Returns false when no step kernel serves the call (16-bit storage outside
-// the tile form).
+// LSE_FORM_AUTO, _STREAM or _GENERIC; `tile_nw` the tile form's warps per
+// CTA, 8 or 4).  Returns false when no step kernel serves the call (16-bit
+// storage outside the tile form).
 bool plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_stride,
                const void *data, float *const phi[2], LseDevState *st,
-               LsePartial *partials, int sm_count, int requested, StepPlan *plan);
+               LsePartial *partials, int sm_count, int requested, int tile_nw,
+               StepPlan *plan);
 // Launches iteration n (0-based) of the plan.
 cudaError_t launch_step(StepPlan &plan, int n, cudaStream_t s);
 // Sets the message lse_last_error(NULL) returns (calls without a context).

@@ -304,8 +304,8 @@ cudaError_t launch_output(float *const *bufs, int pitch, int H, int W, int stora
 
 int partials_needed(int sm_count)
 {
-    // the widest reducing launch: 3 CTAs of 8 warps per SM (TMA step) or
-    // 8 CTAs of 256 threads per SM (grid-stride kernels)
+    // the widest reducing launch: 3 CTAs of 8 warps or 6 of 4 warps per SM
+    // (tile-form step) or 8 CTAs of 256 threads per SM (grid-stride kernels)
     return sm_count * 8;
 }
 

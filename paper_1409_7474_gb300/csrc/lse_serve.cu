@@ -85,14 +85,11 @@ struct Request {
     lse_stats stats{};
 };
 
-// Bytes of one request's planes and partials in the arena.
+// Bytes of one request's planes (of its storage type) and partials in the
+// arena.
 size_t request_bytes(const lse_problem &q, int nparts)
 {
-    const size_t pitch = (size_t)((q.W + 31) / 32 * 32);
-    const size_t plane = (size_t)q.H * pitch * 4;
-    const int bands = q.params.term == LSE_TERM_REGION ? q.B : 1;
-    return align_up(plane * bands) + 2 * align_up(plane) +
-           align_up(sizeof(LsePartial) * (size_t)nparts);
+    return image_planes(q).end + align_up(sizeof(LsePartial) * (size_t)nparts);
 }
 
 }  // namespace
@@ -148,35 +145,31 @@ lse_status admit(lse_server *sv, Request &r, int slot, cudaStream_t s)
     const lse_problem &q = r.q;
     const lse_params &p = q.params;
     const bool region = p.term == LSE_TERM_REGION;
-    const int pitch = (q.W + 31) / 32 * 32;
-    const size_t plane = (size_t)q.H * pitch * 4;
     const int bands = region ? q.B : 1;
+    const ImagePlanes L = image_planes(q);
     unsigned char *base = sv->arena + r.off;
-    float *data = reinterpret_cast<float *>(base);
-    float *phi[2] = {reinterpret_cast<float *>(base + align_up(plane * bands)),
-                     reinterpret_cast<float *>(base + align_up(plane * bands) + align_up(plane))};
-    LsePartial *parts =
-        reinterpret_cast<LsePartial *>(base + align_up(plane * bands) + 2 * align_up(plane));
+    LsePartial *parts = reinterpret_cast<LsePartial *>(base + L.end);
     LseDevState *st = sv->d_states + slot;
-    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(LseDevState), s);
-    if (e == cudaSuccess && region) e = launch_convert(q.image, q.dtype, q.H, q.W, q.B, data, pitch, s);
-    if (e == cudaSuccess)
-        e = launch_prologue(region ? data : nullptr, pitch, (size_t)q.H * pitch, q.phi0,
-                            region ? nullptr : q.g, q.W, phi[0], region ? nullptr : data, pitch,
-                            q.H, q.W, q.B, p.term, p.dt, LSE_F32, st, parts,
-                            ctx->sm_count * 4, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_server: admit");
     StepPlan plan;
-    plan_step(q.H, q.W, q.B, p, pitch, (size_t)q.H * pitch, data, phi, st, parts, ctx->sm_count,
-              LSE_FORM_AUTO, &plan);
+    bool planned = false;
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(LseDevState), s);
+    if (e == cudaSuccess)
+        e = stage_problem(q, base, L, st, parts, ctx->sm_count * 4, ctx->sm_count, LSE_FORM_AUTO,
+                          tile_nw_for(ctx, q.H, q.W, p.term, p.storage, p.ts), &plan, &planned,
+                          s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_server: admit");
+    if (!planned) {
+        set_err(ctx, "lse_server: no batched step kernel serves request %dx%dx%d", q.H, q.W, q.B);
+        return LSE_ERR_INVALID_ARG;
+    }
     BatchItem &it = sv->items[slot];
     memset(&it, 0, sizeof(it));
     it.phi_maps[0] = plan.phi_maps[0];
     it.phi_maps[1] = plan.phi_maps[1];
     it.data_map = plan.data_map;
     it.args = plan.args;
-    it.phi[0] = phi[0];
-    it.phi[1] = phi[1];
+    it.phi[0] = plan.phi[0];
+    it.phi[1] = plan.phi[1];
     it.nblocks = plan.nblocks;
     it.cap = p.iterations;
     it.reinit_period = p.reinit_period;
@@ -184,7 +177,7 @@ lse_status admit(lse_server *sv, Request &r, int slot, cudaStream_t s)
     it.iter0 = sv->tick;
     if (region && q.B > 1) it.nnblocks = normaliser_blocks((long long)q.H * q.W, ctx->sm_count);
     r.key = class_of(plan, p.term, bands);
-    r.pitch = pitch;
+    r.pitch = L.pitch;
     r.slot = slot;
     r.state = REQ_RUNNING;
     return LSE_OK;
@@ -252,10 +245,10 @@ lse_status lse_server_submit(lse_server *sv, const lse_problem *problem, long lo
         return LSE_ERR_INVALID_ARG;
     }
     if ((r = check_params(ctx, q.params, q.B)) != LSE_OK) return r;
-    if (q.params.storage != LSE_F32 || q.params.ts > 15 || (region && q.B > 4) ||
-        q.params.order != LSE_ORDER_LISTING || q.params.padding != LSE_PAD_ZERO) {
-        set_err(ctx, "lse_server_submit: the server runs LSE_F32 storage, ts <= 15, at "
-                     "most 4 bands, the listing's order and zero padding");
+    if (q.params.ts > 15 || (region && q.B > 4) || q.params.order != LSE_ORDER_LISTING ||
+        q.params.padding != LSE_PAD_ZERO) {
+        set_err(ctx, "lse_server_submit: the server runs ts <= 15, at most 4 bands, the "
+                     "listing's order and zero padding");
         return LSE_ERR_INVALID_ARG;
     }
     {
@@ -367,8 +360,9 @@ lse_status lse_server_advance(lse_server *sv, int ticks, int *running, void *str
         const bool finished = h.done || h.iterations_run >= req.q.params.iterations ||
                               (h.status_bits & LSE_SBIT_ABORT);
         if (!finished) continue;
-        e = launch_output(sv->items[slot].phi, req.pitch, req.q.H, req.q.W, LSE_F32,
-                          sv->d_states + slot, req.q.phi_out, req.q.mask_out, s);
+        e = launch_output(sv->items[slot].phi, req.pitch, req.q.H, req.q.W,
+                          req.q.params.storage, sv->d_states + slot, req.q.phi_out,
+                          req.q.mask_out, s);
         fill_stats(h, -1.0f, &req.stats);
         retired.push_back(slot);
     }

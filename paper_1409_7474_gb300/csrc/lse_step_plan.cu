@@ -82,7 +82,8 @@ int step_form_from_env()
 
 bool plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_stride,
                const void *data, float *const phi[2], LseDevState *st,
-               LsePartial *partials, int sm_count, int requested, StepPlan *plan)
+               LsePartial *partials, int sm_count, int requested, int tile_nw,
+               StepPlan *plan)
 {
     StepArgs &a = plan->args;
     memset(&a, 0, sizeof(a));
@@ -123,11 +124,12 @@ bool plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_
         if (sto != LSE_F32) return false;
         requested = LSE_FORM_GENERIC;
     }
+    const int urows = 8 * tile_nw;      // u rows per tile; phi adds one halo row a side
     if (requested == LSE_FORM_AUTO &&
-        plan_step_tile(H, W, a.B, p.term, a.rad, sm_count, &a, &plan->nblocks) &&
-        encode_box(&plan->phi_maps[0], phi[0], sto, W, H, pitch, 0, 1, 136, 66) &&
-        encode_box(&plan->phi_maps[1], phi[1], sto, W, H, pitch, 0, 1, 136, 66) &&
-        encode_box(&plan->data_map, data, sto, W, H, pitch, band_stride, 1, data_box_w, 64)) {
+        plan_step_tile(H, W, a.B, p.term, a.rad, tile_nw, sm_count, &a, &plan->nblocks) &&
+        encode_box(&plan->phi_maps[0], phi[0], sto, W, H, pitch, 0, 1, 136, urows + 2) &&
+        encode_box(&plan->phi_maps[1], phi[1], sto, W, H, pitch, 0, 1, 136, urows + 2) &&
+        encode_box(&plan->data_map, data, sto, W, H, pitch, band_stride, 1, data_box_w, urows)) {
         plan->form = LSE_FORM_TILE;
     } else if (sto != LSE_F32) {
         return false;

@@ -46,11 +46,7 @@
 
 namespace lse_tile {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int kURows = 64;            // u / h rows per tile (TH + 2 RAD)
-constexpr int kURowsPerWarp = kURows / kWarps;
-constexpr int kPhiRows = kURows + 2;  // staged phi rows
+constexpr int kURowsPerWarp = 8;      // u rows each warp computes per tile
 constexpr int kPhiW = 136;            // staged phi columns
 
 // Storage of phi and of the data term in HBM: float, or half / bfloat16
@@ -119,38 +115,45 @@ struct Stor<__half> {
     }
 };
 
-// Shared-memory layout.  FP32 storage: h overwrites the phi rows (70 KB per
-// CTA); the data box is the 128 tile columns.  16-bit storage: a TMA box must
-// start on 16 bytes, so the data box starts with phi's, 4 columns left of the
-// tile (136 wide), and h has its own FP32 buffer (69 KB per CTA).
-template <int RAD, class T>
+// Tile geometry for NW warps per CTA: each warp takes 8 u rows, so a tile
+// has UR = 8 NW u rows and TH = UR - 2 RAD output rows (56 at NW = 8,
+// RAD = 4; 24 at NW = 4).  Shared-memory layout.  FP32 storage: h
+// overwrites the phi rows (70 KB per CTA at NW = 8, 36 KB at NW = 4); the
+// data box is the 128 tile columns.  16-bit storage: a TMA box must start on
+// 16 bytes, so the data box starts with phi's, 4 columns left of the tile
+// (136 wide), and h has its own FP32 buffer.
+template <int RAD, class T, int NW = 8>
 struct TileGeo {
+    static constexpr int THREADS = 32 * NW;
+    static constexpr int UR = kURowsPerWarp * NW;               // u / h rows per tile
+    static constexpr int PHI_ROWS = UR + 2;                     // staged phi rows
     static constexpr bool WIDE = sizeof(T) == 4;
     static constexpr int HL = (RAD + 3) / 4;                    // halo lanes per side
     static constexpr int USEFUL = 128 - 8 * HL;                 // output columns
-    static constexpr int TH = kURows - 2 * RAD;                 // output rows
-    static constexpr int RPW = (TH + kWarps - 1) / kWarps;      // output rows per warp
+    static constexpr int TH = UR - 2 * RAD;                     // output rows
+    static constexpr int RPW = (TH + NW - 1) / NW;              // output rows per warp
     static constexpr int DATA_W = WIDE ? 128 : kPhiW;           // staged data columns
     static constexpr int DATA_X0 = WIDE ? 0 : 4;                // tile column 0 within it
-    static constexpr int PHI_BYTES = kPhiRows * kPhiW * (int)sizeof(T);
-    static constexpr int DATA_BYTES = kURows * DATA_W * (int)sizeof(T);
+    static constexpr int PHI_BYTES = PHI_ROWS * kPhiW * (int)sizeof(T);
+    static constexpr int DATA_BYTES = UR * DATA_W * (int)sizeof(T);
     // offsets in floats: [sqrt table 32][2 mbarriers][old-sign words 64 x 4]
     // [phi][data][h (16-bit storage only)]
     static constexpr int SIGN_OFF = 64;
-    static constexpr int PHI_OFF = SIGN_OFF + kURows * 4;
+    static constexpr int PHI_OFF = SIGN_OFF + UR * 4;
     static constexpr int DATA_OFF = PHI_OFF + ((PHI_BYTES / 4 + 31) & ~31);
     static constexpr int HBUF_OFF = DATA_OFF + ((DATA_BYTES / 4 + 31) & ~31);
-    static constexpr int FLOATS = WIDE ? DATA_OFF + DATA_BYTES / 4 : HBUF_OFF + kURows * 128;
+    static constexpr int FLOATS = WIDE ? DATA_OFF + DATA_BYTES / 4 : HBUF_OFF + UR * 128;
     static constexpr int BYTES = FLOATS * 4 + 128;              // + alignment slack
     // h of u row ur: float index (ur + H_ROW0) * H_STRIDE + H_COL0 + 4 lane
     // from the phi buffer (FP32) or from the h buffer (16-bit)
     static constexpr int H_STRIDE = WIDE ? kPhiW : 128;
     static constexpr int H_ROW0 = WIDE ? 2 : 0;
     static constexpr int H_COL0 = WIDE ? 4 : 0;
-    // the vertical pass reads h rows up to 8 RPW - 1 + 2 RAD; past row 63
-    // they lie in other shared memory (FP32) or are clamped (16-bit)
-    static constexpr bool CLAMP_H = !WIDE && 8 * RPW - 1 + 2 * RAD > kURows - 1;
-    static constexpr int MIN_BLOCKS = RAD <= 4 ? 3 : 2;
+    // the vertical pass reads h rows up to NW RPW - 1 + 2 RAD; past row
+    // UR - 1 they lie in other shared memory (FP32) or are clamped (16-bit)
+    static constexpr bool CLAMP_H = !WIDE && NW * RPW - 1 + 2 * RAD > UR - 1;
+    // CTAs per SM (launch bounds): 24 warps for RAD <= 4, else 16
+    static constexpr int MIN_BLOCKS = (RAD <= 4 ? 24 : 16) / NW;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -216,11 +219,12 @@ __device__ __forceinline__ float4 lds4(const float *p)
 
 // One step over the tiles of one image, run by CTA `cta` of the `ncta` CTAs
 // given to it.
-template <int KIND_EDGE, int RAD, bool FAST, class T>
+template <int KIND_EDGE, int RAD, bool FAST, class T, int NW>
 __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *phi_map,
                                           const CUtensorMap *data_map, int cta, int ncta)
 {
-    using G = TileGeo<RAD, T>;
+    using G = TileGeo<RAD, T, NW>;
+    constexpr int kThreads = G::THREADS, kURows = G::UR, kPhiRows = G::PHI_ROWS;
     using S = Stor<T>;
     constexpr int HL = G::HL, TH = G::TH, P = 2 * RAD + 1, RPW = G::RPW;
     constexpr bool EDGE = KIND_EDGE != 0;
@@ -582,21 +586,21 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
     if (threadIdx.x == 0) lse_step_finalize(a, tot);
 }
 
-template <int KIND_EDGE, int RAD, bool FAST, class T>
-__global__ void __launch_bounds__(kThreads, TileGeo<RAD, T>::MIN_BLOCKS)
+template <int KIND_EDGE, int RAD, bool FAST, class T, int NW>
+__global__ void __launch_bounds__(TileGeo<RAD, T, NW>::THREADS, TileGeo<RAD, T, NW>::MIN_BLOCKS)
 step_tile_kernel(const __grid_constant__ StepArgs a,
                  const __grid_constant__ CUtensorMap phi_map,
                  const __grid_constant__ CUtensorMap data_map)
 {
-    tile_step<KIND_EDGE, RAD, FAST, T>(a, &phi_map, &data_map, blockIdx.x, gridDim.x);
+    tile_step<KIND_EDGE, RAD, FAST, T, NW>(a, &phi_map, &data_map, blockIdx.x, gridDim.x);
 }
 
-// Iteration n of a batch of images of one class (term, radius): CTA
+// Iteration n of a batch of images of one class (term, radius, storage): CTA
 // blockIdx.x works on image blk_item[blockIdx.x] with that image's CTA
 // count, statistics and iteration cap; its per-iteration flags are derived
 // here, so the launches of a whole evolution can be captured in a graph.
-template <int KIND_EDGE, int RAD>
-__global__ void __launch_bounds__(kThreads, TileGeo<RAD, float>::MIN_BLOCKS)
+template <int KIND_EDGE, int RAD, class T, int NW>
+__global__ void __launch_bounds__(TileGeo<RAD, T, NW>::THREADS, TileGeo<RAD, T, NW>::MIN_BLOCKS)
 step_tile_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ blk_item,
                        long long launch)
 {
@@ -606,7 +610,7 @@ step_tile_batch_kernel(const BatchItem *__restrict__ items, const int *__restric
     const int n = (int)nl;
     StepArgs a = it.args;
     lse_iteration_flags(a, n, it.cap, it.reinit_period, it.early_stop != 0, true, it.phi);
-    tile_step<KIND_EDGE, RAD, false, float>(a, &it.phi_maps[n & 1], &it.data_map,
+    tile_step<KIND_EDGE, RAD, false, T, NW>(a, &it.phi_maps[n & 1], &it.data_map,
                                             blockIdx.x - it.start, it.nblocks);
 }
 
@@ -616,64 +620,66 @@ __host__ __device__ inline bool is_fast(const StepArgs &a)
     return a.binary_in && a.store_bin && !a.count_flips && !a.binarise_in;
 }
 
-template <int KIND_EDGE, int RAD, class T>
+template <int KIND_EDGE, int RAD, class T, int NW>
 cudaError_t launch_tile_one(const StepArgs &a, const CUtensorMap &pm, const CUtensorMap &dm,
                             int nblocks, cudaStream_t s)
 {
-    using G = TileGeo<RAD, T>;
-    auto kern = is_fast(a) ? step_tile_kernel<KIND_EDGE, RAD, true, T>
-                           : step_tile_kernel<KIND_EDGE, RAD, false, T>;
+    using G = TileGeo<RAD, T, NW>;
+    auto kern = is_fast(a) ? step_tile_kernel<KIND_EDGE, RAD, true, T, NW>
+                           : step_tile_kernel<KIND_EDGE, RAD, false, T, NW>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          G::BYTES);
     if (e != cudaSuccess) return e;
-    kern<<<nblocks, kThreads, G::BYTES, s>>>(a, pm, dm);
+    kern<<<nblocks, G::THREADS, G::BYTES, s>>>(a, pm, dm);
     return cudaGetLastError();
 }
 
-template <int KIND_EDGE, class T>
+// Instantiations for one tile height (NW warps per CTA), every radius.
+template <int KIND_EDGE, class T, int NW>
 cudaError_t launch_tile_kind(const StepArgs &a, const CUtensorMap &pm, const CUtensorMap &dm,
                              int nblocks, cudaStream_t s)
 {
     switch (a.rad) {
-    case 1: return launch_tile_one<KIND_EDGE, 1, T>(a, pm, dm, nblocks, s);
-    case 2: return launch_tile_one<KIND_EDGE, 2, T>(a, pm, dm, nblocks, s);
-    case 3: return launch_tile_one<KIND_EDGE, 3, T>(a, pm, dm, nblocks, s);
-    case 4: return launch_tile_one<KIND_EDGE, 4, T>(a, pm, dm, nblocks, s);
-    case 5: return launch_tile_one<KIND_EDGE, 5, T>(a, pm, dm, nblocks, s);
-    case 6: return launch_tile_one<KIND_EDGE, 6, T>(a, pm, dm, nblocks, s);
-    case 7: return launch_tile_one<KIND_EDGE, 7, T>(a, pm, dm, nblocks, s);
+    case 1: return launch_tile_one<KIND_EDGE, 1, T, NW>(a, pm, dm, nblocks, s);
+    case 2: return launch_tile_one<KIND_EDGE, 2, T, NW>(a, pm, dm, nblocks, s);
+    case 3: return launch_tile_one<KIND_EDGE, 3, T, NW>(a, pm, dm, nblocks, s);
+    case 4: return launch_tile_one<KIND_EDGE, 4, T, NW>(a, pm, dm, nblocks, s);
+    case 5: return launch_tile_one<KIND_EDGE, 5, T, NW>(a, pm, dm, nblocks, s);
+    case 6: return launch_tile_one<KIND_EDGE, 6, T, NW>(a, pm, dm, nblocks, s);
+    case 7: return launch_tile_one<KIND_EDGE, 7, T, NW>(a, pm, dm, nblocks, s);
     default: return cudaErrorNotSupported;
     }
 }
 
-// CTAs per SM the tile form runs at for a radius (its launch bounds).
-inline int tile_blocks_per_sm(int rad) { return rad <= 4 ? 3 : 2; }
+// CTAs per SM the tile form runs at for a radius and tile height (its
+// launch bounds).
+inline int tile_blocks_per_sm(int rad, int nw) { return (rad <= 4 ? 24 : 16) / nw; }
 
-template <int KIND_EDGE, int RAD>
+template <int KIND_EDGE, int RAD, class T, int NW>
 cudaError_t launch_tile_batch_one(const BatchItem *items, const int *blk_item, long long n,
                                   int nblocks, cudaStream_t s)
 {
-    using G = TileGeo<RAD, float>;
-    auto kern = step_tile_batch_kernel<KIND_EDGE, RAD>;
+    using G = TileGeo<RAD, T, NW>;
+    auto kern = step_tile_batch_kernel<KIND_EDGE, RAD, T, NW>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          G::BYTES);
     if (e != cudaSuccess) return e;
-    kern<<<nblocks, kThreads, G::BYTES, s>>>(items, blk_item, n);
+    kern<<<nblocks, G::THREADS, G::BYTES, s>>>(items, blk_item, n);
     return cudaGetLastError();
 }
 
-template <int KIND_EDGE>
+template <int KIND_EDGE, class T, int NW>
 cudaError_t launch_tile_batch(int rad, const BatchItem *items, const int *blk_item, long long n,
                               int nblocks, cudaStream_t s)
 {
     switch (rad) {
-    case 1: return launch_tile_batch_one<KIND_EDGE, 1>(items, blk_item, n, nblocks, s);
-    case 2: return launch_tile_batch_one<KIND_EDGE, 2>(items, blk_item, n, nblocks, s);
-    case 3: return launch_tile_batch_one<KIND_EDGE, 3>(items, blk_item, n, nblocks, s);
-    case 4: return launch_tile_batch_one<KIND_EDGE, 4>(items, blk_item, n, nblocks, s);
-    case 5: return launch_tile_batch_one<KIND_EDGE, 5>(items, blk_item, n, nblocks, s);
-    case 6: return launch_tile_batch_one<KIND_EDGE, 6>(items, blk_item, n, nblocks, s);
-    case 7: return launch_tile_batch_one<KIND_EDGE, 7>(items, blk_item, n, nblocks, s);
+    case 1: return launch_tile_batch_one<KIND_EDGE, 1, T, NW>(items, blk_item, n, nblocks, s);
+    case 2: return launch_tile_batch_one<KIND_EDGE, 2, T, NW>(items, blk_item, n, nblocks, s);
+    case 3: return launch_tile_batch_one<KIND_EDGE, 3, T, NW>(items, blk_item, n, nblocks, s);
+    case 4: return launch_tile_batch_one<KIND_EDGE, 4, T, NW>(items, blk_item, n, nblocks, s);
+    case 5: return launch_tile_batch_one<KIND_EDGE, 5, T, NW>(items, blk_item, n, nblocks, s);
+    case 6: return launch_tile_batch_one<KIND_EDGE, 6, T, NW>(items, blk_item, n, nblocks, s);
+    case 7: return launch_tile_batch_one<KIND_EDGE, 7, T, NW>(items, blk_item, n, nblocks, s);
     default: return cudaErrorNotSupported;
     }
 }

@@ -15,15 +15,26 @@ cudaError_t launch_step_tma_multiband(const StepArgs &, const CUtensorMap &,
 int step_tma_warp_bytes_region1(int rad);
 int step_tma_warp_bytes_edge(int rad);
 int step_tma_warp_bytes_multiband(int rad);
-cudaError_t launch_step_tile_region1(const StepArgs &, const CUtensorMap &,
-                                     const CUtensorMap &, int, cudaStream_t);
-cudaError_t launch_step_tile_edge(const StepArgs &, const CUtensorMap &,
-                                  const CUtensorMap &, int, cudaStream_t);
-int step_tile_blocks_per_sm(int rad);
-cudaError_t launch_step_tile_bf16(const StepArgs &, const CUtensorMap &,
-                                  const CUtensorMap &, int, cudaStream_t);
-cudaError_t launch_step_tile_f16(const StepArgs &, const CUtensorMap &,
-                                 const CUtensorMap &, int, cudaStream_t);
+// Tile-form instantiations, one file per storage type, term and tile
+// height (lse_step_tile_<storage>_<term>_nw<warps>.cu).
+#define LSE_TILE_DECL(SUF)                                                              \
+    cudaError_t launch_step_tile_##SUF(const StepArgs &, const CUtensorMap &,           \
+                                       const CUtensorMap &, int, cudaStream_t);         \
+    cudaError_t launch_step_tile_batch_##SUF(int, const BatchItem *, const int *,       \
+                                             long long, int, cudaStream_t);
+LSE_TILE_DECL(f32_region_nw8)
+LSE_TILE_DECL(f32_region_nw4)
+LSE_TILE_DECL(f32_edge_nw8)
+LSE_TILE_DECL(f32_edge_nw4)
+LSE_TILE_DECL(bf16_region_nw8)
+LSE_TILE_DECL(bf16_region_nw4)
+LSE_TILE_DECL(bf16_edge_nw8)
+LSE_TILE_DECL(bf16_edge_nw4)
+LSE_TILE_DECL(f16_region_nw8)
+LSE_TILE_DECL(f16_region_nw4)
+LSE_TILE_DECL(f16_edge_nw8)
+LSE_TILE_DECL(f16_edge_nw4)
+#undef LSE_TILE_DECL
 
 }  // namespace lse_detail
 
@@ -95,16 +106,18 @@ cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap &phi_map,
     }
 }
 
-// Tile form: tiles of (64 - 2 rad) output rows x (128 - 8 ceil(rad / 4))
-// output columns, walked by as many CTAs as fit on the SMs at once.
-bool plan_step_tile(int H, int W, int B, int term, int rad, int sm_count,
+// Tile form: tiles of (8 nw - 2 rad) output rows x (128 - 8 ceil(rad / 4))
+// output columns (nw = warps per CTA, 8 or 4), walked by as many CTAs as fit
+// on the SMs at once: 24 warps per SM for rad <= 4, else 16 (the kernels'
+// launch bounds).
+bool plan_step_tile(int H, int W, int B, int term, int rad, int nw, int sm_count,
                     StepArgs *a, int *nblocks)
 {
-    if (rad < 1 || rad > 7) return false;
+    if (rad < 1 || rad > 7 || (nw != 8 && nw != 4)) return false;
     if (term == LSE_TERM_REGION && B != 1) return false;
     const int hl = (rad + 3) / 4;
     const int useful = 128 - 8 * hl;
-    const int th = 64 - 2 * rad;
+    const int th = 8 * nw - 2 * rad;
     const int tiles_x = (W + useful - 1) / useful;
     const int tiles_y = (H + th - 1) / th;
     a->useful = useful;
@@ -112,20 +125,62 @@ bool plan_step_tile(int H, int W, int B, int term, int rad, int sm_count,
     a->n_rowblocks = tiles_y;
     a->th = th;
     a->n_items = tiles_x * tiles_y;
+    a->nw = nw;
     int blocks = a->n_items;
-    const int resident = sm_count * step_tile_blocks_per_sm(rad);
+    const int resident = sm_count * ((rad <= 4 ? 24 : 16) / nw);
     if (blocks > resident) blocks = resident;
     *nblocks = blocks;
     return true;
 }
 
+namespace {
+
+typedef cudaError_t (*TileFn)(const StepArgs &, const CUtensorMap &, const CUtensorMap &, int,
+                              cudaStream_t);
+typedef cudaError_t (*TileBatchFn)(int, const BatchItem *, const int *, long long, int,
+                                   cudaStream_t);
+
+// [storage: f32, f16, bf16][term: region, edge][nw: 8, 4]
+const TileFn kTile[3][2][2] = {
+    {{launch_step_tile_f32_region_nw8, launch_step_tile_f32_region_nw4},
+     {launch_step_tile_f32_edge_nw8, launch_step_tile_f32_edge_nw4}},
+    {{launch_step_tile_f16_region_nw8, launch_step_tile_f16_region_nw4},
+     {launch_step_tile_f16_edge_nw8, launch_step_tile_f16_edge_nw4}},
+    {{launch_step_tile_bf16_region_nw8, launch_step_tile_bf16_region_nw4},
+     {launch_step_tile_bf16_edge_nw8, launch_step_tile_bf16_edge_nw4}}};
+const TileBatchFn kTileBatch[3][2][2] = {
+    {{launch_step_tile_batch_f32_region_nw8, launch_step_tile_batch_f32_region_nw4},
+     {launch_step_tile_batch_f32_edge_nw8, launch_step_tile_batch_f32_edge_nw4}},
+    {{launch_step_tile_batch_f16_region_nw8, launch_step_tile_batch_f16_region_nw4},
+     {launch_step_tile_batch_f16_edge_nw8, launch_step_tile_batch_f16_edge_nw4}},
+    {{launch_step_tile_batch_bf16_region_nw8, launch_step_tile_batch_bf16_region_nw4},
+     {launch_step_tile_batch_bf16_edge_nw8, launch_step_tile_batch_bf16_edge_nw4}}};
+
+bool tile_index(int storage, int term, int nw, int *si, int *ti, int *ni)
+{
+    *si = storage == LSE_F32 ? 0 : storage == LSE_F16 ? 1 : storage == LSE_BF16 ? 2 : -1;
+    *ti = term == LSE_TERM_EDGE ? 1 : 0;
+    *ni = nw == 8 ? 0 : nw == 4 ? 1 : -1;
+    return *si >= 0 && *ni >= 0;
+}
+
+}  // namespace
+
 cudaError_t launch_step_tile(const StepArgs &a, const CUtensorMap &phi_map,
                              const CUtensorMap &data_map, int nblocks, cudaStream_t s)
 {
-    if (a.storage == LSE_BF16) return launch_step_tile_bf16(a, phi_map, data_map, nblocks, s);
-    if (a.storage == LSE_F16) return launch_step_tile_f16(a, phi_map, data_map, nblocks, s);
-    if (a.term == LSE_TERM_EDGE) return launch_step_tile_edge(a, phi_map, data_map, nblocks, s);
-    return launch_step_tile_region1(a, phi_map, data_map, nblocks, s);
+    int si, ti, ni;
+    if (!tile_index(a.storage, a.term, a.nw, &si, &ti, &ni)) return cudaErrorNotSupported;
+    return kTile[si][ti][ni](a, phi_map, data_map, nblocks, s);
+}
+
+cudaError_t launch_step_tile_batch(int storage, int term, int nw, int rad,
+                                   const BatchItem *items, const int *blk_item, long long n,
+                                   int nblocks, cudaStream_t s)
+{
+    int si, ti, ni;
+    if (!tile_index(storage, term, nw, &si, &ti, &ni)) return cudaErrorNotSupported;
+    return kTileBatch[si][ti][ni](rad, items, blk_item, n, nblocks, s);
 }
 
 }  // namespace lse_detail

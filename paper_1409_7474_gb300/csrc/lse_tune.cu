@@ -1,0 +1,145 @@
+// lse_tune.cu -- the tile-height autotuner (lse_autotune) and the table it
+// fills.
+//
+// The tile-form step runs CTAs of 8 warps on 64-row tiles (3 CTAs per SM)
+// or of 4 warps on 32-row tiles (6 per SM).  Tall tiles recompute fewer halo
+// rows (64 / 56 u rows per output row at radius 4, against 32 / 24); short
+// tiles give twice the CTAs, which an image of few tiles needs to fill the
+// GPU, and more CTAs per SM to cover each other's TMA waits.  Which wins
+// depends on the image size, the radius and what else runs beside it, so
+// lse_autotune times both on the caller's own work and keeps the faster per
+// shape class (term, storage type, radius, and the power of two of the tile
+// count).  lse_evolve, lse_evolve_batch and lse_server_* all read the same
+// table, so an image gets the same tiles, the same partial sums and the
+// same bits whichever of them runs it.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "lse_ctx.h"
+
+using namespace lse_detail;
+
+namespace {
+
+// Shape class of an image for the tile-height table, or false when the
+// tile form does not serve it.
+bool tune_key(int H, int W, int B, int term, int storage, int ts, TuneKey *key)
+{
+    const int rad = (ts - 1) / 2;
+    if (rad < 1 || rad > 7 || (term == LSE_TERM_REGION && B != 1)) return false;
+    const int useful = 128 - 8 * ((rad + 3) / 4);
+    const long long tiles =
+        (long long)((W + useful - 1) / useful) * ((H + 64 - 2 * rad - 1) / (64 - 2 * rad));
+    int bucket = 0;
+    while ((2LL << bucket) <= tiles) ++bucket;
+    *key = TuneKey{term, storage, rad, bucket};
+    return true;
+}
+
+}  // namespace
+
+namespace lse_detail {
+
+int tile_nw_from_env()
+{
+    const char *v = getenv("LSE_TILE_ROWS");
+    return (v && strcmp(v, "32") == 0) ? 4 : 8;
+}
+
+int tile_nw_for(const lse_ctx *ctx, int H, int W, int term, int storage, int ts)
+{
+    TuneKey key;
+    if (!tune_key(H, W, 1, term, storage, ts, &key)) return ctx->tile_nw_default;
+    auto it = ctx->tile_tune.find(key);
+    return it == ctx->tile_tune.end() ? ctx->tile_nw_default : it->second;
+}
+
+}  // namespace lse_detail
+
+extern "C" lse_status lse_autotune(lse_ctx *ctx, int n, const lse_problem *problems,
+                                   int iterations, int *tile_rows, void *stream)
+{
+    if (!ctx) return LSE_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (n < 1 || n > LSE_BATCH_MAX || !problems || iterations < 1 || iterations > 1000) {
+        set_err(ctx, "lse_autotune: need 1 <= n <= %d problems and 1 <= iterations <= 1000",
+                LSE_BATCH_MAX);
+        return LSE_ERR_INVALID_ARG;
+    }
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return cuda_fail(ctx, cudaErrorInvalidDevice, "set device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    // the problems the tile form serves, grouped by shape class; trial
+    // copies run `iterations` iterations without early stop into scratch
+    std::map<TuneKey, std::vector<int>> groups;
+    for (int i = 0; i < n; ++i) {
+        const lse_problem &q = problems[i];
+        TuneKey key;
+        if (q.H >= 1 && q.W >= 1 &&
+            tune_key(q.H, q.W, q.B, q.params.term, q.params.storage, q.params.ts, &key))
+            groups[key].push_back(i);
+    }
+    size_t out_bytes = 0;
+    for (int i = 0; i < n; ++i) {
+        const size_t px = (size_t)problems[i].H * problems[i].W;
+        out_bytes += (px * 4 + 255) / 256 * 256 + (px + 255) / 256 * 256;
+    }
+    lse_status r = ensure(ctx, reinterpret_cast<void **>(&ctx->tune_out), &ctx->tune_out_cap,
+                          out_bytes, s, "lse_autotune outputs");
+    if (r != LSE_OK) return r;
+    std::vector<lse_problem> trial(problems, problems + n);
+    unsigned char *o = reinterpret_cast<unsigned char *>(ctx->tune_out);
+    for (int i = 0; i < n; ++i) {
+        const size_t px = (size_t)trial[i].H * trial[i].W;
+        trial[i].phi_out = reinterpret_cast<float *>(o);
+        o += (px * 4 + 255) / 256 * 256;
+        trial[i].mask_out = o;
+        o += (px + 255) / 256 * 256;
+        trial[i].params.iterations = iterations;
+        trial[i].params.early_stop_frac = 0.0f;
+    }
+
+    const int candidates[2] = {8, 4};
+    for (auto &g : groups) {
+        std::vector<lse_problem> set;
+        for (int i : g.second) set.push_back(trial[i]);
+        std::vector<lse_stats> st(set.size());
+        float best_ms = INFINITY;
+        int best = ctx->tile_nw_default;
+        for (int nw : candidates) {
+            ctx->tile_tune[g.first] = nw;
+            float ms = INFINITY;
+            // the first run warms up (modules, scratch growth); the best of
+            // the next two counts
+            for (int rep = 0; rep < 3; ++rep) {
+                r = lse_evolve_batch(ctx, (int)set.size(), set.data(), 0, st.data(), stream);
+                if (r != LSE_OK) {
+                    ctx->tile_tune.erase(g.first);
+                    return r;
+                }
+                if (rep > 0) ms = std::min(ms, st[0].elapsed_ms);
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = nw;
+            }
+        }
+        ctx->tile_tune[g.first] = best;
+    }
+    if (tile_rows)
+        for (int i = 0; i < n; ++i) {
+            const lse_problem &q = problems[i];
+            TuneKey key;
+            tile_rows[i] = q.H >= 1 && q.W >= 1 && tune_key(q.H, q.W, q.B, q.params.term,
+                                                            q.params.storage, q.params.ts, &key)
+                               ? 8 * ctx->tile_tune[key]
+                               : 0;
+        }
+    return LSE_OK;
+}

@@ -109,6 +109,9 @@ _lib.lse_evolve_static.restype = ctypes.c_int
 _lib.lse_evolve_batch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
                                   ctypes.POINTER(Stats), _vp]
 _lib.lse_evolve_batch.restype = ctypes.c_int
+_lib.lse_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
+                              ctypes.POINTER(ctypes.c_int), _vp]
+_lib.lse_autotune.restype = ctypes.c_int
 _lib.lse_server_create.argtypes = [_vp, ctypes.c_size_t, ctypes.POINTER(_vp)]
 _lib.lse_server_create.restype = ctypes.c_int
 _lib.lse_server_destroy.argtypes = [_vp]
@@ -123,7 +126,7 @@ _lib.lse_server_poll.restype = ctypes.c_int
 
 SYMBOLS = ("lse_create", "lse_destroy", "lse_last_error", "lse_precompute_edge",
            "lse_evolve", "lse_get_stats", "lse_version", "lse_evolve_static",
-           "lse_evolve_batch", "lse_server_create", "lse_server_destroy",
+           "lse_evolve_batch", "lse_autotune", "lse_server_create", "lse_server_destroy",
            "lse_server_submit", "lse_server_advance", "lse_server_poll")
 STATIC_MAX_PIXELS = 262144
 
@@ -287,8 +290,9 @@ class Context:
     def evolve_batch(self, items, use_graph: bool = True, stream=None):
         """lse_evolve_batch over `items`, a list of dicts with the keys of
         ``evolve`` (image or g, phi0, term, dt, sigma, ts, iterations,
-        reinit_period, early_stop_frac, and optionally phi_out / mask_out),
-        all CUDA tensors.  Returns a list of (phi_out, mask_out, stats)."""
+        reinit_period, early_stop_frac, storage, and optionally phi_out /
+        mask_out), all CUDA tensors.  Returns a list of (phi_out, mask_out,
+        stats)."""
         n = len(items)
         probs = (Problem * n)()
         outs = []
@@ -299,6 +303,20 @@ class Context:
         self._check(_lib.lse_evolve_batch(self._h, n, probs, 1 if use_graph else 0, st,
                                           _stream_ptr(stream, self.device)))
         return [(o[0], o[1], st[i].to_dict(o[2])) for i, o in enumerate(outs)]
+
+    def autotune(self, items, iterations: int = 12, stream=None):
+        """lse_autotune over `items` (dicts as in ``evolve_batch``): times both
+        tile heights on them and keeps the faster per shape class in this
+        context.  Returns each item's chosen tile height in rows (0 where the
+        tile form does not apply)."""
+        n = len(items)
+        probs = (Problem * n)()
+        for i, it in enumerate(items):
+            probs[i] = _problem(it)[0]
+        rows = (ctypes.c_int * n)()
+        self._check(_lib.lse_autotune(self._h, n, probs, int(iterations), rows,
+                                      _stream_ptr(stream, self.device)))
+        return list(rows)
 
     def stats(self, bands: int = 8) -> dict:
         st = Stats()
@@ -327,7 +345,8 @@ def _problem(it: dict):
         mask_out = torch.empty((H, W), dtype=torch.uint8, device=phi0.device)
     p = Params(term_code, float(it.get("dt", 15.0)), float(it.get("sigma", 1.0)),
                int(it.get("ts", 9)), int(it.get("iterations", 200)),
-               int(it.get("reinit_period", 1)), float(it.get("early_stop_frac", 0.0)), F32)
+               int(it.get("reinit_period", 1)), float(it.get("early_stop_frac", 0.0)),
+               STORAGE[it.get("storage", "f32")])
     prob = Problem(_ptr(image), dcode, H, W, B,
                    _ptr(it.get("g")) if term_code == TERM_EDGE else None,
                    _ptr(phi0), p, _ptr(phi_out), _ptr(mask_out))

@@ -46,7 +46,8 @@ def device_items(torch, ctx, probs):
     for q in probs:
         img = torch.from_numpy(q["image"]).cuda()
         it = {"phi0": torch.from_numpy(q["phi0"]).cuda(), "term": q["term"],
-              "iterations": q["iterations"], "early_stop_frac": q["early_stop_frac"]}
+              "iterations": q["iterations"], "early_stop_frac": q["early_stop_frac"],
+              "storage": q.get("storage", "f32")}
         if q["term"] == "region":
             it["image"] = img
         else:
@@ -59,7 +60,7 @@ def device_items(torch, ctx, probs):
 def single(torch, ctx, it):
     v, m, st = ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
                           iterations=it["iterations"],
-                          early_stop_frac=it["early_stop_frac"])
+                          early_stop_frac=it["early_stop_frac"], storage=it["storage"])
     torch.cuda.synchronize()
     return v.cpu().numpy(), m.cpu().numpy(), st
 
@@ -80,6 +81,34 @@ def test_batch_equals_single_calls(torch, ctx, use_graph):
     for it, (v, m, st) in zip(items, res):
         v1, m1, st1 = single(torch, ctx, it)
         assert same_bits(v.cpu().numpy(), v1)
+        assert np.array_equal(m.cpu().numpy(), m1)
+        for key in ("iterations_run", "last_flips", "area_plus", "status"):
+            assert st[key] == st1[key], key
+        assert st["c_plus"] == st1["c_plus"] and st["c_minus"] == st1["c_minus"]
+
+
+def with_16bit_storage(probs):
+    """BF16 and F16 storage, alternating, for the images 16-bit storage
+    serves (one band, or the edge term); FP32 for the 4-band region images."""
+    k = 0
+    for q in probs:
+        if q["term"] == "edge" or q["image"].shape[0] == 1:
+            q["storage"] = ("bf16", "f16")[k % 2]
+            k += 1
+    return probs
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_16bit_storage_equals_single_calls(torch, ctx, use_graph):
+    probs = with_16bit_storage(scenes.batch_problems(20, seed=13, min_side=40, max_side=400,
+                                                     cap_range=(3, 40)))
+    assert sum(q.get("storage", "f32") != "f32" for q in probs) >= 8
+    items = device_items(torch, ctx, probs)
+    res = ctx.evolve_batch(items, use_graph=use_graph)
+    torch.cuda.synchronize()
+    for it, (v, m, st) in zip(items, res):
+        v1, m1, st1 = single(torch, ctx, it)
+        assert same_bits(v.cpu().numpy(), v1), it["storage"]
         assert np.array_equal(m.cpu().numpy(), m1)
         for key in ("iterations_run", "last_flips", "area_plus", "status"):
             assert st[key] == st1[key], key
@@ -146,7 +175,10 @@ def test_batch_rejections(torch, lse, ctx):
     assert run(x, big_ts) == lse.LSE_ERR_INVALID_ARG
     assert b"plain step kernel" in lib.lse_last_error(ctx._h)
     half = lse.Params(lse.TERM_REGION, 15.0, 1.0, 9, 3, 1, 0.0, lse.BF16)
-    assert run(x, half) == lse.LSE_ERR_INVALID_ARG
+    assert run(x, half) == lse.LSE_OK
+    table1 = lse.Params(lse.TERM_REGION, 15.0, 1.0, 9, 3, 1, 0.0, lse.F32, 1, 0)
+    assert run(x, table1) == lse.LSE_ERR_INVALID_ARG
+    assert b"order" in lib.lse_last_error(ctx._h)
     host_phi = torch.ones((64, 64))
     assert run(x, ok, phi0=host_phi) == lse.LSE_ERR_INVALID_ARG
     assert b"device memory" in lib.lse_last_error(ctx._h)

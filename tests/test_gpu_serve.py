@@ -41,7 +41,8 @@ def device_items(torch, ctx, probs):
     for q in probs:
         img = torch.from_numpy(q["image"]).cuda()
         it = {"phi0": torch.from_numpy(q["phi0"]).cuda(), "term": q["term"],
-              "iterations": q["iterations"], "early_stop_frac": q["early_stop_frac"]}
+              "iterations": q["iterations"], "early_stop_frac": q["early_stop_frac"],
+              "storage": q.get("storage", "f32")}
         if q["term"] == "region":
             it["image"] = img
         else:
@@ -53,7 +54,8 @@ def device_items(torch, ctx, probs):
 
 def alone(torch, ctx, it):
     v, m, st = ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
-                          iterations=it["iterations"], early_stop_frac=it["early_stop_frac"])
+                          iterations=it["iterations"], early_stop_frac=it["early_stop_frac"],
+                          storage=it["storage"])
     torch.cuda.synchronize()
     return v.cpu().numpy(), m.cpu().numpy(), st
 
@@ -98,6 +100,60 @@ def test_served_results_equal_alone(torch, lse, ctx):
         for key in ("iterations_run", "last_flips", "area_plus", "status"):
             assert st[key] == st1[key], key
         assert st["c_plus"] == st1["c_plus"]
+
+
+def test_served_16bit_results_equal_alone(torch, lse, ctx):
+    # BF16 / F16 storage where it applies (one band or the edge term), FP32
+    # for the 4-band region images, all in one mix
+    probs = scenes.batch_problems(14, seed=23, min_side=40, max_side=300, cap_range=(4, 50))
+    k = 0
+    for q in probs:
+        if q["term"] == "edge" or q["image"].shape[0] == 1:
+            q["storage"] = ("bf16", "f16")[k % 2]
+            k += 1
+    items = device_items(torch, ctx, probs)
+    sv = lse.Server(ctx, 512 << 20)
+    ids, results = [], {}
+    for it in items[:7]:
+        ids.append(sv.submit(it))
+    sv.advance(5)
+    for it in items[7:]:
+        ids.append(sv.submit(it))
+    drain(sv, ids, results)
+    sv.destroy()
+    for rid, it in zip(ids, items):
+        v, m, st = results[rid]
+        v1, m1, st1 = alone(torch, ctx, it)
+        assert np.array_equal(v.cpu().numpy().view(np.uint32), v1.view(np.uint32)), it["storage"]
+        assert np.array_equal(m.cpu().numpy(), m1)
+        for key in ("iterations_run", "last_flips", "area_plus", "status"):
+            assert st[key] == st1[key], key
+
+
+def test_16bit_requests_take_half_the_plane_memory(torch, lse, ctx):
+    # a 256 x 256 single-band request holds 3 planes: 768 KiB in FP32,
+    # 384 KiB in BF16, plus the same partial sums; a 3 MiB budget admits at
+    # most three FP32 requests, and more BF16 ones
+    probs = scenes.batch_problems(8, seed=4, min_side=256, max_side=256, cap_range=(6, 12))
+    counts = {}
+    for storage in ("f32", "bf16"):
+        for q in probs:
+            q["image"] = q["image"][:1]
+            q["term"] = "region"
+            q["early_stop_frac"] = 0.0
+            q["storage"] = storage
+        items = device_items(torch, ctx, probs)
+        sv = lse.Server(ctx, 3 << 20)
+        ids = [sv.submit(it) for it in items]
+        counts[storage] = sv.advance(1)
+        results = {}
+        drain(sv, ids, results, ticks=4)
+        sv.destroy()
+        for rid, it in zip(ids, items):
+            v, m, st = results[rid]
+            v1, m1, _ = alone(torch, ctx, it)
+            assert np.array_equal(v.cpu().numpy().view(np.uint32), v1.view(np.uint32))
+    assert 1 <= counts["f32"] <= 3 and counts["bf16"] > counts["f32"], counts
 
 
 def test_budget_queues_and_reuses_memory(torch, lse, ctx):
