@@ -19,10 +19,13 @@ Reported (one JSON line on rank 0):
                term and the LSF (FP32 arithmetic, 6 B/px per region step);
   batch        256 uneven images (sides 128-1024, caps 100-600, early stop)
                through lse_evolve_batch with and without a CUDA graph, and
-               one lse_evolve call per image in sequence;
-  serve        Poisson-arriving requests through lse_server (continuous
-               batching in a 40 GiB budget) against one lse_evolve call per
-               request: p50 / p99 latency and requests/s.
+               one lse_evolve call per image in sequence, on a context whose
+               tile heights lse_autotune chose on a separate sample;
+  serve        Poisson-arriving requests (sides 256-4096, BF16 storage where
+               it applies) through lse_server (continuous batching in a
+               40 GiB budget) against one lse_evolve call per request, at
+               50 and 2000 requests/s offered: p50 / p99 latency and
+               requests/s.
 `--impl reference` times the FP64 oracle alone (the reference arm).
 Under torchrun each rank runs its own replica (no collective on the data
 path): weak scaling.
@@ -72,7 +75,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the continuous-batching serving measurement")
     ap.add_argument("--serve-requests", type=int, default=96)
-    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-rates", default="50,2000",
+                    help="offered request rates (per second), comma-separated")
     return ap.parse_args()
 
 
@@ -230,25 +234,35 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
-def serve_measurement(torch, lse, dev, n_req: int, rate: float, seed: int = 9,
+def serve_measurement(torch, lse, dev, n_req: int, rates, seed: int = 9,
                       ticks: int = 16, budget: int = 40 << 30):
-    """Requests arriving as a Poisson process (rate per second) of uneven
-    images (sides 256-2048, 1 or 4 bands, region or edge term, caps
-    100-600, early stop at 1e-4 of the pixels), replayed in real time:
-    through lse_server (continuous batching, `ticks` iterations per advance,
-    a `budget`-byte memory budget), and one lse_evolve call per request in
-    arrival order.  Latency = completion - arrival; throughput = requests
-    over the makespan."""
+    """Requests arriving as a Poisson process of uneven images (sides
+    log-uniform 256-4096, 1 or 4 bands, region or edge term, caps 100-600,
+    early stop at 1e-4 of the pixels; BF16 storage for the single-band and
+    edge requests, FP32 for the 4-band region ones, which 16-bit storage does
+    not serve), replayed in real time at each offered rate (requests per
+    second): through lse_server (continuous batching, `ticks` iterations per
+    advance, a `budget`-byte memory budget), and one lse_evolve call per
+    request in arrival order with the same storage.  Latency = completion -
+    arrival; throughput = requests over the makespan."""
     import time
     from paper_1409_7474_gb300 import scenes
     distinct = max(n_req // 2, 1)
-    probs = scenes.batch_problems(distinct, seed=seed, min_side=256, max_side=2048)
-    ctx = lse.Context(dev.index, max_pixels=2048 * 2048, max_bands=4)
+    probs = scenes.batch_problems(distinct, seed=seed, min_side=256, max_side=4096)
+    ctx = lse.Context(dev.index, max_pixels=4096 * 4096, max_bands=4)
+    sample = scenes.batch_problems(max(distinct // 2, 1), seed=seed + 1000, min_side=256,
+                                   max_side=4096)
+    for q in sample:
+        if q["term"] == "edge" or q["image"].shape[0] == 1:
+            q["storage"] = "bf16"
+    tune = tune_context(torch, lse, ctx, dev, sample)
     base = []
     for q in probs:
         img = torch.from_numpy(q["image"]).to(dev)
+        half = q["term"] == "edge" or q["image"].shape[0] == 1
         it = {"phi0": torch.from_numpy(q["phi0"]).to(dev), "term": q["term"],
-              "iterations": q["iterations"], "early_stop_frac": q["early_stop_frac"]}
+              "iterations": q["iterations"], "early_stop_frac": q["early_stop_frac"],
+              "storage": "bf16" if half else "f32"}
         if q["term"] == "region":
             it["image"] = img
         else:
@@ -261,8 +275,6 @@ def serve_measurement(torch, lse, dev, n_req: int, rate: float, seed: int = 9,
         it["phi_out"] = torch.empty((H, W), dtype=torch.float32, device=dev)
         it["mask_out"] = torch.empty((H, W), dtype=torch.uint8, device=dev)
         items.append(it)
-    rng = np.random.default_rng(seed)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
     px_it_cap = sum(int(it["phi0"].numel()) * it["iterations"] for it in items)
     torch.cuda.synchronize()
 
@@ -270,59 +282,90 @@ def serve_measurement(torch, lse, dev, n_req: int, rate: float, seed: int = 9,
         while time.perf_counter() - t0 < t:
             pass
 
+    def alone(it, **kw):
+        ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
+                   storage=it["storage"], **kw)
+
     # warm-up of both paths (modules, scratch)
     sv = lse.Server(ctx, budget)
-    sv.submit(dict(items[0], iterations=2))
+    for it in base[:4]:
+        sv.submit(dict(it, iterations=2))
     while sv.advance(2):
         pass
-    ctx.evolve(items[0].get("image"), items[0]["phi0"], items[0]["term"], g=items[0].get("g"),
-               iterations=2)
+    for it in base[:4]:
+        alone(it, iterations=2)
     torch.cuda.synchronize()
-
-    # continuous batching
-    done = np.zeros(n_req)
-    t0 = time.perf_counter()
-    k, live = 0, {}
-    while len(live) or k < n_req:
-        now = time.perf_counter() - t0
-        while k < n_req and arrivals[k] <= now:
-            live[sv.submit(items[k])] = k
-            k += 1
-        if not live:
-            wait_until(t0, arrivals[k])
-            continue
-        sv.advance(ticks)
-        for rid in list(live):
-            if sv.poll(rid) is not None:
-                done[live.pop(rid)] = time.perf_counter() - t0
-    lat_s = done - arrivals
-    span_s = done.max() - arrivals[0]
     sv.destroy()
-
-    # one request at a time
-    done_q = np.zeros(n_req)
-    t0 = time.perf_counter()
-    for k, it in enumerate(items):
-        wait_until(t0, arrivals[k])
-        ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
-                   iterations=it["iterations"], early_stop_frac=it["early_stop_frac"],
-                   phi_out=it["phi_out"], mask_out=it["mask_out"])
-        done_q[k] = time.perf_counter() - t0
-    lat_q = done_q - arrivals
-    span_q = done_q.max() - arrivals[0]
-    ctx.destroy()
 
     def summary(lat, span):
         return {"p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "requests_per_s": n_req / span, "makespan_s": float(span)}
 
-    return {"workload": f"{n_req} requests, Poisson arrivals at {rate:g}/s; sides "
-                        "log-uniform 256-2048, 1 or 4 bands, region or edge term, caps "
-                        "U{100..600}, early stop 1e-4; FP32 storage; "
-                        f"budget {budget >> 30} GiB; {ticks} iterations per advance",
-            "pixel_iterations_at_caps": px_it_cap,
-            "server": summary(lat_s, span_s), "sequential": summary(lat_q, span_q)}
+    out = {"workload": f"{n_req} requests, Poisson arrivals; sides log-uniform 256-4096, "
+                       "1 or 4 bands, region or edge term, caps U{100..600}, early stop "
+                       "1e-4; BF16 storage (1 band or edge), FP32 (4-band region); "
+                       f"budget {budget >> 30} GiB; {ticks} iterations per advance",
+           "pixel_iterations_at_caps": px_it_cap, "autotune": tune, "rates": {}}
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0, size=n_req)
+    for rate in rates:
+        arrivals = np.cumsum(gaps / rate)
+        # continuous batching
+        sv = lse.Server(ctx, budget)
+        done = np.zeros(n_req)
+        t0 = time.perf_counter()
+        k, live = 0, {}
+        while len(live) or k < n_req:
+            now = time.perf_counter() - t0
+            while k < n_req and arrivals[k] <= now:
+                live[sv.submit(items[k])] = k
+                k += 1
+            if not live:
+                wait_until(t0, arrivals[k])
+                continue
+            sv.advance(ticks)
+            for rid in list(live):
+                if sv.poll(rid) is not None:
+                    done[live.pop(rid)] = time.perf_counter() - t0
+        lat_s = done - arrivals
+        span_s = done.max() - arrivals[0]
+        sv.destroy()
+        # one request at a time
+        done_q = np.zeros(n_req)
+        t0 = time.perf_counter()
+        for k, it in enumerate(items):
+            wait_until(t0, arrivals[k])
+            alone(it, iterations=it["iterations"], early_stop_frac=it["early_stop_frac"],
+                  phi_out=it["phi_out"], mask_out=it["mask_out"])
+            done_q[k] = time.perf_counter() - t0
+        lat_q = done_q - arrivals
+        span_q = done_q.max() - arrivals[0]
+        out["rates"][f"{rate:g}/s"] = {"server": summary(lat_s, span_s),
+                                       "sequential": summary(lat_q, span_q)}
+    ctx.destroy()
+    return out
+
+
+def tune_context(torch, lse, ctx, dev, probs, iterations: int = 16):
+    """lse_autotune on a separate sample of the workload's generator: the
+    tile height per shape class that the timed runs then use."""
+    import time
+    items = []
+    for q in probs:
+        img = torch.from_numpy(q["image"]).to(dev)
+        it = {"phi0": torch.from_numpy(q["phi0"]).to(dev), "term": q["term"],
+              "iterations": q["iterations"], "storage": q.get("storage", "f32")}
+        if q["term"] == "region":
+            it["image"] = img
+        else:
+            it["g"] = ctx.precompute_edge(img, 1.0, 9, 255.0)
+        items.append(it)
+    t0 = time.perf_counter()
+    rows = ctx.autotune(items, iterations=iterations)
+    return {"sample_images": len(items), "iterations": iterations,
+            "seconds": round(time.perf_counter() - t0, 3),
+            "rows_32": rows.count(32), "rows_64": rows.count(64)}
 
 
 def batch_measurement(torch, lse, dev, n_images: int, seed: int = 3):
@@ -335,6 +378,9 @@ def batch_measurement(torch, lse, dev, n_images: int, seed: int = 3):
     from paper_1409_7474_gb300 import scenes
     probs = scenes.batch_problems(n_images, seed=seed)
     ctx = lse.Context(dev.index, max_pixels=1024 * 1024, max_bands=4)
+    # tuned on an equally large sample of the generator (another seed): the
+    # tuner judges each class in a mix as full as the timed one
+    tune = tune_context(torch, lse, ctx, dev, scenes.batch_problems(n_images, seed=seed + 1000))
     items = []
     for q in probs:
         img = torch.from_numpy(q["image"]).to(dev)
@@ -379,7 +425,7 @@ def batch_measurement(torch, lse, dev, n_images: int, seed: int = 3):
     ctx.destroy()
     out = {"workload": f"{n_images} uneven images: sides log-uniform 128-1024, 1 or 4 bands, "
                        "region or edge term, caps U{100..600}, early stop 1e-4",
-           "pixel_iterations": px_it, "unit": "Mpixel-iters/s"}
+           "pixel_iterations": px_it, "unit": "Mpixel-iters/s", "autotune": tune}
     for name, ms in (("batch_graph", ms_graph), ("batch_direct", ms_direct),
                      ("sequential", ms_seq)):
         out[name] = {"ms": ms, "value": px_it / (ms / 1e3) / 1e6,
@@ -576,7 +622,8 @@ def main():
         batch = batch_measurement(torch, lse, dev, args.batch_images)
     serve = None
     if not args.no_serve and world == 1:
-        serve = serve_measurement(torch, lse, dev, args.serve_requests, args.serve_rate)
+        serve = serve_measurement(torch, lse, dev, args.serve_requests,
+                                  [float(r) for r in args.serve_rates.split(",") if r])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -314,12 +314,14 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems,
  * works on tiles of 64 rows (8 warps per CTA, 3 CTAs per SM) or 32 rows
  * (4 warps, 6 CTAs per SM): tall tiles recompute fewer halo rows, short
  * tiles give small images enough CTAs to fill the GPU.  lse_autotune runs
- * `iterations` iterations (1..1000, no early stop) of the given problems
- * with each tile height, through lse_evolve_batch on scratch outputs (the
- * problems' phi_out and mask_out are not written), and keeps the faster
- * height per shape class in the context: term, storage type, template size
- * and the power of two of the image's tile count.  Problems in one class are
- * timed together, as a batch.  Later lse_evolve, lse_evolve_batch and
+ * the given problems together, `iterations` iterations each (1..1000, no
+ * early stop), through lse_evolve_batch on scratch outputs (the problems'
+ * phi_out and mask_out are not written), and for one shape class at a time
+ * (term, storage type, template size and the power of two of the image's
+ * tile count; the largest classes first) flips the tile height, keeping the
+ * flip if the whole set runs at least 0.5 % faster.  So the choice fits the
+ * mix it was tuned on: tune on work like what will run.  Later lse_evolve,
+ * lse_evolve_batch and
  * lse_server_* calls on ctx use the table, so an image still gets the same
  * bits from each of them; untuned classes use 64-row tiles (32 when the
  * environment variable LSE_TILE_ROWS=32 was set at lse_create).  Changing an

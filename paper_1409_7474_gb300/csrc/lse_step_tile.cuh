@@ -217,6 +217,53 @@ __device__ __forceinline__ float4 lds4(const float *p)
     return *reinterpret_cast<const float4 *>(p);
 }
 
+// Two FP32 values in one 64-bit register pair.  Blackwell's packed FP32
+// instructions (add / mul / fma .rn.f32x2) round each element exactly as the
+// scalar instruction does, in one instruction for the pair.
+struct f2 {
+    unsigned long long r;
+};
+
+__device__ __forceinline__ f2 f2_pack(float a, float b)
+{
+    f2 o;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(o.r) : "f"(a), "f"(b));
+    return o;
+}
+
+__device__ __forceinline__ void f2_unpack(f2 v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v.r));
+}
+
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    f2 o;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(o.r) : "l"(a.r), "l"(b.r));
+    return o;
+}
+
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b)
+{
+    f2 o;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(o.r) : "l"(a.r), "l"(b.r));
+    return o;
+}
+
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    f2 o;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(o.r) : "l"(a.r), "l"(b.r));
+    return o;
+}
+
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
+{
+    f2 o;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(o.r) : "l"(a.r), "l"(b.r), "l"(c.r));
+    return o;
+}
+
 // One step over the tiles of one image, run by CTA `cta` of the `ncta` CTAs
 // given to it.
 template <int KIND_EDGE, int RAD, bool FAST, class T, int NW>
@@ -271,6 +318,7 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
     for (int k = 0; k <= RAD; ++k) tp[k] = a.taps[k];
     const float coef = EDGE ? a.half_dt : st->a[0];
     const float mid = EDGE ? 0.0f : st->m[0];
+    const f2 coef2 = f2_pack(coef, coef), mid2 = f2_pack(mid, mid);
     const float sqrt8 = sqrtf(8.0f);
     const bool binarise_in = !FAST && a.binarise_in != 0;
     const bool count_flips = !FAST && a.count_flips != 0;
@@ -401,7 +449,7 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
                     }
                 }
             }
-            float u[4];
+            float dxs[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float dx = c[j + 2] - c[j];
@@ -410,15 +458,30 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
                     else if (oneL[j]) dx = 2.0f * (c[j + 2] - c[j + 1]);
                     else if (oneR[j]) dx = 2.0f * (c[j + 1] - c[j]);
                 }
-                const float dy = dn[j] - up[j];
-                const float q = fmaf(dx, dx, dy * dy);
-                // +-1 phi off the image border: q is 0, 4 or 8, and sqrt(q) is
-                // q / 2 (exact) or sqrt(8)
-                const float s2 = !FAST ? sqrtf(q)
-                               : IN ? (q == 8.0f ? sqrt8 : 0.5f * q)
-                                    : lut[(__float_as_uint(q) >> 21) & 31u];
-                const float tj = EDGE ? coef * comp(d4, j) : coef * (comp(d4, j) - mid);
-                u[j] = fmaf(tj, s2, c[j + 1]);
+                dxs[j] = dx;
+            }
+            // the update on column pairs: each packed operation rounds as
+            // its scalar form, so u is bitwise the scalar u
+            float u[4];
+#pragma unroll
+            for (int jp = 0; jp < 2; ++jp) {
+                const int j0 = 2 * jp, j1 = 2 * jp + 1;
+                const f2 dx = f2_pack(dxs[j0], dxs[j1]);
+                const f2 dy = f2_sub(f2_pack(dn[j0], dn[j1]), f2_pack(up[j0], up[j1]));
+                float q[2];
+                f2_unpack(f2_fma(dx, dx, f2_mul(dy, dy)), q[0], q[1]);
+                float s2[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e)
+                    // +-1 phi off the image border: q is 0, 4 or 8, and
+                    // sqrt(q) is q / 2 (exact) or sqrt(8)
+                    s2[e] = !FAST ? sqrtf(q[e])
+                          : IN ? (q[e] == 8.0f ? sqrt8 : 0.5f * q[e])
+                               : lut[(__float_as_uint(q[e]) >> 21) & 31u];
+                const f2 d = f2_pack(comp(d4, j0), comp(d4, j1));
+                const f2 t = EDGE ? f2_mul(coef2, d) : f2_mul(coef2, f2_sub(d, mid2));
+                f2_unpack(f2_fma(t, f2_pack(s2[0], s2[1]), f2_pack(c[j0 + 1], c[j1 + 1])),
+                          u[j0], u[j1]);
             }
             if (!IN) {
                 if (xborder) {
@@ -483,16 +546,20 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
             const bool st_ok = lane_out && x0 < W;
             T *dst = reinterpret_cast<T *>(a.phi_out) + (size_t)(ys + RAD + 1 + r_first) * a.pitch + x0;
             const size_t pitch = (size_t)a.pitch;
-            float rg[P][4];
+            // the ring holds the lane's 4 columns of 2 RAD + 1 h rows as
+            // column pairs, so each tap of the pass is one packed
+            // instruction for two columns
+            f2 rg[P][2];
+            f2 tp2[RAD + 1];
+#pragma unroll
+            for (int q = 0; q <= RAD; ++q) tp2[q] = f2_pack(tp[q], tp[q]);
             // h rows past the tile read other shared memory (finite values);
             // their outputs are never used
-            auto ldh = [&](int hr, float *d) {
+            auto ldh = [&](int hr, f2 *d) {
                 if (G::CLAMP_H) hr = hr < kURows - 1 ? hr : kURows - 1;
                 const float4 h4 = lds4(hl + (hr + G::H_ROW0) * G::H_STRIDE);
-                d[0] = h4.x;
-                d[1] = h4.y;
-                d[2] = h4.z;
-                d[3] = h4.w;
+                d[0] = f2_pack(h4.x, h4.y);
+                d[1] = f2_pack(h4.z, h4.w);
             };
             float fsw = 0.0f, fsa = 0.0f, fcnt = 0.0f;
             auto vrows = [&](auto full_tag) {
@@ -506,16 +573,18 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
                     if (FULL || k < rv) {
                         float v[4], w[4];
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            float acc = tp[0] * rg[(k + RAD) % P][j];
+                        for (int jp = 0; jp < 2; ++jp) {
+                            f2 acc = f2_mul(tp2[0], rg[(k + RAD) % P][jp]);
 #pragma unroll
                             for (int q = 1; q <= RAD; ++q)
-                                acc = fmaf(tp[q],
-                                           rg[(k + RAD - q) % P][j] + rg[(k + RAD + q) % P][j],
-                                           acc);
-                            v[j] = acc;
-                            w[j] = acc >= 0.0f ? 1.0f : -1.0f;
+                                acc = f2_fma(tp2[q],
+                                             f2_add(rg[(k + RAD - q) % P][jp],
+                                                    rg[(k + RAD + q) % P][jp]),
+                                             acc);
+                            f2_unpack(acc, v[2 * jp], v[2 * jp + 1]);
                         }
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) w[j] = v[j] >= 0.0f ? 1.0f : -1.0f;
                         if (st_ok) {
                             if (store_bin)
                                 S::st4(dst + k * pitch, w[0], w[1], w[2], w[3]);

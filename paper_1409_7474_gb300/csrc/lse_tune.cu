@@ -7,9 +7,10 @@
 // tiles give twice the CTAs, which an image of few tiles needs to fill the
 // GPU, and more CTAs per SM to cover each other's TMA waits.  Which wins
 // depends on the image size, the radius and what else runs beside it, so
-// lse_autotune times both on the caller's own work and keeps the faster per
-// shape class (term, storage type, radius, and the power of two of the tile
-// count).  lse_evolve, lse_evolve_batch and lse_server_* all read the same
+// lse_autotune times the caller's own work, run together as one batch, and
+// flips one shape class (term, storage type, radius, and the power of two of
+// the tile count) at a time, keeping a flip that makes the whole set
+// faster.  lse_evolve, lse_evolve_batch and lse_server_* all read the same
 // table, so an image gets the same tiles, the same partial sums and the
 // same bits whichever of them runs it.
 #include <math.h>
@@ -105,32 +106,47 @@ extern "C" lse_status lse_autotune(lse_ctx *ctx, int n, const lse_problem *probl
         trial[i].params.early_stop_frac = 0.0f;
     }
 
-    const int candidates[2] = {8, 4};
-    for (auto &g : groups) {
-        std::vector<lse_problem> set;
-        for (int i : g.second) set.push_back(trial[i]);
-        std::vector<lse_stats> st(set.size());
-        float best_ms = INFINITY;
-        int best = ctx->tile_nw_default;
-        for (int nw : candidates) {
-            ctx->tile_tune[g.first] = nw;
-            float ms = INFINITY;
-            // the first run warms up (modules, scratch growth); the best of
-            // the next two counts
-            for (int rep = 0; rep < 3; ++rep) {
-                r = lse_evolve_batch(ctx, (int)set.size(), set.data(), 0, st.data(), stream);
-                if (r != LSE_OK) {
-                    ctx->tile_tune.erase(g.first);
-                    return r;
-                }
-                if (rep > 0) ms = std::min(ms, st[0].elapsed_ms);
-            }
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = nw;
-            }
+    // coordinate descent over the shape classes, on the whole problem set
+    // run together: a class's height is flipped only if the time of the
+    // whole batch drops, so each class is judged in the company it runs in
+    // (a class alone on an idle GPU favours short tiles; the same class in a
+    // full batch may not)
+    std::vector<lse_stats> st(n);
+    auto time_all = [&](float *ms) -> lse_status {
+        *ms = INFINITY;
+        for (int rep = 0; rep < 3; ++rep) {
+            lse_status rr = lse_evolve_batch(ctx, n, trial.data(), 0, st.data(), stream);
+            if (rr != LSE_OK) return rr;
+            *ms = std::min(*ms, st[0].elapsed_ms);
         }
-        ctx->tile_tune[g.first] = best;
+        return LSE_OK;
+    };
+    std::map<TuneKey, int> saved = ctx->tile_tune;
+    for (auto &g : groups)
+        if (!ctx->tile_tune.count(g.first)) ctx->tile_tune[g.first] = ctx->tile_nw_default;
+    // larger classes first: they move the total the most
+    std::vector<std::pair<double, TuneKey>> order;
+    for (auto &g : groups) {
+        double px = 0.0;
+        for (int i : g.second) px += (double)problems[i].H * problems[i].W;
+        order.push_back({-px, g.first});
+    }
+    std::sort(order.begin(), order.end());
+    float best = 0.0f;
+    lse_status r2 = time_all(&best);          // warms up, then the baseline
+    if (r2 == LSE_OK) r2 = time_all(&best);
+    for (size_t k = 0; k < order.size() && r2 == LSE_OK; ++k) {
+        const TuneKey &key = order[k].second;
+        const int was = ctx->tile_tune[key];
+        ctx->tile_tune[key] = was == 8 ? 4 : 8;
+        float ms = 0.0f;
+        r2 = time_all(&ms);
+        if (r2 == LSE_OK && ms < best * 0.995f) best = ms;
+        else ctx->tile_tune[key] = was;
+    }
+    if (r2 != LSE_OK) {
+        ctx->tile_tune = saved;
+        return r2;
     }
     if (tile_rows)
         for (int i = 0; i < n; ++i) {
