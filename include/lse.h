@@ -181,7 +181,15 @@ typedef struct lse_ctx lse_ctx;
  * edge term, the TMA streaming form for 2-4 bands, the plain shared-memory
  * kernel for what neither covers.  The environment variable LSE_STEP_KERNEL
  * at creation narrows the choice, for cross-checks: "stream" skips the tile
- * form, "generic" runs every iteration on the plain kernel. */
+ * form, "generic" runs every iteration on the plain kernel.
+ * Two more variables at creation are failure-injection hooks for tests:
+ * LSE_TEST_FAIL_ALLOC=N makes the context's next N scratch growths fail as
+ * a failed cudaMalloc would (the call returns LSE_ERR_OOM, nothing is
+ * enqueued past that point, and later calls work); LSE_TEST_STALL_NS=T makes
+ * the first tile-form step of the next lse_evolve wait T nanoseconds on an
+ * mbarrier that nothing completes, so that its bounded wait runs out: the
+ * call ends with status LSE_ERR_TIMEOUT and the context stays usable.  Every
+ * device-side wait of the library gives up after 2^24 polls or 2 s. */
 lse_status lse_create(lse_ctx **ctx, int device, size_t max_pixels,
                       int max_bands);
 

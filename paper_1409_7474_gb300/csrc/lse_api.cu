@@ -83,7 +83,10 @@ lse_status ensure(lse_ctx *ctx, void **p, size_t *cap, size_t bytes,
         *p = nullptr;
         *cap = 0;
     }
-    cudaError_t e = cudaMalloc(p, bytes);
+    // test hook: the next growth fails as a failed cudaMalloc would
+    cudaError_t e = cudaErrorMemoryAllocation;
+    if (ctx->test_fail_alloc > 0) --ctx->test_fail_alloc;
+    else e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -295,6 +298,8 @@ lse_status lse_create(lse_ctx **out, int device, size_t max_pixels, int max_band
     ctx->n_partials = partials_needed(ctx->sm_count);
     ctx->step_form = step_form_from_env();
     ctx->tile_nw_default = tile_nw_from_env();
+    if (const char *v = getenv("LSE_TEST_STALL_NS")) ctx->test_stall_ns = strtoull(v, nullptr, 10);
+    if (const char *v = getenv("LSE_TEST_FAIL_ALLOC")) ctx->test_fail_alloc = atoi(v);
     cudaError_t e = cudaMalloc(&ctx->partials, sizeof(LsePartial) * ctx->n_partials);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->st, sizeof(LseDevState));
     if (e == cudaSuccess) e = cudaMemset(ctx->st, 0, sizeof(LseDevState));
@@ -512,6 +517,12 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
         return LSE_ERR_INVALID_ARG;
     }
 
+    // test hook: the first step of this call waits on a barrier that
+    // nothing completes, so its bounded wait must run out (tile form only)
+    if (ctx->test_stall_ns && plan.form == LSE_FORM_TILE) {
+        plan.args.stall_ns = ctx->test_stall_ns;
+        ctx->test_stall_ns = 0;
+    }
     e = cudaEventRecord(ctx->ev0, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
     for (int n = 0; n < p.iterations; ++n) {
@@ -521,6 +532,7 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
             if (e != cudaSuccess) return cuda_fail(ctx, e, "normaliser");
         }
         e = launch_step(plan, n, s);
+        plan.args.stall_ns = 0;
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step");
     }
     e = cudaEventRecord(ctx->ev1, s);

@@ -180,12 +180,11 @@ cudaError_t launch_class(const ClassKey &k, const Class &c, const BatchItem *ite
     return launch_step_tma_batch_multiband(k.rad, items, blk, n, nb, k.wpc, s);
 }
 
-int normaliser_blocks(long long npix, int sm_count)
+int normaliser_blocks(int H, int sm_count)
 {
-    long long blocks = (npix + 255) / 256;
-    if (blocks < 1) blocks = 1;
+    // one CTA per row at most (the pass walks rows), as lse_evolve launches it
     const int cap = sm_count * 4;
-    return (int)(blocks < cap ? blocks : cap);
+    return H < cap ? (H < 1 ? 1 : H) : cap;
 }
 
 }  // namespace lse_detail
@@ -299,7 +298,7 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
         it.reinit_period = p.reinit_period;
         it.early_stop = p.early_stop_frac > 0.0f;
         it.iter0 = 0;
-        if (region && q.B > 1) it.nnblocks = normaliser_blocks((long long)q.H * q.W, ctx->sm_count);
+        if (region && q.B > 1) it.nnblocks = normaliser_blocks(q.H, ctx->sm_count);
         classes[class_of(plan, p.term, region ? q.B : 1)].items.push_back(i);
     }
 

@@ -75,7 +75,7 @@ void fill_tables(const ClassMap &classes, const BatchItem *items, unsigned char 
 cudaError_t launch_class(const ClassKey &k, const Class &c, const BatchItem *d_items,
                          const unsigned char *d_tables, long long t, cudaStream_t s,
                          int k_act = -1);
-// CTAs the normaliser of an image of `npix` pixels runs with (as lse_evolve).
-int normaliser_blocks(long long npix, int sm_count);
+// CTAs the normaliser of an image of H rows runs with (as lse_evolve).
+int normaliser_blocks(int H, int sm_count);
 
 }  // namespace lse_detail

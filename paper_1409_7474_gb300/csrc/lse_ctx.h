@@ -50,6 +50,11 @@ struct lse_ctx {
     int tile_nw_default = 8;
     float *tune_out = nullptr;       // lse_autotune: outputs of its trial runs
     size_t tune_out_cap = 0;         // bytes
+    // test hooks, from the environment at creation (see lse_create):
+    // the next lse_evolve's first tile-form step waits this long (ns) on a
+    // barrier nothing completes; the next N scratch growths fail
+    unsigned long long test_stall_ns = 0;
+    int test_fail_alloc = 0;
     // lse_evolve_batch: per-image planes, states and partials; the work list
     // and CTA tables; a pinned mirror for uploads and the states
     void *arena = nullptr;

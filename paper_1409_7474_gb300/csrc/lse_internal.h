@@ -22,8 +22,10 @@
 #define LSE_SBIT_DEGENERATE 4u
 #define LSE_SBIT_ABORT (LSE_SBIT_NONFINITE | LSE_SBIT_TIMEOUT)
 
-// Bounded spin: try_wait polls on an mbarrier before a wait is declared lost.
+// Bounded spin: try_wait polls on an mbarrier before a wait is declared
+// lost, and the wall-clock limit (ns, %globaltimer) that ends it sooner.
 #define LSE_WAIT_LIMIT (1u << 24)
+#define LSE_WAIT_NS 2000000000ull
 
 struct alignas(16) LseDevState {
     // constants of the call (prologue)
@@ -93,6 +95,9 @@ struct StepArgs {
     int th;                     // output rows per item
     int n_items;
     int nw;                     // tile form: warps per CTA (8: 64-row tiles, 4: 32-row)
+    // test hook (0 = off): the tile form's CTAs first wait this long (ns) on
+    // an mbarrier that nothing arrives at, so the bounded wait runs out
+    unsigned long long stall_ns;
 };
 
 // One image of a batched evolution (lse_evolve_batch, lse_server), in device

@@ -31,28 +31,26 @@ __device__ __forceinline__ void store_as(void *p, size_t i, float v, int storage
     else static_cast<float *>(p)[i] = v;
 }
 
+// The kernels below walk the image by rows: rows stride over the CTAs and
+// each row's columns over the threads, so no pixel index is divided.
+
 __global__ void __launch_bounds__(kThreads)
 quantise_kernel(const float *__restrict__ src, int src_pitch, int H, int W,
                 void *__restrict__ dst, int pitch, int storage)
 {
-    const long long n = (long long)H * W;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(p / W);
-        const int x = (int)(p - (long long)y * W);
-        store_as(dst, (size_t)y * pitch + x, src[(size_t)y * src_pitch + x], storage);
-    }
+    for (int y = blockIdx.x; y < H; y += gridDim.x)
+        for (int x = threadIdx.x; x < W; x += blockDim.x)
+            store_as(dst, (size_t)y * pitch + x, src[(size_t)y * src_pitch + x], storage);
 }
 
 __global__ void __launch_bounds__(kThreads)
 convert_kernel(const void *__restrict__ src, int dtype, int H, int W, int B,
                float *__restrict__ dst, int pitch)
 {
-    const long long n = (long long)B * H * W;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        long long row = i / W;          // b * H + y
-        int x = (int)(i - row * W);
+    const int rows = B * H;             // row b * H + y
+    for (int row = blockIdx.x; row < rows; row += gridDim.x)
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        const size_t i = (size_t)row * W + x;
         float v;
         switch (dtype) {
         case LSE_F16:
@@ -67,7 +65,7 @@ convert_kernel(const void *__restrict__ src, int dtype, int H, int W, int B,
         default:
             v = static_cast<const float *>(src)[i];
         }
-        dst[row * pitch + x] = v;
+        dst[(size_t)row * pitch + x] = v;
     }
 }
 
@@ -81,15 +79,27 @@ prologue_kernel(const void *__restrict__ img, int img_pitch, size_t band_stride,
     LseAcc acc;
     acc.clear();
     const long long n = (long long)H * W;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-         p += (long long)gridDim.x * blockDim.x) {
-        int y = (int)(p / W);
-        int x = (int)(p - (long long)y * W);
-        float v = phi0[p];
+    // band sums: up to 8 pixels in FP32, then into the FP64 accumulators
+    // (relative error of a partial at most 7 * 2^-24)
+    float sp[LSE_MAXB], sm[LSE_MAXB];
+    int pending = 0, npos = 0;
+    auto fold = [&]() {
+        for (int b = 0; b < B; ++b) {
+            acc.sp[b] += (double)sp[b];
+            acc.sm[b] += (double)sm[b];
+            sp[b] = 0.0f;
+            sm[b] = 0.0f;
+        }
+        pending = 0;
+    };
+    for (int b = 0; b < LSE_MAXB; ++b) sp[b] = sm[b] = 0.0f;
+    for (int y = blockIdx.x; y < H; y += gridDim.x)
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        float v = phi0[(size_t)y * W + x];
         if (!isfinite(v)) acc.bits |= LSE_SBIT_NONFINITE;
         store_as(phi_dst, (size_t)y * pitch + x, v, storage);
         const bool pos = v >= 0.0f;
-        acc.n_plus += pos;
+        npos += pos;
         if (term == LSE_TERM_EDGE) {
             float gv = load_as(g, (size_t)y * g_pitch + x, storage);
             if (!isfinite(gv)) acc.bits |= LSE_SBIT_NONFINITE;
@@ -98,15 +108,18 @@ prologue_kernel(const void *__restrict__ img, int img_pitch, size_t band_stride,
             for (int b = 0; b < B; ++b) {
                 float iv = load_as(img, b * band_stride + (size_t)y * img_pitch + x, storage);
                 if (!isfinite(iv)) acc.bits |= LSE_SBIT_NONFINITE;
-                if (pos) acc.sp[b] += iv;
-                else acc.sm[b] += iv;
+                if (pos) sp[b] += iv;
+                else sm[b] += iv;
                 if (b == 0) {
                     acc.fmax = fmaxf(acc.fmax, iv);
                     acc.fmin = fminf(acc.fmin, iv);
                 }
             }
+            if (++pending == 8) fold();
         }
     }
+    if (term != LSE_TERM_EDGE) fold();
+    acc.n_plus = npos;
     const int nb = term == LSE_TERM_EDGE ? 0 : B;
     LseAcc r;
     lse_cta_reduce(acc, nb, &r);
@@ -156,11 +169,8 @@ __device__ __forceinline__ void normaliser(const float *__restrict__ img, int pi
     }
     LseAcc acc;
     acc.clear();
-    const long long n = (long long)H * W;
-    for (long long p = cta * (long long)blockDim.x + threadIdx.x; p < n;
-         p += (long long)ncta * blockDim.x) {
-        int y = (int)(p / W);
-        int x = (int)(p - (long long)y * W);
+    for (int y = cta; y < H; y += ncta)
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const float *src = img + (size_t)y * pitch + x;
         float d = 0.0f;
 #pragma unroll
@@ -220,22 +230,20 @@ output_kernel(BufPair bufs, int pitch, int H, int W, int storage, const LseDevSt
 {
     if (st->status_bits & LSE_SBIT_ABORT) return;
     const void *src = bufs.b[st->last_buf];
-    const long long n = (long long)H * W;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-         p += (long long)gridDim.x * blockDim.x) {
-        int y = (int)(p / W);
-        int x = (int)(p - (long long)y * W);
+    for (int y = blockIdx.x; y < H; y += gridDim.x)
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        const size_t p = (size_t)y * W + x;
         float v = load_as(src, (size_t)y * pitch + x, storage);
         phi_out[p] = v;
         if (mask_out) mask_out[p] = v >= 0.0f ? 1 : 0;
     }
 }
 
-int grid_for(long long n, int cap)
+// CTAs for a row-wise walk over `rows` rows, at most `cap`.
+int grid_rows(long long rows, int cap)
 {
-    long long blocks = (n + kThreads - 1) / kThreads;
-    if (blocks < 1) blocks = 1;
-    return (int)(blocks < cap ? blocks : cap);
+    if (rows < 1) rows = 1;
+    return (int)(rows < cap ? rows : cap);
 }
 
 }  // namespace
@@ -245,7 +253,7 @@ namespace lse_detail {
 cudaError_t launch_convert(const void *src, int dtype, int H, int W, int B,
                            float *dst, int pitch, cudaStream_t s)
 {
-    int grid = grid_for((long long)B * H * W, 4096);
+    int grid = grid_rows((long long)B * H, 4096);
     convert_kernel<<<grid, kThreads, 0, s>>>(src, dtype, H, W, B, dst, pitch);
     return cudaGetLastError();
 }
@@ -253,7 +261,7 @@ cudaError_t launch_convert(const void *src, int dtype, int H, int W, int B,
 cudaError_t launch_quantise(const float *src, int src_pitch, int H, int W, void *dst,
                             int pitch, int storage, cudaStream_t s)
 {
-    int grid = grid_for((long long)H * W, 4096);
+    int grid = grid_rows(H, 4096);
     quantise_kernel<<<grid, kThreads, 0, s>>>(src, src_pitch, H, W, dst, pitch, storage);
     return cudaGetLastError();
 }
@@ -265,7 +273,7 @@ cudaError_t launch_prologue(const void *img, int img_pitch, size_t band_stride,
                             LseDevState *st, LsePartial *partials, int nblocks,
                             cudaStream_t s)
 {
-    int grid = grid_for((long long)H * W, nblocks);
+    int grid = grid_rows(H, nblocks);
     prologue_kernel<<<grid, kThreads, 0, s>>>(img, img_pitch, band_stride, phi0,
                                               g, g_pitch, phi_dst, g_dst, pitch,
                                               H, W, B, term, dt, storage, st, partials);
@@ -276,7 +284,7 @@ cudaError_t launch_normaliser(const float *img, int pitch, size_t band_stride,
                               int H, int W, int B, float dt, LseDevState *st,
                               LsePartial *partials, int nblocks, cudaStream_t s)
 {
-    int grid = grid_for((long long)H * W, nblocks);
+    int grid = grid_rows(H, nblocks);
     normaliser_kernel<<<grid, kThreads, 0, s>>>(img, pitch, band_stride, H, W,
                                                 B, dt, st, partials);
     return cudaGetLastError();
@@ -296,7 +304,7 @@ cudaError_t launch_output(float *const *bufs, int pitch, int H, int W, int stora
     BufPair bp;
     bp.b[0] = bufs[0];
     bp.b[1] = bufs[1];
-    int grid = grid_for((long long)H * W, 4096);
+    int grid = grid_rows(H, 4096);
     output_kernel<<<grid, kThreads, 0, s>>>(bp, pitch, H, W, storage, st, phi_out,
                                             mask_out);
     return cudaGetLastError();

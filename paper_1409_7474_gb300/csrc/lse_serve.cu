@@ -175,7 +175,7 @@ lse_status admit(lse_server *sv, Request &r, int slot, cudaStream_t s)
     it.reinit_period = p.reinit_period;
     it.early_stop = p.early_stop_frac > 0.0f;
     it.iter0 = sv->tick;
-    if (region && q.B > 1) it.nnblocks = normaliser_blocks((long long)q.H * q.W, ctx->sm_count);
+    if (region && q.B > 1) it.nnblocks = normaliser_blocks(q.H, ctx->sm_count);
     r.key = class_of(plan, p.term, bands);
     r.pitch = L.pitch;
     r.slot = slot;

@@ -174,15 +174,32 @@ __device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait; block-uniform result (every thread polls).
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait; block-uniform result (every thread polls).  Gives up after
+// LSE_WAIT_LIMIT polls or limit_ns nanoseconds, whichever comes first (the
+// clock is read every 256 polls, from the 256th on).
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity,
+                                         unsigned long long limit_ns = LSE_WAIT_NS)
 {
     bool ok = false;
-    for (uint32_t i = 0; i < LSE_WAIT_LIMIT; ++i)
+    unsigned long long t0 = 0;
+    for (uint32_t i = 0; i < LSE_WAIT_LIMIT; ++i) {
         if (try_wait(bar, parity)) {
             ok = true;
             break;
         }
+        if ((i & 255u) == 255u) {
+            const unsigned long long t = global_ns();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > limit_ns) break;
+        }
+    }
     return __syncthreads_and(ok) != 0;
 }
 
@@ -289,6 +306,7 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
     float *hbase = G::WIDE ? smem_f + sb + G::PHI_OFF : smem_f + sb + G::HBUF_OFF;
     const uint32_t bar_phi = sm0 + 4u * (uint32_t)(sb + 32);
     const uint32_t bar_dat = bar_phi + 8;
+    const uint32_t bar_never = bar_phi + 16;   // test hook: nothing arrives here
     const uint32_t phi_dst = sm0 + 4u * (uint32_t)(sb + G::PHI_OFF);
     const uint32_t dat_dst = sm0 + 4u * (uint32_t)(sb + G::DATA_OFF);
     constexpr uint32_t kPhiBytes = G::PHI_BYTES;
@@ -309,6 +327,7 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_phi) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_dat) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_never) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -350,7 +369,14 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
     const T *dl = dat + G::DATA_X0 + 4 * lane;   // ... of a data row
     float *hl = hbase + G::H_COL0 + 4 * lane;    // ... of an h row
 
-    for (; t < n_tiles; t += ncta) {
+    // test hook: a wait that cannot complete (nothing arrives on bar_never)
+    // runs out into the TIMEOUT status; the first tile's copies, issued
+    // above, are drained below like those of any failed wait
+    if (a.stall_ns && t < n_tiles) {
+        (void)wait_bar(bar_never, 0, a.stall_ns);
+        failed = true;
+    }
+    for (; t < n_tiles && !failed; t += ncta) {
         int xs, ys;
         origin(t, xs, ys);
         const int x0 = xs + 4 * lane;

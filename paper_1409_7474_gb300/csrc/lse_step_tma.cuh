@@ -142,15 +142,25 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// Bounded wait on one stage; warp-uniform result.
+// Bounded wait on one stage; warp-uniform result.  Gives up after
+// LSE_WAIT_LIMIT polls or LSE_WAIT_NS nanoseconds of %globaltimer (read
+// every 256 polls, from the 256th on).
 __device__ __forceinline__ bool wait_stage(uint32_t bar, uint32_t parity)
 {
     bool ok = false;
-    for (uint32_t i = 0; i < LSE_WAIT_LIMIT; ++i)
+    unsigned long long t0 = 0;
+    for (uint32_t i = 0; i < LSE_WAIT_LIMIT; ++i) {
         if (mbar_try_wait(bar, parity)) {
             ok = true;
             break;
         }
+        if ((i & 255u) == 255u) {
+            unsigned long long t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > LSE_WAIT_NS) break;
+        }
+    }
     return __all_sync(0xffffffffu, ok);
 }
 
