@@ -186,7 +186,8 @@ typedef struct lse_ctx lse_ctx;
  * LSE_TEST_FAIL_ALLOC=N makes the context's next N scratch growths fail as
  * a failed cudaMalloc would (the call returns LSE_ERR_OOM, nothing is
  * enqueued past that point, and later calls work); LSE_TEST_STALL_NS=T makes
- * the first tile-form step of the next lse_evolve wait T nanoseconds on an
+ * the first tile-form step of the next lse_evolve wait T nanoseconds (at most
+ * 4e9) on an
  * mbarrier that nothing completes, so that its bounded wait runs out: the
  * call ends with status LSE_ERR_TIMEOUT and the context stays usable.  Every
  * device-side wait of the library gives up after 2^24 polls or 2 s. */
@@ -331,8 +332,12 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems,
  * mix it was tuned on: tune on work like what will run.  Later lse_evolve,
  * lse_evolve_batch and
  * lse_server_* calls on ctx use the table, so an image still gets the same
- * bits from each of them; untuned classes use 64-row tiles (32 when the
- * environment variable LSE_TILE_ROWS=32 was set at lse_create).  Changing an
+ * bits from each of them.  Untuned classes use 32-row tiles when the image
+ * has fewer 64-row tiles than the GPU has SMs, else 64-row tiles;
+ * LSE_TILE_ROWS=32 or =64 in the environment at lse_create fixes one
+ * height instead.  32-row steps whose grid leaves SM slots free are
+ * launched as programmatic dependents (the next step's CTAs become
+ * resident while the current one finishes).  Changing an
  * image's tile height regroups the partial sums of its region statistics,
  * so its results may change in the last bits (within the parity tolerances).
  * tile_rows (host, n entries, may be NULL) receives each problem's chosen

@@ -298,7 +298,10 @@ lse_status lse_create(lse_ctx **out, int device, size_t max_pixels, int max_band
     ctx->n_partials = partials_needed(ctx->sm_count);
     ctx->step_form = step_form_from_env();
     ctx->tile_nw_default = tile_nw_from_env();
-    if (const char *v = getenv("LSE_TEST_STALL_NS")) ctx->test_stall_ns = strtoull(v, nullptr, 10);
+    if (const char *v = getenv("LSE_TEST_STALL_NS")) {
+        ctx->test_stall_ns = strtoull(v, nullptr, 10);
+        if (ctx->test_stall_ns > 4000000000ull) ctx->test_stall_ns = 4000000000ull;
+    }
     if (const char *v = getenv("LSE_TEST_FAIL_ALLOC")) ctx->test_fail_alloc = atoi(v);
     cudaError_t e = cudaMalloc(&ctx->partials, sizeof(LsePartial) * ctx->n_partials);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->st, sizeof(LseDevState));

@@ -44,10 +44,10 @@ struct lse_ctx {
     bool have_stats = false;
     int step_form = 0;               // LSE_STEP_KERNEL at creation (LSE_FORM_*)
     // tile form: warps per CTA (8: 64-row tiles, 4: 32-row) per shape class,
-    // chosen by lse_autotune; tile_nw_default (LSE_TILE_ROWS at creation)
-    // for shapes it has not tuned
+    // chosen by lse_autotune; for shapes it has not tuned, tile_nw_default
+    // (LSE_TILE_ROWS at creation), or when that is 0 the automatic choice
     std::map<TuneKey, int> tile_tune;
-    int tile_nw_default = 8;
+    int tile_nw_default = 0;
     float *tune_out = nullptr;       // lse_autotune: outputs of its trial runs
     size_t tune_out_cap = 0;         // bytes
     // test hooks, from the environment at creation (see lse_create):

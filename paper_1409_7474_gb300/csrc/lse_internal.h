@@ -95,6 +95,8 @@ struct StepArgs {
     int th;                     // output rows per item
     int n_items;
     int nw;                     // tile form: warps per CTA (8: 64-row tiles, 4: 32-row)
+    int pdl;                    // tile form: launch as a programmatic dependent
+                                // (the grid leaves SM slots free)
     // test hook (0 = off): the tile form's CTAs first wait this long (ns) on
     // an mbarrier that nothing arrives at, so the bounded wait runs out
     unsigned long long stall_ns;
@@ -259,9 +261,12 @@ struct StepPlan {
 
 void gauss_taps(double sigma, int rad, double *out);
 int step_form_from_env();
-// Warps per CTA of the tile form unless tuned: 4 when LSE_TILE_ROWS=32,
-// else 8 (64-row tiles).
+// Warps per CTA of the tile form for untuned shapes as LSE_TILE_ROWS sets it:
+// 4 for "32", 8 for "64", 0 (automatic, tile_nw_default_for) otherwise.
 int tile_nw_from_env();
+// The automatic choice: 32-row tiles (4 warps) when the image has fewer
+// 64-row tiles than the GPU has SMs, else 64-row tiles (8 warps).
+int tile_nw_default_for(int H, int W, int ts, int sm_count);
 // Fills the step arguments for a call and picks its kernel (`requested` is
 // LSE_FORM_AUTO, _STREAM or _GENERIC; `tile_nw` the tile form's warps per
 // CTA, 8 or 4).  Returns false when no step kernel serves the call (16-bit

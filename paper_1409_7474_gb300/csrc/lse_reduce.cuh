@@ -32,15 +32,18 @@ struct LseAcc {
     }
 };
 
-// Reduces `acc` over the CTA (blockDim.x a multiple of 32, <= 1024) into
-// `out` (visible to thread 0 after return).  `nb` bands are summed.
+// Reduces `acc` over the CTA (blockDim.x a multiple of 32, at most 32 MAXW)
+// into `out` (visible to thread 0 after return).  `nb` bands are summed.
+// MAXW sizes the static shared arrays: a kernel of few warps passes its own
+// count and keeps that shared memory for its tiles.
+template <int MAXW = 32>
 __device__ __forceinline__ void lse_cta_reduce(const LseAcc &acc, int nb,
                                                LseAcc *out)
 {
-    __shared__ double s_d[32][2 * LSE_MAXB];
-    __shared__ long long s_l[32][2];
-    __shared__ float s_f[32][2];
-    __shared__ unsigned int s_u[32];
+    __shared__ double s_d[MAXW][2 * LSE_MAXB];
+    __shared__ long long s_l[MAXW][2];
+    __shared__ float s_f[MAXW][2];
+    __shared__ unsigned int s_u[MAXW];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -133,6 +136,7 @@ __device__ __forceinline__ bool lse_publish_and_ticket(const LseAcc &r, int nb,
 }
 
 // In the last CTA: sums all partials in CTA order into `total` (thread 0).
+template <int MAXW = 32>
 __device__ __forceinline__ void lse_sum_partials(const LsePartial *partials,
                                                  int nparts, int nb,
                                                  LseAcc *total)
@@ -151,7 +155,7 @@ __device__ __forceinline__ void lse_sum_partials(const LsePartial *partials,
         a.fmin = fminf(a.fmin, __ldcg(&p->fmin));
         a.bits |= __ldcg(&p->bits);
     }
-    lse_cta_reduce(a, nb, total);
+    lse_cta_reduce<MAXW>(a, nb, total);
 }
 
 // Region statistics of the current LSF -> c+/c- and the coefficients of the

@@ -42,6 +42,7 @@
 
 #include <type_traits>
 
+#include "lse_f2.cuh"
 #include "lse_reduce.cuh"
 
 namespace lse_tile {
@@ -174,29 +175,50 @@ __device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-__device__ __forceinline__ unsigned long long global_ns()
+// Programmatic dependent launch, for the 32-row (4-warp) instantiations: a
+// grid that leaves SM slots free (StepArgs::pdl) is launched so that the next
+// one may become resident while it finishes.  Every CTA of such a launch
+// waits for the previous grid's completion and memory before anything else,
+// so no CTA can exit earlier and a grid's completion implies its
+// predecessor's (a plain launch starts only after its predecessor
+// completed); each lets the next grid launch once its tiles are done.  The
+// 64-row instantiations carry neither instruction: in them alone it cost a
+// full-grid launch about 1 % (measured), and images small enough to gain
+// from it default to 32-row tiles.  Batches launch plainly.
+__device__ __forceinline__ void wait_prior_grid()
 {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void allow_next_grid()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Low 32 bits of %globaltimer (ns); differences are wrap-safe up to ~4.29 s.
+__device__ __forceinline__ uint32_t global_ns_lo()
+{
+    uint32_t t;
+    asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(t));
     return t;
 }
 
 // Bounded wait; block-uniform result (every thread polls).  Gives up after
-// LSE_WAIT_LIMIT polls or limit_ns nanoseconds, whichever comes first (the
-// clock is read every 256 polls, from the 256th on).
+// LSE_WAIT_LIMIT polls or limit_ns nanoseconds (at most 4e9), whichever
+// comes first (the clock is read every 256 polls, from the 256th on).
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity,
-                                         unsigned long long limit_ns = LSE_WAIT_NS)
+                                         uint32_t limit_ns = (uint32_t)LSE_WAIT_NS)
 {
     bool ok = false;
-    unsigned long long t0 = 0;
+    uint32_t t0 = 0;
     for (uint32_t i = 0; i < LSE_WAIT_LIMIT; ++i) {
         if (try_wait(bar, parity)) {
             ok = true;
             break;
         }
         if ((i & 255u) == 255u) {
-            const unsigned long long t = global_ns();
-            if (t0 == 0) t0 = t;
+            const uint32_t t = global_ns_lo();
+            if (i == 255u) t0 = t;
             else if (t - t0 > limit_ns) break;
         }
     }
@@ -232,53 +254,6 @@ __device__ __forceinline__ float comp(const float4 &v, int j)
 __device__ __forceinline__ float4 lds4(const float *p)
 {
     return *reinterpret_cast<const float4 *>(p);
-}
-
-// Two FP32 values in one 64-bit register pair.  Blackwell's packed FP32
-// instructions (add / mul / fma .rn.f32x2) round each element exactly as the
-// scalar instruction does, in one instruction for the pair.
-struct f2 {
-    unsigned long long r;
-};
-
-__device__ __forceinline__ f2 f2_pack(float a, float b)
-{
-    f2 o;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(o.r) : "f"(a), "f"(b));
-    return o;
-}
-
-__device__ __forceinline__ void f2_unpack(f2 v, float &a, float &b)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v.r));
-}
-
-__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
-{
-    f2 o;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(o.r) : "l"(a.r), "l"(b.r));
-    return o;
-}
-
-__device__ __forceinline__ f2 f2_sub(f2 a, f2 b)
-{
-    f2 o;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(o.r) : "l"(a.r), "l"(b.r));
-    return o;
-}
-
-__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
-{
-    f2 o;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(o.r) : "l"(a.r), "l"(b.r));
-    return o;
-}
-
-__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
-{
-    f2 o;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(o.r) : "l"(a.r), "l"(b.r), "l"(c.r));
-    return o;
 }
 
 // One step over the tiles of one image, run by CTA `cta` of the `ncta` CTAs
@@ -372,8 +347,9 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
     // test hook: a wait that cannot complete (nothing arrives on bar_never)
     // runs out into the TIMEOUT status; the first tile's copies, issued
     // above, are drained below like those of any failed wait
-    if (a.stall_ns && t < n_tiles) {
-        (void)wait_bar(bar_never, 0, a.stall_ns);
+    // (the first step of an evolution never takes the FAST instantiation)
+    if (!FAST && a.stall_ns && t < n_tiles) {
+        (void)wait_bar(bar_never, 0, (uint32_t)a.stall_ns);
         failed = true;
     }
     for (; t < n_tiles && !failed; t += ncta) {
@@ -659,6 +635,7 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
         if (tid == 0 && tn < n_tiles) load_tile(tn);
         par ^= 1u;
     }
+    if (NW == 4 && a.pdl) allow_next_grid();
     if (failed) {
         if (tid == 0) atomicOr(&st->status_bits, LSE_SBIT_TIMEOUT);
         // drain the copies in flight (bounded) before the CTA may exit
@@ -674,10 +651,10 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
     acc.flips = nflip;
     const int nb = EDGE ? 0 : 1;
     LseAcc r;
-    lse_cta_reduce(acc, nb, &r);
+    lse_cta_reduce<NW>(acc, nb, &r);
     if (!lse_publish_and_ticket_at(r, nb, a.partials, st, cta, ncta)) return;
     LseAcc tot;
-    lse_sum_partials(a.partials, ncta, nb, &tot);
+    lse_sum_partials<NW>(a.partials, ncta, nb, &tot);
     if (threadIdx.x == 0) lse_step_finalize(a, tot);
 }
 
@@ -687,6 +664,7 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
                  const __grid_constant__ CUtensorMap phi_map,
                  const __grid_constant__ CUtensorMap data_map)
 {
+    if (NW == 4 && a.pdl) wait_prior_grid();
     tile_step<KIND_EDGE, RAD, FAST, T, NW>(a, &phi_map, &data_map, blockIdx.x, gridDim.x);
 }
 
@@ -709,6 +687,26 @@ step_tile_batch_kernel(const BatchItem *__restrict__ items, const int *__restric
                                             blockIdx.x - it.start, it.nblocks);
 }
 
+// Launches a step kernel with programmatic stream serialisation: it may
+// start while the previous kernel in the stream finishes, and waits for it
+// in wait_prior_grid().
+template <typename Kern, typename... Args>
+cudaError_t launch_dependent(Kern kern, int nblocks, int threads, int smem, cudaStream_t s,
+                             Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // FAST: the steady state of a re-initialising evolution.
 __host__ __device__ inline bool is_fast(const StepArgs &a)
 {
@@ -725,6 +723,8 @@ cudaError_t launch_tile_one(const StepArgs &a, const CUtensorMap &pm, const CUte
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          G::BYTES);
     if (e != cudaSuccess) return e;
+    if (NW == 4 && a.pdl)
+        return launch_dependent(kern, nblocks, G::THREADS, G::BYTES, s, a, pm, dm);
     kern<<<nblocks, G::THREADS, G::BYTES, s>>>(a, pm, dm);
     return cudaGetLastError();
 }

@@ -130,6 +130,10 @@ bool plan_step_tile(int H, int W, int B, int term, int rad, int nw, int sm_count
     const int resident = sm_count * ((rad <= 4 ? 24 : 16) / nw);
     if (blocks > resident) blocks = resident;
     *nblocks = blocks;
+    // a grid smaller than the resident slots lets the next iteration's CTAs
+    // start while this one finishes; a full grid would only hold slots that
+    // other streams' kernels could use
+    a->pdl = blocks < resident ? 1 : 0;
     return true;
 }
 

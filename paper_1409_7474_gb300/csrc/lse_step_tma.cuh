@@ -51,6 +51,7 @@
 #pragma once
 #include <type_traits>
 
+#include "lse_f2.cuh"
 #include "lse_reduce.cuh"
 
 namespace lse_tma {
@@ -239,6 +240,12 @@ __device__ __forceinline__ void tma_step(const StepArgs &a, const CUtensorMap *p
         mid[b] = T::REGION ? st->m[b] : 0.0f;
     }
     const float half_dt = a.half_dt;
+    // the same constants as pairs, for the packed column-pair arithmetic
+    f2 tp2[RAD + 1];
+#pragma unroll
+    for (int k = 0; k <= RAD; ++k) tp2[k] = f2_pack(tp[k], tp[k]);
+    const f2 coef20 = f2_pack(coef[0], coef[0]), mid20 = f2_pack(mid[0], mid[0]);
+    const f2 half_dt2 = f2_pack(half_dt, half_dt);
     const bool binarise_in = !BIN && a.binarise_in != 0;
     const bool count_flips = a.count_flips != 0;
     const bool store_bin = a.store_bin != 0;
@@ -375,7 +382,12 @@ __device__ __forceinline__ void tma_step(const StepArgs &a, const CUtensorMap *p
             pp = bin4(pp);
         }
         float4 pm = p0;
-        float ring_h[P][4];
+        // h rows: as column pairs for the packed vertical pass (one band,
+        // edge term); vector images keep the scalar ring, their band
+        // constants already fill the register budget
+        constexpr bool PK = KIND != K_REGION_MB;
+        f2 ring_h[PK ? P : 1][2];
+        float ring_s[PK ? 1 : P][4];
 
         // one u-row: u of row r, its horizontal pass into ring slot kk, and
         // (OUT) the vertical pass, store and statistics of row r - RAD
@@ -418,31 +430,39 @@ __device__ __forceinline__ void tma_step(const StepArgs &a, const CUtensorMap *p
                 }
             }
             const bool yin = y >= 0 && y < H;
-            // data term factor t = 0.5 dt R
-            float t[4];
+            // data term factor t = 0.5 dt R, on column pairs (each packed
+            // operation rounds as its scalar form)
+            // (vector images: per band in scalar form, which keeps the band
+            // constants out of the register budget)
+            f2 t2[2];
             if (KIND == K_EDGE) {
                 const float4 g4 = ld4(&smem_f[rowR + 4 * lane]);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) t[j] = half_dt * comp(g4, j);
+                t2[0] = f2_mul(half_dt2, f2_pack(g4.x, g4.y));
+                t2[1] = f2_mul(half_dt2, f2_pack(g4.z, g4.w));
+            } else if (KIND == K_REGION1) {
+                const float4 d4 = ld4(&smem_f[rowR + 4 * lane]);
+                t2[0] = f2_mul(coef20, f2_sub(f2_pack(d4.x, d4.y), mid20));
+                t2[1] = f2_mul(coef20, f2_sub(f2_pack(d4.z, d4.w), mid20));
             } else {
                 const float4 d4 = ld4(&smem_f[rowR + 4 * lane]);
+                float t[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) t[j] = coef[0] * (comp(d4, j) - mid[0]);
-                if (KIND == K_REGION_MB) {
 #pragma unroll
-                    for (int b = 1; b < NB; ++b) {
-                        if (b < B) {
-                            const float4 e4 = ld4(&smem_f[rowR + b * kDataBox + 4 * lane]);
+                for (int b = 1; b < NB; ++b) {
+                    if (b < B) {
+                        const float4 e4 = ld4(&smem_f[rowR + b * kDataBox + 4 * lane]);
 #pragma unroll
-                            for (int j = 0; j < 4; ++j)
-                                t[j] = fmaf(coef[b], comp(e4, j) - mid[b], t[j]);
-                        }
+                        for (int j = 0; j < 4; ++j)
+                            t[j] = fmaf(coef[b], comp(e4, j) - mid[b], t[j]);
                     }
                 }
+                t2[0] = f2_pack(t[0], t[1]);
+                t2[1] = f2_pack(t[2], t[3]);
             }
             // u = phi + t * 2|grad phi| (zero outside the image)
             const float c[6] = {lft, p0.x, p0.y, p0.z, p0.w, rgt};
-            float u[4];
+            float dxs[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float dx = c[j + 2] - c[j];
@@ -451,14 +471,39 @@ __device__ __forceinline__ void tma_step(const StepArgs &a, const CUtensorMap *p
                     else if (oneL[j]) dx = 2.0f * (c[j + 2] - c[j + 1]);
                     else if (oneR[j]) dx = 2.0f * (c[j + 1] - c[j]);
                 }
-                const float dy = comp(ppx, j) - comp(pmx, j);
-                const float q = fmaf(dx, dx, dy * dy);
-                float s2;
-                if (BIN)
-                    s2 = smem_f[lut + ((__float_as_uint(q) >> 21) & 31u)];
-                else
-                    s2 = sqrtf(q);
-                u[j] = fmaf(t[j], s2, c[j + 1]);
+                dxs[j] = dx;
+            }
+            float u[4];
+#pragma unroll
+            for (int jp = 0; jp < 2; ++jp) {
+                const int j0 = 2 * jp, j1 = 2 * jp + 1;
+                if constexpr (!PK) {
+                    // vector images: the scalar form of the same update
+                    float tt[2];
+                    f2_unpack(t2[jp], tt[0], tt[1]);
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int j = j0 + e;
+                        const float dy = comp(ppx, j) - comp(pmx, j);
+                        const float q = fmaf(dxs[j], dxs[j], dy * dy);
+                        const float s2 = BIN ? smem_f[lut + ((__float_as_uint(q) >> 21) & 31u)]
+                                             : sqrtf(q);
+                        u[j] = fmaf(tt[e], s2, c[j + 1]);
+                    }
+                    continue;
+                }
+                const f2 dx = f2_pack(dxs[j0], dxs[j1]);
+                const f2 dy = f2_sub(f2_pack(comp(ppx, j0), comp(ppx, j1)),
+                                     f2_pack(comp(pmx, j0), comp(pmx, j1)));
+                float q[2];
+                f2_unpack(f2_fma(dx, dx, f2_mul(dy, dy)), q[0], q[1]);
+                float s2[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e)
+                    s2[e] = BIN ? smem_f[lut + ((__float_as_uint(q[e]) >> 21) & 31u)]
+                                : sqrtf(q[e]);
+                f2_unpack(f2_fma(t2[jp], f2_pack(s2[0], s2[1]), f2_pack(c[j0 + 1], c[j1 + 1])),
+                          u[j0], u[j1]);
             }
             if (xborder) {
 #pragma unroll
@@ -482,27 +527,49 @@ __device__ __forceinline__ void tma_step(const StepArgs &a, const CUtensorMap *p
                         U[4 * HL + j + 4 * o] = __shfl_down_sync(0xffffffffu, u[j], o);
                 }
             }
+            float hv[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float h = tp[0] * U[4 * HL + j];
 #pragma unroll
                 for (int q = 1; q <= RAD; ++q)
                     h = fmaf(tp[q], U[4 * HL + j - q] + U[4 * HL + j + q], h);
-                ring_h[kk][j] = h;
+                hv[j] = h;
+            }
+            if constexpr (PK) {
+                ring_h[kk][0] = f2_pack(hv[0], hv[1]);
+                ring_h[kk][1] = f2_pack(hv[2], hv[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) ring_s[kk][j] = hv[j];
             }
             if (!OUT) return;
-            // vertical pass of row r - RAD
+            // vertical pass of row r - RAD (on column pairs where packed)
             float v[4];
+            if constexpr (PK) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float acc = tp[0] * ring_h[(kk - RAD + P) % P][j];
+                for (int jp = 0; jp < 2; ++jp) {
+                    f2 acc = f2_mul(tp2[0], ring_h[(kk - RAD + P) % P][jp]);
 #pragma unroll
-                for (int q = 1; q <= RAD; ++q)
-                    acc = fmaf(tp[q],
-                               ring_h[(kk - RAD - q + 2 * P) % P][j] +
-                                   ring_h[(kk - RAD + q + P) % P][j],
-                               acc);
-                v[j] = acc;
+                    for (int q = 1; q <= RAD; ++q)
+                        acc = f2_fma(tp2[q],
+                                     f2_add(ring_h[(kk - RAD - q + 2 * P) % P][jp],
+                                            ring_h[(kk - RAD + q + P) % P][jp]),
+                                     acc);
+                    f2_unpack(acc, v[2 * jp], v[2 * jp + 1]);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float acc = tp[0] * ring_s[(kk - RAD + P) % P][j];
+#pragma unroll
+                    for (int q = 1; q <= RAD; ++q)
+                        acc = fmaf(tp[q],
+                                   ring_s[(kk - RAD - q + 2 * P) % P][j] +
+                                       ring_s[(kk - RAD + q + P) % P][j],
+                                   acc);
+                    v[j] = acc;
+                }
             }
             const int yo = ys + r - RAD;
             if (yo >= H) return;

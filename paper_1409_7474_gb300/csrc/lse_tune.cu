@@ -49,15 +49,33 @@ namespace lse_detail {
 int tile_nw_from_env()
 {
     const char *v = getenv("LSE_TILE_ROWS");
-    return (v && strcmp(v, "32") == 0) ? 4 : 8;
+    if (v && strcmp(v, "32") == 0) return 4;
+    if (v && strcmp(v, "64") == 0) return 8;
+    return 0;
+}
+
+int tile_nw_default_for(int H, int W, int ts, int sm_count)
+{
+    // an image with fewer 64-row tiles than SMs leaves SMs idle: halve the
+    // tile height (32-row tiles also overlap consecutive steps, see
+    // launch_dependent)
+    const int rad = (ts - 1) / 2;
+    if (rad < 1 || rad > 7) return 8;
+    const int useful = 128 - 8 * ((rad + 3) / 4);
+    const long long tiles =
+        (long long)((W + useful - 1) / useful) * ((H + 64 - 2 * rad - 1) / (64 - 2 * rad));
+    return tiles < sm_count ? 4 : 8;
 }
 
 int tile_nw_for(const lse_ctx *ctx, int H, int W, int term, int storage, int ts)
 {
     TuneKey key;
-    if (!tune_key(H, W, 1, term, storage, ts, &key)) return ctx->tile_nw_default;
-    auto it = ctx->tile_tune.find(key);
-    return it == ctx->tile_tune.end() ? ctx->tile_nw_default : it->second;
+    if (tune_key(H, W, 1, term, storage, ts, &key)) {
+        auto it = ctx->tile_tune.find(key);
+        if (it != ctx->tile_tune.end()) return it->second;
+    }
+    if (ctx->tile_nw_default) return ctx->tile_nw_default;
+    return tile_nw_default_for(H, W, ts, ctx->sm_count);
 }
 
 }  // namespace lse_detail
@@ -123,7 +141,11 @@ extern "C" lse_status lse_autotune(lse_ctx *ctx, int n, const lse_problem *probl
     };
     std::map<TuneKey, int> saved = ctx->tile_tune;
     for (auto &g : groups)
-        if (!ctx->tile_tune.count(g.first)) ctx->tile_tune[g.first] = ctx->tile_nw_default;
+        if (!ctx->tile_tune.count(g.first)) {
+            const lse_problem &q = problems[g.second[0]];
+            ctx->tile_tune[g.first] =
+                tile_nw_for(ctx, q.H, q.W, q.params.term, q.params.storage, q.params.ts);
+        }
     // larger classes first: they move the total the most
     std::vector<std::pair<double, TuneKey>> order;
     for (auto &g : groups) {

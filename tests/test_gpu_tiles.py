@@ -41,7 +41,12 @@ def lse():
 
 @pytest.fixture(scope="module")
 def ctx64(torch, lse):
-    c = lse.Context(0, max_pixels=1024 * 1024, max_bands=4)
+    # 64-row tiles even for images the automatic choice gives 32-row tiles
+    os.environ["LSE_TILE_ROWS"] = "64"
+    try:
+        c = lse.Context(0, max_pixels=1024 * 1024, max_bands=4)
+    finally:
+        del os.environ["LSE_TILE_ROWS"]
     yield c
     c.destroy()
 
