@@ -102,7 +102,9 @@ typedef enum {
  *                   iteration in which fewer than early_stop_frac * H * W pixels
  *                   changed sign (Step 5: stop when phi stops varying).
  *   storage         type of the work planes in HBM: LSE_F32, or LSE_F16 /
- *                   LSE_BF16 for one band (or the edge term) with ts <= 15.
+ *                   LSE_BF16 for one band (or the edge term) with ts <= 9
+ *                   (at larger radii the tile layout would start TMA copies
+ *                   off the 16-byte boundary that 16-bit rows need).
  *                   16-bit storage rounds the data term (I or g) to the type
  *                   once (round to nearest even) and keeps the LSF between
  *                   iterations in it; arithmetic stays FP32 and the region

@@ -194,8 +194,8 @@ lse_status check_params(lse_ctx *ctx, const lse_params &p, int B)
         set_err(ctx, "storage must be LSE_F32, LSE_F16 or LSE_BF16 (got %d)", (int)p.storage);
         return LSE_ERR_INVALID_ARG;
     }
-    if (p.storage != LSE_F32 && ((p.term == LSE_TERM_REGION && B != 1) || p.ts > 15)) {
-        set_err(ctx, "16-bit storage needs one band (or the edge term) and ts <= 15");
+    if (p.storage != LSE_F32 && ((p.term == LSE_TERM_REGION && B != 1) || p.ts > 9)) {
+        set_err(ctx, "16-bit storage needs one band (or the edge term) and ts <= 9");
         return LSE_ERR_INVALID_ARG;
     }
     if ((p.order != LSE_ORDER_LISTING && p.order != LSE_ORDER_TABLE1) ||

@@ -225,6 +225,9 @@ bool plan_step_tma(int H, int W, int B, int term, int rad, int sm_count,
 // elements.
 bool plan_step_tile(int H, int W, int B, int term, int rad, int nw, int sm_count,
                     StepArgs *a, int *nblocks);
+// Whether every TMA box of the tile form starts on 16 bytes for a radius and
+// element size (false for 16-bit elements at radius 5..7).
+bool tile_boxes_aligned(int rad, int elem_bytes);
 cudaError_t launch_step_tile(const StepArgs &a, const CUtensorMap &phi_map,
                              const CUtensorMap &data_map, int nblocks, cudaStream_t s);
 int partials_needed(int sm_count);

@@ -110,11 +110,24 @@ cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap &phi_map,
 // output columns (nw = warps per CTA, 8 or 4), walked by as many CTAs as fit
 // on the SMs at once: 24 warps per SM for rad <= 4, else 16 (the kernels'
 // launch bounds).
+bool tile_boxes_aligned(int rad, int elem_bytes)
+{
+    // tile k's boxes start at column k * useful - 4 hl - 4 (phi, and the
+    // 16-bit data box) or k * useful - 4 hl (the FP32 data box); a tiled TMA
+    // copy must start on 16 bytes, so every such column must be a multiple
+    // of 16 / elem_bytes.  16-bit elements with hl = 2 (radius 5..7) fail.
+    const int hl = (rad + 3) / 4;
+    const int useful = 128 - 8 * hl;
+    const int q = 16 / elem_bytes;
+    return useful % q == 0 && (4 * hl) % q == 0 && (4 * hl + 4) % q == 0;
+}
+
 bool plan_step_tile(int H, int W, int B, int term, int rad, int nw, int sm_count,
                     StepArgs *a, int *nblocks)
 {
     if (rad < 1 || rad > 7 || (nw != 8 && nw != 4)) return false;
     if (term == LSE_TERM_REGION && B != 1) return false;
+    if (!tile_boxes_aligned(rad, a->storage == LSE_F32 ? 4 : 2)) return false;
     const int hl = (rad + 3) / 4;
     const int useful = 128 - 8 * hl;
     const int th = 8 * nw - 2 * rad;

@@ -132,8 +132,13 @@ def test_storage_limits(torch, ctx):
     with pytest.raises(lse.LseError, match="16-bit storage"):
         gpu(torch, ctx, img4, phi, iterations=1, storage="bf16")
     img1 = np.zeros((1, 32, 32), np.float32)
-    with pytest.raises(lse.LseError, match="16-bit storage"):
-        gpu(torch, ctx, img1, phi, iterations=1, ts=17, storage="f16")
+    # radius 5..7 would start the tile's 16-bit TMA boxes off 16 bytes: the
+    # argument check refuses them before anything reaches the GPU
+    for ts in (11, 13, 15, 17):
+        for sto in ("f16", "bf16"):
+            with pytest.raises(lse.LseError, match="16-bit storage"):
+                gpu(torch, ctx, img1, phi, iterations=1, ts=ts, storage=sto)
+    gpu(torch, ctx, img1, phi, iterations=1, ts=9, storage="bf16")
     p = lse.Params(lse.TERM_REGION, 15.0, 1.0, 9, 1, 1, 0.0, lse.U16)
     st = lse.Stats()
     x = torch.zeros((32, 32), dtype=torch.float32, device="cuda")
