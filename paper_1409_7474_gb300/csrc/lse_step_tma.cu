@@ -113,13 +113,16 @@ cudaError_t launch_step_tma(const StepArgs &a, const CUtensorMap &phi_map,
 bool tile_boxes_aligned(int rad, int elem_bytes)
 {
     // tile k's boxes start at column k * useful - 4 hl - 4 (phi, and the
-    // 16-bit data box) or k * useful - 4 hl (the FP32 data box); a tiled TMA
-    // copy must start on 16 bytes, so every such column must be a multiple
-    // of 16 / elem_bytes.  16-bit elements with hl = 2 (radius 5..7) fail.
+    // 16-bit data box) and, for FP32, k * useful - 4 hl (the data box); a
+    // tiled TMA copy must start on 16 bytes, so every such column must be a
+    // multiple of 16 / elem_bytes.  16-bit elements with hl = 2 (radius
+    // 5..7) fail: 112 k - 12 is 4 modulo 8.
     const int hl = (rad + 3) / 4;
     const int useful = 128 - 8 * hl;
     const int q = 16 / elem_bytes;
-    return useful % q == 0 && (4 * hl) % q == 0 && (4 * hl + 4) % q == 0;
+    const bool phi_ok = useful % q == 0 && (4 * hl + 4) % q == 0;
+    const bool data_ok = elem_bytes == 4 ? (4 * hl) % q == 0 : true;   // 16-bit: phi's column
+    return phi_ok && data_ok;
 }
 
 bool plan_step_tile(int H, int W, int B, int term, int rad, int nw, int sm_count,
