@@ -343,9 +343,10 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems,
  * image's tile height regroups the partial sums of its region statistics,
  * so its results may change in the last bits (within the parity tolerances).
  * tile_rows (host, n entries, may be NULL) receives each problem's chosen
- * height in rows, 0 where the tile form does not apply (more than one band
- * of the region term, ts > 15, ts = 1).  Problems must pass lse_evolve_batch's
- * checks; its errors are returned.  Synchronises `stream`. */
+ * height in rows, 0 where the tile form does not apply (more than four
+ * bands, or more than one with 16-bit storage; ts > 15; ts = 1).  Problems
+ * must pass lse_evolve_batch's checks; its errors are returned.
+ * Synchronises `stream`. */
 lse_status lse_autotune(lse_ctx *ctx, int n, const lse_problem *problems, int iterations,
                         int *tile_rows, void *stream);
 

@@ -256,7 +256,8 @@ void lse_destroy(lse_ctx *ctx)
     DeviceGuard g(ctx->device);
     void *bufs[] = {ctx->phi[0], ctx->phi[1], ctx->img, ctx->gbuf, ctx->raw_in,
                     ctx->phi0_st, ctx->g_st, ctx->out_phi, ctx->out_mask, ctx->q16,
-                    ctx->partials, ctx->st, ctx->arena, ctx->tables, ctx->tune_out};
+                    ctx->partials, ctx->st, ctx->arena, ctx->tables, ctx->tune_out,
+                    ctx->dplane};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (ctx->st_host) cudaFreeHost(ctx->st_host);
@@ -510,11 +511,18 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
                         W, B, p.term, p.dt, sto, ctx->st, ctx->partials, nred, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "prologue");
 
+    // vector images: the plane the band passes write D into, for the tile form
+    float *dplane = nullptr;
+    if (region && B > 1 && sto == LSE_F32 && ctx->step_form == LSE_FORM_AUTO) {
+        if ((r = ensure_t(ctx, &ctx->dplane, &ctx->dplane_cap, (size_t)H * pitch, s, "D plane")) != LSE_OK)
+            return r;
+        dplane = ctx->dplane;
+    }
     // the step's kernel, work decomposition and tensor maps
     StepPlan plan;
     if (!plan_step(H, W, B, p, pitch, band_stride, data_s, ctx->phi, ctx->st, ctx->partials,
-                   ctx->sm_count, ctx->step_form, tile_nw_for(ctx, H, W, p.term, sto, p.ts),
-                   &plan)) {
+                   ctx->sm_count, ctx->step_form, tile_nw_for(ctx, H, W, B, p.term, sto, p.ts),
+                   dplane, &plan)) {
         set_err(ctx, "16-bit storage runs on the tile-form step only (LSE_STEP_KERNEL "
                      "narrowed the choice, or its tensor maps could not be encoded)");
         return LSE_ERR_INVALID_ARG;
@@ -528,8 +536,19 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
     }
     e = cudaEventRecord(ctx->ev0, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
+    const bool bands_pass = plan.args.mb_split != 0;
     for (int n = 0; n < p.iterations; ++n) {
-        if (region && B > 1) {
+        if (bands_pass) {
+            // statistics of the LSF this step reads (the prologue made the
+            // first ones), then D and its maximum
+            if (n > 0)
+                e = launch_band_stats(data, pitch, band_stride, ctx->phi, H, W, B, p.dt, ctx->st,
+                                      ctx->partials, nred, false, s);
+            if (e == cudaSuccess)
+                e = launch_band_dterm(data, pitch, band_stride, dplane, H, W, B, p.dt, ctx->st,
+                                      ctx->partials, nred, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "band passes");
+        } else if (region && B > 1) {
             e = launch_normaliser(data, pitch, band_stride, H, W, B, p.dt, ctx->st,
                                   ctx->partials, nred, s);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "normaliser");
@@ -540,6 +559,12 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
     }
     e = cudaEventRecord(ctx->ev1, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
+    if (bands_pass) {
+        // the statistics lse_stats reports: those of the returned LSF
+        e = launch_band_stats(data, pitch, band_stride, ctx->phi, H, W, B, p.dt, ctx->st,
+                              ctx->partials, nred, true, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "band statistics");
+    }
     e = launch_output(ctx->phi, pitch, H, W, sto, ctx->st, out_phi, out_mask, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "output");
     if (ko == PTR_HOST) {

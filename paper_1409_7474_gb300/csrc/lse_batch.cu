@@ -71,6 +71,11 @@ ImagePlanes image_planes(const lse_problem &q)
     L.phi0 = align_up(plane * bands);
     L.phi1 = L.phi0 + align_up(plane);
     L.end = L.phi1 + align_up(plane);
+    L.dplane = 0;
+    if (bands > 1 && bands <= 4 && L.es == 4) {
+        L.dplane = L.end;
+        L.end += align_up(plane);
+    }
     return L;
 }
 
@@ -113,8 +118,9 @@ cudaError_t stage_problem(const lse_problem &q, unsigned char *base, const Image
                                 q.W, q.B, p.term, p.dt, sto, st, parts, nred, s);
     }
     if (e != cudaSuccess) return e;
+    float *dplane = L.dplane ? reinterpret_cast<float *>(base + L.dplane) : nullptr;
     *planned = plan_step(q.H, q.W, q.B, p, pitch, bstride, data, phi, st, parts, sm_count, form,
-                         tile_nw, plan) &&
+                         tile_nw, dplane, plan) &&
                plan->form != LSE_FORM_GENERIC;
     return cudaSuccess;
 }
@@ -168,8 +174,16 @@ cudaError_t launch_class(const ClassKey &k, const Class &c, const BatchItem *ite
     const int nb = c.pre[k_act], nnb = c.npre[k_act];
     if (nb == 0) return cudaSuccess;
     const int *blk = reinterpret_cast<const int *>(tables + c.blk_off);
-    if (k.form == LSE_FORM_TILE)
-        return launch_step_tile_batch(k.storage, k.term, k.nw, k.rad, items, blk, n, nb, s);
+    if (k.form == LSE_FORM_TILE) {
+        if (k.bands > 1) {
+            // vector images: statistics and D before the step on the D plane
+            const int *nblk = reinterpret_cast<const int *>(tables + c.nblk_off);
+            cudaError_t e = launch_band_passes_batch(items, nblk, n, nnb, s);
+            if (e != cudaSuccess) return e;
+        }
+        return launch_step_tile_batch(k.storage, k.bands > 1 ? LSE_TERM_EDGE : k.term, k.nw,
+                                      k.rad, items, blk, n, nb, s);
+    }
     if (k.term == LSE_TERM_EDGE)
         return launch_step_tma_batch_edge(k.rad, items, blk, n, nb, k.wpc, s);
     if (k.bands == 1)
@@ -275,7 +289,7 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
         StepPlan plan;
         bool planned = false;
         e = stage_problem(q, A + base[i], lay[i], states + i, parts, nred, ctx->sm_count,
-                          ctx->step_form, tile_nw_for(ctx, q.H, q.W, p.term, p.storage, p.ts),
+                          ctx->step_form, tile_nw_for(ctx, q.H, q.W, q.B, p.term, p.storage, p.ts),
                           &plan, &planned, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_evolve_batch: staging and prologue");
         if (!planned) {
@@ -367,9 +381,16 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
         return cuda_fail(ctx, e, "lse_evolve_batch: iterations");
     }
 
-    // ---- outputs and statistics
+    // ---- outputs and statistics (vector images on the band passes first
+    // take the statistics of their returned LSF)
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         const lse_problem &q = problems[i];
+        const StepArgs &a = items[i].args;
+        if (a.mb_split) {
+            e = launch_band_stats(a.bands, a.pitch, a.band_stride, items[i].phi, q.H, q.W, q.B,
+                                  a.dt, states + i, a.partials, nred, true, s);
+            if (e != cudaSuccess) break;
+        }
         e = launch_output(items[i].phi, lay[i].pitch, q.H, q.W, q.params.storage, states + i,
                           q.phi_out, q.mask_out, s);
     }

@@ -26,12 +26,14 @@ struct ClassKey {
 
 // Planes of one image in a batch arena or a server slot, as byte offsets
 // from the image's base: the data term (`bands` planes: the image bands, or
-// g), then the two LSF planes; each plane is H x pitch elements of the
-// storage type (4 or 2 bytes) and starts on 256 bytes.
+// g), then the two LSF planes, then for a vector image the D plane of its
+// band passes; each plane is H x pitch elements of the storage type (4 or 2
+// bytes) and starts on 256 bytes.
 struct ImagePlanes {
     int pitch;
     int es;                        // bytes per element
     size_t data, phi0, phi1, end;
+    size_t dplane;                 // vector images: the D plane (0: none)
 };
 ImagePlanes image_planes(const lse_problem &q);
 

@@ -7,8 +7,9 @@
 
 #include "lse_internal.h"
 
-// Key of the tile-height table: term, storage type, radius, and the bucket
-// floor(log2(tiles)) of the image's tile count at 64-row tiles.
+// Key of the tile-height table: kind (region with one band, edge term, vector
+// image), storage type, radius, and the bucket floor(log2(tiles)) of the
+// image's tile count at 64-row tiles.
 using TuneKey = std::tuple<int, int, int, int>;
 
 struct lse_ctx {
@@ -32,6 +33,8 @@ struct lse_ctx {
     size_t g_st_cap = 0;
     uint16_t *q16 = nullptr;         // data term as F16 / BF16 (16-bit storage)
     size_t q16_cap = 0;
+    float *dplane = nullptr;         // vector images: D of Eq. 17, one plane
+    size_t dplane_cap = 0;
     float *out_phi = nullptr;
     size_t out_cap = 0;
     uint8_t *out_mask = nullptr;
@@ -102,7 +105,7 @@ lse_status check_params(lse_ctx *ctx, const lse_params &p, int B);
 void fill_stats(const LseDevState &h, float elapsed_ms, lse_stats *stats);
 // Warps per CTA of the tile-form step for an image on this context: the
 // lse_autotune choice for its shape class, else the context's default.
-int tile_nw_for(const lse_ctx *ctx, int H, int W, int term, int storage, int ts);
+int tile_nw_for(const lse_ctx *ctx, int H, int W, int B, int term, int storage, int ts);
 
 template <typename T>
 lse_status ensure_t(lse_ctx *ctx, T **p, size_t *cap_elems, size_t elems,

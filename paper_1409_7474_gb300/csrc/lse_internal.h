@@ -97,6 +97,11 @@ struct StepArgs {
     int nw;                     // tile form: warps per CTA (8: 64-row tiles, 4: 32-row)
     int pdl;                    // tile form: launch as a programmatic dependent
                                 // (the grid leaves SM slots free)
+    // vector images on the tile form: the step reads the D plane of the
+    // band passes as its one data plane (data), with the coefficient
+    // st->a[0] = dt / (2 M); the bands themselves are at `bands`
+    int mb_split;
+    const float *bands;
     // test hook (0 = off): the tile form's CTAs first wait this long (ns) on
     // an mbarrier that nothing arrives at, so the bounded wait runs out
     unsigned long long stall_ns;
@@ -201,6 +206,19 @@ cudaError_t launch_prologue(const void *img, int img_pitch, size_t band_stride,
                             int W, int B, int term, float dt, int storage,
                             LseDevState *st, LsePartial *partials, int nblocks,
                             cudaStream_t s);
+// Vector images on the tile form: the statistics pass (Eq. 15) over the LSF
+// bufs[st->last_buf] (final_pass: also after an early stop) and the pass
+// that writes D (Eq. 17) into dplane and sets M and the step coefficient;
+// and both for launch index n of a batch (the pass CTAs of each image).
+cudaError_t launch_band_stats(const float *bands, int pitch, size_t band_stride,
+                              float *const *bufs, int H, int W, int B, float dt,
+                              LseDevState *st, LsePartial *partials, int nblocks,
+                              bool final_pass, cudaStream_t s);
+cudaError_t launch_band_dterm(const float *bands, int pitch, size_t band_stride, float *dplane,
+                              int H, int W, int B, float dt, LseDevState *st,
+                              LsePartial *partials, int nblocks, cudaStream_t s);
+cudaError_t launch_band_passes_batch(const BatchItem *items, const int *blk_item, long long n,
+                                     int nblocks, cudaStream_t s);
 cudaError_t launch_normaliser(const float *img, int pitch, size_t band_stride,
                               int H, int W, int B, float dt, LseDevState *st,
                               LsePartial *partials, int nblocks, cudaStream_t s);
@@ -272,12 +290,13 @@ int tile_nw_from_env();
 int tile_nw_default_for(int H, int W, int ts, int sm_count);
 // Fills the step arguments for a call and picks its kernel (`requested` is
 // LSE_FORM_AUTO, _STREAM or _GENERIC; `tile_nw` the tile form's warps per
-// CTA, 8 or 4).  Returns false when no step kernel serves the call (16-bit
+// CTA, 8 or 4; `dplane`, H x pitch floats or NULL, lets a vector image take
+// the band passes and the tile form).  Returns false when no step kernel serves the call (16-bit
 // storage outside the tile form).
 bool plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_stride,
                const void *data, float *const phi[2], LseDevState *st,
                LsePartial *partials, int sm_count, int requested, int tile_nw,
-               StepPlan *plan);
+               float *dplane, StepPlan *plan);
 // Launches iteration n (0-based) of the plan.
 cudaError_t launch_step(StepPlan &plan, int n, cudaStream_t s);
 // Sets the message lse_last_error(NULL) returns (calls without a context).

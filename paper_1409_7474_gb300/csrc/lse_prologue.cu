@@ -79,20 +79,13 @@ prologue_kernel(const void *__restrict__ img, int img_pitch, size_t band_stride,
     LseAcc acc;
     acc.clear();
     const long long n = (long long)H * W;
-    // band sums: up to 8 pixels in FP32, then into the FP64 accumulators
-    // (relative error of a partial at most 7 * 2^-24)
-    float sp[LSE_MAXB], sm[LSE_MAXB];
-    int pending = 0, npos = 0;
-    auto fold = [&]() {
-        for (int b = 0; b < B; ++b) {
-            acc.sp[b] += (double)sp[b];
-            acc.sm[b] += (double)sm[b];
-            sp[b] = 0.0f;
-            sm[b] = 0.0f;
-        }
-        pending = 0;
-    };
-    for (int b = 0; b < LSE_MAXB; ++b) sp[b] = sm[b] = 0.0f;
+    // band sums over phi >= 0 / phi < 0: compensated FP32 sums
+    // (lse_kahan_add) in registers, turned into FP64 once; `acc`, which the
+    // reduction indexes by a run-time band count, is filled at the end
+    float sp[LSE_MAXB], cp[LSE_MAXB], sm[LSE_MAXB], cm[LSE_MAXB];
+    int npos = 0;
+#pragma unroll
+    for (int b = 0; b < LSE_MAXB; ++b) sp[b] = cp[b] = sm[b] = cm[b] = 0.0f;
     for (int y = blockIdx.x; y < H; y += gridDim.x)
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         float v = phi0[(size_t)y * W + x];
@@ -105,20 +98,28 @@ prologue_kernel(const void *__restrict__ img, int img_pitch, size_t band_stride,
             if (!isfinite(gv)) acc.bits |= LSE_SBIT_NONFINITE;
             if (g_dst) g_dst[(size_t)y * pitch + x] = gv;
         } else {
-            for (int b = 0; b < B; ++b) {
-                float iv = load_as(img, b * band_stride + (size_t)y * img_pitch + x, storage);
-                if (!isfinite(iv)) acc.bits |= LSE_SBIT_NONFINITE;
-                if (pos) sp[b] += iv;
-                else sm[b] += iv;
-                if (b == 0) {
-                    acc.fmax = fmaxf(acc.fmax, iv);
-                    acc.fmin = fminf(acc.fmin, iv);
+#pragma unroll
+            for (int b = 0; b < LSE_MAXB; ++b) {
+                if (b < B) {
+                    float iv = load_as(img, b * band_stride + (size_t)y * img_pitch + x, storage);
+                    if (!isfinite(iv)) acc.bits |= LSE_SBIT_NONFINITE;
+                    lse_kahan_add(sp[b], cp[b], pos ? iv : 0.0f);
+                    lse_kahan_add(sm[b], cm[b], pos ? 0.0f : iv);
+                    if (b == 0) {
+                        acc.fmax = fmaxf(acc.fmax, iv);
+                        acc.fmin = fminf(acc.fmin, iv);
+                    }
                 }
             }
-            if (++pending == 8) fold();
         }
     }
-    if (term != LSE_TERM_EDGE) fold();
+    if (term != LSE_TERM_EDGE) {
+#pragma unroll
+        for (int b = 0; b < LSE_MAXB; ++b) {
+            acc.sp[b] = lse_kahan_value(sp[b], cp[b]);
+            acc.sm[b] = lse_kahan_value(sm[b], cm[b]);
+        }
+    }
     acc.n_plus = npos;
     const int nb = term == LSE_TERM_EDGE ? 0 : B;
     LseAcc r;
@@ -169,15 +170,45 @@ __device__ __forceinline__ void normaliser(const float *__restrict__ img, int pi
     }
     LseAcc acc;
     acc.clear();
-    for (int y = cta; y < H; y += ncta)
-    for (int x = threadIdx.x; x < W; x += blockDim.x) {
-        const float *src = img + (size_t)y * pitch + x;
-        float d = 0.0f;
+    // four columns per thread with float4 loads where the rows allow it
+    // (pitch a multiple of 4 floats, 16-byte aligned planes): more loads in
+    // flight per thread; a maximum does not depend on the order it is taken
+    const bool vec = (pitch & 3) == 0 && (band_stride & 3) == 0 &&
+                     (reinterpret_cast<uintptr_t>(img) & 15) == 0;
+    if (vec) {
+        for (int y = cta; y < H; y += ncta)
+        for (int x = 4 * threadIdx.x; x < W; x += 4 * blockDim.x) {
+            const float *src = img + (size_t)y * pitch + x;
+            float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-        for (int b = 0; b < LSE_MAXB; ++b)
-            if (b < B) d = fmaf(af[b], __ldg(src + b * band_stride) - m[b], d);
-        acc.fmax = fmaxf(acc.fmax, d);
-        acc.fmin = fminf(acc.fmin, d);
+            for (int b = 0; b < LSE_MAXB; ++b) {
+                if (b < B) {
+                    const float4 e = __ldg(reinterpret_cast<const float4 *>(src + b * band_stride));
+                    d[0] = fmaf(af[b], e.x - m[b], d[0]);
+                    d[1] = fmaf(af[b], e.y - m[b], d[1]);
+                    d[2] = fmaf(af[b], e.z - m[b], d[2]);
+                    d[3] = fmaf(af[b], e.w - m[b], d[3]);
+                }
+            }
+            // columns past W are row padding
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (x + j < W) {
+                    acc.fmax = fmaxf(acc.fmax, d[j]);
+                    acc.fmin = fminf(acc.fmin, d[j]);
+                }
+        }
+    } else {
+        for (int y = cta; y < H; y += ncta)
+        for (int x = threadIdx.x; x < W; x += blockDim.x) {
+            const float *src = img + (size_t)y * pitch + x;
+            float d = 0.0f;
+#pragma unroll
+            for (int b = 0; b < LSE_MAXB; ++b)
+                if (b < B) d = fmaf(af[b], __ldg(src + b * band_stride) - m[b], d);
+            acc.fmax = fmaxf(acc.fmax, d);
+            acc.fmin = fminf(acc.fmin, d);
+        }
     }
     LseAcc r;
     lse_cta_reduce(acc, 0, &r);

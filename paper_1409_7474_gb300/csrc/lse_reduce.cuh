@@ -32,6 +32,101 @@ struct LseAcc {
     }
 };
 
+// Compensated summation (Kahan, 1965): s is the running FP32 sum and c the
+// rounding error of its last addition, negated; the sum is s - c, within
+// about 2 * 2^-24 of sum |x| however many terms are added.  The explicit
+// round-to-nearest intrinsics keep the steps from being contracted or
+// reassociated.  Per-pixel sums use it in place of FP64 additions, which
+// this part issues at a small fraction of the FP32 rate.
+__device__ __forceinline__ void lse_kahan_add(float &s, float &c, float x)
+{
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+__device__ __forceinline__ double lse_kahan_value(float s, float c)
+{
+    return (double)s - (double)c;
+}
+
+// Knuth's TwoSum: s = fl(a + b) and e with s + e == a + b exactly.
+__device__ __forceinline__ float lse_two_sum(float a, float b, float &e)
+{
+    const float s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+    return s;
+}
+
+// Float-float addition (h, l) += (bh, bl): the unevaluated sum h + l carries
+// about 48 significant bits, and the error of one addition is a few units of
+// 2^-48 of |h| + |bh|.  The result does not depend on the operand order.
+__device__ __forceinline__ void lse_ff_add(float &h, float &l, float bh, float bl)
+{
+    float e;
+    const float s = lse_two_sum(h, bh, e);
+    e = __fadd_rn(e, __fadd_rn(l, bl));
+    h = __fadd_rn(s, e);                        // |s| >= |e|: Fast2Sum
+    l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+// Reduces NV per-thread compensated sums (value s[k] - c[k], lse_kahan_add)
+// and a count over the CTA in float-float arithmetic: warp shuffles in a
+// fixed pattern, then warps in index order; FP64 only for the final values.
+// out[k] and *count are valid in thread 0 after return.  NV <= 32.
+template <int NV, int MAXW = 32>
+__device__ __forceinline__ void lse_cta_reduce_ff(const float (&s)[NV], const float (&c)[NV],
+                                                  long long n, double (&out)[NV],
+                                                  long long *count)
+{
+    __shared__ float s_h[MAXW][NV], s_l[MAXW][NV];
+    __shared__ long long s_n[MAXW];
+    __shared__ double s_out[NV];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    float h[NV], l[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) h[k] = lse_two_sum(s[k], -c[k], l[k]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const float bh = __shfl_xor_sync(0xffffffffu, h[k], o);
+            const float bl = __shfl_xor_sync(0xffffffffu, l[k], o);
+            lse_ff_add(h[k], l[k], bh, bl);
+        }
+    }
+    n = warp_sum_ll(n);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            s_h[warp][k] = h[k];
+            s_l[warp][k] = l[k];
+        }
+        s_n[warp] = n;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        const int k = threadIdx.x;
+        float th = 0.0f, tl = 0.0f;
+        for (int w = 0; w < nwarps; ++w) lse_ff_add(th, tl, s_h[w][k], s_l[w][k]);
+        s_out[k] = (double)th + (double)tl;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < nwarps; ++w) t += s_n[w];
+        *count = t;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = s_out[k];
+    }
+    __syncthreads();
+}
+
 // Reduces `acc` over the CTA (blockDim.x a multiple of 32, at most 32 MAXW)
 // into `out` (visible to thread 0 after return).  `nb` bands are summed.
 // MAXW sizes the static shared arrays: a kernel of few warps passes its own
@@ -213,7 +308,13 @@ __device__ __forceinline__ void lse_step_finalize(const StepArgs &a,
     st->last_flips = t.flips;
     st->iterations_run = a.iter + 1;
     st->last_buf = a.out_buf;
-    if (a.term == LSE_TERM_REGION) {
+    if (a.term == LSE_TERM_REGION && a.mb_split) {
+        // vector image on the tile form: the next statistics pass makes the
+        // coefficients of the next step
+        if (st->zero_force) st->status_bits |= LSE_SBIT_DEGENERATE;
+        st->norm_used = st->zero_force ? 0.0 : st->norm;
+        st->area_plus = t.n_plus;
+    } else if (a.term == LSE_TERM_REGION) {
         if (st->zero_force) st->status_bits |= LSE_SBIT_DEGENERATE;
         st->norm_used = st->zero_force ? 0.0 : st->norm;
         lse_region_coeffs(st, t, a.B, a.dt);

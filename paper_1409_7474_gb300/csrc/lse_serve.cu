@@ -155,7 +155,7 @@ lse_status admit(lse_server *sv, Request &r, int slot, cudaStream_t s)
     cudaError_t e = cudaMemsetAsync(st, 0, sizeof(LseDevState), s);
     if (e == cudaSuccess)
         e = stage_problem(q, base, L, st, parts, ctx->sm_count * 4, ctx->sm_count, LSE_FORM_AUTO,
-                          tile_nw_for(ctx, q.H, q.W, p.term, p.storage, p.ts), &plan, &planned,
+                          tile_nw_for(ctx, q.H, q.W, q.B, p.term, p.storage, p.ts), &plan, &planned,
                           s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_server: admit");
     if (!planned) {
@@ -360,16 +360,26 @@ lse_status lse_server_advance(lse_server *sv, int ticks, int *running, void *str
         const bool finished = h.done || h.iterations_run >= req.q.params.iterations ||
                               (h.status_bits & LSE_SBIT_ABORT);
         if (!finished) continue;
-        e = launch_output(sv->items[slot].phi, req.pitch, req.q.H, req.q.W,
-                          req.q.params.storage, sv->d_states + slot, req.q.phi_out,
-                          req.q.mask_out, s);
-        fill_stats(h, -1.0f, &req.stats);
+        const StepArgs &a = sv->items[slot].args;
+        if (a.mb_split)
+            e = launch_band_stats(a.bands, a.pitch, a.band_stride, sv->items[slot].phi, req.q.H,
+                                  req.q.W, req.q.B, a.dt, sv->d_states + slot, a.partials,
+                                  ctx->sm_count * 4, true, s);
+        if (e == cudaSuccess)
+            e = launch_output(sv->items[slot].phi, req.pitch, req.q.H, req.q.W,
+                              req.q.params.storage, sv->d_states + slot, req.q.phi_out,
+                              req.q.mask_out, s);
         retired.push_back(slot);
     }
+    // the states again: the final statistics passes of vector images ran
+    // after the copy above
+    if (e == cudaSuccess && !retired.empty())
+        e = cudaMemcpyAsync(hs, sv->d_states, sbytes, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_server: retire");
     for (int slot : retired) {
         Request &req = sv->reqs[sv->slot_req[slot]];
+        fill_stats(hs[slot], -1.0f, &req.stats);
         req.state = REQ_DONE;
         sv->alloc.give(req.off, req.bytes);
         sv->slot_req[slot] = 0;

@@ -166,7 +166,7 @@ extern "C" lse_status lse_evolve_static(const float *image, int H, int W, int B,
     (void)plan_step(H, W, B, p, pitch, band_stride, data, phi, st, partials, sm_count,
               step_form_from_env(),
               tile_nw_from_env() ? tile_nw_from_env() : tile_nw_default_for(H, W, p.ts, sm_count),
-              &plan);
+              nullptr, &plan);
     for (int n = 0; n < p.iterations; ++n) {
         if (region && B > 1) {
             e = launch_normaliser(data, pitch, band_stride, H, W, B, p.dt, st, partials,

@@ -83,7 +83,7 @@ int step_form_from_env()
 bool plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_stride,
                const void *data, float *const phi[2], LseDevState *st,
                LsePartial *partials, int sm_count, int requested, int tile_nw,
-               StepPlan *plan)
+               float *dplane, StepPlan *plan)
 {
     StepArgs &a = plan->args;
     memset(&a, 0, sizeof(a));
@@ -125,6 +125,20 @@ bool plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_
         requested = LSE_FORM_GENERIC;
     }
     const int urows = 8 * tile_nw;      // u rows per tile; phi adds one halo row a side
+    // vector images: the band passes write D into dplane and the tile form
+    // steps on that one plane (FP32, 2-4 bands)
+    if (requested == LSE_FORM_AUTO && dplane && p.term == LSE_TERM_REGION && a.B > 1 &&
+        a.B <= 4 && sto == LSE_F32 &&
+        plan_step_tile(H, W, 1, LSE_TERM_EDGE, a.rad, tile_nw, sm_count, &a, &plan->nblocks) &&
+        encode_box(&plan->phi_maps[0], phi[0], sto, W, H, pitch, 0, 1, 136, urows + 2) &&
+        encode_box(&plan->phi_maps[1], phi[1], sto, W, H, pitch, 0, 1, 136, urows + 2) &&
+        encode_box(&plan->data_map, dplane, sto, W, H, pitch, 0, 1, data_box_w, urows)) {
+        a.mb_split = 1;
+        a.bands = static_cast<const float *>(data);
+        a.data = dplane;
+        plan->form = LSE_FORM_TILE;
+        return true;
+    }
     if (requested == LSE_FORM_AUTO &&
         plan_step_tile(H, W, a.B, p.term, a.rad, tile_nw, sm_count, &a, &plan->nblocks) &&
         encode_box(&plan->phi_maps[0], phi[0], sto, W, H, pitch, 0, 1, 136, urows + 2) &&

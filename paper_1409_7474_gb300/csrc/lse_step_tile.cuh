@@ -310,7 +310,9 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
     float tp[RAD + 1];
 #pragma unroll
     for (int k = 0; k <= RAD; ++k) tp[k] = a.taps[k];
-    const float coef = EDGE ? a.half_dt : st->a[0];
+    // edge term: dt / 2 (t = dt g / 2); the D plane of a vector image: the
+    // coefficient its band pass left, dt / (2 M)
+    const float coef = EDGE ? (a.mb_split ? st->a[0] : a.half_dt) : st->a[0];
     const float mid = EDGE ? 0.0f : st->m[0];
     const f2 coef2 = f2_pack(coef, coef), mid2 = f2_pack(mid, mid);
     const float sqrt8 = sqrtf(8.0f);
@@ -337,7 +339,7 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
 
     long long cnt2 = 0;
     int nflip = 0;
-    double dsw = 0.0, dsa = 0.0;
+    float ksw = 0.0f, csw = 0.0f, ksa = 0.0f, csa = 0.0f;   // compensated lane sums
     const bool lane_out = lane >= HL && lane < 32 - HL;
     const int eidx = lane == 0 ? 3 : 132;        // phi column beyond the warp's edge
     const T *bl = buf + 4 + 4 * lane;            // this lane's 4 columns of a phi row
@@ -622,8 +624,8 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
             else
                 vrows(std::false_type{});
             if (!EDGE && lane_out) {
-                dsw += (double)fsw;
-                dsa += (double)fsa;
+                lse_kahan_add(ksw, csw, fsw);
+                lse_kahan_add(ksa, csa, fsa);
             }
             int cv = 0;
 #pragma unroll
@@ -645,6 +647,7 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
 
     LseAcc acc;
     acc.clear();
+    const double dsw = lse_kahan_value(ksw, csw), dsa = lse_kahan_value(ksa, csa);
     acc.sp[0] = 0.5 * (dsa + dsw);
     acc.sm[0] = 0.5 * (dsa - dsw);
     acc.n_plus = cnt2 / 2;

@@ -190,7 +190,9 @@ cudaError_t launch_step_tile(const StepArgs &a, const CUtensorMap &phi_map,
                              const CUtensorMap &data_map, int nblocks, cudaStream_t s)
 {
     int si, ti, ni;
-    if (!tile_index(a.storage, a.term, a.nw, &si, &ti, &ni)) return cudaErrorNotSupported;
+    // a vector image steps on its D plane like the edge term on g
+    if (!tile_index(a.storage, a.mb_split ? LSE_TERM_EDGE : a.term, a.nw, &si, &ti, &ni))
+        return cudaErrorNotSupported;
     return kTile[si][ti][ni](a, phi_map, data_map, nblocks, s);
 }
 

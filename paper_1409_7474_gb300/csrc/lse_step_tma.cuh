@@ -306,16 +306,17 @@ __device__ __forceinline__ void tma_step(const StepArgs &a, const CUtensorMap *p
     };
 
     // per-lane sums: sum of w = sign(v) over output pixels (fsw_cnt), and per
-    // band sum d and sum d w; FP32 within a ring period, FP64 across periods
+    // band sum d and sum d w; FP32 within a ring period, compensated FP32
+    // (lse_kahan_add) across periods, FP64 from the lane sums on
     long long cnt2 = 0;      // sum over items of (sum w + valid pixels)
     int nflip = 0;
     float fsw_cnt = 0.0f;
     float fsw[NB], fsa[NB];
-    double dsw[NB], dsa[NB];
+    float ksw[NB], csw[NB], ksa[NB], csa[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         fsw[b] = fsa[b] = 0.0f;
-        dsw[b] = dsa[b] = 0.0;
+        ksw[b] = csw[b] = ksa[b] = csa[b] = 0.0f;
     }
     const bool lane_out = lane >= HL && lane < 32 - HL;
 
@@ -639,8 +640,8 @@ __device__ __forceinline__ void tma_step(const StepArgs &a, const CUtensorMap *p
         auto fold = [&]() {
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                dsw[b] += (double)fsw[b];
-                dsa[b] += (double)fsa[b];
+                lse_kahan_add(ksw[b], csw[b], fsw[b]);
+                lse_kahan_add(ksa[b], csa[b], fsa[b]);
                 fsw[b] = fsa[b] = 0.0f;
             }
         };
@@ -678,8 +679,10 @@ __device__ __forceinline__ void tma_step(const StepArgs &a, const CUtensorMap *p
     acc.clear();
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        acc.sp[b] = 0.5 * (dsa[b] + dsw[b]);
-        acc.sm[b] = 0.5 * (dsa[b] - dsw[b]);
+        const double dsw = lse_kahan_value(ksw[b], csw[b]);
+        const double dsa = lse_kahan_value(ksa[b], csa[b]);
+        acc.sp[b] = 0.5 * (dsa + dsw);
+        acc.sm[b] = 0.5 * (dsa - dsw);
     }
     acc.n_plus = cnt2 / 2;
     acc.flips = nflip;

@@ -27,18 +27,22 @@ using namespace lse_detail;
 
 namespace {
 
-// Shape class of an image for the tile-height table, or false when the
-// tile form does not serve it.
+// Shape class of an image for the tile-height table (kind: region with one
+// band, edge term, or a vector image on its D plane), or false when the tile
+// form does not serve it.
 bool tune_key(int H, int W, int B, int term, int storage, int ts, TuneKey *key)
 {
     const int rad = (ts - 1) / 2;
-    if (rad < 1 || rad > 7 || (term == LSE_TERM_REGION && B != 1)) return false;
+    if (rad < 1 || rad > 7) return false;
+    // vector images (2-4 bands, FP32) step on their D plane: a class of their own
+    if (term == LSE_TERM_REGION && B > 1 && (B > 4 || storage != LSE_F32)) return false;
+    const int kind = term == LSE_TERM_EDGE ? 1 : (B > 1 ? 2 : 0);
     const int useful = 128 - 8 * ((rad + 3) / 4);
     const long long tiles =
         (long long)((W + useful - 1) / useful) * ((H + 64 - 2 * rad - 1) / (64 - 2 * rad));
     int bucket = 0;
     while ((2LL << bucket) <= tiles) ++bucket;
-    *key = TuneKey{term, storage, rad, bucket};
+    *key = TuneKey{kind, storage, rad, bucket};
     return true;
 }
 
@@ -67,10 +71,10 @@ int tile_nw_default_for(int H, int W, int ts, int sm_count)
     return tiles < sm_count ? 4 : 8;
 }
 
-int tile_nw_for(const lse_ctx *ctx, int H, int W, int term, int storage, int ts)
+int tile_nw_for(const lse_ctx *ctx, int H, int W, int B, int term, int storage, int ts)
 {
     TuneKey key;
-    if (tune_key(H, W, 1, term, storage, ts, &key)) {
+    if (tune_key(H, W, B, term, storage, ts, &key)) {
         auto it = ctx->tile_tune.find(key);
         if (it != ctx->tile_tune.end()) return it->second;
     }
@@ -144,7 +148,7 @@ extern "C" lse_status lse_autotune(lse_ctx *ctx, int n, const lse_problem *probl
         if (!ctx->tile_tune.count(g.first)) {
             const lse_problem &q = problems[g.second[0]];
             ctx->tile_tune[g.first] =
-                tile_nw_for(ctx, q.H, q.W, q.params.term, q.params.storage, q.params.ts);
+                tile_nw_for(ctx, q.H, q.W, q.B, q.params.term, q.params.storage, q.params.ts);
         }
     // larger classes first: they move the total the most
     std::vector<std::pair<double, TuneKey>> order;
