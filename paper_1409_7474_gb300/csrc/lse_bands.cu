@@ -99,7 +99,7 @@ __device__ __forceinline__ void band_stats(const float *__restrict__ bands, int 
     }
     LseAcc r;
     r.clear();
-    lse_cta_reduce_ff<2 * NBX>(ks, kc, (long long)npos, tot, &r.n_plus);
+    lse_cta_reduce_ff<2 * NBX>(ks, kc, (long long)npos, 0ll, tot, &r.n_plus, &r.flips);
 #pragma unroll
     for (int b = 0; b < NBX; ++b) {
         r.sp[b] = tot[b];

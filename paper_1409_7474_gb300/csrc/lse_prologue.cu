@@ -31,6 +31,40 @@ __device__ __forceinline__ void store_as(void *p, size_t i, float v, int storage
     else static_cast<float *>(p)[i] = v;
 }
 
+__device__ __forceinline__ bool aligned16(const void *p)
+{
+    return (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
+// v[0..3] = plane[i .. i + 3] (the first nj; the rest 0), with one 16-byte
+// load when `vec` (FP32 plane, i a multiple of 4 in a 16-byte aligned row)
+__device__ __forceinline__ void load4(const void *p, size_t i, int nj, int storage, bool vec,
+                                      float (&v)[4])
+{
+    if (vec && nj == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(static_cast<const float *>(p) + i));
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = j < nj ? load_as(p, i + j, storage) : 0.0f;
+}
+
+__device__ __forceinline__ void store4(void *p, size_t i, int nj, int storage, bool vec,
+                                       const float (&v)[4])
+{
+    if (vec && nj == 4) {
+        *reinterpret_cast<float4 *>(static_cast<float *>(p) + i) = make_float4(v[0], v[1], v[2], v[3]);
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (j < nj) store_as(p, i + j, v[j], storage);
+}
+
 // The kernels below walk the image by rows: rows stride over the CTAs and
 // each row's columns over the threads, so no pixel index is divided.
 
@@ -86,33 +120,69 @@ prologue_kernel(const void *__restrict__ img, int img_pitch, size_t band_stride,
     int npos = 0;
 #pragma unroll
     for (int b = 0; b < LSE_MAXB; ++b) sp[b] = cp[b] = sm[b] = cm[b] = 0.0f;
+    // Each thread takes groups of 4 consecutive columns, read with one
+    // 16-byte access where the plane allows it (FP32, 16-byte aligned rows)
+    // and value by value otherwise: the arithmetic, and so every bit of the
+    // result, is the same either way.
+    unsigned int bits = 0;                 // per-pixel state in registers
+    float fmx = -INFINITY, fmn = INFINITY;
+    const bool f32 = storage == LSE_F32;
+    const bool v_phi0 = (W & 3) == 0 && aligned16(phi0);
+    const bool v_dst = f32 && (pitch & 3) == 0 && aligned16(phi_dst) &&
+                       (g_dst == nullptr || aligned16(g_dst));
+    const bool v_img = f32 && img != nullptr && (img_pitch & 3) == 0 &&
+                       (band_stride & 3) == 0 && aligned16(img);
+    const bool v_g = f32 && g != nullptr && (g_pitch & 3) == 0 && aligned16(g);
     for (int y = blockIdx.x; y < H; y += gridDim.x)
-    for (int x = threadIdx.x; x < W; x += blockDim.x) {
-        float v = phi0[(size_t)y * W + x];
-        if (!isfinite(v)) acc.bits |= LSE_SBIT_NONFINITE;
-        store_as(phi_dst, (size_t)y * pitch + x, v, storage);
-        const bool pos = v >= 0.0f;
-        npos += pos;
+    for (int x = 4 * threadIdx.x; x < W; x += 4 * blockDim.x) {
+        const int nj = W - x < 4 ? W - x : 4;
+        float v[4];
+        load4(phi0, (size_t)y * W + x, nj, LSE_F32, v_phi0, v);
+        store4(phi_dst, (size_t)y * pitch + x, nj, storage, v_dst, v);
+        bool pos[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j < nj && !isfinite(v[j])) bits |= LSE_SBIT_NONFINITE;
+            pos[j] = j < nj && v[j] >= 0.0f;
+            npos += pos[j];
+        }
         if (term == LSE_TERM_EDGE) {
-            float gv = load_as(g, (size_t)y * g_pitch + x, storage);
-            if (!isfinite(gv)) acc.bits |= LSE_SBIT_NONFINITE;
-            if (g_dst) g_dst[(size_t)y * pitch + x] = gv;
+            float gv[4];
+            load4(g, (size_t)y * g_pitch + x, nj, storage, v_g, gv);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j < nj && !isfinite(gv[j])) bits |= LSE_SBIT_NONFINITE;
+            if (g_dst) store4(g_dst, (size_t)y * pitch + x, nj, LSE_F32, v_dst, gv);
         } else {
 #pragma unroll
             for (int b = 0; b < LSE_MAXB; ++b) {
                 if (b < B) {
-                    float iv = load_as(img, b * band_stride + (size_t)y * img_pitch + x, storage);
-                    if (!isfinite(iv)) acc.bits |= LSE_SBIT_NONFINITE;
-                    lse_kahan_add(sp[b], cp[b], pos ? iv : 0.0f);
-                    lse_kahan_add(sm[b], cm[b], pos ? 0.0f : iv);
-                    if (b == 0) {
-                        acc.fmax = fmaxf(acc.fmax, iv);
-                        acc.fmin = fminf(acc.fmin, iv);
+                    float iv[4];
+                    load4(img, b * band_stride + (size_t)y * img_pitch + x, nj, storage, v_img,
+                          iv);
+                    // 4-pixel partials (past the row: zero), then the
+                    // compensated sums
+                    float pp = 0.0f, pm = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float e = j < nj ? iv[j] : 0.0f;
+                        if (j < nj && !isfinite(e)) bits |= LSE_SBIT_NONFINITE;
+                        pp = __fadd_rn(pp, pos[j] ? e : 0.0f);
+                        pm = __fadd_rn(pm, pos[j] ? 0.0f : e);
+                        if (b == 0 && j < nj) {
+                            fmx = fmaxf(fmx, e);
+                            fmn = fminf(fmn, e);
+                        }
                     }
+                    lse_kahan_add(sp[b], cp[b], pp);
+                    lse_kahan_add(sm[b], cm[b], pm);
                 }
             }
         }
     }
+    acc.bits = bits;
+    acc.fmax = fmx;
+    acc.fmin = fmn;
     if (term != LSE_TERM_EDGE) {
 #pragma unroll
         for (int b = 0; b < LSE_MAXB; ++b) {

@@ -74,16 +74,17 @@ __device__ __forceinline__ void lse_ff_add(float &h, float &l, float bh, float b
 }
 
 // Reduces NV per-thread compensated sums (value s[k] - c[k], lse_kahan_add)
-// and a count over the CTA in float-float arithmetic: warp shuffles in a
+// and two counts over the CTA in float-float arithmetic: warp shuffles in a
 // fixed pattern, then warps in index order; FP64 only for the final values.
-// out[k] and *count are valid in thread 0 after return.  NV <= 32.
+// out[k], *count0 and *count1 are valid in thread 0 after return.  NV <= 32.
 template <int NV, int MAXW = 32>
 __device__ __forceinline__ void lse_cta_reduce_ff(const float (&s)[NV], const float (&c)[NV],
-                                                  long long n, double (&out)[NV],
-                                                  long long *count)
+                                                  long long n0, long long n1,
+                                                  double (&out)[NV], long long *count0,
+                                                  long long *count1)
 {
     __shared__ float s_h[MAXW][NV], s_l[MAXW][NV];
-    __shared__ long long s_n[MAXW];
+    __shared__ long long s_n[MAXW][2];
     __shared__ double s_out[NV];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -100,14 +101,16 @@ __device__ __forceinline__ void lse_cta_reduce_ff(const float (&s)[NV], const fl
             lse_ff_add(h[k], l[k], bh, bl);
         }
     }
-    n = warp_sum_ll(n);
+    n0 = warp_sum_ll(n0);
+    n1 = warp_sum_ll(n1);
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             s_h[warp][k] = h[k];
             s_l[warp][k] = l[k];
         }
-        s_n[warp] = n;
+        s_n[warp][0] = n0;
+        s_n[warp][1] = n1;
     }
     __syncthreads();
     if (threadIdx.x < NV) {
@@ -118,9 +121,13 @@ __device__ __forceinline__ void lse_cta_reduce_ff(const float (&s)[NV], const fl
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        long long t = 0;
-        for (int w = 0; w < nwarps; ++w) t += s_n[w];
-        *count = t;
+        long long t0 = 0, t1 = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            t0 += s_n[w][0];
+            t1 += s_n[w][1];
+        }
+        *count0 = t0;
+        *count1 = t1;
 #pragma unroll
         for (int k = 0; k < NV; ++k) out[k] = s_out[k];
     }

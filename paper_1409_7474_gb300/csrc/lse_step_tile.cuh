@@ -337,6 +337,9 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
     uint32_t par = 0;
     bool failed = false;
 
+    // 2 |{v >= 0}| over this lane's pixels: sum w + valid pixels.  fcnt is
+    // an exact small integer (at most 4 x 64 in magnitude), converted in 32
+    // bits: a float to 64-bit conversion issues on the FP64 pipe
     long long cnt2 = 0;
     int nflip = 0;
     float ksw = 0.0f, csw = 0.0f, ksa = 0.0f, csa = 0.0f;   // compensated lane sums
@@ -630,7 +633,7 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
             int cv = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) cv += okf[j] != 0.0f ? 1 : 0;
-            cnt2 += (long long)fcnt + (long long)cv * rv;
+            cnt2 += __float2int_rn(fcnt) + cv * rv;          // int, widened
         }
         __syncthreads();
         const int tn = t + ncta;
@@ -653,6 +656,8 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
     acc.n_plus = cnt2 / 2;
     acc.flips = nflip;
     const int nb = EDGE ? 0 : 1;
+    // FP64 shuffles here cost nothing measurable: the persistent CTAs finish
+    // at staggered times, and a float-float version was 0.4 % slower
     LseAcc r;
     lse_cta_reduce<NW>(acc, nb, &r);
     if (!lse_publish_and_ticket_at(r, nb, a.partials, st, cta, ncta)) return;
