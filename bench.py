@@ -19,6 +19,8 @@ Reported (one JSON line on rank 0):
   cpu_baseline the FP64 oracle on the host cores, on crops of the same scene;
   storage_variants  the same workload with BF16 and F16 storage of the data
                term and the LSF (FP32 arithmetic, 6 B/px per region step);
+  multiband    the 4-band 2048x2048 scene: vector region term and edge term,
+               500 iterations each, CUDA events of lse_evolve
   batch        256 uneven images (sides 128-1024, caps 100-600, early stop)
                through lse_evolve_batch with and without a CUDA graph, and
                one lse_evolve call per image in sequence, on a context whose
@@ -79,6 +81,11 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-rates", default="50,2000",
                     help="offered request rates (per second), comma-separated")
+    ap.add_argument("--no-multiband", action="store_true",
+                    help="skip the 4-band 2048x2048 measurement")
+    ap.add_argument("--multiband-iters", type=int, default=500)
+    ap.add_argument("--only-multiband", action="store_true",
+                    help="run and print only the 4-band measurement (profiling)")
     return ap.parse_args()
 
 
@@ -442,6 +449,43 @@ def step_form() -> str:
                                                         "tile")
 
 
+def multiband_measurement(torch, lse, dev, iters: int, steps: int, peak: float):
+    """The 4-band 2048x2048 scene (B, G, R, NIR, uint16 normalised to FP32):
+    the vector region term (Eq. 17) and, separately, the edge term on its
+    precomputed g, `iters` iterations each through lse_evolve, timed with the
+    library's CUDA events.  Bytes per pixel-iteration of the region term as
+    the method needs them: the 4 bands, phi in and phi out (24)."""
+    from paper_1409_7474_gb300 import scenes
+    H = W = 2048
+    sc = scenes.multiband_scene(H, W, 4, seed=7)
+    x = (torch.from_numpy(sc["image"].astype(np.int32)).to(dev).float() / 65535.0).contiguous()
+    phi_r = torch.from_numpy(scenes.circle_phi(H, W, radius=512)).to(dev)
+    y0, x0, y1, x1 = sc["runway_box"]
+    phi_e = torch.from_numpy(scenes.box_phi(H, W, [(y0 - 20, x0 - 20, y1 + 20, x1 + 20)])).to(dev)
+    out = {}
+    with lse.Context(dev.index, max_pixels=H * W, max_bands=4) as c:
+        g = c.precompute_edge(x, 1.0, 9, 255.0)
+        for name, img, phi, term in (("region", x, phi_r, "region"), ("edge", None, phi_e, "edge")):
+            kw = dict(g=g) if term == "edge" else {}
+            c.evolve(img, phi, term, iterations=iters, **kw)          # warm-up
+            ms = []
+            for _ in range(max(1, steps)):
+                _, _, st = c.evolve(img, phi, term, iterations=iters, **kw)
+                ms.append(st["elapsed_ms"])
+            best = statistics.median(ms)
+            out[name] = {"us_per_iter": best / iters * 1e3,
+                         "value": H * W * iters / (best / 1e3) / 1e6,
+                         "status": st["status"], "iterations_run": st["iterations_run"]}
+        torch.cuda.synchronize()
+    alg = 24 * H * W
+    out["region"]["bytes_per_iter"] = alg
+    out["region"]["frac"] = alg / (out["region"]["us_per_iter"] / 1e6) / 1e9 / peak
+    out["workload"] = (f"2048x2048 4-band uint16 scene normalised to FP32; vector region term "
+                       f"and edge term, {iters} iterations each, dt=15 sigma=1 TS=9")
+    out["unit"] = UNIT
+    return out
+
+
 def kernel_profile(size: int, form: str):
     """DRAM traffic per launch of the region step kernel from a committed ncu
     summary, if it was taken on the current kernel source."""
@@ -474,6 +518,20 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    if args.only_multiband:
+        if rank == 0:
+            mb = multiband_measurement(torch, lse, dev, args.multiband_iters, args.steps, peak)
+            print(json.dumps({"impl": "gb300", "multiband": mb}))
+        return 0
 
     size, iters = args.size, args.iters
     img, phi_r, phi_e = scene_inputs(size)
@@ -522,14 +580,6 @@ def main():
     st_r, st_e = ctx_r.stats(), ctx_e.stats()
     value = world * px_iters_per_step * args.steps / (ms / 1e3) / 1e6
 
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    peak = peaks.get("hbm_gbs")
-    peak_src = "measured" if peak else "fallback"
-    peak = peak or 6800.0
     step_kernel_ms = statistics.mean(step_ms_r) / iters
     alg_bytes = BYTES_PER_PX_ITER * npx
     achieved = alg_bytes / (step_kernel_ms / 1e3) / 1e9
@@ -637,6 +687,11 @@ def main():
                 "edge_step_frac": vbytes / (statistics.mean(v_ms_e) / iters / 1e3) / 1e9 / peak,
                 "status": [ctx_r.stats()["status"], ctx_e.stats()["status"]]}
 
+    multiband = None
+    if not args.no_multiband and world == 1:
+        multiband = multiband_measurement(torch, lse, dev, args.multiband_iters, args.steps,
+                                          peak)
+
     batch = None
     if not args.no_batch:
         batch = batch_measurement(torch, lse, dev, args.batch_images)
@@ -663,7 +718,8 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks.summary(), "gpu_launches": launches,
-                "storage_variants": variants, "batch": batch, "serve": serve,
+                "storage_variants": variants, "multiband": multiband, "batch": batch,
+                "serve": serve,
                 "impl": "gb300",
                 "stats": {"region": {k: st_r[k] for k in ("iterations_run", "status",
                                                           "last_flips", "area_plus")},

@@ -543,7 +543,7 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
             // first ones), then D and its maximum
             if (n > 0)
                 e = launch_band_stats(data, pitch, band_stride, ctx->phi, H, W, B, p.dt, ctx->st,
-                                      ctx->partials, nred, false, s);
+                                      ctx->partials, nred, s);
             if (e == cudaSuccess)
                 e = launch_band_dterm(data, pitch, band_stride, dplane, H, W, B, p.dt, ctx->st,
                                       ctx->partials, nred, s);
@@ -562,7 +562,7 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
     if (bands_pass) {
         // the statistics lse_stats reports: those of the returned LSF
         e = launch_band_stats(data, pitch, band_stride, ctx->phi, H, W, B, p.dt, ctx->st,
-                              ctx->partials, nred, true, s);
+                              ctx->partials, nred, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "band statistics");
     }
     e = launch_output(ctx->phi, pitch, H, W, sto, ctx->st, out_phi, out_mask, s);

@@ -1,102 +1,143 @@
 // lse_bands.cu -- the region term for vector images (2-4 bands) around the
 // one-plane tile-form step.  Each iteration runs
-//   stats  c+_b and c-_b (Eq. 15): per-band sums over phi >= 0 / phi < 0 of
-//          the current LSF and the count, then (last CTA) the means, alpha_b,
-//          mid_b and the degenerate rule;
+//   stats  c+_b and c-_b (Eq. 15) of the LSF the last step wrote: the
+//          per-band sums over phi >= 0 / phi < 0, updated from the pixels
+//          that step changed in sign, and the count; then (last CTA) the
+//          means, alpha_b, mid_b and the degenerate rule;
 //   dterm  D(x) = sum_b alpha_b (I_b(x) - mid_b), the numerator of Eq. 17,
 //          written as one plane, and its maximum M = max |D| (last CTA: the
 //          step coefficient dt / (2 M));
 //   step   the tile-form kernel on the D plane, t = dt D / (2 M) (Eq. 18),
 //          as for the edge term's one plane g.
-// The bands are read twice per iteration, the rest once, in passes that
-// stream rows; at the sizes of the multi-band workloads the bands and both
-// LSF planes stay in L2 between them.
+// The bands are read in full once per iteration (dterm); stats reads the two
+// LSF planes and the band values of the changed pixels.
 #include "lse_reduce.cuh"
 
 namespace {
 
 constexpr int kThreads = 256;
 
-// Sums of the bands over phi >= 0 and phi < 0 and the count, for CTA `cta`
-// of `ncta`; rows stride over the CTAs, columns over the threads.  Each
-// thread adds 4-pixel FP32 partials (error at most 3 * 2^-24 of their
-// magnitude) into compensated FP32 sums, then the CTAs' sums meet in FP64.  phi is bufs[st->last_buf], the LSF the next step reads.
-// final_pass: run even after an early stop (statistics of the returned LSF).
+// Error-free sum (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
+{
+    const float s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+    return s;
+}
+
+// Statistics of the LSF the last step wrote (Eq. 15), for CTA `cta` of
+// `ncta`; rows stride over the CTAs, columns over the threads (groups of 4).
+//
+// Update form (one step since the last statistics): the band sums over
+// phi >= 0 and phi < 0 change only at pixels whose sign the step changed,
+// so each thread sums +I_b (now >= 0) or -I_b (now < 0) over those pixels
+// in float-float (TwoSum, error about 2^-44 of the sum of magnitudes) and
+// the last CTA adds the total to the running FP64 sums in the state record.
+// Only the two LSF planes are read in full; near convergence few pixels
+// change sign.  The count |{phi >= 0}| is taken directly.
+// Full form (any other case): the sums themselves, as compensated FP32
+// sums of 4-pixel partials.
+// No step since the last statistics: nothing to do, so the pass may run
+// again after a stopped evolution without counting a change twice.
 __device__ __forceinline__ void band_stats(const float *__restrict__ bands, int pitch,
-                                           size_t band_stride, const float *const *bufs,
-                                           int H, int W, int B, float dt, LseDevState *st,
-                                           LsePartial *partials, int cta, int ncta,
-                                           bool final_pass)
+                                           size_t band_stride, const float *buf0,
+                                           const float *buf1, int H, int W, int B, float dt,
+                                           LseDevState *st, LsePartial *partials, int cta,
+                                           int ncta)
 {
     if (st->status_bits & LSE_SBIT_ABORT) return;
-    if (st->done && !final_pass) return;
-    const float *phi = bufs[st->last_buf];
-    constexpr int NBX = 4;                   // bands of this path, at most
-    // per band and side, a compensated FP32 sum (lse_kahan_add) of 4-pixel
-    // FP32 partials, kept in registers and turned into FP64 once
-    float sp[NBX], cp[NBX], sm[NBX], cm[NBX];
+    const int it = st->iterations_run;
+    const int seen = st->stats_iter;
+    if (it == seen) return;
+    const bool update = it == seen + 1;
+    const bool lb = st->last_buf != 0;
+    const float *phi = lb ? buf1 : buf0;         // written by the last step
+    const float *old = lb ? buf0 : buf1;         // read by it
+    constexpr int NBX = 4;                       // bands of this path, at most
+    // update form: (ks, -kc) per band is a float-float change of the sum
+    // over phi >= 0; full form: Kahan pairs for phi >= 0 (b) and < 0 (4 + b)
+    float ks[2 * NBX], kc[2 * NBX];
 #pragma unroll
-    for (int b = 0; b < NBX; ++b) sp[b] = cp[b] = sm[b] = cm[b] = 0.0f;
+    for (int k = 0; k < 2 * NBX; ++k) ks[k] = kc[k] = 0.0f;
     int npos = 0;
     const bool vec = (pitch & 3) == 0 && (band_stride & 3) == 0 &&
                      (reinterpret_cast<uintptr_t>(bands) & 15) == 0 &&
-                     (reinterpret_cast<uintptr_t>(phi) & 15) == 0;
-    if (vec) {
-        for (int y = cta; y < H; y += ncta)
-        for (int x = 4 * threadIdx.x; x < W; x += 4 * blockDim.x) {
-            const size_t o = (size_t)y * pitch + x;
+                     (reinterpret_cast<uintptr_t>(phi) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(old) & 15) == 0;
+    for (int y = cta; y < H; y += ncta)
+    for (int x = 4 * threadIdx.x; x < W; x += 4 * blockDim.x) {
+        const size_t o = (size_t)y * pitch + x;
+        const int nj = W - x < 4 ? W - x : 4;
+        float pv[4], ov[4];
+        if (vec && nj == 4) {
             const float4 p4 = *reinterpret_cast<const float4 *>(phi + o);
-            const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
-            bool pos[4];
+            pv[0] = p4.x; pv[1] = p4.y; pv[2] = p4.z; pv[3] = p4.w;
+            if (update) {
+                const float4 o4 = *reinterpret_cast<const float4 *>(old + o);
+                ov[0] = o4.x; ov[1] = o4.y; ov[2] = o4.z; ov[3] = o4.w;
+            }
+        } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                pos[j] = x + j < W && pv[j] >= 0.0f;
-                npos += pos[j];
+                pv[j] = j < nj ? phi[o + j] : -1.0f;
+                ov[j] = (update && j < nj) ? old[o + j] : -1.0f;
             }
+        }
+        bool pos[4], chg[4];
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            pos[j] = j < nj && pv[j] >= 0.0f;
+            npos += pos[j];
+            chg[j] = update && j < nj && (ov[j] >= 0.0f) != pos[j];
+            any |= chg[j];
+        }
+        if (update) {
+            if (!any) continue;
 #pragma unroll
             for (int b = 0; b < NBX; ++b) {
                 if (b < B) {
-                    const float4 e = __ldg(reinterpret_cast<const float4 *>(bands + b * band_stride + o));
-                    const float ev[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (!chg[j]) continue;
+                        const float v = __ldg(bands + b * band_stride + o + j);
+                        float e;
+                        ks[b] = two_sum(ks[b], pos[j] ? v : -v, e);
+                        kc[b] = __fsub_rn(kc[b], e);
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < NBX; ++b) {
+                if (b < B) {
+                    float ev[4];
+                    if (vec && nj == 4) {
+                        const float4 e = __ldg(reinterpret_cast<const float4 *>(bands + b * band_stride + o));
+                        ev[0] = e.x; ev[1] = e.y; ev[2] = e.z; ev[3] = e.w;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            ev[j] = j < nj ? __ldg(bands + b * band_stride + o + j) : 0.0f;
+                    }
                     float pp = 0.0f, pm = 0.0f;
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const float v = x + j < W ? ev[j] : 0.0f;    // row padding
+                        const float v = j < nj ? ev[j] : 0.0f;
                         pp = __fadd_rn(pp, pos[j] ? v : 0.0f);
                         pm = __fadd_rn(pm, pos[j] ? 0.0f : v);
                     }
-                    lse_kahan_add(sp[b], cp[b], pp);
-                    lse_kahan_add(sm[b], cm[b], pm);
-                }
-            }
-        }
-    } else {
-        for (int y = cta; y < H; y += ncta)
-        for (int x = threadIdx.x; x < W; x += blockDim.x) {
-            const size_t o = (size_t)y * pitch + x;
-            const bool pos = phi[o] >= 0.0f;
-            npos += pos;
-#pragma unroll
-            for (int b = 0; b < NBX; ++b) {
-                if (b < B) {
-                    const float v = __ldg(bands + b * band_stride + o);
-                    lse_kahan_add(sp[b], cp[b], pos ? v : 0.0f);
-                    lse_kahan_add(sm[b], cm[b], pos ? 0.0f : v);
+                    lse_kahan_add(ks[b], kc[b], pp);
+                    lse_kahan_add(ks[NBX + b], kc[NBX + b], pm);
                 }
             }
         }
     }
     // the CTA's sums: float-float shuffles (the FP64 units of this part are
     // few, and every CTA reduces at the same moment at the end of the pass)
-    float ks[2 * NBX], kc[2 * NBX];
     double tot[2 * NBX];
-#pragma unroll
-    for (int b = 0; b < NBX; ++b) {
-        ks[b] = sp[b];
-        kc[b] = cp[b];
-        ks[NBX + b] = sm[b];
-        kc[NBX + b] = cm[b];
-    }
     LseAcc r;
     r.clear();
     lse_cta_reduce_ff<2 * NBX>(ks, kc, (long long)npos, 0ll, tot, &r.n_plus, &r.flips);
@@ -105,11 +146,24 @@ __device__ __forceinline__ void band_stats(const float *__restrict__ bands, int 
         r.sp[b] = tot[b];
         r.sm[b] = tot[NBX + b];
     }
-    if (!lse_publish_and_ticket_at(r, B, partials, st, cta, ncta)) return;
+    if (!lse_publish_and_ticket_at(r, NBX, partials, st, cta, ncta)) return;
     LseAcc t;
-    lse_sum_partials(partials, ncta, B, &t);
+    // NBX bands (the partials of bands past B are zero): a constant count
+    // lets the last CTA load and add every field at once
+    lse_sum_partials<32, true>(partials, ncta, NBX, &t);
     if (threadIdx.x == 0) {
+        if (update) {
+#pragma unroll
+            for (int b = 0; b < NBX; ++b) {
+                if (b < B) {
+                    const double d = t.sp[b];
+                    t.sp[b] = st->run_sp[b] + d;
+                    t.sm[b] = st->run_sm[b] - d;
+                }
+            }
+        }
         lse_region_coeffs(st, t, B, dt);
+        st->stats_iter = it;
         __threadfence();
         st->ticket = 0;
     }
@@ -193,16 +247,13 @@ __device__ __forceinline__ void band_dterm(const float *__restrict__ bands, int 
     }
 }
 
-struct PlanePair {
-    const float *b[2];
-};
-
 __global__ void __launch_bounds__(kThreads)
-band_stats_kernel(const float *bands, int pitch, size_t band_stride, PlanePair bufs, int H,
-                  int W, int B, float dt, LseDevState *st, LsePartial *partials, int final_pass)
+band_stats_kernel(const float *bands, int pitch, size_t band_stride, const float *buf0,
+                  const float *buf1, int H, int W, int B, float dt, LseDevState *st,
+                  LsePartial *partials)
 {
-    band_stats(bands, pitch, band_stride, bufs.b, H, W, B, dt, st, partials, blockIdx.x,
-               gridDim.x, final_pass != 0);
+    band_stats(bands, pitch, band_stride, buf0, buf1, H, W, B, dt, st, partials, blockIdx.x,
+               gridDim.x);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -225,9 +276,8 @@ band_stats_batch_kernel(const BatchItem *__restrict__ items, const int *__restri
     const long long nl = launch - it.iter0;
     if (nl < 1 || nl >= it.cap) return;
     const StepArgs &a = it.args;
-    const float *bufs[2] = {it.phi[0], it.phi[1]};
-    band_stats(a.bands, a.pitch, a.band_stride, bufs, a.H, a.W, a.B, a.dt, a.st, a.partials,
-               blockIdx.x - it.nstart, it.nnblocks, false);
+    band_stats(a.bands, a.pitch, a.band_stride, it.phi[0], it.phi[1], a.H, a.W, a.B, a.dt, a.st,
+               a.partials, blockIdx.x - it.nstart, it.nnblocks);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -249,14 +299,11 @@ namespace lse_detail {
 cudaError_t launch_band_stats(const float *bands, int pitch, size_t band_stride,
                               float *const *bufs, int H, int W, int B, float dt,
                               LseDevState *st, LsePartial *partials, int nblocks,
-                              bool final_pass, cudaStream_t s)
+                              cudaStream_t s)
 {
-    PlanePair pp;
-    pp.b[0] = bufs[0];
-    pp.b[1] = bufs[1];
     const int grid = H < nblocks ? (H < 1 ? 1 : H) : nblocks;
-    band_stats_kernel<<<grid, kThreads, 0, s>>>(bands, pitch, band_stride, pp, H, W, B, dt,
-                                                st, partials, final_pass ? 1 : 0);
+    band_stats_kernel<<<grid, kThreads, 0, s>>>(bands, pitch, band_stride, bufs[0], bufs[1], H,
+                                                W, B, dt, st, partials);
     return cudaGetLastError();
 }
 

@@ -388,7 +388,7 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
         const StepArgs &a = items[i].args;
         if (a.mb_split) {
             e = launch_band_stats(a.bands, a.pitch, a.band_stride, items[i].phi, q.H, q.W, q.B,
-                                  a.dt, states + i, a.partials, nred, true, s);
+                                  a.dt, states + i, a.partials, nred, s);
             if (e != cudaSuccess) break;
         }
         e = launch_output(items[i].phi, lay[i].pitch, q.H, q.W, q.params.storage, states + i,

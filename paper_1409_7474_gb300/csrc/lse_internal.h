@@ -43,6 +43,11 @@ struct alignas(16) LseDevState {
     double norm_used;           // M of the last executed step
     long long area_plus;        // |{phi >= 0}| of the current LSF
     long long last_flips;
+    // band sums over phi >= 0 / phi < 0 behind c_plus / c_minus; the band
+    // pass of vector images keeps them up to date from the pixels that
+    // changed sign (stats_iter: iterations_run they describe)
+    double run_sp[LSE_MAXB], run_sm[LSE_MAXB];
+    int stats_iter;
     int iterations_run;
     int done;                   // early stop reached: later steps do nothing
     int last_buf;               // ping-pong buffer holding the latest v
@@ -207,13 +212,14 @@ cudaError_t launch_prologue(const void *img, int img_pitch, size_t band_stride,
                             LseDevState *st, LsePartial *partials, int nblocks,
                             cudaStream_t s);
 // Vector images on the tile form: the statistics pass (Eq. 15) over the LSF
-// bufs[st->last_buf] (final_pass: also after an early stop) and the pass
-// that writes D (Eq. 17) into dplane and sets M and the step coefficient;
-// and both for launch index n of a batch (the pass CTAs of each image).
+// the last step wrote (a no-op when no step ran since the last one, so it
+// may close every evolution) and the pass that writes D (Eq. 17) into dplane
+// and sets M and the step coefficient; and both for launch index n of a
+// batch (the pass CTAs of each image).
 cudaError_t launch_band_stats(const float *bands, int pitch, size_t band_stride,
                               float *const *bufs, int H, int W, int B, float dt,
                               LseDevState *st, LsePartial *partials, int nblocks,
-                              bool final_pass, cudaStream_t s);
+                              cudaStream_t s);
 cudaError_t launch_band_dterm(const float *bands, int pitch, size_t band_stride, float *dplane,
                               int H, int W, int B, float dt, LseDevState *st,
                               LsePartial *partials, int nblocks, cudaStream_t s);

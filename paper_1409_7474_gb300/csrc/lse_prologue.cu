@@ -204,6 +204,7 @@ prologue_kernel(const void *__restrict__ img, int img_pitch, size_t band_stride,
         st->imax = t.fmax;
         st->last_flips = 0;
         st->iterations_run = 0;
+        st->stats_iter = 0;
         st->done = 0;
         st->last_buf = 0;
         st->norm_used = 0.0;

@@ -134,11 +134,12 @@ __device__ __forceinline__ void lse_cta_reduce_ff(const float (&s)[NV], const fl
     __syncthreads();
 }
 
-// Reduces `acc` over the CTA (blockDim.x a multiple of 32, at most 32 MAXW)
-// into `out` (visible to thread 0 after return).  `nb` bands are summed.
-// MAXW sizes the static shared arrays: a kernel of few warps passes its own
-// count and keeps that shared memory for its tiles.
-template <int MAXW = 32>
+// Reduces `acc` over the CTA (blockDim.x a multiple of 32 and at least 64,
+// at most 32 MAXW) into `out` (visible to thread 0 after return).  `nb`
+// bands are summed.  MAXW sizes the static shared arrays: a kernel of few
+// warps passes its own count and keeps that shared memory for its tiles.
+// PAR: the per-warp results meet in one thread per value instead of thread 0.
+template <int MAXW = 32, bool PAR = false>
 __device__ __forceinline__ void lse_cta_reduce(const LseAcc &acc, int nb,
                                                LseAcc *out)
 {
@@ -178,18 +179,53 @@ __device__ __forceinline__ void lse_cta_reduce(const LseAcc &acc, int nb,
         s_u[warp] = bits;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        out->clear();
-        for (int w = 0; w < nwarps; ++w) {
+    if constexpr (PAR) {
+        // across the warps in index order, one thread per value (FP64 adds
+        // have a latency of ~64 cycles on this part): for many bands at
+        // the end of a one-wave pass.  The step kernels keep the one-thread
+        // form, which measured faster there.
+        __shared__ double s_sum[2 * LSE_MAXB];
+        __shared__ long long s_cnt[2];
+        const int k = threadIdx.x;
+        if (k < 2 * nb) {
+            const int col = k < nb ? k : LSE_MAXB + (k - nb);
+            double v = 0.0;
+            for (int w = 0; w < nwarps; ++w) v += s_d[w][col];
+            s_sum[k] = v;
+        } else if (k >= 32 && k < 34) {
+            long long v = 0;
+            for (int w = 0; w < nwarps; ++w) v += s_l[w][k - 32];
+            s_cnt[k - 32] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            out->clear();
             for (int b = 0; b < nb; ++b) {
-                out->sp[b] += s_d[w][b];
-                out->sm[b] += s_d[w][LSE_MAXB + b];
+                out->sp[b] = s_sum[b];
+                out->sm[b] = s_sum[nb + b];
             }
-            out->n_plus += s_l[w][0];
-            out->flips += s_l[w][1];
-            out->fmax = fmaxf(out->fmax, s_f[w][0]);
-            out->fmin = fminf(out->fmin, s_f[w][1]);
-            out->bits |= s_u[w];
+            out->n_plus = s_cnt[0];
+            out->flips = s_cnt[1];
+            for (int w = 0; w < nwarps; ++w) {
+                out->fmax = fmaxf(out->fmax, s_f[w][0]);
+                out->fmin = fminf(out->fmin, s_f[w][1]);
+                out->bits |= s_u[w];
+            }
+        }
+    } else {
+        if (threadIdx.x == 0) {
+            out->clear();
+            for (int w = 0; w < nwarps; ++w) {
+                for (int b = 0; b < nb; ++b) {
+                    out->sp[b] += s_d[w][b];
+                    out->sm[b] += s_d[w][LSE_MAXB + b];
+                }
+                out->n_plus += s_l[w][0];
+                out->flips += s_l[w][1];
+                out->fmax = fmaxf(out->fmax, s_f[w][0]);
+                out->fmin = fminf(out->fmin, s_f[w][1]);
+                out->bits |= s_u[w];
+            }
         }
     }
     __syncthreads();
@@ -238,26 +274,63 @@ __device__ __forceinline__ bool lse_publish_and_ticket(const LseAcc &r, int nb,
 }
 
 // In the last CTA: sums all partials in CTA order into `total` (thread 0).
-template <int MAXW = 32>
+template <int MAXW = 32, bool PAR = false>
 __device__ __forceinline__ void lse_sum_partials(const LsePartial *partials,
                                                  int nparts, int nb,
                                                  LseAcc *total)
 {
     LseAcc a;
     a.clear();
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-        const LsePartial *p = partials + i;
-        for (int b = 0; b < nb; ++b) {
-            a.sp[b] += __ldcg(&p->sp[b]);
-            a.sm[b] += __ldcg(&p->sm[b]);
+    if constexpr (PAR) {
+        // every field of a partial loaded at once into register sums (band
+        // loop unrolled; pass a constant nb), so the L2 latency is paid once
+        // per partial rather than once per field
+        double sp[LSE_MAXB], sm[LSE_MAXB];
+#pragma unroll
+        for (int b = 0; b < LSE_MAXB; ++b) sp[b] = sm[b] = 0.0;
+        long long np = 0, fl = 0;
+        float fx = -INFINITY, fn = INFINITY;
+        unsigned int bits = 0;
+        for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+            const LsePartial *p = partials + i;
+#pragma unroll
+            for (int b = 0; b < LSE_MAXB; ++b) {
+                if (b < nb) {
+                    sp[b] += __ldcg(&p->sp[b]);
+                    sm[b] += __ldcg(&p->sm[b]);
+                }
+            }
+            np += __ldcg(&p->n_plus);
+            fl += __ldcg(&p->flips);
+            fx = fmaxf(fx, __ldcg(&p->fmax));
+            fn = fminf(fn, __ldcg(&p->fmin));
+            bits |= __ldcg(&p->bits);
         }
-        a.n_plus += __ldcg(&p->n_plus);
-        a.flips += __ldcg(&p->flips);
-        a.fmax = fmaxf(a.fmax, __ldcg(&p->fmax));
-        a.fmin = fminf(a.fmin, __ldcg(&p->fmin));
-        a.bits |= __ldcg(&p->bits);
+#pragma unroll
+        for (int b = 0; b < LSE_MAXB; ++b) {
+            a.sp[b] = sp[b];
+            a.sm[b] = sm[b];
+        }
+        a.n_plus = np;
+        a.flips = fl;
+        a.fmax = fx;
+        a.fmin = fn;
+        a.bits = bits;
+    } else {
+        for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+            const LsePartial *p = partials + i;
+            for (int b = 0; b < nb; ++b) {
+                a.sp[b] += __ldcg(&p->sp[b]);
+                a.sm[b] += __ldcg(&p->sm[b]);
+            }
+            a.n_plus += __ldcg(&p->n_plus);
+            a.flips += __ldcg(&p->flips);
+            a.fmax = fmaxf(a.fmax, __ldcg(&p->fmax));
+            a.fmin = fminf(a.fmin, __ldcg(&p->fmin));
+            a.bits |= __ldcg(&p->bits);
+        }
     }
-    lse_cta_reduce<MAXW>(a, nb, total);
+    lse_cta_reduce<MAXW, PAR>(a, nb, total);
 }
 
 // Region statistics of the current LSF -> c+/c- and the coefficients of the
@@ -272,10 +345,17 @@ __device__ __forceinline__ void lse_region_coeffs(LseDevState *st,
     const long long N = st->npix;
     const long long np = t.n_plus;
     const long long nm = N - np;
+    // the means as products with the two reciprocals: an FP64 division
+    // takes ~400 cycles here, and this runs on one thread at the end of a
+    // launch (the products differ from quotients by at most 1 ulp of FP64)
+    const double rp = np > 0 ? 1.0 / (double)np : 0.0;
+    const double rm = nm > 0 ? 1.0 / (double)nm : 0.0;
     double contrast = 0.0, scale = 0.0;
     for (int b = 0; b < B; ++b) {
         double cp = np > 0 ? t.sp[b] / (double)np : 0.0;
         double cm = nm > 0 ? t.sm[b] / (double)nm : 0.0;
+        st->run_sp[b] = t.sp[b];
+        st->run_sm[b] = t.sm[b];
         st->c_plus[b] = cp;
         st->c_minus[b] = cm;
         st->alpha[b] = 2.0 * (cp - cm);

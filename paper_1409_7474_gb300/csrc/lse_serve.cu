@@ -364,7 +364,7 @@ lse_status lse_server_advance(lse_server *sv, int ticks, int *running, void *str
         if (a.mb_split)
             e = launch_band_stats(a.bands, a.pitch, a.band_stride, sv->items[slot].phi, req.q.H,
                                   req.q.W, req.q.B, a.dt, sv->d_states + slot, a.partials,
-                                  ctx->sm_count * 4, true, s);
+                                  ctx->sm_count * 4, s);
         if (e == cudaSuccess)
             e = launch_output(sv->items[slot].phi, req.pitch, req.q.H, req.q.W,
                               req.q.params.storage, sv->d_states + slot, req.q.phi_out,
