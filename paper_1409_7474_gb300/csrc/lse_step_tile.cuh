@@ -24,7 +24,9 @@
 //      accumulates the statistics.
 // With h in the phi buffer a CTA needs 70 KB of shared memory, so three CTAs
 // share an SM (radius <= 4) and cover each other's TMA waits; the next tile
-// is loaded as soon as the vertical pass is done.
+// is loaded as soon as the vertical pass is done.  (Starting the edge term's
+// data copy right after the u pass, which last reads it, cost that kernel
+// 5 %: the split load pushed it into register spills.)
 //
 // FAST instantiations serve the steady state of a re-initialising evolution
 // (phi = +-1 in, sign(v) out, no sign-change count): ghost columns make the
