@@ -12,7 +12,8 @@ Reported (one JSON line on rank 0):
   value        Mpixel-iterations/s over all ranks, inputs resident in HBM;
   e2e          the same with the step's inputs and results in pinned host
                memory, copied by the library inside the timing (region and
-               edge term on two streams, so copies overlap kernels);
+               edge term on two streams, the edge evolution ordered after the
+               region's, so copies overlap kernels);
   roofline     the fused region step kernel: algorithmic bytes per launch
                (12 B/px: read I, read phi, write v) / its mean duration from
                CUDA events on the library's stream, against measured HBM;
@@ -596,8 +597,10 @@ def main():
     # mask of both terms) are pinned host buffers passed to the C ABI, which
     # copies them in and out inside the timed region.  The edge indicator g
     # is an intermediate between two calls and stays on the device.  The
-    # region evolution runs on one stream and the edge term on another, so
-    # each one's host copies overlap the other's kernels.
+    # region evolution runs on one stream and the edge term on another: the
+    # edge precompute and its copies run beside the region evolution, the
+    # edge evolution after it, so each one's host copies overlap the other's
+    # kernels while the step kernels never share the SMs.
     e2e = None
     if not args.no_e2e:
         hx = torch.from_numpy(img).pin_memory()
@@ -614,6 +617,13 @@ def main():
         def step_host():
             ctx_r.evolve(hx, hpr, "region", phi_out=ho_r, mask_out=hm_r, stream=s_r, **common)
             ctx_e.precompute_edge(hx, 1.0, 9, 255.0, out=dg, stream=s_e)
+            # the edge evolution after the region's: two persistent step
+            # kernels sharing the SMs interleave unpredictably (360-470 k
+            # Mpixel-it/s over runs); ordered, the copies still overlap the
+            # other term's kernels
+            done_r = torch.cuda.Event()
+            done_r.record(s_r)
+            s_e.wait_event(done_r)
             ctx_e.evolve(None, hpe, "edge", g=dg, phi_out=ho_e, mask_out=hm_e, stream=s_e,
                          **common)
 
@@ -644,8 +654,9 @@ def main():
                "h2d_bytes_per_step": 4 * plane,
                # v + mask (region), v + mask (edge)
                "d2h_bytes_per_step": 2 * plane + 2 * npx,
-               "streams": "region on one stream, edge on another; host buffers for "
-                          "inputs and results, g on the device"}
+               "streams": "region on one stream, edge on another (edge precompute and "
+                          "copies beside the region evolution, edge evolution after it); "
+                          "host buffers for inputs and results, g on the device"}
 
     # the same workload with 16-bit storage of the data term and the LSF
     # (FP32 arithmetic): 6 bytes per pixel-iteration of the region step
