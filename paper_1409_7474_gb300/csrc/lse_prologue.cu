@@ -209,7 +209,7 @@ prologue_kernel(const void *__restrict__ img, int img_pitch, size_t band_stride,
         st->last_buf = 0;
         st->norm_used = 0.0;
         if (term == LSE_TERM_REGION) {
-            lse_region_coeffs(st, t, B, dt);
+            lse_region_coeffs_v(st, t, B, dt, n, t.fmin, t.fmax);
         } else {
             st->area_plus = t.n_plus;
             st->zero_force = 0;

@@ -214,18 +214,41 @@ __device__ __forceinline__ void lse_cta_reduce(const LseAcc &acc, int nb,
         }
     } else {
         if (threadIdx.x == 0) {
-            out->clear();
+            // warps in index order, in registers (not through `out`, a
+            // generic pointer the compiler must reload and store every step)
+            double sp[LSE_MAXB], sm[LSE_MAXB];
+#pragma unroll
+            for (int b = 0; b < LSE_MAXB; ++b) sp[b] = sm[b] = 0.0;
+            long long np = 0, fl = 0;
+            float fx = -INFINITY, fn = INFINITY;
+            unsigned int bits = 0;
             for (int w = 0; w < nwarps; ++w) {
-                for (int b = 0; b < nb; ++b) {
-                    out->sp[b] += s_d[w][b];
-                    out->sm[b] += s_d[w][LSE_MAXB + b];
+#pragma unroll
+                for (int b = 0; b < LSE_MAXB; ++b) {
+                    if (b < nb) {
+                        sp[b] += s_d[w][b];
+                        sm[b] += s_d[w][LSE_MAXB + b];
+                    }
                 }
-                out->n_plus += s_l[w][0];
-                out->flips += s_l[w][1];
-                out->fmax = fmaxf(out->fmax, s_f[w][0]);
-                out->fmin = fminf(out->fmin, s_f[w][1]);
-                out->bits |= s_u[w];
+                np += s_l[w][0];
+                fl += s_l[w][1];
+                fx = fmaxf(fx, s_f[w][0]);
+                fn = fminf(fn, s_f[w][1]);
+                bits |= s_u[w];
             }
+            out->clear();
+#pragma unroll
+            for (int b = 0; b < LSE_MAXB; ++b) {
+                if (b < nb) {
+                    out->sp[b] = sp[b];
+                    out->sm[b] = sm[b];
+                }
+            }
+            out->n_plus = np;
+            out->flips = fl;
+            out->fmax = fx;
+            out->fmin = fn;
+            out->bits = bits;
         }
     }
     __syncthreads();
@@ -338,77 +361,120 @@ __device__ __forceinline__ void lse_sum_partials(const LsePartial *partials,
 // form M = |c+ - c-| max(|2 Imax - c+ - c-|, |2 Imin - c+ - c-|) (|2I - s|
 // is convex in I, so its maximum over the image sits at Imin or Imax); for
 // several bands M comes from the normaliser pass.  Thread 0 only.
+__device__ __forceinline__ void lse_region_coeffs_v(LseDevState *st, const LseAcc &t, int B,
+                                                    float dt, long long N, double imin,
+                                                    double imax)
+{
+    // writes the state record only: a read back of a field just stored (or
+    // any dependent read of the record) is a memory round trip at the end of
+    // a launch, on one thread, with every other SM idle
+    const long long np = t.n_plus;
+    const long long nm = N - np;
+    double contrast = 0.0, scale = 0.0, cp0 = 0.0, cm0 = 0.0, al0 = 0.0;
+    for (int b = 0; b < B; ++b) {
+        const double cp = np > 0 ? t.sp[b] / (double)np : 0.0;
+        const double cm = nm > 0 ? t.sm[b] / (double)nm : 0.0;
+        const double al = 2.0 * (cp - cm);
+        const double md = 0.5 * (cp + cm);
+        st->run_sp[b] = t.sp[b];
+        st->run_sm[b] = t.sm[b];
+        st->c_plus[b] = cp;
+        st->c_minus[b] = cm;
+        st->alpha[b] = al;
+        st->mid[b] = md;
+        st->af[b] = (float)al;
+        st->m[b] = (float)md;
+        contrast = fmax(contrast, fabs(cp - cm));
+        scale = fmax(scale, fabs(cp) + fabs(cm));
+        if (b == 0) {
+            cp0 = cp;
+            cm0 = cm;
+            al0 = al;
+        }
+    }
+    st->area_plus = np;
+    int zero = (np == 0 || nm == 0 || contrast <= LSE_CONTRAST_TOL * scale);
+    double norm = 0.0;
+    float a0 = 0.0f;
+    if (!zero && B == 1) {
+        const double s = cp0 + cm0;
+        const double M = fabs(cp0 - cm0) * fmax(fabs(2.0 * imax - s), fabs(2.0 * imin - s));
+        if (!(M > 0.0)) {
+            zero = 1;
+        } else {
+            norm = M;
+            a0 = (float)((double)dt * al0 / (2.0 * M));
+        }
+    }
+    st->norm = norm;
+    if (zero) {
+        for (int b = 0; b < LSE_MAXB; ++b) st->a[b] = 0.0f;
+    } else if (B == 1) {
+        st->a[0] = a0;
+    }
+    st->zero_force = zero;
+}
+
 __device__ __forceinline__ void lse_region_coeffs(LseDevState *st,
                                                   const LseAcc &t, int B,
                                                   float dt)
 {
     const long long N = st->npix;
-    const long long np = t.n_plus;
-    const long long nm = N - np;
-    // the means as products with the two reciprocals: an FP64 division
-    // takes ~400 cycles here, and this runs on one thread at the end of a
-    // launch (the products differ from quotients by at most 1 ulp of FP64)
-    const double rp = np > 0 ? 1.0 / (double)np : 0.0;
-    const double rm = nm > 0 ? 1.0 / (double)nm : 0.0;
-    double contrast = 0.0, scale = 0.0;
-    for (int b = 0; b < B; ++b) {
-        double cp = np > 0 ? t.sp[b] / (double)np : 0.0;
-        double cm = nm > 0 ? t.sm[b] / (double)nm : 0.0;
-        st->run_sp[b] = t.sp[b];
-        st->run_sm[b] = t.sm[b];
-        st->c_plus[b] = cp;
-        st->c_minus[b] = cm;
-        st->alpha[b] = 2.0 * (cp - cm);
-        st->mid[b] = 0.5 * (cp + cm);
-        st->af[b] = (float)st->alpha[b];
-        st->m[b] = (float)st->mid[b];
-        contrast = fmax(contrast, fabs(cp - cm));
-        scale = fmax(scale, fabs(cp) + fabs(cm));
-    }
-    st->area_plus = np;
-    int zero = (np == 0 || nm == 0 || contrast <= LSE_CONTRAST_TOL * scale);
-    st->norm = 0.0;
-    if (!zero && B == 1) {
-        double s = st->c_plus[0] + st->c_minus[0];
-        double M = fabs(st->c_plus[0] - st->c_minus[0]) *
-                   fmax(fabs(2.0 * st->imax - s), fabs(2.0 * st->imin - s));
-        if (!(M > 0.0)) {
-            zero = 1;
-        } else {
-            st->norm = M;
-            st->a[0] = (float)((double)dt * st->alpha[0] / (2.0 * M));
-        }
-    }
-    if (zero)
-        for (int b = 0; b < LSE_MAXB; ++b) st->a[b] = 0.0f;
-    st->zero_force = zero;
+    const double imin = st->imin, imax = st->imax;
+    lse_region_coeffs_v(st, t, B, dt, N, imin, imax);
+}
+
+// The state fields a step's finalisation reads, loaded together (one
+// latency) by thread 0 before the CTA's reduction; none of them changes
+// during the step.
+struct LseStatePre {
+    double norm, imin, imax;
+    long long npix;
+    int zero_force;
+};
+
+__device__ __forceinline__ LseStatePre lse_state_pre(const LseDevState *st)
+{
+    LseStatePre p;
+    p.norm = st->norm;
+    p.imin = st->imin;
+    p.imax = st->imax;
+    p.npix = st->npix;
+    p.zero_force = st->zero_force;
+    return p;
 }
 
 // End of one executed step (thread 0 of the last CTA): record the step,
 // then compute the statistics of the new LSF and the next step's
 // coefficients.  `t` holds the grid-wide sums over the new LSF.
-__device__ __forceinline__ void lse_step_finalize(const StepArgs &a,
-                                                  const LseAcc &t)
+__device__ __forceinline__ void lse_step_finalize(const StepArgs &a, const LseAcc &t,
+                                                  const LseStatePre &pre)
 {
     LseDevState *st = a.st;
-    st->status_bits |= t.bits;
+    unsigned int bits = t.bits;
     st->last_flips = t.flips;
     st->iterations_run = a.iter + 1;
     st->last_buf = a.out_buf;
     if (a.term == LSE_TERM_REGION && a.mb_split) {
         // vector image on the tile form: the next statistics pass makes the
         // coefficients of the next step
-        if (st->zero_force) st->status_bits |= LSE_SBIT_DEGENERATE;
-        st->norm_used = st->zero_force ? 0.0 : st->norm;
+        if (pre.zero_force) bits |= LSE_SBIT_DEGENERATE;
+        st->norm_used = pre.zero_force ? 0.0 : pre.norm;
         st->area_plus = t.n_plus;
     } else if (a.term == LSE_TERM_REGION) {
-        if (st->zero_force) st->status_bits |= LSE_SBIT_DEGENERATE;
-        st->norm_used = st->zero_force ? 0.0 : st->norm;
-        lse_region_coeffs(st, t, a.B, a.dt);
+        if (pre.zero_force) bits |= LSE_SBIT_DEGENERATE;
+        st->norm_used = pre.zero_force ? 0.0 : pre.norm;
+        lse_region_coeffs_v(st, t, a.B, a.dt, pre.npix, pre.imin, pre.imax);
     } else {
         st->area_plus = t.n_plus;
     }
+    if (bits) atomicOr(&st->status_bits, bits);
     if (a.early_thresh > 0.0 && (double)t.flips < a.early_thresh) st->done = 1;
     __threadfence();
     st->ticket = 0;
+}
+
+__device__ __forceinline__ void lse_step_finalize(const StepArgs &a, const LseAcc &t)
+{
+    lse_step_finalize(a, t, lse_state_pre(a.st));
 }

@@ -650,6 +650,10 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
         wait_bar(bar_dat, par);
     }
 
+    // the fields the last CTA's finalisation reads, fetched while the CTA
+    // reduces
+    LseStatePre pre;
+    if (tid == 0) pre = lse_state_pre(st);
     LseAcc acc;
     acc.clear();
     const double dsw = lse_kahan_value(ksw, csw), dsa = lse_kahan_value(ksa, csa);
@@ -665,7 +669,7 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
     if (!lse_publish_and_ticket_at(r, nb, a.partials, st, cta, ncta)) return;
     LseAcc tot;
     lse_sum_partials<NW>(a.partials, ncta, nb, &tot);
-    if (threadIdx.x == 0) lse_step_finalize(a, tot);
+    if (threadIdx.x == 0) lse_step_finalize(a, tot, pre);
 }
 
 template <int KIND_EDGE, int RAD, bool FAST, class T, int NW>
