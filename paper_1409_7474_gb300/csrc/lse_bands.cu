@@ -147,6 +147,20 @@ __device__ __forceinline__ void band_stats(const float *__restrict__ bands, int 
         r.sm[b] = tot[NBX + b];
     }
     if (!lse_publish_and_ticket_at(r, NBX, partials, st, cta, ncta)) return;
+    // the state fields the finalisation reads, in flight while the partials
+    // are summed (one latency instead of a chain of them)
+    double rsp[NBX], rsm[NBX], imin = 0.0, imax = 0.0;
+    long long npix = 0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int b = 0; b < NBX; ++b) {
+            rsp[b] = st->run_sp[b];
+            rsm[b] = st->run_sm[b];
+        }
+        npix = st->npix;
+        imin = st->imin;
+        imax = st->imax;
+    }
     LseAcc t;
     // NBX bands (the partials of bands past B are zero): a constant count
     // lets the last CTA load and add every field at once
@@ -157,12 +171,12 @@ __device__ __forceinline__ void band_stats(const float *__restrict__ bands, int 
             for (int b = 0; b < NBX; ++b) {
                 if (b < B) {
                     const double d = t.sp[b];
-                    t.sp[b] = st->run_sp[b] + d;
-                    t.sm[b] = st->run_sm[b] - d;
+                    t.sp[b] = rsp[b] + d;
+                    t.sm[b] = rsm[b] - d;
                 }
             }
         }
-        lse_region_coeffs(st, t, B, dt);
+        lse_region_coeffs_v(st, t, B, dt, npix, imin, imax);
         st->stats_iter = it;
         __threadfence();
         st->ticket = 0;
@@ -231,12 +245,13 @@ __device__ __forceinline__ void band_dterm(const float *__restrict__ bands, int 
     LseAcc r;
     lse_cta_reduce(acc, 0, &r);
     if (!lse_publish_and_ticket_at(r, 0, partials, st, cta, ncta)) return;
+    const int zf = threadIdx.x == 0 ? st->zero_force : 0;   // in flight during the sum
     LseAcc t;
     lse_sum_partials(partials, ncta, 0, &t);
     if (threadIdx.x == 0) {
         const double M = fmax(fabs((double)t.fmax), fabs((double)t.fmin));
-        st->norm = st->zero_force ? 0.0 : M;
-        if (st->zero_force || !(M > 0.0)) {
+        st->norm = zf ? 0.0 : M;
+        if (zf || !(M > 0.0)) {
             st->zero_force = 1;
             st->a[0] = 0.0f;
         } else {
