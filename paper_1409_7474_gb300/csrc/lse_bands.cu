@@ -17,6 +17,21 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// The D pass follows the statistics pass as a programmatic dependent
+// launch: the statistics CTAs allow it on entry, so its CTAs are resident
+// and waiting when the statistics' last CTA finishes its one-thread
+// finalisation, instead of being launched after it.  The D pass waits for
+// the whole statistics grid (and its memory) before it reads anything.
+__device__ __forceinline__ void allow_dependent_grid()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+__device__ __forceinline__ void wait_primary_grid()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // Error-free sum (Knuth's TwoSum): s + e == a + b exactly.
 __device__ __forceinline__ float two_sum(float a, float b, float &e)
 {
@@ -267,6 +282,7 @@ band_stats_kernel(const float *bands, int pitch, size_t band_stride, const float
                   const float *buf1, int H, int W, int B, float dt, LseDevState *st,
                   LsePartial *partials)
 {
+    allow_dependent_grid();
     band_stats(bands, pitch, band_stride, buf0, buf1, H, W, B, dt, st, partials, blockIdx.x,
                gridDim.x);
 }
@@ -275,6 +291,7 @@ __global__ void __launch_bounds__(kThreads)
 band_dterm_kernel(const float *bands, int pitch, size_t band_stride, float *dplane, int H,
                   int W, int B, float dt, LseDevState *st, LsePartial *partials)
 {
+    wait_primary_grid();
     band_dterm(bands, pitch, band_stride, dplane, H, W, B, dt, st, partials, blockIdx.x,
                gridDim.x);
 }
@@ -287,6 +304,7 @@ __global__ void __launch_bounds__(kThreads)
 band_stats_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ blk_item,
                         long long launch)
 {
+    allow_dependent_grid();
     const BatchItem &it = items[blk_item[blockIdx.x]];
     const long long nl = launch - it.iter0;
     if (nl < 1 || nl >= it.cap) return;
@@ -299,12 +317,34 @@ __global__ void __launch_bounds__(kThreads)
 band_dterm_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ blk_item,
                         long long launch)
 {
+    wait_primary_grid();
     const BatchItem &it = items[blk_item[blockIdx.x]];
     const long long nl = launch - it.iter0;
     if (nl < 0 || nl >= it.cap) return;
     const StepArgs &a = it.args;
     band_dterm(a.bands, a.pitch, a.band_stride, const_cast<float *>(a.data), a.H, a.W, a.B,
                a.dt, a.st, a.partials, blockIdx.x - it.nstart, it.nnblocks);
+}
+
+}  // namespace
+
+namespace {
+
+// A programmatic dependent launch (see allow_dependent_grid).
+template <class Kern, class... Args>
+cudaError_t launch_after_primary(Kern kern, int nblocks, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 }  // namespace
@@ -327,9 +367,8 @@ cudaError_t launch_band_dterm(const float *bands, int pitch, size_t band_stride,
                               LsePartial *partials, int nblocks, cudaStream_t s)
 {
     const int grid = H < nblocks ? (H < 1 ? 1 : H) : nblocks;
-    band_dterm_kernel<<<grid, kThreads, 0, s>>>(bands, pitch, band_stride, dplane, H, W, B, dt,
-                                                st, partials);
-    return cudaGetLastError();
+    return launch_after_primary(band_dterm_kernel, grid, s, bands, pitch, band_stride, dplane,
+                                H, W, B, dt, st, partials);
 }
 
 cudaError_t launch_band_passes_batch(const BatchItem *items, const int *blk_item, long long n,
@@ -338,8 +377,7 @@ cudaError_t launch_band_passes_batch(const BatchItem *items, const int *blk_item
     band_stats_batch_kernel<<<nblocks, kThreads, 0, s>>>(items, blk_item, n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    band_dterm_batch_kernel<<<nblocks, kThreads, 0, s>>>(items, blk_item, n);
-    return cudaGetLastError();
+    return launch_after_primary(band_dterm_batch_kernel, nblocks, s, items, blk_item, n);
 }
 
 }  // namespace lse_detail
