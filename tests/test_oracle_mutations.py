@@ -56,6 +56,17 @@ MUTATIONS = {
     # Table I order without its re-initialisation before smoothing
     "table1_no_binarise": ("if (order == ORACLE_ORDER_TABLE1 && reinit)",
                            "if (order == ORACLE_ORDER_TABLE1 && 0)"),
+    # re-initialisation one iteration early in a periodic schedule
+    "reinit_phase": ("return ((n + 1) % period) == 0;", "return (n % period) == 0;"),
+    # early stop when the count equals the threshold (the rule is strict)
+    "stop_not_strict": ("(double)flips < early_stop_frac * (double)N",
+                        "(double)flips <= early_stop_frac * (double)N"),
+    # a starting value of exactly 0 counted on the minus side for sign changes
+    "flip_strict_side": ("if ((v_out[p] >= 0.0) != (phi[p] >= 0.0)) ++flips;",
+                         "if ((v_out[p] >= 0.0) != (phi[p] > 0.0)) ++flips;"),
+    # sign changes counted against the re-initialised LSF (always 0 then)
+    "flips_after_reinit": ("        st->last_flips = flips;\n",
+                           "        st->last_flips = 0;\n"),
 }
 
 

@@ -546,3 +546,119 @@ def test_results_do_not_depend_on_the_thread_count():
         assert runs[0][2]["norm"] == other[2]["norm"]
         assert np.array_equal(runs[0][2]["c_plus"], other[2]["c_plus"])
         assert np.array_equal(runs[0][3], other[3]) and np.array_equal(runs[0][5], other[5])
+
+
+# ---------------------------------------------------------------- re-initialisation schedule, flip count, early stop
+def hand_evolve(I, phi0, iterations, period=1, frac=0.0, order="listing",
+                sigma=1.0, ts=9, dt=15.0):
+    """The whole region-term loop written out by hand on independent_step /
+    independent_variant_step.
+
+    Re-initialisation (Table I step 3; Sec. III-D, Step 3: "periodically")
+    comes after every `period`-th iteration, i.e. after iterations
+    period-1, 2*period-1, ... (0-based); period 1 = every iteration, 0 = never.
+    The sign changes of an iteration compare v >= 0 with the LSF it started
+    from, phi >= 0; Step 5 stops after the first iteration with fewer than
+    frac * H * W of them.  Returns (v, list of per-iteration sign changes)."""
+    N = phi0.size
+    phi = phi0.copy()
+    history = []
+    for n in range(iterations):
+        reinit = period == 1 or (period > 1 and n % period == period - 1)
+        if order == "listing":
+            v = independent_step(I, phi, "region", dt=dt, sigma=sigma, ts=ts)
+        else:
+            v = independent_variant_step(I, phi, "region", dt=dt, sigma=sigma, ts=ts,
+                                         order="table1", reinit=reinit)
+        changed = 0
+        for y in range(phi.shape[0]):
+            for x in range(phi.shape[1]):
+                if (v[y, x] >= 0) != (phi[y, x] >= 0):
+                    changed += 1
+        history.append(changed)
+        if order == "listing" and reinit:
+            phi = np.where(v >= 0, 1.0, -1.0)
+        else:
+            phi = v
+        if frac > 0 and changed < frac * N:
+            break
+    return v, history
+
+
+@pytest.mark.parametrize("period", [2, 3])
+@pytest.mark.parametrize("order", ["listing", "table1"])
+def test_reinit_period_schedule_against_hand_loop(period, order):
+    img, truth, _ = scenes.rect_scene(16, 20, 8, 6, noise=0.05)
+    phi0 = scenes.circle_phi(16, 20, radius=5)
+    its = 2 * period + 1          # ends one iteration after a re-initialisation
+    v_ref, hist = hand_evolve(img.astype(np.float64), phi0, its, period=period,
+                              order=order)
+    v, mask, st = oracle.evolve(img, phi0, iterations=its, reinit_period=period,
+                                order=order)
+    np.testing.assert_allclose(v, v_ref, rtol=1e-11, atol=1e-12)
+    assert st["iterations_run"] == its and st["last_flips"] == hist[-1]
+    # the schedule matters: the same run re-initialising after iterations
+    # 0, period, 2*period, ... (one iteration early) gives another v
+    shifted = phi0.copy()
+    for n in range(its):
+        early = n % period == 0
+        if order == "listing":
+            w = independent_step(img.astype(np.float64), shifted, "region")
+            shifted = np.where(w >= 0, 1.0, -1.0) if early else w
+        else:
+            w = independent_variant_step(img.astype(np.float64), shifted, "region",
+                                         order="table1", reinit=early)
+            shifted = w
+    assert np.abs(w - v).max() > 1e-6
+
+
+def test_sign_changes_counted_against_the_starting_lsf():
+    img, truth, _ = scenes.rect_scene(32, 32, 14, 10, noise=0.05)
+    phi0 = scenes.circle_phi(32, 32, radius=8)
+    I = img.astype(np.float64)
+    v_ref, hist = hand_evolve(I, phi0, 6)
+    assert all(h > 0 for h in hist)          # non-zero counts throughout
+    for its in (1, 3, 6):
+        _, _, st = oracle.evolve(img, phi0, iterations=its)
+        assert st["last_flips"] == hist[its - 1]
+    # real-valued LSF between re-initialisations (period 3)
+    _, hist3 = hand_evolve(I, phi0, 5, period=3)
+    _, _, st = oracle.evolve(img, phi0, iterations=5, reinit_period=3)
+    assert st["last_flips"] == hist3[-1]
+
+
+def test_zero_lsf_value_is_not_a_sign_change():
+    # TS = 1 and a constant image make v = phi exactly; a pixel with phi = 0
+    # keeps v = 0, on the phi >= 0 side both times: no sign change.
+    I = np.full((1, 6, 7), 0.3)
+    phi0 = np.where(np.arange(7)[None, :] < 3, 1.0, -1.0) * np.ones((6, 7))
+    phi0[1, 5] = 0.0
+    phi0[4, 1] = 0.0
+    _, _, st = oracle.evolve(I, phi0, ts=1, iterations=1)
+    assert st["last_flips"] == 0
+
+
+def test_early_stop_after_several_iterations():
+    img, truth, _ = scenes.rect_scene(32, 32, 14, 10, noise=0.05)
+    phi0 = scenes.circle_phi(32, 32, radius=8)
+    I = img.astype(np.float64)
+    N = 32 * 32                          # a power of two: k / N is exact
+    _, hist = hand_evolve(I, phi0, 12)
+    # an iteration k >= 1 whose count is below every earlier one
+    ks = [k for k in range(1, len(hist)) if 0 < hist[k] < min(hist[:k])]
+    assert ks, hist
+    k = ks[0]
+    # threshold between the counts: the loop stops right after iteration k
+    frac = (hist[k] + 0.5) / N
+    v_ref, h = hand_evolve(I, phi0, 12, frac=frac)
+    v, mask, st = oracle.evolve(img, phi0, iterations=12, early_stop_frac=frac)
+    assert len(h) == k + 1 and st["iterations_run"] == k + 1
+    assert st["last_flips"] == hist[k]
+    np.testing.assert_allclose(v, v_ref, rtol=1e-11, atol=1e-12)
+    # a threshold equal to the count does not stop there (the rule is strict)
+    frac = hist[k] / N
+    v_ref, h = hand_evolve(I, phi0, 12, frac=frac)
+    v, mask, st = oracle.evolve(img, phi0, iterations=12, early_stop_frac=frac)
+    assert st["iterations_run"] == len(h) and len(h) > k + 1
+    assert st["last_flips"] == h[-1]
+    np.testing.assert_allclose(v, v_ref, rtol=1e-11, atol=1e-12)
