@@ -262,16 +262,25 @@ const char *lse_version(void);
  *   - W is a multiple of 4 and H * W <= LSE_STATIC_MAX_PIXELS (262144,
  *     e.g. 512 x 512); 1 <= B <= 4;
  *   - stats->elapsed_ms is -1 (timing would need CUDA events).
- * Anything else returns LSE_ERR_INVALID_ARG without touching the GPU, and
- * lse_last_error(NULL) says why.  The call allocates nothing: its scratch
- * (two LSF planes, per-block partial sums, the device statistics record,
- * about 2.7 MB) is a fixed array in the library's device memory that every
- * GPU which loads the library holds until the process exits.  The first
- * call on each device looks up that array's device address; make that
- * first call before capturing a stream.  All calls on a device share the
- * array: calls whose work overlaps on the GPU race and must be ordered by
- * the caller (one stream, or synchronisation).  Each call clears the parts
- * of the array that must start at zero. */
+ *   - stats must be NULL while `stream` is capturing (filling it
+ *     synchronises the stream).
+ * Anything else returns LSE_ERR_INVALID_ARG without launching work, and
+ * lse_last_error(NULL) says why; a failing CUDA call (the device query,
+ * the look-up of the array below, a launch) returns LSE_ERR_CUDA.
+ *
+ * The call allocates nothing itself: its scratch (two LSF planes, per-block
+ * partial sums, the device statistics record, about 2.7 MB) is a fixed
+ * array in the library's device memory that every GPU which loads the
+ * library holds until the process exits.  The first call on each device
+ * looks up that array's device address.  Under CUDA's lazy module loading
+ * that first look-up, and the first launch of each kernel, load the
+ * library's device code, and loading reserves device memory (the array
+ * included); a caller that must never allocate therefore makes one warm-up
+ * call on each device at start-up, before capturing any stream.  All calls
+ * on a device share the array and it keeps the last call's contents: calls
+ * whose work overlaps on the GPU race and must be ordered by the caller
+ * (one stream, or synchronisation).  Each call clears the parts of the
+ * array that must start at zero. */
 #define LSE_STATIC_MAX_PIXELS 262144
 lse_status lse_evolve_static(const float *image, int H, int W, int B,
                              const float *g, const float *phi0,

@@ -138,10 +138,22 @@ extern "C" lse_status lse_evolve_static(const float *image, int H, int W, int B,
     if (!aligned16(data))
         return fail("lse_evolve_static: image / g must be 16-byte aligned");
     int sm_count = 0;
-    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: SM count");
+    if (sm_count < 1) return fail("lse_evolve_static: device %d reports %d SMs", dev, sm_count);
     if (partials_needed(sm_count) > kMaxPartials)
         return fail("lse_evolve_static: %d SMs need more partial sums than the fixed %d",
                     sm_count, kMaxPartials);
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (stats) {
+        // reading the statistics synchronises the stream, which a capture forbids
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(s, &cap);
+        if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: stream capture status");
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail("lse_evolve_static: stats must be NULL while the stream is capturing");
+    }
 
     unsigned char *scratch = scratch_on(dev, &e);
     if (!scratch) return cuda_fail(e, "lse_evolve_static: cudaGetSymbolAddress");
@@ -149,24 +161,28 @@ extern "C" lse_status lse_evolve_static(const float *image, int H, int W, int B,
                      reinterpret_cast<float *>(scratch) + kPlane};
     LsePartial *partials = reinterpret_cast<LsePartial *>(scratch + kPartialOff);
     LseDevState *st = reinterpret_cast<LseDevState *>(scratch + kStateOff);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    // the step's kernel and work decomposition, decided before any GPU work
+    const int pitch = W;
+    const size_t band_stride = (size_t)H * W;
+    StepPlan plan;
+    if (!plan_step(H, W, B, p, pitch, band_stride, data, phi, st, partials, sm_count,
+                   step_form_from_env(),
+                   tile_nw_from_env() ? tile_nw_from_env()
+                                      : tile_nw_default_for(H, W, p.ts, sm_count),
+                   nullptr, &plan))
+        return fail("lse_evolve_static: no step kernel for this shape (LSE_STEP_KERNEL "
+                    "narrowed the choice, or its tensor maps could not be encoded)");
 
     // the ticket and the counters of the statistics record start at zero
     e = cudaMemsetAsync(st, 0, sizeof(LseDevState), s);
     if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: clear state");
-    const int pitch = W;
-    const size_t band_stride = (size_t)H * W;
     const int nred = sm_count * 4;
     e = launch_prologue(region ? data : nullptr, pitch, band_stride, phi0,
                         region ? nullptr : g, W, phi[0], nullptr, pitch, H, W, B,
                         p.term, p.dt, LSE_F32, st, partials, nred, s);
     if (e != cudaSuccess) return cuda_fail(e, "lse_evolve_static: prologue");
 
-    StepPlan plan;
-    (void)plan_step(H, W, B, p, pitch, band_stride, data, phi, st, partials, sm_count,
-              step_form_from_env(),
-              tile_nw_from_env() ? tile_nw_from_env() : tile_nw_default_for(H, W, p.ts, sm_count),
-              nullptr, &plan);
     for (int n = 0; n < p.iterations; ++n) {
         if (region && B > 1) {
             e = launch_normaliser(data, pitch, band_stride, H, W, B, p.dt, st, partials,
