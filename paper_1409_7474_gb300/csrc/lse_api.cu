@@ -537,7 +537,17 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
     e = cudaEventRecord(ctx->ev0, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
     const bool bands_pass = plan.args.mb_split != 0;
-    for (int n = 0; n < p.iterations; ++n) {
+    // one band or the edge term on the tile form: every iteration in one
+    // persistent launch; otherwise (or when the grid cannot all be resident)
+    // one launch per step
+    bool persisted = false;
+    if (!bands_pass && !(region && B > 1)) {
+        e = launch_evolve(plan, ctx->sm_count, s);
+        if (e == cudaSuccess) persisted = true;
+        else if (e != cudaErrorNotSupported) return cuda_fail(ctx, e, "persistent evolution");
+        else cudaGetLastError();
+    }
+    for (int n = 0; n < p.iterations && !persisted; ++n) {
         if (bands_pass) {
             // statistics of the LSF this step reads (the prologue made the
             // first ones), then D and its maximum

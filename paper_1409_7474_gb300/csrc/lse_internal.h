@@ -54,6 +54,16 @@ struct alignas(16) LseDevState {
     int zero_force;             // next step's force is zero (degenerate rule)
     unsigned int status_bits;
     unsigned int ticket;        // last-CTA-done counter, reset by the last CTA
+    unsigned int grid_bar;      // arrivals at the persistent evolution's grid
+                                // barriers (zeroed before each such launch)
+    // tile-form steps: the sums over the new LSF as exact 64-bit fixed-point
+    // integers (value x 2^fix_k), added up with atomics in any order --
+    // sum w I, sum I, |{v >= 0}|, sign changes -- one slot per step in
+    // flight (one launch per step uses slot 0; the persistent evolution
+    // rotates three); and the tile queues the CTAs take tiles from
+    long long acc[3][4];
+    unsigned int tile_ctr[2];
+    int fix_k;
 };
 
 struct alignas(16) LsePartial {
@@ -112,6 +122,18 @@ struct StepArgs {
     unsigned long long stall_ns;
 };
 
+// The persistent evolution: every iteration of one image in one cooperative
+// launch of the tile form, the CTAs meeting at a grid barrier after each
+// step (lse_step_tile.cuh).  `a` holds the iteration-independent arguments;
+// the per-iteration flags are derived on the device.
+struct EvolveArgs {
+    StepArgs a;
+    float *phi[2];              // the ping-pong pair
+    int cap;                    // iterations to run
+    int reinit_period;
+    int early_stop;
+};
+
 // One image of a batched evolution (lse_evolve_batch, lse_server), in device
 // memory.  The CTAs [start, start + nblocks) of its class's step launch work
 // on it; vector images also own the normaliser CTAs [nstart, nstart +
@@ -144,22 +166,38 @@ __host__ __device__ inline bool lse_reinit_after(int n, int period)
 // kernel can (`bin_out`), unless an early stop may make it the last one;
 // then it stores v and the next step binarises on load.  Sign changes are
 // counted for the early stop and on the last step.
-__host__ __device__ inline void lse_iteration_flags(StepArgs &a, int n, int cap,
-                                                    int reinit_period, bool early_stop,
-                                                    bool bin_out, float *const phi[2])
+struct LseStepFlags {
+    int store_bin, binary_in, binarise_in, count_flips;
+};
+
+__host__ __device__ inline LseStepFlags lse_step_flags(int n, int cap, int reinit_period,
+                                                       bool early_stop, bool bin_out)
 {
     auto stores_bin = [&](int k) {
         return bin_out && lse_reinit_after(k, reinit_period) && k < cap - 1 && !early_stop;
     };
+    LseStepFlags f;
+    f.store_bin = stores_bin(n) ? 1 : 0;
+    f.binary_in = (n > 0 && stores_bin(n - 1)) ? 1 : 0;
+    f.binarise_in =
+        (n > 0 && lse_reinit_after(n - 1, reinit_period) && !stores_bin(n - 1)) ? 1 : 0;
+    f.count_flips = (early_stop || n == cap - 1) ? 1 : 0;
+    return f;
+}
+
+__host__ __device__ inline void lse_iteration_flags(StepArgs &a, int n, int cap,
+                                                    int reinit_period, bool early_stop,
+                                                    bool bin_out, float *const phi[2])
+{
+    const LseStepFlags f = lse_step_flags(n, cap, reinit_period, early_stop, bin_out);
     a.iter = n;
     a.phi_in = phi[n & 1];
     a.phi_out = phi[(n + 1) & 1];
     a.out_buf = (n + 1) & 1;
-    a.store_bin = stores_bin(n) ? 1 : 0;
-    a.binary_in = (n > 0 && stores_bin(n - 1)) ? 1 : 0;
-    a.binarise_in =
-        (n > 0 && lse_reinit_after(n - 1, reinit_period) && !stores_bin(n - 1)) ? 1 : 0;
-    a.count_flips = (early_stop || n == cap - 1) ? 1 : 0;
+    a.store_bin = f.store_bin;
+    a.binary_in = f.binary_in;
+    a.binarise_in = f.binarise_in;
+    a.count_flips = f.count_flips;
     a.reinit_u = 0;
     if (a.order == LSE_ORDER_TABLE1) {
         // Table I: the re-initialisation (step 3) acts on u, before the
@@ -255,6 +293,11 @@ bool tile_boxes_aligned(int rad, int elem_bytes);
 cudaError_t launch_step_tile(const StepArgs &a, const CUtensorMap &phi_map,
                              const CUtensorMap &data_map, int nblocks, cudaStream_t s);
 int partials_needed(int sm_count);
+// The persistent evolution of the tile form (one band or the edge term):
+// cudaErrorNotSupported, with nothing launched, when the call cannot take it.
+cudaError_t launch_evolve_tile(const EvolveArgs &e, const CUtensorMap &pm0,
+                               const CUtensorMap &pm1, const CUtensorMap &dm, int nblocks,
+                               int sm_count, cudaStream_t s);
 
 // Batched launches (lse_evolve_batch): iteration n over every image of one
 // class; CTA blockIdx.x works on image blk_item[blockIdx.x].  Step kernels
@@ -305,6 +348,10 @@ bool plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_
                float *dplane, StepPlan *plan);
 // Launches iteration n (0-based) of the plan.
 cudaError_t launch_step(StepPlan &plan, int n, cudaStream_t s);
+// Launches every iteration of the plan as one persistent evolution when the
+// plan is of the tile form and LSE_PERSIST is not "0"; cudaErrorNotSupported
+// (nothing launched) otherwise, and the caller launches one step at a time.
+cudaError_t launch_evolve(StepPlan &plan, int sm_count, cudaStream_t s);
 // Sets the message lse_last_error(NULL) returns (calls without a context).
 void set_contextless_error(const char *msg);
 

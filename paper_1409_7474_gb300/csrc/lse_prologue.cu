@@ -208,6 +208,11 @@ prologue_kernel(const void *__restrict__ img, int img_pitch, size_t band_stride,
         st->done = 0;
         st->last_buf = 0;
         st->norm_used = 0.0;
+        st->grid_bar = 0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 4; ++j) st->acc[i][j] = 0;
+        st->tile_ctr[0] = st->tile_ctr[1] = 0;
+        st->fix_k = lse_fix_scale(fmax(fabs((double)t.fmin), fabs((double)t.fmax)), n);
         if (term == LSE_TERM_REGION) {
             lse_region_coeffs_v(st, t, B, dt, n, t.fmin, t.fmax);
         } else {
@@ -415,8 +420,10 @@ cudaError_t launch_output(float *const *bufs, int pitch, int H, int W, int stora
 int partials_needed(int sm_count)
 {
     // the widest reducing launch: 3 CTAs of 8 warps or 6 of 4 warps per SM
-    // (tile-form step) or 8 CTAs of 256 threads per SM (grid-stride kernels)
-    return sm_count * 8;
+    // (tile-form step) or 8 CTAs of 256 threads per SM (grid-stride kernels);
+    // the persistent evolution keeps two sets (step n and step n + 1) of up
+    // to 6 per SM
+    return sm_count * 12;
 }
 
 }  // namespace lse_detail

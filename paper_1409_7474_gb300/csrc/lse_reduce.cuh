@@ -356,6 +356,109 @@ __device__ __forceinline__ void lse_sum_partials(const LsePartial *partials,
     lse_cta_reduce<MAXW, PAR>(a, nb, total);
 }
 
+// Exact sums for the tile form.  A lane's sums over one tile are FP32
+// values x with |x| <= 32 max|I| (at most 28 pixels); round(x 2^k) is taken
+// from the bits of x with integer operations only and added up as 64-bit
+// integers.  Integer addition is associative, so the totals do not depend on
+// which CTA took which tile nor on the order of the additions, and the
+// statistics are the same bits however the tiles are scheduled.  k is chosen
+// per call (lse_fix_scale) so that every total fits: the rounding is 2^-k,
+// about 2^-35 of max|I| at 2^26 pixels.
+__device__ __forceinline__ long long lse_fix(float x, int k)
+{
+    const unsigned int u = __float_as_uint(x);
+    const int e = (int)((u >> 23) & 255u);
+    if (e == 0 || e == 255) return 0;           // zero / subnormal (< one unit); never inf
+    const long long m = (long long)((u & 0x7FFFFFu) | 0x800000u);
+    const int sh = e - 150 + k;                 // |x| 2^k = m 2^sh
+    long long r;
+    if (sh >= 0) r = m << sh;
+    else if (sh >= -24) r = (m + (1ll << (-sh - 1))) >> (-sh);
+    else r = 0;
+    return (u >> 31) ? -r : r;
+}
+
+// The exponent k of lse_fix for N pixels of magnitude at most `maxabs`:
+// sums of N values below 2^62 once scaled, and a lane's partial (at most 32
+// values) too.
+__device__ __forceinline__ int lse_fix_scale(double maxabs, long long n)
+{
+    if (!(maxabs > 0.0) || !isfinite(maxabs)) return 30;
+    int e;
+    const double f = frexp((double)(n > 32 ? n : 32) * maxabs, &e);   // f in [0.5, 1)
+    const int ceil_log2 = f == 0.5 ? e - 1 : e;
+    int k = 61 - ceil_log2;
+    return k < -120 ? -120 : (k > 120 ? 120 : k);
+}
+
+// The totals of a tile-form step from the fixed-point sums (slot of the
+// state record): sum I over v >= 0 and over v < 0, the count and the sign
+// changes.
+__device__ __forceinline__ void lse_fix_totals(long long sw, long long sa, long long np,
+                                               long long fl, int k, LseAcc &t)
+{
+    t.clear();
+    t.sp[0] = ldexp((double)(sa + sw), -(k + 1));
+    t.sm[0] = ldexp((double)(sa - sw), -(k + 1));
+    t.n_plus = np;
+    t.flips = fl;
+}
+
+// Sums NV 64-bit integers over the CTA (warp shuffles, then the warps in
+// index order); the totals are valid in thread 0.
+template <int NV, int MAXW>
+__device__ __forceinline__ void lse_cta_sum_i64(long long (&v)[NV])
+{
+    __shared__ long long s_v[MAXW][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum_ll(v[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s_v[warp][k] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            long long t = 0;
+            for (int w = 0; w < MAXW; ++w) t += s_v[w][k];
+            v[k] = t;
+        }
+    }
+    __syncthreads();
+}
+
+// Means of one band over the two sides (Eq. 15) and the factors of the data
+// term D = alpha (I - mid), alpha = 2 (c+ - c-), mid = (c+ + c-) / 2
+// (Eq. 17's numerator).  Explicit round-to-nearest operations: every kernel
+// that makes these coefficients (the last CTA of a step, every CTA of the
+// persistent evolution, the band statistics pass) gets the same bits.
+__device__ __forceinline__ void lse_band_coeffs(double sp, double sm, long long np, long long nm,
+                                                double &cp, double &cm, double &al, double &md)
+{
+    cp = np > 0 ? __ddiv_rn(sp, (double)np) : 0.0;
+    cm = nm > 0 ? __ddiv_rn(sm, (double)nm) : 0.0;
+    al = __dmul_rn(2.0, __dsub_rn(cp, cm));
+    md = __dmul_rn(0.5, __dadd_rn(cp, cm));
+}
+
+// One band: the normaliser M = |c+ - c-| max(|2 Imax - s|, |2 Imin - s|),
+// s = c+ + c-, and the step coefficient dt alpha / (2 M).  Returns false
+// when M is not positive (zero force).
+__device__ __forceinline__ bool lse_norm_one_band(double cp, double cm, double al, double imin,
+                                                  double imax, float dt, double &norm, float &a0)
+{
+    const double s = __dadd_rn(cp, cm);
+    const double M = __dmul_rn(fabs(__dsub_rn(cp, cm)),
+                               fmax(fabs(__dsub_rn(__dmul_rn(2.0, imax), s)),
+                                    fabs(__dsub_rn(__dmul_rn(2.0, imin), s))));
+    if (!(M > 0.0)) return false;
+    norm = M;
+    a0 = __double2float_rn(__ddiv_rn(__dmul_rn((double)dt, al), __dmul_rn(2.0, M)));
+    return true;
+}
+
 // Region statistics of the current LSF -> c+/c- and the coefficients of the
 // next step (Eqs. 15 and 17).  For one band the normaliser has the closed
 // form M = |c+ - c-| max(|2 Imax - c+ - c-|, |2 Imin - c+ - c-|) (|2I - s|
@@ -372,18 +475,16 @@ __device__ __forceinline__ void lse_region_coeffs_v(LseDevState *st, const LseAc
     const long long nm = N - np;
     double contrast = 0.0, scale = 0.0, cp0 = 0.0, cm0 = 0.0, al0 = 0.0;
     for (int b = 0; b < B; ++b) {
-        const double cp = np > 0 ? t.sp[b] / (double)np : 0.0;
-        const double cm = nm > 0 ? t.sm[b] / (double)nm : 0.0;
-        const double al = 2.0 * (cp - cm);
-        const double md = 0.5 * (cp + cm);
+        double cp, cm, al, md;
+        lse_band_coeffs(t.sp[b], t.sm[b], np, nm, cp, cm, al, md);
         st->run_sp[b] = t.sp[b];
         st->run_sm[b] = t.sm[b];
         st->c_plus[b] = cp;
         st->c_minus[b] = cm;
         st->alpha[b] = al;
         st->mid[b] = md;
-        st->af[b] = (float)al;
-        st->m[b] = (float)md;
+        st->af[b] = __double2float_rn(al);
+        st->m[b] = __double2float_rn(md);
         contrast = fmax(contrast, fabs(cp - cm));
         scale = fmax(scale, fabs(cp) + fabs(cm));
         if (b == 0) {
@@ -396,15 +497,9 @@ __device__ __forceinline__ void lse_region_coeffs_v(LseDevState *st, const LseAc
     int zero = (np == 0 || nm == 0 || contrast <= LSE_CONTRAST_TOL * scale);
     double norm = 0.0;
     float a0 = 0.0f;
-    if (!zero && B == 1) {
-        const double s = cp0 + cm0;
-        const double M = fabs(cp0 - cm0) * fmax(fabs(2.0 * imax - s), fabs(2.0 * imin - s));
-        if (!(M > 0.0)) {
-            zero = 1;
-        } else {
-            norm = M;
-            a0 = (float)((double)dt * al0 / (2.0 * M));
-        }
+    if (!zero && B == 1 && !lse_norm_one_band(cp0, cm0, al0, imin, imax, dt, norm, a0)) {
+        zero = 1;
+        norm = 0.0;
     }
     st->norm = norm;
     if (zero) {

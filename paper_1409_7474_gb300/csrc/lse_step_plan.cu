@@ -6,6 +6,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "lse_internal.h"
 
 namespace {
@@ -57,9 +59,60 @@ bool encode_box(CUtensorMap *m, const void *base, int storage, int W, int H, int
     return r == CUDA_SUCCESS;
 }
 
+// Persistent evolutions run one at a time on a device, in the order they
+// were enqueued, whatever their streams: two of them resident together could
+// each hold part of the SMs while their grid barriers wait for CTAs that
+// cannot become resident.  Each one waits on an event the previous one
+// recorded (not under stream capture, where the graph's own order applies).
+constexpr int kMaxDev = 64;
+std::mutex g_coop_mutex;
+cudaEvent_t g_coop_event[kMaxDev];
+
+bool persist_enabled()
+{
+    const char *v = getenv("LSE_PERSIST");
+    return !(v && strcmp(v, "0") == 0);
+}
+
 }  // namespace
 
 namespace lse_detail {
+
+cudaError_t launch_evolve(StepPlan &plan, int sm_count, cudaStream_t s)
+{
+    if (plan.form != LSE_FORM_TILE || plan.args.mb_split || !persist_enabled())
+        return cudaErrorNotSupported;
+    EvolveArgs e;
+    e.a = plan.args;
+    e.phi[0] = plan.phi[0];
+    e.phi[1] = plan.phi[1];
+    e.cap = plan.iterations;
+    e.reinit_period = plan.reinit_period;
+    e.early_stop = plan.early_stop ? 1 : 0;
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorNotSupported;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    err = cudaStreamIsCapturing(s, &cs);
+    if (err != cudaSuccess) return err;
+    const bool chain = cs == cudaStreamCaptureStatusNone;
+    std::lock_guard<std::mutex> lock(g_coop_mutex);
+    if (chain && !g_coop_event[dev]) {
+        err = cudaEventCreateWithFlags(&g_coop_event[dev], cudaEventDisableTiming);
+        if (err != cudaSuccess) {
+            g_coop_event[dev] = nullptr;
+            return err;
+        }
+        err = cudaEventRecord(g_coop_event[dev], s);
+        if (err != cudaSuccess) return err;
+    }
+    if (chain && (err = cudaStreamWaitEvent(s, g_coop_event[dev], 0)) != cudaSuccess) return err;
+    err = launch_evolve_tile(e, plan.phi_maps[0], plan.phi_maps[1], plan.data_map, plan.nblocks,
+                             sm_count, s);
+    if (err != cudaSuccess) return err;
+    return chain ? cudaEventRecord(g_coop_event[dev], s) : cudaSuccess;
+}
 
 void gauss_taps(double sigma, int rad, double *out)
 {

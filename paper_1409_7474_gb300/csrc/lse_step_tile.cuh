@@ -258,11 +258,55 @@ __device__ __forceinline__ float4 lds4(const float *p)
     return *reinterpret_cast<const float4 *>(p);
 }
 
+// What one step of the persistent evolution (all iterations in one launch)
+// passes to tile_step and gets back.
+struct TilePersist {
+    LseStepFlags f;             // the step's flags (lse_step_flags)
+    float *phi_out;             // the LSF plane the step writes
+    unsigned long long stall_ns;   // test hook, first step only
+    float coef, mid;            // step coefficients (every CTA computed them)
+    uint32_t par;               // mbarrier parity, carried from step to step
+    int issued;                 // boxes of the first tile already issued:
+                                // 0 none, 1 data (prefetched), 2 data and phi
+    int prefetch;               // issue the next step's first data box at the end
+    int slot;                   // the state record's sum slot of the step
+    int queue;                  // the tile queue of the step
+};
+
+// The 128-byte aligned base (in floats) of the dynamic shared memory, the
+// table of square roots the FAST code reads, and the mbarriers.  Once per
+// CTA, before any box is issued.
+template <int RAD, class T, int NW>
+__device__ __forceinline__ void tile_smem_init()
+{
+    extern __shared__ float smem_f[];
+    const uint32_t sm0 = smem_u32(smem_f);
+    const int sb = (int)(((128u - (sm0 & 127u)) & 127u) >> 2);
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        // sqrt table indexed by bits(q) >> 21 & 31 for q in {0,4,8,16,20,32}
+        const float q = tid == 4 ? 4.f : tid == 8 ? 8.f : tid == 12 ? 16.f
+                      : tid == 13 ? 20.f : tid == 16 ? 32.f : 0.f;
+        smem_f[sb + tid] = sqrtf(q);
+    }
+    if (tid == 0) {
+        const uint32_t bar_phi = sm0 + 4u * (uint32_t)(sb + 32);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_phi) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_phi + 8) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_phi + 16) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+}
+
 // One step over the tiles of one image, run by CTA `cta` of the `ncta` CTAs
-// given to it.
-template <int KIND_EDGE, int RAD, bool FAST, class T, int NW>
-__device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *phi_map,
-                                          const CUtensorMap *data_map, int cta, int ncta)
+// given to it.  PERSIST: one step of the persistent evolution (pc holds the
+// coefficients and the box state; the CTA's reduced sums go to ps->slot and
+// nothing is finalised here); returns whether a wait ran out.
+template <int KIND_EDGE, int RAD, bool FAST, class T, int NW, bool PERSIST = false>
+__device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *phi_map,
+                                          const CUtensorMap *data_map, int cta, int ncta,
+                                          TilePersist *ps = nullptr)
 {
     using G = TileGeo<RAD, T, NW>;
     constexpr int kThreads = G::THREADS, kURows = G::UR, kPhiRows = G::PHI_ROWS;
@@ -271,7 +315,9 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
     constexpr bool EDGE = KIND_EDGE != 0;
 
     LseDevState *st = a.st;
-    if (st->done || (st->status_bits & LSE_SBIT_ABORT)) return;
+    if constexpr (!PERSIST) {
+        if (st->done || (st->status_bits & LSE_SBIT_ABORT)) return false;
+    }
 
     extern __shared__ float smem_f[];
     const uint32_t sm0 = smem_u32(smem_f);
@@ -295,48 +341,76 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
     const int H = a.H, W = a.W;
     const int tiles_x = a.n_strips, n_tiles = a.n_items;
 
-    if (FAST && tid < 32) {
-        // sqrt table indexed by bits(q) >> 21 & 31 for q in {0,4,8,16,20,32}
-        const float q = tid == 4 ? 4.f : tid == 8 ? 8.f : tid == 12 ? 16.f
-                      : tid == 13 ? 20.f : tid == 16 ? 32.f : 0.f;
-        lut[tid] = sqrtf(q);
+    if constexpr (!PERSIST) {
+        if (FAST && tid < 32) {
+            // sqrt table indexed by bits(q) >> 21 & 31 for q in {0,4,8,16,20,32}
+            const float q = tid == 4 ? 4.f : tid == 8 ? 8.f : tid == 12 ? 16.f
+                          : tid == 13 ? 20.f : tid == 16 ? 32.f : 0.f;
+            lut[tid] = sqrtf(q);
+        }
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_phi) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_dat) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_never) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
     }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_phi) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_dat) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_never) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
 
     float tp[RAD + 1];
 #pragma unroll
     for (int k = 0; k <= RAD; ++k) tp[k] = a.taps[k];
     // edge term: dt / 2 (t = dt g / 2); the D plane of a vector image: the
     // coefficient its band pass left, dt / (2 M)
-    const float coef = EDGE ? (a.mb_split ? st->a[0] : a.half_dt) : st->a[0];
-    const float mid = EDGE ? 0.0f : st->m[0];
+    const float coef = PERSIST ? ps->coef : EDGE ? (a.mb_split ? st->a[0] : a.half_dt) : st->a[0];
+    const float mid = PERSIST ? ps->mid : EDGE ? 0.0f : st->m[0];
     const f2 coef2 = f2_pack(coef, coef), mid2 = f2_pack(mid, mid);
     const float sqrt8 = sqrtf(8.0f);
-    const bool binarise_in = !FAST && a.binarise_in != 0;
-    const bool count_flips = !FAST && a.count_flips != 0;
-    const bool store_bin = FAST || a.store_bin != 0;
+    const bool binarise_in = !FAST && (PERSIST ? ps->f.binarise_in : a.binarise_in) != 0;
+    const bool count_flips = !FAST && (PERSIST ? ps->f.count_flips : a.count_flips) != 0;
+    const bool store_bin = FAST || (PERSIST ? ps->f.store_bin : a.store_bin) != 0;
+    const unsigned long long stall_ns = PERSIST ? ps->stall_ns : a.stall_ns;
+    float *const phi_out = PERSIST ? ps->phi_out : a.phi_out;
 
     auto origin = [&](int t, int &xs, int &ys) {
         const int ty = t / tiles_x;
         xs = (t - ty * tiles_x) * G::USEFUL - 4 * HL;   // first staged data column
         ys = ty * TH - (RAD + 1);                        // first staged phi row
     };
-    auto load_tile = [&](int t) {
+    auto load_phi = [&](int t) {
         int xs, ys;
         origin(t, xs, ys);
         tma_box(phi_dst, phi_map, xs - 4, ys, bar_phi, kPhiBytes);
+    };
+    auto load_data = [&](int t) {
+        int xs, ys;
+        origin(t, xs, ys);
         tma_box(dat_dst, data_map, xs - G::DATA_X0, ys + 1, bar_dat, kDatBytes);
     };
+    auto load_tile = [&](int t) {
+        load_phi(t);
+        load_data(t);
+    };
 
+    // tile order.  Region term: the first tile of CTA c is tile c, the rest
+    // are taken from a queue as the CTAs get to them (the three CTAs sharing
+    // an SM run at different speeds, so equal static shares finish far
+    // apart); the statistics are exact integer sums, the same whoever takes
+    // a tile.  Edge term: CTA c takes tiles c, c + ncta, ... (the queue
+    // measured slower there: 143.8 against 135.0 us per 8192 x 8192 step).
+    constexpr bool QUEUE = !EDGE;
+    unsigned int *const queue = &st->tile_ctr[PERSIST ? ps->queue : 0];
+    __shared__ int s_next;
+    const int fix_k = st->fix_k;
     int t = cta;
-    if (tid == 0 && t < n_tiles) load_tile(t);
-    uint32_t par = 0;
+    if (tid == 0 && t < n_tiles) {
+        if (!PERSIST || ps->issued == 0) {
+            load_tile(t);
+        } else if (ps->issued == 1) {
+            load_phi(t);
+        }
+    }
+    uint32_t par = PERSIST ? ps->par : 0u;
     bool failed = false;
 
     // 2 |{v >= 0}| over this lane's pixels: sum w + valid pixels.  fcnt is
@@ -344,7 +418,7 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
     // bits: a float to 64-bit conversion issues on the FP64 pipe
     long long cnt2 = 0;
     int nflip = 0;
-    float ksw = 0.0f, csw = 0.0f, ksa = 0.0f, csa = 0.0f;   // compensated lane sums
+    long long sw_x = 0, sa_x = 0;                // fixed-point lane sums (lse_fix)
     const bool lane_out = lane >= HL && lane < 32 - HL;
     const int eidx = lane == 0 ? 3 : 132;        // phi column beyond the warp's edge
     const T *bl = buf + 4 + 4 * lane;            // this lane's 4 columns of a phi row
@@ -355,11 +429,11 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
     // runs out into the TIMEOUT status; the first tile's copies, issued
     // above, are drained below like those of any failed wait
     // (the first step of an evolution never takes the FAST instantiation)
-    if (!FAST && a.stall_ns && t < n_tiles) {
-        (void)wait_bar(bar_never, 0, (uint32_t)a.stall_ns);
+    if (!FAST && stall_ns && t < n_tiles) {
+        (void)wait_bar(bar_never, 0, (uint32_t)stall_ns);
         failed = true;
     }
-    for (; t < n_tiles && !failed; t += ncta) {
+    for (; t < n_tiles && !failed;) {
         int xs, ys;
         origin(t, xs, ys);
         const int x0 = xs + 4 * lane;
@@ -367,6 +441,10 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
             failed = true;
             break;
         }
+        // take the next tile while this one is worked on: the claim stays
+        // in flight (nothing reads it) until the tile is done
+        unsigned int claim = 0;
+        if (QUEUE && tid == 0) claim = atomicAdd(queue, 1u);
         // tiles that touch column 0 or W - 1 (or lie partly outside) take the
         // border code; so do tiles whose u rows reach row 0 or H - 1
         const bool xborder = xs < 0 || xs + 128 >= W;
@@ -553,7 +631,7 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
             // x0 + 4 <= pitch whenever x0 < W (x0 and the pitch are multiples
             // of 4): the lane stores all 4 columns, the padding is scratch
             const bool st_ok = lane_out && x0 < W;
-            T *dst = reinterpret_cast<T *>(a.phi_out) + (size_t)(ys + RAD + 1 + r_first) * a.pitch + x0;
+            T *dst = reinterpret_cast<T *>(phi_out) + (size_t)(ys + RAD + 1 + r_first) * a.pitch + x0;
             const size_t pitch = (size_t)a.pitch;
             // the ring holds the lane's 4 columns of 2 RAD + 1 h rows as
             // column pairs, so each tap of the pass is one packed
@@ -629,18 +707,24 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
             else
                 vrows(std::false_type{});
             if (!EDGE && lane_out) {
-                lse_kahan_add(ksw, csw, fsw);
-                lse_kahan_add(ksa, csa, fsa);
+                sw_x += lse_fix(fsw, fix_k);
+                sa_x += lse_fix(fsa, fix_k);
             }
             int cv = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) cv += okf[j] != 0.0f ? 1 : 0;
             cnt2 += __float2int_rn(fcnt) + cv * rv;          // int, widened
         }
+        // every thread read the last claim before this tile's first barrier
+        if (tid == 0) s_next = QUEUE ? ncta + (int)claim : t + ncta;
         __syncthreads();
-        const int tn = t + ncta;
+        const int tn = s_next;
         if (tid == 0 && tn < n_tiles) load_tile(tn);
+        // the data term does not change between steps: the next step's
+        // first data box is in flight while the grid meets at its barrier
+        if (PERSIST && tid == 0 && tn >= n_tiles && ps->prefetch) load_data(cta);
         par ^= 1u;
+        t = tn;
     }
     if (NW == 4 && a.pdl) allow_next_grid();
     if (failed) {
@@ -649,27 +733,54 @@ __device__ __forceinline__ void tile_step(const StepArgs &a, const CUtensorMap *
         wait_bar(bar_phi, par);
         wait_bar(bar_dat, par);
     }
+    // the CTA's exact sums, added to the step's slot of the state record
+    long long v[4] = {sw_x, sa_x, cnt2 / 2, (long long)nflip};
+    lse_cta_sum_i64<4, NW>(v);
+    long long *slot = st->acc[PERSIST ? ps->slot : 0];
+    auto add_sums = [&]() {
+        unsigned long long *sl = reinterpret_cast<unsigned long long *>(slot);
+        if (!EDGE) {
+            atomicAdd(sl + 0, (unsigned long long)v[0]);
+            atomicAdd(sl + 1, (unsigned long long)v[1]);
+        }
+        atomicAdd(sl + 2, (unsigned long long)v[2]);
+        if (v[3]) atomicAdd(sl + 3, (unsigned long long)v[3]);
+    };
+    if constexpr (PERSIST) {
+        // ps is in shared memory: one writer (the caller synchronises)
+        if (tid == 0) {
+            ps->par = par;
+            ps->issued = (!failed && ps->prefetch) ? 1 : 0;
+            add_sums();
+        }
+        return failed;
+    }
 
-    // the fields the last CTA's finalisation reads, fetched while the CTA
-    // reduces
+    // the fields the last CTA's finalisation reads, fetched while the sums
+    // are added
+    __shared__ int s_last;
     LseStatePre pre;
-    if (tid == 0) pre = lse_state_pre(st);
-    LseAcc acc;
-    acc.clear();
-    const double dsw = lse_kahan_value(ksw, csw), dsa = lse_kahan_value(ksa, csa);
-    acc.sp[0] = 0.5 * (dsa + dsw);
-    acc.sm[0] = 0.5 * (dsa - dsw);
-    acc.n_plus = cnt2 / 2;
-    acc.flips = nflip;
-    const int nb = EDGE ? 0 : 1;
-    // FP64 shuffles here cost nothing measurable: the persistent CTAs finish
-    // at staggered times, and a float-float version was 0.4 % slower
-    LseAcc r;
-    lse_cta_reduce<NW>(acc, nb, &r);
-    if (!lse_publish_and_ticket_at(r, nb, a.partials, st, cta, ncta)) return;
-    LseAcc tot;
-    lse_sum_partials<NW>(a.partials, ncta, nb, &tot);
-    if (threadIdx.x == 0) lse_step_finalize(a, tot, pre);
+    if (tid == 0) {
+        pre = lse_state_pre(st);
+        add_sums();
+        __threadfence();
+        s_last = atomicAdd(&st->ticket, 1u) == (unsigned int)ncta - 1;
+    }
+    __syncthreads();
+    if (!s_last) return failed;
+    if (tid == 0) {
+        __threadfence();
+        // the totals, and the slot and the queue cleared for the next step
+        unsigned long long *sl = reinterpret_cast<unsigned long long *>(slot);
+        long long tot[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tot[j] = (long long)atomicExch(sl + j, 0ull);
+        if (QUEUE) *queue = 0;
+        LseAcc t;
+        lse_fix_totals(tot[0], tot[1], tot[2], tot[3], fix_k, t);
+        lse_step_finalize(a, t, pre);
+    }
+    return failed;
 }
 
 template <int KIND_EDGE, int RAD, bool FAST, class T, int NW>
@@ -680,6 +791,219 @@ step_tile_kernel(const __grid_constant__ StepArgs a,
 {
     if (NW == 4 && a.pdl) wait_prior_grid();
     tile_step<KIND_EDGE, RAD, FAST, T, NW>(a, &phi_map, &data_map, blockIdx.x, gridDim.x);
+}
+
+// FAST: the steady state of a re-initialising evolution.
+__host__ __device__ inline bool is_fast(const StepArgs &a)
+{
+    return a.binary_in && a.store_bin && !a.count_flips && !a.binarise_in;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier of the persistent evolution: arrival `target` - 1 of the
+// counter st->grid_bar (zeroed by the prologue) waits until `target` CTAs
+// have arrived.  The step's stores of the LSF (generic proxy) are ordered
+// before the arrival and the next step's TMA reads (async proxy) after the
+// wait, with the proxy fences on both sides.  Bounded: gives up after
+// LSE_WAIT_LIMIT polls or LSE_WAIT_NS, or as soon as another CTA has set an
+// abort bit, and then sets TIMEOUT.  Block-uniform result.
+__device__ __forceinline__ bool grid_barrier(LseDevState *st, unsigned int target)
+{
+    __shared__ int s_go;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        __threadfence();
+        atomicAdd(&st->grid_bar, 1u);
+        bool ok = false;
+        const uint32_t t0 = global_ns_lo();
+        for (uint32_t i = 0; i < LSE_WAIT_LIMIT; ++i) {
+            if (ld_acquire_u32(&st->grid_bar) >= target) {
+                ok = true;
+                break;
+            }
+            if ((i & 31u) == 31u) {
+                if (*reinterpret_cast<volatile unsigned int *>(&st->status_bits) &
+                    LSE_SBIT_ABORT)
+                    break;
+                if (global_ns_lo() - t0 > (uint32_t)LSE_WAIT_NS) break;
+            }
+        }
+        if (!ok) atomicOr(&st->status_bits, LSE_SBIT_TIMEOUT);
+        __threadfence();
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        s_go = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return s_go != 0;
+}
+
+// Coefficients of a step of the persistent evolution (every CTA holds them).
+struct PersistCoef {
+    float coef, mid;            // Eq. 18: t = coef (d - mid) (region), coef d (edge)
+    double norm;                // M of the step (region)
+    int zero;                   // the step's force is zero (degenerate rule)
+};
+
+// The end of step n in thread 0 of every CTA of the persistent evolution:
+// the grid-wide sums `t` over the new LSF give its statistics (Eq. 15) and
+// the next step's coefficients (Eq. 17, one band), with the arithmetic of
+// lse_step_finalize, so that one launch per step and the persistent
+// evolution agree bit for bit.  CTA 0 also records them in the state
+// record.  Returns whether the early stop ends the evolution here.
+template <bool EDGE>
+__device__ __forceinline__ bool persist_finalize(const StepArgs &a, int n, const LseAcc &t,
+                                                 PersistCoef &c, double imin, double imax,
+                                                 bool record)
+{
+    LseDevState *st = a.st;
+    unsigned int bits = t.bits;
+    const bool done = a.early_thresh > 0.0 && (double)t.flips < a.early_thresh;
+    if (!EDGE) {
+        if (c.zero) bits |= LSE_SBIT_DEGENERATE;
+        const double norm_used = c.zero ? 0.0 : c.norm;
+        const long long np = t.n_plus, nm = a.npix - np;
+        double cp, cm, al, md;
+        lse_band_coeffs(t.sp[0], t.sm[0], np, nm, cp, cm, al, md);
+        const double contrast = fmax(0.0, fabs(cp - cm));
+        const double scale = fmax(0.0, fabs(cp) + fabs(cm));
+        int zero = (np == 0 || nm == 0 || contrast <= LSE_CONTRAST_TOL * scale);
+        double norm = 0.0;
+        float a0 = 0.0f;
+        if (!zero && !lse_norm_one_band(cp, cm, al, imin, imax, a.dt, norm, a0)) {
+            zero = 1;
+            norm = 0.0;
+        }
+        c.coef = zero ? 0.0f : a0;
+        c.mid = __double2float_rn(md);
+        c.norm = norm;
+        c.zero = zero;
+        if (record) {
+            st->norm_used = norm_used;
+            st->run_sp[0] = t.sp[0];
+            st->run_sm[0] = t.sm[0];
+            st->c_plus[0] = cp;
+            st->c_minus[0] = cm;
+            st->alpha[0] = al;
+            st->mid[0] = md;
+            st->af[0] = __double2float_rn(al);
+            st->m[0] = c.mid;
+            st->area_plus = np;
+            st->norm = norm;
+            for (int b = 0; b < LSE_MAXB; ++b) st->a[b] = 0.0f;
+            if (!zero) st->a[0] = a0;
+            st->zero_force = zero;
+        }
+    } else if (record) {
+        st->area_plus = t.n_plus;
+    }
+    if (record) {
+        st->last_flips = t.flips;
+        st->iterations_run = n + 1;
+        st->last_buf = (n + 1) & 1;
+        if (bits) atomicOr(&st->status_bits, bits);
+        if (done) st->done = 1;
+    }
+    return done;
+}
+
+// Thread 0 of every CTA after the barrier of step n: the step's totals
+// (slot n mod 3) and the next coefficients; CTA 0 records them and clears
+// the slot and the tile queue of step n - 1 (every CTA read that slot
+// before it arrived at this barrier) for step n + 2.  A function of its
+// own: inline, its FP64 code pushed the tile loops into register spills.
+template <bool EDGE>
+__device__ __noinline__ void persist_sum(const StepArgs &a, int n, PersistCoef *coef, int *done,
+                                         bool record)
+{
+    LseDevState *st = a.st;
+    const volatile long long *sl = st->acc[n % 3];
+    LseAcc t;
+    lse_fix_totals(sl[0], sl[1], sl[2], sl[3], st->fix_k, t);
+    PersistCoef c = *coef;
+    *done = persist_finalize<EDGE>(a, n, t, c, st->imin, st->imax, record) ? 1 : 0;
+    *coef = c;
+    if (record) {
+        long long *old = st->acc[(n + 2) % 3];
+        old[0] = old[1] = old[2] = old[3] = 0;
+        st->tile_ctr[n & 1] = 0;
+    }
+}
+
+// Every iteration of one image in one cooperative launch (the grid is at
+// most the resident CTAs, so all of them run at once).  The CTAs take the
+// step's tiles from its queue and add their exact sums to its slot of the
+// state record; after the grid barrier every CTA reads the totals and makes
+// the next step's coefficients itself, with the arithmetic of the last CTA
+// of a one-step launch, so both give the same bits.  Each step takes the
+// FAST or the general instantiation as its flags say.
+template <int KIND_EDGE, int RAD, class T, int NW>
+__global__ void __launch_bounds__(TileGeo<RAD, T, NW>::THREADS, TileGeo<RAD, T, NW>::MIN_BLOCKS)
+evolve_tile_kernel(const __grid_constant__ EvolveArgs e,
+                   const __grid_constant__ CUtensorMap phi_map0,
+                   const __grid_constant__ CUtensorMap phi_map1,
+                   const __grid_constant__ CUtensorMap data_map)
+{
+    constexpr bool EDGE = KIND_EDGE != 0;
+    const StepArgs &a = e.a;
+    LseDevState *st = a.st;
+    // every CTA sees the prologue's record (the previous kernel in the stream)
+    if (st->done || (st->status_bits & LSE_SBIT_ABORT)) return;
+    // what lives from step to step is kept in shared memory, so that no
+    // register is held across the steps' tile loops
+    __shared__ TilePersist s_pc;
+    __shared__ PersistCoef s_coef;
+    __shared__ int s_done;
+    const int cta = blockIdx.x, ncta = gridDim.x;
+    if (threadIdx.x == 0) {
+        s_coef.coef = EDGE ? a.half_dt : st->a[0];
+        s_coef.mid = EDGE ? 0.0f : st->m[0];
+        s_coef.norm = st->norm;
+        s_coef.zero = st->zero_force;
+        s_pc.par = 0u;
+        s_pc.issued = 0;
+        s_pc.stall_ns = a.stall_ns;
+    }
+    tile_smem_init<RAD, T, NW>();   // ends with a CTA barrier
+    for (int n = 0; n < e.cap; ++n) {
+        if (threadIdx.x == 0) {
+            s_pc.f = lse_step_flags(n, e.cap, e.reinit_period, e.early_stop != 0, true);
+            s_pc.phi_out = e.phi[(n + 1) & 1];
+            s_pc.coef = s_coef.coef;
+            s_pc.mid = s_coef.mid;
+            s_pc.prefetch = n + 1 < e.cap;
+            s_pc.slot = n % 3;
+            s_pc.queue = n & 1;
+        }
+        __syncthreads();
+        const CUtensorMap *pm = (n & 1) ? &phi_map1 : &phi_map0;
+        const LseStepFlags f = s_pc.f;
+        if (f.binary_in && f.store_bin && !f.count_flips && !f.binarise_in)
+            tile_step<KIND_EDGE, RAD, true, T, NW, true>(a, pm, &data_map, cta, ncta, &s_pc);
+        else
+            tile_step<KIND_EDGE, RAD, false, T, NW, true>(a, pm, &data_map, cta, ncta, &s_pc);
+        if (threadIdx.x == 0) s_pc.stall_ns = 0;
+        if (!grid_barrier(st, (unsigned int)(n + 1) * (unsigned int)ncta)) break;
+        if (*reinterpret_cast<volatile unsigned int *>(&st->status_bits) & LSE_SBIT_ABORT) break;
+        if (threadIdx.x == 0) persist_sum<EDGE>(a, n, &s_coef, &s_done, cta == 0);
+        __syncthreads();
+        if (s_done) break;
+    }
+    // a data box prefetched for a step that did not run: wait for it
+    // (bounded) before the CTA exits
+    __syncthreads();
+    if (s_pc.issued == 1) {
+        extern __shared__ float smem_f[];
+        const uint32_t sm0 = smem_u32(smem_f);
+        const int sb = (int)(((128u - (sm0 & 127u)) & 127u) >> 2);
+        wait_bar(sm0 + 4u * (uint32_t)(sb + 32) + 8u, s_pc.par);
+    }
 }
 
 // Iteration n of a batch of images of one class (term, radius, storage): CTA
@@ -721,11 +1045,53 @@ cudaError_t launch_dependent(Kern kern, int nblocks, int threads, int smem, cuda
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-// FAST: the steady state of a re-initialising evolution.
-__host__ __device__ inline bool is_fast(const StepArgs &a)
+// The persistent evolution as one cooperative launch of `nblocks` CTAs;
+// cudaErrorNotSupported (nothing launched) when that many CTAs cannot all be
+// resident on the device's `sm_count` SMs.
+template <int KIND_EDGE, int RAD, class T, int NW>
+cudaError_t launch_evolve_one(const EvolveArgs &e, const CUtensorMap &pm0,
+                              const CUtensorMap &pm1, const CUtensorMap &dm, int nblocks,
+                              int sm_count, cudaStream_t s)
 {
-    return a.binary_in && a.store_bin && !a.count_flips && !a.binarise_in;
+    using G = TileGeo<RAD, T, NW>;
+    auto kern = evolve_tile_kernel<KIND_EDGE, RAD, T, NW>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           G::BYTES);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::THREADS, G::BYTES);
+    if (err != cudaSuccess) return err;
+    if ((long long)per_sm * sm_count < nblocks) return cudaErrorNotSupported;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(G::THREADS);
+    cfg.dynamicSmemBytes = G::BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, e, pm0, pm1, dm);
 }
+
+template <int KIND_EDGE, class T, int NW>
+cudaError_t launch_evolve_kind(const EvolveArgs &e, const CUtensorMap &pm0,
+                               const CUtensorMap &pm1, const CUtensorMap &dm, int nblocks,
+                               int sm_count, cudaStream_t s)
+{
+    switch (e.a.rad) {
+    case 1: return launch_evolve_one<KIND_EDGE, 1, T, NW>(e, pm0, pm1, dm, nblocks, sm_count, s);
+    case 2: return launch_evolve_one<KIND_EDGE, 2, T, NW>(e, pm0, pm1, dm, nblocks, sm_count, s);
+    case 3: return launch_evolve_one<KIND_EDGE, 3, T, NW>(e, pm0, pm1, dm, nblocks, sm_count, s);
+    case 4: return launch_evolve_one<KIND_EDGE, 4, T, NW>(e, pm0, pm1, dm, nblocks, sm_count, s);
+    case 5: return launch_evolve_one<KIND_EDGE, 5, T, NW>(e, pm0, pm1, dm, nblocks, sm_count, s);
+    case 6: return launch_evolve_one<KIND_EDGE, 6, T, NW>(e, pm0, pm1, dm, nblocks, sm_count, s);
+    case 7: return launch_evolve_one<KIND_EDGE, 7, T, NW>(e, pm0, pm1, dm, nblocks, sm_count, s);
+    default: return cudaErrorNotSupported;
+    }
+}
+
 
 template <int KIND_EDGE, int RAD, class T, int NW>
 cudaError_t launch_tile_one(const StepArgs &a, const CUtensorMap &pm, const CUtensorMap &dm,

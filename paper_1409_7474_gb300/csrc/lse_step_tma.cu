@@ -35,6 +35,25 @@ LSE_TILE_DECL(f16_region_nw4)
 LSE_TILE_DECL(f16_edge_nw8)
 LSE_TILE_DECL(f16_edge_nw4)
 #undef LSE_TILE_DECL
+// The persistent evolution, one file per storage type, term and tile height
+// (lse_evolve_tile_<storage>_<term>_nw<warps>.cu).
+#define LSE_EVOLVE_DECL(SUF)                                                           \
+    cudaError_t launch_evolve_tile_##SUF(const EvolveArgs &, const CUtensorMap &,      \
+                                         const CUtensorMap &, const CUtensorMap &, int, \
+                                         int, cudaStream_t);
+LSE_EVOLVE_DECL(f32_region_nw8)
+LSE_EVOLVE_DECL(f32_region_nw4)
+LSE_EVOLVE_DECL(f32_edge_nw8)
+LSE_EVOLVE_DECL(f32_edge_nw4)
+LSE_EVOLVE_DECL(bf16_region_nw8)
+LSE_EVOLVE_DECL(bf16_region_nw4)
+LSE_EVOLVE_DECL(bf16_edge_nw8)
+LSE_EVOLVE_DECL(bf16_edge_nw4)
+LSE_EVOLVE_DECL(f16_region_nw8)
+LSE_EVOLVE_DECL(f16_region_nw4)
+LSE_EVOLVE_DECL(f16_edge_nw8)
+LSE_EVOLVE_DECL(f16_edge_nw4)
+#undef LSE_EVOLVE_DECL
 
 }  // namespace lse_detail
 
@@ -180,6 +199,16 @@ const TileBatchFn kTileBatch[3][2][2] = {
     {{launch_step_tile_batch_bf16_region_nw8, launch_step_tile_batch_bf16_region_nw4},
      {launch_step_tile_batch_bf16_edge_nw8, launch_step_tile_batch_bf16_edge_nw4}}};
 
+typedef cudaError_t (*EvolveFn)(const EvolveArgs &, const CUtensorMap &, const CUtensorMap &,
+                                const CUtensorMap &, int, int, cudaStream_t);
+const EvolveFn kEvolve[3][2][2] = {
+    {{launch_evolve_tile_f32_region_nw8, launch_evolve_tile_f32_region_nw4},
+     {launch_evolve_tile_f32_edge_nw8, launch_evolve_tile_f32_edge_nw4}},
+    {{launch_evolve_tile_f16_region_nw8, launch_evolve_tile_f16_region_nw4},
+     {launch_evolve_tile_f16_edge_nw8, launch_evolve_tile_f16_edge_nw4}},
+    {{launch_evolve_tile_bf16_region_nw8, launch_evolve_tile_bf16_region_nw4},
+     {launch_evolve_tile_bf16_edge_nw8, launch_evolve_tile_bf16_edge_nw4}}};
+
 bool tile_index(int storage, int term, int nw, int *si, int *ti, int *ni)
 {
     *si = storage == LSE_F32 ? 0 : storage == LSE_F16 ? 1 : storage == LSE_BF16 ? 2 : -1;
@@ -198,6 +227,16 @@ cudaError_t launch_step_tile(const StepArgs &a, const CUtensorMap &phi_map,
     if (!tile_index(a.storage, a.mb_split ? LSE_TERM_EDGE : a.term, a.nw, &si, &ti, &ni))
         return cudaErrorNotSupported;
     return kTile[si][ti][ni](a, phi_map, data_map, nblocks, s);
+}
+
+cudaError_t launch_evolve_tile(const EvolveArgs &e, const CUtensorMap &pm0,
+                               const CUtensorMap &pm1, const CUtensorMap &dm, int nblocks,
+                               int sm_count, cudaStream_t s)
+{
+    int si, ti, ni;
+    if (e.a.mb_split || !tile_index(e.a.storage, e.a.term, e.a.nw, &si, &ti, &ni))
+        return cudaErrorNotSupported;
+    return kEvolve[si][ti][ni](e, pm0, pm1, dm, nblocks, sm_count, s);
 }
 
 cudaError_t launch_step_tile_batch(int storage, int term, int nw, int rad,
