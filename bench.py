@@ -14,9 +14,12 @@ Reported (one JSON line on rank 0):
                memory, copied by the library inside the timing (region and
                edge term on two streams, the edge evolution ordered after the
                region's, so copies overlap kernels);
-  roofline     the fused region step kernel: algorithmic bytes per launch
-               (12 B/px: read I, read phi, write v) / its mean duration from
-               CUDA events on the library's stream, against measured HBM;
+  roofline     the region evolution's kernel (one persistent launch for all
+               iterations on the tile form): algorithmic bytes per launch
+               (12 B/px per iteration: read I, read phi, write v) / its mean
+               duration from CUDA events on the library's stream, against
+               measured HBM; `gpu_launches` is the library's own count
+               (lse_kernel_launches) over the timed steps;
   cpu_baseline the FP64 oracle on the host cores, on crops of the same scene;
   storage_variants  the same workload with BF16 and F16 storage of the data
                term and the LSF (FP32 arithmetic, 6 B/px per region step);
@@ -487,10 +490,12 @@ def multiband_measurement(torch, lse, dev, iters: int, steps: int, peak: float):
     return out
 
 
-def kernel_profile(size: int, form: str):
-    """DRAM traffic per launch of the region step kernel from a committed ncu
-    summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", f"step_{form}_region_traffic.json")
+def kernel_profile(size: int, name: str, iterations: int):
+    """DRAM traffic per launch of the region kernel `name` from a committed ncu
+    summary (profiles/<name>_region_traffic.json), if it was taken on the
+    current kernel source; scaled to `size` x `size` pixels and `iterations`
+    steps per launch (traffic grows with both)."""
+    path = os.path.join(ROOT, "profiles", f"{name}_region_traffic.json")
     try:
         prof = json.load(open(path))
     except (OSError, ValueError):
@@ -501,8 +506,8 @@ def kernel_profile(size: int, form: str):
     digest = h.hexdigest()[:16]
     if prof.get("kernel_sha256_16") != digest:
         return None
-    per_px = prof["dram_bytes_per_launch"] / prof["pixels"]
-    return per_px * size * size
+    per_px_step = prof["dram_bytes_per_launch"] / prof["pixels"] / prof.get("iterations", 1)
+    return per_px_step * size * size * iterations
 
 
 def main():
@@ -563,6 +568,8 @@ def main():
     if world > 1:
         dist.barrier()
     step_ms_r, step_ms_e = [], []
+    launches0 = ctx_r.kernel_launches() + ctx_e.kernel_launches()
+    region_launches0 = ctx_r.kernel_launches()
     with ClockSampler(local) as clocks:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
@@ -575,23 +582,39 @@ def main():
             step_ms_e.append(ctx_e.stats()["elapsed_ms"])
         t1.record(stream)
         torch.cuda.synchronize()
+    launches = ctx_r.kernel_launches() + ctx_e.kernel_launches() - launches0
+    region_per_call = (ctx_r.kernel_launches() - region_launches0) // args.steps
     if world > 1:
         dist.barrier()
     ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
     st_r, st_e = ctx_r.stats(), ctx_e.stats()
     value = world * px_iters_per_step * args.steps / (ms / 1e3) / 1e6
 
-    step_kernel_ms = statistics.mean(step_ms_r) / iters
-    alg_bytes = BYTES_PER_PX_ITER * npx
-    achieved = alg_bytes / (step_kernel_ms / 1e3) / 1e9
+    # The region evolution's step kernel.  On the tile form every iteration
+    # runs in one persistent launch (prologue + 1 + output = 3 kernels per
+    # call); otherwise one launch per iteration.  The library's CUDA events
+    # bracket the iteration loop on its stream, so their time is the
+    # launch's (or the launches') own.
+    loop_ms = statistics.mean(step_ms_r)
+    step_kernel_ms = loop_ms / iters
+    alg_step = BYTES_PER_PX_ITER * npx
     edge_kernel_ms = statistics.mean(step_ms_e) / iters
+    persistent = region_per_call == 3
     form = step_form()
-    traffic = kernel_profile(size, form)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": f"step_{form}_kernel<region, r=4>", "peak_source": peak_src,
-                "bytes_per_launch": alg_bytes, "mean_launch_ms": step_kernel_ms,
-                "edge_kernel_frac": alg_bytes / (edge_kernel_ms / 1e3) / 1e9 / peak}
+    if persistent:
+        kname, per_launch = "evolve_tile", iters
+    else:
+        kname, per_launch = f"step_{form}", 1
+    roofline = {"bound": "hbm", "achieved": alg_step / (step_kernel_ms / 1e3) / 1e9,
+                "peak": peak, "unit": "GB/s",
+                "frac": alg_step / (step_kernel_ms / 1e3) / 1e9 / peak,
+                "traffic": kernel_profile(size, kname, per_launch),
+                "kernel": f"{kname}_kernel<region, r=4>", "peak_source": peak_src,
+                "iterations_per_launch": per_launch,
+                "bytes_per_launch": alg_step * per_launch,
+                "mean_launch_ms": step_kernel_ms * per_launch,
+                "bytes_per_step": alg_step, "step_ms": step_kernel_ms,
+                "edge_kernel_frac": alg_step / (edge_kernel_ms / 1e3) / 1e9 / peak}
 
     # e2e: the step's inputs (image, both initial LSFs) and results (v and
     # mask of both terms) are pinned host buffers passed to the C ABI, which
@@ -718,7 +741,6 @@ def main():
     if world > 1:
         dist.barrier()
     if rank == 0:
-        launches = args.steps * (2 * (iters + 2) + 1)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms / args.steps, "higher_is_better": True,

@@ -245,6 +245,15 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype,
  * call's stream; returns LSE_ERR_INVALID_ARG if no evolve has run yet. */
 lse_status lse_get_stats(lse_ctx *ctx, lse_stats *stats);
 
+/* The number of GPU kernels that lse_evolve and lse_precompute_edge calls
+ * on ctx have enqueued since lse_create (0 for NULL).  An evolution of one
+ * band or of the edge term on the tile form enqueues its prologue, one
+ * persistent kernel for all its iterations and its output kernel; other
+ * evolutions one step kernel per iteration (and two band passes per
+ * iteration for vector images).  A diagnostic: it lets a caller see which
+ * path ran. */
+unsigned long long lse_kernel_launches(const lse_ctx *ctx);
+
 /* Library version string, e.g. "0.1.0". */
 const char *lse_version(void);
 

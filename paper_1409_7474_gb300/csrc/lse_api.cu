@@ -162,6 +162,7 @@ lse_status stage_image(lse_ctx *ctx, const void *image, PtrKind kind,
         return r;
     cudaError_t e = launch_convert(src, dtype, H, W, B, ctx->img, pitch, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "convert image");
+    ++ctx->launches;
     *img_out = ctx->img;
     *pitch_out = pitch;
     *band_stride = (size_t)H * pitch;
@@ -257,7 +258,7 @@ void lse_destroy(lse_ctx *ctx)
     void *bufs[] = {ctx->phi[0], ctx->phi[1], ctx->img, ctx->gbuf, ctx->raw_in,
                     ctx->phi0_st, ctx->g_st, ctx->out_phi, ctx->out_mask, ctx->q16,
                     ctx->partials, ctx->st, ctx->arena, ctx->tables, ctx->tune_out,
-                    ctx->dplane};
+                    ctx->dplane, ctx->cand};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (ctx->st_host) cudaFreeHost(ctx->st_host);
@@ -330,6 +331,11 @@ lse_status lse_create(lse_ctx **out, int device, size_t max_pixels, int max_band
     return LSE_OK;
 }
 
+unsigned long long lse_kernel_launches(const lse_ctx *ctx)
+{
+    return ctx ? ctx->launches : 0ull;
+}
+
 lse_status lse_get_stats(lse_ctx *ctx, lse_stats *stats)
 {
     if (!ctx || !stats) return LSE_ERR_INVALID_ARG;
@@ -392,6 +398,7 @@ lse_status lse_precompute_edge(lse_ctx *ctx, const void *image, lse_dtype dtype,
     cudaError_t e = launch_edge(img, pitch, band_stride, H, W, B, taps, rad1,
                                 (double)edge_scale, dst, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "edge kernel");
+    ++ctx->launches;
     if (ko == PTR_HOST) {
         e = cudaMemcpyAsync(g_out, dst, (size_t)H * W * 4, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "copy g to host");
@@ -475,6 +482,7 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
         const int src_pitch = region ? pitch : g_src_pitch;
         e = launch_quantise(src, src_pitch, H, W, ctx->q16, pitch16, sto, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "quantise");
+        ++ctx->launches;
         data_s = ctx->q16;
         pitch = pitch16;
         band_stride = (size_t)H * pitch16;
@@ -510,10 +518,38 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
                         sto == LSE_F32 ? g_src_pitch : pitch, ctx->phi[0], g_dst, pitch, H,
                         W, B, p.term, p.dt, sto, ctx->st, ctx->partials, nred, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "prologue");
+    ++ctx->launches;
 
-    // vector images: the plane the band passes write D into, for the tile form
+    // vector images on the persistent evolution: the step stages the bands
+    // and forms D itself; M comes from candidate pixels found here, once
+    bool fused_bands = false;
+    if (region && B > 1 && ctx->step_form == LSE_FORM_AUTO &&
+        evolve_bands_applies(H, W, B, p)) {
+        void *cp = ctx->cand;
+        if ((r = ensure(ctx, &cp, &ctx->cand_cap, sizeof(LseCandidates), s, "candidates")) != LSE_OK)
+            return r;
+        ctx->cand = static_cast<LseCandidates *>(cp);
+        e = launch_mb_candidates(data, pitch, band_stride, H, W, B, ctx->cand, ctx->st,
+                                 ctx->sm_count, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "normaliser candidates");
+        ctx->launches += 2;
+        e = cudaEventRecord(ctx->ev0, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
+        e = launch_evolve_bands(H, W, B, p, pitch, band_stride, data, ctx->phi, ctx->st,
+                                ctx->cand, ctx->sm_count, s);
+        if (e == cudaSuccess) {
+            fused_bands = true;
+            ++ctx->launches;
+        } else if (e != cudaErrorNotSupported) {
+            return cuda_fail(ctx, e, "persistent evolution of the bands");
+        } else {
+            cudaGetLastError();
+        }
+    }
+    // vector images otherwise: the plane the band passes write D into, for
+    // the tile form
     float *dplane = nullptr;
-    if (region && B > 1 && sto == LSE_F32 && ctx->step_form == LSE_FORM_AUTO) {
+    if (!fused_bands && region && B > 1 && sto == LSE_F32 && ctx->step_form == LSE_FORM_AUTO) {
         if ((r = ensure_t(ctx, &ctx->dplane, &ctx->dplane_cap, (size_t)H * pitch, s, "D plane")) != LSE_OK)
             return r;
         dplane = ctx->dplane;
@@ -534,16 +570,21 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
         plan.args.stall_ns = ctx->test_stall_ns;
         ctx->test_stall_ns = 0;
     }
-    e = cudaEventRecord(ctx->ev0, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
-    const bool bands_pass = plan.args.mb_split != 0;
+    if (!fused_bands) {
+        e = cudaEventRecord(ctx->ev0, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
+    }
+    const bool bands_pass = !fused_bands && plan.args.mb_split != 0;
     // one band or the edge term on the tile form: every iteration in one
     // persistent launch; otherwise (or when the grid cannot all be resident)
     // one launch per step
-    bool persisted = false;
-    if (!bands_pass && !(region && B > 1)) {
+    bool persisted = fused_bands;
+    if (!persisted && !bands_pass && !(region && B > 1)) {
         e = launch_evolve(plan, ctx->sm_count, s);
-        if (e == cudaSuccess) persisted = true;
+        if (e == cudaSuccess) {
+            persisted = true;
+            ++ctx->launches;
+        }
         else if (e != cudaErrorNotSupported) return cuda_fail(ctx, e, "persistent evolution");
         else cudaGetLastError();
     }
@@ -551,21 +592,26 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
         if (bands_pass) {
             // statistics of the LSF this step reads (the prologue made the
             // first ones), then D and its maximum
-            if (n > 0)
+            if (n > 0) {
                 e = launch_band_stats(data, pitch, band_stride, ctx->phi, H, W, B, p.dt, ctx->st,
                                       ctx->partials, nred, s);
+                ++ctx->launches;
+            }
             if (e == cudaSuccess)
                 e = launch_band_dterm(data, pitch, band_stride, dplane, H, W, B, p.dt, ctx->st,
                                       ctx->partials, nred, s);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "band passes");
+            ++ctx->launches;
         } else if (region && B > 1) {
             e = launch_normaliser(data, pitch, band_stride, H, W, B, p.dt, ctx->st,
                                   ctx->partials, nred, s);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "normaliser");
+            ++ctx->launches;
         }
         e = launch_step(plan, n, s);
         plan.args.stall_ns = 0;
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step");
+        ++ctx->launches;
     }
     e = cudaEventRecord(ctx->ev1, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
@@ -574,9 +620,11 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
         e = launch_band_stats(data, pitch, band_stride, ctx->phi, H, W, B, p.dt, ctx->st,
                               ctx->partials, nred, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "band statistics");
+        ++ctx->launches;
     }
     e = launch_output(ctx->phi, pitch, H, W, sto, ctx->st, out_phi, out_mask, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "output");
+    ++ctx->launches;
     if (ko == PTR_HOST) {
         e = cudaMemcpyAsync(phi_out, out_phi, (size_t)H * W * 4, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "copy phi to host");

@@ -35,6 +35,8 @@ struct lse_ctx {
     size_t q16_cap = 0;
     float *dplane = nullptr;         // vector images: D of Eq. 17, one plane
     size_t dplane_cap = 0;
+    LseCandidates *cand = nullptr;   // vector images: the normaliser's candidates
+    size_t cand_cap = 0;
     float *out_phi = nullptr;
     size_t out_cap = 0;
     uint8_t *out_mask = nullptr;
@@ -45,6 +47,7 @@ struct lse_ctx {
     LseDevState *st_host = nullptr;  // pinned mirror
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool have_stats = false;
+    unsigned long long launches = 0; // kernels enqueued by lse_evolve / lse_precompute_edge
     int step_form = 0;               // LSE_STEP_KERNEL at creation (LSE_FORM_*)
     // tile form: warps per CTA (8: 64-row tiles, 4: 32-row) per shape class,
     // chosen by lse_autotune; for shapes it has not tuned, tile_nw_default

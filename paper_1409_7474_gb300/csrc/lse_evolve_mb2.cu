@@ -1,0 +1,15 @@
+// lse_evolve_mb2.cu -- instantiations of the persistent evolution of a
+// 2-band image (the vector region term of Eq. 17), FP32 storage, 32-row
+// tiles, every radius 1..7.
+#include "lse_step_tile.cuh"
+
+namespace lse_detail {
+
+cudaError_t launch_evolve_mb2(const EvolveArgs &e, const CUtensorMap &pm0,
+                               const CUtensorMap &pm1, const CUtensorMap &dm, int nblocks,
+                               int sm_count, cudaStream_t s)
+{
+    return lse_tile::launch_evolve_mb_bands<2>(e, pm0, pm1, dm, nblocks, sm_count, s);
+}
+
+}  // namespace lse_detail

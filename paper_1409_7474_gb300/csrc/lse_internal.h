@@ -58,10 +58,11 @@ struct alignas(16) LseDevState {
                                 // barriers (zeroed before each such launch)
     // tile-form steps: the sums over the new LSF as exact 64-bit fixed-point
     // integers (value x 2^fix_k), added up with atomics in any order --
-    // sum w I, sum I, |{v >= 0}|, sign changes -- one slot per step in
+    // sum w I_b, sum I_b, |{v >= 0}|, sign changes (lse_step_tile.cuh has
+    // the layout of a slot) -- one slot per step in
     // flight (one launch per step uses slot 0; the persistent evolution
     // rotates three); and the tile queues the CTAs take tiles from
-    long long acc[3][4];
+    long long acc[3][12];
     unsigned int tile_ctr[2];
     int fix_k;
 };
@@ -122,6 +123,24 @@ struct StepArgs {
     unsigned long long stall_ns;
 };
 
+// Vector images on the persistent evolution: M = max_x |D(x)| of Eq. 17,
+// D = sum_b alpha_b (I_b - mid_b), is the maximum of a linear function of
+// the pixel's colour, so it is reached at a vertex of the colour cloud's
+// convex hull.  The pixels that are largest and smallest along
+// LSE_MB_DIRS fixed directions seed a candidate set; every step takes M over
+// the candidates (FP64) and checks |D| at every pixel against it; a pixel
+// beyond it joins the candidates and the step is done again with its |D|.
+#define LSE_MB_DIRS 64
+#define LSE_MB_CAND 512
+struct LseCandidates {
+    unsigned long long key[2 * LSE_MB_DIRS];  // per direction: largest / smallest pixel
+    float val[LSE_MB_CAND][4];                // band values of each candidate
+    unsigned int amax_bits;                   // max |I_b| over the bands (float bits)
+    int count;
+    int redone;                               // steps done again (a pixel beyond M)
+    int pad;
+};
+
 // The persistent evolution: every iteration of one image in one cooperative
 // launch of the tile form, the CTAs meeting at a grid barrier after each
 // step (lse_step_tile.cuh).  `a` holds the iteration-independent arguments;
@@ -132,6 +151,7 @@ struct EvolveArgs {
     int cap;                    // iterations to run
     int reinit_period;
     int early_stop;
+    LseCandidates *cand;        // vector images: the normaliser's candidates
 };
 
 // One image of a batched evolution (lse_evolve_batch, lse_server), in device
@@ -298,6 +318,15 @@ int partials_needed(int sm_count);
 cudaError_t launch_evolve_tile(const EvolveArgs &e, const CUtensorMap &pm0,
                                const CUtensorMap &pm1, const CUtensorMap &dm, int nblocks,
                                int sm_count, cudaStream_t s);
+// Vector images (2-4 bands, FP32) on the persistent evolution: the candidate
+// seeds of the normaliser (once per image, after the prologue), and the
+// evolution itself (32-row tiles; dm maps the bands as one 3-D box).
+cudaError_t launch_mb_candidates(const float *bands, int pitch, size_t band_stride, int H,
+                                 int W, int B, LseCandidates *cand, LseDevState *st,
+                                 int sm_count, cudaStream_t s);
+cudaError_t launch_evolve_mb(const EvolveArgs &e, const CUtensorMap &pm0,
+                             const CUtensorMap &pm1, const CUtensorMap &dm, int nblocks,
+                             int sm_count, cudaStream_t s);
 
 // Batched launches (lse_evolve_batch): iteration n over every image of one
 // class; CTA blockIdx.x works on image blk_item[blockIdx.x].  Step kernels
@@ -352,6 +381,17 @@ cudaError_t launch_step(StepPlan &plan, int n, cudaStream_t s);
 // plan is of the tile form and LSE_PERSIST is not "0"; cudaErrorNotSupported
 // (nothing launched) otherwise, and the caller launches one step at a time.
 cudaError_t launch_evolve(StepPlan &plan, int sm_count, cudaStream_t s);
+// Vector images (2-4 bands, FP32, the listing's order, zero padding, TS
+// 3..15): the persistent evolution with the bands staged by the step
+// (32-row tiles), after launch_mb_candidates.  evolve_bands_applies says
+// whether a call can take it (LSE_PERSIST=0 says no);
+// launch_evolve_bands returns cudaErrorNotSupported, with nothing launched,
+// when the grid cannot be resident.
+bool evolve_bands_applies(int H, int W, int B, const lse_params &p);
+cudaError_t launch_evolve_bands(int H, int W, int B, const lse_params &p, int pitch,
+                                size_t band_stride, const float *bands, float *const phi[2],
+                                LseDevState *st, LseCandidates *cand, int sm_count,
+                                cudaStream_t s);
 // Sets the message lse_last_error(NULL) returns (calls without a context).
 void set_contextless_error(const char *msg);
 

@@ -210,7 +210,7 @@ prologue_kernel(const void *__restrict__ img, int img_pitch, size_t band_stride,
         st->norm_used = 0.0;
         st->grid_bar = 0;
         for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 4; ++j) st->acc[i][j] = 0;
+            for (int j = 0; j < 12; ++j) st->acc[i][j] = 0;
         st->tile_ctr[0] = st->tile_ctr[1] = 0;
         st->fix_k = lse_fix_scale(fmax(fabs((double)t.fmin), fabs((double)t.fmax)), n);
         if (term == LSE_TERM_REGION) {

@@ -114,6 +114,83 @@ cudaError_t launch_evolve(StepPlan &plan, int sm_count, cudaStream_t s)
     return chain ? cudaEventRecord(g_coop_event[dev], s) : cudaSuccess;
 }
 
+bool evolve_bands_applies(int H, int W, int B, const lse_params &p)
+{
+    return persist_enabled() && p.term == LSE_TERM_REGION && B >= 2 && B <= 4 &&
+           p.storage == LSE_F32 && p.order == LSE_ORDER_LISTING && p.padding == LSE_PAD_ZERO &&
+           p.ts >= 3 && p.ts <= 15 && (long long)H * W < 0xFFFFFFFFll;
+}
+
+cudaError_t launch_evolve_bands(int H, int W, int B, const lse_params &p, int pitch,
+                                size_t band_stride, const float *bands, float *const phi[2],
+                                LseDevState *st, LseCandidates *cand, int sm_count,
+                                cudaStream_t s)
+{
+    if (!evolve_bands_applies(H, W, B, p) || !cand) return cudaErrorNotSupported;
+    StepPlan plan;
+    StepArgs &a = plan.args;
+    memset(&a, 0, sizeof(a));
+    a.rad = (p.ts - 1) / 2;
+    a.storage = LSE_F32;
+    constexpr int kNw = 4;            // 32-row tiles: the bands of a tile fill the memory
+    if (!plan_step_tile(H, W, 1, LSE_TERM_EDGE, a.rad, kNw, sm_count, &a, &plan.nblocks))
+        return cudaErrorNotSupported;
+    a.H = H;
+    a.W = W;
+    a.B = B;
+    a.term = LSE_TERM_REGION;
+    double taps[16];
+    gauss_taps(p.sigma, a.rad, taps);
+    for (int k = 0; k < 16; ++k) a.taps[k] = k <= a.rad ? (float)taps[k] : 0.0f;
+    a.dt = p.dt;
+    a.half_dt = 0.5f * p.dt;
+    a.early_thresh = p.early_stop_frac > 0.0f ? (double)p.early_stop_frac * H * W : 0.0;
+    a.npix = (long long)H * W;
+    a.pitch = pitch;
+    a.band_stride = band_stride;
+    a.data = bands;
+    a.order = LSE_ORDER_LISTING;
+    a.pad = LSE_PAD_ZERO;
+    a.st = st;
+    a.pdl = 0;
+    const int urows = 8 * kNw;
+    if (!encode_box(&plan.phi_maps[0], phi[0], LSE_F32, W, H, pitch, 0, 1, 136, urows + 2) ||
+        !encode_box(&plan.phi_maps[1], phi[1], LSE_F32, W, H, pitch, 0, 1, 136, urows + 2) ||
+        !encode_box(&plan.data_map, bands, LSE_F32, W, H, pitch, band_stride, B, 128, urows))
+        return cudaErrorNotSupported;
+    EvolveArgs e;
+    e.a = a;
+    e.phi[0] = phi[0];
+    e.phi[1] = phi[1];
+    e.cap = p.iterations;
+    e.reinit_period = p.reinit_period;
+    e.early_stop = p.early_stop_frac > 0.0f ? 1 : 0;
+    e.cand = cand;
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorNotSupported;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    err = cudaStreamIsCapturing(s, &cs);
+    if (err != cudaSuccess) return err;
+    const bool chain = cs == cudaStreamCaptureStatusNone;
+    std::lock_guard<std::mutex> lock(g_coop_mutex);
+    if (chain && !g_coop_event[dev]) {
+        err = cudaEventCreateWithFlags(&g_coop_event[dev], cudaEventDisableTiming);
+        if (err != cudaSuccess) {
+            g_coop_event[dev] = nullptr;
+            return err;
+        }
+        err = cudaEventRecord(g_coop_event[dev], s);
+        if (err != cudaSuccess) return err;
+    }
+    if (chain && (err = cudaStreamWaitEvent(s, g_coop_event[dev], 0)) != cudaSuccess) return err;
+    err = launch_evolve_mb(e, plan.phi_maps[0], plan.phi_maps[1], plan.data_map, plan.nblocks,
+                           sm_count, s);
+    if (err != cudaSuccess) return err;
+    return chain ? cudaEventRecord(g_coop_event[dev], s) : cudaSuccess;
+}
+
 void gauss_taps(double sigma, int rad, double *out)
 {
     double total = 0.0;

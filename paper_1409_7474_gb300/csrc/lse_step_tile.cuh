@@ -125,7 +125,7 @@ struct Stor<__half> {
 // data box is the 128 tile columns.  16-bit storage: a TMA box must start on
 // 16 bytes, so the data box starts with phi's, 4 columns left of the tile
 // (136 wide), and h has its own FP32 buffer.
-template <int RAD, class T, int NW = 8>
+template <int RAD, class T, int NW = 8, int NB = 1>
 struct TileGeo {
     static constexpr int THREADS = 32 * NW;
     static constexpr int UR = kURowsPerWarp * NW;               // u / h rows per tile
@@ -138,7 +138,9 @@ struct TileGeo {
     static constexpr int DATA_W = WIDE ? 128 : kPhiW;           // staged data columns
     static constexpr int DATA_X0 = WIDE ? 0 : 4;                // tile column 0 within it
     static constexpr int PHI_BYTES = PHI_ROWS * kPhiW * (int)sizeof(T);
-    static constexpr int DATA_BYTES = UR * DATA_W * (int)sizeof(T);
+    // NB data planes (the bands of a vector image), one box each
+    static constexpr int PLANE = UR * DATA_W;                   // elements per data plane
+    static constexpr int DATA_BYTES = NB * PLANE * (int)sizeof(T);
     // offsets in floats: [sqrt table 32][2 mbarriers][old-sign words 64 x 4]
     // [phi][data][h (16-bit storage only)]
     static constexpr int SIGN_OFF = 64;
@@ -155,8 +157,11 @@ struct TileGeo {
     // the vertical pass reads h rows up to NW RPW - 1 + 2 RAD; past row
     // UR - 1 they lie in other shared memory (FP32) or are clamped (16-bit)
     static constexpr bool CLAMP_H = !WIDE && NW * RPW - 1 + 2 * RAD > UR - 1;
-    // CTAs per SM (launch bounds): 24 warps for RAD <= 4, else 16
-    static constexpr int MIN_BLOCKS = (RAD <= 4 ? 24 : 16) / NW;
+    // CTAs per SM (launch bounds): 24 warps for RAD <= 4, else 16; vector
+    // images as many as their shared memory allows (228 KB per SM)
+    static constexpr int MIN_BLOCKS =
+        NB == 1 ? (RAD <= 4 ? 24 : 16) / NW
+                : ((227 * 1024) / (BYTES + 3072) > 0 ? (227 * 1024) / (BYTES + 3072) : 1);
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -241,6 +246,21 @@ __device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap *map, in
         : "memory");
 }
 
+// One 3-D box load (x, y, plane 0 .. box depth - 1), issued by the calling
+// thread: the bands of a vector image in one copy.
+__device__ __forceinline__ void tma_box3(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                         uint32_t bar, uint32_t bytes)
+{
+    asm volatile(
+        "fence.proxy.async.shared::cta;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%4], %5;\n\t"
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %6}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar),
+          "r"(bytes), "r"(0)
+        : "memory");
+}
+
 __device__ __forceinline__ float bin(float v) { return v >= 0.0f ? 1.0f : -1.0f; }
 
 __device__ __forceinline__ float4 bin4(float4 v)
@@ -271,7 +291,18 @@ struct TilePersist {
     int prefetch;               // issue the next step's first data box at the end
     int slot;                   // the state record's sum slot of the step
     int queue;                  // the tile queue of the step
+    // vector images: D = sum_b af[b] (I_b - m[b]) (Eq. 17's numerator) and
+    // the largest |D| the step's normaliser allows (beyond it a pixel is
+    // reported to the slot's miss word)
+    float af[4], m[4];
+    float thr;
 };
+
+// Slot layout of LseDevState::acc (fixed-point sums of a step): sum w I_b
+// and sum I_b for up to 4 bands, the count, the sign changes, and for vector
+// images the pixel whose |D| exceeded the normaliser (orderable |D| bits
+// above the inverted pixel index, combined with atomicMax).
+enum { LSE_ACC_SW = 0, LSE_ACC_SA = 4, LSE_ACC_NP = 8, LSE_ACC_FL = 9, LSE_ACC_MISS = 10 };
 
 // The 128-byte aligned base (in floats) of the dynamic shared memory, the
 // table of square roots the FAST code reads, and the mbarriers.  Once per
@@ -303,16 +334,25 @@ __device__ __forceinline__ void tile_smem_init()
 // given to it.  PERSIST: one step of the persistent evolution (pc holds the
 // coefficients and the box state; the CTA's reduced sums go to ps->slot and
 // nothing is finalised here); returns whether a wait ran out.
-template <int KIND_EDGE, int RAD, bool FAST, class T, int NW, bool PERSIST = false>
+// NB > 1: the region term of a vector image (Eq. 17 summed over NB bands,
+// FP32 storage, persistent evolution only): the NB band boxes are staged
+// together, D is formed per pixel in the u pass, and the band sums come from
+// the staged bands.
+template <int KIND_EDGE, int RAD, bool FAST, class T, int NW, bool PERSIST = false, int NB = 1>
 __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *phi_map,
                                           const CUtensorMap *data_map, int cta, int ncta,
                                           TilePersist *ps = nullptr)
 {
-    using G = TileGeo<RAD, T, NW>;
+    using G = TileGeo<RAD, T, NW, NB>;
     constexpr int kThreads = G::THREADS, kURows = G::UR, kPhiRows = G::PHI_ROWS;
     using S = Stor<T>;
     constexpr int HL = G::HL, TH = G::TH, P = 2 * RAD + 1, RPW = G::RPW;
     constexpr bool EDGE = KIND_EDGE != 0;
+    constexpr bool MB = NB > 1;
+    // the update takes t = coef d (edge term: d = g; vector image: d = D)
+    constexpr bool DIRECT = EDGE || MB;
+    static_assert(!MB || (PERSIST && !EDGE && sizeof(T) == 4 && NB <= 4),
+                  "vector images: FP32 region term, persistent evolution");
 
     LseDevState *st = a.st;
     if constexpr (!PERSIST) {
@@ -365,6 +405,15 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
     const float coef = PERSIST ? ps->coef : EDGE ? (a.mb_split ? st->a[0] : a.half_dt) : st->a[0];
     const float mid = PERSIST ? ps->mid : EDGE ? 0.0f : st->m[0];
     const f2 coef2 = f2_pack(coef, coef), mid2 = f2_pack(mid, mid);
+    float af[NB], mb_m[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        af[b] = MB ? ps->af[b] : 0.0f;
+        mb_m[b] = MB ? ps->m[b] : 0.0f;
+    }
+    const float thr = MB ? ps->thr : 0.0f;
+    unsigned long long *const miss_word = reinterpret_cast<unsigned long long *>(
+        &st->acc[PERSIST ? ps->slot : 0][LSE_ACC_MISS]);
     const float sqrt8 = sqrtf(8.0f);
     const bool binarise_in = !FAST && (PERSIST ? ps->f.binarise_in : a.binarise_in) != 0;
     const bool count_flips = !FAST && (PERSIST ? ps->f.count_flips : a.count_flips) != 0;
@@ -385,7 +434,10 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
     auto load_data = [&](int t) {
         int xs, ys;
         origin(t, xs, ys);
-        tma_box(dat_dst, data_map, xs - G::DATA_X0, ys + 1, bar_dat, kDatBytes);
+        if (MB)
+            tma_box3(dat_dst, data_map, xs - G::DATA_X0, ys + 1, bar_dat, kDatBytes);
+        else
+            tma_box(dat_dst, data_map, xs - G::DATA_X0, ys + 1, bar_dat, kDatBytes);
     };
     auto load_tile = [&](int t) {
         load_phi(t);
@@ -418,7 +470,9 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
     // bits: a float to 64-bit conversion issues on the FP64 pipe
     long long cnt2 = 0;
     int nflip = 0;
-    long long sw_x = 0, sa_x = 0;                // fixed-point lane sums (lse_fix)
+    long long sw_x[NB], sa_x[NB];                // fixed-point lane sums (lse_fix)
+#pragma unroll
+    for (int b = 0; b < NB; ++b) sw_x[b] = sa_x[b] = 0;
     const bool lane_out = lane >= HL && lane < 32 - HL;
     const int eidx = lane == 0 ? 3 : 132;        // phi column beyond the warp's edge
     const T *bl = buf + 4 + 4 * lane;            // this lane's 4 columns of a phi row
@@ -497,7 +551,23 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
             constexpr bool IN = decltype(in_tag)::value;
             float4 pp = S::ld4(bl + (ur + 2) * kPhiW);
             float ep = S::ld1(buf + (ur + 2) * kPhiW + eidx);
-            const float4 d4 = S::ld4(dl + ur * G::DATA_W);
+            float4 d4;
+            if constexpr (MB) {
+                // D = sum_b af_b (I_b - m_b), bands in order
+                float dd[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const float4 e = lds4(reinterpret_cast<const float *>(dl) + b * G::PLANE +
+                                          ur * G::DATA_W);
+                    dd[0] = fmaf(af[b], e.x - mb_m[b], dd[0]);
+                    dd[1] = fmaf(af[b], e.y - mb_m[b], dd[1]);
+                    dd[2] = fmaf(af[b], e.z - mb_m[b], dd[2]);
+                    dd[3] = fmaf(af[b], e.w - mb_m[b], dd[3]);
+                }
+                d4 = make_float4(dd[0], dd[1], dd[2], dd[3]);
+            } else {
+                d4 = S::ld4(dl + ur * G::DATA_W);
+            }
             if (binarise_in) {
                 pp = bin4(pp);
                 ep = bin(ep);
@@ -566,7 +636,7 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
                           : IN ? (q[e] == 8.0f ? sqrt8 : 0.5f * q[e])
                                : lut[(__float_as_uint(q[e]) >> 21) & 31u];
                 const f2 d = f2_pack(comp(d4, j0), comp(d4, j1));
-                const f2 t = EDGE ? f2_mul(coef2, d) : f2_mul(coef2, f2_sub(d, mid2));
+                const f2 t = DIRECT ? f2_mul(coef2, d) : f2_mul(coef2, f2_sub(d, mid2));
                 f2_unpack(f2_fma(t, f2_pack(s2[0], s2[1]), f2_pack(c[j0 + 1], c[j1 + 1])),
                           u[j0], u[j1]);
             }
@@ -578,6 +648,29 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
                 if (!yin) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) u[j] = 0.0f;
+                }
+            }
+            if constexpr (MB) {
+                // the normaliser must bound |D| at every pixel of the image
+                // (Eq. 17); a pixel beyond it is reported (rare: the step
+                // is then done again with that pixel's |D|)
+                bool over = false;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    over |= (IN || (inb[j] != 0.0f && yin)) && fabsf(comp(d4, j)) > thr;
+                if (over) {
+                    const int y = ys + 1 + ur;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float ad = fabsf(comp(d4, j));
+                        if ((IN || (inb[j] != 0.0f && yin)) && ad > thr) {
+                            const unsigned int pix = (unsigned int)y * (unsigned int)W +
+                                                     (unsigned int)(x0 + j);
+                            atomicMax(miss_word,
+                                      ((unsigned long long)__float_as_uint(ad) << 32) |
+                                          (unsigned long long)(0xFFFFFFFFu - pix));
+                        }
+                    }
                 }
             }
             float U[4 + 8 * HL];
@@ -648,7 +741,9 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
                 d[0] = f2_pack(h4.x, h4.y);
                 d[1] = f2_pack(h4.z, h4.w);
             };
-            float fsw = 0.0f, fsa = 0.0f, fcnt = 0.0f;
+            float fsw[NB], fsa[NB], fcnt = 0.0f;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) fsw[b] = fsa[b] = 0.0f;
             auto vrows = [&](auto full_tag) {
                 constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
@@ -692,11 +787,17 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
                         if (!EDGE) {
                             // outside the image the staged data is zero; halo
                             // lanes drop their sums below
-                            const float4 d4 = S::ld4(dl + (ro + RAD) * G::DATA_W);
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                fsw = fmaf(comp(d4, j), w[j], fsw);
-                                fsa += comp(d4, j);
+                            for (int b = 0; b < NB; ++b) {
+                                const float4 d4 =
+                                    MB ? lds4(reinterpret_cast<const float *>(dl) +
+                                              b * G::PLANE + (ro + RAD) * G::DATA_W)
+                                       : S::ld4(dl + (ro + RAD) * G::DATA_W);
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    fsw[b] = fmaf(comp(d4, j), w[j], fsw[b]);
+                                    fsa[b] += comp(d4, j);
+                                }
                             }
                         }
                     }
@@ -707,8 +808,11 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
             else
                 vrows(std::false_type{});
             if (!EDGE && lane_out) {
-                sw_x += lse_fix(fsw, fix_k);
-                sa_x += lse_fix(fsa, fix_k);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    sw_x[b] += lse_fix(fsw[b], fix_k);
+                    sa_x[b] += lse_fix(fsa[b], fix_k);
+                }
             }
             int cv = 0;
 #pragma unroll
@@ -734,17 +838,27 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
         wait_bar(bar_dat, par);
     }
     // the CTA's exact sums, added to the step's slot of the state record
-    long long v[4] = {sw_x, sa_x, cnt2 / 2, (long long)nflip};
-    lse_cta_sum_i64<4, NW>(v);
+    long long v[2 * NB + 2];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        v[b] = sw_x[b];
+        v[NB + b] = sa_x[b];
+    }
+    v[2 * NB] = cnt2 / 2;
+    v[2 * NB + 1] = nflip;
+    lse_cta_sum_i64<2 * NB + 2, NW>(v);
     long long *slot = st->acc[PERSIST ? ps->slot : 0];
     auto add_sums = [&]() {
         unsigned long long *sl = reinterpret_cast<unsigned long long *>(slot);
         if (!EDGE) {
-            atomicAdd(sl + 0, (unsigned long long)v[0]);
-            atomicAdd(sl + 1, (unsigned long long)v[1]);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                atomicAdd(sl + LSE_ACC_SW + b, (unsigned long long)v[b]);
+                atomicAdd(sl + LSE_ACC_SA + b, (unsigned long long)v[NB + b]);
+            }
         }
-        atomicAdd(sl + 2, (unsigned long long)v[2]);
-        if (v[3]) atomicAdd(sl + 3, (unsigned long long)v[3]);
+        atomicAdd(sl + LSE_ACC_NP, (unsigned long long)v[2 * NB]);
+        if (v[2 * NB + 1]) atomicAdd(sl + LSE_ACC_FL, (unsigned long long)v[2 * NB + 1]);
     };
     if constexpr (PERSIST) {
         // ps is in shared memory: one writer (the caller synchronises)
@@ -772,12 +886,13 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
         __threadfence();
         // the totals, and the slot and the queue cleared for the next step
         unsigned long long *sl = reinterpret_cast<unsigned long long *>(slot);
-        long long tot[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) tot[j] = (long long)atomicExch(sl + j, 0ull);
+        const long long sw = (long long)atomicExch(sl + LSE_ACC_SW, 0ull);
+        const long long sa = (long long)atomicExch(sl + LSE_ACC_SA, 0ull);
+        const long long np = (long long)atomicExch(sl + LSE_ACC_NP, 0ull);
+        const long long fl = (long long)atomicExch(sl + LSE_ACC_FL, 0ull);
         if (QUEUE) *queue = 0;
         LseAcc t;
-        lse_fix_totals(tot[0], tot[1], tot[2], tot[3], fix_k, t);
+        lse_fix_totals(sw, sa, np, fl, fix_k, t);
         lse_step_finalize(a, t, pre);
     }
     return failed;
@@ -925,13 +1040,13 @@ __device__ __noinline__ void persist_sum(const StepArgs &a, int n, PersistCoef *
     LseDevState *st = a.st;
     const volatile long long *sl = st->acc[n % 3];
     LseAcc t;
-    lse_fix_totals(sl[0], sl[1], sl[2], sl[3], st->fix_k, t);
+    lse_fix_totals(sl[LSE_ACC_SW], sl[LSE_ACC_SA], sl[LSE_ACC_NP], sl[LSE_ACC_FL], st->fix_k, t);
     PersistCoef c = *coef;
     *done = persist_finalize<EDGE>(a, n, t, c, st->imin, st->imax, record) ? 1 : 0;
     *coef = c;
     if (record) {
         long long *old = st->acc[(n + 2) % 3];
-        old[0] = old[1] = old[2] = old[3] = 0;
+        for (int j = 0; j < 12; ++j) old[j] = 0;
         st->tile_ctr[n & 1] = 0;
     }
 }
@@ -1003,6 +1118,281 @@ evolve_tile_kernel(const __grid_constant__ EvolveArgs e,
         const uint32_t sm0 = smem_u32(smem_f);
         const int sb = (int)(((128u - (sm0 & 127u)) & 127u) >> 2);
         wait_bar(sm0 + 4u * (uint32_t)(sb + 32) + 8u, s_pc.par);
+    }
+}
+
+// ---------------------------------------------------------------- vector images
+// What a CTA of the vector-image evolution keeps from step to step: the
+// FP64 factors of the coming step's D (Eq. 17's numerator), its normaliser
+// M and whether its force is zero.
+template <int NB>
+struct MbCoef {
+    double al[NB], md[NB];      // alpha_b = 2 (c+ - c-), mid_b = (c+ + c-) / 2
+    double norm;                // M
+    int zero;                   // R = 0 (degenerate rule, or M = 0)
+};
+
+// M = max over the candidate pixels of |D| (FP64), by the whole CTA; the
+// maximum does not depend on the order, so every CTA gets the same bits.
+template <int NB>
+__device__ __forceinline__ double mb_norm(const LseCandidates *cand, const MbCoef<NB> &c)
+{
+    __shared__ double s_m[32];
+    const int n = *reinterpret_cast<const volatile int *>(&cand->count);
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double d = 0.0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            d = fma(c.al[b], (double)__ldcg(&cand->val[i][b]) - c.md[b], d);
+        m = fmax(m, fabs(d));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, s_m[w]);
+        s_m[0] = t;
+    }
+    __syncthreads();
+    const double r = s_m[0];
+    __syncthreads();
+    return r;
+}
+
+// D of one pixel in FP64 with the step's factors.
+template <int NB>
+__device__ __forceinline__ double mb_d_at(const StepArgs &a, unsigned int pix,
+                                          const MbCoef<NB> &c)
+{
+    const unsigned int y = pix / (unsigned int)a.W, x = pix % (unsigned int)a.W;
+    double d = 0.0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+        d = fma(c.al[b],
+                (double)__ldg(a.data + b * a.band_stride + (size_t)y * a.pitch + x) - c.md[b], d);
+    return d;
+}
+
+// The persistent evolution of a vector image (2-4 bands, FP32): every
+// iteration in one cooperative launch, as evolve_tile_kernel does for one
+// band.  Each step stages the NB band boxes, forms D per pixel (Eq. 17) and
+// sums every band over v >= 0 exactly (Eq. 15).  M comes from the candidate
+// pixels (LseCandidates); a pixel whose |D| exceeds it (in FP64: the step
+// reports the largest FP32 |D| above M (1 + 2^-20)) joins the candidates and
+// the step is done again from the same input LSF with that pixel's |D| as M,
+// so every step uses M = max_x |D(x)|.  All CTAs decide a redo identically.
+template <int RAD, int NB, int NW>
+__global__ void __launch_bounds__(TileGeo<RAD, float, NW, NB>::THREADS,
+                                  TileGeo<RAD, float, NW, NB>::MIN_BLOCKS)
+evolve_mb_kernel(const __grid_constant__ EvolveArgs e,
+                 const __grid_constant__ CUtensorMap phi_map0,
+                 const __grid_constant__ CUtensorMap phi_map1,
+                 const __grid_constant__ CUtensorMap data_map)
+{
+    const StepArgs &a = e.a;
+    LseDevState *st = a.st;
+    LseCandidates *cand = e.cand;
+    if (st->done || (st->status_bits & LSE_SBIT_ABORT)) return;
+    __shared__ TilePersist s_pc;
+    __shared__ MbCoef<NB> s_c;
+    __shared__ int s_done, s_redo;
+    const int cta = blockIdx.x, ncta = gridDim.x;
+    if (threadIdx.x == 0) {
+        // the prologue made the first step's statistics
+        for (int b = 0; b < NB; ++b) {
+            s_c.al[b] = st->alpha[b];
+            s_c.md[b] = st->mid[b];
+        }
+        s_c.zero = st->zero_force;
+        s_pc.par = 0u;
+        s_pc.issued = 0;
+        s_pc.stall_ns = a.stall_ns;
+    }
+    tile_smem_init<RAD, float, NW>();   // ends with a CTA barrier
+    {
+        const double m = mb_norm<NB>(cand, s_c);
+        if (threadIdx.x == 0) {
+            s_c.norm = m;
+            if (!(m > 0.0)) s_c.zero = 1;
+        }
+    }
+    int redos = 0;
+    for (int n = 0, pass = 0; n < e.cap; ++pass) {
+        if (threadIdx.x == 0) {
+            s_pc.f = lse_step_flags(n, e.cap, e.reinit_period, e.early_stop != 0, true);
+            s_pc.phi_out = e.phi[(n + 1) & 1];
+            const bool z = s_c.zero != 0;
+            s_pc.coef = z ? 0.0f : __double2float_rn(__ddiv_rn((double)a.dt, 2.0 * s_c.norm));
+            s_pc.mid = 0.0f;
+            for (int b = 0; b < 4; ++b) {
+                s_pc.af[b] = b < NB ? __double2float_rn(s_c.al[b]) : 0.0f;
+                s_pc.m[b] = b < NB ? __double2float_rn(s_c.md[b]) : 0.0f;
+            }
+            s_pc.thr = z ? INFINITY : __double2float_rn(s_c.norm * (1.0 + 0x1p-20));
+            s_pc.prefetch = n + 1 < e.cap;
+            s_pc.slot = pass % 3;
+            s_pc.queue = pass & 1;
+        }
+        __syncthreads();
+        const CUtensorMap *pm = (n & 1) ? &phi_map1 : &phi_map0;
+        const LseStepFlags f = s_pc.f;
+        if (f.binary_in && f.store_bin && !f.count_flips && !f.binarise_in)
+            tile_step<0, RAD, true, float, NW, true, NB>(a, pm, &data_map, cta, ncta, &s_pc);
+        else
+            tile_step<0, RAD, false, float, NW, true, NB>(a, pm, &data_map, cta, ncta, &s_pc);
+        if (threadIdx.x == 0) s_pc.stall_ns = 0;
+        if (!grid_barrier(st, (unsigned int)(pass + 1) * (unsigned int)ncta)) break;
+        if (*reinterpret_cast<volatile unsigned int *>(&st->status_bits) & LSE_SBIT_ABORT) break;
+        if (threadIdx.x == 0) {
+            const volatile long long *sl = st->acc[pass % 3];
+            const unsigned long long miss = (unsigned long long)sl[LSE_ACC_MISS];
+            bool redo = false;
+            if (miss && !s_c.zero && redos < 16) {
+                const unsigned int pix = 0xFFFFFFFFu - (unsigned int)(miss & 0xFFFFFFFFull);
+                const double d = fabs(mb_d_at<NB>(a, pix, s_c));
+                if (d > s_c.norm) {
+                    // the step used too small an M: again, with this pixel's |D|
+                    redo = true;
+                    s_c.norm = d;
+                    if (cta == 0) {
+                        const int k = cand->count;
+                        if (k < LSE_MB_CAND) {
+                            const unsigned int y = pix / (unsigned int)a.W;
+                            const unsigned int x = pix % (unsigned int)a.W;
+                            for (int b = 0; b < 4; ++b)
+                                cand->val[k][b] =
+                                    b < NB ? a.data[b * a.band_stride + (size_t)y * a.pitch + x]
+                                           : 0.0f;
+                            cand->count = k + 1;
+                        }
+                        cand->redone += 1;
+                    }
+                }
+            }
+            s_redo = redo ? 1 : 0;
+            s_done = 0;
+            if (!redo) {
+                // the new LSF's statistics (Eq. 15) and the next step's factors
+                const int k = st->fix_k;
+                const long long np = sl[LSE_ACC_NP], nm = a.npix - np;
+                double cp[NB], cm[NB], contrast = 0.0, scale = 0.0;
+                MbCoef<NB> nc;
+                for (int b = 0; b < NB; ++b) {
+                    const long long sw = sl[LSE_ACC_SW + b], sa = sl[LSE_ACC_SA + b];
+                    const double sp = ldexp((double)(sa + sw), -(k + 1));
+                    const double sm = ldexp((double)(sa - sw), -(k + 1));
+                    lse_band_coeffs(sp, sm, np, nm, cp[b], cm[b], nc.al[b], nc.md[b]);
+                    contrast = fmax(contrast, fabs(cp[b] - cm[b]));
+                    scale = fmax(scale, fabs(cp[b]) + fabs(cm[b]));
+                    if (cta == 0) {
+                        st->run_sp[b] = sp;
+                        st->run_sm[b] = sm;
+                        st->c_plus[b] = cp[b];
+                        st->c_minus[b] = cm[b];
+                        st->alpha[b] = nc.al[b];
+                        st->mid[b] = nc.md[b];
+                    }
+                }
+                nc.zero = (np == 0 || nm == 0 || contrast <= LSE_CONTRAST_TOL * scale);
+                nc.norm = 0.0;
+                const bool done = a.early_thresh > 0.0 && (double)sl[LSE_ACC_FL] < a.early_thresh;
+                if (cta == 0) {
+                    st->norm_used = s_c.zero ? 0.0 : s_c.norm;
+                    st->area_plus = np;
+                    st->last_flips = sl[LSE_ACC_FL];
+                    st->iterations_run = n + 1;
+                    st->last_buf = (n + 1) & 1;
+                    st->zero_force = nc.zero;
+                    if (s_c.zero) atomicOr(&st->status_bits, LSE_SBIT_DEGENERATE);
+                    if (done) st->done = 1;
+                }
+                s_c = nc;
+                s_done = done ? 1 : 0;
+                redos = 0;
+            } else {
+                ++redos;
+            }
+            if (cta == 0) {
+                // the slot and queue of pass - 1, read by every CTA before
+                // it arrived here, are cleared for pass + 2
+                long long *old = st->acc[(pass + 2) % 3];
+                for (int j = 0; j < 12; ++j) old[j] = 0;
+                st->tile_ctr[pass & 1] = 0;
+            }
+        }
+        __syncthreads();
+        if (s_redo) continue;
+        if (s_done) break;
+        ++n;
+        if (n < e.cap) {
+            // M of the next step over the candidates (one added by a redo
+            // is in place: CTA 0 wrote it before this barrier)
+            const double m = mb_norm<NB>(cand, s_c);
+            if (threadIdx.x == 0) {
+                s_c.norm = m;
+                if (!(m > 0.0)) s_c.zero = 1;
+            }
+        }
+    }
+    // a data box prefetched for a step that did not run: wait for it
+    // (bounded) before the CTA exits
+    __syncthreads();
+    if (s_pc.issued == 1) {
+        extern __shared__ float smem_f[];
+        const uint32_t sm0 = smem_u32(smem_f);
+        const int sb = (int)(((128u - (sm0 & 127u)) & 127u) >> 2);
+        wait_bar(sm0 + 4u * (uint32_t)(sb + 32) + 8u, s_pc.par);
+    }
+}
+
+template <int RAD, int NB>
+cudaError_t launch_evolve_mb_one(const EvolveArgs &e, const CUtensorMap &pm0,
+                                 const CUtensorMap &pm1, const CUtensorMap &dm, int nblocks,
+                                 int sm_count, cudaStream_t s)
+{
+    constexpr int NW = 4;
+    using G = TileGeo<RAD, float, NW, NB>;
+    auto kern = evolve_mb_kernel<RAD, NB, NW>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           G::BYTES);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::THREADS, G::BYTES);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorNotSupported;
+    // every resident slot, at most one CTA per tile
+    long long grid = (long long)per_sm * sm_count;
+    if (grid > nblocks) grid = nblocks;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned int)grid);
+    cfg.blockDim = dim3(G::THREADS);
+    cfg.dynamicSmemBytes = G::BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, e, pm0, pm1, dm);
+}
+
+template <int NB>
+cudaError_t launch_evolve_mb_bands(const EvolveArgs &e, const CUtensorMap &pm0,
+                                   const CUtensorMap &pm1, const CUtensorMap &dm, int nblocks,
+                                   int sm_count, cudaStream_t s)
+{
+    switch (e.a.rad) {
+    case 1: return launch_evolve_mb_one<1, NB>(e, pm0, pm1, dm, nblocks, sm_count, s);
+    case 2: return launch_evolve_mb_one<2, NB>(e, pm0, pm1, dm, nblocks, sm_count, s);
+    case 3: return launch_evolve_mb_one<3, NB>(e, pm0, pm1, dm, nblocks, sm_count, s);
+    case 4: return launch_evolve_mb_one<4, NB>(e, pm0, pm1, dm, nblocks, sm_count, s);
+    case 5: return launch_evolve_mb_one<5, NB>(e, pm0, pm1, dm, nblocks, sm_count, s);
+    case 6: return launch_evolve_mb_one<6, NB>(e, pm0, pm1, dm, nblocks, sm_count, s);
+    case 7: return launch_evolve_mb_one<7, NB>(e, pm0, pm1, dm, nblocks, sm_count, s);
+    default: return cudaErrorNotSupported;
     }
 }
 

@@ -54,6 +54,12 @@ LSE_EVOLVE_DECL(f16_region_nw4)
 LSE_EVOLVE_DECL(f16_edge_nw8)
 LSE_EVOLVE_DECL(f16_edge_nw4)
 #undef LSE_EVOLVE_DECL
+cudaError_t launch_evolve_mb2(const EvolveArgs &, const CUtensorMap &, const CUtensorMap &,
+                              const CUtensorMap &, int, int, cudaStream_t);
+cudaError_t launch_evolve_mb3(const EvolveArgs &, const CUtensorMap &, const CUtensorMap &,
+                              const CUtensorMap &, int, int, cudaStream_t);
+cudaError_t launch_evolve_mb4(const EvolveArgs &, const CUtensorMap &, const CUtensorMap &,
+                              const CUtensorMap &, int, int, cudaStream_t);
 
 }  // namespace lse_detail
 
@@ -237,6 +243,18 @@ cudaError_t launch_evolve_tile(const EvolveArgs &e, const CUtensorMap &pm0,
     if (e.a.mb_split || !tile_index(e.a.storage, e.a.term, e.a.nw, &si, &ti, &ni))
         return cudaErrorNotSupported;
     return kEvolve[si][ti][ni](e, pm0, pm1, dm, nblocks, sm_count, s);
+}
+
+cudaError_t launch_evolve_mb(const EvolveArgs &e, const CUtensorMap &pm0,
+                             const CUtensorMap &pm1, const CUtensorMap &dm, int nblocks,
+                             int sm_count, cudaStream_t s)
+{
+    switch (e.a.B) {
+    case 2: return launch_evolve_mb2(e, pm0, pm1, dm, nblocks, sm_count, s);
+    case 3: return launch_evolve_mb3(e, pm0, pm1, dm, nblocks, sm_count, s);
+    case 4: return launch_evolve_mb4(e, pm0, pm1, dm, nblocks, sm_count, s);
+    default: return cudaErrorNotSupported;
+    }
 }
 
 cudaError_t launch_step_tile_batch(int storage, int term, int nw, int rad,

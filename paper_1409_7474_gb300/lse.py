@@ -102,6 +102,8 @@ _lib.lse_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
 _lib.lse_get_stats.restype = ctypes.c_int
 _lib.lse_version.argtypes = []
 _lib.lse_version.restype = ctypes.c_char_p
+_lib.lse_kernel_launches.argtypes = [_vp]
+_lib.lse_kernel_launches.restype = ctypes.c_ulonglong
 _lib.lse_evolve_static.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                    ctypes.POINTER(Params), _vp, _vp, ctypes.POINTER(Stats),
                                    _vp]
@@ -125,7 +127,8 @@ _lib.lse_server_poll.argtypes = [_vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c
 _lib.lse_server_poll.restype = ctypes.c_int
 
 SYMBOLS = ("lse_create", "lse_destroy", "lse_last_error", "lse_precompute_edge",
-           "lse_evolve", "lse_get_stats", "lse_version", "lse_evolve_static",
+           "lse_evolve", "lse_get_stats", "lse_version", "lse_kernel_launches",
+           "lse_evolve_static",
            "lse_evolve_batch", "lse_autotune", "lse_server_create", "lse_server_destroy",
            "lse_server_submit", "lse_server_advance", "lse_server_poll")
 STATIC_MAX_PIXELS = 262144
@@ -317,6 +320,11 @@ class Context:
         self._check(_lib.lse_autotune(self._h, n, probs, int(iterations), rows,
                                       _stream_ptr(stream, self.device)))
         return list(rows)
+
+    def kernel_launches(self) -> int:
+        """lse_kernel_launches: kernels this context's evolve and
+        precompute_edge calls have enqueued."""
+        return int(_lib.lse_kernel_launches(self._h))
 
     def stats(self, bands: int = 8) -> dict:
         st = Stats()

@@ -25,3 +25,33 @@ def assert_mask_parity(gpu_mask, ref_mask, max_frac=5e-4):
     rep = mask_report(gpu_mask, ref_mask)
     assert rep["frac"] <= max_frac and rep["far"] == 0, rep
     return rep
+
+
+class step_launches:
+    """Within the block lse_evolve launches one kernel per step (LSE_PERSIST=0,
+    read at every call).  Batches and the server advance their images one
+    step per launch; vector images there take the band passes, and this is
+    how a single call reproduces that path to compare bit for bit."""
+
+    def __init__(self, on=True):
+        self.on = on
+
+    def __enter__(self):
+        import os
+        self._old = os.environ.get("LSE_PERSIST")
+        if self.on:
+            os.environ["LSE_PERSIST"] = "0"
+        return self
+
+    def __exit__(self, *exc):
+        import os
+        if self._old is None:
+            os.environ.pop("LSE_PERSIST", None)
+        else:
+            os.environ["LSE_PERSIST"] = self._old
+        return False
+
+
+def is_vector_region(it):
+    img = it.get("image")
+    return it.get("term", "region") == "region" and img is not None and img.shape[0] > 1

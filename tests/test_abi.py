@@ -86,6 +86,7 @@ def test_version_and_errors_without_gpu(lse):
     st = lse.Stats()
     assert lib.lse_get_stats(None, ctypes.byref(st)) == lse.LSE_ERR_INVALID_ARG
     assert lib.lse_evolve_batch(None, 1, None, 1, None, None) == lse.LSE_ERR_INVALID_ARG
+    assert lib.lse_kernel_launches(None) == 0
     lib.lse_destroy(None)
 
 

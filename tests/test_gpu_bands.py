@@ -1,18 +1,23 @@
-"""Statistics of vector images (2-4 bands) on the band-pass path, through
+"""Statistics of vector images (2-4 bands) on both of their paths, through
 the C ABI.
 
-The band statistics pass keeps running FP64 band sums over phi >= 0 and
-phi < 0 (Eq. 15) and updates them, each iteration, from the pixels whose
-sign the step changed.  After hundreds of iterations, with and without an
-early stop, the c+ / c- and |{phi >= 0}| the library reports must still be
-those of the LSF it returns, as the oracle computes them directly from that
-LSF: the count exactly, c+- within 1e-7 relative (rounding of the sums is
-orders of magnitude below; a lost or double-counted update is not).
+lse_evolve runs a vector image as one persistent launch whose step stages
+the bands and sums them over phi >= 0 exactly (fixed point); with
+LSE_PERSIST=0, and in batches, it takes the band passes, whose statistics
+pass keeps running FP64 band sums over phi >= 0 and phi < 0 (Eq. 15) and
+updates them, each iteration, from the pixels whose sign the step changed.
+After hundreds of iterations, with and without an early stop, the c+ / c-
+and |{phi >= 0}| the library reports must still be those of the LSF it
+returns, as the oracle computes them directly from that LSF: the count
+exactly, c+- within 1e-7 relative (rounding of the sums is orders of
+magnitude below; a lost or double-counted update is not).  The two paths
+agree with each other within the parity tolerance.
 """
 import numpy as np
 import pytest
 
 import oracle
+from _parity import assert_mask_parity, step_launches
 from paper_1409_7474_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -50,27 +55,31 @@ def check_stats(img, v, st):
         assert abs(st["c_minus"][b] - cm[b]) <= TOL_REL * abs(cm[b]), (b, st["c_minus"][b], cm[b])
 
 
+@pytest.mark.parametrize("path", ["persistent", "band passes"])
 @pytest.mark.parametrize("B", [2, 3, 4])
 @pytest.mark.parametrize("iterations", [1, 2, 37, 400])
-def test_statistics_are_those_of_the_returned_lsf(torch, ctx, scene, B, iterations):
+def test_statistics_are_those_of_the_returned_lsf(torch, ctx, scene, B, iterations, path):
     img = np.ascontiguousarray(scene[:B])
     phi0 = scenes.circle_phi(768, 1024, radius=300)
-    v, m, st = ctx.evolve(torch.from_numpy(img).cuda(), torch.from_numpy(phi0).cuda(),
-                          "region", iterations=iterations)
+    with step_launches(path == "band passes"):
+        v, m, st = ctx.evolve(torch.from_numpy(img).cuda(), torch.from_numpy(phi0).cuda(),
+                              "region", iterations=iterations)
     torch.cuda.synchronize()
     assert st["status"] == "LSE_OK"
     assert st["iterations_run"] == iterations
     check_stats(img, v.cpu().numpy(), st)
 
 
+@pytest.mark.parametrize("path", ["persistent", "band passes"])
 @pytest.mark.parametrize("B", [2, 4])
-def test_statistics_after_an_early_stop(torch, ctx, scene, B):
+def test_statistics_after_an_early_stop(torch, ctx, scene, B, path):
     # the statistics pass after the stopping step updates the sums once; the
     # passes scheduled after it (and the closing one) must change nothing
     img = np.ascontiguousarray(scene[:B])
     phi0 = scenes.circle_phi(768, 1024, radius=300)
-    v, m, st = ctx.evolve(torch.from_numpy(img).cuda(), torch.from_numpy(phi0).cuda(),
-                          "region", iterations=600, early_stop_frac=1e-2)
+    with step_launches(path == "band passes"):
+        v, m, st = ctx.evolve(torch.from_numpy(img).cuda(), torch.from_numpy(phi0).cuda(),
+                              "region", iterations=600, early_stop_frac=1e-2)
     torch.cuda.synchronize()
     assert st["status"] == "LSE_OK"
     assert st["iterations_run"] < 600
@@ -90,3 +99,27 @@ def test_batched_vector_images_report_their_own_statistics(torch, ctx, scene):
     for img, (v, m, st) in zip(imgs, res):
         assert st["status"] == "LSE_OK"
         check_stats(img, v.cpu().numpy(), st)
+
+
+@pytest.mark.parametrize("B", [2, 3, 4])
+def test_persistent_path_agrees_with_the_band_passes_and_the_oracle(torch, ctx, scene, B):
+    img = np.ascontiguousarray(scene[:B, :300, :412])
+    phi0 = scenes.circle_phi(300, 412, radius=110)
+    x = torch.from_numpy(img).cuda()
+    p = torch.from_numpy(phi0).cuda()
+    # one step: v within 1e-5 of the oracle, the normaliser within 1e-6
+    v, m, st = ctx.evolve(x, p, "region", iterations=1)
+    torch.cuda.synchronize()
+    v_ref, norm, cp, cm, _ = oracle.step(img, phi0)
+    assert np.abs(v.cpu().numpy() - v_ref).max() <= 1e-5
+    assert abs(st["norm"] - norm) <= 1e-6 * norm
+    # many steps: masks within the parity bar of the oracle and of the
+    # band passes
+    v, m, st = ctx.evolve(x, p, "region", iterations=120)
+    with step_launches():
+        v2, m2, st2 = ctx.evolve(x, p, "region", iterations=120)
+    torch.cuda.synchronize()
+    v_ref, m_ref, st_ref = oracle.evolve(img, phi0, iterations=120)
+    assert_mask_parity(m.cpu().numpy(), m_ref)
+    assert_mask_parity(m.cpu().numpy(), m2.cpu().numpy())
+    assert abs(st["norm"] - st_ref["norm"]) <= 1e-6 * st_ref["norm"]

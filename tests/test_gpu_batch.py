@@ -3,7 +3,8 @@ vs the FP64 oracle.
 
 Every image of a batch keeps its own planes, statistics, CTA count,
 iteration cap and early stop, so its results must equal lse_evolve's on the
-same image bit for bit, with and without CUDA-graph capture.  lse_evolve is
+same image bit for bit, with and without CUDA-graph capture (for vector
+images: lse_evolve on the band passes, which batches take too).  lse_evolve is
 itself held to the oracle by the parity tests; a few small batch images are
 also compared with the oracle directly (mask parity, the early stop's
 iteration count).
@@ -14,7 +15,7 @@ import numpy as np
 import pytest
 
 import oracle
-from _parity import assert_mask_parity
+from _parity import assert_mask_parity, is_vector_region, step_launches
 from paper_1409_7474_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -58,9 +59,13 @@ def device_items(torch, ctx, probs):
 
 
 def single(torch, ctx, it):
-    v, m, st = ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
-                          iterations=it["iterations"],
-                          early_stop_frac=it["early_stop_frac"], storage=it["storage"])
+    # vector images in a batch take the band passes: the single call takes
+    # them too (the persistent path agrees within the parity tolerance,
+    # tests/test_gpu_bands.py)
+    with step_launches(is_vector_region(it)):
+        v, m, st = ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
+                              iterations=it["iterations"],
+                              early_stop_frac=it["early_stop_frac"], storage=it["storage"])
     torch.cuda.synchronize()
     return v.cpu().numpy(), m.cpu().numpy(), st
 

@@ -125,3 +125,24 @@ def test_persistent_early_stop(torch, lse):
         assert_same(a, b)
         assert 1 < a[2]["iterations_run"] < 300
         assert a[2]["last_flips"] < 500
+
+
+def test_kernel_launch_count(torch, lse):
+    # the persistent path enqueues the prologue, one kernel for every
+    # iteration and the output; one launch per step enqueues one per iteration
+    img, _, _ = scenes.rect_scene()
+    with lse.Context(0, max_pixels=256 * 256, max_bands=1) as ctx:
+        x = torch.from_numpy(img).cuda()
+        p = torch.from_numpy(scenes.circle_phi(256, 256)).cuda()
+        n0 = ctx.kernel_launches()
+        ctx.evolve(x, p, "region", iterations=40)
+        n1 = ctx.kernel_launches()
+        os.environ["LSE_PERSIST"] = "0"
+        try:
+            ctx.evolve(x, p, "region", iterations=40)
+        finally:
+            os.environ.pop("LSE_PERSIST", None)
+        n2 = ctx.kernel_launches()
+        g = ctx.precompute_edge(x, 1.0, 9, 255.0)
+        n3 = ctx.kernel_launches()
+        assert (n1 - n0, n2 - n1, n3 - n2) == (3, 42, 1)

@@ -11,6 +11,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from _parity import is_vector_region, step_launches
 from paper_1409_7474_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -53,9 +54,11 @@ def device_items(torch, ctx, probs):
 
 
 def alone(torch, ctx, it):
-    v, m, st = ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
-                          iterations=it["iterations"], early_stop_frac=it["early_stop_frac"],
-                          storage=it["storage"])
+    # vector images on the server take the band passes: so does the call alone
+    with step_launches(is_vector_region(it)):
+        v, m, st = ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
+                              iterations=it["iterations"],
+                              early_stop_frac=it["early_stop_frac"], storage=it["storage"])
     torch.cuda.synchronize()
     return v.cpu().numpy(), m.cpu().numpy(), st
 

@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 import oracle
-from _parity import assert_mask_parity, mask_report
+from _parity import assert_mask_parity, is_vector_region, mask_report, step_launches
 from paper_1409_7474_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -182,10 +182,11 @@ def test_autotuned_context_keeps_batch_and_server_equal_to_evolve(torch, lse):
         sv.destroy()
         assert len(served) == len(ids)
         for it, (v, m, st), rid in zip(items, res, ids):
-            v1, m1, st1 = ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
-                                     iterations=it["iterations"],
-                                     early_stop_frac=it["early_stop_frac"],
-                                     storage=it["storage"])
+            with step_launches(is_vector_region(it)):
+                v1, m1, st1 = ctx.evolve(it.get("image"), it["phi0"], it["term"],
+                                         g=it.get("g"), iterations=it["iterations"],
+                                         early_stop_frac=it["early_stop_frac"],
+                                         storage=it["storage"])
             torch.cuda.synchronize()
             v1 = v1.cpu().numpy()
             assert same_bits(v.cpu().numpy(), v1)
