@@ -523,7 +523,7 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
     // vector images on the persistent evolution: the step stages the bands
     // and forms D itself; M comes from candidate pixels found here, once
     bool fused_bands = false;
-    if (region && B > 1 && ctx->step_form == LSE_FORM_AUTO &&
+    if (region && B > 1 && ctx->step_form == LSE_FORM_AUTO && sto == LSE_F32 &&
         evolve_bands_applies(H, W, B, p)) {
         void *cp = ctx->cand;
         if ((r = ensure(ctx, &cp, &ctx->cand_cap, sizeof(LseCandidates), s, "candidates")) != LSE_OK)
@@ -556,7 +556,10 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
     }
     // the step's kernel, work decomposition and tensor maps
     StepPlan plan;
-    if (!plan_step(H, W, B, p, pitch, band_stride, data_s, ctx->phi, ctx->st, ctx->partials,
+    plan.form = LSE_FORM_GENERIC;
+    plan.args.mb_split = 0;
+    if (!fused_bands &&
+        !plan_step(H, W, B, p, pitch, band_stride, data_s, ctx->phi, ctx->st, ctx->partials,
                    ctx->sm_count, ctx->step_form, tile_nw_for(ctx, H, W, B, p.term, sto, p.ts),
                    dplane, &plan)) {
         set_err(ctx, "16-bit storage runs on the tile-form step only (LSE_STEP_KERNEL "

@@ -158,10 +158,12 @@ struct TileGeo {
     // UR - 1 they lie in other shared memory (FP32) or are clamped (16-bit)
     static constexpr bool CLAMP_H = !WIDE && NW * RPW - 1 + 2 * RAD > UR - 1;
     // CTAs per SM (launch bounds): 24 warps for RAD <= 4, else 16; vector
-    // images as many as their shared memory allows (228 KB per SM)
+    // images as many as their shared memory allows (228 KB per SM), at most
+    // 3 (the step of a vector image needs about 170 registers a thread)
+    static constexpr int MB_BLOCKS = (227 * 1024) / (BYTES + 3072);
     static constexpr int MIN_BLOCKS =
         NB == 1 ? (RAD <= 4 ? 24 : 16) / NW
-                : ((227 * 1024) / (BYTES + 3072) > 0 ? (227 * 1024) / (BYTES + 3072) : 1);
+                : (MB_BLOCKS < 1 ? 1 : MB_BLOCKS > 3 ? 3 : MB_BLOCKS);
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -296,6 +298,8 @@ struct TilePersist {
     // reported to the slot's miss word)
     float af[4], m[4];
     float thr;
+    int need_sa;                // sum I_b over the image too (a vector image's
+                                // first step; the total is the same later)
 };
 
 // Slot layout of LseDevState::acc (fixed-point sums of a step): sum w I_b
@@ -412,6 +416,7 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
         mb_m[b] = MB ? ps->m[b] : 0.0f;
     }
     const float thr = MB ? ps->thr : 0.0f;
+    const bool need_sa = MB && ps->need_sa != 0;
     unsigned long long *const miss_word = reinterpret_cast<unsigned long long *>(
         &st->acc[PERSIST ? ps->slot : 0][LSE_ACC_MISS]);
     const float sqrt8 = sqrtf(8.0f);
@@ -553,18 +558,18 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
             float ep = S::ld1(buf + (ur + 2) * kPhiW + eidx);
             float4 d4;
             if constexpr (MB) {
-                // D = sum_b af_b (I_b - m_b), bands in order
-                float dd[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                // D = sum_b af_b (I_b - m_b), bands in order, on column pairs
+                f2 d01 = f2_pack(0.0f, 0.0f), d23 = d01;
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
                     const float4 e = lds4(reinterpret_cast<const float *>(dl) + b * G::PLANE +
                                           ur * G::DATA_W);
-                    dd[0] = fmaf(af[b], e.x - mb_m[b], dd[0]);
-                    dd[1] = fmaf(af[b], e.y - mb_m[b], dd[1]);
-                    dd[2] = fmaf(af[b], e.z - mb_m[b], dd[2]);
-                    dd[3] = fmaf(af[b], e.w - mb_m[b], dd[3]);
+                    const f2 a2 = f2_pack(af[b], af[b]), m2 = f2_pack(mb_m[b], mb_m[b]);
+                    d01 = f2_fma(a2, f2_sub(f2_pack(e.x, e.y), m2), d01);
+                    d23 = f2_fma(a2, f2_sub(f2_pack(e.z, e.w), m2), d23);
                 }
-                d4 = make_float4(dd[0], dd[1], dd[2], dd[3]);
+                f2_unpack(d01, d4.x, d4.y);
+                f2_unpack(d23, d4.z, d4.w);
             } else {
                 d4 = S::ld4(dl + ur * G::DATA_W);
             }
@@ -744,6 +749,11 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
             float fsw[NB], fsa[NB], fcnt = 0.0f;
 #pragma unroll
             for (int b = 0; b < NB; ++b) fsw[b] = fsa[b] = 0.0f;
+            // vector images: the band sums on column pairs (sum w I_b, and on
+            // the first step sum I_b), folded per tile
+            f2 psw[NB], psa[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) psw[b] = psa[b] = f2_pack(0.0f, 0.0f);
             auto vrows = [&](auto full_tag) {
                 constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
@@ -784,20 +794,25 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
                         }
 #pragma unroll
                         for (int j = 0; j < 4; ++j) fcnt = fmaf(w[j], okf[j], fcnt);
-                        if (!EDGE) {
+                        if (!EDGE && !MB) {
                             // outside the image the staged data is zero; halo
                             // lanes drop their sums below
+                            const float4 d4 = S::ld4(dl + (ro + RAD) * G::DATA_W);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                fsw[0] = fmaf(comp(d4, j), w[j], fsw[0]);
+                                fsa[0] += comp(d4, j);
+                            }
+                        }
+                        if constexpr (MB) {
+                            const f2 w01 = f2_pack(w[0], w[1]), w23 = f2_pack(w[2], w[3]);
 #pragma unroll
                             for (int b = 0; b < NB; ++b) {
-                                const float4 d4 =
-                                    MB ? lds4(reinterpret_cast<const float *>(dl) +
-                                              b * G::PLANE + (ro + RAD) * G::DATA_W)
-                                       : S::ld4(dl + (ro + RAD) * G::DATA_W);
-#pragma unroll
-                                for (int j = 0; j < 4; ++j) {
-                                    fsw[b] = fmaf(comp(d4, j), w[j], fsw[b]);
-                                    fsa[b] += comp(d4, j);
-                                }
+                                const float4 e = lds4(reinterpret_cast<const float *>(dl) +
+                                                      b * G::PLANE + (ro + RAD) * G::DATA_W);
+                                const f2 e01 = f2_pack(e.x, e.y), e23 = f2_pack(e.z, e.w);
+                                psw[b] = f2_fma(e23, w23, f2_fma(e01, w01, psw[b]));
+                                if (need_sa) psa[b] = f2_add(psa[b], f2_add(e01, e23));
                             }
                         }
                     }
@@ -810,8 +825,18 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
             if (!EDGE && lane_out) {
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
-                    sw_x[b] += lse_fix(fsw[b], fix_k);
-                    sa_x[b] += lse_fix(fsa[b], fix_k);
+                    if (MB) {
+                        float lo, hi;
+                        f2_unpack(psw[b], lo, hi);
+                        sw_x[b] += lse_fix(__fadd_rn(lo, hi), fix_k);
+                        if (need_sa) {
+                            f2_unpack(psa[b], lo, hi);
+                            sa_x[b] += lse_fix(__fadd_rn(lo, hi), fix_k);
+                        }
+                    } else {
+                        sw_x[b] += lse_fix(fsw[b], fix_k);
+                        sa_x[b] += lse_fix(fsa[b], fix_k);
+                    }
                 }
             }
             int cv = 0;
@@ -854,7 +879,7 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 atomicAdd(sl + LSE_ACC_SW + b, (unsigned long long)v[b]);
-                atomicAdd(sl + LSE_ACC_SA + b, (unsigned long long)v[NB + b]);
+                if (!MB || need_sa) atomicAdd(sl + LSE_ACC_SA + b, (unsigned long long)v[NB + b]);
             }
         }
         atomicAdd(sl + LSE_ACC_NP, (unsigned long long)v[2 * NB]);
@@ -1028,6 +1053,36 @@ __device__ __forceinline__ bool persist_finalize(const StepArgs &a, int n, const
     return done;
 }
 
+// Thread 0, between steps of a persistent evolution: the phi box of tile t
+// for the coming step, issued as soon as the grid barrier has made the last
+// step's LSF visible, so that its copy overlaps the step's finalisation
+// (tile_step then issues nothing for its first tile: TilePersist::issued).
+template <int RAD, class T, int NW, int NB>
+__device__ __forceinline__ void issue_phi_box(const StepArgs &a, const CUtensorMap *pm, int t)
+{
+    using G = TileGeo<RAD, T, NW, NB>;
+    extern __shared__ float smem_f[];
+    const uint32_t sm0 = smem_u32(smem_f);
+    const int sb = (int)(((128u - (sm0 & 127u)) & 127u) >> 2);
+    const int ty = t / a.n_strips;
+    const int xs = (t - ty * a.n_strips) * G::USEFUL - 4 * G::HL;
+    const int ys = ty * G::TH - (RAD + 1);
+    tma_box(sm0 + 4u * (uint32_t)(sb + G::PHI_OFF), pm, xs - 4, ys,
+            sm0 + 4u * (uint32_t)(sb + 32), (uint32_t)G::PHI_BYTES);
+}
+
+// At the end of a persistent evolution: the boxes issued for a step that did
+// not run are waited for (bounded) before the CTA exits.
+__device__ __forceinline__ void drain_issued(const TilePersist &pc)
+{
+    extern __shared__ float smem_f[];
+    const uint32_t sm0 = smem_u32(smem_f);
+    const int sb = (int)(((128u - (sm0 & 127u)) & 127u) >> 2);
+    const uint32_t bar_phi = sm0 + 4u * (uint32_t)(sb + 32);
+    if (pc.issued >= 1) wait_bar(bar_phi + 8u, pc.par);
+    if (pc.issued >= 2) wait_bar(bar_phi, pc.par);
+}
+
 // Thread 0 of every CTA after the barrier of step n: the step's totals
 // (slot n mod 3) and the next coefficients; CTA 0 records them and clears
 // the slot and the tile queue of step n - 1 (every CTA read that slot
@@ -1106,19 +1161,18 @@ evolve_tile_kernel(const __grid_constant__ EvolveArgs e,
         if (threadIdx.x == 0) s_pc.stall_ns = 0;
         if (!grid_barrier(st, (unsigned int)(n + 1) * (unsigned int)ncta)) break;
         if (*reinterpret_cast<volatile unsigned int *>(&st->status_bits) & LSE_SBIT_ABORT) break;
-        if (threadIdx.x == 0) persist_sum<EDGE>(a, n, &s_coef, &s_done, cta == 0);
+        if (threadIdx.x == 0) {
+            if (s_pc.issued == 1) {
+                issue_phi_box<RAD, T, NW, 1>(a, (n & 1) ? &phi_map0 : &phi_map1, cta);
+                s_pc.issued = 2;
+            }
+            persist_sum<EDGE>(a, n, &s_coef, &s_done, cta == 0);
+        }
         __syncthreads();
         if (s_done) break;
     }
-    // a data box prefetched for a step that did not run: wait for it
-    // (bounded) before the CTA exits
     __syncthreads();
-    if (s_pc.issued == 1) {
-        extern __shared__ float smem_f[];
-        const uint32_t sm0 = smem_u32(smem_f);
-        const int sb = (int)(((128u - (sm0 & 127u)) & 127u) >> 2);
-        wait_bar(sm0 + 4u * (uint32_t)(sb + 32) + 8u, s_pc.par);
-    }
+    drain_issued(s_pc);
 }
 
 // ---------------------------------------------------------------- vector images
@@ -1199,7 +1253,10 @@ evolve_mb_kernel(const __grid_constant__ EvolveArgs e,
     __shared__ TilePersist s_pc;
     __shared__ MbCoef<NB> s_c;
     __shared__ int s_done, s_redo;
+    __shared__ long long s_tot[NB];     // sum I_b over the image (lse_fix units)
+    __shared__ double s_cp[NB], s_cm[NB];
     const int cta = blockIdx.x, ncta = gridDim.x;
+    bool have_tot = false;
     if (threadIdx.x == 0) {
         // the prologue made the first step's statistics
         for (int b = 0; b < NB; ++b) {
@@ -1235,6 +1292,7 @@ evolve_mb_kernel(const __grid_constant__ EvolveArgs e,
             s_pc.prefetch = n + 1 < e.cap;
             s_pc.slot = pass % 3;
             s_pc.queue = pass & 1;
+            s_pc.need_sa = have_tot ? 0 : 1;
         }
         __syncthreads();
         const CUtensorMap *pm = (n & 1) ? &phi_map1 : &phi_map0;
@@ -1250,6 +1308,7 @@ evolve_mb_kernel(const __grid_constant__ EvolveArgs e,
             const volatile long long *sl = st->acc[pass % 3];
             const unsigned long long miss = (unsigned long long)sl[LSE_ACC_MISS];
             bool redo = false;
+            const bool more = n + 1 < e.cap;
             if (miss && !s_c.zero && redos < 16) {
                 const unsigned int pix = 0xFFFFFFFFu - (unsigned int)(miss & 0xFFFFFFFFull);
                 const double d = fabs(mb_d_at<NB>(a, pix, s_c));
@@ -1274,28 +1333,52 @@ evolve_mb_kernel(const __grid_constant__ EvolveArgs e,
             }
             s_redo = redo ? 1 : 0;
             s_done = 0;
-            if (!redo) {
-                // the new LSF's statistics (Eq. 15) and the next step's factors
-                const int k = st->fix_k;
+            // the coming step's first phi box: this step again, or the next
+            if (s_pc.issued == 1 && (redo || more)) {
+                issue_phi_box<RAD, float, NW, NB>(
+                    a, ((redo ? n : n + 1) & 1) ? &phi_map1 : &phi_map0, cta);
+                s_pc.issued = 2;
+            }
+        }
+        __syncthreads();
+        if (!s_redo && threadIdx.x < NB) {
+            // the new LSF's statistics (Eq. 15), one band per thread (FP64
+            // has a long latency on this part); sum I_b over the image is
+            // that of the first step, whose tiles sum it the same way
+            const int b = threadIdx.x;
+            const volatile long long *sl = st->acc[pass % 3];
+            if (!have_tot) s_tot[b] = sl[LSE_ACC_SA + b];
+            const long long np = sl[LSE_ACC_NP], nm = a.npix - np;
+            const long long sw = sl[LSE_ACC_SW + b], sa = s_tot[b];
+            const int k = st->fix_k;
+            const double sp = ldexp((double)(sa + sw), -(k + 1));
+            const double sm = ldexp((double)(sa - sw), -(k + 1));
+            double al, md;
+            lse_band_coeffs(sp, sm, np, nm, s_cp[b], s_cm[b], al, md);
+            s_c.al[b] = al;      // the finished step's factors are read no more
+            s_c.md[b] = md;
+            if (cta == 0) {
+                st->run_sp[b] = sp;
+                st->run_sm[b] = sm;
+                st->c_plus[b] = s_cp[b];
+                st->c_minus[b] = s_cm[b];
+                st->alpha[b] = al;
+                st->mid[b] = md;
+            }
+        }
+        have_tot = have_tot || !s_redo;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const volatile long long *sl = st->acc[pass % 3];
+            if (!s_redo) {
+                // norm and zero of s_c are still those of the finished step
                 const long long np = sl[LSE_ACC_NP], nm = a.npix - np;
-                double cp[NB], cm[NB], contrast = 0.0, scale = 0.0;
-                MbCoef<NB> nc;
+                double contrast = 0.0, scale = 0.0;
                 for (int b = 0; b < NB; ++b) {
-                    const long long sw = sl[LSE_ACC_SW + b], sa = sl[LSE_ACC_SA + b];
-                    const double sp = ldexp((double)(sa + sw), -(k + 1));
-                    const double sm = ldexp((double)(sa - sw), -(k + 1));
-                    lse_band_coeffs(sp, sm, np, nm, cp[b], cm[b], nc.al[b], nc.md[b]);
-                    contrast = fmax(contrast, fabs(cp[b] - cm[b]));
-                    scale = fmax(scale, fabs(cp[b]) + fabs(cm[b]));
-                    if (cta == 0) {
-                        st->run_sp[b] = sp;
-                        st->run_sm[b] = sm;
-                        st->c_plus[b] = cp[b];
-                        st->c_minus[b] = cm[b];
-                        st->alpha[b] = nc.al[b];
-                        st->mid[b] = nc.md[b];
-                    }
+                    contrast = fmax(contrast, fabs(s_cp[b] - s_cm[b]));
+                    scale = fmax(scale, fabs(s_cp[b]) + fabs(s_cm[b]));
                 }
+                MbCoef<NB> nc = s_c;
                 nc.zero = (np == 0 || nm == 0 || contrast <= LSE_CONTRAST_TOL * scale);
                 nc.norm = 0.0;
                 const bool done = a.early_thresh > 0.0 && (double)sl[LSE_ACC_FL] < a.early_thresh;
@@ -1337,15 +1420,8 @@ evolve_mb_kernel(const __grid_constant__ EvolveArgs e,
             }
         }
     }
-    // a data box prefetched for a step that did not run: wait for it
-    // (bounded) before the CTA exits
     __syncthreads();
-    if (s_pc.issued == 1) {
-        extern __shared__ float smem_f[];
-        const uint32_t sm0 = smem_u32(smem_f);
-        const int sb = (int)(((128u - (sm0 & 127u)) & 127u) >> 2);
-        wait_bar(sm0 + 4u * (uint32_t)(sb + 32) + 8u, s_pc.par);
-    }
+    drain_issued(s_pc);
 }
 
 template <int RAD, int NB>

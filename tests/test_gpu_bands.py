@@ -123,3 +123,50 @@ def test_persistent_path_agrees_with_the_band_passes_and_the_oracle(torch, ctx, 
     assert_mask_parity(m.cpu().numpy(), m_ref)
     assert_mask_parity(m.cpu().numpy(), m2.cpu().numpy())
     assert abs(st["norm"] - st_ref["norm"]) <= 1e-6 * st_ref["norm"]
+
+
+@pytest.fixture(scope="module")
+def scene_u16():
+    sc = scenes.multiband_scene(768, 1024, 4, seed=11, n_roofs=25)
+    return np.ascontiguousarray(sc["image"])
+
+
+@pytest.mark.parametrize("B", [2, 3, 4])
+def test_u16_bands_against_the_oracle(torch, ctx, scene_u16, B):
+    # a uint16 vector image (the library reads it as k / 65535, as the
+    # oracle does): the same bars against the oracle
+    img16 = np.ascontiguousarray(scene_u16[:B, :300, :412])
+    img = img16.astype(np.float32) / np.float32(65535.0)
+    phi0 = scenes.circle_phi(300, 412, radius=110)
+    x16 = torch.from_numpy(img16).cuda()
+    p = torch.from_numpy(phi0).cuda()
+    n0 = ctx.kernel_launches()
+    v, m, st = ctx.evolve(x16, p, "region", iterations=1)
+    torch.cuda.synchronize()
+    # conversion, prologue, candidates (2), the persistent evolution, output
+    assert ctx.kernel_launches() - n0 == 6
+    v_ref, norm, cp, cm, _ = oracle.step(img, phi0)
+    assert np.abs(v.cpu().numpy() - v_ref).max() <= 1e-5
+    assert abs(st["norm"] - norm) <= 1e-6 * norm
+    check_stats(img, v.cpu().numpy(), st)
+    v, m, st = ctx.evolve(x16, p, "region", iterations=150)
+    x32 = torch.from_numpy(img).cuda()
+    v2, m2, st2 = ctx.evolve(x32, p, "region", iterations=150)
+    torch.cuda.synchronize()
+    v_ref, m_ref, st_ref = oracle.evolve(img, phi0, iterations=150)
+    assert st["status"] == "LSE_OK" and st["iterations_run"] == 150
+    assert_mask_parity(m.cpu().numpy(), m_ref)
+    assert np.array_equal(m.cpu().numpy(), m2.cpu().numpy())
+    check_stats(img, v.cpu().numpy(), st)
+
+
+def test_u16_bands_from_host_memory_and_ragged_width(torch, ctx, scene_u16):
+    # host input and a width that is no multiple of the pitch: the library
+    # converts the planes into its pitched FP32 buffer
+    img16 = np.ascontiguousarray(scene_u16[:3, :211, :333])
+    img = img16.astype(np.float32) / np.float32(65535.0)
+    phi0 = scenes.circle_phi(211, 333, radius=70)
+    v, m, st = ctx.evolve(img16, phi0, "region", iterations=40)
+    v_ref, m_ref, st_ref = oracle.evolve(img, phi0, iterations=40)
+    assert_mask_parity(np.asarray(m), m_ref)
+    check_stats(img, np.asarray(v), st)
