@@ -22,7 +22,9 @@ Reported (one JSON line on rank 0):
                (lse_kernel_launches) over the timed steps;
   cpu_baseline the FP64 oracle on the host cores, on crops of the same scene;
   storage_variants  the same workload with BF16 and F16 storage of the data
-               term and the LSF (FP32 arithmetic, 6 B/px per region step);
+               term and the LSF (FP32 arithmetic, 6 B/px per region step), and
+               each storage type's error against the FP64 oracle on a
+               2048 x 2048 crop (mask disagreement, max |v - v_oracle|);
   multiband    the 4-band 2048x2048 scene: vector region term and edge term,
                500 iterations each, CUDA events of lse_evolve
   batch        256 uneven images (sides 128-1024, caps 100-600, early stop)
@@ -77,6 +79,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the 16-bit storage variants")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the storage types' error against the FP64 oracle")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched uneven-image measurement")
     ap.add_argument("--batch-images", type=int, default=256)
@@ -215,6 +219,58 @@ def oracle_throughput(img, phi_r, phi_e, seconds: float, crop: int = 256):
             "sample": f"{cores} crops of {crop}x{crop} px of the benchmark scene, "
                       f"region + edge term, {iters} iterations each, FP64, one thread "
                       f"per crop"}
+
+
+def precision_report(torch, lse, dev, img, phi_r, phi_e, crop: int = 2048, iters: int = 300,
+                     y0: int = 2048, x0: int = 2048):
+    """The error of each storage type against the FP64 oracle on a crop of
+    the benchmark scene (the crop is its own problem: both sides run it),
+    outside any timed region: the fraction of mask pixels that differ, those
+    more than 1 px from the oracle's contour, and max |v - v_oracle| over the
+    pixels where the masks agree.  Region term and edge term (g from each
+    side's own edge indicator), `iters` iterations."""
+    import oracle
+    from scipy import ndimage
+    sl = (slice(y0, y0 + crop), slice(x0, x0 + crop))
+    im = np.ascontiguousarray(img[:, sl[0], sl[1]])
+    pr = np.ascontiguousarray(phi_r[sl])
+    pe = np.ascontiguousarray(phi_e[sl])
+    oracle.build()
+    oracle.set_threads(0)
+    t = time.perf_counter()
+    g_ref = oracle.edge_indicator(im, 1.0, 9, 255.0)
+    ref = {"region": oracle.evolve(im, pr, "region", iterations=iters),
+           "edge": oracle.evolve(im, pe, "edge", g=g_ref, iterations=iters)}
+    oracle_s = time.perf_counter() - t
+    cross = ndimage.generate_binary_structure(2, 1)
+    out = {"crop": f"{crop}x{crop} at ({y0}, {x0}) of the benchmark scene, {iters} iterations",
+           "oracle_seconds": round(oracle_s, 1)}
+    with lse.Context(dev.index, max_pixels=crop * crop, max_bands=1) as c:
+        x = torch.from_numpy(im).to(dev)
+        g = c.precompute_edge(x, 1.0, 9, 255.0)
+        for term, phi in (("region", pr), ("edge", pe)):
+            v_ref, m_ref, _ = ref[term]
+            r = ref_mask = m_ref.astype(bool)
+            ring = (ndimage.binary_dilation(r, cross) & ~r) | (r & ~ndimage.binary_erosion(
+                r, cross, border_value=1))
+            near = ndimage.binary_dilation(ring, np.ones((3, 3), bool))
+            out[term] = {}
+            for sto in ("f32", "bf16", "f16"):
+                v, m, st = c.evolve(x if term == "region" else None,
+                                    torch.from_numpy(phi).to(dev), term,
+                                    g=g if term == "edge" else None, iterations=iters,
+                                    storage=sto)
+                v = v.cpu().numpy()
+                m = m.cpu().numpy().astype(bool)
+                bad = m != ref_mask
+                same = ~bad
+                out[term][sto] = {
+                    "mask_disagree_frac": float(bad.mean()),
+                    "mask_disagree_far_px": int((bad & ~near).sum()),
+                    "v_max_abs_err_where_masks_agree":
+                        float(np.abs(v - v_ref)[same].max()) if same.any() else None,
+                    "status": st["status"]}
+    return out
 
 
 def run_reference(args):
@@ -638,15 +694,12 @@ def main():
         s_e = torch.cuda.Stream(dev)
 
         def step_host():
+            # the library runs its persistent evolutions one at a time, in
+            # the order they were enqueued, whatever their streams: the edge
+            # evolution follows the region's, while each term's copies and
+            # small kernels overlap the other term's evolution
             ctx_r.evolve(hx, hpr, "region", phi_out=ho_r, mask_out=hm_r, stream=s_r, **common)
             ctx_e.precompute_edge(hx, 1.0, 9, 255.0, out=dg, stream=s_e)
-            # the edge evolution after the region's: two persistent step
-            # kernels sharing the SMs interleave unpredictably (360-470 k
-            # Mpixel-it/s over runs); ordered, the copies still overlap the
-            # other term's kernels
-            done_r = torch.cuda.Event()
-            done_r.record(s_r)
-            s_e.wait_event(done_r)
             ctx_e.evolve(None, hpe, "edge", g=dg, phi_out=ho_e, mask_out=hm_e, stream=s_e,
                          **common)
 
@@ -678,8 +731,9 @@ def main():
                # v + mask (region), v + mask (edge)
                "d2h_bytes_per_step": 2 * plane + 2 * npx,
                "streams": "region on one stream, edge on another (edge precompute and "
-                          "copies beside the region evolution, edge evolution after it); "
-                          "host buffers for inputs and results, g on the device"}
+                          "copies beside the region evolution, the library orders the two "
+                          "persistent evolutions); host buffers for inputs and results, "
+                          "g on the device"}
 
     # the same workload with 16-bit storage of the data term and the LSF
     # (FP32 arithmetic): 6 bytes per pixel-iteration of the region step
@@ -720,6 +774,9 @@ def main():
                 "frac": vbytes / (kms / 1e3) / 1e9 / peak,
                 "edge_step_frac": vbytes / (statistics.mean(v_ms_e) / iters / 1e3) / 1e9 / peak,
                 "status": [ctx_r.stats()["status"], ctx_e.stats()["status"]]}
+
+    if variants is not None and not args.no_precision and rank == 0 and world == 1:
+        variants["error_vs_oracle"] = precision_report(torch, lse, dev, img, phi_r, phi_e)
 
     multiband = None
     if not args.no_multiband and world == 1:
