@@ -111,6 +111,9 @@ def _load():
             lib.oracle_step_sampled.argtypes = [dp, i, i, i, i, dp, dp, d, d,
                                                 i, i, ip, ip, dp, dp, dp, dp]
             lib.oracle_step_sampled.restype = i
+            lib.oracle_step_given.argtypes = [dp, i, i, i, i, dp, dp, d, d, i, dp, dp, d, i,
+                                              dp]
+            lib.oracle_step_given.restype = None
             lib.oracle_evolve.argtypes = [dp, i, i, i, i, dp, dp, d, d, i, i,
                                           i, d, dp,
                                           ctypes.POINTER(ctypes.c_ubyte),
@@ -264,6 +267,25 @@ def step(image, phi, term="region", g=None, dt: float = 15.0,
                                         ORDERS[order], int(bool(reinit)), PADDINGS[padding],
                                         _ptr(v), _ptr(norm), _ptr(cp), _ptr(cm))
     return v, float(norm[0]), cp, cm, bool(z)
+
+
+def step_given(image, phi, c_plus, c_minus, norm, zero_force=False, term="region", g=None,
+               dt: float = 15.0, sigma: float = 1.0, ts: int = 9):
+    """One iteration (Eq. 18, Table I step 4) with the region statistics given
+    (c+ / c- per band, the normaliser M of Eq. 17) instead of taken from phi:
+    a row strip of a larger image stepping with the whole image's
+    statistics.  Not re-initialised."""
+    img = _image3(image)
+    B, H, W = img.shape
+    phi = _f64(phi)
+    gg = _f64(g) if g is not None else None
+    cp = _f64(np.resize(np.asarray(c_plus, np.float64), B))
+    cm = _f64(np.resize(np.asarray(c_minus, np.float64), B))
+    v = np.empty((H, W))
+    _load().oracle_step_given(_ptr(img), H, W, B, _term(term), _ptr(gg), _ptr(phi), float(dt),
+                              float(sigma), int(ts), _ptr(cp), _ptr(cm), float(norm),
+                              int(bool(zero_force)), _ptr(v))
+    return v
 
 
 def step_sampled(image, phi, ys, xs, term="region", g=None, dt: float = 15.0,

@@ -432,6 +432,42 @@ int oracle_step(const double *I, int H, int W, int B, int term,
                                c_plus, c_minus);
 }
 
+/* One iteration (listing order, zero padding, not re-initialised) with the
+ * region statistics given instead of taken from phi: c+ / c- per band and
+ * the normaliser M (Eq. 17), as a row strip of a larger image steps with the
+ * whole image's statistics.  zero_force: R = 0.  The edge term ignores them. */
+void oracle_step_given(const double *I, int H, int W, int B, int term, const double *g,
+                       const double *phi, double dt, double sigma, int ts,
+                       const double *c_plus, const double *c_minus, double norm,
+                       int zero_force, double *v)
+{
+    size_t N = (size_t)H * W;
+    double *u = (double *)malloc(N * sizeof(double));
+    double *G = (double *)malloc((size_t)ts * ts * sizeof(double));
+    step_ctx c;
+    c.I = I;
+    c.g = g;
+    c.phi = phi;
+    c.H = H;
+    c.W = W;
+    c.B = B;
+    c.term = term;
+    c.dt = dt;
+    for (int b = 0; b < B; ++b) {
+        c.c_plus[b] = c_plus[b];
+        c.c_minus[b] = c_minus[b];
+    }
+    c.norm = norm;
+    c.zero_force = zero_force || !(norm > 0.0);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            u[(size_t)y * W + x] = update_at(&c, y, x);
+    oracle_gaussian_taps(sigma, ts, G);
+    oracle_conv_same(u, H, W, G, ts, v);
+    free(u);
+    free(G);
+}
+
 /* The same iteration evaluated only at n sample pixels (ys[k], xs[k]).
  * The global quantities (c+/c-, max|D|) are still computed over the whole
  * image; u is evaluated on the window each sample needs.  For checks of

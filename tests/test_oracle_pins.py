@@ -662,3 +662,29 @@ def test_early_stop_after_several_iterations():
     assert st["iterations_run"] == len(h) and len(h) > k + 1
     assert st["last_flips"] == h[-1]
     np.testing.assert_allclose(v, v_ref, rtol=1e-11, atol=1e-12)
+
+
+# ---------------------------------------------------------------- given statistics (row strips)
+@pytest.mark.parametrize("B,term", [(1, "region"), (3, "region"), (1, "edge")])
+def test_step_with_given_statistics(B, term):
+    # with the image's own statistics the step is the ordinary step; on a
+    # row strip with r + 1 halo rows and the whole image's statistics the
+    # owned rows are those of the whole image's step (Eq. 18 and the
+    # smoothing reach r + 1 rows)
+    I = rng_image((B, 23, 17), 120 + B)
+    phi = rng_phi(23, 17, 121)
+    g = oracle.edge_indicator(I) if term == "edge" else None
+    v, norm, cp, cm, z = oracle.step(I, phi, term=term, g=g, sigma=1.5, ts=7)
+    v2 = oracle.step_given(I, phi, cp, cm, norm, z, term=term, g=g, sigma=1.5, ts=7)
+    np.testing.assert_array_equal(v, v2)
+    h = 4                                     # r + 1 for TS 7
+    y0, y1 = 9, 15
+    sl = slice(y0 - h, y1 + h)
+    gs = g[sl] if g is not None else None
+    vs = oracle.step_given(I[:, sl], phi[sl], cp, cm, norm, z, term=term, g=gs, sigma=1.5,
+                           ts=7)
+    np.testing.assert_array_equal(vs[h:h + (y1 - y0)], v[y0:y1])
+    # a strip at the image's top edge has no halo above
+    vt = oracle.step_given(I[:, :6 + h], phi[:6 + h], cp, cm, norm, z, term=term,
+                           g=g[:6 + h] if g is not None else None, sigma=1.5, ts=7)
+    np.testing.assert_array_equal(vt[:6], v[:6])
