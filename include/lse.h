@@ -406,6 +406,111 @@ lse_status lse_server_advance(lse_server *sv, int ticks, int *running, void *str
  * the request: a later poll of the id returns LSE_ERR_INVALID_ARG. */
 lse_status lse_server_poll(lse_server *sv, long long id, int *state, lse_stats *stats);
 
+/* ------------------------------------------------------------ row strips
+ * One image split by rows between processes (one GPU each).  The paper runs
+ * one image in one process; these calls are this library's.  A rank owns
+ * rows [y0, y1) of the H x W image and holds the strip [y0 - h, y1 + h) of
+ * it, clipped to the image, with h = r + 1 halo rows, r = (ts - 1) / 2:
+ * Eq. 18's central differences reach one row and Step 4's smoothing r rows,
+ * so a step on the strip gives the owned rows of the whole image's step
+ * exactly, provided it uses the whole image's region statistics (the means
+ * of Eq. 15 and the normaliser of Eq. 17, global quantities).  The caller
+ * (a driver such as the package's strips module) sums the strips'
+ * partial statistics over the ranks, steps each strip with the totals,
+ * and copies each strip's first and last h owned rows into its neighbours'
+ * halos after every step.
+ *
+ * Strips of one image, given the same totals, compute the same bits
+ * however the image is split: the sums are exact integers (each value
+ * rounded once to a multiple of 2^-fix_k), so their total does not depend
+ * on which rank added which pixel. */
+
+/* Partial statistics of the owned rows of one strip (lse_strip_partials),
+ * or their sums over all ranks (the caller adds the integer fields, takes
+ * the minimum of imin and the maximum of imax and amax).
+ *   npix      pixels summed.
+ *   n_plus    |{phi >= 0}|.
+ *   flips     pixels where (phi >= 0) differs from (phi_prev >= 0).
+ *   sum_w[b]  sum of s(x) q_b(x), s = +1 where phi >= 0 and -1 elsewhere,
+ *   sum_a[b]  and sum of q_b(x), where q_b(x) = I_b(x) 2^fix_k rounded to
+ *             the nearest integer: sum_{phi>=0} I_b = (sum_a + sum_w) / 2
+ *             and sum_{phi<0} I_b = (sum_a - sum_w) / 2, times 2^-fix_k.
+ *   imin/imax range of band 0; amax = max |I_b| over all bands.
+ *   fix_k     the scale the sums use (lse_strip_scale). */
+typedef struct {
+    long long npix;
+    long long n_plus;
+    long long flips;
+    long long sum_w[8];
+    long long sum_a[8];
+    double imin, imax, amax;
+    int fix_k;
+    int bands;
+} lse_strip_sums;
+
+/* The fixed-point scale for an image of npix pixels whose band values are at
+ * most amax in magnitude: the largest k (within -120..120) with
+ * max(npix, 32) * amax * 2^k at most 2^61, so that no total, nor any sum
+ * of 32 values, overflows 64 bits (30 when amax is 0 or not finite).  A
+ * host function: it needs no context and no GPU. */
+int lse_strip_scale(double amax, long long npix);
+
+/* Partial statistics of rows [row0, row1) of a strip of Hs rows.
+ *   image     B x Hs x W in `dtype` (see conventions), host or device; NULL
+ *             for the edge term (the sums and the range are then 0).
+ *   phi       Hs x W float32 LSF, host or device; NULL: only npix and the
+ *             range are computed (a first call, before fix_k is known).
+ *   phi_prev  Hs x W float32 LSF of the previous iteration for the flip
+ *             count, or NULL (flips = 0).
+ *   fix_k     the scale of the sums, from lse_strip_scale on the whole
+ *             image's amax and pixel count (-120..120).
+ * Synchronises `stream` and fills *out. */
+lse_status lse_strip_partials(lse_ctx *ctx, const void *image, lse_dtype dtype, int Hs, int W,
+                              int B, int row0, int row1, const float *phi,
+                              const float *phi_prev, int fix_k, lse_strip_sums *out,
+                              void *stream);
+
+/* Vector images (B > 1), region term: the normaliser of Eq. 17 is the
+ * maximum of |D(x)| over the whole image, D(x) = sum_b alpha_b (I_b(x) -
+ * mid_b), alpha_b = 2 (c+_b - c-_b), mid_b = (c+_b + c-_b) / 2 from the
+ * totals (Eq. 15).  *dmax receives that maximum over rows [row0, row1) of
+ * the strip (D evaluated in FP32 as the step does); the caller takes the
+ * maximum over the ranks and passes it to lse_strip_step.  0 when the
+ * totals make the force zero (see lse_params' degenerate rule).
+ * Synchronises `stream`. */
+lse_status lse_strip_dmax(lse_ctx *ctx, const void *image, lse_dtype dtype, int Hs, int W,
+                          int B, int row0, int row1, const lse_strip_sums *totals, float dt,
+                          double *dmax, void *stream);
+
+/* One iteration (Eq. 18 then Step 4) on a strip of Hs rows with the whole
+ * image's statistics.
+ *   image       region term: B x Hs x W in `dtype`, host or device.
+ *   g           edge term: Hs x W float32 rows of the whole image's g
+ *               (lse_precompute_edge); NULL for the region term.
+ *   phi         Hs x W float32 LSF, host or device.
+ *   binarise_in nonzero: the step reads phi as +1 where phi >= 0 and -1
+ *               elsewhere (the re-initialisation of the previous iteration,
+ *               in the listing's order).
+ *   params      term, dt, sigma and ts as for lse_evolve; the iteration
+ *               count, re-initialisation and early stop are the caller's
+ *               (ignored here); storage F32, the listing's order and zero
+ *               padding only.
+ *   totals      region term: the ranks' summed lse_strip_sums of phi
+ *               (npix = H * W); NULL for the edge term.
+ *   norm        B > 1 region term: the maximum over the ranks of
+ *               lse_strip_dmax; ignored otherwise (one band takes max|D|
+ *               in closed form from the totals' range).
+ *   v_out       Hs x W float32: v of this iteration, host or device.  Rows
+ *               within h of a cut edge of the strip (an edge that is not the
+ *               image's) are not the whole image's: the neighbours' halo
+ *               exchange replaces them.
+ * Synchronises `stream`.  Returns LSE_ERR_NONFINITE or LSE_ERR_TIMEOUT for
+ * the device-side conditions of lse_stats.status. */
+lse_status lse_strip_step(lse_ctx *ctx, const void *image, lse_dtype dtype, const float *g,
+                          int Hs, int W, int B, const float *phi, int binarise_in,
+                          const lse_params *params, const lse_strip_sums *totals, double norm,
+                          float *v_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

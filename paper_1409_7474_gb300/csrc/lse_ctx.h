@@ -70,6 +70,8 @@ struct lse_ctx {
     void *bhost = nullptr;
     size_t bhost_cap = 0;            // bytes (pinned)
     cudaStream_t cap_stream = nullptr;  // stream on which batches are captured
+    void *strip_acc = nullptr;       // lse_strip_*: the pass's device accumulator
+    size_t strip_acc_cap = 0;        // bytes
 };
 
 namespace lse_detail {
@@ -102,6 +104,15 @@ lse_status cuda_fail(lse_ctx *ctx, cudaError_t e, const char *what);
 lse_status ensure(lse_ctx *ctx, void **p, size_t *cap, size_t bytes, cudaStream_t s,
                   const char *name);
 bool aligned16(const void *p);
+// Validates the image shape against the context.
+lse_status check_image_args(lse_ctx *ctx, lse_dtype dtype, int H, int W, int B);
+// Grows both LSF buffers to `elems` elements each.
+lse_status ensure_phi(lse_ctx *ctx, size_t elems, cudaStream_t s);
+// Makes `image` available as pitched float32 on the device (in place when it
+// already is, else converted into the context's buffer).
+lse_status stage_image(lse_ctx *ctx, const void *image, PtrKind kind, lse_dtype dtype, int H,
+                       int W, int B, cudaStream_t s, const float **img_out, int *pitch_out,
+                       size_t *band_stride);
 // Validates lse_params for an image of B bands (messages via set_err).
 lse_status check_params(lse_ctx *ctx, const lse_params &p, int B);
 // Converts a device state record into the caller's statistics.

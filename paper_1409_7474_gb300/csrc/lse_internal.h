@@ -377,6 +377,10 @@ bool plan_step(int H, int W, int B, const lse_params &p, int pitch, size_t band_
                float *dplane, StepPlan *plan);
 // Launches iteration n (0-based) of the plan.
 cudaError_t launch_step(StepPlan &plan, int n, cudaStream_t s);
+// Launches one step from phi[0] into phi[1] with the coefficients already in
+// the state record: the plan's only iteration, reading phi[0] as sign(phi[0])
+// when binarise_in (the caller's previous step re-initialised).
+cudaError_t launch_step_once(StepPlan &plan, bool binarise_in, cudaStream_t s);
 // Launches every iteration of the plan as one persistent evolution when the
 // plan is of the tile form and LSE_PERSIST is not "0"; cudaErrorNotSupported
 // (nothing launched) otherwise, and the caller launches one step at a time.

@@ -381,7 +381,7 @@ __device__ __forceinline__ long long lse_fix(float x, int k)
 // The exponent k of lse_fix for N pixels of magnitude at most `maxabs`:
 // sums of N values below 2^62 once scaled, and a lane's partial (at most 32
 // values) too.
-__device__ __forceinline__ int lse_fix_scale(double maxabs, long long n)
+__host__ __device__ inline int lse_fix_scale(double maxabs, long long n)
 {
     if (!(maxabs > 0.0) || !isfinite(maxabs)) return 30;
     int e;

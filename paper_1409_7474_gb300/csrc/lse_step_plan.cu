@@ -306,4 +306,19 @@ cudaError_t launch_step(StepPlan &plan, int n, cudaStream_t s)
     }
 }
 
+cudaError_t launch_step_once(StepPlan &plan, bool binarise_in, cudaStream_t s)
+{
+    StepArgs &a = plan.args;
+    lse_iteration_flags(a, 0, 1, 0, false, plan.form != LSE_FORM_GENERIC, plan.phi);
+    a.binarise_in = binarise_in ? 1 : 0;
+    switch (plan.form) {
+    case LSE_FORM_TILE:
+        return launch_step_tile(a, plan.phi_maps[0], plan.data_map, plan.nblocks, s);
+    case LSE_FORM_STREAM:
+        return launch_step_tma(a, plan.phi_maps[0], plan.data_map, plan.nblocks, plan.wpc, s);
+    default:
+        return launch_step_generic(a, plan.nblocks, s);
+    }
+}
+
 }  // namespace lse_detail

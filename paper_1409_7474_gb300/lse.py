@@ -83,6 +83,16 @@ class Problem(ctypes.Structure):
                 ("phi_out", ctypes.c_void_p), ("mask_out", ctypes.c_void_p)]
 
 
+class StripSums(ctypes.Structure):
+    """lse_strip_sums: partial statistics of a strip's owned rows, or their
+    totals over the ranks."""
+    _fields_ = [("npix", ctypes.c_longlong), ("n_plus", ctypes.c_longlong),
+                ("flips", ctypes.c_longlong), ("sum_w", ctypes.c_longlong * 8),
+                ("sum_a", ctypes.c_longlong * 8), ("imin", ctypes.c_double),
+                ("imax", ctypes.c_double), ("amax", ctypes.c_double),
+                ("fix_k", ctypes.c_int), ("bands", ctypes.c_int)]
+
+
 _vp = ctypes.c_void_p
 _lib.lse_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int]
 _lib.lse_create.restype = ctypes.c_int
@@ -125,12 +135,28 @@ _lib.lse_server_advance.restype = ctypes.c_int
 _lib.lse_server_poll.argtypes = [_vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(Stats)]
 _lib.lse_server_poll.restype = ctypes.c_int
+_lib.lse_strip_scale.argtypes = [ctypes.c_double, ctypes.c_longlong]
+_lib.lse_strip_scale.restype = ctypes.c_int
+_lib.lse_strip_partials.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                    ctypes.c_int, ctypes.POINTER(StripSums), _vp]
+_lib.lse_strip_partials.restype = ctypes.c_int
+_lib.lse_strip_dmax.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(StripSums), ctypes.c_float,
+                                ctypes.POINTER(ctypes.c_double), _vp]
+_lib.lse_strip_dmax.restype = ctypes.c_int
+_lib.lse_strip_step.argtypes = [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(Params),
+                                ctypes.POINTER(StripSums), ctypes.c_double, _vp, _vp]
+_lib.lse_strip_step.restype = ctypes.c_int
 
 SYMBOLS = ("lse_create", "lse_destroy", "lse_last_error", "lse_precompute_edge",
            "lse_evolve", "lse_get_stats", "lse_version", "lse_kernel_launches",
            "lse_evolve_static",
            "lse_evolve_batch", "lse_autotune", "lse_server_create", "lse_server_destroy",
-           "lse_server_submit", "lse_server_advance", "lse_server_poll")
+           "lse_server_submit", "lse_server_advance", "lse_server_poll",
+           "lse_strip_scale", "lse_strip_partials", "lse_strip_dmax", "lse_strip_step")
 STATIC_MAX_PIXELS = 262144
 
 
@@ -321,6 +347,63 @@ class Context:
                                       _stream_ptr(stream, self.device)))
         return list(rows)
 
+    # -- row strips (lse_strip_*)
+    def strip_partials(self, image, phi, row0: int, row1: int, fix_k: int = 0,
+                       phi_prev=None, bands: int = None, width: int = None,
+                       stream=None) -> StripSums:
+        """lse_strip_partials over rows [row0, row1) of a strip: image
+        (B x Hs x W, or None for the edge term), phi / phi_prev (Hs x W
+        float32, or None).  Returns the StripSums."""
+        if image is not None:
+            B, Hs, W = _shape3(image)
+            dcode = _dtype_code(image)
+        else:
+            B = bands or 1
+            Hs, W = tuple(phi.shape)
+            dcode = F32
+        out = StripSums()
+        self._check(_lib.lse_strip_partials(
+            self._h, _ptr(image), dcode, Hs, W, B, int(row0), int(row1), _ptr(phi),
+            _ptr(phi_prev), int(fix_k), ctypes.byref(out), _stream_ptr(stream, self.device)))
+        return out
+
+    def strip_dmax(self, image, row0: int, row1: int, totals: StripSums, dt: float = 15.0,
+                   stream=None) -> float:
+        """lse_strip_dmax: max |D| over rows [row0, row1) of the strip for the
+        totals' statistics (vector images)."""
+        B, Hs, W = _shape3(image)
+        out = ctypes.c_double()
+        self._check(_lib.lse_strip_dmax(
+            self._h, _ptr(image), _dtype_code(image), Hs, W, B, int(row0), int(row1),
+            ctypes.byref(totals), float(dt), ctypes.byref(out),
+            _stream_ptr(stream, self.device)))
+        return out.value
+
+    def strip_step(self, image, phi, totals: StripSums = None, norm: float = 0.0,
+                   term: str = "region", g=None, binarise_in: bool = False,
+                   dt: float = 15.0, sigma: float = 1.0, ts: int = 9, v_out=None,
+                   stream=None):
+        """lse_strip_step: one iteration on a strip with the whole image's
+        statistics.  Returns v_out (Hs x W float32, on phi's device)."""
+        term_code = TERM_REGION if term in ("region", TERM_REGION) else TERM_EDGE
+        Hs, W = tuple(phi.shape)
+        if term_code == TERM_REGION:
+            B, _, _ = _shape3(image)
+            dcode = _dtype_code(image)
+        else:
+            B, dcode = 1, F32
+        if v_out is None:
+            v_out = _empty_like_place(phi, (Hs, W), np.float32,
+                                      torch.float32 if torch is not None else None)
+        p = Params(term_code, float(dt), float(sigma), int(ts), 1, 0, 0.0, F32, 0, 0)
+        self._check(_lib.lse_strip_step(
+            self._h, _ptr(image) if term_code == TERM_REGION else None, dcode,
+            _ptr(g) if term_code == TERM_EDGE else None, Hs, W, B, _ptr(phi),
+            int(bool(binarise_in)), ctypes.byref(p),
+            ctypes.byref(totals) if totals is not None else None, float(norm), _ptr(v_out),
+            _stream_ptr(stream, self.device)))
+        return v_out
+
     def kernel_launches(self) -> int:
         """lse_kernel_launches: kernels this context's evolve and
         precompute_edge calls have enqueued."""
@@ -419,6 +502,11 @@ def create(device: int = 0, max_pixels: int = 1 << 20, max_bands: int = 4) -> Co
 
 def destroy(ctx: Context) -> None:
     ctx.destroy()
+
+
+def strip_scale(amax: float, npix: int) -> int:
+    """lse_strip_scale: the fixed-point exponent of the strips' sums."""
+    return int(_lib.lse_strip_scale(float(amax), int(npix)))
 
 
 def raw_library():

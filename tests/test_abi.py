@@ -94,3 +94,43 @@ def test_no_cpu_fallback_in_binding(lse):
     # the binding refuses to import without the library
     src = open(os.path.join(ROOT, "paper_1409_7474_gb300", "lse.py")).read()
     assert "raise ImportError" in src and "oracle" not in src
+
+
+def test_strip_sums_layout_matches_header(lse, tmp_path):
+    src = tmp_path / "strip.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "lse.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(lse_strip_sums),"
+        " offsetof(lse_strip_sums, sum_w), offsetof(lse_strip_sums, sum_a),"
+        " offsetof(lse_strip_sums, imin), offsetof(lse_strip_sums, fix_k),"
+        " offsetof(lse_strip_sums, bands));return 0;}\n")
+    exe = tmp_path / "strip"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    S = lse.StripSums
+    assert vals == [ctypes.sizeof(S), S.sum_w.offset, S.sum_a.offset, S.imin.offset,
+                    S.fix_k.offset, S.bands.offset]
+
+
+@pytest.mark.parametrize("amax,npix", [(1.0, 65536), (0.7, 1000), (255.0, 8192 * 8192),
+                                       (3.0, 5), (1e-30, 10 ** 6), (1e30, 4)])
+def test_strip_scale_is_the_largest_safe_exponent(lse, amax, npix):
+    # a host function: no context, no GPU.  k is the largest exponent with
+    # max(npix, 32) * amax * 2^k <= 2^61
+    k = lse.strip_scale(amax, npix)
+    n = max(npix, 32)
+    if -120 < k < 120:
+        assert n * amax * 2.0 ** k <= 2.0 ** 61 < n * amax * 2.0 ** (k + 1)
+    assert lse.strip_scale(0.0, npix) == 30 and lse.strip_scale(float("nan"), npix) == 30
+
+
+def test_strip_calls_reject_a_null_context(lse):
+    s = lse.StripSums()
+    lib = lse.raw_library()
+    assert lib.lse_strip_partials(None, None, 0, 4, 4, 1, 0, 4, None, None, 0,
+                                  ctypes.byref(s), None) == lse.LSE_ERR_INVALID_ARG
+    d = ctypes.c_double()
+    assert lib.lse_strip_dmax(None, None, 0, 4, 4, 2, 0, 4, ctypes.byref(s), 15.0,
+                              ctypes.byref(d), None) == lse.LSE_ERR_INVALID_ARG
+    assert lib.lse_strip_step(None, None, 0, None, 4, 4, 1, None, 0, None, None, 0.0,
+                              None, None) == lse.LSE_ERR_INVALID_ARG
