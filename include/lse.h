@@ -375,9 +375,22 @@ lse_status lse_autotune(lse_ctx *ctx, int n, const lse_problem *problems, int it
  * budget; every lse_server_advance call then runs the next iterations of all
  * admitted requests together (in the launches lse_evolve_batch uses) and
  * retires those that reached their cap or stopped early, writing their
- * phi_out / mask_out.  A request's result is bit for bit that of lse_evolve
- * on the same image, whatever else runs beside it.  One server belongs to
- * one context; its calls are not thread-safe. */
+ * phi_out / mask_out.  Three kinds of request skip the mix and run alone,
+ * to their end, inside one advance, through lse_evolve itself (one
+ * persistent launch; the oldest first, one per advance, before the mix's
+ * iterations): vector images of the region term (their own path stages the
+ * bands in one launch per evolution; the mix needs three per iteration),
+ * images of 2^21 pixels or more (their tiles fill the GPU alone), and,
+ * under light load (nothing in the mix, at most 4 requests waiting), every
+ * request: an advance then runs only the oldest, so that a lightly loaded
+ * server answers as fast as a direct call per request.  Each needs H * W
+ * within the context's max_pixels and B within its max_bands, else it joins
+ * the mix.  A request's result is bit for bit that of
+ * lse_evolve on the same image, whatever else runs beside it (in the mix,
+ * a single-band or edge request keeps the CTA count, statistics and
+ * reductions lse_evolve gives it; a vector image too large for the context
+ * joins the mix and matches lse_evolve with LSE_PERSIST=0).  One server
+ * belongs to one context; its calls are not thread-safe. */
 typedef struct lse_server lse_server;
 
 /* Creates a server on ctx's GPU whose requests share budget_bytes (>= 1 MiB)
@@ -395,10 +408,12 @@ void lse_server_destroy(lse_server *sv);
  * ts > 15, more than 4 bands, or a request larger than the budget. */
 lse_status lse_server_submit(lse_server *sv, const lse_problem *problem, long long *id);
 
-/* Admits queued requests that fit, runs `ticks` iterations of every running
- * request on `stream`, retires the finished ones, and synchronises the
- * stream.  *running (may be NULL) receives the number of requests still
- * running. */
+/* Runs the oldest request that runs alone (see above) to its end, admits
+ * queued requests of the mix that fit, runs `ticks` iterations of every
+ * request in the mix on `stream`, retires the finished ones, and
+ * synchronises the stream.  *running (may be NULL) receives the number of
+ * requests in the mix (queued requests, and those that run alone, are not
+ * counted: poll each request to see it done). */
 lse_status lse_server_advance(lse_server *sv, int ticks, int *running, void *stream);
 
 /* *state = 0 queued, 1 running, 2 done.  When done, *stats (may be NULL)

@@ -9,7 +9,13 @@
 // reaches its cap or stops early: its output is written, its statistics
 // kept for lse_server_poll, and its memory returned.  Each request keeps the
 // CTA count, statistics and reductions lse_evolve would give it alone, so
-// its result does not depend on what else is running.
+// its result does not depend on what else is running.  Vector images and
+// large images never join the mix: each runs alone, to its end, through
+// lse_evolve itself (one persistent launch) inside one advance, the oldest
+// first, one per advance.  Under light load (the mix empty, a few requests
+// waiting) every request runs that way, one per advance, in arrival order.
+// For one band and the edge term lse_evolve's persistent launch gives the
+// bits the mix gives.
 #include <math.h>
 #include <string.h>
 
@@ -27,6 +33,16 @@ using namespace lse_detail;
 namespace {
 
 constexpr int kMaxSlots = 1024;
+// Requests that run alone rather than in the mix: vector images of the
+// region term, whose own path is one persistent launch that stages the
+// bands itself (the mix takes three launches per iteration for them), and
+// images of at least this many pixels, whose tiles fill the GPU by
+// themselves (more than twice its SM count of 64-row tiles), so that the
+// mix's per-iteration launches would only add their overhead.
+constexpr long long kSoloPixels = 1ll << 21;
+// At most this many requests waiting and none in the mix: light load, one
+// request at a time, alone.
+constexpr size_t kLightQueue = 4;
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
@@ -83,6 +99,7 @@ struct Request {
     int pitch = 0;
     ClassKey key{};
     lse_stats stats{};
+    bool solo = false;          // runs alone, through lse_evolve (see kSoloPixels)
 };
 
 // Bytes of one request's planes (of its storage type) and partials in the
@@ -272,6 +289,9 @@ lse_status lse_server_submit(lse_server *sv, const lse_problem *problem, long lo
     const long long rid = sv->next_id++;
     Request &req = sv->reqs[rid];
     req.q = q;
+    // (lse_evolve needs the image to fit the context)
+    req.solo = ((region && q.B > 1) || (long long)q.H * q.W >= kSoloPixels) &&
+               (size_t)q.H * q.W <= ctx->max_pixels && q.B <= ctx->max_bands;
     sv->queue.push_back(rid);
     *id = rid;
     return LSE_OK;
@@ -287,9 +307,53 @@ lse_status lse_server_advance(lse_server *sv, int ticks, int *running, void *str
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     lse_status r;
 
-    // ---- admission, first come first served, while the budget allows
-    while (!sv->queue.empty() && sv->running < kMaxSlots) {
-        Request &req = sv->reqs[sv->queue.front()];
+    // ---- one request alone, to its end, through lse_evolve's own path (one
+    // persistent launch; for one band and the edge term the same bits as
+    // the mix's launches give it).  Light load (the mix empty, at most
+    // kLightQueue requests waiting): the oldest request, and nothing else
+    // this advance -- a direct call per request in arrival order, which is
+    // the fastest way through when requests rarely overlap.  Otherwise the
+    // oldest request that always runs alone, beside the mix.
+    if (ticks > 0) {
+        auto pick = sv->queue.end();
+        bool light = false;
+        if (sv->running == 0 && !sv->queue.empty() && sv->queue.size() <= kLightQueue) {
+            const lse_problem &q = sv->reqs[sv->queue.front()].q;
+            if ((size_t)q.H * q.W <= ctx->max_pixels && q.B <= ctx->max_bands) {
+                pick = sv->queue.begin();
+                light = true;
+            }
+        }
+        if (pick == sv->queue.end())
+            pick = std::find_if(sv->queue.begin(), sv->queue.end(),
+                                [&](long long id) { return sv->reqs[id].solo; });
+        if (pick != sv->queue.end()) {
+            Request &req = sv->reqs[*pick];
+            const lse_problem &q = req.q;
+            lse_stats st;
+            r = lse_evolve(ctx, q.params.term == LSE_TERM_REGION ? q.image : nullptr, q.dtype,
+                           q.H, q.W, q.B, q.g, q.phi0, &q.params, q.phi_out, q.mask_out, &st,
+                           stream);
+            if (r != LSE_OK) return r;
+            st.elapsed_ms = -1.0f;
+            req.stats = st;
+            req.state = REQ_DONE;
+            sv->queue.erase(pick);
+            if (light) {
+                if (running) *running = 0;
+                return LSE_OK;
+            }
+        }
+    }
+
+    // ---- admission into the mix, first come first served, while the budget
+    // allows (requests that run alone wait for their turn above)
+    for (auto qi = sv->queue.begin(); qi != sv->queue.end() && sv->running < kMaxSlots;) {
+        Request &req = sv->reqs[*qi];
+        if (req.solo) {
+            ++qi;
+            continue;
+        }
         const size_t bytes = request_bytes(req.q, sv->nparts);
         size_t off = 0;
         if (!sv->alloc.take(bytes, &off)) break;
@@ -301,8 +365,8 @@ lse_status lse_server_advance(lse_server *sv, int ticks, int *running, void *str
             sv->alloc.give(off, bytes);
             return r;
         }
-        sv->slot_req[slot] = sv->queue.front();
-        sv->queue.pop_front();
+        sv->slot_req[slot] = *qi;
+        qi = sv->queue.erase(qi);
         ++sv->running;
     }
     if (running) *running = sv->running;

@@ -11,7 +11,6 @@ import ctypes
 import numpy as np
 import pytest
 
-from _parity import is_vector_region, step_launches
 from paper_1409_7474_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -54,11 +53,9 @@ def device_items(torch, ctx, probs):
 
 
 def alone(torch, ctx, it):
-    # vector images on the server take the band passes: so does the call alone
-    with step_launches(is_vector_region(it)):
-        v, m, st = ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
-                              iterations=it["iterations"],
-                              early_stop_frac=it["early_stop_frac"], storage=it["storage"])
+    v, m, st = ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
+                          iterations=it["iterations"],
+                          early_stop_frac=it["early_stop_frac"], storage=it["storage"])
     torch.cuda.synchronize()
     return v.cpu().numpy(), m.cpu().numpy(), st
 
@@ -209,4 +206,86 @@ def test_server_rejections(torch, lse, ctx):
     assert results[rid][2]["iterations_run"] == 2
     # reported once, then forgotten
     assert lib.lse_server_poll(sv._h, rid, ctypes.byref(st), None) == lse.LSE_ERR_INVALID_ARG
+    sv.destroy()
+
+
+def test_a_lone_request_runs_to_its_end_in_one_advance(torch, lse, ctx):
+    # one band or the edge term alone, and a vector image always: lse_evolve's
+    # persistent path inside the advance, the same bits
+    probs = scenes.batch_problems(6, seed=31, min_side=64, max_side=200, cap_range=(30, 40))
+    probs[0]["image"] = probs[0]["image"][:1]
+    probs[0]["term"] = "region"
+    probs[1]["term"] = "edge"
+    probs[2]["image"] = np.ascontiguousarray(np.repeat(probs[2]["image"][:1], 3, axis=0))
+    probs[2]["term"] = "region"
+    for q in probs[:3]:
+        q["early_stop_frac"] = 0.0
+    items = device_items(torch, ctx, probs[:3])
+    for k, it in enumerate(items):
+        sv = lse.Server(ctx, 512 << 20)
+        rid = sv.submit(it)
+        left = sv.advance(1)
+        r = sv.poll(rid)
+        assert left == 0 and r is not None
+        v, m, st = r
+        v1, m1, st1 = alone(torch, ctx, it)
+        assert np.array_equal(v.cpu().numpy().view(np.uint32), v1.view(np.uint32))
+        assert np.array_equal(m.cpu().numpy(), m1)
+        assert st["iterations_run"] == it["iterations"] and st["elapsed_ms"] == -1.0
+        sv.destroy()
+
+
+def test_vector_and_large_requests_run_alone_beside_the_mix(torch, lse, ctx):
+    # small single-band requests join the mix and advance `ticks` iterations
+    # per call; a vector image and an image of 2^21 pixels or more each run
+    # alone, to their end, one per advance, oldest first
+    probs = scenes.batch_problems(5, seed=41, min_side=64, max_side=128, cap_range=(40, 50))
+    for q in probs:
+        q["image"] = q["image"][:1]
+        q["term"] = "region"
+        q["early_stop_frac"] = 0.0
+    big = scenes.batch_problems(1, seed=42, min_side=1449, max_side=1449, cap_range=(20, 21))[0]
+    big["image"] = big["image"][:1]
+    big["term"], big["early_stop_frac"] = "region", 0.0
+    vec = scenes.batch_problems(1, seed=43, min_side=100, max_side=100, cap_range=(30, 31))[0]
+    vec["image"] = np.ascontiguousarray(np.repeat(vec["image"][:1], 4, axis=0))
+    vec["term"], vec["early_stop_frac"] = "region", 0.0
+    assert big["phi0"].size >= 1 << 21
+    ctx = lse.Context(0, max_pixels=1 << 22, max_bands=4)
+    items = device_items(torch, ctx, probs[:3] + [big, vec] + probs[3:])
+    sv = lse.Server(ctx, 512 << 20)
+    ids = [sv.submit(it) for it in items]
+    running = sv.advance(4)            # the big image alone; the small ones join the mix
+    assert running == 5
+    assert sv.poll(ids[3]) is not None and sv.poll(ids[4]) is None
+    running = sv.advance(4)            # the vector image alone
+    assert sv.poll(ids[4]) is not None and running == 5
+    results = {}
+    drain(sv, [ids[k] for k in (0, 1, 2, 5, 6)], results)
+    sv.destroy()
+    for k in (0, 1, 2, 5, 6):
+        v, m, st = results[ids[k]]
+        v1, m1, _ = alone(torch, ctx, items[k])
+        assert np.array_equal(v.cpu().numpy().view(np.uint32), v1.view(np.uint32))
+    ctx.destroy()
+
+
+def test_light_load_runs_one_request_per_advance_in_arrival_order(torch, lse, ctx):
+    # at most four waiting and nothing in the mix: each advance runs the
+    # oldest request alone, to its end; five waiting start the mix
+    probs = scenes.batch_problems(5, seed=51, min_side=48, max_side=96, cap_range=(20, 30))
+    for q in probs:
+        q["image"] = q["image"][:1]
+        q["early_stop_frac"] = 0.0
+    items = device_items(torch, ctx, probs)
+    sv = lse.Server(ctx, 512 << 20)
+    ids = [sv.submit(it) for it in items[:3]]
+    for k in range(3):
+        assert sv.advance(2) == 0
+        assert sv.poll(ids[k]) is not None
+        assert all(sv.poll(r) is None for r in ids[k + 1:])
+    ids = [sv.submit(it) for it in items]
+    assert sv.advance(2) == 5
+    results = {}
+    drain(sv, ids, results)
     sv.destroy()
