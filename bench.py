@@ -27,6 +27,8 @@ Reported (one JSON line on rank 0):
                2048 x 2048 crop (mask disagreement, max |v - v_oracle|);
   multiband    the 4-band 2048x2048 scene: vector region term and edge term,
                500 iterations each, CUDA events of lse_evolve
+  sizes        per-iteration time of one lse_evolve call on square crops
+               (sides 256-4096), region and edge term, FP32
   batch        256 uneven images (sides 128-1024, caps 100-600, early stop)
                through lse_evolve_batch with and without a CUDA graph, and
                one lse_evolve call per image in sequence, on a context whose
@@ -81,6 +83,8 @@ def parse():
                     help="skip the 16-bit storage variants")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the storage types' error against the FP64 oracle")
+    ap.add_argument("--no-sizes", action="store_true",
+                    help="skip the per-iteration time of single calls by image side")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched uneven-image measurement")
     ap.add_argument("--batch-images", type=int, default=256)
@@ -548,6 +552,37 @@ def multiband_measurement(torch, lse, dev, iters: int, steps: int, peak: float):
     return out
 
 
+def sizes_measurement(torch, lse, dev, iters: int = 200):
+    """Per-iteration time of one lse_evolve on square crops of the benchmark
+    scene (sides 256-4096), region and edge term, FP32, `iters` iterations,
+    the library's CUDA events (best of 3): what one call costs when the image
+    is too small to fill the GPU."""
+    from paper_1409_7474_gb300 import scenes
+    out = {"workload": f"square crops of the benchmark scene, {iters} iterations, "
+                       "FP32, dt=15 sigma=1 TS=9; one lse_evolve call each",
+           "unit": "us per iteration", "sides": {}}
+    big = 4096
+    img = scenes.large_scene(big, big, n_roofs=500, n_roads=50)["image"]
+    with lse.Context(dev.index, max_pixels=big * big, max_bands=1) as c:
+        for side in (256, 512, 1024, 2048, 4096):
+            x = torch.from_numpy(np.ascontiguousarray(img[:, :side, :side])).to(dev)
+            pr = torch.from_numpy(scenes.circle_phi(side, side, radius=side / 4)).to(dev)
+            pe = torch.from_numpy(scenes.box_phi(side, side, [(4, 4, side - 4, side - 4)])).to(dev)
+            g = c.precompute_edge(x, 1.0, 9, 255.0)
+            row = {}
+            for term, phi in (("region", pr), ("edge", pe)):
+                kw = {"g": g} if term == "edge" else {}
+                src = x if term == "region" else None
+                c.evolve(src, phi, term, iterations=iters, **kw)         # warm-up
+                ms = min(c.evolve(src, phi, term, iterations=iters, **kw)[2]["elapsed_ms"]
+                         for _ in range(3))
+                row[term] = ms / iters * 1e3
+            row["region_mpx_it_s"] = side * side / row["region"]
+            out["sides"][str(side)] = row
+        torch.cuda.synchronize()
+    return out
+
+
 def kernel_profile(size: int, name: str, iterations: int):
     """DRAM traffic per launch of the region kernel `name` from a committed ncu
     summary (profiles/<name>_region_traffic.json), if it was taken on the
@@ -785,6 +820,9 @@ def main():
         multiband = multiband_measurement(torch, lse, dev, args.multiband_iters, args.steps,
                                           peak)
 
+    sizes = None
+    if not args.no_sizes and rank == 0 and world == 1:
+        sizes = sizes_measurement(torch, lse, dev)
     batch = None
     if not args.no_batch:
         batch = batch_measurement(torch, lse, dev, args.batch_images)
@@ -810,7 +848,8 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks.summary(), "gpu_launches": launches,
-                "storage_variants": variants, "multiband": multiband, "batch": batch,
+                "storage_variants": variants, "multiband": multiband, "sizes": sizes,
+                "batch": batch,
                 "serve": serve,
                 "impl": "gb300",
                 "stats": {"region": {k: st_r[k] for k in ("iterations_run", "status",
