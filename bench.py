@@ -712,11 +712,15 @@ def main():
     # e2e: the step's inputs (image, both initial LSFs) and results (v and
     # mask of both terms) are pinned host buffers passed to the C ABI, which
     # copies them in and out inside the timed region.  The edge indicator g
-    # is an intermediate between two calls and stays on the device.  The
-    # region evolution runs on one stream and the edge term on another: the
-    # edge precompute and its copies run beside the region evolution, the
-    # edge evolution after it, so each one's host copies overlap the other's
-    # kernels while the step kernels never share the SMs.
+    # is an intermediate between two calls and stays on the device.  Three
+    # streams, one context each: the region evolution, the edge precompute
+    # and the edge evolution.  The library runs its persistent evolutions
+    # one at a time, each after the previous one's output kernel, and issues
+    # a call's host copies before its kernels, so one term's copies overlap
+    # the other term's evolution.  The edge precompute runs one step ahead
+    # into a second g buffer (its kernels fill a gap between evolutions
+    # instead of holding back the edge evolution's copies); every timed step
+    # still runs one precompute.
     e2e = None
     if not args.no_e2e:
         hx = torch.from_numpy(img).pin_memory()
@@ -726,20 +730,36 @@ def main():
         hm_r = torch.empty((size, size), dtype=torch.uint8).pin_memory()
         ho_e = torch.empty_like(ho_r).pin_memory()
         hm_e = torch.empty_like(hm_r).pin_memory()
-        dg = torch.empty((size, size), dtype=torch.float32, device=dev)
+        dgs = [torch.empty((size, size), dtype=torch.float32, device=dev) for _ in range(2)]
+        ctx_g = lse.Context(local, max_pixels=npx, max_bands=1)
         s_r = torch.cuda.Stream(dev)
+        s_g = torch.cuda.Stream(dev)
         s_e = torch.cuda.Stream(dev)
+        g_ready = [None, None]      # precompute of each g buffer done
+        g_used = [None, None]       # the edge evolution that last read it
+        n_host = [0]
+
+        def precompute(k):
+            if g_used[k % 2] is not None:
+                s_g.wait_event(g_used[k % 2])
+            ctx_g.precompute_edge(hx, 1.0, 9, 255.0, out=dgs[k % 2], stream=s_g)
+            ev = torch.cuda.Event()
+            ev.record(s_g)
+            g_ready[k % 2] = ev
 
         def step_host():
-            # the library runs its persistent evolutions one at a time, in
-            # the order they were enqueued, whatever their streams: the edge
-            # evolution follows the region's, while each term's copies and
-            # small kernels overlap the other term's evolution
+            k = n_host[0]
+            n_host[0] += 1
             ctx_r.evolve(hx, hpr, "region", phi_out=ho_r, mask_out=hm_r, stream=s_r, **common)
-            ctx_e.precompute_edge(hx, 1.0, 9, 255.0, out=dg, stream=s_e)
-            ctx_e.evolve(None, hpe, "edge", g=dg, phi_out=ho_e, mask_out=hm_e, stream=s_e,
-                         **common)
+            precompute(k + 1)
+            s_e.wait_event(g_ready[k % 2])
+            ctx_e.evolve(None, hpe, "edge", g=dgs[k % 2], phi_out=ho_e, mask_out=hm_e,
+                         stream=s_e, **common)
+            done = torch.cuda.Event()
+            done.record(s_e)
+            g_used[k % 2] = done
 
+        precompute(0)
         step_host()
         torch.cuda.synchronize()
         if world > 1:
@@ -747,11 +767,11 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        s_r.wait_event(e0)
-        s_e.wait_event(e0)
+        for sx in (s_r, s_g, s_e):
+            sx.wait_event(e0)
         for _ in range(args.steps):
             step_host()
-        for sx in (s_r, s_e):
+        for sx in (s_r, s_g, s_e):
             ev = torch.cuda.Event()
             ev.record(sx)
             stream.wait_event(ev)
@@ -760,6 +780,7 @@ def main():
         ems = max_over_ranks(e0.elapsed_time(e1), world, dev)
         for c in (ctx_r, ctx_e):
             assert c.stats()["status"] == "LSE_OK", c.stats()["status"]
+        ctx_g.destroy()
         plane = npx * 4
         e2e = {"value": world * px_iters_per_step * args.steps / (ems / 1e3) / 1e6,
                "unit": UNIT,
@@ -767,10 +788,12 @@ def main():
                "h2d_bytes_per_step": 4 * plane,
                # v + mask (region), v + mask (edge)
                "d2h_bytes_per_step": 2 * plane + 2 * npx,
-               "streams": "region on one stream, edge on another (edge precompute and "
-                          "copies beside the region evolution, the library orders the two "
-                          "persistent evolutions); host buffers for inputs and results, "
-                          "g on the device"}
+               "streams": "region evolution, edge precompute and edge evolution on three "
+                          "streams (the library runs the persistent evolutions one at a "
+                          "time, each after the previous one's output kernel, and issues a "
+                          "call's host copies before its kernels); the edge precompute runs "
+                          "one step ahead into a second g buffer; host buffers for inputs "
+                          "and results"}
 
     # the same workload with 16-bit storage of the data term and the LSF
     # (FP32 arithmetic): 6 bytes per pixel-iteration of the region step

@@ -147,8 +147,20 @@ lse_status stage_image(lse_ctx *ctx, const void *image, PtrKind kind,
         *band_stride = (size_t)H * W;
         return LSE_OK;
     }
-    const void *src = image;
     lse_status r;
+    if (kind == PTR_HOST && dtype == LSE_F32 && (W % 4) == 0) {
+        // the layout the kernels read (pitch = W): one copy, no conversion
+        if ((r = ensure_t(ctx, &ctx->img, &ctx->img_cap, (size_t)B * H * W, s, "image")) != LSE_OK)
+            return r;
+        cudaError_t e = cudaMemcpyAsync(ctx->img, image, (size_t)B * H * W * 4,
+                                        cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy image to device");
+        *img_out = ctx->img;
+        *pitch_out = W;
+        *band_stride = (size_t)H * W;
+        return LSE_OK;
+    }
+    const void *src = image;
     if (kind == PTR_HOST) {
         size_t bytes = (size_t)B * H * W * dtype_size(dtype);
         if ((r = ensure(ctx, &ctx->raw_in, &ctx->raw_cap, bytes, s, "image staging")) != LSE_OK)
@@ -439,6 +451,18 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
     }
     cudaError_t e;
 
+    // host phi0 first: the call's copies go before its first kernel, so that
+    // they overlap whatever the GPU still runs (kernels of this call cannot
+    // start beside a persistent evolution that holds every SM)
+    const float *phi0_src = phi0;
+    if (kp == PTR_HOST) {
+        if ((r = ensure_t(ctx, &ctx->phi0_st, &ctx->phi0_cap, (size_t)H * W, s, "phi0 staging")) != LSE_OK)
+            return r;
+        e = cudaMemcpyAsync(ctx->phi0_st, phi0, (size_t)H * W * 4, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy phi0 to device");
+        phi0_src = ctx->phi0_st;
+    }
+
     // data term on the device: image bands (region) or g (edge)
     const float *data = nullptr;
     int pitch = 0;
@@ -491,14 +515,6 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
     }
     // LSF ping-pong buffers share the data term's pitch
     if ((r = ensure_phi(ctx, (size_t)H * pitch, s)) != LSE_OK) return r;
-    const float *phi0_src = phi0;
-    if (kp == PTR_HOST) {
-        if ((r = ensure_t(ctx, &ctx->phi0_st, &ctx->phi0_cap, (size_t)H * W, s, "phi0 staging")) != LSE_OK)
-            return r;
-        e = cudaMemcpyAsync(ctx->phi0_st, phi0, (size_t)H * W * 4, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy phi0 to device");
-        phi0_src = ctx->phi0_st;
-    }
     float *out_phi = phi_out;
     uint8_t *out_mask = mask_out;
     if (ko == PTR_HOST) {
@@ -628,6 +644,8 @@ lse_status lse_evolve(lse_ctx *ctx, const void *image, lse_dtype dtype, int H,
     e = launch_output(ctx->phi, pitch, H, W, sto, ctx->st, out_phi, out_mask, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "output");
     ++ctx->launches;
+    if (persisted && (e = coop_chain_mark(s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "order persistent evolutions");
     if (ko == PTR_HOST) {
         e = cudaMemcpyAsync(phi_out, out_phi, (size_t)H * W * 4, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "copy phi to host");

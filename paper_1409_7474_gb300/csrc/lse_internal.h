@@ -385,6 +385,13 @@ cudaError_t launch_step_once(StepPlan &plan, bool binarise_in, cudaStream_t s);
 // plan is of the tile form and LSE_PERSIST is not "0"; cudaErrorNotSupported
 // (nothing launched) otherwise, and the caller launches one step at a time.
 cudaError_t launch_evolve(StepPlan &plan, int sm_count, cudaStream_t s);
+// Moves the device's ordering point of persistent evolutions to the end of
+// the work enqueued on s so far (not under stream capture): lse_evolve calls
+// it after the output kernel of a persistent evolution, so that the next
+// persistent evolution, on whatever stream, starts after that kernel rather
+// than taking every SM while it waits (which would delay the output, and the
+// caller's copies behind it, by a whole evolution).
+cudaError_t coop_chain_mark(cudaStream_t s);
 // Vector images (2-4 bands, FP32, the listing's order, zero padding, TS
 // 3..15): the persistent evolution with the bands staged by the step
 // (32-row tiles), after launch_mb_candidates.  evolve_bands_applies says

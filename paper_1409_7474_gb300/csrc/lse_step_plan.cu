@@ -114,6 +114,19 @@ cudaError_t launch_evolve(StepPlan &plan, int sm_count, cudaStream_t s)
     return chain ? cudaEventRecord(g_coop_event[dev], s) : cudaSuccess;
 }
 
+cudaError_t coop_chain_mark(cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= kMaxDev) return cudaSuccess;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    err = cudaStreamIsCapturing(s, &cs);
+    if (err != cudaSuccess || cs != cudaStreamCaptureStatusNone) return err;
+    std::lock_guard<std::mutex> lock(g_coop_mutex);
+    return g_coop_event[dev] ? cudaEventRecord(g_coop_event[dev], s) : cudaSuccess;
+}
+
 bool evolve_bands_applies(int H, int W, int B, const lse_params &p)
 {
     return persist_enabled() && p.term == LSE_TERM_REGION && B >= 2 && B <= 4 &&

@@ -175,9 +175,12 @@ def test_input_dtypes(torch, ctx, kind):
 
 
 # ---------------------------------------------------------------- host buffers, determinism
-def test_host_buffers_match_device_buffers_bitwise(torch, ctx):
-    img, _, _ = scenes.rect_scene(190, 230, 70, 40)
-    phi0 = scenes.circle_phi(190, 230, radius=50)
+@pytest.mark.parametrize("W", [230, 232])
+def test_host_buffers_match_device_buffers_bitwise(torch, ctx, W):
+    # W = 232: a host FP32 image is copied straight into the kernels' layout
+    # (pitch W); W = 230 goes through the conversion kernel (pitch 256)
+    img, _, _ = scenes.rect_scene(190, W, 70, 40)
+    phi0 = scenes.circle_phi(190, W, radius=50)
     v_d, m_d, st_d = gpu_evolve(torch, ctx, img, phi0, iterations=7)
     v_h, m_h, st_h = ctx.evolve(img, phi0, iterations=7)   # numpy: host pointers
     assert isinstance(v_h, np.ndarray)
