@@ -29,6 +29,8 @@ Reported (one JSON line on rank 0):
                500 iterations each, CUDA events of lse_evolve
   sizes        per-iteration time of one lse_evolve call on square crops
                (sides 256-4096), region and edge term, FP32
+  strips       the row-strip driver with one rank (lse_strip_* per
+               iteration) against one lse_evolve call, 4096x4096 region term
   batch        256 uneven images (sides 128-1024, caps 100-600, early stop)
                through lse_evolve_batch with and without a CUDA graph, and
                one lse_evolve call per image in sequence, on a context whose
@@ -85,6 +87,8 @@ def parse():
                     help="skip the storage types' error against the FP64 oracle")
     ap.add_argument("--no-sizes", action="store_true",
                     help="skip the per-iteration time of single calls by image side")
+    ap.add_argument("--no-strips", action="store_true",
+                    help="skip the one-rank row-strip path against lse_evolve")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched uneven-image measurement")
     ap.add_argument("--batch-images", type=int, default=256)
@@ -583,6 +587,39 @@ def sizes_measurement(torch, lse, dev, iters: int = 200):
     return out
 
 
+def strips_measurement(torch, lse, dev, size: int = 4096, iters: int = 50):
+    """The row-strip path on one GPU: the strip driver with one rank
+    (`strips.LocalComm`, the library's lse_strip_* calls: exact partial sums,
+    one strip step and a host synchronisation per iteration) against one
+    lse_evolve call on the same image, region term, FP32.  What a rank of
+    a split evolution pays for stepping one launch at a time with
+    host-visible statistics; no collective runs (one GPU)."""
+    import time
+    from paper_1409_7474_gb300 import scenes, strips
+    img = scenes.large_scene(size, size, n_roofs=500, n_roads=50)["image"]
+    phi0 = scenes.circle_phi(size, size, radius=size / 4)
+    x = torch.from_numpy(img).to(dev)
+    p0 = torch.from_numpy(phi0).to(dev)
+    out = {"workload": f"{size}x{size} crop of the benchmark scene's generator, region "
+                       f"term, {iters} iterations, FP32; one rank",
+           "unit": "us per iteration"}
+    with lse.Context(dev.index, max_pixels=size * size, max_bands=1) as c:
+        part = strips.partition(size, size, 9, 0, 1)
+        comp = strips.LibraryCompute(c, part, x, term="region")
+        runs = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            strips.evolve(strips.LocalComm(), comp, part, p0, term="region",
+                          iterations=iters)
+            torch.cuda.synchronize()
+            runs.append((time.perf_counter() - t0) / iters * 1e6)
+        out["strip_driver"] = min(runs)
+        ms = min(c.evolve(x, p0, "region", iterations=iters)[2]["elapsed_ms"] for _ in range(3))
+        out["lse_evolve"] = ms / iters * 1e3
+    return out
+
+
 def kernel_profile(size: int, name: str, iterations: int):
     """DRAM traffic per launch of the region kernel `name` from a committed ncu
     summary (profiles/<name>_region_traffic.json), if it was taken on the
@@ -846,6 +883,9 @@ def main():
     sizes = None
     if not args.no_sizes and rank == 0 and world == 1:
         sizes = sizes_measurement(torch, lse, dev)
+    strip_leg = None
+    if not args.no_strips and rank == 0 and world == 1:
+        strip_leg = strips_measurement(torch, lse, dev)
     batch = None
     if not args.no_batch:
         batch = batch_measurement(torch, lse, dev, args.batch_images)
@@ -872,6 +912,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks.summary(), "gpu_launches": launches,
                 "storage_variants": variants, "multiband": multiband, "sizes": sizes,
+                "strips": strip_leg,
                 "batch": batch,
                 "serve": serve,
                 "impl": "gb300",

@@ -515,12 +515,17 @@ lse_status lse_strip_dmax(lse_ctx *ctx, const void *image, lse_dtype dtype, int 
  *   norm        B > 1 region term: the maximum over the ranks of
  *               lse_strip_dmax; ignored otherwise (one band takes max|D|
  *               in closed form from the totals' range).
- *   v_out       Hs x W float32: v of this iteration, host or device.  Rows
- *               within h of a cut edge of the strip (an edge that is not the
- *               image's) are not the whole image's: the neighbours' halo
- *               exchange replaces them.
- * Synchronises `stream`.  Returns LSE_ERR_NONFINITE or LSE_ERR_TIMEOUT for
- * the device-side conditions of lse_stats.status. */
+ *   v_out       Hs x W float32: v of this iteration, host or device (not
+ *               phi's buffer).  Rows within h of a cut edge of the strip (an
+ *               edge that is not the image's) are not the whole image's: the
+ *               neighbours' halo exchange replaces them.
+ * Device buffers with W a multiple of 4 and 16-byte alignment (phi, v_out
+ * and the image or g) are read and written in place; others are staged.
+ * With v_out in host memory the call synchronises `stream` and returns
+ * LSE_ERR_NONFINITE or LSE_ERR_TIMEOUT for the device-side conditions of
+ * lse_stats.status; with v_out on the device it returns without waiting,
+ * and the next lse_strip_partials on the context (which synchronises)
+ * returns those conditions instead of its own result. */
 lse_status lse_strip_step(lse_ctx *ctx, const void *image, lse_dtype dtype, const float *g,
                           int Hs, int W, int B, const float *phi, int binarise_in,
                           const lse_params *params, const lse_strip_sums *totals, double norm,

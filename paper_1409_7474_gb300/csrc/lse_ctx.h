@@ -72,6 +72,7 @@ struct lse_ctx {
     cudaStream_t cap_stream = nullptr;  // stream on which batches are captured
     void *strip_acc = nullptr;       // lse_strip_*: the pass's device accumulator
     size_t strip_acc_cap = 0;        // bytes
+    bool strip_unchecked = false;    // a strip step's status not yet read back
 };
 
 namespace lse_detail {

@@ -374,9 +374,23 @@ lse_status lse_strip_partials(lse_ctx *ctx, const void *image, lse_dtype dtype, 
         ++ctx->launches;
     }
     StripAcc h;
+    unsigned int step_bits = 0;
+    const bool check_step = ctx->strip_unchecked;
     cudaError_t e = cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && check_step)
+        e = cudaMemcpyAsync(&step_bits, &ctx->st->status_bits, sizeof(step_bits),
+                            cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "read strip partials");
+    ctx->strip_unchecked = false;
+    if (step_bits & LSE_SBIT_TIMEOUT) {
+        set_err(ctx, "a bounded device wait of the last strip step ran out");
+        return LSE_ERR_TIMEOUT;
+    }
+    if (step_bits & LSE_SBIT_NONFINITE) {
+        set_err(ctx, "the last strip step met NaN or Inf");
+        return LSE_ERR_NONFINITE;
+    }
     memset(out, 0, sizeof(*out));
     out->npix = (long long)(row1 - row0) * W;
     out->n_plus = (long long)h.v[0];
@@ -495,11 +509,22 @@ lse_status lse_strip_step(lse_ctx *ctx, const void *image, lse_dtype dtype, cons
         return LSE_ERR_INVALID_ARG;
     }
     cudaError_t e;
+    // device buffers already in the kernels' layout (W a multiple of 4,
+    // 16-byte aligned) are read and written in place: no staging copies
+    const bool in_place =
+        kp == PTR_DEVICE && ko == PTR_DEVICE && (W % 4) == 0 && aligned16(phi) &&
+        aligned16(v_out) && phi != v_out &&
+        (region ? ki == PTR_DEVICE && dtype == LSE_F32 && aligned16(image)
+                : kg == PTR_DEVICE && aligned16(g));
     // the data plane, pitched like the LSF buffers
     const float *data;
     int pitch;
     size_t band_stride;
-    if (region) {
+    if (in_place) {
+        data = region ? static_cast<const float *>(image) : g;
+        pitch = W;
+        band_stride = (size_t)Hs * W;
+    } else if (region) {
         if ((r = stage_image(ctx, image, ki, dtype, Hs, W, B, s, &data, &pitch,
                              &band_stride)) != LSE_OK)
             return r;
@@ -513,10 +538,15 @@ lse_status lse_strip_step(lse_ctx *ctx, const void *image, lse_dtype dtype, cons
         data = ctx->gbuf;
         band_stride = (size_t)Hs * pitch;
     }
-    if ((r = ensure_phi(ctx, (size_t)Hs * pitch, s)) != LSE_OK) return r;
-    e = cudaMemcpy2DAsync(ctx->phi[0], (size_t)pitch * 4, phi, (size_t)W * 4, (size_t)W * 4, Hs,
-                          cudaMemcpyDefault, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "stage phi");
+    float *bufs[2] = {const_cast<float *>(phi), v_out};
+    if (!in_place) {
+        if ((r = ensure_phi(ctx, (size_t)Hs * pitch, s)) != LSE_OK) return r;
+        e = cudaMemcpy2DAsync(ctx->phi[0], (size_t)pitch * 4, phi, (size_t)W * 4, (size_t)W * 4,
+                              Hs, cudaMemcpyDefault, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "stage phi");
+        bufs[0] = ctx->phi[0];
+        bufs[1] = ctx->phi[1];
+    }
     StripTotals t;
     memset(&t, 0, sizeof(t));
     if (region) {
@@ -530,7 +560,7 @@ lse_status lse_strip_step(lse_ctx *ctx, const void *image, lse_dtype dtype, cons
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "strip coefficients");
     ++ctx->launches;
     StepPlan plan;
-    if (!plan_step(Hs, W, region ? B : 1, p, pitch, band_stride, data, ctx->phi, ctx->st,
+    if (!plan_step(Hs, W, region ? B : 1, p, pitch, band_stride, data, bufs, ctx->st,
                    ctx->partials, ctx->sm_count, ctx->step_form,
                    tile_nw_for(ctx, Hs, W, region ? B : 1, p.term, LSE_F32, p.ts), nullptr,
                    &plan)) {
@@ -540,9 +570,18 @@ lse_status lse_strip_step(lse_ctx *ctx, const void *image, lse_dtype dtype, cons
     if ((e = launch_step_once(plan, binarise_in != 0, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "strip step");
     ++ctx->launches;
-    e = cudaMemcpy2DAsync(v_out, (size_t)W * 4, ctx->phi[1], (size_t)pitch * 4, (size_t)W * 4, Hs,
-                          cudaMemcpyDefault, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy v");
+    if (!in_place) {
+        e = cudaMemcpy2DAsync(v_out, (size_t)W * 4, ctx->phi[1], (size_t)pitch * 4,
+                              (size_t)W * 4, Hs, cudaMemcpyDefault, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy v");
+    }
+    if (ko != PTR_HOST) {
+        // no wait: the next lse_strip_partials on this context, which
+        // synchronises, reports what the device found
+        ctx->strip_unchecked = true;
+        return LSE_OK;
+    }
+    ctx->strip_unchecked = false;
     e = cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(LseDevState), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
