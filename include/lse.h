@@ -479,7 +479,15 @@ int lse_strip_scale(double amax, long long npix);
  *             count, or NULL (flips = 0).
  *   fix_k     the scale of the sums, from lse_strip_scale on the whole
  *             image's amax and pixel count (-120..120).
- * Synchronises `stream` and fills *out. */
+ *   out       host memory: the call synchronises `stream`, fills *out and
+ *             returns the device-side conditions of earlier strip calls
+ *             that did not wait (see lse_strip_status) or its own.  Device
+ *             memory (of the context's GPU): the sums are written there on
+ *             `stream` and the call returns at once -- the caller can then
+ *             add the ranks' records on the device (the first 19 64-bit
+ *             words, npix .. sum_a, are integers to sum) and pass the
+ *             result to lse_strip_step with no host round trip; a NaN or
+ *             Inf found is kept for lse_strip_status. */
 lse_status lse_strip_partials(lse_ctx *ctx, const void *image, lse_dtype dtype, int Hs, int W,
                               int B, int row0, int row1, const float *phi,
                               const float *phi_prev, int fix_k, lse_strip_sums *out,
@@ -511,7 +519,10 @@ lse_status lse_strip_dmax(lse_ctx *ctx, const void *image, lse_dtype dtype, int 
  *               (ignored here); storage F32, the listing's order and zero
  *               padding only.
  *   totals      region term: the ranks' summed lse_strip_sums of phi
- *               (npix = H * W); NULL for the edge term.
+ *               (npix = H * W), in host memory (checked here) or in device
+ *               memory of the context's GPU (read by the step's kernels in
+ *               stream order, unchecked: the caller puts the whole image's
+ *               imin, imax, fix_k and bands there); NULL for the edge term.
  *   norm        B > 1 region term: the maximum over the ranks of
  *               lse_strip_dmax; ignored otherwise (one band takes max|D|
  *               in closed form from the totals' range).
@@ -524,12 +535,19 @@ lse_status lse_strip_dmax(lse_ctx *ctx, const void *image, lse_dtype dtype, int 
  * With v_out in host memory the call synchronises `stream` and returns
  * LSE_ERR_NONFINITE or LSE_ERR_TIMEOUT for the device-side conditions of
  * lse_stats.status; with v_out on the device it returns without waiting,
- * and the next lse_strip_partials on the context (which synchronises)
- * returns those conditions instead of its own result. */
+ * and the next call on the context that synchronises (lse_strip_partials
+ * into host memory, lse_strip_status) returns those conditions. */
 lse_status lse_strip_step(lse_ctx *ctx, const void *image, lse_dtype dtype, const float *g,
                           int Hs, int W, int B, const float *phi, int binarise_in,
                           const lse_params *params, const lse_strip_sums *totals, double norm,
                           float *v_out, void *stream);
+
+/* Synchronises `stream` and returns the device-side conditions that strip
+ * calls on ctx found since the last call that reported them:
+ * LSE_ERR_TIMEOUT (a step's bounded device wait ran out), LSE_ERR_NONFINITE
+ * (NaN or Inf in a strip's image or LSF), else LSE_OK.  The record is then
+ * cleared. */
+lse_status lse_strip_status(lse_ctx *ctx, void *stream);
 
 #ifdef __cplusplus
 }

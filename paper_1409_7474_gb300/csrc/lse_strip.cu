@@ -11,6 +11,7 @@
 // (lse_fix), so the totals, and every result after them, do not depend on
 // how the image is split.
 #include <math.h>
+#include <stddef.h>
 #include <string.h>
 
 #include "lse_ctx.h"
@@ -31,7 +32,10 @@ struct StripAcc {
     unsigned int amax;          // ordered bits of max |I_b|
     unsigned int nonfinite;
     unsigned int dmax, dmin;    // ordered bits of max D and of -min D (lse_strip_dmax)
-    unsigned int pad[2];
+    unsigned int pad;
+    // status bits of strip calls that returned without waiting, kept until
+    // a call that synchronises reads them (not cleared with the sums)
+    unsigned int sticky;
 };
 
 // The whole image's totals as the coefficient kernel takes them.
@@ -83,71 +87,151 @@ __device__ __forceinline__ void cta_max_to(float (&v)[N], unsigned int *const (&
     }
 }
 
+// One pixel's contribution to the sums (NB bands at most, B of them used).
+template <int NB>
+__device__ __forceinline__ void strip_pixel(float p, float q, bool has_phi, bool has_prev,
+                                            const float (&e)[NB], int B, bool has_img,
+                                            int fix_k, long long (&v)[2 + 2 * NB],
+                                            float (&mx)[3], unsigned int &bad)
+{
+    bool plus = true;
+    if (has_phi) {
+        bad |= !isfinite(p);
+        plus = p >= 0.0f;
+        v[0] += plus ? 1 : 0;
+        if (has_prev) v[1] += (q >= 0.0f) != plus;
+    }
+    if (has_img) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            if (b < B) {
+                bad |= !isfinite(e[b]);
+                if (b == 0) {
+                    mx[0] = fmaxf(mx[0], e[b]);
+                    mx[1] = fmaxf(mx[1], -e[b]);
+                }
+                mx[2] = fmaxf(mx[2], fabsf(e[b]));
+                if (has_phi) {
+                    const long long qv = lse_fix(e[b], fix_k);
+                    v[2 + b] += plus ? qv : -qv;
+                    v[2 + NB + b] += qv;
+                }
+            }
+        }
+    }
+}
+
 // Sums over rows [row0, row1): sign counts and flips of phi, and the
 // fixed-point band sums with and without the sign (see lse_strip_sums).
-// Grid-stride over the owned pixels.
+// CTAs over rows, threads over columns; VEC: four columns a thread with
+// 16-byte loads (every row and plane 16-byte aligned, W a multiple of 4),
+// so that each thread has four pixels' loads in flight.  NB: the band
+// count rounded up (B of them used).
+template <int NB, bool VEC>
 __global__ void __launch_bounds__(kThreads)
 strip_partials_kernel(const float *__restrict__ img, int pitch, size_t band_stride,
                       const float *__restrict__ phi, int phi_pitch,
                       const float *__restrict__ prev, int prev_pitch, int W, int B,
                       int row0, int row1, int fix_k, StripAcc *acc)
 {
-    long long v[kNv];
+    constexpr int NV = 2 + 2 * NB;
+    long long v[NV];
 #pragma unroll
-    for (int i = 0; i < kNv; ++i) v[i] = 0;
+    for (int i = 0; i < NV; ++i) v[i] = 0;
     float mx[3] = {-INFINITY, -INFINITY, 0.0f};      // max I_0, max -I_0, max |I_b|
     unsigned int bad = 0;
-    const long long n = (long long)(row1 - row0) * W;
-    for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n;
-         i += (long long)gridDim.x * kThreads) {
-        const int y = row0 + (int)(i / W), x = (int)(i % W);
-        bool plus = true;
-        if (phi) {
-            const float p = __ldg(phi + (size_t)y * phi_pitch + x);
-            bad |= !isfinite(p);
-            plus = p >= 0.0f;
-            v[0] += plus ? 1 : 0;
-            if (prev) v[1] += (__ldg(prev + (size_t)y * prev_pitch + x) >= 0.0f) != plus;
-        }
-        if (img) {
+    const bool hp = phi != nullptr, hq = prev != nullptr, hi = img != nullptr;
+    for (int y = row0 + blockIdx.x; y < row1; y += gridDim.x) {
+        if (VEC) {
+            for (int x = 4 * threadIdx.x; x < W; x += 4 * kThreads) {
+                const float4 p4 = hp ? __ldg(reinterpret_cast<const float4 *>(
+                                           phi + (size_t)y * phi_pitch + x))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 q4 = hq ? __ldg(reinterpret_cast<const float4 *>(
+                                           prev + (size_t)y * prev_pitch + x))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 e4[NB];
 #pragma unroll
-            for (int b = 0; b < LSE_MAXB; ++b) {
-                if (b < B) {
-                    const float e = __ldg(img + b * band_stride + (size_t)y * pitch + x);
-                    bad |= !isfinite(e);
-                    if (b == 0) {
-                        mx[0] = fmaxf(mx[0], e);
-                        mx[1] = fmaxf(mx[1], -e);
-                    }
-                    mx[2] = fmaxf(mx[2], fabsf(e));
-                    if (phi) {
-                        const long long q = lse_fix(e, fix_k);
-                        v[2 + b] += plus ? q : -q;
-                        v[2 + LSE_MAXB + b] += q;
-                    }
+                for (int b = 0; b < NB; ++b)
+                    e4[b] = (hi && b < B) ? __ldg(reinterpret_cast<const float4 *>(
+                                                img + b * band_stride + (size_t)y * pitch + x))
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float pp[4] = {p4.x, p4.y, p4.z, p4.w};
+                const float qq[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float e[NB];
+#pragma unroll
+                    for (int b = 0; b < NB; ++b)
+                        e[b] = j == 0 ? e4[b].x : j == 1 ? e4[b].y : j == 2 ? e4[b].z : e4[b].w;
+                    strip_pixel<NB>(pp[j], qq[j], hp, hq, e, B, hi, fix_k, v, mx, bad);
                 }
+            }
+        } else {
+            for (int x = threadIdx.x; x < W; x += kThreads) {
+                const float p = hp ? __ldg(phi + (size_t)y * phi_pitch + x) : 0.0f;
+                const float q = hq ? __ldg(prev + (size_t)y * prev_pitch + x) : 0.0f;
+                float e[NB];
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+                    e[b] = (hi && b < B) ? __ldg(img + b * band_stride + (size_t)y * pitch + x)
+                                         : 0.0f;
+                strip_pixel<NB>(p, q, hp, hq, e, B, hi, fix_k, v, mx, bad);
             }
         }
     }
-    lse_cta_sum_i64<kNv, kWarps>(v);
+    lse_cta_sum_i64<NV, kWarps>(v);
     if (threadIdx.x == 0) {
         unsigned long long *dst = acc->v;
+        if (v[0]) atomicAdd(dst + 0, (unsigned long long)v[0]);
+        if (v[1]) atomicAdd(dst + 1, (unsigned long long)v[1]);
 #pragma unroll
-        for (int i = 0; i < kNv; ++i)
-            if (v[i]) atomicAdd(dst + i, (unsigned long long)v[i]);
+        for (int b = 0; b < NB; ++b) {
+            if (v[2 + b]) atomicAdd(dst + 2 + b, (unsigned long long)v[2 + b]);
+            if (v[2 + NB + b]) atomicAdd(dst + 2 + LSE_MAXB + b, (unsigned long long)v[2 + NB + b]);
+        }
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&acc->nonfinite, 1u);
     unsigned int *const dst[3] = {&acc->max0, &acc->neg_min, &acc->amax};
     cta_max_to<3>(mx, dst);
 }
 
+template <int NB>
+cudaError_t launch_partials_nb(bool vec, int grid, cudaStream_t s, const float *img, int pitch,
+                               size_t band_stride, const float *phi, const float *prev, int W,
+                               int B, int row0, int row1, int fix_k, StripAcc *acc)
+{
+    if (vec)
+        strip_partials_kernel<NB, true><<<grid, kThreads, 0, s>>>(
+            img, pitch, band_stride, phi, W, prev, W, W, B, row0, row1, fix_k, acc);
+    else
+        strip_partials_kernel<NB, false><<<grid, kThreads, 0, s>>>(
+            img, pitch, band_stride, phi, W, prev, W, W, B, row0, row1, fix_k, acc);
+    return cudaGetLastError();
+}
+
 // One thread: the state record for one step of a strip (or for the D pass
 // of lse_strip_dmax) from the whole image's totals -- c+/c-, alpha, mid and,
 // for one band, M and the step coefficient (Eqs. 15 and 17, the arithmetic
 // of the whole-image path); for several bands M = norm when use_norm.
-__global__ void strip_coeffs_kernel(LseDevState *st, StripTotals t, int B, int region,
-                                    float dt, double norm, int use_norm)
+__global__ void strip_coeffs_kernel(LseDevState *st, StripTotals t, const lse_strip_sums *dev,
+                                    int B, int region, float dt, double norm, int use_norm,
+                                    unsigned int *sticky, int fold)
 {
+    if (fold && (st->status_bits & LSE_SBIT_ABORT))
+        atomicOr(sticky, st->status_bits & LSE_SBIT_ABORT);
+    if (dev) {
+        // the ranks' totals in device memory (summed there by the caller)
+        t.npix = dev->npix;
+        t.n_plus = dev->n_plus;
+        for (int b = 0; b < LSE_MAXB; ++b) {
+            t.sum_w[b] = b < B ? dev->sum_w[b] : 0;
+            t.sum_a[b] = b < B ? dev->sum_a[b] : 0;
+        }
+        t.imin = dev->imin;
+        t.imax = dev->imax;
+        t.fix_k = dev->fix_k;
+    }
     st->npix = t.npix;
     st->imin = t.imin;
     st->imax = t.imax;
@@ -190,6 +274,25 @@ __global__ void strip_coeffs_kernel(LseDevState *st, StripTotals t, int B, int r
     }
 }
 
+// One thread: the pass's sums as an lse_strip_sums in device memory.
+__global__ void strip_export_kernel(StripAcc *acc, lse_strip_sums *out, long long npix,
+                                    int fix_k, int B, int any)
+{
+    out->npix = npix;
+    out->n_plus = (long long)acc->v[0];
+    out->flips = (long long)acc->v[1];
+    for (int b = 0; b < 8; ++b) {
+        out->sum_w[b] = b < B ? (long long)acc->v[2 + b] : 0;
+        out->sum_a[b] = b < B ? (long long)acc->v[2 + LSE_MAXB + b] : 0;
+    }
+    out->imin = any ? -(double)ord_value(acc->neg_min) : INFINITY;
+    out->imax = any ? (double)ord_value(acc->max0) : -INFINITY;
+    out->amax = any ? (double)ord_value(acc->amax) : 0.0;
+    out->fix_k = fix_k;
+    out->bands = B;
+    if (acc->nonfinite) atomicOr(&acc->sticky, LSE_SBIT_NONFINITE);
+}
+
 // Largest and smallest D = sum_b alpha_b (I_b - mid_b) over rows [row0, row1),
 // in FP32 with the normaliser pass's arithmetic (nothing when the totals
 // made the force zero).
@@ -205,10 +308,8 @@ strip_dmax_kernel(const float *__restrict__ img, int pitch, size_t band_stride, 
         m[b] = st->m[b];
     }
     float mx[2] = {-INFINITY, -INFINITY};              // max D, max -D
-    const long long n = (long long)(row1 - row0) * W;
-    for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n;
-         i += (long long)gridDim.x * kThreads) {
-        const int y = row0 + (int)(i / W), x = (int)(i % W);
+    for (int y = row0 + blockIdx.x; y < row1; y += gridDim.x)
+    for (int x = threadIdx.x; x < W; x += kThreads) {
         const float *src = img + (size_t)y * pitch + x;
         float d = 0.0f;
 #pragma unroll
@@ -293,8 +394,10 @@ lse_status device_plane(lse_ctx *ctx, const float *src, PtrKind kind, int Hs, in
     return LSE_OK;
 }
 
-lse_status ensure_acc(lse_ctx *ctx, cudaStream_t s)
+// The accumulator, allocated (and cleared, sticky word included) on first use.
+lse_status acc_alloc(lse_ctx *ctx, cudaStream_t s)
 {
+    if (ctx->strip_acc) return LSE_OK;
     lse_status r = ensure(ctx, &ctx->strip_acc, &ctx->strip_acc_cap, sizeof(StripAcc), s,
                           "strip sums");
     if (r != LSE_OK) return r;
@@ -302,11 +405,52 @@ lse_status ensure_acc(lse_ctx *ctx, cudaStream_t s)
     return e == cudaSuccess ? LSE_OK : cuda_fail(ctx, e, "clear strip sums");
 }
 
+// The accumulator with its sums cleared for a pass (the sticky word kept).
+lse_status ensure_acc(lse_ctx *ctx, cudaStream_t s)
+{
+    lse_status r = acc_alloc(ctx, s);
+    if (r != LSE_OK) return r;
+    cudaError_t e = cudaMemsetAsync(ctx->strip_acc, 0, offsetof(StripAcc, sticky), s);
+    return e == cudaSuccess ? LSE_OK : cuda_fail(ctx, e, "clear strip sums");
+}
+
+// Enqueues the reads of the device-side status of strip calls that did not
+// wait (the sticky word, and the last step's bits if nothing read them
+// yet) into *bits and clears the sticky word; the caller synchronises.
+cudaError_t read_strip_status(lse_ctx *ctx, unsigned int *bits, unsigned int *step_bits,
+                              cudaStream_t s)
+{
+    *bits = 0;
+    *step_bits = 0;
+    if (!ctx->strip_acc) return cudaSuccess;
+    StripAcc *acc = static_cast<StripAcc *>(ctx->strip_acc);
+    cudaError_t e = cudaMemcpyAsync(bits, &acc->sticky, sizeof(*bits), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&acc->sticky, 0, sizeof(acc->sticky), s);
+    if (e == cudaSuccess && ctx->strip_unchecked)
+        e = cudaMemcpyAsync(step_bits, &ctx->st->status_bits, sizeof(*step_bits),
+                            cudaMemcpyDeviceToHost, s);
+    return e;
+}
+
+lse_status strip_status_of(lse_ctx *ctx, unsigned int bits)
+{
+    if (bits & LSE_SBIT_TIMEOUT) {
+        set_err(ctx, "a bounded device wait of a strip step ran out");
+        return LSE_ERR_TIMEOUT;
+    }
+    if (bits & LSE_SBIT_NONFINITE) {
+        set_err(ctx, "a strip call met NaN or Inf");
+        return LSE_ERR_NONFINITE;
+    }
+    return LSE_OK;
+}
+
+// CTAs of a pass over `rows` rows: one per row, at most 8 per SM.
 int pass_blocks(const lse_ctx *ctx, int rows, int W)
 {
-    const long long want = ((long long)rows * W + kThreads - 1) / kThreads;
-    const long long cap = (long long)ctx->sm_count * 8;
-    return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+    (void)W;
+    const int cap = ctx->sm_count * 8;
+    return rows < 1 ? 1 : (rows < cap ? rows : cap);
 }
 
 }  // namespace
@@ -344,8 +488,8 @@ lse_status lse_strip_partials(lse_ctx *ctx, const void *image, lse_dtype dtype, 
     if (!guard.ok) return cuda_fail(ctx, cudaErrorInvalidDevice, "set device");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const PtrKind ki = classify(image, ctx->device), kp = classify(phi, ctx->device),
-                  kq = classify(phi_prev, ctx->device);
-    if (ki == PTR_BAD || kp == PTR_BAD || kq == PTR_BAD) {
+                  kq = classify(phi_prev, ctx->device), ko = classify(out, ctx->device);
+    if (ki == PTR_BAD || kp == PTR_BAD || kq == PTR_BAD || ko == PTR_BAD) {
         set_err(ctx, "a device pointer belongs to another GPU than the context's");
         return LSE_ERR_INVALID_ARG;
     }
@@ -367,30 +511,45 @@ lse_status lse_strip_partials(lse_ctx *ctx, const void *image, lse_dtype dtype, 
     if ((r = ensure_acc(ctx, s)) != LSE_OK) return r;
     StripAcc *acc = static_cast<StripAcc *>(ctx->strip_acc);
     if (row1 > row0 && (img || dphi)) {
-        strip_partials_kernel<<<pass_blocks(ctx, row1 - row0, W), kThreads, 0, s>>>(
-            img, pitch, band_stride, dphi, W, dprev, W, W, img ? B : 0, row0, row1, fix_k, acc);
-        cudaError_t e = cudaGetLastError();
+        const int nb = img ? B : 0;
+        const bool vec = (W % 4) == 0 && (pitch % 4) == 0 && (band_stride % 4) == 0 &&
+                         (!img || aligned16(img)) && (!dphi || aligned16(dphi)) &&
+                         (!dprev || aligned16(dprev));
+        const int grid = pass_blocks(ctx, row1 - row0, W);
+        cudaError_t e;
+        if (nb <= 1)
+            e = launch_partials_nb<1>(vec, grid, s, img, pitch, band_stride, dphi, dprev, W, nb,
+                                      row0, row1, fix_k, acc);
+        else if (nb <= 2)
+            e = launch_partials_nb<2>(vec, grid, s, img, pitch, band_stride, dphi, dprev, W, nb,
+                                      row0, row1, fix_k, acc);
+        else if (nb <= 4)
+            e = launch_partials_nb<4>(vec, grid, s, img, pitch, band_stride, dphi, dprev, W, nb,
+                                      row0, row1, fix_k, acc);
+        else
+            e = launch_partials_nb<8>(vec, grid, s, img, pitch, band_stride, dphi, dprev, W, nb,
+                                      row0, row1, fix_k, acc);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "strip partials");
         ++ctx->launches;
     }
+    const bool any = img && row1 > row0;
+    if (ko == PTR_DEVICE) {
+        // the sums into the caller's device record; no wait
+        strip_export_kernel<<<1, 1, 0, s>>>(acc, out, (long long)(row1 - row0) * W, fix_k, B,
+                                            any ? 1 : 0);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "strip sums export");
+        ++ctx->launches;
+        return LSE_OK;
+    }
     StripAcc h;
-    unsigned int step_bits = 0;
-    const bool check_step = ctx->strip_unchecked;
+    unsigned int bits = 0, step_bits = 0;
     cudaError_t e = cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && check_step)
-        e = cudaMemcpyAsync(&step_bits, &ctx->st->status_bits, sizeof(step_bits),
-                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = read_strip_status(ctx, &bits, &step_bits, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "read strip partials");
     ctx->strip_unchecked = false;
-    if (step_bits & LSE_SBIT_TIMEOUT) {
-        set_err(ctx, "a bounded device wait of the last strip step ran out");
-        return LSE_ERR_TIMEOUT;
-    }
-    if (step_bits & LSE_SBIT_NONFINITE) {
-        set_err(ctx, "the last strip step met NaN or Inf");
-        return LSE_ERR_NONFINITE;
-    }
+    if ((r = strip_status_of(ctx, bits | step_bits)) != LSE_OK) return r;
     memset(out, 0, sizeof(*out));
     out->npix = (long long)(row1 - row0) * W;
     out->n_plus = (long long)h.v[0];
@@ -399,7 +558,6 @@ lse_status lse_strip_partials(lse_ctx *ctx, const void *image, lse_dtype dtype, 
         out->sum_w[b] = (long long)h.v[2 + b];
         out->sum_a[b] = (long long)h.v[2 + LSE_MAXB + b];
     }
-    const bool any = img && row1 > row0;
     out->imin = any ? -(double)ord_value(h.neg_min) : INFINITY;
     out->imax = any ? (double)ord_value(h.max0) : -INFINITY;
     out->amax = any ? (double)ord_value(h.amax) : 0.0;
@@ -445,7 +603,9 @@ lse_status lse_strip_dmax(lse_ctx *ctx, const void *image, lse_dtype dtype, int 
         return r;
     if ((r = ensure_acc(ctx, s)) != LSE_OK) return r;
     StripAcc *acc = static_cast<StripAcc *>(ctx->strip_acc);
-    strip_coeffs_kernel<<<1, 1, 0, s>>>(ctx->st, to_totals(*totals, B), B, 1, dt, 0.0, 0);
+    strip_coeffs_kernel<<<1, 1, 0, s>>>(ctx->st, to_totals(*totals, B), nullptr, B, 1, dt, 0.0,
+                                        0, &acc->sticky, ctx->strip_unchecked ? 1 : 0);
+    ctx->strip_unchecked = false;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "strip coefficients");
     ++ctx->launches;
@@ -494,7 +654,18 @@ lse_status lse_strip_step(lse_ctx *ctx, const void *image, lse_dtype dtype, cons
         set_err(ctx, "need image (region term, g NULL) or g (edge term)");
         return LSE_ERR_INVALID_ARG;
     }
-    if (region && (r = check_totals(ctx, totals, B)) != LSE_OK) return r;
+    // totals in device memory are the caller's (summed there); host ones
+    // are checked here
+    const PtrKind kt = region ? classify(totals, ctx->device) : PTR_NULL;
+    if (kt == PTR_BAD) {
+        set_err(ctx, "the totals belong to another GPU than the context's");
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (region && kt != PTR_DEVICE && (r = check_totals(ctx, totals, B)) != LSE_OK) return r;
+    if (region && !totals) {
+        set_err(ctx, "the region term needs the ranks' totals");
+        return LSE_ERR_INVALID_ARG;
+    }
     if (region && B > 1 && !(norm >= 0.0 && isfinite(norm))) {
         set_err(ctx, "norm must be finite and >= 0 (got %g)", norm);
         return LSE_ERR_INVALID_ARG;
@@ -549,15 +720,18 @@ lse_status lse_strip_step(lse_ctx *ctx, const void *image, lse_dtype dtype, cons
     }
     StripTotals t;
     memset(&t, 0, sizeof(t));
-    if (region) {
+    if (region && kt != PTR_DEVICE) {
         t = to_totals(*totals, B);
-    } else {
+    } else if (!region) {
         t.npix = (long long)Hs * W;
         t.fix_k = 30;
     }
-    strip_coeffs_kernel<<<1, 1, 0, s>>>(ctx->st, t, region ? B : 1, region ? 1 : 0, p.dt, norm,
-                                        1);
+    if ((r = acc_alloc(ctx, s)) != LSE_OK) return r;
+    strip_coeffs_kernel<<<1, 1, 0, s>>>(
+        ctx->st, t, kt == PTR_DEVICE ? totals : nullptr, region ? B : 1, region ? 1 : 0, p.dt,
+        norm, 1, &static_cast<StripAcc *>(ctx->strip_acc)->sticky, ctx->strip_unchecked ? 1 : 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "strip coefficients");
+    ctx->strip_unchecked = false;
     ++ctx->launches;
     StepPlan plan;
     if (!plan_step(Hs, W, region ? B : 1, p, pitch, band_stride, data, bufs, ctx->st,
@@ -576,25 +750,34 @@ lse_status lse_strip_step(lse_ctx *ctx, const void *image, lse_dtype dtype, cons
         if (e != cudaSuccess) return cuda_fail(ctx, e, "copy v");
     }
     if (ko != PTR_HOST) {
-        // no wait: the next lse_strip_partials on this context, which
-        // synchronises, reports what the device found
+        // no wait: the next call on this context that synchronises
+        // (lse_strip_partials into host memory, lse_strip_status) reports
+        // what the device found
         ctx->strip_unchecked = true;
         return LSE_OK;
     }
-    ctx->strip_unchecked = false;
-    e = cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(LseDevState), cudaMemcpyDeviceToHost, s);
+    ctx->strip_unchecked = true;
+    unsigned int bits = 0, step_bits = 0;
+    e = read_strip_status(ctx, &bits, &step_bits, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
-    const unsigned int bits = ctx->st_host->status_bits;
-    if (bits & LSE_SBIT_TIMEOUT) {
-        set_err(ctx, "a bounded device wait of the step ran out");
-        return LSE_ERR_TIMEOUT;
-    }
-    if (bits & LSE_SBIT_NONFINITE) {
-        set_err(ctx, "the step met NaN or Inf");
-        return LSE_ERR_NONFINITE;
-    }
-    return LSE_OK;
+    ctx->strip_unchecked = false;
+    return strip_status_of(ctx, bits | step_bits);
+}
+
+lse_status lse_strip_status(lse_ctx *ctx, void *stream)
+{
+    if (!ctx) return LSE_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return cuda_fail(ctx, cudaErrorInvalidDevice, "set device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned int bits = 0, step_bits = 0;
+    cudaError_t e = read_strip_status(ctx, &bits, &step_bits, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
+    ctx->strip_unchecked = false;
+    return strip_status_of(ctx, bits | step_bits);
 }
 
 }  // extern "C"

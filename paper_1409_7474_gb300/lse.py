@@ -83,6 +83,10 @@ class Problem(ctypes.Structure):
                 ("phi_out", ctypes.c_void_p), ("mask_out", ctypes.c_void_p)]
 
 
+STRIP_SUMS_WORDS = 23                # an lse_strip_sums record in 64-bit words
+STRIP_SUM_INT_WORDS = 19             # npix .. sum_a: integers the ranks add
+
+
 class StripSums(ctypes.Structure):
     """lse_strip_sums: partial statistics of a strip's owned rows, or their
     totals over the ranks."""
@@ -139,7 +143,7 @@ _lib.lse_strip_scale.argtypes = [ctypes.c_double, ctypes.c_longlong]
 _lib.lse_strip_scale.restype = ctypes.c_int
 _lib.lse_strip_partials.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
-                                    ctypes.c_int, ctypes.POINTER(StripSums), _vp]
+                                    ctypes.c_int, _vp, _vp]
 _lib.lse_strip_partials.restype = ctypes.c_int
 _lib.lse_strip_dmax.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -148,15 +152,18 @@ _lib.lse_strip_dmax.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_i
 _lib.lse_strip_dmax.restype = ctypes.c_int
 _lib.lse_strip_step.argtypes = [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(Params),
-                                ctypes.POINTER(StripSums), ctypes.c_double, _vp, _vp]
+                                _vp, ctypes.c_double, _vp, _vp]
 _lib.lse_strip_step.restype = ctypes.c_int
+_lib.lse_strip_status.argtypes = [_vp, _vp]
+_lib.lse_strip_status.restype = ctypes.c_int
 
 SYMBOLS = ("lse_create", "lse_destroy", "lse_last_error", "lse_precompute_edge",
            "lse_evolve", "lse_get_stats", "lse_version", "lse_kernel_launches",
            "lse_evolve_static",
            "lse_evolve_batch", "lse_autotune", "lse_server_create", "lse_server_destroy",
            "lse_server_submit", "lse_server_advance", "lse_server_poll",
-           "lse_strip_scale", "lse_strip_partials", "lse_strip_dmax", "lse_strip_step")
+           "lse_strip_scale", "lse_strip_partials", "lse_strip_dmax", "lse_strip_step",
+           "lse_strip_status")
 STATIC_MAX_PIXELS = 262144
 
 
@@ -349,11 +356,12 @@ class Context:
 
     # -- row strips (lse_strip_*)
     def strip_partials(self, image, phi, row0: int, row1: int, fix_k: int = 0,
-                       phi_prev=None, bands: int = None, width: int = None,
-                       stream=None) -> StripSums:
+                       phi_prev=None, bands: int = None, out=None, stream=None):
         """lse_strip_partials over rows [row0, row1) of a strip: image
         (B x Hs x W, or None for the edge term), phi / phi_prev (Hs x W
-        float32, or None).  Returns the StripSums."""
+        float32, or None).  Returns a StripSums (synchronous), or, with
+        ``out`` a CUDA int64 tensor of STRIP_SUMS_WORDS words, writes the
+        record there without waiting and returns ``out``."""
         if image is not None:
             B, Hs, W = _shape3(image)
             dcode = _dtype_code(image)
@@ -361,11 +369,23 @@ class Context:
             B = bands or 1
             Hs, W = tuple(phi.shape)
             dcode = F32
-        out = StripSums()
+        dev_out = out is not None
+        if dev_out:
+            if out.numel() * out.element_size() < ctypes.sizeof(StripSums):
+                raise ValueError("out is smaller than an lse_strip_sums record")
+            ptr = _ptr(out)
+        else:
+            out = StripSums()
+            ptr = ctypes.byref(out)
         self._check(_lib.lse_strip_partials(
             self._h, _ptr(image), dcode, Hs, W, B, int(row0), int(row1), _ptr(phi),
-            _ptr(phi_prev), int(fix_k), ctypes.byref(out), _stream_ptr(stream, self.device)))
+            _ptr(phi_prev), int(fix_k), ptr, _stream_ptr(stream, self.device)))
         return out
+
+    def strip_status(self, stream=None) -> None:
+        """lse_strip_status: raises LseError for a device-side condition that
+        strip calls found since the last report."""
+        self._check(_lib.lse_strip_status(self._h, _stream_ptr(stream, self.device)))
 
     def strip_dmax(self, image, row0: int, row1: int, totals: StripSums, dt: float = 15.0,
                    stream=None) -> float:
@@ -396,11 +416,16 @@ class Context:
             v_out = _empty_like_place(phi, (Hs, W), np.float32,
                                       torch.float32 if torch is not None else None)
         p = Params(term_code, float(dt), float(sigma), int(ts), 1, 0, 0.0, F32, 0, 0)
+        if totals is None:
+            tptr = None
+        elif isinstance(totals, StripSums):
+            tptr = ctypes.byref(totals)
+        else:
+            tptr = _ptr(totals)            # a device record (CUDA tensor)
         self._check(_lib.lse_strip_step(
             self._h, _ptr(image) if term_code == TERM_REGION else None, dcode,
             _ptr(g) if term_code == TERM_EDGE else None, Hs, W, B, _ptr(phi),
-            int(bool(binarise_in)), ctypes.byref(p),
-            ctypes.byref(totals) if totals is not None else None, float(norm), _ptr(v_out),
+            int(bool(binarise_in)), ctypes.byref(p), tptr, float(norm), _ptr(v_out),
             _stream_ptr(stream, self.device)))
         return v_out
 

@@ -27,6 +27,14 @@ entries; any object with the same methods (``range``, ``scale``,
 ``partials``, ``dmax``, ``step``) can stand in for it.  The communicator
 wraps ``torch.distributed`` (NCCL for CUDA buffers, gloo on CPU); halos go
 by point-to-point send and receive into each GPU's own memory.
+
+With one band or the edge term, ``LibraryCompute`` keeps the statistics in
+device memory (``device_sums``): the partial sums are written into a device
+record, the ranks add its integer words on the device, and the next step
+reads it in stream order, so an iteration enqueues its work without waiting
+on the host (the early stop, when on, reads the sign-change count each
+iteration).  Vector images take the host path: each step's max |D| is a
+second reduction over the ranks.
 """
 from __future__ import annotations
 
@@ -97,6 +105,9 @@ class LocalComm:
     def all_reduce(self, values: np.ndarray, op: str) -> np.ndarray:
         return np.array(values, copy=True)
 
+    def all_reduce_tensor(self, t, op: str):
+        return t
+
     def exchange(self, to_prev, to_next, like_prev, like_next):
         return None, None
 
@@ -127,6 +138,18 @@ class TorchComm:
         rop = {"sum": self._dist.ReduceOp.SUM, "max": self._dist.ReduceOp.MAX}[op]
         self._dist.all_reduce(t, op=rop, group=self.group)
         return t.cpu().numpy()
+
+    def all_reduce_tensor(self, t, op: str):
+        """In place on a tensor: on its device with NCCL, through the host
+        otherwise."""
+        rop = {"sum": self._dist.ReduceOp.SUM, "max": self._dist.ReduceOp.MAX}[op]
+        if self._nccl or t.device.type == "cpu":
+            self._dist.all_reduce(t, op=rop, group=self.group)
+        else:
+            h = t.cpu()
+            self._dist.all_reduce(h, op=rop, group=self.group)
+            t.copy_(h)
+        return t
 
     def exchange(self, to_prev, to_next, like_prev, like_next):
         """Sends ``to_prev`` to rank - 1 and ``to_next`` to rank + 1 (None
@@ -261,6 +284,9 @@ def evolve(comm, compute, part: Partition, phi0, *, term: str = "region", bands:
         got = comm.all_reduce(np.array([-lo, hi, am], dtype=np.float64), "max")
         tot.imin, tot.imax, tot.amax = -float(got[0]), float(got[1]), float(got[2])
         tot.fix_k = int(compute.scale(tot.amax, npix))
+    if getattr(compute, "device_sums", False):
+        return _evolve_device(comm, compute, part, phi0, tot, region, B, iterations,
+                              reinit_period, early_stop_frac)
     phi = phi0
     tot = _reduce_partials(comm, compute.partials(phi, None, tot.fix_k), True, tot)
     first_n_plus = tot.n_plus
@@ -287,6 +313,58 @@ def evolve(comm, compute, part: Partition, phi0, *, term: str = "region", bands:
     if region:
         cp, cm = means(tot)
         stats.update(c_plus=list(cp), c_minus=list(cm), norm=norm)
+    return v, stats
+
+
+# words of a device lse_strip_sums record: npix, n_plus, flips, sum_w[8],
+# sum_a[8] (integers the ranks add), then imin, imax, amax and fix_k | bands
+_INT_WORDS = 19
+_W_NPLUS, _W_FLIPS, _W_SW, _W_SA = 1, 2, 3, 11
+
+
+def _evolve_device(comm, compute, part, phi0, tot, region, B, iterations, reinit_period,
+                   early_stop_frac):
+    """``evolve`` with the statistics kept in device memory: each iteration's
+    partial sums go into a device record, the ranks add its integer words
+    on the device (one all-reduce), the whole image's constants are written
+    over the rest, and the next step reads the record in stream order -- no
+    host round trip per iteration (but one to read the sign changes when
+    the early stop is on)."""
+    npix = tot.npix
+    const = compute.constants(tot)
+
+    def reduce(rec):
+        comm.all_reduce_tensor(rec[:_INT_WORDS], "sum")
+        rec[_INT_WORDS:] = const
+        return rec
+
+    phi = phi0
+    rec = reduce(compute.partials_device(phi, None, tot.fix_k))
+    first = rec
+    binarise_in = False
+    v = phi
+    n_run = 0
+    for n in range(int(iterations)):
+        v = compute.step(phi, binarise_in, rec, 0.0)
+        reinit = reinit_after(n, reinit_period)
+        v = exchange_halo(comm, part, v, binary=reinit)
+        rec = reduce(compute.partials_device(v, phi, tot.fix_k))
+        n_run = n + 1
+        phi = v
+        binarise_in = reinit
+        if early_stop_frac > 0.0 and int(rec[_W_FLIPS].item()) < early_stop_frac * npix:
+            break
+    words = rec.cpu().numpy()
+    n_plus0 = int(first[_W_NPLUS].item())
+    compute.finish()
+    fin = Totals(npix=npix, n_plus=int(words[_W_NPLUS]), flips=int(words[_W_FLIPS]),
+                 sum_w=words[_W_SW:_W_SW + B].copy(), sum_a=words[_W_SA:_W_SA + B].copy(),
+                 imin=tot.imin, imax=tot.imax, amax=tot.amax, fix_k=tot.fix_k, bands=B)
+    stats = {"iterations_run": n_run, "last_flips": fin.flips, "area_plus": fin.n_plus,
+             "initial_area_plus": n_plus0, "totals": fin}
+    if region:
+        cp, cm = means(fin)
+        stats.update(c_plus=list(cp), c_minus=list(cm), norm=0.0)
     return v, stats
 
 
@@ -338,7 +416,7 @@ class LibraryCompute:
     The LSF strips are CUDA float32 tensors."""
 
     def __init__(self, ctx, part: Partition, image=None, g=None, *, term: str = "region",
-                 dt: float = 15.0, sigma: float = 1.0, ts: int = 9):
+                 dt: float = 15.0, sigma: float = 1.0, ts: int = 9, device_sums=None):
         from . import lse
         self._lse = lse
         self.ctx = ctx
@@ -348,6 +426,11 @@ class LibraryCompute:
         self.term = term
         self.dt, self.sigma, self.ts = float(dt), float(sigma), int(ts)
         self.bands = 1 if image is None or image.dim() == 2 else int(image.shape[0])
+        # statistics in device memory (one band or the edge term: vector
+        # images need each step's max |D| on the host)
+        if device_sums is None:
+            device_sums = term == "edge" or self.bands == 1
+        self.device_sums = bool(device_sums) and (term == "edge" or self.bands == 1)
 
     def _sums(self, tot: Totals):
         s = self._lse.StripSums()
@@ -375,13 +458,32 @@ class LibraryCompute:
         return Partials(s.n_plus, s.flips, np.array(s.sum_w[:B], dtype=np.int64),
                         np.array(s.sum_a[:B], dtype=np.int64))
 
+    def constants(self, tot: Totals):
+        """The record's last four words for the whole image (imin, imax,
+        amax, fix_k | bands << 32), on the LSF's device."""
+        words = np.concatenate([
+            np.array([tot.imin, tot.imax, tot.amax], dtype=np.float64).view(np.int64),
+            np.array([tot.fix_k, tot.bands], dtype=np.int32).view(np.int64)])
+        dev = self.image.device if self.image is not None else self.g.device
+        return torch.from_numpy(words).to(dev)
+
+    def partials_device(self, phi, phi_prev, fix_k: int):
+        a, b = self.part.own
+        rec = torch.empty(self._lse.STRIP_SUMS_WORDS, dtype=torch.int64, device=phi.device)
+        return self.ctx.strip_partials(self.image, phi, a, b, fix_k, phi_prev,
+                                       bands=self.bands, out=rec)
+
+    def finish(self):
+        self.ctx.strip_status()
+
     def dmax(self, tot: Totals) -> float:
         a, b = self.part.own
         return self.ctx.strip_dmax(self.image, a, b, self._sums(tot), self.dt)
 
-    def step(self, phi, binarise_in: bool, tot: Totals, norm: float):
+    def step(self, phi, binarise_in: bool, tot, norm: float):
         if self.term == "region":
-            return self.ctx.strip_step(self.image, phi, self._sums(tot), norm, "region",
+            rec = tot if torch is not None and isinstance(tot, torch.Tensor) else self._sums(tot)
+            return self.ctx.strip_step(self.image, phi, rec, norm, "region",
                                        binarise_in=binarise_in, dt=self.dt,
                                        sigma=self.sigma, ts=self.ts)
         return self.ctx.strip_step(None, phi, None, 0.0, "edge", g=self.g,

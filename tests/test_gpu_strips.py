@@ -40,6 +40,11 @@ def lse():
     return m
 
 
+def torch_max(a, b):
+    import torch
+    return torch.maximum(a, b)
+
+
 class ThreadComm:
     """Ranks as threads of one process: all-reduce and neighbour exchange
     through shared slots and a barrier (timed, so a failing rank fails the
@@ -66,6 +71,17 @@ class ThreadComm:
             out = out + v if op == "sum" else np.maximum(out, v)
         return out
 
+    def all_reduce_tensor(self, t, op):
+        self.w.slots[("t", self.rank)] = t.clone()
+        self.w.barrier.wait()
+        vals = [self.w.slots[("t", r)] for r in range(self.world)]
+        self.w.barrier.wait()
+        acc = vals[0].clone()
+        for v in vals[1:]:
+            acc = acc + v if op == "sum" else torch_max(acc, v)
+        t.copy_(acc)
+        return t
+
     def exchange(self, to_prev, to_next, like_prev, like_next):
         if to_prev is not None:
             self.w.slots[("x", self.rank, self.rank - 1)] = to_prev.clone()
@@ -80,7 +96,8 @@ class ThreadComm:
         return got_prev, got_next
 
 
-def run_split(torch, lse, world, img, phi0, g, term, ts, iterations, period, frac):
+def run_split(torch, lse, world, img, phi0, g, term, ts, iterations, period, frac,
+              device_sums=None):
     """The strip driver over `world` thread ranks; returns the whole v
     (owned rows stacked) and rank 0's statistics."""
     B = img.shape[0] if img is not None else 1
@@ -98,7 +115,8 @@ def run_split(torch, lse, world, img, phi0, g, term, ts, iterations, period, fra
             dimg = torch.from_numpy(np.ascontiguousarray(img[:, sl])).cuda() \
                 if term == "region" else None
             dg = torch.from_numpy(np.ascontiguousarray(g[sl])).cuda() if g is not None else None
-            comp = strips.LibraryCompute(ctxs[r], part, dimg, dg, term=term, ts=ts)
+            comp = strips.LibraryCompute(ctxs[r], part, dimg, dg, term=term, ts=ts,
+                                         device_sums=device_sums)
             p0 = torch.from_numpy(np.ascontiguousarray(phi0[sl])).cuda()
             v, st = strips.evolve(ThreadComm(w, r), comp, part, p0, term=term, bands=B,
                                   iterations=iterations, reinit_period=period,
@@ -128,6 +146,7 @@ CASES = [
     (257, 200, 3, "region", 9, 30, 1, 0.0),
     (270, 190, 1, "edge", 9, 40, 1, 0.0),
     (301, 244, 1, "region", 7, 30, 3, 0.0),
+    (280, 256, 1, "region", 9, 200, 1, 4e-3),
 ]
 
 
@@ -152,6 +171,11 @@ def test_split_runs_agree(torch, lse, case):
     runs = {n: run_split(torch, lse, n, img, phi0, g, term, ts, iters, period, frac)
             for n in (1, 2, 3)}
     v1, st1, _ = runs[1]
+    # the statistics kept on the host (one round trip per iteration) give
+    # the same bits as the device-resident record
+    runs["host"] = run_split(torch, lse, 2, img, phi0, g, term, ts, iters, period, frac,
+                             device_sums=False)
+    assert np.array_equal(runs["host"][0].view(np.uint32), v1.view(np.uint32))
     for n in (2, 3):
         vn, stn, all_st = runs[n]
         # the bits of the unsplit run, and the same statistics on every rank
@@ -176,8 +200,10 @@ def test_split_runs_agree(torch, lse, case):
     assert st1["iterations_run"] == s_ref["iterations_run"]
 
 
-def test_partials_are_exact_fixed_point_sums(torch, lse):
-    H, W, B = 97, 61, 3
+@pytest.mark.parametrize("W,B", [(61, 3), (64, 3), (64, 1), (68, 5)])
+def test_partials_are_exact_fixed_point_sums(torch, lse, W, B):
+    # W a multiple of 4: the pass reads four columns a thread (16-byte loads)
+    H = 97
     rng = np.random.default_rng(5)
     img = rng.uniform(-2.0, 3.0, (B, H, W)).astype(np.float32)
     phi = rng.normal(size=(H, W)).astype(np.float32)
@@ -211,7 +237,7 @@ def test_partials_are_exact_fixed_point_sums(torch, lse):
         assert s.n_plus == 0 and s.sum_a[0] == 0 and s.imax == float(img[0].max())
         # a NaN in the owned rows is reported
         bad = img.copy()
-        bad[1, 50, 7] = np.nan
+        bad[B - 1, 50, 7] = np.nan
         with pytest.raises(lse.LseError) as e:
             c.strip_partials(torch.from_numpy(bad).cuda(), torch.from_numpy(phi).cuda(), 40, 60,
                              k)
