@@ -499,8 +499,8 @@ lse_status lse_strip_partials(lse_ctx *ctx, const void *image, lse_dtype dtype, 
  * totals (Eq. 15).  *dmax receives that maximum over rows [row0, row1) of
  * the strip (D evaluated in FP32 as the step does); the caller takes the
  * maximum over the ranks and passes it to lse_strip_step.  0 when the
- * totals make the force zero (see lse_params' degenerate rule).
- * Synchronises `stream`. */
+ * totals make the force zero (see lse_params' degenerate rule).  totals in
+ * host memory only.  Synchronises `stream`. */
 lse_status lse_strip_dmax(lse_ctx *ctx, const void *image, lse_dtype dtype, int Hs, int W,
                           int B, int row0, int row1, const lse_strip_sums *totals, float dt,
                           double *dmax, void *stream);

@@ -582,8 +582,15 @@ lse_status lse_strip_dmax(lse_ctx *ctx, const void *image, lse_dtype dtype, int 
     }
     lse_status r = check_rows(ctx, Hs, W, B, row0, row1);
     if (r == LSE_OK) r = check_image_args(ctx, dtype, Hs, W, B);
-    if (r == LSE_OK) r = check_totals(ctx, totals, B);
     if (r != LSE_OK) return r;
+    {
+        DeviceGuard g0(ctx->device);
+        if (classify(totals, ctx->device) != PTR_HOST) {
+            set_err(ctx, "lse_strip_dmax takes the totals in host memory");
+            return LSE_ERR_INVALID_ARG;
+        }
+    }
+    if ((r = check_totals(ctx, totals, B)) != LSE_OK) return r;
     if (!(dt > 0.0f) || !isfinite(dt)) {
         set_err(ctx, "need a finite dt > 0 (got %g)", dt);
         return LSE_ERR_INVALID_ARG;
@@ -652,6 +659,10 @@ lse_status lse_strip_step(lse_ctx *ctx, const void *image, lse_dtype dtype, cons
     }
     if ((region && (!image || g)) || (!region && !g)) {
         set_err(ctx, "need image (region term, g NULL) or g (edge term)");
+        return LSE_ERR_INVALID_ARG;
+    }
+    if (v_out == phi || (const void *)v_out == image || v_out == g) {
+        set_err(ctx, "v_out must not share memory with phi, the image or g");
         return LSE_ERR_INVALID_ARG;
     }
     // totals in device memory are the caller's (summed there); host ones

@@ -309,3 +309,28 @@ def test_strip_step_rejects_bad_arguments(torch, lse):
             c.strip_step(x, p, bad, 0.0, "region")
         with pytest.raises(lse.LseError):           # dt must be positive
             c.strip_dmax(x, 0, 32, tot, dt=-1.0)
+
+
+def test_device_records_defer_their_conditions_to_strip_status(torch, lse):
+    # partial sums written into device memory return at once; a NaN they met
+    # is reported by lse_strip_status (once), as is nothing for clean data
+    H, W = 64, 64
+    rng = np.random.default_rng(3)
+    img = rng.uniform(0.0, 1.0, (1, H, W)).astype(np.float32)
+    phi = rng.normal(size=(H, W)).astype(np.float32)
+    with lse.Context(0, max_pixels=H * W, max_bands=1) as c:
+        rec = torch.empty(lse.STRIP_SUMS_WORDS, dtype=torch.int64, device="cuda")
+        x = torch.from_numpy(img).cuda()
+        p = torch.from_numpy(phi).cuda()
+        c.strip_partials(x, p, 0, H, 40, out=rec)
+        c.strip_status()
+        host = c.strip_partials(x, p, 0, H, 40)
+        words = rec.cpu().numpy()
+        assert words[0] == H * W and words[1] == host.n_plus and words[3] == host.sum_w[0]
+        bad = img.copy()
+        bad[0, 10, 10] = np.inf
+        c.strip_partials(torch.from_numpy(bad).cuda(), p, 0, H, 40, out=rec)
+        with pytest.raises(lse.LseError) as e:
+            c.strip_status()
+        assert e.value.status == lse.LSE_ERR_NONFINITE
+        c.strip_status()                   # reported once
