@@ -327,7 +327,12 @@ typedef struct {
  * Images that need the same step kernel (term, band count, template size)
  * share one launch per iteration, so small images fill the GPU together;
  * use_graph != 0 captures the whole iteration loop in a CUDA graph and
- * launches it once.  stats (host, n entries, may be NULL) receives each
+ * launches it once.  Vector images of the region term (2-4 bands, FP32
+ * storage, ts 3..15) run instead as groups of persistent evolutions: one
+ * cooperative launch per band count and radius (or several, when more
+ * images than the device holds CTAs), each image on its own share of the
+ * CTAs with its own grid barrier, all its iterations, before the other
+ * images' loop.  stats (host, n entries, may be NULL) receives each
  * image's statistics; elapsed_ms is the time of the whole iteration loop.
  * The call synchronises `stream` before it returns.  Context scratch grows
  * to hold every image's planes (about (B + 2) * 4 * H * round_up(W, 32)

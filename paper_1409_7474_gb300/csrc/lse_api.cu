@@ -270,7 +270,7 @@ void lse_destroy(lse_ctx *ctx)
     void *bufs[] = {ctx->phi[0], ctx->phi[1], ctx->img, ctx->gbuf, ctx->raw_in,
                     ctx->phi0_st, ctx->g_st, ctx->out_phi, ctx->out_mask, ctx->q16,
                     ctx->partials, ctx->st, ctx->arena, ctx->tables, ctx->tune_out,
-                    ctx->dplane, ctx->cand, ctx->strip_acc};
+                    ctx->dplane, ctx->cand, ctx->strip_acc, ctx->mbgroup};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (ctx->st_host) cudaFreeHost(ctx->st_host);

@@ -50,6 +50,54 @@ lse_status ensure_host(lse_ctx *ctx, size_t bytes, cudaStream_t s)
     return LSE_OK;
 }
 
+// A group launch of vector images: one band count and radius, images
+// [first, first + count) of the group list, with their CTA shares.
+struct MbChunk {
+    int B, rad;
+    std::vector<int> images;         // batch indices
+    std::vector<int> ncta;
+    int total = 0;
+};
+
+// Splits the vector images of one band count and radius into launches the
+// device holds at once (`cap` CTAs each, at least one a image) and shares
+// each launch's CTAs by the images' work (tiles x iteration cap), at most
+// one CTA per tile.  The shares change no result: an image's sums are exact
+// integers, the same however many CTAs add them.
+void share_ctas(const std::vector<int> &imgs, const std::vector<long long> &tiles,
+                const std::vector<long long> &work, int cap, int B, int rad,
+                std::vector<MbChunk> *out)
+{
+    for (size_t i0 = 0; i0 < imgs.size(); i0 += (size_t)cap) {
+        MbChunk c;
+        c.B = B;
+        c.rad = rad;
+        const size_t i1 = std::min(imgs.size(), i0 + (size_t)cap);
+        c.images.assign(imgs.begin() + i0, imgs.begin() + i1);
+        c.ncta.assign(c.images.size(), 1);
+        int used = (int)c.images.size();
+        // greedily to the image with the most work per CTA
+        while (used < cap) {
+            int best = -1;
+            double best_w = 0.0;
+            for (size_t k = 0; k < c.images.size(); ++k) {
+                const int i = c.images[k];
+                if (c.ncta[k] >= tiles[i]) continue;
+                const double w = (double)work[i] / c.ncta[k];
+                if (w > best_w) {
+                    best_w = w;
+                    best = (int)k;
+                }
+            }
+            if (best < 0) break;
+            ++c.ncta[best];
+            ++used;
+        }
+        c.total = used;
+        out->push_back(c);
+    }
+}
+
 }  // namespace
 
 namespace lse_detail {
@@ -269,11 +317,24 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
     off = align_up(off + sizeof(LsePartial) * (size_t)nparts * n);
     const size_t item_off = off;
     off = align_up(off + sizeof(BatchItem) * n);
+    // vector images (2-4 bands, FP32) run as groups of persistent
+    // evolutions, each with the normaliser's candidates
+    std::vector<char> mb(n, 0);
+    int n_mb = 0;
+    for (int i = 0; i < n; ++i) {
+        const lse_problem &q = problems[i];
+        mb[i] = q.params.term == LSE_TERM_REGION && q.params.storage == LSE_F32 &&
+                ctx->step_form == LSE_FORM_AUTO && evolve_bands_applies(q.H, q.W, q.B, q.params);
+        n_mb += mb[i];
+    }
+    const size_t cand_off = off;
+    off = align_up(off + sizeof(LseCandidates) * (size_t)n_mb);
     if ((r = ensure(ctx, &ctx->arena, &ctx->arena_cap, off, s, "batch arena")) != LSE_OK) return r;
     unsigned char *A = static_cast<unsigned char *>(ctx->arena);
     LseDevState *states = reinterpret_cast<LseDevState *>(A + st_off);
     LsePartial *partials = reinterpret_cast<LsePartial *>(A + part_off);
     BatchItem *d_items = reinterpret_cast<BatchItem *>(A + item_off);
+    LseCandidates *cands = reinterpret_cast<LseCandidates *>(A + cand_off);
     cudaError_t e = cudaMemsetAsync(states, 0, sizeof(LseDevState) * n, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_evolve_batch: clear states");
 
@@ -281,6 +342,10 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
     std::vector<BatchItem> items(n);
     ClassMap classes;
     const int nred = ctx->sm_count * 4;
+    std::vector<MbGroupItem> mb_items;
+    std::vector<int> mb_index(n, -1);
+    std::vector<long long> mb_tiles(n, 0), mb_work(n, 0);
+    std::map<std::pair<int, int>, std::vector<int>> mb_groups;
     for (int i = 0; i < n; ++i) {
         const lse_problem &q = problems[i];
         const lse_params &p = q.params;
@@ -313,8 +378,87 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
         it.early_stop = p.early_stop_frac > 0.0f;
         it.iter0 = 0;
         if (region && q.B > 1) it.nnblocks = normaliser_blocks(q.H, ctx->sm_count);
+        if (mb[i]) {
+            // the normaliser's candidates, then the persistent evolution's plan
+            LseCandidates *cand = cands + mb_items.size();
+            const float *bands = reinterpret_cast<const float *>(A + base[i] + lay[i].data);
+            const int pitch = lay[i].pitch;
+            const size_t bstride = (size_t)q.H * pitch;
+            e = launch_mb_candidates(bands, pitch, bstride, q.H, q.W, q.B, cand, states + i,
+                                     ctx->sm_count, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_evolve_batch: candidates");
+            MbGroupItem g;
+            memset(&g, 0, sizeof(g));
+            int tiles = 0;
+            float *phis[2] = {reinterpret_cast<float *>(A + base[i] + lay[i].phi0),
+                              reinterpret_cast<float *>(A + base[i] + lay[i].phi1)};
+            if (!plan_evolve_bands(q.H, q.W, q.B, p, pitch, bstride, bands, phis, states + i,
+                                   cand, ctx->sm_count, &g.e, g.maps, &tiles)) {
+                set_err(ctx, "lse_evolve_batch: image %d: no tensor maps for its bands", i);
+                return LSE_ERR_INVALID_ARG;
+            }
+            mb_index[i] = (int)mb_items.size();
+            mb_items.push_back(g);
+            mb_tiles[i] = g.e.a.n_items;
+            mb_work[i] = (long long)g.e.a.n_items * p.iterations;
+            mb_groups[{q.B, g.e.a.rad}].push_back(i);
+            continue;
+        }
         classes[class_of(plan, p.term, region ? q.B : 1)].items.push_back(i);
     }
+    // the vector images' group launches: CTA shares and tables, uploaded once
+    std::vector<MbChunk> chunks;
+    for (auto &kg : mb_groups) {
+        const int cap = evolve_mb_group_capacity(kg.first.first, kg.first.second, ctx->sm_count);
+        if (cap < 1) {
+            set_err(ctx, "lse_evolve_batch: the vector-image evolution cannot be resident");
+            return LSE_ERR_CUDA;
+        }
+        share_ctas(kg.second, mb_tiles, mb_work, cap, kg.first.first, kg.first.second, &chunks);
+    }
+    std::vector<size_t> chunk_items_off, chunk_table_off;
+    size_t mb_bytes = 0;
+    for (auto &c : chunks) {
+        chunk_items_off.push_back(mb_bytes);
+        mb_bytes = align_up(mb_bytes + sizeof(MbGroupItem) * c.images.size());
+        chunk_table_off.push_back(mb_bytes);
+        mb_bytes = align_up(mb_bytes + sizeof(int) * (size_t)c.total);
+    }
+    std::vector<unsigned char> mb_host(mb_bytes);
+    for (size_t ci = 0; ci < chunks.size(); ++ci) {
+        MbChunk &c = chunks[ci];
+        MbGroupItem *gi = reinterpret_cast<MbGroupItem *>(mb_host.data() + chunk_items_off[ci]);
+        int *tab = reinterpret_cast<int *>(mb_host.data() + chunk_table_off[ci]);
+        int cta = 0;
+        for (size_t k = 0; k < c.images.size(); ++k) {
+            MbGroupItem g = mb_items[mb_index[c.images[k]]];
+            g.cta0 = cta;
+            g.ncta = c.ncta[k];
+            memcpy(gi + k, &g, sizeof(g));
+            for (int j = 0; j < c.ncta[k]; ++j) tab[cta++] = (int)k;
+        }
+    }
+    if (mb_bytes) {
+        void *mp = ctx->mbgroup;
+        if ((r = ensure(ctx, &mp, &ctx->mbgroup_cap, mb_bytes, s, "vector-image groups")) != LSE_OK)
+            return r;
+        ctx->mbgroup = mp;
+        e = cudaMemcpyAsync(ctx->mbgroup, mb_host.data(), mb_bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_evolve_batch: upload groups");
+        e = cudaStreamSynchronize(s);       // the pageable source goes out of scope
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "lse_evolve_batch: upload groups");
+    }
+    auto launch_groups = [&]() -> cudaError_t {
+        const unsigned char *base_d = static_cast<const unsigned char *>(ctx->mbgroup);
+        for (size_t ci = 0; ci < chunks.size(); ++ci) {
+            cudaError_t ge = launch_evolve_bands_group(
+                chunks[ci].B, chunks[ci].rad,
+                reinterpret_cast<const MbGroupItem *>(base_d + chunk_items_off[ci]),
+                reinterpret_cast<const int *>(base_d + chunk_table_off[ci]), chunks[ci].total, s);
+            if (ge != cudaSuccess) return ge;
+        }
+        return cudaSuccess;
+    };
 
     // ---- CTA tables and the work list, uploaded once
     const size_t toff = layout_classes(classes, items.data());
@@ -346,7 +490,7 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
     };
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    if (use_graph) {
+    if (use_graph && !classes.empty()) {
         // kernel attributes are set by one launch per class in which every
         // image is past its cap (its CTAs return at once), outside the capture
         for (auto &kc : classes) {
@@ -373,7 +517,9 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
         }
     }
     e = cudaEventRecord(ctx->ev0, s);
-    if (e == cudaSuccess) e = use_graph ? cudaGraphLaunch(exec, s) : enqueue_loop(s);
+    if (e == cudaSuccess) e = launch_groups();
+    if (e == cudaSuccess && !classes.empty())
+        e = use_graph ? cudaGraphLaunch(exec, s) : enqueue_loop(s);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev1, s);
     if (e != cudaSuccess) {
         if (exec) cudaGraphExecDestroy(exec);
@@ -386,7 +532,7 @@ lse_status lse_evolve_batch(lse_ctx *ctx, int n, const lse_problem *problems, in
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         const lse_problem &q = problems[i];
         const StepArgs &a = items[i].args;
-        if (a.mb_split) {
+        if (a.mb_split && !mb[i]) {
             e = launch_band_stats(a.bands, a.pitch, a.band_stride, items[i].phi, q.H, q.W, q.B,
                                   a.dt, states + i, a.partials, nred, s);
             if (e != cudaSuccess) break;

@@ -70,6 +70,8 @@ struct lse_ctx {
     void *bhost = nullptr;
     size_t bhost_cap = 0;            // bytes (pinned)
     cudaStream_t cap_stream = nullptr;  // stream on which batches are captured
+    void *mbgroup = nullptr;         // lse_evolve_batch: vector images' group items
+    size_t mbgroup_cap = 0;          // and CTA tables (bytes)
     void *strip_acc = nullptr;       // lse_strip_*: the pass's device accumulator
     size_t strip_acc_cap = 0;        // bytes
     bool strip_unchecked = false;    // a strip step's status not yet read back

@@ -12,4 +12,15 @@ cudaError_t launch_evolve_mb3(const EvolveArgs &e, const CUtensorMap &pm0,
     return lse_tile::launch_evolve_mb_bands<3>(e, pm0, pm1, dm, nblocks, sm_count, s);
 }
 
+cudaError_t launch_evolve_mb_group3(int rad, const MbGroupItem *items, const int *cta_item,
+                                    int nblocks, cudaStream_t s)
+{
+    return lse_tile::launch_evolve_mb_group<3>(rad, items, cta_item, nblocks, s);
+}
+
+int evolve_mb_group_capacity3(int rad, int sm_count)
+{
+    return lse_tile::evolve_mb_group_capacity<3>(rad, sm_count);
+}
+
 }  // namespace lse_detail

@@ -12,4 +12,15 @@ cudaError_t launch_evolve_mb4(const EvolveArgs &e, const CUtensorMap &pm0,
     return lse_tile::launch_evolve_mb_bands<4>(e, pm0, pm1, dm, nblocks, sm_count, s);
 }
 
+cudaError_t launch_evolve_mb_group4(int rad, const MbGroupItem *items, const int *cta_item,
+                                    int nblocks, cudaStream_t s)
+{
+    return lse_tile::launch_evolve_mb_group<4>(rad, items, cta_item, nblocks, s);
+}
+
+int evolve_mb_group_capacity4(int rad, int sm_count)
+{
+    return lse_tile::evolve_mb_group_capacity<4>(rad, sm_count);
+}
+
 }  // namespace lse_detail

@@ -154,6 +154,15 @@ struct EvolveArgs {
     LseCandidates *cand;        // vector images: the normaliser's candidates
 };
 
+// One vector image of a group launch of the persistent vector-image
+// evolution (lse_evolve_batch), in device memory: its tensor maps (phi[0],
+// phi[1], the bands), its evolution, and its CTAs [cta0, cta0 + ncta).
+struct alignas(128) MbGroupItem {  // CUtensorMap needs 128-byte alignment
+    CUtensorMap maps[3];
+    EvolveArgs e;
+    int cta0, ncta;
+};
+
 // One image of a batched evolution (lse_evolve_batch, lse_server), in device
 // memory.  The CTAs [start, start + nblocks) of its class's step launch work
 // on it; vector images also own the normaliser CTAs [nstart, nstart +
@@ -327,6 +336,12 @@ cudaError_t launch_mb_candidates(const float *bands, int pitch, size_t band_stri
 cudaError_t launch_evolve_mb(const EvolveArgs &e, const CUtensorMap &pm0,
                              const CUtensorMap &pm1, const CUtensorMap &dm, int nblocks,
                              int sm_count, cudaStream_t s);
+// Vector images of B bands and radius rad as one cooperative group launch
+// (MbGroupItem, CTA table cta_item of nblocks entries), and the number of
+// its CTAs the device holds at once (0: none).
+cudaError_t launch_evolve_mb_group(int B, int rad, const MbGroupItem *items,
+                                   const int *cta_item, int nblocks, cudaStream_t s);
+int evolve_mb_group_capacity(int B, int rad, int sm_count);
 
 // Batched launches (lse_evolve_batch): iteration n over every image of one
 // class; CTA blockIdx.x works on image blk_item[blockIdx.x].  Step kernels
@@ -403,6 +418,16 @@ cudaError_t launch_evolve_bands(int H, int W, int B, const lse_params &p, int pi
                                 size_t band_stride, const float *bands, float *const phi[2],
                                 LseDevState *st, LseCandidates *cand, int sm_count,
                                 cudaStream_t s);
+// The arguments, tensor maps (phi[0], phi[1], the bands) and tile count of
+// that evolution, without launching it; false when it does not apply.
+bool plan_evolve_bands(int H, int W, int B, const lse_params &p, int pitch,
+                       size_t band_stride, const float *bands, float *const phi[2],
+                       LseDevState *st, LseCandidates *cand, int sm_count, EvolveArgs *e,
+                       CUtensorMap maps[3], int *nblocks);
+// A group of such evolutions (one band count and radius) as one cooperative
+// launch, ordered like the one-image launches.
+cudaError_t launch_evolve_bands_group(int B, int rad, const MbGroupItem *items,
+                                      const int *cta_item, int nblocks, cudaStream_t s);
 // Sets the message lse_last_error(NULL) returns (calls without a context).
 void set_contextless_error(const char *msg);
 

@@ -74,21 +74,12 @@ bool persist_enabled()
     return !(v && strcmp(v, "0") == 0);
 }
 
-}  // namespace
-
-namespace lse_detail {
-
-cudaError_t launch_evolve(StepPlan &plan, int sm_count, cudaStream_t s)
+// Runs `launch` (a cooperative launch on s) after the device's previous
+// persistent evolution and makes it the one the next waits for (not under
+// stream capture, where the graph's own order applies).
+template <class F>
+cudaError_t coop_ordered(cudaStream_t s, F launch)
 {
-    if (plan.form != LSE_FORM_TILE || plan.args.mb_split || !persist_enabled())
-        return cudaErrorNotSupported;
-    EvolveArgs e;
-    e.a = plan.args;
-    e.phi[0] = plan.phi[0];
-    e.phi[1] = plan.phi[1];
-    e.cap = plan.iterations;
-    e.reinit_period = plan.reinit_period;
-    e.early_stop = plan.early_stop ? 1 : 0;
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
@@ -108,10 +99,30 @@ cudaError_t launch_evolve(StepPlan &plan, int sm_count, cudaStream_t s)
         if (err != cudaSuccess) return err;
     }
     if (chain && (err = cudaStreamWaitEvent(s, g_coop_event[dev], 0)) != cudaSuccess) return err;
-    err = launch_evolve_tile(e, plan.phi_maps[0], plan.phi_maps[1], plan.data_map, plan.nblocks,
-                             sm_count, s);
+    err = launch();
     if (err != cudaSuccess) return err;
     return chain ? cudaEventRecord(g_coop_event[dev], s) : cudaSuccess;
+}
+
+}  // namespace
+
+namespace lse_detail {
+
+cudaError_t launch_evolve(StepPlan &plan, int sm_count, cudaStream_t s)
+{
+    if (plan.form != LSE_FORM_TILE || plan.args.mb_split || !persist_enabled())
+        return cudaErrorNotSupported;
+    EvolveArgs e;
+    e.a = plan.args;
+    e.phi[0] = plan.phi[0];
+    e.phi[1] = plan.phi[1];
+    e.cap = plan.iterations;
+    e.reinit_period = plan.reinit_period;
+    e.early_stop = plan.early_stop ? 1 : 0;
+    return coop_ordered(s, [&]() {
+        return launch_evolve_tile(e, plan.phi_maps[0], plan.phi_maps[1], plan.data_map,
+                                  plan.nblocks, sm_count, s);
+    });
 }
 
 cudaError_t coop_chain_mark(cudaStream_t s)
@@ -134,20 +145,19 @@ bool evolve_bands_applies(int H, int W, int B, const lse_params &p)
            p.ts >= 3 && p.ts <= 15 && (long long)H * W < 0xFFFFFFFFll;
 }
 
-cudaError_t launch_evolve_bands(int H, int W, int B, const lse_params &p, int pitch,
-                                size_t band_stride, const float *bands, float *const phi[2],
-                                LseDevState *st, LseCandidates *cand, int sm_count,
-                                cudaStream_t s)
+bool plan_evolve_bands(int H, int W, int B, const lse_params &p, int pitch,
+                       size_t band_stride, const float *bands, float *const phi[2],
+                       LseDevState *st, LseCandidates *cand, int sm_count, EvolveArgs *e,
+                       CUtensorMap maps[3], int *nblocks)
 {
-    if (!evolve_bands_applies(H, W, B, p) || !cand) return cudaErrorNotSupported;
-    StepPlan plan;
-    StepArgs &a = plan.args;
+    if (!evolve_bands_applies(H, W, B, p) || !cand) return false;
+    StepArgs a;
     memset(&a, 0, sizeof(a));
     a.rad = (p.ts - 1) / 2;
     a.storage = LSE_F32;
     constexpr int kNw = 4;            // 32-row tiles: the bands of a tile fill the memory
-    if (!plan_step_tile(H, W, 1, LSE_TERM_EDGE, a.rad, kNw, sm_count, &a, &plan.nblocks))
-        return cudaErrorNotSupported;
+    if (!plan_step_tile(H, W, 1, LSE_TERM_EDGE, a.rad, kNw, sm_count, &a, nblocks))
+        return false;
     a.H = H;
     a.W = W;
     a.B = B;
@@ -167,41 +177,42 @@ cudaError_t launch_evolve_bands(int H, int W, int B, const lse_params &p, int pi
     a.st = st;
     a.pdl = 0;
     const int urows = 8 * kNw;
-    if (!encode_box(&plan.phi_maps[0], phi[0], LSE_F32, W, H, pitch, 0, 1, 136, urows + 2) ||
-        !encode_box(&plan.phi_maps[1], phi[1], LSE_F32, W, H, pitch, 0, 1, 136, urows + 2) ||
-        !encode_box(&plan.data_map, bands, LSE_F32, W, H, pitch, band_stride, B, 128, urows))
-        return cudaErrorNotSupported;
+    if (!encode_box(&maps[0], phi[0], LSE_F32, W, H, pitch, 0, 1, 136, urows + 2) ||
+        !encode_box(&maps[1], phi[1], LSE_F32, W, H, pitch, 0, 1, 136, urows + 2) ||
+        !encode_box(&maps[2], bands, LSE_F32, W, H, pitch, band_stride, B, 128, urows))
+        return false;
+    e->a = a;
+    e->phi[0] = phi[0];
+    e->phi[1] = phi[1];
+    e->cap = p.iterations;
+    e->reinit_period = p.reinit_period;
+    e->early_stop = p.early_stop_frac > 0.0f ? 1 : 0;
+    e->cand = cand;
+    return true;
+}
+
+cudaError_t launch_evolve_bands(int H, int W, int B, const lse_params &p, int pitch,
+                                size_t band_stride, const float *bands, float *const phi[2],
+                                LseDevState *st, LseCandidates *cand, int sm_count,
+                                cudaStream_t s)
+{
     EvolveArgs e;
-    e.a = a;
-    e.phi[0] = phi[0];
-    e.phi[1] = phi[1];
-    e.cap = p.iterations;
-    e.reinit_period = p.reinit_period;
-    e.early_stop = p.early_stop_frac > 0.0f ? 1 : 0;
-    e.cand = cand;
-    int dev = 0;
-    cudaError_t err = cudaGetDevice(&dev);
-    if (err != cudaSuccess) return err;
-    if (dev < 0 || dev >= kMaxDev) return cudaErrorNotSupported;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    err = cudaStreamIsCapturing(s, &cs);
-    if (err != cudaSuccess) return err;
-    const bool chain = cs == cudaStreamCaptureStatusNone;
-    std::lock_guard<std::mutex> lock(g_coop_mutex);
-    if (chain && !g_coop_event[dev]) {
-        err = cudaEventCreateWithFlags(&g_coop_event[dev], cudaEventDisableTiming);
-        if (err != cudaSuccess) {
-            g_coop_event[dev] = nullptr;
-            return err;
-        }
-        err = cudaEventRecord(g_coop_event[dev], s);
-        if (err != cudaSuccess) return err;
-    }
-    if (chain && (err = cudaStreamWaitEvent(s, g_coop_event[dev], 0)) != cudaSuccess) return err;
-    err = launch_evolve_mb(e, plan.phi_maps[0], plan.phi_maps[1], plan.data_map, plan.nblocks,
-                           sm_count, s);
-    if (err != cudaSuccess) return err;
-    return chain ? cudaEventRecord(g_coop_event[dev], s) : cudaSuccess;
+    CUtensorMap maps[3];
+    int nblocks = 0;
+    if (!plan_evolve_bands(H, W, B, p, pitch, band_stride, bands, phi, st, cand, sm_count, &e,
+                           maps, &nblocks))
+        return cudaErrorNotSupported;
+    return coop_ordered(s, [&]() {
+        return launch_evolve_mb(e, maps[0], maps[1], maps[2], nblocks, sm_count, s);
+    });
+}
+
+cudaError_t launch_evolve_bands_group(int B, int rad, const MbGroupItem *items,
+                                      const int *cta_item, int nblocks, cudaStream_t s)
+{
+    return coop_ordered(s, [&]() {
+        return launch_evolve_mb_group(B, rad, items, cta_item, nblocks, s);
+    });
 }
 
 void gauss_taps(double sigma, int rad, double *out)

@@ -1238,14 +1238,17 @@ __device__ __forceinline__ double mb_d_at(const StepArgs &a, unsigned int pix,
 // reports the largest FP32 |D| above M (1 + 2^-20)) joins the candidates and
 // the step is done again from the same input LSF with that pixel's |D| as M,
 // so every step uses M = max_x |D(x)|.  All CTAs decide a redo identically.
+// The body, run by CTA `cta` of the `ncta` CTAs given to the image (the
+// whole grid of a one-image launch, or the image's share of a group
+// launch): its grid barrier counts those CTAs only.
 template <int RAD, int NB, int NW>
-__global__ void __launch_bounds__(TileGeo<RAD, float, NW, NB>::THREADS,
-                                  TileGeo<RAD, float, NW, NB>::MIN_BLOCKS)
-evolve_mb_kernel(const __grid_constant__ EvolveArgs e,
-                 const __grid_constant__ CUtensorMap phi_map0,
-                 const __grid_constant__ CUtensorMap phi_map1,
-                 const __grid_constant__ CUtensorMap data_map)
+__device__ __forceinline__ void mb_evolve(const EvolveArgs &e, const CUtensorMap *pm0,
+                                          const CUtensorMap *pm1, const CUtensorMap *dmap,
+                                          int cta, int ncta)
 {
+    const CUtensorMap &phi_map0 = *pm0;
+    const CUtensorMap &phi_map1 = *pm1;
+    const CUtensorMap &data_map = *dmap;
     const StepArgs &a = e.a;
     LseDevState *st = a.st;
     LseCandidates *cand = e.cand;
@@ -1255,7 +1258,6 @@ evolve_mb_kernel(const __grid_constant__ EvolveArgs e,
     __shared__ int s_done, s_redo;
     __shared__ long long s_tot[NB];     // sum I_b over the image (lse_fix units)
     __shared__ double s_cp[NB], s_cm[NB];
-    const int cta = blockIdx.x, ncta = gridDim.x;
     bool have_tot = false;
     if (threadIdx.x == 0) {
         // the prologue made the first step's statistics
@@ -1422,6 +1424,106 @@ evolve_mb_kernel(const __grid_constant__ EvolveArgs e,
     }
     __syncthreads();
     drain_issued(s_pc);
+}
+
+template <int RAD, int NB, int NW>
+__global__ void __launch_bounds__(TileGeo<RAD, float, NW, NB>::THREADS,
+                                  TileGeo<RAD, float, NW, NB>::MIN_BLOCKS)
+evolve_mb_kernel(const __grid_constant__ EvolveArgs e,
+                 const __grid_constant__ CUtensorMap phi_map0,
+                 const __grid_constant__ CUtensorMap phi_map1,
+                 const __grid_constant__ CUtensorMap data_map)
+{
+    mb_evolve<RAD, NB, NW>(e, &phi_map0, &phi_map1, &data_map, blockIdx.x, gridDim.x);
+}
+
+// Several vector images of one band count and radius in one cooperative
+// launch: CTA c works on image cta_item[c], as CTA c - cta0 of its ncta.
+// Each image keeps its own state record, candidates, tile queue and grid
+// barrier; the exact sums make its results those of the one-image launch.
+template <int RAD, int NB, int NW>
+__global__ void __launch_bounds__(TileGeo<RAD, float, NW, NB>::THREADS,
+                                  TileGeo<RAD, float, NW, NB>::MIN_BLOCKS)
+evolve_mb_group_kernel(const MbGroupItem *__restrict__ items, const int *__restrict__ cta_item)
+{
+    const MbGroupItem &it = items[cta_item[blockIdx.x]];
+    mb_evolve<RAD, NB, NW>(it.e, &it.maps[0], &it.maps[1], &it.maps[2],
+                           (int)blockIdx.x - it.cta0, it.ncta);
+}
+
+// CTAs of the group kernel that fit on the device at once.
+template <int RAD, int NB>
+int evolve_mb_group_capacity_one(int sm_count)
+{
+    constexpr int NW = 4;
+    using G = TileGeo<RAD, float, NW, NB>;
+    auto kern = evolve_mb_group_kernel<RAD, NB, NW>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::BYTES) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::THREADS, G::BYTES) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * sm_count;
+}
+
+template <int RAD, int NB>
+cudaError_t launch_evolve_mb_group_one(const MbGroupItem *items, const int *cta_item,
+                                       int nblocks, cudaStream_t s)
+{
+    constexpr int NW = 4;
+    using G = TileGeo<RAD, float, NW, NB>;
+    auto kern = evolve_mb_group_kernel<RAD, NB, NW>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           G::BYTES);
+    if (err != cudaSuccess) return err;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned int)nblocks);
+    cfg.blockDim = dim3(G::THREADS);
+    cfg.dynamicSmemBytes = G::BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, items, cta_item);
+}
+
+template <int NB>
+int evolve_mb_group_capacity(int rad, int sm_count)
+{
+    switch (rad) {
+    case 1: return evolve_mb_group_capacity_one<1, NB>(sm_count);
+    case 2: return evolve_mb_group_capacity_one<2, NB>(sm_count);
+    case 3: return evolve_mb_group_capacity_one<3, NB>(sm_count);
+    case 4: return evolve_mb_group_capacity_one<4, NB>(sm_count);
+    case 5: return evolve_mb_group_capacity_one<5, NB>(sm_count);
+    case 6: return evolve_mb_group_capacity_one<6, NB>(sm_count);
+    case 7: return evolve_mb_group_capacity_one<7, NB>(sm_count);
+    default: return 0;
+    }
+}
+
+template <int NB>
+cudaError_t launch_evolve_mb_group(int rad, const MbGroupItem *items, const int *cta_item,
+                                   int nblocks, cudaStream_t s)
+{
+    switch (rad) {
+    case 1: return launch_evolve_mb_group_one<1, NB>(items, cta_item, nblocks, s);
+    case 2: return launch_evolve_mb_group_one<2, NB>(items, cta_item, nblocks, s);
+    case 3: return launch_evolve_mb_group_one<3, NB>(items, cta_item, nblocks, s);
+    case 4: return launch_evolve_mb_group_one<4, NB>(items, cta_item, nblocks, s);
+    case 5: return launch_evolve_mb_group_one<5, NB>(items, cta_item, nblocks, s);
+    case 6: return launch_evolve_mb_group_one<6, NB>(items, cta_item, nblocks, s);
+    case 7: return launch_evolve_mb_group_one<7, NB>(items, cta_item, nblocks, s);
+    default: return cudaErrorNotSupported;
+    }
 }
 
 template <int RAD, int NB>

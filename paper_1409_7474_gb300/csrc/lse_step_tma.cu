@@ -60,6 +60,12 @@ cudaError_t launch_evolve_mb3(const EvolveArgs &, const CUtensorMap &, const CUt
                               const CUtensorMap &, int, int, cudaStream_t);
 cudaError_t launch_evolve_mb4(const EvolveArgs &, const CUtensorMap &, const CUtensorMap &,
                               const CUtensorMap &, int, int, cudaStream_t);
+cudaError_t launch_evolve_mb_group2(int, const MbGroupItem *, const int *, int, cudaStream_t);
+cudaError_t launch_evolve_mb_group3(int, const MbGroupItem *, const int *, int, cudaStream_t);
+cudaError_t launch_evolve_mb_group4(int, const MbGroupItem *, const int *, int, cudaStream_t);
+int evolve_mb_group_capacity2(int, int);
+int evolve_mb_group_capacity3(int, int);
+int evolve_mb_group_capacity4(int, int);
 
 }  // namespace lse_detail
 
@@ -254,6 +260,27 @@ cudaError_t launch_evolve_mb(const EvolveArgs &e, const CUtensorMap &pm0,
     case 3: return launch_evolve_mb3(e, pm0, pm1, dm, nblocks, sm_count, s);
     case 4: return launch_evolve_mb4(e, pm0, pm1, dm, nblocks, sm_count, s);
     default: return cudaErrorNotSupported;
+    }
+}
+
+cudaError_t launch_evolve_mb_group(int B, int rad, const MbGroupItem *items,
+                                   const int *cta_item, int nblocks, cudaStream_t s)
+{
+    switch (B) {
+    case 2: return launch_evolve_mb_group2(rad, items, cta_item, nblocks, s);
+    case 3: return launch_evolve_mb_group3(rad, items, cta_item, nblocks, s);
+    case 4: return launch_evolve_mb_group4(rad, items, cta_item, nblocks, s);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+int evolve_mb_group_capacity(int B, int rad, int sm_count)
+{
+    switch (B) {
+    case 2: return evolve_mb_group_capacity2(rad, sm_count);
+    case 3: return evolve_mb_group_capacity3(rad, sm_count);
+    case 4: return evolve_mb_group_capacity4(rad, sm_count);
+    default: return 0;
     }
 }
 

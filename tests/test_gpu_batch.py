@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import oracle
-from _parity import assert_mask_parity, is_vector_region, step_launches
+from _parity import assert_mask_parity
 from paper_1409_7474_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -59,13 +59,11 @@ def device_items(torch, ctx, probs):
 
 
 def single(torch, ctx, it):
-    # vector images in a batch take the band passes: the single call takes
-    # them too (the persistent path agrees within the parity tolerance,
-    # tests/test_gpu_bands.py)
-    with step_launches(is_vector_region(it)):
-        v, m, st = ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
-                              iterations=it["iterations"],
-                              early_stop_frac=it["early_stop_frac"], storage=it["storage"])
+    # vector images in a batch run as a group of persistent evolutions, each
+    # with its own share of the CTAs: the bits of one call alone
+    v, m, st = ctx.evolve(it.get("image"), it["phi0"], it["term"], g=it.get("g"),
+                          iterations=it["iterations"],
+                          early_stop_frac=it["early_stop_frac"], storage=it["storage"])
     torch.cuda.synchronize()
     return v.cpu().numpy(), m.cpu().numpy(), st
 
@@ -187,3 +185,27 @@ def test_batch_rejections(torch, lse, ctx):
     host_phi = torch.ones((64, 64))
     assert run(x, ok, phi0=host_phi) == lse.LSE_ERR_INVALID_ARG
     assert b"device memory" in lib.lse_last_error(ctx._h)
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_vector_images_beyond_one_group_launch(torch, ctx, use_graph):
+    # 320 small 4-band images: more than one cooperative launch holds (two
+    # CTAs per SM), so they run as several group launches; each image's
+    # bits are those of one call alone, and a batch of vector images only
+    # has no per-iteration launches at all
+    probs = scenes.batch_problems(320, seed=17, min_side=24, max_side=72, cap_range=(2, 9))
+    for q in probs:
+        q["image"] = np.ascontiguousarray(np.repeat(q["image"][:1], 4, axis=0) *
+                                          np.array([1.0, 0.9, 0.8, 0.7], np.float32)[:, None, None])
+        q["term"] = "region"
+        q["early_stop_frac"] = 0.0
+    items = device_items(torch, ctx, probs)
+    res = ctx.evolve_batch(items, use_graph=use_graph)
+    torch.cuda.synchronize()
+    for k in range(0, len(items), 23):
+        v, m, st = res[k]
+        v1, m1, st1 = single(torch, ctx, items[k])
+        assert same_bits(v.cpu().numpy(), v1)
+        assert np.array_equal(m.cpu().numpy(), m1)
+        assert st["iterations_run"] == st1["iterations_run"] == items[k]["iterations"]
+        assert st["c_plus"] == st1["c_plus"]

@@ -191,14 +191,12 @@ def test_autotuned_context_keeps_batch_and_server_equal_to_evolve(torch, lse):
             return v1.cpu().numpy(), st1
 
         for it, (v, m, st), rid in zip(items, res, ids):
-            # a batch takes vector images one launch per step; the server
-            # runs them alone through lse_evolve's default path
-            v1, st1 = alone(it, is_vector_region(it))
+            # batches and the server give every image lse_evolve's bits
+            v1, st1 = alone(it, False)
             assert same_bits(v.cpu().numpy(), v1)
             assert st["iterations_run"] == st1["iterations_run"]
             assert st["c_plus"] == st1["c_plus"]
-            v2 = v1 if not is_vector_region(it) else alone(it, False)[0]
-            assert same_bits(served[rid][0].cpu().numpy(), v2)
+            assert same_bits(served[rid][0].cpu().numpy(), v1)
 
 
 def test_autotune_rejects_bad_arguments(torch, lse, ctx64):
