@@ -10,12 +10,13 @@
 // kept for lse_server_poll, and its memory returned.  Each request keeps the
 // CTA count, statistics and reductions lse_evolve would give it alone, so
 // its result does not depend on what else is running.  Vector images and
-// large images never join the mix: each runs alone, to its end, through
-// lse_evolve itself (one persistent launch) inside one advance, the oldest
-// first, one per advance.  Under light load (the mix empty, a few requests
-// waiting) every request runs that way, one per advance, in arrival order.
-// For one band and the edge term lse_evolve's persistent launch gives the
-// bits the mix gives.
+// large images never join the mix: each runs to its end inside one advance
+// through lse_evolve's own path -- a large image alone, the oldest first, one
+// per advance; the queued vector images together, in one lse_evolve_batch
+// whose group launch gives each its own CTAs (lse_evolve's bits).  Under
+// light load (the mix empty, a few requests waiting) every request runs
+// alone, one per advance, in arrival order.  For one band and the edge term
+// lse_evolve's persistent launch gives the bits the mix gives.
 #include <math.h>
 #include <string.h>
 
@@ -43,6 +44,8 @@ constexpr long long kSoloPixels = 1ll << 21;
 // At most this many requests waiting and none in the mix: light load, one
 // request at a time, alone.
 constexpr size_t kLightQueue = 4;
+// At most this many queued vector images run together in one advance.
+constexpr int kVectorGroup = 32;
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
@@ -322,6 +325,33 @@ lse_status lse_server_advance(lse_server *sv, int ticks, int *running, void *str
             if ((size_t)q.H * q.W <= ctx->max_pixels && q.B <= ctx->max_bands) {
                 pick = sv->queue.begin();
                 light = true;
+            }
+        }
+        if (pick == sv->queue.end()) {
+            // the queued vector images together: one lse_evolve_batch, whose
+            // group launches step each on its own CTAs (lse_evolve's bits),
+            // so small ones no longer hold the whole GPU each
+            std::vector<long long> vec;
+            for (long long id : sv->queue) {
+                const Request &rq = sv->reqs[id];
+                if (rq.solo && rq.q.params.term == LSE_TERM_REGION && rq.q.B > 1)
+                    vec.push_back(id);
+                if ((int)vec.size() == kVectorGroup) break;
+            }
+            if (vec.size() > 1) {
+                std::vector<lse_problem> probs;
+                for (long long id : vec) probs.push_back(sv->reqs[id].q);
+                std::vector<lse_stats> sts(vec.size());
+                r = lse_evolve_batch(ctx, (int)probs.size(), probs.data(), 0, sts.data(),
+                                     stream);
+                if (r != LSE_OK) return r;
+                for (size_t k = 0; k < vec.size(); ++k) {
+                    Request &rq = sv->reqs[vec[k]];
+                    sts[k].elapsed_ms = -1.0f;
+                    rq.stats = sts[k];
+                    rq.state = REQ_DONE;
+                    sv->queue.erase(std::find(sv->queue.begin(), sv->queue.end(), vec[k]));
+                }
             }
         }
         if (pick == sv->queue.end())

@@ -289,3 +289,32 @@ def test_light_load_runs_one_request_per_advance_in_arrival_order(torch, lse, ct
     results = {}
     drain(sv, ids, results)
     sv.destroy()
+
+
+def test_queued_vector_images_run_together(torch, lse, ctx):
+    # three vector images queued behind small requests: one advance runs
+    # them together (one batch, each on its own CTAs) and admits the rest
+    # into the mix; every result keeps lse_evolve's bits
+    probs = scenes.batch_problems(8, seed=61, min_side=48, max_side=160, cap_range=(20, 40))
+    for k, q in enumerate(probs):
+        q["early_stop_frac"] = 0.0
+        if k < 5:
+            q["image"] = q["image"][:1]
+        else:
+            q["image"] = np.ascontiguousarray(np.repeat(q["image"][:1], 3, axis=0) *
+                                              np.array([1.0, 0.8, 0.6], np.float32)[:, None, None])
+            q["term"] = "region"
+    items = device_items(torch, ctx, probs)
+    sv = lse.Server(ctx, 512 << 20)
+    ids = [sv.submit(it) for it in items]
+    running = sv.advance(1)
+    assert running == 5
+    for k in (5, 6, 7):
+        r = sv.poll(ids[k])
+        assert r is not None
+        v1, m1, st1 = alone(torch, ctx, items[k])
+        assert np.array_equal(r[0].cpu().numpy().view(np.uint32), v1.view(np.uint32))
+        assert r[2]["iterations_run"] == st1["iterations_run"]
+    results = {}
+    drain(sv, ids[:5], results)
+    sv.destroy()
