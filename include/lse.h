@@ -383,10 +383,11 @@ lse_status lse_autotune(lse_ctx *ctx, int n, const lse_problem *problems, int it
  * phi_out / mask_out.  Three kinds of request skip the mix and run to
  * their end inside one advance, before the mix's iterations: vector images
  * of the region term (their own path stages the bands in one launch per
- * evolution; the mix needs three per iteration) -- those queued run
- * together, up to 32, as one lse_evolve_batch whose group launch gives each
- * its own CTAs; images of 2^21 pixels or more (their tiles fill the GPU
- * alone), alone through lse_evolve, the oldest first, one per advance; and,
+ * evolution; the mix needs three per iteration) -- the queued ones below
+ * 2^21 pixels run together, up to 32, as one lse_evolve_batch whose group
+ * launch gives each its own CTAs; images of 2^21 pixels or more (their
+ * tiles fill the GPU alone), alone through lse_evolve, the oldest first, one
+ * per advance; and,
  * under light load (nothing in the mix, at most 4 requests waiting), every
  * request: an advance then runs only the oldest, so that a lightly loaded
  * server answers as fast as a direct call per request.  Each needs H * W

@@ -12,8 +12,9 @@
 // its result does not depend on what else is running.  Vector images and
 // large images never join the mix: each runs to its end inside one advance
 // through lse_evolve's own path -- a large image alone, the oldest first, one
-// per advance; the queued vector images together, in one lse_evolve_batch
-// whose group launch gives each its own CTAs (lse_evolve's bits).  Under
+// per advance; the queued small vector images together, in one
+// lse_evolve_batch whose group launch gives each its own CTAs (lse_evolve's
+// bits).  Under
 // light load (the mix empty, a few requests waiting) every request runs
 // alone, one per advance, in arrival order.  For one band and the edge term
 // lse_evolve's persistent launch gives the bits the mix gives.
@@ -44,7 +45,8 @@ constexpr long long kSoloPixels = 1ll << 21;
 // At most this many requests waiting and none in the mix: light load, one
 // request at a time, alone.
 constexpr size_t kLightQueue = 4;
-// At most this many queued vector images run together in one advance.
+// At most this many queued vector images (each below kSoloPixels) run
+// together in one advance.
 constexpr int kVectorGroup = 32;
 constexpr size_t kAlign = 256;
 
@@ -327,14 +329,16 @@ lse_status lse_server_advance(lse_server *sv, int ticks, int *running, void *str
                 light = true;
             }
         }
-        if (pick == sv->queue.end()) {
+        if (!light) {
             // the queued vector images together: one lse_evolve_batch, whose
             // group launches step each on its own CTAs (lse_evolve's bits),
             // so small ones no longer hold the whole GPU each
             std::vector<long long> vec;
             for (long long id : sv->queue) {
                 const Request &rq = sv->reqs[id];
-                if (rq.solo && rq.q.params.term == LSE_TERM_REGION && rq.q.B > 1)
+                // the small ones: a large vector image fills the GPU alone
+                if (rq.solo && rq.q.params.term == LSE_TERM_REGION && rq.q.B > 1 &&
+                    (long long)rq.q.H * rq.q.W < kSoloPixels)
                     vec.push_back(id);
                 if ((int)vec.size() == kVectorGroup) break;
             }
@@ -354,7 +358,8 @@ lse_status lse_server_advance(lse_server *sv, int ticks, int *running, void *str
                 }
             }
         }
-        if (pick == sv->queue.end())
+        // (the erasures above invalidated the queue's iterators)
+        if (!light)
             pick = std::find_if(sv->queue.begin(), sv->queue.end(),
                                 [&](long long id) { return sv->reqs[id].solo; });
         if (pick != sv->queue.end()) {
