@@ -320,9 +320,10 @@ def serve_measurement(torch, lse, dev, n_req: int, rates, seed: int = 9,
     not serve), replayed in real time at each offered rate (requests per
     second): through lse_server (continuous batching of the small
     single-band and edge requests, `ticks` iterations per advance, a
-    `budget`-byte memory budget; vector and large images each alone, one per
-    advance), and one lse_evolve call per request in arrival order with the
-    same storage.  Latency = completion - arrival; throughput = requests over
+    `budget`-byte memory budget; large images alone, one per advance; the
+    queued small vector images together as one batch of group launches),
+    and one lse_evolve call per request in arrival order with the same
+    storage.  Latency = completion - arrival; throughput = requests over
     the makespan; percentiles over all requests of one trial."""
     import time
     from paper_1409_7474_gb300 import scenes
