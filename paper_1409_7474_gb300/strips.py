@@ -151,6 +151,14 @@ class TorchComm:
             t.copy_(h)
         return t
 
+    def send(self, t, dst: int):
+        """Blocking point-to-point send of tensor ``t`` to rank ``dst``."""
+        self._dist.send(t, dst=self._peer(dst), group=self.group)
+
+    def recv(self, t, src: int):
+        """Blocking receive into tensor ``t`` from rank ``src``."""
+        self._dist.recv(t, src=self._peer(src), group=self.group)
+
     def exchange(self, to_prev, to_next, like_prev, like_next):
         """Sends ``to_prev`` to rank - 1 and ``to_next`` to rank + 1 (None
         where there is no neighbour) and receives buffers shaped like
@@ -393,16 +401,15 @@ def gather_rows(comm, part: Partition, v):
         else own.contiguous()
     if comm.world == 1:
         return own_t.cpu().numpy()
-    d = comm._dist
     if part.rank == 0:
         rows = [own_t.cpu()]
         for r in range(1, part.world):
             pr = partition(part.H, part.W, 2 * part.halo - 1, r, part.world)
             buf = torch.empty((pr.y1 - pr.y0, part.W), dtype=own_t.dtype, device=own_t.device)
-            d.recv(buf, src=comm._peer(r), group=comm.group)
+            comm.recv(buf, r)
             rows.append(buf.cpu())
         return torch.cat(rows).numpy()
-    d.send(own_t, dst=comm._peer(0), group=comm.group)
+    comm.send(own_t, 0)
     return None
 
 

@@ -160,6 +160,17 @@ def _worker(rank, world, port, out):
             from test_strips import compare, run_strips
             p, v_own, st, _ = run_strips(comm, case, rank, world)
             res[i] = compare(case, p, v_own, st)
+            if i == 0:
+                # rank 0 gathers the owned rows into the whole image
+                strip = np.zeros((p.rows, p.W))
+                a, b = p.own
+                strip[a:b] = v_own
+                full = S.gather_rows(comm, p, strip)
+                if rank == 0:
+                    from test_strips import whole_image
+                    res["gathered_err"] = float(np.max(np.abs(full - whole_image(case)[0])))
+                else:
+                    res["gathered_none"] = full is None
         # a driver whose halo exchange does nothing
         real = S.exchange_halo
         S.exchange_halo = lambda comm, part, v, binary: v
@@ -213,5 +224,7 @@ def test_gloo_ranks_reproduce_the_whole_image(world):
         for r in range(world):
             err, bad, diff, _ = res[r][i]
             assert diff == [] and bad == 0 and err < 1e-9, (case, r, err, bad, diff)
+    assert res[0]["gathered_err"] < 1e-9
+    assert all(res[r]["gathered_none"] for r in range(1, world))
     # without the exchange the rows next to a cut go wrong
     assert any(res[r]["no_halo"][0] > 1e-3 or res[r]["no_halo"][1] > 0 for r in range(world))
