@@ -179,7 +179,8 @@ bool plan_evolve_bands(int H, int W, int B, const lse_params &p, int pitch,
     const int urows = 8 * kNw;
     if (!encode_box(&maps[0], phi[0], LSE_F32, W, H, pitch, 0, 1, 136, urows + 2) ||
         !encode_box(&maps[1], phi[1], LSE_F32, W, H, pitch, 0, 1, 136, urows + 2) ||
-        !encode_box(&maps[2], bands, LSE_F32, W, H, pitch, band_stride, B, 128, urows))
+        !encode_box(&maps[2], bands, LSE_F32, W, H, pitch, band_stride, B, 128,
+                    urows - 2 * a.rad))
         return false;
     e->a = a;
     e->phi[0] = phi[0];

@@ -138,16 +138,24 @@ struct TileGeo {
     static constexpr int DATA_W = WIDE ? 128 : kPhiW;           // staged data columns
     static constexpr int DATA_X0 = WIDE ? 0 : 4;                // tile column 0 within it
     static constexpr int PHI_BYTES = PHI_ROWS * kPhiW * (int)sizeof(T);
-    // NB data planes (the bands of a vector image), one box each
-    static constexpr int PLANE = UR * DATA_W;                   // elements per data plane
+    // NB data planes (the bands of a vector image), one box each.  A vector
+    // image stages the bands of its TH output rows only (u rows RAD ..
+    // RAD + TH - 1); D of the 2 RAD halo u rows is formed from global memory
+    // into a buffer of its own, which leaves room for a third CTA per SM
+    static constexpr int DROW0 = NB > 1 ? RAD : 0;              // first staged u row
+    static constexpr int DROWS = UR - 2 * DROW0;                // staged data rows
+    static constexpr int PLANE = DROWS * DATA_W;                // elements per data plane
     static constexpr int DATA_BYTES = NB * PLANE * (int)sizeof(T);
     // offsets in floats: [sqrt table 32][2 mbarriers][old-sign words 64 x 4]
-    // [phi][data][h (16-bit storage only)]
+    // [phi][data][h (16-bit storage only) | halo D (vector images)]
     static constexpr int SIGN_OFF = 64;
     static constexpr int PHI_OFF = SIGN_OFF + UR * 4;
     static constexpr int DATA_OFF = PHI_OFF + ((PHI_BYTES / 4 + 31) & ~31);
     static constexpr int HBUF_OFF = DATA_OFF + ((DATA_BYTES / 4 + 31) & ~31);
-    static constexpr int FLOATS = WIDE ? DATA_OFF + DATA_BYTES / 4 : HBUF_OFF + UR * 128;
+    static constexpr int DH_OFF = HBUF_OFF;                     // 2 RAD rows x 128
+    static constexpr int FLOATS = !WIDE ? HBUF_OFF + UR * 128
+                                : NB > 1 ? DH_OFF + 2 * RAD * 128
+                                         : DATA_OFF + DATA_BYTES / 4;
     static constexpr int BYTES = FLOATS * 4 + 128;              // + alignment slack
     // h of u row ur: float index (ur + H_ROW0) * H_STRIDE + H_COL0 + 4 lane
     // from the phi buffer (FP32) or from the h buffer (16-bit)
@@ -159,7 +167,7 @@ struct TileGeo {
     static constexpr bool CLAMP_H = !WIDE && NW * RPW - 1 + 2 * RAD > UR - 1;
     // CTAs per SM (launch bounds): 24 warps for RAD <= 4, else 16; vector
     // images as many as their shared memory allows (228 KB per SM), at most
-    // 3 (the step of a vector image needs about 170 registers a thread)
+    // 3 (the step of a vector image needs 150-170 registers a thread)
     static constexpr int MB_BLOCKS = (227 * 1024) / (BYTES + 3072);
     static constexpr int MIN_BLOCKS =
         NB == 1 ? (RAD <= 4 ? 24 : 16) / NW
@@ -440,7 +448,7 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
         int xs, ys;
         origin(t, xs, ys);
         if (MB)
-            tma_box3(dat_dst, data_map, xs - G::DATA_X0, ys + 1, bar_dat, kDatBytes);
+            tma_box3(dat_dst, data_map, xs - G::DATA_X0, ys + 1 + G::DROW0, bar_dat, kDatBytes);
         else
             tma_box(dat_dst, data_map, xs - G::DATA_X0, ys + 1, bar_dat, kDatBytes);
     };
@@ -483,6 +491,24 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
     const T *bl = buf + 4 + 4 * lane;            // this lane's 4 columns of a phi row
     const T *dl = dat + G::DATA_X0 + 4 * lane;   // ... of a data row
     float *hl = hbase + G::H_COL0 + 4 * lane;    // ... of an h row
+    float *dhl = smem_f + sb + G::DH_OFF + 4 * lane;   // ... of a halo D row
+
+    // D = sum_b af_b (I_b - m_b) (Eq. 17's numerator) on the lane's 4
+    // columns, bands in order, on column pairs; band(b) gives I_b there
+    auto mb_d = [&](auto band) {
+        f2 d01 = f2_pack(0.0f, 0.0f), d23 = d01;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const float4 e = band(b);
+            const f2 a2 = f2_pack(af[b], af[b]), m2 = f2_pack(mb_m[b], mb_m[b]);
+            d01 = f2_fma(a2, f2_sub(f2_pack(e.x, e.y), m2), d01);
+            d23 = f2_fma(a2, f2_sub(f2_pack(e.z, e.w), m2), d23);
+        }
+        float4 d4;
+        f2_unpack(d01, d4.x, d4.y);
+        f2_unpack(d23, d4.z, d4.w);
+        return d4;
+    };
 
     // test hook: a wait that cannot complete (nothing arrives on bar_never)
     // runs out into the TIMEOUT status; the first tile's copies, issued
@@ -496,6 +522,35 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
         int xs, ys;
         origin(t, xs, ys);
         const int x0 = xs + 4 * lane;
+        if constexpr (MB) {
+            // D of the halo u rows 0 .. RAD - 1 and TH + RAD .. UR - 1 (slots
+            // k = 0 .. 2 RAD - 1), from global memory while the tile's boxes
+            // land; outside the image a band reads as zero, as the boxes'
+            // fill gives it, so D is that of the staged rows bit for bit.
+            // The slots were last read before the previous tile's vertical
+            // pass; the waits below order these stores before their reads
+            const bool xin = x0 >= 0 && x0 < W;       // x0 is a multiple of 4
+#pragma unroll 1
+            for (int k = warp; k < 2 * RAD; k += NW) {
+                const int y = ys + 1 + (k < RAD ? k : TH + k);
+                const bool in = xin && y >= 0 && y < H;
+                const float4 d4 = mb_d([&](int b) {
+                    float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    if (in) {
+                        // x0 < W and the pitch is a multiple of 4, so the
+                        // load stays in the row; columns at or past W are
+                        // zeroed
+                        e = __ldg(reinterpret_cast<const float4 *>(
+                            a.data + b * a.band_stride + (size_t)y * a.pitch + x0));
+                        if (x0 + 1 >= W) e.y = 0.0f;
+                        if (x0 + 2 >= W) e.z = 0.0f;
+                        if (x0 + 3 >= W) e.w = 0.0f;
+                    }
+                    return e;
+                });
+                *reinterpret_cast<float4 *>(dhl + k * 128) = d4;
+            }
+        }
         if (!wait_bar(bar_phi, par) || !wait_bar(bar_dat, par)) {
             failed = true;
             break;
@@ -558,18 +613,17 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
             float ep = S::ld1(buf + (ur + 2) * kPhiW + eidx);
             float4 d4;
             if constexpr (MB) {
-                // D = sum_b af_b (I_b - m_b), bands in order, on column pairs
-                f2 d01 = f2_pack(0.0f, 0.0f), d23 = d01;
-#pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    const float4 e = lds4(reinterpret_cast<const float *>(dl) + b * G::PLANE +
-                                          ur * G::DATA_W);
-                    const f2 a2 = f2_pack(af[b], af[b]), m2 = f2_pack(mb_m[b], mb_m[b]);
-                    d01 = f2_fma(a2, f2_sub(f2_pack(e.x, e.y), m2), d01);
-                    d23 = f2_fma(a2, f2_sub(f2_pack(e.z, e.w), m2), d23);
-                }
-                f2_unpack(d01, d4.x, d4.y);
-                f2_unpack(d23, d4.z, d4.w);
+                // halo rows: D from its buffer; output rows: from the
+                // staged bands (row ur - RAD of each plane)
+                if (ur < RAD)
+                    d4 = lds4(dhl + ur * 128);
+                else if (ur >= RAD + TH)
+                    d4 = lds4(dhl + (ur - TH) * 128);
+                else
+                    d4 = mb_d([&](int b) {
+                        return lds4(reinterpret_cast<const float *>(dl) + b * G::PLANE +
+                                    (ur - RAD) * G::DATA_W);
+                    });
             } else {
                 d4 = S::ld4(dl + ur * G::DATA_W);
             }
@@ -809,7 +863,7 @@ __device__ __forceinline__ bool tile_step(const StepArgs &a, const CUtensorMap *
 #pragma unroll
                             for (int b = 0; b < NB; ++b) {
                                 const float4 e = lds4(reinterpret_cast<const float *>(dl) +
-                                                      b * G::PLANE + (ro + RAD) * G::DATA_W);
+                                                      b * G::PLANE + ro * G::DATA_W);
                                 const f2 e01 = f2_pack(e.x, e.y), e23 = f2_pack(e.z, e.w);
                                 psw[b] = f2_fma(e23, w23, f2_fma(e01, w01, psw[b]));
                                 if (need_sa) psa[b] = f2_add(psa[b], f2_add(e01, e23));
@@ -1186,19 +1240,29 @@ struct MbCoef {
     int zero;                   // R = 0 (degenerate rule, or M = 0)
 };
 
-// M = max over the candidate pixels of |D| (FP64), by the whole CTA; the
-// maximum does not depend on the order, so every CTA gets the same bits.
+// The band values of candidate i.
+__device__ __forceinline__ float4 mb_cand_ld(const LseCandidates *cand, int i)
+{
+    const float *p = cand->val[i];
+    return make_float4(__ldcg(p), __ldcg(p + 1), __ldcg(p + 2), __ldcg(p + 3));
+}
+
+// M = max over the n candidate pixels of |D| (FP64), by the whole CTA; v0
+// holds candidate threadIdx.x (read beforehand, with other loads), the rest
+// are read here.  The maximum does not depend on the order, so every CTA
+// gets the same bits.
 template <int NB>
-__device__ __forceinline__ double mb_norm(const LseCandidates *cand, const MbCoef<NB> &c)
+__device__ __forceinline__ double mb_norm(const LseCandidates *cand, const MbCoef<NB> &c,
+                                          int n, const float4 &v0)
 {
     __shared__ double s_m[32];
-    const int n = *reinterpret_cast<const volatile int *>(&cand->count);
     double m = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float4 v = i == (int)threadIdx.x ? v0 : mb_cand_ld(cand, i);
+        const float vb[4] = {v.x, v.y, v.z, v.w};
         double d = 0.0;
 #pragma unroll
-        for (int b = 0; b < NB; ++b)
-            d = fma(c.al[b], (double)__ldcg(&cand->val[i][b]) - c.md[b], d);
+        for (int b = 0; b < NB; ++b) d = fma(c.al[b], (double)vb[b] - c.md[b], d);
         m = fmax(m, fabs(d));
     }
 #pragma unroll
@@ -1258,6 +1322,12 @@ __device__ __forceinline__ void mb_evolve(const EvolveArgs &e, const CUtensorMap
     __shared__ int s_done, s_redo;
     __shared__ long long s_tot[NB];     // sum I_b over the image (lse_fix units)
     __shared__ double s_cp[NB], s_cm[NB];
+    // after each grid barrier: the step's slot, the status word and the
+    // candidate count, read in one wave (each a round trip to L2 that every
+    // CTA makes at once)
+    __shared__ long long s_sl[LSE_ACC_MISS + 1];
+    __shared__ unsigned int s_status;
+    __shared__ int s_ncand;
     bool have_tot = false;
     if (threadIdx.x == 0) {
         // the prologue made the first step's statistics
@@ -1272,7 +1342,9 @@ __device__ __forceinline__ void mb_evolve(const EvolveArgs &e, const CUtensorMap
     }
     tile_smem_init<RAD, float, NW>();   // ends with a CTA barrier
     {
-        const double m = mb_norm<NB>(cand, s_c);
+        const double m = mb_norm<NB>(cand, s_c,
+                                     *reinterpret_cast<const volatile int *>(&cand->count),
+                                     mb_cand_ld(cand, threadIdx.x));
         if (threadIdx.x == 0) {
             s_c.norm = m;
             if (!(m > 0.0)) s_c.zero = 1;
@@ -1305,9 +1377,22 @@ __device__ __forceinline__ void mb_evolve(const EvolveArgs &e, const CUtensorMap
             tile_step<0, RAD, false, float, NW, true, NB>(a, pm, &data_map, cta, ncta, &s_pc);
         if (threadIdx.x == 0) s_pc.stall_ns = 0;
         if (!grid_barrier(st, (unsigned int)(pass + 1) * (unsigned int)ncta)) break;
-        if (*reinterpret_cast<volatile unsigned int *>(&st->status_bits) & LSE_SBIT_ABORT) break;
+        float4 cv;      // candidate threadIdx.x (blockDim <= LSE_MB_CAND)
+        {
+            const int tid = threadIdx.x;
+            const volatile long long *slv = st->acc[pass % 3];
+            if (tid <= LSE_ACC_MISS)
+                s_sl[tid] = slv[tid];
+            else if (tid == LSE_ACC_MISS + 1)
+                s_status = *reinterpret_cast<volatile unsigned int *>(&st->status_bits);
+            else if (tid == LSE_ACC_MISS + 2)
+                s_ncand = *reinterpret_cast<const volatile int *>(&cand->count);
+            cv = mb_cand_ld(cand, tid);
+        }
+        __syncthreads();
+        if (s_status & LSE_SBIT_ABORT) break;
+        const long long *sl = s_sl;
         if (threadIdx.x == 0) {
-            const volatile long long *sl = st->acc[pass % 3];
             const unsigned long long miss = (unsigned long long)sl[LSE_ACC_MISS];
             bool redo = false;
             const bool more = n + 1 < e.cap;
@@ -1348,7 +1433,6 @@ __device__ __forceinline__ void mb_evolve(const EvolveArgs &e, const CUtensorMap
             // has a long latency on this part); sum I_b over the image is
             // that of the first step, whose tiles sum it the same way
             const int b = threadIdx.x;
-            const volatile long long *sl = st->acc[pass % 3];
             if (!have_tot) s_tot[b] = sl[LSE_ACC_SA + b];
             const long long np = sl[LSE_ACC_NP], nm = a.npix - np;
             const long long sw = sl[LSE_ACC_SW + b], sa = s_tot[b];
@@ -1371,7 +1455,6 @@ __device__ __forceinline__ void mb_evolve(const EvolveArgs &e, const CUtensorMap
         have_tot = have_tot || !s_redo;
         __syncthreads();
         if (threadIdx.x == 0) {
-            const volatile long long *sl = st->acc[pass % 3];
             if (!s_redo) {
                 // norm and zero of s_c are still those of the finished step
                 const long long np = sl[LSE_ACC_NP], nm = a.npix - np;
@@ -1415,7 +1498,7 @@ __device__ __forceinline__ void mb_evolve(const EvolveArgs &e, const CUtensorMap
         if (n < e.cap) {
             // M of the next step over the candidates (one added by a redo
             // is in place: CTA 0 wrote it before this barrier)
-            const double m = mb_norm<NB>(cand, s_c);
+            const double m = mb_norm<NB>(cand, s_c, s_ncand, cv);
             if (threadIdx.x == 0) {
                 s_c.norm = m;
                 if (!(m > 0.0)) s_c.zero = 1;

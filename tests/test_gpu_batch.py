@@ -209,3 +209,28 @@ def test_vector_images_beyond_one_group_launch(torch, ctx, use_graph):
         assert np.array_equal(m.cpu().numpy(), m1)
         assert st["iterations_run"] == st1["iterations_run"] == items[k]["iterations"]
         assert st["c_plus"] == st1["c_plus"]
+
+
+def test_vector_groups_by_band_count_and_radius(torch, ctx):
+    # 2, 3 and 4 bands at two template sizes, with and without the early
+    # stop: one group launch per (bands, radius), every image lse_evolve's bits
+    probs = scenes.batch_problems(18, seed=29, min_side=40, max_side=180, cap_range=(5, 30))
+    for k, q in enumerate(probs):
+        B = 2 + k % 3
+        q["image"] = np.ascontiguousarray(np.repeat(q["image"][:1], B, axis=0) *
+                                          np.linspace(1.0, 0.6, B, dtype=np.float32)[:, None, None])
+        q["term"] = "region"
+        q["early_stop_frac"] = 0.0 if k % 2 else 2e-3
+    items = device_items(torch, ctx, probs)
+    for k, it in enumerate(items):
+        it["ts"] = 9 if k % 4 < 2 else 7
+    res = ctx.evolve_batch(items, use_graph=False)
+    torch.cuda.synchronize()
+    for it, (v, m, st) in zip(items, res):
+        v1, m1, st1 = ctx.evolve(it["image"], it["phi0"], "region", ts=it["ts"],
+                                 iterations=it["iterations"],
+                                 early_stop_frac=it["early_stop_frac"])
+        torch.cuda.synchronize()
+        assert same_bits(v.cpu().numpy(), v1.cpu().numpy())
+        assert st["iterations_run"] == st1["iterations_run"]
+        assert st["last_flips"] == st1["last_flips"]
