@@ -3,6 +3,14 @@
 // tiles, every radius 1..7.
 #include "lse_step_tile.cuh"
 
+// At the default template (TS = 9, r = 4) a 4-band tile stages the bands of
+// its 24 output rows and keeps D of its 8 halo rows apart: 72.7 KB of
+// shared memory, so three CTAs share an SM (the measured 156 registers a
+// thread allow three as well).
+static_assert(lse_tile::TileGeo<4, float, 4, 4>::BYTES == 72704 &&
+                  lse_tile::TileGeo<4, float, 4, 4>::MIN_BLOCKS == 3,
+              "4-band tiles at r = 4: three CTAs per SM");
+
 namespace lse_detail {
 
 cudaError_t launch_evolve_mb4(const EvolveArgs &e, const CUtensorMap &pm0,
