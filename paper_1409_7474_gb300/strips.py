@@ -18,6 +18,14 @@ the normaliser of Eq. 17 are global.  Per iteration the driver therefore
   halo rows (only the sign when the next step re-initialises: one byte a
   pixel).
 
+With an exchange period of ``k`` steps (``partition(..., steps=k)``) the
+halo is ``h = k (r + 1)`` rows deep and the copy runs after every ``k``-th
+step only.  Each step spoils the ``r + 1`` rows next to a cut it cannot see
+past, so ``k`` steps leave the owned rows exact (temporal blocking of the
+halo).  Each exchange then carries ``k`` times the rows, but there are
+``1 / k`` as many; the ranks compute ``2 (k - 1) (r + 1)`` more rows a step.
+The statistics stay per iteration: they come from the owned rows.
+
 Once per evolution it also reduces the image's range (the one-band
 normaliser's closed form and the fixed-point scale) and ``sum I_b``.
 
@@ -53,7 +61,8 @@ except ImportError:  # the driver itself only needs numpy
 class Partition:
     """Rows of rank ``rank``: it owns image rows [y0, y1) and holds the strip
     [s0, s1) (owned rows plus ``halo`` rows on each side, clipped to the
-    image)."""
+    image).  ``steps``: steps between halo exchanges (the halo is that many
+    steps deep)."""
     H: int
     W: int
     rank: int
@@ -63,6 +72,7 @@ class Partition:
     y1: int
     s0: int
     s1: int
+    steps: int = 1
 
     @property
     def rows(self) -> int:
@@ -75,25 +85,35 @@ class Partition:
         return self.y0 - self.s0, self.y1 - self.s0
 
 
-def halo_rows(ts: int) -> int:
-    """Halo rows a strip needs for template size ts: r + 1."""
-    return (int(ts) - 1) // 2 + 1
+def halo_rows(ts: int, steps: int = 1) -> int:
+    """Halo rows a strip needs for template size ts to take ``steps`` steps
+    between exchanges: steps (r + 1)."""
+    return int(steps) * ((int(ts) - 1) // 2 + 1)
 
 
-def partition(H: int, W: int, ts: int, rank: int, world: int) -> Partition:
-    """Splits H rows into ``world`` runs of H // world or H // world + 1 rows
-    (the longer ones first).  Every rank must own at least the halo's rows,
-    so that a halo comes from one neighbour."""
+def owned_rows(H: int, rank: int, world: int) -> tuple[int, int]:
+    """The image rows [y0, y1) rank ``rank`` owns: ``world`` runs of
+    H // world or H // world + 1 rows, the longer ones first."""
+    base, extra = divmod(int(H), int(world))
+    y0 = rank * base + min(rank, extra)
+    return y0, y0 + base + (1 if rank < extra else 0)
+
+
+def partition(H: int, W: int, ts: int, rank: int, world: int, steps: int = 1) -> Partition:
+    """Splits H rows over ``world`` ranks (``owned_rows``) with halos deep
+    enough for ``steps`` steps between exchanges.  Every rank must own at
+    least the halo's rows, so that a halo comes from one neighbour."""
     if world < 1 or not 0 <= rank < world:
         raise ValueError(f"rank {rank} outside a world of {world}")
-    h = halo_rows(ts)
-    base, extra = divmod(int(H), int(world))
-    if base < h:
+    if int(steps) < 1:
+        raise ValueError(f"steps between exchanges must be at least 1, not {steps}")
+    h = halo_rows(ts, steps)
+    if int(H) // int(world) < h:
         raise ValueError(f"{H} rows over {world} ranks leave fewer than the {h} halo rows "
-                         f"a rank must own (ts = {ts})")
-    y0 = rank * base + min(rank, extra)
-    y1 = y0 + base + (1 if rank < extra else 0)
-    return Partition(int(H), int(W), rank, world, h, y0, y1, max(0, y0 - h), min(H, y1 + h))
+                         f"a rank must own (ts = {ts}, {steps} steps between exchanges)")
+    y0, y1 = owned_rows(H, rank, world)
+    return Partition(int(H), int(W), rank, world, h, y0, y1, max(0, y0 - h), min(H, y1 + h),
+                     int(steps))
 
 
 # ---------------------------------------------------------------- communicators
@@ -309,7 +329,8 @@ def evolve(comm, compute, part: Partition, phi0, *, term: str = "region", bands:
             norm = float(comm.all_reduce(np.array([d], dtype=np.float64), "max")[0])
         v = compute.step(phi, binarise_in, tot, norm)
         reinit = reinit_after(n, reinit_period)
-        v = exchange_halo(comm, part, v, binary=reinit)
+        if (n + 1) % part.steps == 0:
+            v = exchange_halo(comm, part, v, binary=reinit)
         tot = _reduce_partials(comm, compute.partials(v, phi, tot.fix_k), False, tot)
         n_run = n + 1
         phi = v
@@ -355,7 +376,8 @@ def _evolve_device(comm, compute, part, phi0, tot, region, B, iterations, reinit
     for n in range(int(iterations)):
         v = compute.step(phi, binarise_in, rec, 0.0)
         reinit = reinit_after(n, reinit_period)
-        v = exchange_halo(comm, part, v, binary=reinit)
+        if (n + 1) % part.steps == 0:
+            v = exchange_halo(comm, part, v, binary=reinit)
         rec = reduce(compute.partials_device(v, phi, tot.fix_k))
         n_run = n + 1
         phi = v
@@ -404,8 +426,8 @@ def gather_rows(comm, part: Partition, v):
     if part.rank == 0:
         rows = [own_t.cpu()]
         for r in range(1, part.world):
-            pr = partition(part.H, part.W, 2 * part.halo - 1, r, part.world)
-            buf = torch.empty((pr.y1 - pr.y0, part.W), dtype=own_t.dtype, device=own_t.device)
+            y0, y1 = owned_rows(part.H, r, part.world)
+            buf = torch.empty((y1 - y0, part.W), dtype=own_t.dtype, device=own_t.device)
             comm.recv(buf, r)
             rows.append(buf.cpu())
         return torch.cat(rows).numpy()

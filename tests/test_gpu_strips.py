@@ -97,14 +97,14 @@ class ThreadComm:
 
 
 def run_split(torch, lse, world, img, phi0, g, term, ts, iterations, period, frac,
-              device_sums=None):
-    """The strip driver over `world` thread ranks; returns the whole v
-    (owned rows stacked) and rank 0's statistics."""
+              device_sums=None, steps=1):
+    """The strip driver over `world` thread ranks, halos `steps` steps deep;
+    returns the whole v (owned rows stacked) and rank 0's statistics."""
     B = img.shape[0] if img is not None else 1
     H, W = phi0.shape
     w = ThreadComm.World(world)
     out, errors = {}, []
-    parts = [strips.partition(H, W, ts, r, world) for r in range(world)]
+    parts = [strips.partition(H, W, ts, r, world, steps=steps) for r in range(world)]
     ctxs = [lse.Context(0, max_pixels=parts[r].rows * W, max_bands=max(B, 1))
             for r in range(world)]
 
@@ -176,7 +176,11 @@ def test_split_runs_agree(torch, lse, case):
     runs["host"] = run_split(torch, lse, 2, img, phi0, g, term, ts, iters, period, frac,
                              device_sums=False)
     assert np.array_equal(runs["host"][0].view(np.uint32), v1.view(np.uint32))
-    for n in (2, 3):
+    # halos two and three steps deep, exchanged after every second / third step
+    for n, k in ((2, 2), (3, 3)):
+        runs[(n, k)] = run_split(torch, lse, n, img, phi0, g, term, ts, iters, period, frac,
+                                 steps=k)
+    for n in (2, 3, (2, 2), (3, 3)):
         vn, stn, all_st = runs[n]
         # the bits of the unsplit run, and the same statistics on every rank
         assert np.array_equal(vn.view(np.uint32), v1.view(np.uint32)), n

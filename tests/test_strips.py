@@ -53,10 +53,11 @@ def whole_image(case):
                          reinit_period=period, early_stop_frac=frac)
 
 
-def run_strips(comm, case, rank, world):
+def run_strips(comm, case, rank, world, steps=1, part=None):
     H, W, B, term, ts, iters, period, frac = case
     img, phi0, g = case_inputs(H, W, B, term, ts)
-    part = strips.partition(H, W, ts, rank, world)
+    if part is None:
+        part = strips.partition(H, W, ts, rank, world, steps=steps)
     sl = slice(part.s0, part.s1)
     comp = OracleCompute(part, img[:, sl] if term == "region" else None,
                          g[sl] if g is not None else None, term=term, ts=ts)
@@ -83,18 +84,20 @@ def compare(case, part, v_own, st):
 
 
 # ---------------------------------------------------------------- partition
-@pytest.mark.parametrize("H,world,ts", [(37, 2, 9), (37, 3, 9), (100, 7, 15), (10, 2, 3)])
-def test_partition_covers_rows_once(H, world, ts):
-    parts = [strips.partition(H, 17, ts, r, world) for r in range(world)]
-    h = strips.halo_rows(ts)
+@pytest.mark.parametrize("H,world,ts,steps", [(37, 2, 9, 1), (37, 3, 9, 1), (100, 7, 15, 1),
+                                               (10, 2, 3, 1), (37, 3, 9, 2), (100, 4, 7, 3)])
+def test_partition_covers_rows_once(H, world, ts, steps):
+    parts = [strips.partition(H, 17, ts, r, world, steps=steps) for r in range(world)]
+    h = strips.halo_rows(ts, steps)
     assert parts[0].y0 == 0 and parts[-1].y1 == H
     for p, q in zip(parts, parts[1:]):
         assert p.y1 == q.y0
     sizes = [p.y1 - p.y0 for p in parts]
     assert max(sizes) - min(sizes) <= 1 and min(sizes) >= h
-    for p in parts:
-        assert p.halo == h == (ts - 1) // 2 + 1
+    for r, p in enumerate(parts):
+        assert p.halo == h == steps * ((ts - 1) // 2 + 1) and p.steps == steps
         assert p.s0 == max(0, p.y0 - h) and p.s1 == min(H, p.y1 + h)
+        assert (p.y0, p.y1) == strips.owned_rows(H, r, world)
         a, b = p.own
         assert b - a == p.y1 - p.y0 and p.rows == p.s1 - p.s0
 
@@ -104,6 +107,10 @@ def test_partition_refuses_thin_strips():
         strips.partition(9, 8, 9, 0, 2)            # 4 rows a rank, halo 5
     with pytest.raises(ValueError):
         strips.partition(20, 8, 9, 2, 2)
+    with pytest.raises(ValueError):
+        strips.partition(37, 8, 9, 0, 3, steps=3)  # 12 rows a rank, halo 15
+    with pytest.raises(ValueError):
+        strips.partition(37, 8, 9, 0, 2, steps=0)
 
 
 def test_reinit_schedule():
@@ -171,6 +178,28 @@ def _worker(rank, world, port, out):
                     res["gathered_err"] = float(np.max(np.abs(full - whole_image(case)[0])))
                 else:
                     res["gathered_none"] = full is None
+        # halos k steps deep, exchanged after every k-th step: the owned rows
+        # stay the whole image's (k = 2 for every case; k = 3 where each
+        # rank owns 3 (r + 1) rows)
+        # Each case runs in full and stopped after 3 iterations, before
+        # re-initialisation can wash out an error next to a cut
+        for i, case in enumerate(CASES):
+            short = case[:5] + (min(case[5], 3),) + case[6:]
+            for k in (2, 3):
+                if case[0] // world >= k * ((case[4] - 1) // 2 + 1):
+                    for tag, c in (("full", case), ("short", short)):
+                        p, v_own, st, calls = run_strips(comm, c, rank, world, steps=k)
+                        res[("steps", i, k, tag)] = compare(c, p, v_own, st)
+        # k steps between exchanges over a halo one step deep: rows next to
+        # a cut go wrong.  The case that re-initialises every third step,
+        # stopped after 3 iterations: the stale rows' values, not only their
+        # signs, reach the owned rows, and the later re-initialisations
+        # would wash the error out again
+        import dataclasses
+        c = CASES[1][:5] + (3,) + CASES[1][6:]
+        p1 = S.partition(c[0], c[1], c[4], rank, world)
+        p, v_own, st, _ = run_strips(comm, c, rank, world, part=dataclasses.replace(p1, steps=2))
+        res["shallow"] = compare(c, p, v_own, st)
         # a driver whose halo exchange does nothing
         real = S.exchange_halo
         S.exchange_halo = lambda comm, part, v, binary: v
@@ -226,5 +255,14 @@ def test_gloo_ranks_reproduce_the_whole_image(world):
             assert diff == [] and bad == 0 and err < 1e-9, (case, r, err, bad, diff)
     assert res[0]["gathered_err"] < 1e-9
     assert all(res[r]["gathered_none"] for r in range(1, world))
+    # k-step halos: every case at k = 2, the ones that fit at k = 3
+    ks = sorted({key[2] for key in res[0] if isinstance(key, tuple)})
+    assert ks == [2, 3]
+    for key in res[0]:
+        if isinstance(key, tuple):
+            for r in range(world):
+                err, bad, diff, _ = res[r][key]
+                assert diff == [] and bad == 0 and err < 1e-9, (key, r, err, bad, diff)
+    assert any(res[r]["shallow"][0] > 1e-3 or res[r]["shallow"][1] > 0 for r in range(world))
     # without the exchange the rows next to a cut go wrong
     assert any(res[r]["no_halo"][0] > 1e-3 or res[r]["no_halo"][1] > 0 for r in range(world))
