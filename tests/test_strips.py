@@ -190,6 +190,17 @@ def _worker(rank, world, port, out):
                     for tag, c in (("full", case), ("short", short)):
                         p, v_own, st, calls = run_strips(comm, c, rank, world, steps=k)
                         res[("steps", i, k, tag)] = compare(c, p, v_own, st)
+        # the exchanges a k-step run makes: one after every k-th step
+        sent = []
+        real_exchange = comm.exchange
+        comm.exchange = lambda *args: sent.append(1) or real_exchange(*args)
+        try:
+            for k in (1, 2, 3):
+                sent.clear()
+                run_strips(comm, CASES[3][:5] + (7, 1, 0.0), rank, world, steps=k)
+                res[("exchanges", k)] = len(sent)
+        finally:
+            comm.exchange = real_exchange
         # k steps between exchanges over a halo one step deep: rows next to
         # a cut go wrong.  The case that re-initialises every third step,
         # stopped after 3 iterations: the stale rows' values, not only their
@@ -256,10 +267,12 @@ def test_gloo_ranks_reproduce_the_whole_image(world):
     assert res[0]["gathered_err"] < 1e-9
     assert all(res[r]["gathered_none"] for r in range(1, world))
     # k-step halos: every case at k = 2, the ones that fit at k = 3
-    ks = sorted({key[2] for key in res[0] if isinstance(key, tuple)})
+    ks = sorted({key[2] for key in res[0] if isinstance(key, tuple) and key[0] == "steps"})
     assert ks == [2, 3]
+    for r in range(world):
+        assert [res[r][("exchanges", k)] for k in (1, 2, 3)] == [7, 3, 2]
     for key in res[0]:
-        if isinstance(key, tuple):
+        if isinstance(key, tuple) and key[0] == "steps":
             for r in range(world):
                 err, bad, diff, _ = res[r][key]
                 assert diff == [] and bad == 0 and err < 1e-9, (key, r, err, bad, diff)
