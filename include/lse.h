@@ -534,9 +534,12 @@ lse_status lse_strip_dmax(lse_ctx *ctx, const void *image, lse_dtype dtype, int 
  *               lse_strip_dmax; ignored otherwise (one band takes max|D|
  *               in closed form from the totals' range).
  *   v_out       Hs x W float32: v of this iteration, host or device (not
- *               phi's buffer).  Rows within h of a cut edge of the strip (an
- *               edge that is not the image's) are not the whole image's: the
- *               neighbours' halo exchange replaces them.
+ *               phi's buffer).  The r + 1 rows (r = (ts - 1) / 2) next to a
+ *               cut edge of the strip (an edge that is not the image's) are
+ *               not the whole image's, and each further step without an
+ *               exchange spoils r + 1 more: a strip with halos k (r + 1)
+ *               rows deep takes k steps before the neighbours' halo
+ *               exchange must replace them.
  * Device buffers with W a multiple of 4 and 16-byte alignment (phi, v_out
  * and the image or g) are read and written in place; others are staged.
  * With v_out in host memory the call synchronises `stream` and returns
